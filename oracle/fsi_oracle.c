@@ -1,0 +1,592 @@
+/*
+ * fsi_oracle.c -- plain, slow, FP64 CPU restatement of the hot path of BIFROST's
+ * fourth-order forward symplectic integrator (Rantala et al. 2022, arXiv 2210.02472).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the oracle that the CUDA library is checked
+ * against.  Only the test suite, the package smoke check and the CPU-baseline leg of the
+ * benchmark may load it.  It shares no code, header, table or constant with the CUDA
+ * path, and it never reads anything the CUDA path computed.
+ *
+ * Every routine is a direct double loop over particle pairs in the order the paper's
+ * equations are written, in FP64 with libm's correctly rounded sqrt.  There is no
+ * blocking, no fusion and no reordering of the sums beyond the loop order stated.
+ *
+ * Layout: positions, velocities and accelerations are structure-of-arrays, 3 x N
+ * doubles (all x, then all y, then all z).  Index lists are int32 global particle ids;
+ * a NULL list means "all N particles in order".  Per-set outputs are 3 x n, in the
+ * order of the index list.
+ *
+ * Pins (checked by the CPU test suite against closed forms, finite differences,
+ * brute force and invariants): see the tests directory.  Every function here is pinned;
+ * none is "parity unpinned".
+ */
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+#define OR_OK 0
+#define OR_ERR_ARG (-1)
+#define OR_ERR_NOMEM (-2)
+#define OR_ERR_COINCIDENT (-4)
+#define OR_ERR_MAXLEVEL (-6)
+
+/* ------------------------------------------------------------------------------- */
+static int or_threads = 1;
+
+void or_set_threads(int n) { or_threads = n > 0 ? n : 1; }
+int or_get_threads(void) { return or_threads; }
+
+static int idx_at(const int *list, int k) { return list ? list[k] : k; }
+
+/* ------------------------------------------------------------------------------- *
+ * Newtonian acceleration, Sect. 2.1 Eq. (new-newton-acc):
+ *   a_i = sum_{j in B, j != i} G m_j r_ji / |r_ji|^3,  r_ji = r_j - r_i,  G = 1.
+ * With Plummer softening |r_ji|^2 -> |r_ji|^2 + eps2.  Self pairs are excluded by
+ * global index.  Two distinct particles at the same point with eps2 == 0 make the
+ * sum undefined: the routine returns OR_ERR_COINCIDENT.
+ * ------------------------------------------------------------------------------- */
+int or_acc(int N, const double *pos, const double *mass,
+           const int *A, int nA, const int *B, int nB, double eps2, double *acc)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    int err = OR_OK;
+    int k;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (k = 0; k < nA; ++k) {
+        int i = idx_at(A, k);
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int l = 0; l < nB; ++l) {
+            int j = idx_at(B, l);
+            if (j == i) continue;
+            double dx = X[j] - X[i], dy = Y[j] - Y[i], dz = Z[j] - Z[i];
+            double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double r = sqrt(r2);
+            double f = mass[j] / (r2 * r);
+            ax += f * dx;
+            ay += f * dy;
+            az += f * dz;
+        }
+        acc[k] = ax;
+        acc[(size_t)nA + k] = ay;
+        acc[2 * (size_t)nA + k] = az;
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------------- *
+ * Force-gradient sum of the gradient acceleration, Sect. 2.1 Eq. (new-grad-acc):
+ *   G_i = sum_{j in B, j != i} G m_j / |r_ji|^5 ( |r_ji|^2 a_ji - 3 (a_ji . r_ji) r_ji ),
+ *   a_ji = a_j - a_i,
+ * so that the gradient acceleration is  a~_i = a_i + (eps^2 / 24) G_i.  The
+ * accelerations are read from accg, a 3 x N array indexed by global particle id; the
+ * caller fills it with the accelerations of the same splitting term (Sect. 2.2).
+ * With softening, |r|^2 -> |r|^2 + eps2 in both powers (the exact softened Jacobian).
+ * ------------------------------------------------------------------------------- */
+int or_grad(int N, const double *pos, const double *mass, const double *accg,
+            const int *A, int nA, const int *B, int nB, double eps2, double *grad)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    const double *AX = accg, *AY = accg + N, *AZ = accg + 2 * (size_t)N;
+    int err = OR_OK;
+    int k;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (k = 0; k < nA; ++k) {
+        int i = idx_at(A, k);
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int l = 0; l < nB; ++l) {
+            int j = idx_at(B, l);
+            if (j == i) continue;
+            double dx = X[j] - X[i], dy = Y[j] - Y[i], dz = Z[j] - Z[i];
+            double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double bx = AX[j] - AX[i], by = AY[j] - AY[i], bz = AZ[j] - AZ[i];
+            double r = sqrt(r2);
+            double r5 = r2 * r2 * r;
+            double f = mass[j] / r5;
+            double adotr = bx * dx + by * dy + bz * dz;
+            gx += f * (r2 * bx - 3.0 * adotr * dx);
+            gy += f * (r2 * by - 3.0 * adotr * dy);
+            gz += f * (r2 * bz - 3.0 * adotr * dz);
+        }
+        grad[k] = gx;
+        grad[(size_t)nA + k] = gy;
+        grad[2 * (size_t)nA + k] = gz;
+    }
+    return err;
+}
+
+/* 1 if the two lists hold the same ids in the same order, 0 if they share no id,
+ * -1 otherwise (partial overlap has no meaning for a splitting term). */
+static int classify_sets(int N, const int *A, int nA, const int *B, int nB)
+{
+    if (nA == nB) {
+        int same = 1;
+        for (int k = 0; k < nA; ++k)
+            if (idx_at(A, k) != idx_at(B, k)) { same = 0; break; }
+        if (same) return 1;
+    }
+    unsigned char *mark = (unsigned char *)calloc((size_t)N, 1);
+    if (!mark) return -2;
+    for (int k = 0; k < nA; ++k) mark[idx_at(A, k)] = 1;
+    int overlap = 0;
+    for (int l = 0; l < nB; ++l)
+        if (mark[idx_at(B, l)]) { overlap = 1; break; }
+    free(mark);
+    return overlap ? -1 : 0;
+}
+
+/* Scatter a 3 x n per-set array into a 3 x N global-id array. */
+static void scatter3(int N, const int *list, int n, const double *src, double *dstg)
+{
+    for (int k = 0; k < n; ++k) {
+        int i = idx_at(list, k);
+        dstg[i] = src[k];
+        dstg[(size_t)N + i] = src[(size_t)n + k];
+        dstg[2 * (size_t)N + i] = src[2 * (size_t)n + k];
+    }
+}
+
+/* ------------------------------------------------------------------------------- *
+ * acc(A <- B) and the gradient sum G(A <- B) of one splitting term.
+ *  - A and B the same list: the term is the set's self-interaction (FSI, Sect. 2.1);
+ *    the accelerations inside G are acc(A <- A).
+ *  - A and B disjoint: the term is the slow-fast inter-level interaction (Sect. 2.2);
+ *    a_i = acc(A <- B) for i in A and a_j = acc(B <- A) for j in B.
+ * Any other overlap is rejected with OR_ERR_ARG.
+ * ------------------------------------------------------------------------------- */
+int or_accel_grad(int N, const double *pos, const double *mass,
+                  const int *A, int nA, const int *B, int nB, double eps2,
+                  double *acc_out, double *grad_out)
+{
+    int kind = classify_sets(N, A, nA, B, nB);
+    if (kind == -2) return OR_ERR_NOMEM;
+    if (kind < 0) return OR_ERR_ARG;
+    double *accg = (double *)calloc(3 * (size_t)N, sizeof(double));
+    double *tmp = (double *)malloc(3 * (size_t)(nB > 0 ? nB : 1) * sizeof(double));
+    if (!accg || !tmp) { free(accg); free(tmp); return OR_ERR_NOMEM; }
+    int err = or_acc(N, pos, mass, A, nA, B, nB, eps2, acc_out);
+    scatter3(N, A, nA, acc_out, accg);
+    if (kind == 0 && err == OR_OK) {
+        err = or_acc(N, pos, mass, B, nB, A, nA, eps2, tmp);
+        scatter3(N, B, nB, tmp, accg);
+    }
+    if (err == OR_OK)
+        err = or_grad(N, pos, mass, accg, A, nA, B, nB, eps2, grad_out);
+    free(accg);
+    free(tmp);
+    return err;
+}
+
+/* ------------------------------------------------------------------------------- *
+ * PN1.0 pair acceleration (Sect. 3.9, Eqs. subsyspn-mass and the FSI+PN splitting).
+ * The paper does not print the pair formula; it takes the PN terms of Thorne (1985)
+ * and the Einstein-Infeld-Hoffmann equations restricted to pairs.  The two-body 1PN
+ * EIH acceleration of body i due to body j in harmonic coordinates, with
+ * n = (x_i - x_j)/r, is
+ *   a_i = (G m_j / (c^2 r^2)) { n [ -v_i^2 - 2 v_j^2 + 4 v_i.v_j + 3/2 (n.v_j)^2
+ *                                   + 5 G m_i / r + 4 G m_j / r ]
+ *                               + (v_i - v_j) [ 4 n.v_i - 3 n.v_j ] }.
+ * A pair contributes only when at least one member is flagged as a black hole (the
+ * mass cut of Eq. subsyspn-mass, read as m > m_PN).  No softening is applied.
+ * For i in A the sum runs over j in B, j != i.
+ * ------------------------------------------------------------------------------- */
+int or_pn_acc(int N, const double *pos, const double *vel, const double *mass,
+              const unsigned char *is_bh, double c,
+              const int *A, int nA, const int *B, int nB, double *out)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    const double *VX = vel, *VY = vel + N, *VZ = vel + 2 * (size_t)N;
+    double ic2 = 1.0 / (c * c);
+    int err = OR_OK;
+    int k;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (k = 0; k < nA; ++k) {
+        int i = idx_at(A, k);
+        double px = 0.0, py = 0.0, pz = 0.0;
+        for (int l = 0; l < nB; ++l) {
+            int j = idx_at(B, l);
+            if (j == i) continue;
+            if (!is_bh[i] && !is_bh[j]) continue;
+            double rx = X[i] - X[j], ry = Y[i] - Y[j], rz = Z[i] - Z[j];
+            double r = sqrt(rx * rx + ry * ry + rz * rz);
+            if (r == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double nx = rx / r, ny = ry / r, nz = rz / r;
+            double vi2 = VX[i] * VX[i] + VY[i] * VY[i] + VZ[i] * VZ[i];
+            double vj2 = VX[j] * VX[j] + VY[j] * VY[j] + VZ[j] * VZ[j];
+            double vivj = VX[i] * VX[j] + VY[i] * VY[j] + VZ[i] * VZ[j];
+            double nvi = nx * VX[i] + ny * VY[i] + nz * VZ[i];
+            double nvj = nx * VX[j] + ny * VY[j] + nz * VZ[j];
+            double cn = -vi2 - 2.0 * vj2 + 4.0 * vivj + 1.5 * nvj * nvj
+                        + 5.0 * mass[i] / r + 4.0 * mass[j] / r;
+            double cv = 4.0 * nvi - 3.0 * nvj;
+            double pre = mass[j] * ic2 / (r * r);
+            px += pre * (cn * nx + cv * (VX[i] - VX[j]));
+            py += pre * (cn * ny + cv * (VY[i] - VY[j]));
+            pz += pre * (cn * nz + cv * (VZ[i] - VZ[j]));
+        }
+        out[k] = px;
+        out[(size_t)nA + k] = py;
+        out[2 * (size_t)nA + k] = pz;
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------------- *
+ * Energy, Sect. 2.1 (the Hamiltonian):
+ *   T = sum_i 1/2 m_i |v_i|^2,  W = - sum_{i<j} G m_i m_j / sqrt(|r_ij|^2 + eps2),
+ * over the listed set.
+ * ------------------------------------------------------------------------------- */
+int or_energy(int N, const double *pos, const double *vel, const double *mass,
+              const int *P, int n, double eps2, double *ekin, double *epot)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    const double *VX = vel, *VY = vel + N, *VZ = vel + 2 * (size_t)N;
+    double t = 0.0, w = 0.0;
+    int err = OR_OK;
+    for (int k = 0; k < n; ++k) {
+        int i = idx_at(P, k);
+        t += 0.5 * mass[i] * (VX[i] * VX[i] + VY[i] * VY[i] + VZ[i] * VZ[i]);
+    }
+    int k;
+#pragma omp parallel for schedule(dynamic, 16) reduction(+ : w) num_threads(or_threads)
+    for (k = 0; k < n; ++k) {
+        int i = idx_at(P, k);
+        for (int l = k + 1; l < n; ++l) {
+            int j = idx_at(P, l);
+            double dx = X[j] - X[i], dy = Y[j] - Y[i], dz = Z[j] - Z[i];
+            double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            w -= mass[i] * mass[j] / sqrt(r2);
+        }
+    }
+    *ekin = t;
+    *epot = w;
+    return err;
+}
+
+/* ------------------------------------------------------------------------------- */
+typedef struct {
+    double eps2;
+    double c;                    /* speed of light; 0 switches the PN1.0 term off */
+    const unsigned char *is_bh;  /* black-hole flags, N entries (may be NULL if c == 0) */
+} or_force_params;
+
+static void kick(int N, double *vel, const int *P, int n, const double *a, double w)
+{
+    for (int k = 0; k < n; ++k) {
+        int i = idx_at(P, k);
+        vel[i] += w * a[k];
+        vel[(size_t)N + i] += w * a[(size_t)n + k];
+        vel[2 * (size_t)N + i] += w * a[2 * (size_t)n + k];
+    }
+}
+
+static void drift(int N, double *pos, const double *vel, const int *P, int n, double w)
+{
+    for (int k = 0; k < n; ++k) {
+        int i = idx_at(P, k);
+        pos[i] += w * vel[i];
+        pos[(size_t)N + i] += w * vel[(size_t)N + i];
+        pos[2 * (size_t)N + i] += w * vel[2 * (size_t)N + i];
+    }
+}
+
+/* PN1.0 kick of the pairs (A x B), both directions for disjoint sets: all PN
+ * accelerations are evaluated from the velocities at the start of the kick, then
+ * applied (Sect. 3.9, the half-kicks that wrap the FSI). */
+static int pn_kick(int N, const double *pos, double *vel, const double *mass,
+                   const or_force_params *fp, const int *A, int nA,
+                   const int *B, int nB, int same, double w)
+{
+    if (fp == NULL || fp->c <= 0.0 || w == 0.0) return OR_OK;
+    double *aA = (double *)malloc(3 * (size_t)(nA > 0 ? nA : 1) * sizeof(double));
+    double *aB = (double *)malloc(3 * (size_t)(nB > 0 ? nB : 1) * sizeof(double));
+    if (!aA || !aB) { free(aA); free(aB); return OR_ERR_NOMEM; }
+    int err = or_pn_acc(N, pos, vel, mass, fp->is_bh, fp->c, A, nA, B, nB, aA);
+    if (!same && err == OR_OK)
+        err = or_pn_acc(N, pos, vel, mass, fp->is_bh, fp->c, B, nB, A, nA, aB);
+    if (err == OR_OK) {
+        kick(N, vel, A, nA, aA, w);
+        if (!same) kick(N, vel, B, nB, aB, w);
+    }
+    free(aA);
+    free(aB);
+    return err;
+}
+
+/* ------------------------------------------------------------------------------- *
+ * One FSI cycle of step h on the listed set, interacting with itself only
+ * (Sect. 2.1, Eq. fsi-cycle):
+ *   kick h/6 with a;  drift h/2;  kick 2h/3 with a~ = a + (h^2/24) G;  drift h/2;
+ *   kick h/6 with a,
+ * every acceleration evaluated at the current positions.  With the PN1.0 term on,
+ * PN half-kicks of h/2 wrap the cycle (Sect. 3.9).
+ * ------------------------------------------------------------------------------- */
+int or_fsi_step(int N, double *pos, double *vel, const double *mass,
+                const int *P, int n, double h, const or_force_params *fp)
+{
+    if (n <= 0) return OR_OK;
+    double eps2 = fp ? fp->eps2 : 0.0;
+    double *a = (double *)malloc(3 * (size_t)n * sizeof(double));
+    double *g = (double *)malloc(3 * (size_t)n * sizeof(double));
+    double *a3 = (double *)malloc(3 * (size_t)n * sizeof(double));
+    if (!a || !g || !a3) { free(a); free(g); free(a3); return OR_ERR_NOMEM; }
+    int err = pn_kick(N, pos, vel, mass, fp, P, n, P, n, 1, 0.5 * h);
+    if (err == OR_OK) err = or_acc(N, pos, mass, P, n, P, n, eps2, a);
+    if (err == OR_OK) {
+        kick(N, vel, P, n, a, h / 6.0);
+        drift(N, pos, vel, P, n, 0.5 * h);
+        err = or_accel_grad(N, pos, mass, P, n, P, n, eps2, a, g);
+    }
+    if (err == OR_OK) {
+        for (size_t q = 0; q < 3 * (size_t)n; ++q) a3[q] = a[q] + (h * h / 24.0) * g[q];
+        kick(N, vel, P, n, a3, 2.0 * h / 3.0);
+        drift(N, pos, vel, P, n, 0.5 * h);
+        err = or_acc(N, pos, mass, P, n, P, n, eps2, a);
+    }
+    if (err == OR_OK) {
+        kick(N, vel, P, n, a, h / 6.0);
+        err = pn_kick(N, pos, vel, mass, fp, P, n, P, n, 1, 0.5 * h);
+    }
+    free(a);
+    free(g);
+    free(a3);
+    return err;
+}
+
+/* ------------------------------------------------------------------------------- *
+ * Time steps of the listed set against itself (Sect. 3.4):
+ *   free fall  eps_ff = eta_ff min_{j != i} ( |r_ij|^3 / (G (m_i + m_j)) )^{1/2},
+ *   fly-by     eps_fb = eta_fb min_{j != i} |r_ij| / |v_ij|,
+ *   jerk       eps_j  = eta_j |a_i| / |j_i|,
+ *              j_i = sum_{j != i} G m_j / |r_ji|^5 ( |r_ji|^2 v_ji - 3 (r_ji . v_ji) r_ji ),
+ * the step being the minimum of the three.  A pair at zero relative speed gives no
+ * fly-by bound and a zero jerk gives no jerk bound (both +inf).  The free-fall and
+ * fly-by distances are unsoftened; a_i and j_i use the softened kernel of the force.
+ * ------------------------------------------------------------------------------- */
+int or_timesteps(int N, const double *pos, const double *vel, const double *mass,
+                 const int *P, int n, double eta_ff, double eta_fb, double eta_jerk,
+                 double eps2, double *step)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    const double *VX = vel, *VY = vel + N, *VZ = vel + 2 * (size_t)N;
+    int err = OR_OK;
+    int k;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (k = 0; k < n; ++k) {
+        int i = idx_at(P, k);
+        double ff2 = INFINITY, fb = INFINITY;
+        double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+        for (int l = 0; l < n; ++l) {
+            int j = idx_at(P, l);
+            if (j == i) continue;
+            double dx = X[j] - X[i], dy = Y[j] - Y[i], dz = Z[j] - Z[i];
+            double ux = VX[j] - VX[i], uy = VY[j] - VY[i], uz = VZ[j] - VZ[i];
+            double d2 = dx * dx + dy * dy + dz * dz;
+            double s2 = d2 + eps2;
+            if (s2 == 0.0 || d2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double d = sqrt(d2);
+            double t2 = d2 * d / (mass[i] + mass[j]);
+            if (t2 < ff2) ff2 = t2;
+            double u2 = ux * ux + uy * uy + uz * uz;
+            if (u2 > 0.0) {
+                double t = d / sqrt(u2);
+                if (t < fb) fb = t;
+            }
+            double s = sqrt(s2);
+            double f3 = mass[j] / (s2 * s);
+            double f5 = f3 / s2;
+            double rv = dx * ux + dy * uy + dz * uz;
+            ax += f3 * dx; ay += f3 * dy; az += f3 * dz;
+            jx += f5 * (s2 * ux - 3.0 * rv * dx);
+            jy += f5 * (s2 * uy - 3.0 * rv * dy);
+            jz += f5 * (s2 * uz - 3.0 * rv * dz);
+        }
+        double e = eta_ff * sqrt(ff2);
+        double efb = eta_fb * fb;
+        if (efb < e) e = efb;
+        double jn = sqrt(jx * jx + jy * jy + jz * jz);
+        if (jn > 0.0) {
+            double ej = eta_jerk * sqrt(ax * ax + ay * ay + az * az) / jn;
+            if (ej < e) e = ej;
+        }
+        step[k] = e;
+    }
+    return err;
+}
+
+/* ------------------------------------------------------------------------------- *
+ * Hierarchical Hamiltonian splitting with the FSI (Sect. 2.2, Eq. hhsfsi-cycle),
+ * literal reading: a level of pivot tau over set P
+ *   1. assigns time steps against P (level 0: against all N, stored as the level-0
+ *      steps; deeper levels take min(eps_i, eps_i^{level 0}), Sect. 3.4),
+ *   2. splits S = {eps_i >= tau}, F = {eps_i < tau} (at max_level, S = P),
+ *   3. runs  U_SF(tau/6)  FSI(S, tau/2)  HHS(F, tau/2)  U~_SF(2 tau/3)  HHS(F, tau/2)
+ *            FSI(S, tau/2)  U_SF(tau/6),
+ *      where U_SF kicks S with acc(S <- F) and F with acc(F <- S), and U~_SF uses the
+ *      gradient accelerations of the same inter-level term with eps = tau.
+ * With the PN1.0 term on, S-S pairs get the half-kicks that wrap each FSI(S, .) and
+ * S-F pairs get PN kicks of tau/2 together with the opening and closing U_SF.
+ * ------------------------------------------------------------------------------- */
+typedef struct {
+    double eta_ff, eta_fb, eta_jerk;
+    double eps2;
+    double c;
+    const unsigned char *is_bh;
+    int max_level;
+    const double *fixed_steps;   /* if non-NULL: eps_i = fixed_steps[i] at every level */
+} or_hhs_params;
+
+typedef struct {
+    int N;
+    double *pos, *vel;
+    const double *mass;
+    const or_hhs_params *p;
+    double *step0;        /* level-0 steps, global id */
+    long long *level_counts;
+    int max_level_hit;
+} hhs_ctx;
+
+static int cross_kick(hhs_ctx *c, const int *S, int nS, const int *F, int nF,
+                      double w, int gradient, double eps)
+{
+    int N = c->N;
+    double *aS = (double *)malloc(3 * (size_t)nS * sizeof(double));
+    double *aF = (double *)malloc(3 * (size_t)nF * sizeof(double));
+    double *gS = (double *)malloc(3 * (size_t)nS * sizeof(double));
+    double *gF = (double *)malloc(3 * (size_t)nF * sizeof(double));
+    if (!aS || !aF || !gS || !gF) {
+        free(aS); free(aF); free(gS); free(gF);
+        return OR_ERR_NOMEM;
+    }
+    int err;
+    if (!gradient) {
+        err = or_acc(N, c->pos, c->mass, S, nS, F, nF, c->p->eps2, aS);
+        if (err == OR_OK) err = or_acc(N, c->pos, c->mass, F, nF, S, nS, c->p->eps2, aF);
+    } else {
+        err = or_accel_grad(N, c->pos, c->mass, S, nS, F, nF, c->p->eps2, aS, gS);
+        if (err == OR_OK)
+            err = or_accel_grad(N, c->pos, c->mass, F, nF, S, nS, c->p->eps2, aF, gF);
+        if (err == OR_OK) {
+            double f = eps * eps / 24.0;
+            for (size_t q = 0; q < 3 * (size_t)nS; ++q) aS[q] += f * gS[q];
+            for (size_t q = 0; q < 3 * (size_t)nF; ++q) aF[q] += f * gF[q];
+        }
+    }
+    if (err == OR_OK) {
+        kick(N, c->vel, S, nS, aS, w);
+        kick(N, c->vel, F, nF, aF, w);
+    }
+    free(aS); free(aF); free(gS); free(gF);
+    return err;
+}
+
+static int hhs_level(hhs_ctx *c, const int *P, int n, double tau, int level)
+{
+    int N = c->N;
+    const or_hhs_params *p = c->p;
+    if (n <= 0) return OR_OK;
+    double *st = (double *)malloc((size_t)n * sizeof(double));
+    int *S = (int *)malloc((size_t)n * sizeof(int));
+    int *F = (int *)malloc((size_t)n * sizeof(int));
+    if (!st || !S || !F) { free(st); free(S); free(F); return OR_ERR_NOMEM; }
+    int err = OR_OK;
+    if (p->fixed_steps)
+        for (int k = 0; k < n; ++k) st[k] = p->fixed_steps[P[k]];
+    else
+        err = or_timesteps(N, c->pos, c->vel, c->mass, P, n, p->eta_ff, p->eta_fb,
+                           p->eta_jerk, p->eps2, st);
+    int nS = 0, nF = 0;
+    if (err == OR_OK) {
+        for (int k = 0; k < n; ++k) {
+            int i = P[k];
+            double e = st[k];
+            if (level == 0) c->step0[i] = e;
+            else if (c->step0[i] < e) e = c->step0[i];
+            if (level >= p->max_level || e >= tau) S[nS++] = i;
+            else F[nF++] = i;
+        }
+        if (level >= p->max_level && nS > 0 && n > 0) {
+            /* count particles that wanted a smaller step than the deepest level allows */
+            for (int k = 0; k < n; ++k) {
+                double e = st[k];
+                if (c->step0[P[k]] < e) e = c->step0[P[k]];
+                if (e < tau) { c->max_level_hit = 1; break; }
+            }
+        }
+        if (c->level_counts) c->level_counts[level] += nS;
+    }
+    or_force_params fp = {p->eps2, p->c, p->is_bh};
+    int cross = (nS > 0 && nF > 0);
+    if (err == OR_OK && cross) {
+        err = pn_kick(N, c->pos, c->vel, c->mass, &fp, S, nS, F, nF, 0, 0.5 * tau);
+        if (err == OR_OK) err = cross_kick(c, S, nS, F, nF, tau / 6.0, 0, 0.0);
+    }
+    if (err == OR_OK && nS > 0) err = or_fsi_step(N, c->pos, c->vel, c->mass, S, nS, 0.5 * tau, &fp);
+    if (err == OR_OK && nF > 0) err = hhs_level(c, F, nF, 0.5 * tau, level + 1);
+    if (err == OR_OK && cross) err = cross_kick(c, S, nS, F, nF, 2.0 * tau / 3.0, 1, tau);
+    if (err == OR_OK && nF > 0) err = hhs_level(c, F, nF, 0.5 * tau, level + 1);
+    if (err == OR_OK && nS > 0) err = or_fsi_step(N, c->pos, c->vel, c->mass, S, nS, 0.5 * tau, &fp);
+    if (err == OR_OK && cross) {
+        err = cross_kick(c, S, nS, F, nF, tau / 6.0, 0, 0.0);
+        if (err == OR_OK)
+            err = pn_kick(N, c->pos, c->vel, c->mass, &fp, S, nS, F, nF, 0, 0.5 * tau);
+    }
+    free(st); free(S); free(F);
+    return err;
+}
+
+/* One HHS interval of length tau over all N particles.  level_counts (max_level + 1
+ * entries, may be NULL) receives, per level, the number of slow-set particles summed
+ * over that level's visits.  Returns OR_ERR_MAXLEVEL (after completing the interval)
+ * if some particle wanted a step below the deepest level's pivot. */
+int or_hhs_interval(int N, double *pos, double *vel, const double *mass, double tau,
+                    const or_hhs_params *p, long long *level_counts)
+{
+    hhs_ctx c;
+    c.N = N; c.pos = pos; c.vel = vel; c.mass = mass; c.p = p;
+    c.level_counts = level_counts;
+    c.max_level_hit = 0;
+    c.step0 = (double *)malloc((size_t)N * sizeof(double));
+    int *all = (int *)malloc((size_t)N * sizeof(int));
+    if (!c.step0 || !all) { free(c.step0); free(all); return OR_ERR_NOMEM; }
+    for (int i = 0; i < N; ++i) all[i] = i;
+    if (level_counts) memset(level_counts, 0, (size_t)(p->max_level + 1) * sizeof(long long));
+    int err = hhs_level(&c, all, N, tau, 0);
+    free(c.step0);
+    free(all);
+    if (err == OR_OK && c.max_level_hit) err = OR_ERR_MAXLEVEL;
+    return err;
+}
+
+/* Time steps of the level-0 set as the interval would assign them (for tests). */
+int or_level0_steps(int N, const double *pos, const double *vel, const double *mass,
+                    const or_hhs_params *p, double *step)
+{
+    return or_timesteps(N, pos, vel, mass, NULL, N, p->eta_ff, p->eta_fb, p->eta_jerk,
+                        p->eps2, step);
+}
