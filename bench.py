@@ -1,0 +1,344 @@
+#!/usr/bin/env python3
+"""Benchmark of the FSI hot path on B300: acc+grad pair interactions per second.
+
+Workload (default): N = 2^20 Plummer stars with a Kroupa IMF plus 16 black holes of
+50-100 Msun in the core, Henon units, speed of light c = 1e4 (PN1.0 pair terms for every
+pair with a black hole), mixed precision.  One step = one complete FSI cycle of the whole
+set (Sect. 2.1, Eq. fsi-cycle) wrapped in PN1.0 half-kicks (Sect. 3.9):
+    PN(h/2)  kick h/6 [acc pass]  drift h/2  acc pass  kick 2h/3 with a + h^2/24 G
+    [grad pass]  drift h/2  kick h/6 [acc pass]  PN(h/2)
+i.e. 3 acceleration passes and 1 gradient pass over all N(N-1) ordered pairs.
+
+Metric: acc+grad pair interactions per second, one interaction = one acceleration pair
+term (20 flops) plus one gradient pair term (36 flops); a step therefore counts
+N(N-1) (3*20 + 36) / 56 interactions.
+
+Usage:  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+Under torchrun (N > 1) every rank runs an independent replica (the pair sum of one
+cluster does not need more than one B300); value = total interactions of all ranks / the
+slowest rank's time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+import numpy as np
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+from paper_2210_02472_b300 import inputs  # noqa: E402
+
+METRIC = "acc+grad pair interactions/s at N=2^20 (mixed precision, FSI cycle with PN1.0)"
+UNIT = "interactions/s"
+FLOP_ACC, FLOP_GRAD = 20, 36
+FLOP_PAIR = FLOP_ACC + FLOP_GRAD
+SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
+CPU_ROWS = 4096
+
+
+def step_interactions(n: int) -> float:
+    pairs = float(n) * float(n - 1)
+    return pairs * (3 * FLOP_ACC + FLOP_GRAD) / FLOP_PAIR
+
+
+def fp32_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
+    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def measured_peaks():
+    p = ROOT / "MEASURED_PEAKS.json"
+    try:
+        return json.loads(p.read_text())
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.lines = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 8:
+                continue
+            try:
+                sm.append(float(f[0]))
+                smax.append(float(f[1]))
+            except ValueError:
+                continue
+            for nm, val in zip(names, f[4:8]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(c, rows: int, threads: int):
+    """The FP64 CPU oracle, as it stands, on a seeded sample of `rows` active particles
+    against all N sources: acc and grad pair sums.  Returns interactions/s."""
+    import oracle
+    oracle.set_threads(threads)
+    A = inputs.random_subset(c.n, rows, 4242)
+    accg = inputs.random_field(c.n, 4243)
+    t0 = time.perf_counter()
+    oracle.acc(c.pos, c.mass, A, None)
+    t1 = time.perf_counter()
+    oracle.grad(c.pos, c.mass, accg, A, None)
+    t2 = time.perf_counter()
+    pairs = float(rows) * (c.n - 1)
+    inter = pairs * (FLOP_ACC + FLOP_GRAD) / FLOP_PAIR
+    return inter / (t2 - t0), {"acc_s": t1 - t0, "grad_s": t2 - t1,
+                               "sample": f"{rows} seeded active rows x all {c.n} sources, "
+                                         f"acc + grad (FP64 oracle)"}
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("FSI_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend)
+        return rank, ws, local, dist
+    return rank, ws, local, None
+
+
+def run_reference(args):
+    rank, ws, local, dist = dist_init()
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+    c = inputs.workload(args.workload)
+    threads = os.cpu_count() or 1
+    rows = max(16, args.ref_rows)
+    for _ in range(args.warmup):
+        cpu_baseline(c, 16, threads)
+    vals, times = [], []
+    info = None
+    for _ in range(args.steps):
+        v, info = cpu_baseline(c, rows, threads)
+        vals.append(v)
+        times.append(info["acc_s"] + info["grad_s"])
+    value = float(np.mean(vals))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * float(np.mean(times)), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": c.n, "oracle": "plain FP64 C, OpenMP over rows"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": info["sample"]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_fsi(args):
+    import torch
+    rank, ws, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2210_02472_b300 import fsi as F
+
+    c = inputs.workload(args.workload)
+    if args.n:
+        c = inputs.plummer(args.n, inputs.SEED_BASE + 3, imf="kroupa", n_bh=16)
+    N = c.n
+    dev = torch.device("cuda", local)
+    pos0 = torch.as_tensor(c.pos).to(dev)
+    vel0 = torch.as_tensor(c.vel).to(dev)
+    mass = torch.as_tensor(c.mass).to(dev)
+    bh = torch.as_tensor(c.is_bh.astype(np.uint8)).to(dev)
+    pos, vel = pos0.clone(), vel0.clone()
+    h = 1.0 / 1024
+    cl = 1e4
+    ctx = F.Context(args.precision, c=cl)
+    F.fsi_reserve(ctx, N, N)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
+    stream = torch.cuda.current_stream()
+
+    def step():
+        F.fsi_step(ctx, pos, vel, mass, h, nsteps=1, is_bh=bh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if F.fsi_sync_status(ctx) != F.FSI_OK:
+        raise SystemExit(f"device error after warm-up: {F._lib.fsi_last_error()}")
+
+    # ---- device-timed region (inputs resident in HBM)
+    sampler = ClockSampler(local)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler.start()
+    F.fsi_profile(ctx, True)
+    n0 = F.fsi_launch_count()
+    t0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.zero_()                       # L2 flush between steps (outside the events)
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = F.fsi_launch_count() - n0 - 0
+    clocks = sampler.stop()
+    prof = F.fsi_profile_read(ctx)
+    F.fsi_profile(ctx, False)
+    if F.fsi_sync_status(ctx) != F.FSI_OK:
+        raise SystemExit("device error in the timed region")
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_dev = sum(step_ms) / 1e3
+    if dist:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    inter = step_interactions(N) * args.steps
+    value = inter * ws / t_dev
+
+    # ---- end to end through the C ABI with host buffers (pinned), copies timed
+    hpos = torch.as_tensor(c.pos).pin_memory()
+    hvel = torch.as_tensor(c.vel).pin_memory()
+    opos = torch.empty_like(hpos).pin_memory()
+    ovel = torch.empty_like(hvel).pin_memory()
+    e2e_steps = max(1, min(args.steps, args.e2e_steps))
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e2e_steps):
+        pos.copy_(hpos, non_blocking=True)
+        vel.copy_(hvel, non_blocking=True)
+        step()
+        opos.copy_(pos, non_blocking=True)
+        ovel.copy_(vel, non_blocking=True)
+    torch.cuda.synchronize()
+    t_e2e = time.perf_counter() - t0
+    if dist:
+        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    e2e_value = step_interactions(N) * e2e_steps * ws / t_e2e
+    bytes_io = 2 * 3 * N * 8
+
+    # ---- roofline of the dominant pair kernel (FP32 pipe bound for the mixed path)
+    kinds = {"acc": FLOP_ACC, "grad": FLOP_GRAD}
+    dom = max(kinds, key=lambda k: prof[k][1])
+    nl, ms = prof[dom]
+    achieved = (float(N) * (N - 1) * kinds[dom]) / (ms / nl / 1e3) / 1e12
+    peak_mhz = SM_MAX_MHZ
+    peak = fp32_peak_tflops(peak_mhz) if args.precision == "mixed" else args.fp64_peak_tflops
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": f"pair_kernel<{args.precision},{dom}>",
+                "peak_basis": ("148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"
+                               if args.precision == "mixed" else "FP64 FMA probe"),
+                "per_kernel_ms": {k: prof[k][1] / max(prof[k][0], 1) for k in prof},
+                "per_kernel_launches": {k: prof[k][0] for k in prof}}
+    if clocks.get("sm_mhz"):
+        roofline["frac_at_median_clock"] = achieved / fp32_peak_tflops(clocks["sm_mhz"]) \
+            if args.precision == "mixed" else None
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": N, "precision": args.precision,
+                   "step": "one FSI cycle of all N + PN1.0 half-kicks (3 acc + 1 grad pair passes)",
+                   "c": cl, "h": h, "l2": "flushed between steps (256 MB write)",
+                   "parallelism": f"replicas x{ws}"},
+        "wall_s": wall, "gpu_launches": launches,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,
+                "d2h_bytes_per_step": bytes_io, "steps": e2e_steps},
+        "roofline": roofline, "clocks": clocks,
+    }
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        threads = os.cpu_count() or 1
+        v, info = cpu_baseline(c, args.cpu_rows, threads)
+        line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
+                                "sample": info["sample"]}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="fsi", choices=["fsi", "reference"])
+    ap.add_argument("--precision", default="mixed", choices=["mixed", "fp64"])
+    ap.add_argument("--workload", default="kroupa1m_bh16")
+    ap.add_argument("--n", type=int, default=0, help="override N (stars) for quick runs")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cpu-rows", type=int, default=CPU_ROWS)
+    ap.add_argument("--ref-rows", type=int, default=1024)
+    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_fsi(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,210 @@
+/*
+ * fsi.h -- C ABI of libfsi, the B300 (sm_103a) hot path of the fourth-order forward
+ * symplectic integrator (FSI) with hierarchical Hamiltonian splitting (HHS) of
+ * BIFROST (Rantala et al. 2022, arXiv 2210.02472).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - All array arguments are DEVICE pointers owned by the caller, unless a comment
+ *    says "host".  Floating point is IEEE double.  Positions, velocities and
+ *    accelerations are structure-of-arrays "3 x N": the x components of all N
+ *    particles, then all y, then all z, each row contiguous.
+ *  - Index lists are int32 global particle ids in [0, N).  A NULL list means all N
+ *    particles in order (the fast path: no gather).  Per-set outputs are 3 x n
+ *    (row stride n) in the order of the list.
+ *  - `stream` is a cudaStream_t passed as void*; NULL is the legacy default stream.
+ *    Every call only enqueues work on `stream` and returns; results are ready when
+ *    the stream is.  Calls never synchronise the device, except fsi_sync_status, the
+ *    calls documented as "synchronous", and workspace growth (see fsi_reserve).
+ *  - The library never allocates per call except to grow the context's workspace;
+ *    call fsi_reserve first to keep a call sequence free of allocations (required
+ *    under CUDA graph capture).
+ *  - Return value: FSI_OK (0) or a negative FSI_ERR_* code for errors detected on the
+ *    host (bad arguments, CUDA launch errors).  Errors detected on the device (a
+ *    non-finite result, a timed-out wait) are latched in a per-context device word
+ *    and reported by fsi_sync_status.  fsi_last_error() returns a thread-local text
+ *    message for the last host-side error.
+ *  - Self-interaction is excluded by global particle id, never by position.
+ *  - G = 1 (N-body units).
+ *
+ * Precision (fsi_params.precision)
+ * --------------------------------
+ *  FSI_FP64:  every pair term in FP64; agrees with an FP64 direct sum to ~1e-13
+ *             relative (summation order differs).
+ *  FSI_MIXED: positions are split into FP32 hi + lo parts so that each pair
+ *             difference is accurate to FP32 precision relative to the separation;
+ *             the pair arithmetic (r^-3, gradient terms) is FP32 with one residual
+ *             correction of the hardware rsqrt; per-tile FP32 partial sums are
+ *             accumulated in FP64.  Per-particle acceleration error is ~1e-7 relative
+ *             (typically 2e-8).  Valid for separations > ~1e-7 (FP32 range of r^-5).
+ */
+#ifndef LIBFSI_FSI_H
+#define LIBFSI_FSI_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- status codes ---------------------------------------------------------- */
+#define FSI_OK 0
+#define FSI_ERR_ARG (-1)          /* invalid argument (sizes, NULL, overlapping sets) */
+#define FSI_ERR_CUDA (-2)         /* a CUDA runtime call failed */
+#define FSI_ERR_NONFINITE (-3)    /* a result was inf/NaN (coincident particles with
+                                     eps2 = 0, or FP32 overflow in the mixed path) */
+#define FSI_ERR_COINCIDENT (-4)   /* reserved: coincident particles reported as such */
+#define FSI_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
+#define FSI_ERR_MAXLEVEL (-6)     /* HHS: a particle wanted a level deeper than max_level */
+#define FSI_ERR_UNSUPPORTED (-7)
+#define FSI_ERR_NOMEM (-8)        /* workspace allocation failed */
+
+#define FSI_FP64 0
+#define FSI_MIXED 1
+
+/* ---- context ----------------------------------------------------------------- */
+typedef struct fsi_ctx fsi_ctx;
+
+typedef struct fsi_params {
+    int precision;        /* FSI_FP64 or FSI_MIXED */
+    double eps2;          /* Plummer softening squared (0 = none), used by step/HHS */
+    double eta_ff;        /* free-fall time-step parameter (Sect. 3.4), e.g. 0.2 */
+    double eta_fb;        /* fly-by time-step parameter, e.g. 0.2 */
+    double eta_jerk;      /* jerk time-step parameter, e.g. 0.1 */
+    int max_level;        /* deepest HHS level (pivot tau / 2^max_level), e.g. 40 */
+    double c;             /* speed of light in N-body units; 0 switches PN1.0 off */
+    int split;            /* source-split factor override (0 = automatic) */
+    long long timeout_ns; /* budget of every bounded device wait (0 = 2e9 ns) */
+} fsi_params;
+
+/* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off). */
+void fsi_default_params(fsi_params *p);
+
+/* Create a context on the current CUDA device.  *ctx receives the handle.
+ * The context owns a device workspace (grown on demand) and a device error word. */
+int fsi_create(fsi_ctx **ctx, const fsi_params *p);
+
+/* Free the workspace and the handle.  Synchronises the device first. */
+int fsi_destroy(fsi_ctx *ctx);
+
+/* Change precision / parameters of an existing context (host only, no sync). */
+int fsi_set_params(fsi_ctx *ctx, const fsi_params *p);
+
+/* Grow the workspace so that calls on sets of up to n particles (out of N total)
+ * allocate nothing.  Synchronous. */
+int fsi_reserve(fsi_ctx *ctx, int N, int n);
+
+/* Thread-local text of the last host-side error (never NULL). */
+const char *fsi_last_error(void);
+
+/* Synchronise `stream`, then return and clear the latched device error word
+ * (FSI_OK if none).  Synchronous. */
+int fsi_sync_status(fsi_ctx *ctx, void *stream);
+
+/* ---- pair sums ------------------------------------------------------------------- */
+
+/* Newtonian acceleration, Sect. 2.1 Eq. (new-newton-acc), of the active set A from the
+ * source set B:  acc_out[:, k] = sum_{j in B, j != A[k]} m_j (r_j - r_i) /
+ *                                  (|r_j - r_i|^2 + eps2)^{3/2},  i = A[k].
+ * pos: 3 x N, mass: N, A: nA ids (NULL = all), B: nB ids (NULL = all),
+ * acc_out: 3 x nA (row stride nA).  A and B may overlap arbitrarily. */
+int fsi_accel(fsi_ctx *ctx, int N, const double *pos, const double *mass,
+              const int *A, int nA, const int *B, int nB, double eps2,
+              double *acc_out, void *stream);
+
+/* Gradient sum of the FSI gradient kick, Sect. 2.1 Eq. (new-grad-acc):
+ *   grad_out[:, k] = sum_{j in B, j != i} m_j / r^5 ( r^2 a_ji - 3 (a_ji . r_ji) r_ji ),
+ *   r_ji = r_j - r_i, r^2 = |r_ji|^2 + eps2, a_ji = a_j - a_i, i = A[k],
+ * WITHOUT the factor eps^2/24 (the gradient acceleration is a + (eps^2/24) grad).
+ * accg: 3 x N accelerations indexed by global id (only the entries of A and B are
+ * read).  A and B may overlap arbitrarily. */
+int fsi_grad(fsi_ctx *ctx, int N, const double *pos, const double *mass,
+             const double *accg, const int *A, int nA, const int *B, int nB,
+             double eps2, double *grad_out, void *stream);
+
+/* acc(A <- B) and the gradient sum G(A <- B) of one splitting term:
+ *  - A and B the same list (same pointer, or both NULL): the set's self-interaction
+ *    (Sect. 2.1); the a_j inside G are acc(A <- A).
+ *  - A and B disjoint: the slow-fast inter-level term (Sect. 2.2); a_i = acc(A <- B),
+ *    a_j = acc(B <- A).
+ * Partial overlap is an error (latched on the device as FSI_ERR_ARG).
+ * vel may be NULL.  acc_out, grad_out: 3 x nA. */
+int fsi_accel_grad(fsi_ctx *ctx, int N, const double *pos, const double *vel,
+                   const double *mass, const int *A, int nA, const int *B, int nB,
+                   double eps2, double *acc_out, double *grad_out, void *stream);
+
+/* PN1.0 pair acceleration (Sect. 3.9): for i = A[k], the sum over j in B, j != i, of
+ * the two-body 1PN Einstein-Infeld-Hoffmann acceleration of i due to j, restricted to
+ * pairs with at least one black hole (is_bh: N bytes, nonzero = black hole).
+ * With n = (x_i - x_j)/r:
+ *   a_i = m_j/(c^2 r^2) { n [ -v_i^2 - 2 v_j^2 + 4 v_i.v_j + 3/2 (n.v_j)^2
+ *                              + 5 m_i/r + 4 m_j/r ] + (v_i - v_j) [4 n.v_i - 3 n.v_j] }.
+ * out: 3 x nA.  Unsoftened. */
+int fsi_pn_accel(fsi_ctx *ctx, int N, const double *pos, const double *vel,
+                 const double *mass, const unsigned char *is_bh, double c,
+                 const int *A, int nA, const int *B, int nB, double *out, void *stream);
+
+/* ---- integrator steps -------------------------------------------------------------- */
+
+/* nsteps FSI cycles of step h (Sect. 2.1, Eq. fsi-cycle) of the set idx (n ids, NULL =
+ * all N) interacting with itself only, in place on pos/vel (3 x N):
+ *   kick h/6 (a), drift h/2, kick 2h/3 (a + h^2/24 G), drift h/2, kick h/6 (a).
+ * Consecutive cycles share the acceleration between the closing and the next opening
+ * kick (three pair passes per cycle).  With fsi_params.c > 0, PN1.0 half-kicks of h/2
+ * wrap every cycle (Sect. 3.9) for pairs with a black hole (is_bh, N bytes; may be
+ * NULL when c == 0).  eps2 comes from fsi_params. */
+int fsi_step(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
+             const unsigned char *is_bh, const int *idx, int n, double h, int nsteps,
+             void *stream);
+
+/* Time steps of the set P against itself (Sect. 3.4): min of the free-fall
+ * eta_ff min_j (r^3/(m_i+m_j))^{1/2}, fly-by eta_fb min_j r/|v_ij| and jerk
+ * eta_jerk |a_i|/|j_i| criteria (eta's and eps2 from fsi_params).  step_out: n. */
+int fsi_timesteps(fsi_ctx *ctx, int N, const double *pos, const double *vel,
+                  const double *mass, const int *P, int n, double *step_out, void *stream);
+
+/* Kinetic and potential energy of the set P (Sect. 2.1 Hamiltonian), FP64:
+ * out[0] = sum 1/2 m v^2, out[1] = -sum_{i<j} m_i m_j / (r^2 + eps2)^{1/2}.
+ * out: 2 doubles, device. */
+int fsi_energy(fsi_ctx *ctx, int N, const double *pos, const double *vel,
+               const double *mass, const int *P, int n, double *out, void *stream);
+
+/* One HHS interval of length tau over all N particles (Sect. 2.2, Eq. hhsfsi-cycle):
+ * per level, time steps against the level set (level 0 against all N; deeper levels
+ * take min with the level-0 step), the split S = {eps >= tau}, F = {eps < tau}, then
+ * U_SF(tau/6) FSI(S, tau/2) HHS(F, tau/2) U~_SF(2 tau/3) HHS(F, tau/2) FSI(S, tau/2)
+ * U_SF(tau/6).  In place on pos/vel.  Synchronous (the host walks the hierarchy). */
+int fsi_hhs_interval(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
+                     const unsigned char *is_bh, double tau, void *stream);
+
+/* Per-level slow-set sizes summed over the visits of the last fsi_hhs_interval.
+ * counts: host array of `max` entries.  Returns the number of levels used. */
+int fsi_level_stats(fsi_ctx *ctx, long long *counts, int max);
+
+/* ---- instrumentation ------------------------------------------------------------ */
+
+/* Start (enable = 1) or stop (0) recording a CUDA event pair around every pair-kernel
+ * launch of this context, on the stream the kernel is launched on.  Recording costs two
+ * event records per launch and no synchronisation. */
+int fsi_profile(fsi_ctx *ctx, int enable);
+
+/* Synchronise the recorded events and return, per kernel kind (0 = acceleration pass,
+ * 1 = gradient pass, 2 = split-finalize), the number of launches and their summed device
+ * milliseconds, then clear the record.  launches: host long long[3], ms: host double[3]. */
+int fsi_profile_read(fsi_ctx *ctx, long long *launches, double *ms);
+
+/* Number of kernels this library has launched in this process (all contexts). */
+long long fsi_launch_count(void);
+
+/* FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add throughput probe: launches
+ * `blocks` CTAs of 256 threads, each thread running 8 independent FMA chains for
+ * `iters` iterations, writing one value per thread to sink (device, blocks*256 entries of
+ * the probe's type).  *flops receives the nominal flop count (2 per FMA).  Time it with
+ * CUDA events on `stream`.  The paper has no counterpart: it measures the pipe peaks
+ * that the pair kernels' roofline fractions are quoted against. */
+int fsi_fma_probe(int fp64, int blocks, int iters, void *sink, double *flops, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LIBFSI_FSI_H */

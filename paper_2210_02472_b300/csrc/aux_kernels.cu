@@ -1,0 +1,679 @@
+// aux_kernels.cu -- O(n) and small O(n^2) kernels around the pair passes:
+// record packing (gather), scatter, kick/drift, PN1.0 pair kicks, time steps, energy,
+// set checks.
+#include "fsi_internal.cuh"
+
+namespace fsi {
+
+constexpr int kB = 256;
+
+static inline int blocks_for(long long n, int b = kB) {
+    long long g = (n + b - 1) / b;
+    return (int)(g < 1 ? 1 : (g > 2147483647LL ? 2147483647LL : g));
+}
+
+__device__ __forceinline__ int idx_at(const int* idx, int k) { return idx ? idx[k] : k; }
+
+// ---------------------------------------------------------------------------------
+// Packing: global SoA (3 x N) -> compact records of the listed set; optionally also a
+// compact FP64 copy xc (3 x n).
+template <int P>
+__global__ void pack_kernel(int N, const double* __restrict__ pos, const double* __restrict__ mass,
+                            const int* __restrict__ idx, int n, void* __restrict__ rec,
+                            double* __restrict__ xc) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = idx_at(idx, k);
+    const double x = pos[i], y = pos[(size_t)N + i], z = pos[2 * (size_t)N + i];
+    const double m = mass[i];
+    if constexpr (P == FSI_MIXED) {
+        const float xh = (float)x, yh = (float)y, zh = (float)z;
+        RecMix r;
+        r.hi = make_float4(xh, yh, zh, (float)m);
+        r.lo = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
+        reinterpret_cast<RecMix*>(rec)[k] = r;
+    } else {
+        reinterpret_cast<D4*>(rec)[k] = make_d4(x, y, z, m);
+    }
+    if (xc) {
+        xc[k] = x;
+        xc[(size_t)n + k] = y;
+        xc[2 * (size_t)n + k] = z;
+    }
+}
+
+cudaError_t launch_pack(int precision, int N, const double* pos, const double* mass,
+                        const int* idx, int n, void* rec, double* xc, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (precision == FSI_MIXED)
+        { pack_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(N, pos, mass, idx, n, rec, xc); note_launch(); }
+    else
+        { pack_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(N, pos, mass, idx, n, rec, xc); note_launch(); }
+    return cudaGetLastError();
+}
+
+template <int P>
+__global__ void pack_acc_kernel(int N, const double* __restrict__ accg, const int* __restrict__ idx,
+                                int n, void* __restrict__ accrec, double* __restrict__ ac) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = idx_at(idx, k);
+    const double x = accg[i], y = accg[(size_t)N + i], z = accg[2 * (size_t)N + i];
+    if constexpr (P == FSI_MIXED)
+        reinterpret_cast<float4*>(accrec)[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+    else
+        reinterpret_cast<D4*>(accrec)[k] = make_d4(x, y, z, 0.0);
+    if (ac) {
+        ac[k] = x;
+        ac[(size_t)n + k] = y;
+        ac[2 * (size_t)n + k] = z;
+    }
+}
+
+cudaError_t launch_pack_acc(int precision, int N, const double* accg, const int* idx, int n,
+                            void* accrec, double* ac, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (precision == FSI_MIXED)
+        { pack_acc_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(N, accg, idx, n, accrec, ac); note_launch(); }
+    else
+        { pack_acc_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(N, accg, idx, n, accrec, ac); note_launch(); }
+    return cudaGetLastError();
+}
+
+__global__ void gather3_kernel(int N, const double* __restrict__ src, const int* __restrict__ idx,
+                               int n, double* __restrict__ dst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = idx_at(idx, k);
+    dst[k] = src[i];
+    dst[(size_t)n + k] = src[(size_t)N + i];
+    dst[2 * (size_t)n + k] = src[2 * (size_t)N + i];
+}
+
+cudaError_t launch_gather3(int N, const double* src, const int* idx, int n, double* dst,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { gather3_kernel<<<blocks_for(n), kB, 0, s>>>(N, src, idx, n, dst); note_launch(); }
+    return cudaGetLastError();
+}
+
+__global__ void scatter3_kernel(int N, const double* __restrict__ src, const int* __restrict__ idx,
+                                int n, double* __restrict__ dst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = idx_at(idx, k);
+    dst[i] = src[k];
+    dst[(size_t)N + i] = src[(size_t)n + k];
+    dst[2 * (size_t)N + i] = src[2 * (size_t)n + k];
+}
+
+cudaError_t launch_scatter3(int N, const double* src, const int* idx, int n, double* dst,
+                            cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { scatter3_kernel<<<blocks_for(n), kB, 0, s>>>(N, src, idx, n, dst); note_launch(); }
+    return cudaGetLastError();
+}
+
+// v[idx[k]] += w * a[:, k]   (scatter-add of a compact 3 x n array into a global 3 x N one)
+__global__ void scatter_axpy3_kernel(int N, const double* __restrict__ a, const int* __restrict__ idx,
+                                     int n, double w, double* __restrict__ v) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = idx_at(idx, k);
+    v[i] = fma(w, a[k], v[i]);
+    v[(size_t)N + i] = fma(w, a[(size_t)n + k], v[(size_t)N + i]);
+    v[2 * (size_t)N + i] = fma(w, a[2 * (size_t)n + k], v[2 * (size_t)N + i]);
+}
+
+cudaError_t launch_scatter_axpy3(int N, const double* a, const int* idx, int n, double w,
+                                 double* v, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { scatter_axpy3_kernel<<<blocks_for(n), kB, 0, s>>>(N, a, idx, n, w, v); note_launch(); }
+    return cudaGetLastError();
+}
+
+__global__ void gather1_kernel(int N, const double* __restrict__ src, const int* __restrict__ idx,
+                               int n, double* __restrict__ dst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    dst[k] = src[idx_at(idx, k)];
+}
+
+cudaError_t launch_gather1(int N, const double* src, const int* idx, int n, double* dst,
+                           cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { gather1_kernel<<<blocks_for(n), kB, 0, s>>>(N, src, idx, n, dst); note_launch(); }
+    return cudaGetLastError();
+}
+
+__global__ void gather_u8_kernel(const unsigned char* __restrict__ src, const int* __restrict__ idx,
+                                 int n, unsigned char* __restrict__ dst) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    dst[k] = src[idx_at(idx, k)];
+}
+
+cudaError_t launch_gather_u8(const unsigned char* src, const int* idx, int n,
+                             unsigned char* dst, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { gather_u8_kernel<<<blocks_for(n), kB, 0, s>>>(src, idx, n, dst); note_launch(); }
+    return cudaGetLastError();
+}
+
+// ids[k] = idx[k] (or k) for k < n; -1 up to cap (the padding the bulk copies may read).
+__global__ void ids_kernel(const int* __restrict__ idx, int n, int cap, int* __restrict__ ids) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= cap) return;
+    ids[k] = k < n ? idx_at(idx, k) : -1;
+}
+
+cudaError_t launch_ids(const int* idx, int n, int cap, int* ids, cudaStream_t s) {
+    if (cap <= 0) return cudaSuccess;
+    { ids_kernel<<<blocks_for(cap), kB, 0, s>>>(idx, n, cap, ids); note_launch(); }
+    return cudaGetLastError();
+}
+
+// accg[:, idx[k]] = ac[:, k]
+cudaError_t launch_scatter_acc_global(int n, const double* ac, const int* idx, int N,
+                                      double* accg, cudaStream_t s) {
+    return launch_scatter3(N, ac, idx, n, accg, s);
+}
+
+// ---------------------------------------------------------------------------------
+// Disjointness of two id lists: mark B, test A, unmark B.  mark: N zeroed bytes.
+__global__ void mark_kernel(const int* __restrict__ B, int nB, unsigned char* mark, unsigned char v) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nB) mark[idx_at(B, k)] = v;
+}
+
+__global__ void test_kernel(const int* __restrict__ A, int nA, const unsigned char* mark, int* err) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < nA && mark[idx_at(A, k)]) set_error(err, FSI_ERR_ARG);
+}
+
+cudaError_t launch_check_disjoint(int N, const int* A, int nA, const int* B, int nB,
+                                  unsigned char* mark, int* err, cudaStream_t s) {
+    (void)N;
+    if (nA <= 0 || nB <= 0) return cudaSuccess;
+    { mark_kernel<<<blocks_for(nB), kB, 0, s>>>(B, nB, mark, 1); note_launch(); }
+    { test_kernel<<<blocks_for(nA), kB, 0, s>>>(A, nA, mark, err); note_launch(); }
+    { mark_kernel<<<blocks_for(nB), kB, 0, s>>>(B, nB, mark, 0); note_launch(); }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Kick + drift on a compact set, rewriting its position records:
+//   v += c_kick a;  x += c_drift v;  rec_out <- (x, m from rec_in).
+template <int P>
+__global__ void kick_drift_kernel(int n, double* __restrict__ xc, double* __restrict__ vc,
+                                  const double* __restrict__ ac, double c_kick, double c_drift,
+                                  const void* __restrict__ rec_in, void* __restrict__ rec_out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double v[3], x[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        v[c] = vc[(size_t)c * n + k];
+        if (ac) v[c] = fma(c_kick, ac[(size_t)c * n + k], v[c]);
+        vc[(size_t)c * n + k] = v[c];
+        x[c] = xc[(size_t)c * n + k];
+        if (c_drift != 0.0) {
+            x[c] = fma(c_drift, v[c], x[c]);
+            xc[(size_t)c * n + k] = x[c];
+        }
+    }
+    if (rec_out) {
+        if constexpr (P == FSI_MIXED) {
+            const float m = reinterpret_cast<const RecMix*>(rec_in)[k].hi.w;
+            RecMix r;
+            const float xh = (float)x[0], yh = (float)x[1], zh = (float)x[2];
+            r.hi = make_float4(xh, yh, zh, m);
+            r.lo = make_float4((float)(x[0] - (double)xh), (float)(x[1] - (double)yh),
+                               (float)(x[2] - (double)zh), 0.f);
+            reinterpret_cast<RecMix*>(rec_out)[k] = r;
+        } else {
+            const double m = reinterpret_cast<const D4*>(rec_in)[k].w;
+            reinterpret_cast<D4*>(rec_out)[k] = make_d4(x[0], x[1], x[2], m);
+        }
+    }
+}
+
+cudaError_t launch_kick_drift(int precision, int n, double* xc, double* vc, const double* ac,
+                              double c_kick, double c_drift, const void* rec_in, void* rec_out,
+                              cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (precision == FSI_MIXED)
+        { kick_drift_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, rec_in, rec_out); note_launch(); }
+    else
+        { kick_drift_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, rec_in, rec_out); note_launch(); }
+    return cudaGetLastError();
+}
+
+__global__ void axpy3_kernel(int n, double* __restrict__ v, const double* __restrict__ a, double w) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[(size_t)c * n + k] = fma(w, a[(size_t)c * n + k], v[(size_t)c * n + k]);
+}
+
+cudaError_t launch_axpy3(int n, double* v, const double* a, double w, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { axpy3_kernel<<<blocks_for(n), kB, 0, s>>>(n, v, a, w); note_launch(); }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// PN1.0 pair acceleration (two-body 1PN EIH, harmonic coordinates), body i due to j:
+//   n = (x_i - x_j)/r,
+//   a = m_j/(c^2 r^2) { n [ -v_i^2 - 2 v_j^2 + 4 v_i.v_j + 1.5 (n.v_j)^2 + 5 m_i/r + 4 m_j/r ]
+//                      + (v_i - v_j) [ 4 n.v_i - 3 n.v_j ] }
+__device__ __forceinline__ void pn_pair(double xi, double yi, double zi, double vxi, double vyi,
+                                        double vzi, double mi, double xj, double yj, double zj,
+                                        double vxj, double vyj, double vzj, double mj, double ic2,
+                                        double& ax, double& ay, double& az, int* err) {
+    const double rx = xi - xj, ry = yi - yj, rz = zi - zj;
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 == 0.0) { set_error(err, FSI_ERR_NONFINITE); return; }
+    const double ir = 1.0 / sqrt(r2);
+    const double nx = rx * ir, ny = ry * ir, nz = rz * ir;
+    const double vi2 = vxi * vxi + vyi * vyi + vzi * vzi;
+    const double vj2 = vxj * vxj + vyj * vyj + vzj * vzj;
+    const double vivj = vxi * vxj + vyi * vyj + vzi * vzj;
+    const double nvi = nx * vxi + ny * vyi + nz * vzi;
+    const double nvj = nx * vxj + ny * vyj + nz * vzj;
+    const double cn = -vi2 - 2.0 * vj2 + 4.0 * vivj + 1.5 * nvj * nvj + (5.0 * mi + 4.0 * mj) * ir;
+    const double cv = 4.0 * nvi - 3.0 * nvj;
+    const double pre = mj * ic2 * ir * ir;
+    ax += pre * (cn * nx + cv * (vxi - vxj));
+    ay += pre * (cn * ny + cv * (vyi - vyj));
+    az += pre * (cn * nz + cv * (vzi - vzj));
+}
+
+// Ordered list of the black holes of a compact set (single CTA, warp-ballot scan).
+constexpr int kMaxBH = kMaxBHList;
+
+__global__ void bh_list_kernel(int n, const unsigned char* __restrict__ bhc, int* __restrict__ list,
+                               int* __restrict__ count, int* err) {
+    __shared__ int warp_tot[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k0 = 0; k0 < n; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        const bool f = k < n && bhc[k];
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_tot[wid] = __popc(b);
+        __syncthreads();
+        int off = base;
+        for (int w = 0; w < wid; ++w) off += warp_tot[w];
+        off += __popc(b & ((1u << lane) - 1u));
+        if (f) {
+            if (off < kMaxBH) list[off] = k;
+            else set_error(err, FSI_ERR_UNSUPPORTED);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < nw; ++w) base += warp_tot[w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = min(base, kMaxBH);
+}
+
+cudaError_t launch_bh_list(int n, const unsigned char* bhc, int* bh_list, int* n_bh, int* err,
+                           cudaStream_t s) {
+    { bh_list_kernel<<<1, 1024, 0, s>>>(n, bhc, bh_list, n_bh, err); note_launch(); }
+    return cudaGetLastError();
+}
+
+// (a) every particle i of the compact set <- every black hole j != i
+__global__ void pn_from_bh_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
+                                  const double* __restrict__ mc, const int* __restrict__ list,
+                                  const int* __restrict__ count, double ic2, double* __restrict__ apn,
+                                  int* err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int nb = *count;
+    const double xi = xc[i], yi = xc[(size_t)n + i], zi = xc[2 * (size_t)n + i];
+    const double vxi = vc[i], vyi = vc[(size_t)n + i], vzi = vc[2 * (size_t)n + i];
+    double ax = 0, ay = 0, az = 0;
+    for (int b = 0; b < nb; ++b) {
+        const int j = list[b];
+        if (j == i) continue;
+        pn_pair(xi, yi, zi, vxi, vyi, vzi, mc[i], xc[j], xc[(size_t)n + j], xc[2 * (size_t)n + j],
+                vc[j], vc[(size_t)n + j], vc[2 * (size_t)n + j], mc[j], ic2, ax, ay, az, err);
+    }
+    apn[i] = ax;
+    apn[(size_t)n + i] = ay;
+    apn[2 * (size_t)n + i] = az;
+}
+
+// (b) black hole b <- every non-black-hole j: per-CTA partial sums, in a fixed order.
+constexpr int kPnCtas = kPnPartCtas;
+
+__global__ void pn_bh_from_all_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
+                                      const double* __restrict__ mc, const unsigned char* __restrict__ bhc,
+                                      const int* __restrict__ list, const int* __restrict__ count,
+                                      double ic2, double* __restrict__ part, int* err) {
+    for (int b = blockIdx.y; b < *count; b += gridDim.y) {
+    const int i = list[b];
+    const double xi = xc[i], yi = xc[(size_t)n + i], zi = xc[2 * (size_t)n + i];
+    const double vxi = vc[i], vyi = vc[(size_t)n + i], vzi = vc[2 * (size_t)n + i];
+    const double mi = mc[i];
+    double s[3] = {0, 0, 0};
+    for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
+        if (bhc[j]) continue;
+        pn_pair(xi, yi, zi, vxi, vyi, vzi, mi, xc[j], xc[(size_t)n + j], xc[2 * (size_t)n + j],
+                vc[j], vc[(size_t)n + j], vc[2 * (size_t)n + j], mc[j], ic2, s[0], s[1], s[2], err);
+    }
+    __shared__ double red[3][kB];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) red[c][threadIdx.x] = s[c];
+    __syncthreads();
+    for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+        if (threadIdx.x < w)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) part[((size_t)b * 3 + c) * kPnCtas + blockIdx.x] = red[c][0];
+    __syncthreads();
+    }
+}
+
+__global__ void pn_bh_finish_kernel(int n, const int* __restrict__ list, const int* __restrict__ count,
+                                    const double* __restrict__ part, double* __restrict__ apn) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= *count) return;
+    const int i = list[b];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        double s = 0;
+        for (int q = 0; q < kPnCtas; ++q) s += part[((size_t)b * 3 + c) * kPnCtas + q];
+        apn[(size_t)c * n + i] += s;
+    }
+}
+
+// PN1.0 accelerations of the compact set on itself (pairs with a black hole), apn: 3 x n.
+cudaError_t launch_pn(int n, const double* xc, const double* vc, const double* mc,
+                      const unsigned char* bhc, double c, const int* bh_list, const int* n_bh,
+                      int max_bh, double* apn, double* part, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const double ic2 = 1.0 / (c * c);
+    { pn_from_bh_kernel<<<blocks_for(n), kB, 0, s>>>(n, xc, vc, mc, bh_list, n_bh, ic2, apn, err); note_launch(); }
+    dim3 g(kPnCtas, max_bh < 32 ? max_bh : 32);
+    { pn_bh_from_all_kernel<<<g, kB, 0, s>>>(n, xc, vc, mc, bhc, bh_list, n_bh, ic2, part, err); note_launch(); }
+    { pn_bh_finish_kernel<<<blocks_for(max_bh), kB, 0, s>>>(n, bh_list, n_bh, part, apn); note_launch(); }
+    return cudaGetLastError();
+}
+
+// General (masked) PN pair sum over index lists: thread per i in A, loop over B.
+__global__ void pn_pairs_kernel(int N, const double* __restrict__ pos, const double* __restrict__ vel,
+                                const double* __restrict__ mass, const unsigned char* __restrict__ is_bh,
+                                double ic2, const int* __restrict__ A, int nA,
+                                const int* __restrict__ B, int nB, double* __restrict__ out,
+                                double wscale, int accumulate, int* err) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nA) return;
+    const int i = idx_at(A, k);
+    const double xi = pos[i], yi = pos[(size_t)N + i], zi = pos[2 * (size_t)N + i];
+    const double vxi = vel[i], vyi = vel[(size_t)N + i], vzi = vel[2 * (size_t)N + i];
+    const bool bi = is_bh[i] != 0;
+    double ax = 0, ay = 0, az = 0;
+    for (int l = 0; l < nB; ++l) {
+        const int j = idx_at(B, l);
+        if (j == i || (!bi && !is_bh[j])) continue;
+        pn_pair(xi, yi, zi, vxi, vyi, vzi, mass[i], pos[j], pos[(size_t)N + j], pos[2 * (size_t)N + j],
+                vel[j], vel[(size_t)N + j], vel[2 * (size_t)N + j], mass[j], ic2, ax, ay, az, err);
+    }
+    if (accumulate) {
+        out[k] += wscale * ax;
+        out[(size_t)nA + k] += wscale * ay;
+        out[2 * (size_t)nA + k] += wscale * az;
+    } else {
+        out[k] = wscale * ax;
+        out[(size_t)nA + k] = wscale * ay;
+        out[2 * (size_t)nA + k] = wscale * az;
+    }
+}
+
+cudaError_t launch_pn_pairs(int N, const double* pos, const double* vel, const double* mass,
+                            const unsigned char* is_bh, double c, const int* A, int nA,
+                            const int* B, int nB, double* out, int* err, cudaStream_t s) {
+    if (nA <= 0) return cudaSuccess;
+    { pn_pairs_kernel<<<blocks_for(nA), kB, 0, s>>>(N, pos, vel, mass, is_bh, 1.0 / (c * c), A, nA,
+                                                  B, nB, out, 1.0, 0, err); note_launch(); }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// Small O(n^2) FP64 loops (time steps, energy): thread per i, sources through shared
+// memory in plain cooperative tiles.
+constexpr int kAuxTile = 128;
+
+// Time steps (Sect. 3.4): min over j of eta_ff (r^3/(m_i+m_j))^{1/2} and eta_fb r/|v_ij|,
+// and eta_jerk |a|/|j| with a and the jerk from the softened kernel.
+__global__ void timesteps_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
+                                 const double* __restrict__ mc, double eta_ff, double eta_fb,
+                                 double eta_jerk, double eps2, double* __restrict__ step, int* err) {
+    __shared__ double sx[kAuxTile], sy[kAuxTile], sz[kAuxTile], su[kAuxTile], sv[kAuxTile],
+        sw[kAuxTile], sm[kAuxTile];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ii = min(i, n - 1);
+    const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
+    const double ui = vc[ii], vi = vc[(size_t)n + ii], wi = vc[2 * (size_t)n + ii];
+    const double mi = mc[ii];
+    double ff2 = INFINITY, fb = INFINITY;
+    double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kAuxTile; t += blockDim.x) {
+            const int j = j0 + t;
+            if (j < n) {
+                sx[t] = xc[j]; sy[t] = xc[(size_t)n + j]; sz[t] = xc[2 * (size_t)n + j];
+                su[t] = vc[j]; sv[t] = vc[(size_t)n + j]; sw[t] = vc[2 * (size_t)n + j];
+                sm[t] = mc[j];
+            }
+        }
+        __syncthreads();
+        const int cnt = min(kAuxTile, n - j0);
+        for (int t = 0; t < cnt; ++t) {
+            if (j0 + t == ii) continue;
+            const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
+            const double du = su[t] - ui, dv = sv[t] - vi, dw = sw[t] - wi;
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            const double s2 = d2 + eps2;
+            if (d2 == 0.0) { if (i < n) set_error(err, FSI_ERR_NONFINITE); continue; }
+            const double d = sqrt(d2);
+            ff2 = fmin(ff2, d2 * d / (mi + sm[t]));
+            const double u2 = du * du + dv * dv + dw * dw;
+            if (u2 > 0.0) fb = fmin(fb, d / sqrt(u2));
+            const double sr = sqrt(s2);
+            const double f3 = sm[t] / (s2 * sr);
+            const double f5 = f3 / s2;
+            const double rv = dx * du + dy * dv + dz * dw;
+            ax += f3 * dx; ay += f3 * dy; az += f3 * dz;
+            jx += f5 * (s2 * du - 3.0 * rv * dx);
+            jy += f5 * (s2 * dv - 3.0 * rv * dy);
+            jz += f5 * (s2 * dw - 3.0 * rv * dz);
+        }
+    }
+    if (i >= n) return;
+    double e = fmin(eta_ff * sqrt(ff2), eta_fb * fb);
+    const double jn = sqrt(jx * jx + jy * jy + jz * jz);
+    if (jn > 0.0) e = fmin(e, eta_jerk * sqrt(ax * ax + ay * ay + az * az) / jn);
+    step[i] = e;
+}
+
+cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
+                             double eta_ff, double eta_fb, double eta_jerk, double eps2,
+                             double* step, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { timesteps_kernel<<<blocks_for(n, kAuxTile), kAuxTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb,
+                                                                  eta_jerk, eps2, step, err); note_launch(); }
+    return cudaGetLastError();
+}
+
+// Energy: per-CTA partial sums of the kinetic energy and of -1/2 sum_i sum_{j != i}
+// m_i m_j / sqrt(r^2 + eps2), reduced in a fixed order by energy_finish_kernel.
+__global__ void energy_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
+                              const double* __restrict__ mc, double eps2, double* __restrict__ part,
+                              int* err) {
+    __shared__ double sx[kAuxTile], sy[kAuxTile], sz[kAuxTile], sm[kAuxTile];
+    __shared__ double rk[kAuxTile], rw[kAuxTile];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ii = min(i, n - 1);
+    const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
+    double w = 0.0;
+    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kAuxTile; t += blockDim.x) {
+            const int j = j0 + t;
+            if (j < n) { sx[t] = xc[j]; sy[t] = xc[(size_t)n + j]; sz[t] = xc[2 * (size_t)n + j]; sm[t] = mc[j]; }
+        }
+        __syncthreads();
+        const int cnt = min(kAuxTile, n - j0);
+        for (int t = 0; t < cnt; ++t) {
+            if (j0 + t == ii) continue;
+            const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
+            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) { if (i < n) set_error(err, FSI_ERR_NONFINITE); continue; }
+            w += sm[t] / sqrt(r2);
+        }
+    }
+    double kin = 0.0;
+    if (i < n) {
+        const double u = vc[i], v = vc[(size_t)n + i], ww = vc[2 * (size_t)n + i];
+        kin = 0.5 * mc[i] * (u * u + v * v + ww * ww);
+        w = -0.5 * mc[i] * w;
+    } else {
+        w = 0.0;
+    }
+    rk[threadIdx.x] = kin;
+    rw[threadIdx.x] = w;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            rk[threadIdx.x] += rk[threadIdx.x + h];
+            rw[threadIdx.x] += rw[threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        part[2 * blockIdx.x] = rk[0];
+        part[2 * blockIdx.x + 1] = rw[0];
+    }
+}
+
+__global__ void energy_finish_kernel(int nb, const double* __restrict__ part, double* __restrict__ out) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double k = 0, w = 0, ck = 0, cw = 0;   // Kahan-compensated sums over the CTA partials
+    for (int b = 0; b < nb; ++b) {
+        double y = part[2 * b] - ck, t = k + y;
+        ck = (t - k) - y; k = t;
+        y = part[2 * b + 1] - cw; t = w + y;
+        cw = (t - w) - y; w = t;
+    }
+    out[0] = k;
+    out[1] = w;
+}
+
+int energy_blocks(int n) { return blocks_for(n, kAuxTile); }
+
+cudaError_t launch_energy(int n, const double* xc, const double* vc, const double* mc,
+                          double eps2, double* part, double* out, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    const int nb = energy_blocks(n);
+    { energy_kernel<<<nb, kAuxTile, 0, s>>>(n, xc, vc, mc, eps2, part, err); note_launch(); }
+    { energy_finish_kernel<<<1, 32, 0, s>>>(nb, part, out); note_launch(); }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
+// HHS helpers.
+// step[k] = min(step[k], step0[ids[k]]) at deeper levels; step0[ids[k]] = step[k] at level 0.
+__global__ void level_steps_kernel(int n, const int* __restrict__ ids, double* __restrict__ step,
+                                   double* __restrict__ step0, int level0) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    const int i = ids[k];
+    if (level0) step0[i] = step[k];
+    else step[k] = fmin(step[k], step0[i]);
+}
+
+cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step0, int level0,
+                               cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { level_steps_kernel<<<blocks_for(n), kB, 0, s>>>(n, ids, step, step0, level0); note_launch(); }
+    return cudaGetLastError();
+}
+
+// Stable partition of ids by (step >= tau) into S (slow) and F (fast), single CTA scan.
+// counts[0] = |S|, counts[1] = |F|, counts[2] = 1 if some particle wanted a step < tau
+// at the deepest level (force_slow).
+__global__ void partition_kernel(int n, const int* __restrict__ ids, const double* __restrict__ step,
+                                 double tau, int force_slow, int* __restrict__ S, int* __restrict__ F,
+                                 int* __restrict__ counts) {
+    __shared__ int wS[32], wF[32];
+    __shared__ int baseS, baseF, anyfast;
+    if (threadIdx.x == 0) { baseS = 0; baseF = 0; anyfast = 0; }
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k0 = 0; k0 < n; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        const bool valid = k < n;
+        const bool fastw = valid && step[k] < tau;
+        const bool slow = valid && (force_slow || !fastw);
+        const bool fast = valid && !slow;
+        if (fastw && force_slow) anyfast = 1;
+        const unsigned bs = __ballot_sync(0xffffffffu, slow);
+        const unsigned bf = __ballot_sync(0xffffffffu, fast);
+        if (lane == 0) { wS[wid] = __popc(bs); wF[wid] = __popc(bf); }
+        __syncthreads();
+        int oS = baseS, oF = baseF;
+        for (int w = 0; w < wid; ++w) { oS += wS[w]; oF += wF[w]; }
+        const unsigned lm = (1u << lane) - 1u;
+        if (slow) S[oS + __popc(bs & lm)] = ids[k];
+        if (fast) F[oF + __popc(bf & lm)] = ids[k];
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < nw; ++w) { baseS += wS[w]; baseF += wF[w]; }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) { counts[0] = baseS; counts[1] = baseF; counts[2] = anyfast; }
+}
+
+cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,
+                             int* S, int* F, int* counts, cudaStream_t s) {
+    { partition_kernel<<<1, 1024, 0, s>>>(n, ids, step, tau, force_slow, S, F, counts); note_launch(); }
+    return cudaGetLastError();
+}
+
+__global__ void iota_kernel(int n, int* ids) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) ids[k] = k;
+}
+
+cudaError_t launch_iota(int n, int* ids, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { iota_kernel<<<blocks_for(n), kB, 0, s>>>(n, ids); note_launch(); }
+    return cudaGetLastError();
+}
+
+// out = a + c * g  (3 x n), elementwise
+__global__ void axpby3_kernel(int n3, const double* __restrict__ a, const double* __restrict__ g,
+                              double c, double* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n3) out[k] = fma(c, g[k], a[k]);
+}
+
+cudaError_t launch_axpby3(int n, const double* a, const double* g, double c, double* out,
+                          cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { axpby3_kernel<<<blocks_for(3LL * n), kB, 0, s>>>(3 * n, a, g, c, out); note_launch(); }
+    return cudaGetLastError();
+}
+
+}  // namespace fsi

@@ -1,0 +1,772 @@
+// fsi_api.cu -- host side of libfsi's C ABI (declared in include/fsi.h).
+//
+// The host code only gathers index lists into compact device records, schedules the
+// pair passes and their fused epilogues, and walks the HHS hierarchy; every arithmetic
+// step runs in the kernels of pair_kernels.cu and aux_kernels.cu.
+#include <atomic>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "fsi_internal.cuh"
+
+using namespace fsi;
+
+namespace {
+std::atomic<long long> g_launches{0};
+}
+
+void fsi::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
+
+namespace {
+
+thread_local std::string g_err = "";
+
+int fail(int code, const char* fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_err = buf;
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(FSI_ERR_CUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
+                        __FILE__, __LINE__);                                            \
+    } while (0)
+
+#define CK(expr)                      \
+    do {                              \
+        int r_ = (expr);              \
+        if (r_ != FSI_OK) return r_;  \
+    } while (0)
+
+struct Buf {
+    void* p = nullptr;
+    size_t bytes = 0;
+};
+
+}  // namespace
+
+struct fsi_ctx {
+    fsi_params p;
+    int device = 0;
+    int sm_count = 148;
+    int* err_d = nullptr;
+    int* err_h = nullptr;          // pinned
+    int* counts_h = nullptr;       // pinned, 3 ints (HHS partition)
+    Buf rec[2], accrec[2], xc, vc, ac, ad, gA, gB, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
+        nbh, apn, pnpart, epart, iota, steps, step0, counts;
+    std::vector<Buf> lvS, lvF;
+    std::vector<long long> level_counts;
+    int max_level_used = 0;
+    int max_level_hit = 0;
+    // instrumentation: event pairs around pair-kernel launches
+    struct ProfRec { int kind; cudaEvent_t a, b; };
+    bool profiling = false;
+    std::vector<ProfRec> prof;
+    std::vector<cudaEvent_t> ev_pool;
+};
+
+namespace {
+
+int ensure(Buf& b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return FSI_OK;
+    if (b.p) {
+        CU(cudaFree(b.p));
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = (bytes + 255) & ~size_t(255);
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(FSI_ERR_NOMEM, "cudaMalloc of %zu bytes failed", want);
+    }
+    b.bytes = want;
+    return FSI_OK;
+}
+
+template <class T>
+T* P(Buf& b) { return reinterpret_cast<T*>(b.p); }
+
+cudaStream_t S(void* s) { return reinterpret_cast<cudaStream_t>(s); }
+
+long long budget(const fsi_ctx* c) { return c->p.timeout_ns > 0 ? c->p.timeout_ns : 2000000000LL; }
+
+size_t pad_tile(int n) { return (size_t)((n + kTileJ - 1) / kTileJ) * kTileJ; }
+
+// Source-split factor: the smallest S whose CTA count (i-blocks x S) fills the resident
+// slots of the GPU (2 CTAs/SM) to >= 90 % in the last wave, keeping >= 4 tiles per slice.
+int choose_split(const fsi_ctx* c, int n_i, int n_j, int ipc) {
+    const int ctas = (n_i + ipc - 1) / ipc;
+    const int max_s = std::max(1, std::min(64, n_j / (4 * kTileJ)));
+    if (c->p.split > 0) return std::min(c->p.split, max_s);
+    const int slots = c->sm_count * 2;
+    int best = 1;
+    double best_eff = 0.0;
+    for (int s = 1; s <= max_s; ++s) {
+        const long long tot = (long long)ctas * s;
+        const long long waves = (tot + slots - 1) / slots;
+        const double eff = (double)tot / (double)(waves * slots);
+        if (eff >= 0.9) return s;
+        if (eff > best_eff + 1e-9) { best_eff = eff; best = s; }
+    }
+    return best;
+}
+
+cudaEvent_t get_event(fsi_ctx* c) {
+    if (!c->ev_pool.empty()) {
+        cudaEvent_t e = c->ev_pool.back();
+        c->ev_pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+    return e;
+}
+
+// Launch f() bracketed by an event pair when profiling is on.
+template <class F>
+int timed(fsi_ctx* c, int kind, cudaStream_t s, F&& f) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (c->profiling) {
+        e0 = get_event(c);
+        e1 = get_event(c);
+        if (e0 && e1) CU(cudaEventRecord(e0, s));
+    }
+    CU(f());
+    if (c->profiling && e0 && e1) {
+        CU(cudaEventRecord(e1, s));
+        c->prof.push_back({kind, e0, e1});
+    }
+    return FSI_OK;
+}
+
+int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
+    if (a.n_i <= 0) return FSI_OK;
+    const int prec = c->p.precision;
+    const int ipc = pair_i_per_cta_for(prec, kind);
+    int split = choose_split(c, a.n_i, a.n_j, ipc);
+    int jps = (a.n_j + split - 1) / split;
+    jps = std::max(kTileJ, (jps + kTileJ - 1) / kTileJ * kTileJ);
+    split = std::max(1, (a.n_j + jps - 1) / jps);
+    a.j_per_split = jps;
+    a.err = c->err_d;
+    a.timeout_ns = budget(c);
+    if (split > 1) {
+        CK(ensure(c->part, (size_t)split * 3 * a.n_i * sizeof(double)));
+        a.part = P<double>(c->part);
+    }
+    CK(timed(c, kind, s, [&] { return launch_pair(prec, kind, a, split, s); }));
+    if (split > 1) CK(timed(c, 2, s, [&] { return launch_finalize_p(prec, a, split, s); }));
+    return FSI_OK;
+}
+
+bool valid_prec(int p) { return p == FSI_FP64 || p == FSI_MIXED; }
+
+int check_common(fsi_ctx* c, int N) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    if (N <= 0) return fail(FSI_ERR_ARG, "N must be positive (got %d)", N);
+    return FSI_OK;
+}
+
+// ---------------------------------------------------------------------------------
+// FSI cycles of a set on itself (compact buffers; see fsi_step in fsi.h).
+int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+              const unsigned char* is_bh, const int* idx, int n, double h, int nsteps,
+              cudaStream_t s) {
+    if (n <= 0 || nsteps <= 0) return FSI_OK;
+    const int prec = c->p.precision;
+    const bool pn = c->p.c > 0.0;
+    if (pn && !is_bh) return fail(FSI_ERR_ARG, "PN on (c > 0) needs is_bh");
+    CK(ensure(c->rec[0], pad_tile(n) * 32));
+    CK(ensure(c->rec[1], pad_tile(n) * 32));
+    CK(ensure(c->accrec[0], pad_tile(n) * 32));
+    CK(ensure(c->ac, 3 * (size_t)n * 8));
+    double* xc = pos;
+    double* vc = vel;
+    const double* mc = mass;
+    const unsigned char* bhc = is_bh;
+    if (idx) {
+        CK(ensure(c->xc, 3 * (size_t)n * 8));
+        CK(ensure(c->vc, 3 * (size_t)n * 8));
+        xc = P<double>(c->xc);
+        vc = P<double>(c->vc);
+        CU(launch_gather3(N, vel, idx, n, vc, s));
+    }
+    CU(launch_pack(prec, N, pos, mass, idx, n, c->rec[0].p, idx ? xc : nullptr, s));
+    if (pn) {
+        CK(ensure(c->ad, 3 * (size_t)n * 8));
+        CK(ensure(c->apn, 3 * (size_t)n * 8));
+        CK(ensure(c->bhlist, kMaxBHList * 4));
+        CK(ensure(c->nbh, 16));
+        CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
+        if (idx) {
+            CK(ensure(c->mc, (size_t)n * 8));
+            CK(ensure(c->bhc, (size_t)n));
+            CU(launch_gather1(N, mass, idx, n, P<double>(c->mc), s));
+            CU(launch_gather_u8(is_bh, idx, n, P<unsigned char>(c->bhc), s));
+            mc = P<double>(c->mc);
+            bhc = P<unsigned char>(c->bhc);
+        }
+        CU(launch_bh_list(n, bhc, P<int>(c->bhlist), P<int>(c->nbh), c->err_d, s));
+    }
+    auto pn_kick = [&](double w) -> int {
+        CU(launch_pn(n, xc, vc, mc, bhc, c->p.c, P<int>(c->bhlist), P<int>(c->nbh), kMaxBHList,
+                     P<double>(c->apn), P<double>(c->pnpart), c->err_d, s));
+        CU(launch_axpy3(n, vc, P<double>(c->apn), w, s));
+        return FSI_OK;
+    };
+    auto acc_pass = [&](void* rin, void* rout, double ck, double cd, double* out, void* accrec) {
+        PairArgs a{};
+        a.irec = a.jrec = rin;
+        a.n_i = a.n_j = n;
+        a.check = CHECK_DIAG;
+        a.eps2 = c->p.eps2;
+        a.epi.out = out;
+        a.epi.accrec = accrec;
+        if (ck != 0.0 || cd != 0.0) {
+            a.epi.v = vc;
+            a.epi.x = xc;
+            a.epi.c_kick = ck;
+            a.epi.c_drift = cd;
+            a.epi.rec_out = rout;
+        }
+        return run_pair(c, KIND_ACC, a, s);
+    };
+    auto grad_pass = [&](void* rin, void* rout, double ck, double cg, double cd) {
+        PairArgs a{};
+        a.irec = a.jrec = rin;
+        a.iacc = a.jacc = c->accrec[0].p;
+        a.n_i = a.n_j = n;
+        a.check = CHECK_DIAG;
+        a.eps2 = c->p.eps2;
+        a.epi.v = vc;
+        a.epi.x = xc;
+        a.epi.base = P<double>(c->ac);
+        a.epi.c_kick = ck;
+        a.epi.c_grad = cg;
+        a.epi.c_drift = cd;
+        a.epi.rec_out = rout;
+        return run_pair(c, KIND_GRAD, a, s);
+    };
+    void* r0 = c->rec[0].p;
+    void* r1 = c->rec[1].p;
+    if (pn) CK(pn_kick(0.5 * h));
+    CK(acc_pass(r0, r1, h / 6.0, 0.5 * h, nullptr, nullptr));
+    for (int k = 0; k < nsteps; ++k) {
+        const bool last = (k == nsteps - 1);
+        CK(acc_pass(r1, nullptr, 0.0, 0.0, P<double>(c->ac), c->accrec[0].p));
+        CK(grad_pass(r1, r0, 2.0 * h / 3.0, h * h / 24.0, 0.5 * h));
+        if (!pn && !last) {
+            CK(acc_pass(r0, r1, h / 3.0, 0.5 * h, nullptr, nullptr));
+        } else {
+            CK(acc_pass(r0, nullptr, h / 6.0, 0.0, pn ? P<double>(c->ad) : nullptr, nullptr));
+            if (pn) CK(pn_kick(0.5 * h));
+            if (!last) {
+                CK(pn_kick(0.5 * h));
+                CU(launch_kick_drift(prec, n, xc, vc, P<double>(c->ad), h / 6.0, 0.5 * h, r0, r1, s));
+            }
+        }
+    }
+    if (idx) {
+        CU(launch_scatter3(N, xc, idx, n, pos, s));
+        CU(launch_scatter3(N, vc, idx, n, vel, s));
+    }
+    return FSI_OK;
+}
+
+// Inter-level kick of the slow set S and fast set F (Sect. 2.2):
+//   gradient == 0:  v_S += w acc(S <- F),  v_F += w acc(F <- S)
+//   gradient == 1:  the same with a~ = a + (eps^2/24) G of the same inter-level term.
+int cross_kick(fsi_ctx* c, int N, const double* pos, double* vel, const double* mass,
+               const int* Sids, int nS, const int* Fids, int nF, double w, int gradient,
+               double eps, cudaStream_t s) {
+    const int prec = c->p.precision;
+    CK(ensure(c->rec[0], pad_tile(nS) * 32));
+    CK(ensure(c->rec[1], pad_tile(nF) * 32));
+    CK(ensure(c->accrec[0], pad_tile(nS) * 32));
+    CK(ensure(c->accrec[1], pad_tile(nF) * 32));
+    CK(ensure(c->tA, 3 * (size_t)nS * 8));
+    CK(ensure(c->tB, 3 * (size_t)nF * 8));
+    CU(launch_pack(prec, N, pos, mass, Sids, nS, c->rec[0].p, nullptr, s));
+    CU(launch_pack(prec, N, pos, mass, Fids, nF, c->rec[1].p, nullptr, s));
+    PairArgs a{};
+    a.check = CHECK_NONE;
+    a.eps2 = c->p.eps2;
+    a.irec = c->rec[0].p; a.jrec = c->rec[1].p; a.n_i = nS; a.n_j = nF;
+    a.epi.out = P<double>(c->tA);
+    a.epi.accrec = gradient ? c->accrec[0].p : nullptr;
+    CK(run_pair(c, KIND_ACC, a, s));
+    PairArgs b{};
+    b.check = CHECK_NONE;
+    b.eps2 = c->p.eps2;
+    b.irec = c->rec[1].p; b.jrec = c->rec[0].p; b.n_i = nF; b.n_j = nS;
+    b.epi.out = P<double>(c->tB);
+    b.epi.accrec = gradient ? c->accrec[1].p : nullptr;
+    CK(run_pair(c, KIND_ACC, b, s));
+    if (gradient) {
+        CK(ensure(c->gA, 3 * (size_t)nS * 8));
+        CK(ensure(c->gB, 3 * (size_t)nF * 8));
+        a.iacc = c->accrec[0].p; a.jacc = c->accrec[1].p;
+        a.epi = Epi{};
+        a.epi.out = P<double>(c->gA);
+        CK(run_pair(c, KIND_GRAD, a, s));
+        b.iacc = c->accrec[1].p; b.jacc = c->accrec[0].p;
+        b.epi = Epi{};
+        b.epi.out = P<double>(c->gB);
+        CK(run_pair(c, KIND_GRAD, b, s));
+        const double cg = eps * eps / 24.0;
+        CU(launch_axpby3(nS, P<double>(c->tA), P<double>(c->gA), cg, P<double>(c->tA), s));
+        CU(launch_axpby3(nF, P<double>(c->tB), P<double>(c->gB), cg, P<double>(c->tB), s));
+    }
+    CU(launch_scatter_axpy3(N, P<double>(c->tA), Sids, nS, w, vel, s));
+    CU(launch_scatter_axpy3(N, P<double>(c->tB), Fids, nF, w, vel, s));
+    return FSI_OK;
+}
+
+// PN1.0 kick of the S-F pairs (both directions, velocities from the start of the kick).
+int cross_pn_kick(fsi_ctx* c, int N, const double* pos, double* vel, const double* mass,
+                  const unsigned char* is_bh, const int* Sids, int nS, const int* Fids, int nF,
+                  double w, cudaStream_t s) {
+    CK(ensure(c->tA, 3 * (size_t)nS * 8));
+    CK(ensure(c->tB, 3 * (size_t)nF * 8));
+    CU(launch_pn_pairs(N, pos, vel, mass, is_bh, c->p.c, Sids, nS, Fids, nF, P<double>(c->tA),
+                       c->err_d, s));
+    CU(launch_pn_pairs(N, pos, vel, mass, is_bh, c->p.c, Fids, nF, Sids, nS, P<double>(c->tB),
+                       c->err_d, s));
+    CU(launch_scatter_axpy3(N, P<double>(c->tA), Sids, nS, w, vel, s));
+    CU(launch_scatter_axpy3(N, P<double>(c->tB), Fids, nF, w, vel, s));
+    return FSI_OK;
+}
+
+int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+                   const int* Pids, int n, double* step, cudaStream_t s) {
+    if (n <= 0) return FSI_OK;
+    const double* xc = pos;
+    const double* vc = vel;
+    const double* mc = mass;
+    if (Pids) {
+        CK(ensure(c->xc, 3 * (size_t)n * 8));
+        CK(ensure(c->vc, 3 * (size_t)n * 8));
+        CK(ensure(c->mc, (size_t)n * 8));
+        CU(launch_gather3(N, pos, Pids, n, P<double>(c->xc), s));
+        CU(launch_gather3(N, vel, Pids, n, P<double>(c->vc), s));
+        CU(launch_gather1(N, mass, Pids, n, P<double>(c->mc), s));
+        xc = P<double>(c->xc);
+        vc = P<double>(c->vc);
+        mc = P<double>(c->mc);
+    }
+    CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
+                        c->err_d, s));
+    return FSI_OK;
+}
+
+int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+              const unsigned char* is_bh, const int* Pids, int n, double tau, int level,
+              cudaStream_t s) {
+    if (n <= 0) return FSI_OK;
+    if ((int)c->lvS.size() <= level) {
+        c->lvS.resize(level + 1);
+        c->lvF.resize(level + 1);
+    }
+    c->max_level_used = std::max(c->max_level_used, level);
+    CK(ensure(c->steps, (size_t)n * 8));
+    CK(ensure(c->lvS[level], (size_t)n * 4));
+    CK(ensure(c->lvF[level], (size_t)n * 4));
+    CK(timesteps_core(c, N, pos, vel, mass, Pids, n, P<double>(c->steps), s));
+    CU(launch_level_steps(n, Pids, P<double>(c->steps), P<double>(c->step0), level == 0, s));
+    const int force_slow = level >= c->p.max_level;
+    int* Sids = P<int>(c->lvS[level]);
+    int* Fids = P<int>(c->lvF[level]);
+    CU(launch_partition(n, Pids, P<double>(c->steps), tau, force_slow, Sids, Fids, P<int>(c->counts), s));
+    CU(cudaMemcpyAsync(c->counts_h, c->counts.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    const int nS = c->counts_h[0], nF = c->counts_h[1];
+    if (c->counts_h[2]) c->max_level_hit = 1;
+    if ((int)c->level_counts.size() <= level) c->level_counts.resize(level + 1, 0);
+    c->level_counts[level] += nS;
+    const bool cross = nS > 0 && nF > 0;
+    const bool pn = c->p.c > 0.0;
+    if (cross) {
+        if (pn) CK(cross_pn_kick(c, N, pos, vel, mass, is_bh, Sids, nS, Fids, nF, 0.5 * tau, s));
+        CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, tau / 6.0, 0, 0.0, s));
+    }
+    if (nS > 0) CK(step_core(c, N, pos, vel, mass, is_bh, Sids, nS, 0.5 * tau, 1, s));
+    if (nF > 0) CK(hhs_level(c, N, pos, vel, mass, is_bh, Fids, nF, 0.5 * tau, level + 1, s));
+    if (cross) CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, 2.0 * tau / 3.0, 1, tau, s));
+    if (nF > 0) CK(hhs_level(c, N, pos, vel, mass, is_bh, Fids, nF, 0.5 * tau, level + 1, s));
+    if (nS > 0) CK(step_core(c, N, pos, vel, mass, is_bh, Sids, nS, 0.5 * tau, 1, s));
+    if (cross) {
+        CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, tau / 6.0, 0, 0.0, s));
+        if (pn) CK(cross_pn_kick(c, N, pos, vel, mass, is_bh, Sids, nS, Fids, nF, 0.5 * tau, s));
+    }
+    return FSI_OK;
+}
+
+}  // namespace
+
+// =================================================================================
+extern "C" {
+
+void fsi_default_params(fsi_params* p) {
+    if (!p) return;
+    std::memset(p, 0, sizeof *p);
+    p->precision = FSI_FP64;
+    p->eps2 = 0.0;
+    p->eta_ff = 0.2;
+    p->eta_fb = 0.2;
+    p->eta_jerk = 0.1;
+    p->max_level = 40;
+    p->c = 0.0;
+    p->split = 0;
+    p->timeout_ns = 0;
+}
+
+const char* fsi_last_error(void) { return g_err.c_str(); }
+
+int fsi_create(fsi_ctx** out, const fsi_params* p) {
+    if (!out) return fail(FSI_ERR_ARG, "NULL output handle");
+    *out = nullptr;
+    fsi_params q;
+    if (p) q = *p;
+    else fsi_default_params(&q);
+    if (!valid_prec(q.precision)) return fail(FSI_ERR_ARG, "unknown precision %d", q.precision);
+    fsi_ctx* c = new fsi_ctx();
+    c->p = q;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess ||
+        cudaMalloc(&c->err_d, sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->err_d, 0, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->err_h, sizeof(int)) != cudaSuccess ||
+        cudaMallocHost(&c->counts_h, 4 * sizeof(int)) != cudaSuccess) {
+        const char* msg = cudaGetErrorString(cudaGetLastError());
+        delete c;
+        return fail(FSI_ERR_CUDA, "context creation failed: %s", msg);
+    }
+    *out = c;
+    return FSI_OK;
+}
+
+int fsi_destroy(fsi_ctx* c) {
+    if (!c) return FSI_OK;
+    cudaDeviceSynchronize();
+    Buf* bufs[] = {&c->rec[0], &c->rec[1], &c->accrec[0], &c->accrec[1], &c->xc, &c->vc, &c->ac,
+                   &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->mc, &c->bhc, &c->ids[0], &c->ids[1],
+                   &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
+                   &c->iota, &c->steps, &c->step0, &c->counts};
+    for (Buf* b : bufs)
+        if (b->p) cudaFree(b->p);
+    for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
+    for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& b : c->lvS) if (b.p) cudaFree(b.p);
+    for (auto& b : c->lvF) if (b.p) cudaFree(b.p);
+    if (c->err_d) cudaFree(c->err_d);
+    if (c->err_h) cudaFreeHost(c->err_h);
+    if (c->counts_h) cudaFreeHost(c->counts_h);
+    delete c;
+    return FSI_OK;
+}
+
+int fsi_set_params(fsi_ctx* c, const fsi_params* p) {
+    if (!c || !p) return fail(FSI_ERR_ARG, "NULL argument");
+    if (!valid_prec(p->precision)) return fail(FSI_ERR_ARG, "unknown precision %d", p->precision);
+    c->p = *p;
+    return FSI_OK;
+}
+
+int fsi_reserve(fsi_ctx* c, int N, int n) {
+    CK(check_common(c, N));
+    if (n < 0 || n > N) return fail(FSI_ERR_ARG, "bad set size %d", n);
+    const size_t pt = pad_tile(n) * 32;
+    for (int k = 0; k < 2; ++k) {
+        CK(ensure(c->rec[k], pt));
+        CK(ensure(c->accrec[k], pt));
+        CK(ensure(c->ids[k], pad_tile(n) * 4));
+    }
+    Buf* b3[] = {&c->xc, &c->vc, &c->ac, &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->apn};
+    for (Buf* b : b3) CK(ensure(*b, 3 * (size_t)n * 8));
+    CK(ensure(c->mc, (size_t)n * 8));
+    CK(ensure(c->bhc, (size_t)n));
+    CK(ensure(c->bhlist, kMaxBHList * 4));
+    CK(ensure(c->nbh, 16));
+    CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
+    CK(ensure(c->part, (size_t)64 * 3 * n * 8));
+    CK(ensure(c->epart, (size_t)(energy_blocks(n) * 2 + 2) * 8));
+    CU(cudaDeviceSynchronize());
+    return FSI_OK;
+}
+
+int fsi_sync_status(fsi_ctx* c, void* stream) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    CU(cudaStreamSynchronize(S(stream)));
+    CU(cudaMemcpy(c->err_h, c->err_d, sizeof(int), cudaMemcpyDeviceToHost));
+    CU(cudaMemset(c->err_d, 0, sizeof(int)));
+    const int e = *c->err_h;
+    if (e != FSI_OK) fail(e, "device reported status %d", e);
+    return e;
+}
+
+int fsi_accel(fsi_ctx* c, int N, const double* pos, const double* mass, const int* A, int nA,
+              const int* B, int nB, double eps2, double* acc_out, void* stream) {
+    CK(check_common(c, N));
+    if (nA == 0) return FSI_OK;
+    if (nA < 0 || nB < 0 || (!A && nA != N) || (!B && nB != N))
+        return fail(FSI_ERR_ARG, "bad set sizes nA=%d nB=%d N=%d", nA, nB, N);
+    if (!pos || !mass || !acc_out) return fail(FSI_ERR_ARG, "NULL array");
+    const cudaStream_t s = S(stream);
+    const int prec = c->p.precision;
+    const bool same = (A == B) && (nA == nB);
+    CK(ensure(c->rec[0], pad_tile(nA) * 32));
+    CU(launch_pack(prec, N, pos, mass, A, nA, c->rec[0].p, nullptr, s));
+    PairArgs a{};
+    a.irec = c->rec[0].p;
+    a.n_i = nA;
+    a.n_j = nB;
+    a.eps2 = eps2;
+    a.epi.out = acc_out;
+    if (same) {
+        a.jrec = c->rec[0].p;
+        a.check = CHECK_DIAG;
+    } else {
+        CK(ensure(c->rec[1], pad_tile(nB) * 32));
+        CK(ensure(c->ids[0], pad_tile(nA) * 4));
+        CK(ensure(c->ids[1], pad_tile(nB) * 4));
+        CU(launch_pack(prec, N, pos, mass, B, nB, c->rec[1].p, nullptr, s));
+        CU(launch_ids(A, nA, (int)pad_tile(nA), P<int>(c->ids[0]), s));
+        CU(launch_ids(B, nB, (int)pad_tile(nB), P<int>(c->ids[1]), s));
+        a.jrec = c->rec[1].p;
+        a.check = CHECK_IDS;
+        a.iid = P<int>(c->ids[0]);
+        a.jid = P<int>(c->ids[1]);
+    }
+    return run_pair(c, KIND_ACC, a, s);
+}
+
+int fsi_grad(fsi_ctx* c, int N, const double* pos, const double* mass, const double* accg,
+             const int* A, int nA, const int* B, int nB, double eps2, double* grad_out,
+             void* stream) {
+    CK(check_common(c, N));
+    if (nA == 0) return FSI_OK;
+    if (nA < 0 || nB < 0 || (!A && nA != N) || (!B && nB != N))
+        return fail(FSI_ERR_ARG, "bad set sizes nA=%d nB=%d N=%d", nA, nB, N);
+    if (!pos || !mass || !accg || !grad_out) return fail(FSI_ERR_ARG, "NULL array");
+    const cudaStream_t s = S(stream);
+    const int prec = c->p.precision;
+    const bool same = (A == B) && (nA == nB);
+    CK(ensure(c->rec[0], pad_tile(nA) * 32));
+    CK(ensure(c->accrec[0], pad_tile(nA) * 32));
+    CU(launch_pack(prec, N, pos, mass, A, nA, c->rec[0].p, nullptr, s));
+    CU(launch_pack_acc(prec, N, accg, A, nA, c->accrec[0].p, nullptr, s));
+    PairArgs a{};
+    a.irec = c->rec[0].p;
+    a.iacc = c->accrec[0].p;
+    a.n_i = nA;
+    a.n_j = nB;
+    a.eps2 = eps2;
+    a.epi.out = grad_out;
+    if (same) {
+        a.jrec = a.irec;
+        a.jacc = a.iacc;
+        a.check = CHECK_DIAG;
+    } else {
+        CK(ensure(c->rec[1], pad_tile(nB) * 32));
+        CK(ensure(c->accrec[1], pad_tile(nB) * 32));
+        CK(ensure(c->ids[0], pad_tile(nA) * 4));
+        CK(ensure(c->ids[1], pad_tile(nB) * 4));
+        CU(launch_pack(prec, N, pos, mass, B, nB, c->rec[1].p, nullptr, s));
+        CU(launch_pack_acc(prec, N, accg, B, nB, c->accrec[1].p, nullptr, s));
+        CU(launch_ids(A, nA, (int)pad_tile(nA), P<int>(c->ids[0]), s));
+        CU(launch_ids(B, nB, (int)pad_tile(nB), P<int>(c->ids[1]), s));
+        a.jrec = c->rec[1].p;
+        a.jacc = c->accrec[1].p;
+        a.check = CHECK_IDS;
+        a.iid = P<int>(c->ids[0]);
+        a.jid = P<int>(c->ids[1]);
+    }
+    return run_pair(c, KIND_GRAD, a, s);
+}
+
+int fsi_accel_grad(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+                   const int* A, int nA, const int* B, int nB, double eps2, double* acc_out,
+                   double* grad_out, void* stream) {
+    (void)vel;
+    CK(check_common(c, N));
+    if (nA == 0) return FSI_OK;
+    if (nA < 0 || nB < 0 || (!A && nA != N) || (!B && nB != N))
+        return fail(FSI_ERR_ARG, "bad set sizes nA=%d nB=%d N=%d", nA, nB, N);
+    if (!pos || !mass || !acc_out || !grad_out) return fail(FSI_ERR_ARG, "NULL array");
+    const cudaStream_t s = S(stream);
+    const int prec = c->p.precision;
+    const bool same = (A == B) && (nA == nB);
+    CK(ensure(c->rec[0], pad_tile(nA) * 32));
+    CK(ensure(c->accrec[0], pad_tile(nA) * 32));
+    CU(launch_pack(prec, N, pos, mass, A, nA, c->rec[0].p, nullptr, s));
+    if (same) {
+        PairArgs a{};
+        a.irec = a.jrec = c->rec[0].p;
+        a.n_i = a.n_j = nA;
+        a.check = CHECK_DIAG;
+        a.eps2 = eps2;
+        a.epi.out = acc_out;
+        a.epi.accrec = c->accrec[0].p;
+        CK(run_pair(c, KIND_ACC, a, s));
+        a.iacc = a.jacc = c->accrec[0].p;
+        a.epi = Epi{};
+        a.epi.out = grad_out;
+        return run_pair(c, KIND_GRAD, a, s);
+    }
+    if (!A || !B) return fail(FSI_ERR_ARG, "a NULL (all-particle) list overlaps any other list");
+    CK(ensure(c->mark, (size_t)N));
+    CU(cudaMemsetAsync(c->mark.p, 0, (size_t)N, s));
+    CU(launch_check_disjoint(N, A, nA, B, nB, P<unsigned char>(c->mark), c->err_d, s));
+    CK(ensure(c->rec[1], pad_tile(nB) * 32));
+    CK(ensure(c->accrec[1], pad_tile(nB) * 32));
+    CU(launch_pack(prec, N, pos, mass, B, nB, c->rec[1].p, nullptr, s));
+    PairArgs a{};
+    a.check = CHECK_NONE;
+    a.eps2 = eps2;
+    a.irec = c->rec[0].p; a.jrec = c->rec[1].p; a.n_i = nA; a.n_j = nB;
+    a.epi.out = acc_out;
+    a.epi.accrec = c->accrec[0].p;
+    CK(run_pair(c, KIND_ACC, a, s));
+    PairArgs b{};
+    b.check = CHECK_NONE;
+    b.eps2 = eps2;
+    b.irec = c->rec[1].p; b.jrec = c->rec[0].p; b.n_i = nB; b.n_j = nA;
+    b.epi.accrec = c->accrec[1].p;
+    CK(run_pair(c, KIND_ACC, b, s));
+    a.iacc = c->accrec[0].p;
+    a.jacc = c->accrec[1].p;
+    a.epi = Epi{};
+    a.epi.out = grad_out;
+    return run_pair(c, KIND_GRAD, a, s);
+}
+
+int fsi_pn_accel(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+                 const unsigned char* is_bh, double cl, const int* A, int nA, const int* B, int nB,
+                 double* out, void* stream) {
+    CK(check_common(c, N));
+    if (nA < 0 || nB < 0 || (!A && nA != N) || (!B && nB != N))
+        return fail(FSI_ERR_ARG, "bad set sizes nA=%d nB=%d N=%d", nA, nB, N);
+    if (!(cl > 0.0)) return fail(FSI_ERR_ARG, "speed of light must be positive");
+    if (nA == 0) return FSI_OK;
+    if (!pos || !vel || !mass || !is_bh || !out) return fail(FSI_ERR_ARG, "NULL array");
+    CU(launch_pn_pairs(N, pos, vel, mass, is_bh, cl, A, nA, B, nB, out, c->err_d, S(stream)));
+    return FSI_OK;
+}
+
+int fsi_step(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+             const unsigned char* is_bh, const int* idx, int n, double h, int nsteps,
+             void* stream) {
+    CK(check_common(c, N));
+    if (n < 0 || (!idx && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (nsteps < 0) return fail(FSI_ERR_ARG, "nsteps must be >= 0");
+    if (n == 0 || nsteps == 0) return FSI_OK;
+    if (!pos || !vel || !mass) return fail(FSI_ERR_ARG, "NULL array");
+    return step_core(c, N, pos, vel, mass, is_bh, idx, n, h, nsteps, S(stream));
+}
+
+int fsi_timesteps(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+                  const int* Pids, int n, double* step_out, void* stream) {
+    CK(check_common(c, N));
+    if (n < 0 || (!Pids && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (n == 0) return FSI_OK;
+    if (!pos || !vel || !mass || !step_out) return fail(FSI_ERR_ARG, "NULL array");
+    return timesteps_core(c, N, pos, vel, mass, Pids, n, step_out, S(stream));
+}
+
+int fsi_energy(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+               const int* Pids, int n, double* out, void* stream) {
+    CK(check_common(c, N));
+    if (n < 0 || (!Pids && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (!pos || !vel || !mass || !out) return fail(FSI_ERR_ARG, "NULL array");
+    const cudaStream_t s = S(stream);
+    if (n == 0) {
+        CU(cudaMemsetAsync(out, 0, 2 * sizeof(double), s));
+        return FSI_OK;
+    }
+    const double* xc = pos;
+    const double* vc = vel;
+    const double* mc = mass;
+    if (Pids) {
+        CK(ensure(c->xc, 3 * (size_t)n * 8));
+        CK(ensure(c->vc, 3 * (size_t)n * 8));
+        CK(ensure(c->mc, (size_t)n * 8));
+        CU(launch_gather3(N, pos, Pids, n, P<double>(c->xc), s));
+        CU(launch_gather3(N, vel, Pids, n, P<double>(c->vc), s));
+        CU(launch_gather1(N, mass, Pids, n, P<double>(c->mc), s));
+        xc = P<double>(c->xc);
+        vc = P<double>(c->vc);
+        mc = P<double>(c->mc);
+    }
+    CK(ensure(c->epart, (size_t)(energy_blocks(n) * 2 + 2) * 8));
+    CU(launch_energy(n, xc, vc, mc, c->p.eps2, P<double>(c->epart), out, c->err_d, s));
+    return FSI_OK;
+}
+
+int fsi_hhs_interval(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                     const unsigned char* is_bh, double tau, void* stream) {
+    CK(check_common(c, N));
+    if (!pos || !vel || !mass) return fail(FSI_ERR_ARG, "NULL array");
+    if (!(tau > 0.0)) return fail(FSI_ERR_ARG, "tau must be positive");
+    if (c->p.c > 0.0 && !is_bh) return fail(FSI_ERR_ARG, "PN on (c > 0) needs is_bh");
+    const cudaStream_t s = S(stream);
+    CK(ensure(c->iota, (size_t)N * 4));
+    CK(ensure(c->step0, (size_t)N * 8));
+    CK(ensure(c->counts, 16));
+    CU(launch_iota(N, P<int>(c->iota), s));
+    c->level_counts.assign(c->p.max_level + 1, 0);
+    c->max_level_used = 0;
+    c->max_level_hit = 0;
+    CK(hhs_level(c, N, pos, vel, mass, is_bh, P<int>(c->iota), N, tau, 0, s));
+    if (c->max_level_hit) return fail(FSI_ERR_MAXLEVEL, "a particle needed a level deeper than %d", c->p.max_level);
+    return FSI_OK;
+}
+
+int fsi_level_stats(fsi_ctx* c, long long* counts, int max) {
+    if (!c || (!counts && max > 0)) return fail(FSI_ERR_ARG, "NULL argument");
+    const int used = std::min<int>((int)c->level_counts.size(), c->max_level_used + 1);
+    for (int k = 0; k < max; ++k) counts[k] = k < (int)c->level_counts.size() ? c->level_counts[k] : 0;
+    return used;
+}
+
+int fsi_profile(fsi_ctx* c, int enable) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    c->profiling = enable != 0;
+    return FSI_OK;
+}
+
+int fsi_profile_read(fsi_ctx* c, long long* launches, double* ms) {
+    if (!c || !launches || !ms) return fail(FSI_ERR_ARG, "NULL argument");
+    for (int k = 0; k < 3; ++k) { launches[k] = 0; ms[k] = 0.0; }
+    for (auto& r : c->prof) {
+        float t = 0.f;
+        CU(cudaEventSynchronize(r.b));
+        CU(cudaEventElapsedTime(&t, r.a, r.b));
+        if (r.kind >= 0 && r.kind < 3) { launches[r.kind] += 1; ms[r.kind] += t; }
+        c->ev_pool.push_back(r.a);
+        c->ev_pool.push_back(r.b);
+    }
+    c->prof.clear();
+    return FSI_OK;
+}
+
+long long fsi_launch_count(void) { return g_launches.load(); }
+
+int fsi_fma_probe(int fp64, int blocks, int iters, void* sink, double* flops, void* stream) {
+    if (blocks <= 0 || iters <= 0 || !sink) return fail(FSI_ERR_ARG, "bad probe arguments");
+    CU(launch_fma_probe(fp64, blocks, iters, sink, S(stream)));
+    if (flops) *flops = (double)blocks * 256.0 * (double)iters * 4.0 * 8.0 * 2.0;
+    return FSI_OK;
+}
+
+}  // extern "C"

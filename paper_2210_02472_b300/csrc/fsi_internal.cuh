@@ -1,0 +1,194 @@
+// fsi_internal.cuh -- internal types and device helpers of libfsi (not part of the ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include "../../include/fsi.h"
+
+namespace fsi {
+
+// ---------------------------------------------------------------------------------
+// Compact particle records.  A "set" of n particles is gathered once into records so
+// that the O(n^2) kernels read contiguous, 16-byte-aligned tiles with bulk copies.
+//
+//  FP64 position record (32 B):  double4 (x, y, z, m)
+//  FP64 accel record    (32 B):  double4 (ax, ay, az, 0)
+//  MIXED position record (32 B): float4 (xh, yh, zh, m), float4 (xl, yl, zl, 0)
+//        with xh = fl32(x) and xl = fl32(x - xh): xh + xl carries ~48 bits of x, so a
+//        pair difference (xh_j - xh_i) + (xl_j - xl_i) is accurate to FP32 precision
+//        relative to the separation even when |x| >> |r_ij|.
+//  MIXED accel record   (16 B):  float4 (ax, ay, az, 0)
+// ---------------------------------------------------------------------------------
+struct alignas(32) D4 { double x, y, z, w; };   // 32-byte aligned FP64 quadruple
+__host__ __device__ __forceinline__ D4 make_d4(double x, double y, double z, double w) {
+    D4 r; r.x = x; r.y = y; r.z = z; r.w = w; return r;
+}
+struct RecF64 { double x, y, z, m; };
+struct RecMix { float4 hi; float4 lo; };
+static_assert(sizeof(RecF64) == 32 && sizeof(RecMix) == 32, "record size");
+
+constexpr int kThreads = 256;      // threads per pair-kernel CTA
+constexpr int kTileJ = 256;        // sources per shared-memory tile
+constexpr int kStages = 3;         // bulk-copy pipeline depth
+
+enum Kind { KIND_ACC = 0, KIND_GRAD = 1 };
+enum Check { CHECK_NONE = 0, CHECK_DIAG = 1, CHECK_IDS = 2 };
+
+// Epilogue of a pair pass, applied by the owner of particle i once its sum is complete.
+//   out     : if non-null, out[c * n_i + i] = result_c              (3 x n_i FP64)
+//   kick    : if x != null:  v += c_kick * (base + c_grad * result)  (base = a_i for
+//             the gradient pass, 0 otherwise -> v += c_kick * result for acc)
+//             then x += c_drift * v, and the new position record is written to rec_out.
+//   accrec  : if non-null, the accel record of i is written there (acc pass feeding grad)
+struct Epi {
+    double* out;
+    double* x;          // compact 3 x n_i, FP64 master positions (may be null)
+    double* v;          // compact 3 x n_i
+    const double* base; // compact 3 x n_i (grad pass: a_i), may be null
+    double c_kick, c_grad, c_drift;
+    void* rec_out;      // position records for the next pass
+    void* accrec;       // accel records (FP64: RecF64-like double4; MIXED: float4)
+};
+
+struct PairArgs {
+    const void* irec; const void* jrec;   // position records
+    const void* iacc; const void* jacc;   // accel records (gradient pass)
+    const int* iid; const int* jid;       // global ids (CHECK_IDS); jid padded to 4
+    int n_i, n_j;
+    int check;                            // Check
+    int j_per_split;                      // sources per blockIdx.y slice
+    double eps2;
+    double* part;                         // split > 1: partial sums [split][3][n_i]
+    int* err;
+    long long timeout_ns;
+    Epi epi;
+};
+
+// ---------------------------------------------------------------------------------
+// Error word helpers.
+__device__ __forceinline__ void set_error(int* err, int code) {
+    if (err) atomicCAS(err, 0, code);
+}
+
+// mbar_wait_bounded with err == nullptr only gives up silently.
+
+__device__ __forceinline__ long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return (long long)t;
+}
+
+// ---------------------------------------------------------------------------------
+// mbarrier + bulk-copy (TMA, non-tensor) helpers, inline PTX.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" :: "r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.release.cta.shared::cta.b64 _, [%0], %1;"
+                 :: "r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+
+// Global -> shared bulk copy completing on `bar`.  dst, src 16-byte aligned; bytes a
+// multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+        :: "r"(smem_u32(dst)), "l"(src), "r"(bytes), "r"(smem_u32(bar)) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\t"
+        "mbarrier.try_wait.parity.acquire.cta.shared::cta.b64 p, [%1], %2;\n\t"
+        "selp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(ok) : "r"(smem_u32(bar)), "r"(parity) : "memory");
+    return ok != 0;
+}
+
+// Bounded wait: spins until the phase with `parity` completes or the wall-clock budget
+// runs out; on timeout latches FSI_ERR_TIMEOUT and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity,
+                                                  long long budget_ns, int* err) {
+    if (mbar_try_wait(bar, parity)) return true;
+    long long t0 = global_ns();
+    while (true) {
+        if (mbar_try_wait(bar, parity)) return true;
+        if (global_ns() - t0 > budget_ns) {
+            set_error(err, FSI_ERR_TIMEOUT);
+            return false;
+        }
+    }
+}
+
+// FP32 reciprocal square root from the hardware approximation (MUFU).
+__device__ __forceinline__ float rsqrt_hw(float x) {
+    float y;
+    asm("rsqrt.approx.ftz.f32 %0, %1;" : "=f"(y) : "f"(x));
+    return y;
+}
+
+}  // namespace fsi
+
+// ---------------------------------------------------------------------------------
+// Host-side launchers (defined in pair_kernels.cu / aux_kernels.cu).
+namespace fsi {
+void note_launch();                 // counts every kernel launch (fsi_launch_count)
+cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* sink, cudaStream_t s);
+cudaError_t launch_pair(int precision, int kind, const PairArgs& a, int split, cudaStream_t s);
+cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s);
+int pair_i_per_cta_for(int precision, int kind);   // active particles per CTA
+
+cudaError_t launch_pack(int precision, int N, const double* pos, const double* mass,
+                        const int* idx, int n, void* rec, double* xc, cudaStream_t s);
+cudaError_t launch_pack_acc(int precision, int N, const double* accg, const int* idx, int n,
+                            void* accrec, double* ac, cudaStream_t s);
+cudaError_t launch_gather3(int N, const double* src, const int* idx, int n, double* dst,
+                           cudaStream_t s);
+cudaError_t launch_scatter3(int N, const double* src, const int* idx, int n, double* dst,
+                            cudaStream_t s);
+cudaError_t launch_scatter_axpy3(int N, const double* a, const int* idx, int n, double w,
+                                 double* v, cudaStream_t s);
+cudaError_t launch_gather1(int N, const double* src, const int* idx, int n, double* dst,
+                           cudaStream_t s);
+cudaError_t launch_gather_u8(const unsigned char* src, const int* idx, int n,
+                             unsigned char* dst, cudaStream_t s);
+cudaError_t launch_ids(const int* idx, int n, int cap, int* ids, cudaStream_t s);
+cudaError_t launch_check_disjoint(int N, const int* A, int nA, const int* B, int nB,
+                                  unsigned char* mark, int* err, cudaStream_t s);
+cudaError_t launch_kick_drift(int precision, int n, double* xc, double* vc, const double* ac,
+                              double c_kick, double c_drift, const void* rec_in, void* rec_out,
+                              cudaStream_t s);
+cudaError_t launch_axpy3(int n, double* v, const double* a, double w, cudaStream_t s);
+cudaError_t launch_axpby3(int n, const double* a, const double* g, double c, double* out,
+                          cudaStream_t s);
+constexpr int kMaxBHList = 1024;   // black holes per set handled by the PN kernels
+constexpr int kPnPartCtas = 64;    // CTAs per black hole in the PN reduction
+cudaError_t launch_bh_list(int n, const unsigned char* bhc, int* bh_list, int* n_bh, int* err,
+                           cudaStream_t s);
+cudaError_t launch_pn(int n, const double* xc, const double* vc, const double* mc,
+                      const unsigned char* bhc, double c, const int* bh_list, const int* n_bh,
+                      int max_bh, double* apn, double* part, int* err, cudaStream_t s);
+cudaError_t launch_pn_pairs(int N, const double* pos, const double* vel, const double* mass,
+                            const unsigned char* is_bh, double c, const int* A, int nA,
+                            const int* B, int nB, double* out, int* err, cudaStream_t s);
+int energy_blocks(int n);
+cudaError_t launch_energy(int n, const double* xc, const double* vc, const double* mc,
+                          double eps2, double* part, double* out, int* err, cudaStream_t s);
+cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
+                             double eta_ff, double eta_fb, double eta_jerk, double eps2,
+                             double* step, int* err, cudaStream_t s);
+cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step0, int level0,
+                               cudaStream_t s);
+cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,
+                             int* S, int* F, int* counts, cudaStream_t s);
+cudaError_t launch_iota(int n, int* ids, cudaStream_t s);
+}  // namespace fsi

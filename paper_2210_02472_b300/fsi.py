@@ -1,0 +1,291 @@
+"""Thin ctypes binding of libfsi's C ABI (include/fsi.h).
+
+Argument marshalling only: every arithmetic step runs in the CUDA library.  Arrays are
+torch CUDA tensors in FP64 (positions/velocities (3, N) contiguous, masses (N,)), index
+lists int32 CUDA tensors, black-hole flags uint8/bool CUDA tensors.  Work is enqueued on
+torch's current CUDA stream.
+
+Importing this module loads ``libfsi.so`` and raises ImportError if it is missing: there
+is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from pathlib import Path
+from typing import Optional
+
+import torch
+
+_LIB_PATH = Path(__file__).resolve().parent / "libfsi.so"
+if not _LIB_PATH.exists():
+    raise ImportError(f"libfsi.so not built at {_LIB_PATH}; run "
+                      "`python -m paper_2210_02472_b300.build` (needs nvcc)")
+_lib = C.CDLL(str(_LIB_PATH))
+
+FSI_OK = 0
+FSI_ERR_ARG = -1
+FSI_ERR_CUDA = -2
+FSI_ERR_NONFINITE = -3
+FSI_ERR_COINCIDENT = -4
+FSI_ERR_TIMEOUT = -5
+FSI_ERR_MAXLEVEL = -6
+FSI_ERR_UNSUPPORTED = -7
+FSI_ERR_NOMEM = -8
+FSI_FP64 = 0
+FSI_MIXED = 1
+
+EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params", "fsi_reserve",
+            "fsi_last_error", "fsi_sync_status", "fsi_accel", "fsi_grad", "fsi_accel_grad",
+            "fsi_pn_accel", "fsi_step", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
+            "fsi_level_stats", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
+            "fsi_fma_probe"]
+
+
+class fsi_params(C.Structure):
+    _fields_ = [("precision", C.c_int), ("eps2", C.c_double), ("eta_ff", C.c_double),
+                ("eta_fb", C.c_double), ("eta_jerk", C.c_double), ("max_level", C.c_int),
+                ("c", C.c_double), ("split", C.c_int), ("timeout_ns", C.c_longlong)]
+
+
+_vp, _ip, _dp = C.c_void_p, C.c_int, C.c_double
+_lib.fsi_default_params.argtypes = [C.POINTER(fsi_params)]
+_lib.fsi_default_params.restype = None
+_lib.fsi_create.argtypes = [C.POINTER(_vp), C.POINTER(fsi_params)]
+_lib.fsi_destroy.argtypes = [_vp]
+_lib.fsi_set_params.argtypes = [_vp, C.POINTER(fsi_params)]
+_lib.fsi_reserve.argtypes = [_vp, _ip, _ip]
+_lib.fsi_last_error.restype = C.c_char_p
+_lib.fsi_sync_status.argtypes = [_vp, _vp]
+_lib.fsi_accel.argtypes = [_vp, _ip, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp, _vp]
+_lib.fsi_grad.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp, _vp]
+_lib.fsi_accel_grad.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp, _vp, _vp]
+_lib.fsi_pn_accel.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp, _ip, _vp, _ip, _vp, _vp]
+_lib.fsi_step.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _vp, _ip, _dp, _ip, _vp]
+_lib.fsi_timesteps.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
+_lib.fsi_energy.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
+_lib.fsi_hhs_interval.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp]
+_lib.fsi_level_stats.argtypes = [_vp, C.POINTER(C.c_longlong), _ip]
+_lib.fsi_profile.argtypes = [_vp, _ip]
+_lib.fsi_profile_read.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
+_lib.fsi_launch_count.restype = C.c_longlong
+_lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
+
+
+class FsiError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        msg = _lib.fsi_last_error().decode(errors="replace")
+        super().__init__(f"{what}: status {code} ({msg})")
+        self.code = code
+
+
+def _check(code: int, what: str) -> None:
+    if code != FSI_OK:
+        raise FsiError(code, what)
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+
+
+def _f64(t: torch.Tensor, shape, name: str) -> int:
+    if not (t.is_cuda and t.dtype == torch.float64 and t.is_contiguous()):
+        raise TypeError(f"{name} must be a contiguous CUDA float64 tensor")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+    return t.data_ptr()
+
+
+def _ids(t: Optional[torch.Tensor], N: int, name: str):
+    if t is None:
+        return None, N
+    if not (t.is_cuda and t.dtype == torch.int32 and t.is_contiguous() and t.dim() == 1):
+        raise TypeError(f"{name} must be a contiguous 1-D CUDA int32 tensor")
+    return (t.data_ptr() if t.numel() else None), int(t.numel())
+
+
+def _u8(t: Optional[torch.Tensor], N: int, name: str):
+    if t is None:
+        return None
+    if t.dtype == torch.bool:
+        t = t.view(torch.uint8)
+    if not (t.is_cuda and t.dtype == torch.uint8 and t.is_contiguous() and t.numel() == N):
+        raise TypeError(f"{name} must be a contiguous CUDA uint8/bool tensor of N entries")
+    return t.data_ptr()
+
+
+class Context:
+    """Owns an fsi_ctx (device workspace + error word) on the current CUDA device."""
+
+    def __init__(self, precision: str = "fp64", eps2: float = 0.0, eta_ff: float = 0.2,
+                 eta_fb: float = 0.2, eta_jerk: float = 0.1, max_level: int = 40,
+                 c: float = 0.0, split: int = 0, timeout_ns: int = 0):
+        p = fsi_params()
+        _lib.fsi_default_params(C.byref(p))
+        p.precision = {"fp64": FSI_FP64, "mixed": FSI_MIXED}[precision]
+        p.eps2, p.eta_ff, p.eta_fb, p.eta_jerk = eps2, eta_ff, eta_fb, eta_jerk
+        p.max_level, p.c, p.split, p.timeout_ns = max_level, c, split, timeout_ns
+        self.params = p
+        self.precision = precision
+        h = _vp()
+        _check(_lib.fsi_create(C.byref(h), C.byref(p)), "fsi_create")
+        self.handle = h
+
+    def close(self) -> None:
+        if getattr(self, "handle", None):
+            _lib.fsi_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def fsi_reserve(ctx: Context, N: int, n: int) -> None:
+    _check(_lib.fsi_reserve(ctx.handle, N, n), "fsi_reserve")
+
+
+def fsi_sync_status(ctx: Context, stream=None) -> int:
+    return int(_lib.fsi_sync_status(ctx.handle, _stream(stream)))
+
+
+def fsi_accel(ctx: Context, pos, mass, A=None, B=None, eps2: float = 0.0, out=None, stream=None):
+    N = mass.numel()
+    pa, nA = _ids(A, N, "A")
+    pb, nB = _ids(B, N, "B")
+    if out is None:
+        out = torch.empty((3, nA), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_accel(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
+                          pa, nA, pb, nB, float(eps2), _f64(out, (3, nA), "out"), _stream(stream)),
+           "fsi_accel")
+    return out
+
+
+def fsi_grad(ctx: Context, pos, mass, accg, A=None, B=None, eps2: float = 0.0, out=None,
+             stream=None):
+    N = mass.numel()
+    pa, nA = _ids(A, N, "A")
+    pb, nB = _ids(B, N, "B")
+    if out is None:
+        out = torch.empty((3, nA), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_grad(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
+                         _f64(accg, (3, N), "accg"), pa, nA, pb, nB, float(eps2),
+                         _f64(out, (3, nA), "out"), _stream(stream)), "fsi_grad")
+    return out
+
+
+def fsi_accel_grad(ctx: Context, pos, vel, mass, A=None, B=None, eps2: float = 0.0,
+                   acc_out=None, grad_out=None, stream=None):
+    N = mass.numel()
+    pa, nA = _ids(A, N, "A")
+    pb, nB = _ids(B, N, "B")
+    if A is not None and B is not None and A is B:
+        pb = pa
+    if acc_out is None:
+        acc_out = torch.empty((3, nA), dtype=torch.float64, device=pos.device)
+    if grad_out is None:
+        grad_out = torch.empty((3, nA), dtype=torch.float64, device=pos.device)
+    pv = _f64(vel, (3, N), "vel") if vel is not None else None
+    _check(_lib.fsi_accel_grad(ctx.handle, N, _f64(pos, (3, N), "pos"), pv, _f64(mass, (N,), "mass"),
+                               pa, nA, pb, nB, float(eps2), _f64(acc_out, (3, nA), "acc_out"),
+                               _f64(grad_out, (3, nA), "grad_out"), _stream(stream)),
+           "fsi_accel_grad")
+    return acc_out, grad_out
+
+
+def fsi_pn_accel(ctx: Context, pos, vel, mass, is_bh, c: float, A=None, B=None, out=None,
+                 stream=None):
+    N = mass.numel()
+    pa, nA = _ids(A, N, "A")
+    pb, nB = _ids(B, N, "B")
+    if out is None:
+        out = torch.empty((3, nA), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_pn_accel(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                             _f64(mass, (N,), "mass"), _u8(is_bh, N, "is_bh"), float(c), pa, nA,
+                             pb, nB, _f64(out, (3, nA), "out"), _stream(stream)), "fsi_pn_accel")
+    return out
+
+
+def fsi_step(ctx: Context, pos, vel, mass, h: float, nsteps: int = 1, is_bh=None, idx=None,
+             stream=None) -> None:
+    """nsteps FSI cycles of step h, in place on pos/vel."""
+    N = mass.numel()
+    pi, n = _ids(idx, N, "idx")
+    _check(_lib.fsi_step(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                         _f64(mass, (N,), "mass"), _u8(is_bh, N, "is_bh"), pi, n, float(h),
+                         int(nsteps), _stream(stream)), "fsi_step")
+
+
+def fsi_timesteps(ctx: Context, pos, vel, mass, P=None, out=None, stream=None):
+    N = mass.numel()
+    pp, n = _ids(P, N, "P")
+    if out is None:
+        out = torch.empty((n,), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_timesteps(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                              _f64(mass, (N,), "mass"), pp, n, _f64(out, (n,), "out"),
+                              _stream(stream)), "fsi_timesteps")
+    return out
+
+
+def fsi_energy(ctx: Context, pos, vel, mass, P=None, out=None, stream=None):
+    """Device tensor (2,): kinetic and potential energy of the set."""
+    N = mass.numel()
+    pp, n = _ids(P, N, "P")
+    if out is None:
+        out = torch.empty((2,), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_energy(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                           _f64(mass, (N,), "mass"), pp, n, _f64(out, (2,), "out"),
+                           _stream(stream)), "fsi_energy")
+    return out
+
+
+def fsi_hhs_interval(ctx: Context, pos, vel, mass, tau: float, is_bh=None, stream=None) -> int:
+    """One HHS interval in place; returns FSI_OK or FSI_ERR_MAXLEVEL (interval completed)."""
+    N = mass.numel()
+    code = _lib.fsi_hhs_interval(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                                 _f64(mass, (N,), "mass"), _u8(is_bh, N, "is_bh"), float(tau),
+                                 _stream(stream))
+    if code not in (FSI_OK, FSI_ERR_MAXLEVEL):
+        raise FsiError(code, "fsi_hhs_interval")
+    return int(code)
+
+
+def fsi_level_stats(ctx: Context, max_levels: int = 64):
+    counts = (C.c_longlong * max_levels)()
+    used = _lib.fsi_level_stats(ctx.handle, counts, max_levels)
+    return [int(x) for x in counts[:max(used, 0)]]
+
+
+def fsi_profile(ctx: Context, enable: bool = True) -> None:
+    """Record an event pair around every pair-kernel launch on its launch stream."""
+    _check(_lib.fsi_profile(ctx.handle, int(bool(enable))), "fsi_profile")
+
+
+def fsi_profile_read(ctx: Context):
+    """{kind: (launches, milliseconds)} for kinds 'acc', 'grad', 'finalize'; clears."""
+    n = (C.c_longlong * 3)()
+    ms = (C.c_double * 3)()
+    _check(_lib.fsi_profile_read(ctx.handle, n, ms), "fsi_profile_read")
+    return {k: (int(n[i]), float(ms[i])) for i, k in enumerate(("acc", "grad", "finalize"))}
+
+
+def fsi_launch_count() -> int:
+    """Kernels launched by libfsi in this process."""
+    return int(_lib.fsi_launch_count())
+
+
+def fsi_fma_probe(fp64: bool, blocks: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Enqueue the FMA throughput probe; returns its nominal flop count."""
+    f = C.c_double()
+    _check(_lib.fsi_fma_probe(int(bool(fp64)), int(blocks), int(iters), sink.data_ptr(),
+                              C.byref(f), _stream(stream)), "fsi_fma_probe")
+    return f.value

@@ -1,0 +1,379 @@
+"""Parity of the CUDA library (through its C ABI) with the FP64 CPU oracle.
+
+Tolerances (per particle, max component error):
+  FP64 path   1e-12 of the oracle vector's norm (every pair term in FP64; only the
+              summation order differs).
+  MIXED path  acceleration: 1e-6 of S_i = sum_j m_j / r_ij^2, the sum of the absolute
+              pair-term magnitudes, and a median of 2e-7 of |a_i|.  Derivation: a pair
+              term carries about five FP32 roundings (u = 2^-24 = 6e-8) on top of a
+              separation that is itself FP32-accurate (hi/lo split), i.e. <= ~4u = 2.4e-7
+              of its magnitude, and the FP32 partial sum over one source tile adds up to
+              another ~4u of the tile's term magnitudes before it is added in FP64; the
+              errors of different terms add at most linearly, so the sum is good to
+              ~8u S_i = 5e-7 S_i (observed up to 5.1e-7), bounded here by 16u = 1e-6.
+              Relative to |a_i| the error is larger where terms cancel.
+              gradient: the a_j - a_i differences are taken in FP32 from FP32 copies of
+              the accelerations, so the bound is relative to the scale
+              sum_j m_j (|a_i| + |a_j|) / r^3 (checked as 1e-5 of that scale).
+"""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2210_02472_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+PRECS = ["fp64", "mixed"]
+TOL = {"fp64": 1e-12, "mixed": 1e-6}
+TOL_MED = {"fp64": 1e-13, "mixed": 2e-7}
+
+
+@pytest.fixture(scope="module")
+def F():
+    oracle.set_threads(os.cpu_count() or 1)
+    from paper_2210_02472_b300 import fsi
+    return fsi
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+def ids(a):
+    return None if a is None else dev(np.asarray(a, dtype=np.int32), torch.int32)
+
+
+def host(t):
+    torch.cuda.synchronize()
+    return t.detach().cpu().numpy()
+
+
+def rel_err(got, ref):
+    nrm = np.linalg.norm(ref, axis=0)
+    nrm = np.where(nrm > 0, nrm, 1.0)
+    return np.abs(got - ref).max(axis=0) / nrm
+
+
+def abs_scale(pos, mass, A=None, B=None, eps2=0.0):
+    """S_i = sum_{j in B, j != i} m_j / (r_ij^2 + eps2) for i in A (numpy, chunked)."""
+    N = mass.shape[0]
+    A = np.arange(N) if A is None else np.asarray(A)
+    B = np.arange(N) if B is None else np.asarray(B)
+    pb, mb = pos[:, B], mass[B]
+    out = np.zeros(len(A))
+    for k, i in enumerate(A):
+        d = pb - pos[:, [i]]
+        r2 = (d * d).sum(axis=0) + eps2
+        w = np.where(B != i, mb / np.where(r2 > 0, r2, 1.0), 0.0)
+        out[k] = w.sum()
+    return out
+
+
+def assert_close(got, ref, prec, what="", scale=None):
+    e = rel_err(got, ref)
+    assert np.all(np.isfinite(got)), what
+    assert np.median(e) <= TOL_MED[prec], (what, e.max(), np.median(e))
+    if prec == "fp64" or scale is None:
+        assert e.max() <= (TOL[prec] if prec == "fp64" else 5e-5), (what, e.max(), np.median(e))
+    if prec == "mixed" and scale is not None:
+        es = np.abs(got - ref).max(axis=0) / scale
+        assert es.max() <= TOL[prec], (what, es.max(), e.max(), np.median(e))
+
+
+# ----------------------------------------------------------------------------- acc
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [2, 3, 255, 1024, 3001])
+def test_accel_same_set(F, prec, n):
+    c = inputs.plummer(n, 100 + n, imf="kroupa")
+    ref = oracle.acc(c.pos, c.mass)
+    with F.Context(prec) as ctx:
+        got = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(got, ref, prec, f"n={n}", abs_scale(c.pos, c.mass))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_accel_single_particle_and_empty(F, prec):
+    c = inputs.plummer(1, 5)
+    with F.Context(prec) as ctx:
+        got = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass)))
+        assert np.all(got == 0.0)
+        e = F.fsi_accel(ctx, dev(c.pos), dev(c.mass), A=ids(np.zeros(0)), B=None)
+        assert e.shape == (3, 0)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_accel_general_overlapping_lists(F, prec):
+    c = inputs.plummer(2000, 7, imf="kroupa")
+    A = inputs.random_subset(2000, 333, 1)
+    B = inputs.random_subset(2000, 1500, 2)       # overlaps A: self pairs by id
+    ref = oracle.acc(c.pos, c.mass, A, B)
+    with F.Context(prec) as ctx:
+        got = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass), ids(A), ids(B)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(got, ref, prec, scale=abs_scale(c.pos, c.mass, A, B))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_accel_softened_with_coincident_points(F, prec):
+    c = inputs.plummer(700, 8)
+    c.pos[:, 5] = c.pos[:, 6]                    # coincident distinct particles
+    eps2 = 1e-4
+    ref = oracle.acc(c.pos, c.mass, eps2=eps2)
+    with F.Context(prec) as ctx:
+        got = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass), eps2=eps2))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(got, ref, prec, scale=abs_scale(c.pos, c.mass, eps2=eps2))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_coincident_unsoftened_is_reported(F, prec):
+    c = inputs.plummer(300, 9)
+    c.pos[:, 10] = c.pos[:, 11]
+    with F.Context(prec) as ctx:
+        F.fsi_accel(ctx, dev(c.pos), dev(c.mass))
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_NONFINITE
+        # the error word is cleared by the read
+        F.fsi_accel(ctx, dev(inputs.plummer(300, 10).pos), dev(c.mass))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_split_factor_does_not_change_results(F, prec):
+    c = inputs.plummer(5000, 11, imf="kroupa")
+    outs = []
+    for split in (1, 3, 7):
+        with F.Context(prec, split=split) as ctx:
+            outs.append(host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass))))
+    for o in outs[1:]:
+        e = rel_err(o, outs[0])
+        assert e.max() <= (1e-13 if prec == "fp64" else 1e-9)
+
+
+# ----------------------------------------------------------------------------- grad
+def grad_scale(pos, mass, accg, A, B):
+    """sum_j m_j (|a_i| + |a_j|) / r^3 per active particle (numpy, small sizes)."""
+    an = np.linalg.norm(accg, axis=0)
+    out = np.zeros(len(A))
+    for k, i in enumerate(A):
+        d = pos[:, B] - pos[:, [i]]
+        r = np.linalg.norm(d, axis=0)
+        m = (B != i)
+        out[k] = (mass[B][m] * (an[i] + an[B][m]) / r[m] ** 3).sum()
+    return out
+
+
+def assert_grad_close(got, ref, prec, scale):
+    if prec == "fp64":
+        assert_close(got, ref, prec)
+    else:
+        e = np.abs(got - ref).max(axis=0) / scale
+        assert e.max() <= 1e-5, e.max()
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("general", [False, True])
+def test_grad_given_field(F, prec, general):
+    n = 1500
+    c = inputs.plummer(n, 12, imf="kroupa")
+    accg = inputs.random_field(n, 13)
+    if general:
+        A = inputs.random_subset(n, 200, 3)
+        B = inputs.random_subset(n, 900, 4)
+    else:
+        A = B = None
+    ref = oracle.grad(c.pos, c.mass, accg, A, B)
+    with F.Context(prec) as ctx:
+        Ad = ids(A)
+        Bd = Ad if (A is None and B is None) else ids(B)
+        got = host(F.fsi_grad(ctx, dev(c.pos), dev(c.mass), dev(accg), Ad, Bd))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    Aa = np.arange(n) if A is None else A
+    Ba = np.arange(n) if B is None else B
+    assert_grad_close(got, ref, prec, grad_scale(c.pos, c.mass, accg, Aa, Ba))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [2, 1000, 2333])
+def test_accel_grad_same_set(F, prec, n):
+    c = inputs.plummer(n, 14 + n, imf="kroupa")
+    ra, rg = oracle.accel_grad(c.pos, c.mass)
+    with F.Context(prec) as ctx:
+        a, g = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
+        a, g = host(a), host(g)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(a, ra, prec, scale=abs_scale(c.pos, c.mass))
+    assert_grad_close(g, rg, prec, grad_scale(c.pos, c.mass, np.asarray(
+        oracle.acc(c.pos, c.mass)), np.arange(n), np.arange(n)))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_accel_grad_disjoint_inter_level(F, prec):
+    n = 1800
+    c = inputs.plummer(n, 15, imf="kroupa")
+    perm = np.random.default_rng(5).permutation(n).astype(np.int32)
+    S, Fs = np.sort(perm[:1500]), np.sort(perm[1500:])
+    ra, rg = oracle.accel_grad(c.pos, c.mass, S, Fs)
+    with F.Context(prec) as ctx:
+        a, g = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass), ids(S), ids(Fs))
+        a, g = host(a), host(g)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(a, ra, prec, scale=abs_scale(c.pos, c.mass, S, Fs))
+    accg = np.zeros((3, n))
+    accg[:, S] = ra
+    accg[:, Fs] = oracle.acc(c.pos, c.mass, Fs, S)
+    assert_grad_close(g, rg, prec, grad_scale(c.pos, c.mass, accg, S, Fs))
+
+
+def test_accel_grad_partial_overlap_is_reported(F):
+    c = inputs.plummer(500, 16)
+    with F.Context("fp64") as ctx:
+        F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass), ids(np.arange(0, 300)),
+                         ids(np.arange(200, 500)))
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_ARG
+
+
+# ----------------------------------------------------------------------------- step
+STEP_TOL = {"fp64": 1e-12, "mixed": 1e-9}
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fsi_step_plummer1k_ten_steps(F, prec):
+    """N = 1024 equal-mass Plummer, eps = 0, 10 FSI steps of h = 1e-3."""
+    c = inputs.workload("plummer1k")
+    rp, rv = oracle.fsi_step(c.pos, c.vel, c.mass, 1e-3, steps=10)
+    with F.Context(prec) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        F.fsi_step(ctx, p, v, dev(c.mass), 1e-3, nsteps=10)
+        p, v = host(p), host(v)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    sx = np.abs(c.pos).max()
+    sv = np.abs(c.vel).max()
+    assert np.abs(p - rp).max() <= STEP_TOL[prec] * sx
+    assert np.abs(v - rv).max() <= STEP_TOL[prec] * 10 * sv
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fsi_step_calls_chain_like_one_call(F, prec):
+    c = inputs.plummer(600, 17)
+    with F.Context(prec) as ctx:
+        p1, v1 = dev(c.pos), dev(c.vel)
+        F.fsi_step(ctx, p1, v1, dev(c.mass), 2e-3, nsteps=4)
+        p2, v2 = dev(c.pos), dev(c.vel)
+        for _ in range(4):
+            F.fsi_step(ctx, p2, v2, dev(c.mass), 2e-3, nsteps=1)
+        d = np.abs(host(p1) - host(p2)).max()
+    assert d <= (1e-14 if prec == "fp64" else 1e-11)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fsi_step_subset(F, prec):
+    c = inputs.plummer(900, 18, imf="kroupa")
+    P = inputs.random_subset(900, 321, 6)
+    rp, rv = oracle.fsi_step(c.pos, c.vel, c.mass, 1e-3, P=P, steps=3)
+    with F.Context(prec) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        F.fsi_step(ctx, p, v, dev(c.mass), 1e-3, nsteps=3, idx=ids(P))
+        p, v = host(p), host(v)
+    assert np.abs(p - rp).max() <= STEP_TOL[prec]
+    assert np.abs(v - rv).max() <= STEP_TOL[prec] * 100
+    others = np.setdiff1d(np.arange(900), P)
+    assert np.array_equal(p[:, others], c.pos[:, others])
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_fsi_step_with_pn(F, prec):
+    c = inputs.plummer(400, 19, imf="kroupa", n_bh=4)
+    cl = 30.0
+    rp, rv = oracle.fsi_step(c.pos, c.vel, c.mass, 1e-3, c=cl, is_bh=c.is_bh, steps=3)
+    np0, nv0 = oracle.fsi_step(c.pos, c.vel, c.mass, 1e-3, steps=3)
+    assert np.abs(rv - nv0).max() > 1e-9      # the PN term matters at this c
+    with F.Context(prec, c=cl) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        F.fsi_step(ctx, p, v, dev(c.mass), 1e-3, nsteps=3, is_bh=dev(c.is_bh, torch.uint8))
+        p, v = host(p), host(v)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert np.abs(p - rp).max() <= STEP_TOL[prec]
+    assert np.abs(v - rv).max() <= STEP_TOL[prec] * 100
+
+
+def test_pn_accel_pairs(F):
+    c = inputs.plummer(500, 20, imf="kroupa", n_bh=5)
+    ref = oracle.pn_acc(c.pos, c.vel, c.mass, c.is_bh, 25.0)
+    with F.Context("fp64") as ctx:
+        got = host(F.fsi_pn_accel(ctx, dev(c.pos), dev(c.vel), dev(c.mass),
+                                  dev(c.is_bh, torch.uint8), 25.0))
+    assert_close(got, ref, "fp64")
+
+
+# ----------------------------------------------------------------------------- misc
+def test_timesteps_and_energy(F):
+    c = inputs.plummer(1500, 21, imf="kroupa")
+    ref = oracle.timesteps(c.pos, c.vel, c.mass)
+    T, W = oracle.energy(c.pos, c.vel, c.mass)
+    with F.Context("fp64") as ctx:
+        s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+        e = host(F.fsi_energy(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+        P = inputs.random_subset(1500, 400, 7)
+        sp = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P)))
+    assert np.abs(s / ref - 1).max() < 1e-12
+    assert np.abs(sp / oracle.timesteps(c.pos, c.vel, c.mass, P) - 1).max() < 1e-12
+    assert abs(e[0] / T - 1) < 1e-13 and abs(e[1] / W - 1) < 1e-12
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_hhs_interval(F, prec):
+    c = inputs.plummer(160, 22, imf="kroupa")
+    tau = 1.0 / 16
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    with F.Context(prec) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
+
+
+# ----------------------------------------------------------------------------- full size
+@pytest.fixture(scope="module")
+def big():
+    return inputs.workload("kroupa1m_bh16")
+
+
+def test_full_size_mixed_acc_sampled_rows(F, big):
+    """N = 2^20 + 16 (Kroupa + 16 black holes): the all-pairs mixed pass of the benchmark's
+    launch configuration, checked on 256 sampled rows against the oracle."""
+    rows = inputs.random_subset(big.n, 256, 31)
+    ref = oracle.acc(big.pos, big.mass, rows, None)
+    with F.Context("mixed") as ctx:
+        got = host(F.fsi_accel(ctx, dev(big.pos), dev(big.mass)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(got[:, rows], ref, "mixed", scale=abs_scale(big.pos, big.mass, rows))
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_full_size_sampled_rows_general_path(F, big, prec):
+    rows = inputs.random_subset(big.n, 128, 32)
+    ref = oracle.acc(big.pos, big.mass, rows, None)
+    accg = inputs.random_field(big.n, 33)
+    refg = oracle.grad(big.pos, big.mass, accg, rows, None)
+    with F.Context(prec) as ctx:
+        got = host(F.fsi_accel(ctx, dev(big.pos), dev(big.mass), ids(rows), None))
+        gg = host(F.fsi_grad(ctx, dev(big.pos), dev(big.mass), dev(accg), ids(rows), None))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(got, ref, prec, scale=abs_scale(big.pos, big.mass, rows))
+    if prec == "fp64":
+        assert_close(gg, refg, prec)
+    else:
+        e = np.abs(gg - refg).max(axis=0) / np.linalg.norm(refg, axis=0)
+        assert np.median(e) < 1e-4, np.median(e)
