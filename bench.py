@@ -206,6 +206,7 @@ def run_fsi(args):
     cl = 1e4
     ctx = F.Context(args.precision, c=cl)
     F.fsi_reserve(ctx, N, N)
+    tuning = F.fsi_autotune(ctx, pos, mass, n=min(N, 1 << 18))   # variant per kernel kind
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
@@ -301,6 +302,7 @@ def run_fsi(args):
         "config": {"workload": args.workload, "n": N, "precision": args.precision,
                    "step": "one FSI cycle of all N + PN1.0 half-kicks (3 acc + 1 grad pair passes)",
                    "c": cl, "h": h, "l2": "flushed between steps (256 MB write)",
+                   "tuning": {"acc_variant": tuning[0], "grad_variant": tuning[1]},
                    "parallelism": f"replicas x{ws}"},
         "wall_s": wall, "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,

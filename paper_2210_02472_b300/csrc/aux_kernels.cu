@@ -27,11 +27,7 @@ __global__ void pack_kernel(int N, const double* __restrict__ pos, const double*
     const double x = pos[i], y = pos[(size_t)N + i], z = pos[2 * (size_t)N + i];
     const double m = mass[i];
     if constexpr (P == FSI_MIXED) {
-        const float xh = (float)x, yh = (float)y, zh = (float)z;
-        RecMix r;
-        r.hi = make_float4(xh, yh, zh, (float)m);
-        r.lo = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh), 0.f);
-        reinterpret_cast<RecMix*>(rec)[k] = r;
+        reinterpret_cast<RecMix*>(rec)[k] = make_mix_rec(x, y, z, m);
     } else {
         reinterpret_cast<D4*>(rec)[k] = make_d4(x, y, z, m);
     }
@@ -203,11 +199,11 @@ cudaError_t launch_check_disjoint(int N, const int* A, int nA, const int* B, int
 
 // ---------------------------------------------------------------------------------
 // Kick + drift on a compact set, rewriting its position records:
-//   v += c_kick a;  x += c_drift v;  rec_out <- (x, m from rec_in).
+//   v += c_kick a;  x += c_drift v;  rec_out <- (x, m from the FP64 masses mc).
 template <int P>
 __global__ void kick_drift_kernel(int n, double* __restrict__ xc, double* __restrict__ vc,
                                   const double* __restrict__ ac, double c_kick, double c_drift,
-                                  const void* __restrict__ rec_in, void* __restrict__ rec_out) {
+                                  const double* __restrict__ mc, void* __restrict__ rec_out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     double v[3], x[3];
@@ -223,29 +219,21 @@ __global__ void kick_drift_kernel(int n, double* __restrict__ xc, double* __rest
         }
     }
     if (rec_out) {
-        if constexpr (P == FSI_MIXED) {
-            const float m = reinterpret_cast<const RecMix*>(rec_in)[k].hi.w;
-            RecMix r;
-            const float xh = (float)x[0], yh = (float)x[1], zh = (float)x[2];
-            r.hi = make_float4(xh, yh, zh, m);
-            r.lo = make_float4((float)(x[0] - (double)xh), (float)(x[1] - (double)yh),
-                               (float)(x[2] - (double)zh), 0.f);
-            reinterpret_cast<RecMix*>(rec_out)[k] = r;
-        } else {
-            const double m = reinterpret_cast<const D4*>(rec_in)[k].w;
-            reinterpret_cast<D4*>(rec_out)[k] = make_d4(x[0], x[1], x[2], m);
-        }
+        if constexpr (P == FSI_MIXED)
+            reinterpret_cast<RecMix*>(rec_out)[k] = make_mix_rec(x[0], x[1], x[2], mc[k]);
+        else
+            reinterpret_cast<D4*>(rec_out)[k] = make_d4(x[0], x[1], x[2], mc[k]);
     }
 }
 
 cudaError_t launch_kick_drift(int precision, int n, double* xc, double* vc, const double* ac,
-                              double c_kick, double c_drift, const void* rec_in, void* rec_out,
+                              double c_kick, double c_drift, const double* mc, void* rec_out,
                               cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (precision == FSI_MIXED)
-        { kick_drift_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, rec_in, rec_out); note_launch(); }
+        { kick_drift_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, mc, rec_out); note_launch(); }
     else
-        { kick_drift_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, rec_in, rec_out); note_launch(); }
+        { kick_drift_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, mc, rec_out); note_launch(); }
     return cudaGetLastError();
 }
 

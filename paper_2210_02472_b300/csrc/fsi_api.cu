@@ -68,6 +68,7 @@ struct fsi_ctx {
     std::vector<long long> level_counts;
     int max_level_used = 0;
     int max_level_hit = 0;
+    int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] pair-kernel variant (see pair_variants)
     // instrumentation: event pairs around pair-kernel launches
     struct ProfRec { int kind; cudaEvent_t a, b; };
     bool profiling = false;
@@ -153,7 +154,8 @@ int timed(fsi_ctx* c, int kind, cudaStream_t s, F&& f) {
 int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
     if (a.n_i <= 0) return FSI_OK;
     const int prec = c->p.precision;
-    const int ipc = pair_i_per_cta_for(prec, kind);
+    const int ipt = c->ipt[prec][kind];
+    const int ipc = kThreads * variant_ipt(ipt);
     int split = choose_split(c, a.n_i, a.n_j, ipc);
     int jps = (a.n_j + split - 1) / split;
     jps = std::max(kTileJ, (jps + kTileJ - 1) / kTileJ * kTileJ);
@@ -165,7 +167,7 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
         CK(ensure(c->part, (size_t)split * 3 * a.n_i * sizeof(double)));
         a.part = P<double>(c->part);
     }
-    CK(timed(c, kind, s, [&] { return launch_pair(prec, kind, a, split, s); }));
+    CK(timed(c, kind, s, [&] { return launch_pair(prec, kind, ipt, a, split, s); }));
     if (split > 1) CK(timed(c, 2, s, [&] { return launch_finalize_p(prec, a, split, s); }));
     return FSI_OK;
 }
@@ -198,9 +200,12 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     if (idx) {
         CK(ensure(c->xc, 3 * (size_t)n * 8));
         CK(ensure(c->vc, 3 * (size_t)n * 8));
+        CK(ensure(c->mc, (size_t)n * 8));
         xc = P<double>(c->xc);
         vc = P<double>(c->vc);
         CU(launch_gather3(N, vel, idx, n, vc, s));
+        CU(launch_gather1(N, mass, idx, n, P<double>(c->mc), s));
+        mc = P<double>(c->mc);
     }
     CU(launch_pack(prec, N, pos, mass, idx, n, c->rec[0].p, idx ? xc : nullptr, s));
     if (pn) {
@@ -210,11 +215,8 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
         CK(ensure(c->nbh, 16));
         CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
         if (idx) {
-            CK(ensure(c->mc, (size_t)n * 8));
             CK(ensure(c->bhc, (size_t)n));
-            CU(launch_gather1(N, mass, idx, n, P<double>(c->mc), s));
             CU(launch_gather_u8(is_bh, idx, n, P<unsigned char>(c->bhc), s));
-            mc = P<double>(c->mc);
             bhc = P<unsigned char>(c->bhc);
         }
         CU(launch_bh_list(n, bhc, P<int>(c->bhlist), P<int>(c->nbh), c->err_d, s));
@@ -239,6 +241,7 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
             a.epi.c_kick = ck;
             a.epi.c_drift = cd;
             a.epi.rec_out = rout;
+            a.epi.mc = mc;
         }
         return run_pair(c, KIND_ACC, a, s);
     };
@@ -256,6 +259,7 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
         a.epi.c_grad = cg;
         a.epi.c_drift = cd;
         a.epi.rec_out = rout;
+        a.epi.mc = mc;
         return run_pair(c, KIND_GRAD, a, s);
     };
     void* r0 = c->rec[0].p;
@@ -273,7 +277,7 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
             if (pn) CK(pn_kick(0.5 * h));
             if (!last) {
                 CK(pn_kick(0.5 * h));
-                CU(launch_kick_drift(prec, n, xc, vc, P<double>(c->ad), h / 6.0, 0.5 * h, r0, r1, s));
+                CU(launch_kick_drift(prec, n, xc, vc, P<double>(c->ad), h / 6.0, 0.5 * h, mc, r1, s));
             }
         }
     }
@@ -761,6 +765,81 @@ int fsi_profile_read(fsi_ctx* c, long long* launches, double* ms) {
 }
 
 long long fsi_launch_count(void) { return g_launches.load(); }
+
+int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n, int reps,
+                 void* stream) {
+    CK(check_common(c, N));
+    if (n <= 0 || n > N || !pos || !mass) return fail(FSI_ERR_ARG, "bad autotune arguments");
+    if (reps <= 0) reps = 2;
+    const cudaStream_t s = S(stream);
+    const int prec = c->p.precision;
+    CK(ensure(c->rec[0], pad_tile(n) * 32));
+    CK(ensure(c->accrec[0], pad_tile(n) * 32));
+    CK(ensure(c->tA, 3 * (size_t)n * 8));
+    CU(launch_pack(prec, N, pos, mass, nullptr, n, c->rec[0].p, nullptr, s));
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    const bool was = c->profiling;
+    c->profiling = false;
+    int rc = FSI_OK;
+    for (int kind = 0; kind < 2 && rc == FSI_OK; ++kind) {
+        int cand[8];
+        const int nc = pair_variants(prec, kind, cand);
+        float best = 3.4e38f;
+        int best_ipt = c->ipt[prec][kind];
+        for (int v = 0; v < nc && rc == FSI_OK; ++v) {
+            c->ipt[prec][kind] = cand[v];
+            PairArgs a{};
+            a.irec = a.jrec = c->rec[0].p;
+            a.iacc = a.jacc = c->accrec[0].p;
+            a.n_i = a.n_j = n;
+            a.check = CHECK_DIAG;
+            a.eps2 = c->p.eps2;
+            a.epi.out = P<double>(c->tA);
+            if (kind == KIND_ACC) a.epi.accrec = c->accrec[0].p;
+            rc = run_pair(c, kind, a, s);                      // warm-up (and accel records)
+            if (rc != FSI_OK) break;
+            if (cudaEventRecord(e0, s) != cudaSuccess) { rc = fail(FSI_ERR_CUDA, "event"); break; }
+            for (int r = 0; r < reps && rc == FSI_OK; ++r) rc = run_pair(c, kind, a, s);
+            if (cudaEventRecord(e1, s) != cudaSuccess || cudaEventSynchronize(e1) != cudaSuccess) {
+                rc = fail(FSI_ERR_CUDA, "event");
+                break;
+            }
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; best_ipt = cand[v]; }
+        }
+        c->ipt[prec][kind] = best_ipt;
+    }
+    c->profiling = was;
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    return rc;
+}
+
+int fsi_get_tuning(fsi_ctx* c, int* ipt_acc, int* ipt_grad) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    if (ipt_acc) *ipt_acc = c->ipt[c->p.precision][KIND_ACC];
+    if (ipt_grad) *ipt_grad = c->ipt[c->p.precision][KIND_GRAD];
+    return FSI_OK;
+}
+
+int fsi_set_tuning(fsi_ctx* c, int ipt_acc, int ipt_grad) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    int cand[8];
+    const int prec = c->p.precision;
+    for (int kind = 0; kind < 2; ++kind) {
+        const int want = kind == KIND_ACC ? ipt_acc : ipt_grad;
+        const int nc = pair_variants(prec, kind, cand);
+        bool ok = false;
+        for (int v = 0; v < nc; ++v) ok |= cand[v] == want;
+        if (!ok) return fail(FSI_ERR_ARG, "unsupported particles-per-thread %d", want);
+    }
+    c->ipt[prec][KIND_ACC] = ipt_acc;
+    c->ipt[prec][KIND_GRAD] = ipt_grad;
+    return FSI_OK;
+}
 
 int fsi_fma_probe(int fp64, int blocks, int iters, void* sink, double* flops, void* stream) {
     if (blocks <= 0 || iters <= 0 || !sink) return fail(FSI_ERR_ARG, "bad probe arguments");

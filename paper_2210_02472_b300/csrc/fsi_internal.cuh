@@ -12,10 +12,12 @@ namespace fsi {
 //
 //  FP64 position record (32 B):  double4 (x, y, z, m)
 //  FP64 accel record    (32 B):  double4 (ax, ay, az, 0)
-//  MIXED position record (32 B): float4 (xh, yh, zh, m), float4 (xl, yl, zl, 0)
+//  MIXED position record (32 B): float4 (xh, yh, zh, 2.5 m), float4 (xl, yl, zl, -1.5 m)
 //        with xh = fl32(x) and xl = fl32(x - xh): xh + xl carries ~48 bits of x, so a
 //        pair difference (xh_j - xh_i) + (xl_j - xl_i) is accurate to FP32 precision
-//        relative to the separation even when |x| >> |r_ij|.
+//        relative to the separation even when |x| >> |r_ij|.  The two mass multiples
+//        fold the residual correction of the hardware rsqrt into one FMA:
+//        m r^-3 = y^3 (2.5 m - 1.5 m r^2 y^2) to first order in e = 1 - r^2 y^2.
 //  MIXED accel record   (16 B):  float4 (ax, ay, az, 0)
 // ---------------------------------------------------------------------------------
 struct alignas(32) D4 { double x, y, z, w; };   // 32-byte aligned FP64 quadruple
@@ -25,6 +27,15 @@ __host__ __device__ __forceinline__ D4 make_d4(double x, double y, double z, dou
 struct RecF64 { double x, y, z, m; };
 struct RecMix { float4 hi; float4 lo; };
 static_assert(sizeof(RecF64) == 32 && sizeof(RecMix) == 32, "record size");
+
+__device__ __forceinline__ RecMix make_mix_rec(double x, double y, double z, double m) {
+    const float xh = (float)x, yh = (float)y, zh = (float)z;
+    RecMix r;
+    r.hi = make_float4(xh, yh, zh, (float)(2.5 * m));
+    r.lo = make_float4((float)(x - (double)xh), (float)(y - (double)yh), (float)(z - (double)zh),
+                       (float)(-1.5 * m));
+    return r;
+}
 
 constexpr int kThreads = 256;      // threads per pair-kernel CTA
 constexpr int kTileJ = 256;        // sources per shared-memory tile
@@ -46,6 +57,7 @@ struct Epi {
     const double* base; // compact 3 x n_i (grad pass: a_i), may be null
     double c_kick, c_grad, c_drift;
     void* rec_out;      // position records for the next pass
+    const double* mc;   // compact FP64 masses (needed when rec_out is written)
     void* accrec;       // accel records (FP64: RecF64-like double4; MIXED: float4)
 };
 
@@ -143,9 +155,15 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
 namespace fsi {
 void note_launch();                 // counts every kernel launch (fsi_launch_count)
 cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* sink, cudaStream_t s);
-cudaError_t launch_pair(int precision, int kind, const PairArgs& a, int split, cudaStream_t s);
+// variant: active particles per thread (ipt, low 4 bits) + 16 if the mixed kernel
+// accumulates its tile partials as float-float pairs (see pair_variants).
+cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int split,
+                        cudaStream_t s);
 cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s);
-int pair_i_per_cta_for(int precision, int kind);   // active particles per CTA
+// Supported ipt values for (precision, kind): writes up to 8 into out, returns the count.
+int pair_variants(int precision, int kind, int* out);
+int pair_default_ipt(int precision, int kind);
+int variant_ipt(int variant);
 
 cudaError_t launch_pack(int precision, int N, const double* pos, const double* mass,
                         const int* idx, int n, void* rec, double* xc, cudaStream_t s);
@@ -165,7 +183,7 @@ cudaError_t launch_ids(const int* idx, int n, int cap, int* ids, cudaStream_t s)
 cudaError_t launch_check_disjoint(int N, const int* A, int nA, const int* B, int nB,
                                   unsigned char* mark, int* err, cudaStream_t s);
 cudaError_t launch_kick_drift(int precision, int n, double* xc, double* vc, const double* ac,
-                              double c_kick, double c_drift, const void* rec_in, void* rec_out,
+                              double c_kick, double c_drift, const double* mc, void* rec_out,
                               cudaStream_t s);
 cudaError_t launch_axpy3(int n, double* v, const double* a, double w, cudaStream_t s);
 cudaError_t launch_axpby3(int n, const double* a, const double* g, double c, double* out,

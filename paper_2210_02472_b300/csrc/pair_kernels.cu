@@ -51,10 +51,9 @@ __device__ __forceinline__ void mix_acc_pair(const float4 h, const float4 l, con
     if (CHK) r2 = self ? 1.0f : r2;
     const float y = rsqrt_hw(r2);
     const float y2 = y * y;
-    // E = 1.5 e with e = 1 - r^2 y^2; r^-3 = y^3 (1 - e)^{-3/2} ~ y^3 (1 + E)
-    const float E = fmaf(-1.5f * r2, y2, 1.5f);
-    const float w0 = h.w * (y2 * y);
-    const float w = fmaf(w0, E, w0);
+    const float sres = r2 * y2;                      // 1 - e, e = rsqrt residual
+    // m r^-3 = m y^3 (1 - e)^{-3/2} ~ y^3 (2.5 m - 1.5 m (1 - e)); h.w = 2.5 m, l.w = -1.5 m
+    const float w = (y2 * y) * fmaf(sres, l.w, h.w);
     fx = fmaf(w, dx, fx);
     fy = fmaf(w, dy, fy);
     fz = fmaf(w, dz, fz);
@@ -71,13 +70,12 @@ __device__ __forceinline__ void mix_grad_pair(const float4 h, const float4 l, co
     if (CHK) r2 = self ? 1.0f : r2;
     const float y = rsqrt_hw(r2);
     const float y2 = y * y;
-    const float E = fmaf(-1.5f * r2, y2, 1.5f);
-    const float w0 = h.w * (y2 * y);
-    const float w = fmaf(w0, E, w0);                 // m r^-3
+    const float sres = r2 * y2;                      // 1 - e
+    const float w = (y2 * y) * fmaf(sres, l.w, h.w); // m r^-3
     const float bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;   // a_ji
     const float dot = fmaf(bx, dx, fmaf(by, dy, bz * dz));
-    // q = -3 m r^-5 = -3 w y^2 (1 + e) = w y^2 (-3 - 2E)
-    const float q = (w * y2) * fmaf(-2.0f, E, -3.0f);
+    // -3 m r^-5 = -3 w y^2 (1 + e) = w y^2 (3 (1 - e) - 6)
+    const float q = (w * y2) * fmaf(3.0f, sres, -6.0f);
     const float s = q * dot;
     gx = fmaf(w, bx, fmaf(s, dx, gx));
     gy = fmaf(w, by, fmaf(s, dy, gy));
@@ -133,7 +131,7 @@ __device__ __forceinline__ void f64_grad_pair(const D4 j, const D4 aj, const F64
 // Epilogue shared by the pair kernel (split == 1) and the finalize kernel.
 template <int P>
 __device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, double ry,
-                                         double rz, double m, int* err) {
+                                         double rz, int* err) {
     if (!(isfinite(rx) && isfinite(ry) && isfinite(rz))) set_error(err, FSI_ERR_NONFINITE);
     if (e.out) {
         e.out[i] = rx;
@@ -167,16 +165,10 @@ __device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, 
             e.x[(size_t)n + i] = y;
             e.x[2 * (size_t)n + i] = z;
             if (e.rec_out) {
-                if (P == FSI_MIXED) {
-                    const float xh = (float)x, yh = (float)y, zh = (float)z;
-                    RecMix r;
-                    r.hi = make_float4(xh, yh, zh, (float)m);
-                    r.lo = make_float4((float)(x - (double)xh), (float)(y - (double)yh),
-                                       (float)(z - (double)zh), 0.f);
-                    reinterpret_cast<RecMix*>(e.rec_out)[i] = r;
-                } else {
-                    reinterpret_cast<D4*>(e.rec_out)[i] = make_d4(x, y, z, m);
-                }
+                if constexpr (P == FSI_MIXED)
+                    reinterpret_cast<RecMix*>(e.rec_out)[i] = make_mix_rec(x, y, z, e.mc[i]);
+                else
+                    reinterpret_cast<D4*>(e.rec_out)[i] = make_d4(x, y, z, e.mc[i]);
             }
         }
     }
@@ -184,19 +176,19 @@ __device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, 
 
 // ---------------------------------------------------------------------------------
 template <int P, int KIND>
-struct Cfg;
-template <> struct Cfg<FSI_MIXED, KIND_ACC>  { static constexpr int I = 4; static constexpr int ACCREC = 0; };
-template <> struct Cfg<FSI_MIXED, KIND_GRAD> { static constexpr int I = 4; static constexpr int ACCREC = 16; };
-template <> struct Cfg<FSI_FP64, KIND_ACC>   { static constexpr int I = 2; static constexpr int ACCREC = 0; };
-template <> struct Cfg<FSI_FP64, KIND_GRAD>  { static constexpr int I = 2; static constexpr int ACCREC = 32; };
+struct Cfg {
+    static constexpr int ACCREC = KIND == KIND_ACC ? 0 : (P == FSI_MIXED ? 16 : 32);
+};
 
 constexpr int kRec = 32;
 
 __host__ __device__ constexpr int stage_bytes(int accrec) { return kTileJ * (kRec + accrec + 4); }
 
-template <int P, int KIND>
-__global__ void __launch_bounds__(kThreads, 2) pair_kernel(const PairArgs a) {
-    constexpr int I = Cfg<P, KIND>::I;
+// P: precision; KIND: acc or grad; I: active particles per thread; FF (mixed only): the
+// per-tile FP32 partial sums are accumulated as float-float pairs by TwoSum (FP32 pipe)
+// instead of FP64 additions (FP64 pipe, 1/64 of the FP32 rate on B300).
+template <int P, int KIND, int I, int FF>
+__global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const PairArgs a) {
     constexpr int ACCREC = Cfg<P, KIND>::ACCREC;
     constexpr int SB = stage_bytes(ACCREC);
     extern __shared__ __align__(128) unsigned char smem[];
@@ -234,7 +226,6 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(const PairArgs a) {
 
     // ---- i-side registers
     int my_id[I];
-    double mi[I];
     double acc64[I][3];
 #pragma unroll
     for (int u = 0; u < I; ++u) {
@@ -248,13 +239,13 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(const PairArgs a) {
     if constexpr (P == FSI_MIXED) {
         MixI pi[I];
         float f[I][3];
+        float hi[I][3], lo[I][3];   // float-float running sums (FF variant)
 #pragma unroll
         for (int u = 0; u < I; ++u) {
             const int i = min(i0 + u * kThreads + tid, max(a.n_i - 1, 0));
             const RecMix r = reinterpret_cast<const RecMix*>(a.irec)[i];
             pi[u].xh = r.hi.x; pi[u].yh = r.hi.y; pi[u].zh = r.hi.z;
             pi[u].xl = r.lo.x; pi[u].yl = r.lo.y; pi[u].zl = r.lo.z;
-            mi[u] = r.hi.w;
             if constexpr (KIND == KIND_GRAD) {
                 const float4 ai = reinterpret_cast<const float4*>(a.iacc)[i];
                 pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
@@ -262,6 +253,8 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(const PairArgs a) {
                 pi[u].ax = pi[u].ay = pi[u].az = 0.f;
             }
             f[u][0] = f[u][1] = f[u][2] = 0.f;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) hi[u][q] = lo[u][q] = 0.f;
         }
         const float eps2f = (float)a.eps2;
         for (int t = 0; t < ntiles; ++t) {
@@ -309,13 +302,29 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(const PairArgs a) {
             }
 #pragma unroll
             for (int u = 0; u < I; ++u) {
-                acc64[u][0] += (double)f[u][0];
-                acc64[u][1] += (double)f[u][1];
-                acc64[u][2] += (double)f[u][2];
-                f[u][0] = f[u][1] = f[u][2] = 0.f;
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    if constexpr (FF) {
+                        // error-free transformation (Knuth's TwoSum): hi + f = s + e exactly
+                        const float sum = hi[u][q] + f[u][q];
+                        const float bb = sum - hi[u][q];
+                        const float e = (hi[u][q] - (sum - bb)) + (f[u][q] - bb);
+                        hi[u][q] = sum;
+                        lo[u][q] += e;
+                    } else {
+                        acc64[u][q] += (double)f[u][q];
+                    }
+                    f[u][q] = 0.f;
+                }
             }
             if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
             if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+        }
+        if constexpr (FF) {
+#pragma unroll
+            for (int u = 0; u < I; ++u)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) acc64[u][q] = (double)hi[u][q] + (double)lo[u][q];
         }
     } else {
         F64I pi[I];
@@ -324,7 +333,6 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(const PairArgs a) {
             const int i = min(i0 + u * kThreads + tid, max(a.n_i - 1, 0));
             const D4 r = reinterpret_cast<const D4*>(a.irec)[i];
             pi[u].x = r.x; pi[u].y = r.y; pi[u].z = r.z;
-            mi[u] = r.w;
             if constexpr (KIND == KIND_GRAD) {
                 const D4 ai = reinterpret_cast<const D4*>(a.iacc)[i];
                 pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
@@ -401,7 +409,7 @@ __global__ void __launch_bounds__(kThreads, 2) pair_kernel(const PairArgs a) {
             p[(size_t)a.n_i + i] = acc64[u][1];
             p[2 * (size_t)a.n_i + i] = acc64[u][2];
         } else {
-            epilogue<P>(a.epi, i, a.n_i, acc64[u][0], acc64[u][1], acc64[u][2], mi[u], a.err);
+            epilogue<P>(a.epi, i, a.n_i, acc64[u][0], acc64[u][1], acc64[u][2], a.err);
         }
     }
 }
@@ -418,41 +426,67 @@ __global__ void finalize_kernel(const PairArgs a, int split) {
         r[1] += p[(size_t)a.n_i + i];
         r[2] += p[2 * (size_t)a.n_i + i];
     }
-    double m;
-    if (P == FSI_MIXED) m = reinterpret_cast<const RecMix*>(a.irec)[i].hi.w;
-    else m = reinterpret_cast<const D4*>(a.irec)[i].w;
-    epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], m, a.err);
+    epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], a.err);
 }
 
 // ---------------------------------------------------------------------------------
-template <int P, int KIND>
+template <int P, int KIND, int I, int FF>
 static cudaError_t launch_one(const PairArgs& a, int split, cudaStream_t s) {
-    constexpr int I = Cfg<P, KIND>::I;
     constexpr int SMEM = kStages * stage_bytes(Cfg<P, KIND>::ACCREC);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pair_kernel<P, KIND>,
+        cudaError_t e = cudaFuncSetAttribute(pair_kernel<P, KIND, I, FF>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
     dim3 grid((a.n_i + kThreads * I - 1) / (kThreads * I), split);
-    { pair_kernel<P, KIND><<<grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    { pair_kernel<P, KIND, I, FF><<<grid, kThreads, SMEM, s>>>(a); note_launch(); }
     return cudaGetLastError();
 }
 
-int pair_i_per_cta_for(int precision, int kind) {
-    if (precision == FSI_MIXED) return kThreads * (kind == KIND_ACC ? Cfg<FSI_MIXED, KIND_ACC>::I : Cfg<FSI_MIXED, KIND_GRAD>::I);
-    return kThreads * (kind == KIND_ACC ? Cfg<FSI_FP64, KIND_ACC>::I : Cfg<FSI_FP64, KIND_GRAD>::I);
+// A variant is encoded as ipt + 16 * ff.
+template <int P, int KIND>
+static cudaError_t launch_variant(int v, const PairArgs& a, int split, cudaStream_t s) {
+    switch (v) {
+        case 1: return launch_one<P, KIND, 1, 0>(a, split, s);
+        case 2: return launch_one<P, KIND, 2, 0>(a, split, s);
+        case 3: return launch_one<P, KIND, 3, 0>(a, split, s);
+        case 4: return launch_one<P, KIND, 4, 0>(a, split, s);
+        case 16 + 2: return launch_one<P, KIND, 2, 1>(a, split, s);
+        case 16 + 3: return launch_one<P, KIND, 3, 1>(a, split, s);
+        case 16 + 4: return launch_one<P, KIND, 4, 1>(a, split, s);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
-cudaError_t launch_pair(int precision, int kind, const PairArgs& a, int split, cudaStream_t s) {
+int pair_variants(int precision, int kind, int* out) {
+    (void)kind;
+    int n = 0;
+    if (precision == FSI_MIXED) {
+        for (int ipt = 2; ipt <= 4; ++ipt) out[n++] = ipt;
+        for (int ipt = 2; ipt <= 4; ++ipt) out[n++] = 16 + ipt;
+    } else {
+        out[n++] = 1; out[n++] = 2; out[n++] = 3;
+    }
+    return n;
+}
+
+int pair_default_ipt(int precision, int kind) {
+    return precision == FSI_MIXED ? (kind == KIND_ACC ? 4 : 2) : 2;
+}
+
+int variant_ipt(int v) { return v & 15; }
+
+cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int split,
+                        cudaStream_t s) {
     if (a.n_i <= 0) return cudaSuccess;
     if (precision == FSI_MIXED)
-        return kind == KIND_ACC ? launch_one<FSI_MIXED, KIND_ACC>(a, split, s)
-                                : launch_one<FSI_MIXED, KIND_GRAD>(a, split, s);
-    return kind == KIND_ACC ? launch_one<FSI_FP64, KIND_ACC>(a, split, s)
-                            : launch_one<FSI_FP64, KIND_GRAD>(a, split, s);
+        return kind == KIND_ACC ? launch_variant<FSI_MIXED, KIND_ACC>(ipt, a, split, s)
+                                : launch_variant<FSI_MIXED, KIND_GRAD>(ipt, a, split, s);
+    if (ipt >= 16) return cudaErrorInvalidValue;
+    return kind == KIND_ACC ? launch_variant<FSI_FP64, KIND_ACC>(ipt, a, split, s)
+                            : launch_variant<FSI_FP64, KIND_GRAD>(ipt, a, split, s);
 }
 
 cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s) {

@@ -38,7 +38,7 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_last_error", "fsi_sync_status", "fsi_accel", "fsi_grad", "fsi_accel_grad",
             "fsi_pn_accel", "fsi_step", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
             "fsi_level_stats", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
-            "fsi_fma_probe"]
+            "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning"]
 
 
 class fsi_params(C.Structure):
@@ -69,6 +69,9 @@ _lib.fsi_profile.argtypes = [_vp, _ip]
 _lib.fsi_profile_read.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
 _lib.fsi_launch_count.restype = C.c_longlong
 _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
+_lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
+_lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
+_lib.fsi_set_tuning.argtypes = [_vp, _ip, _ip]
 
 
 class FsiError(RuntimeError):
@@ -289,3 +292,22 @@ def fsi_fma_probe(fp64: bool, blocks: int, iters: int, sink: torch.Tensor, strea
     _check(_lib.fsi_fma_probe(int(bool(fp64)), int(blocks), int(iters), sink.data_ptr(),
                               C.byref(f), _stream(stream)), "fsi_fma_probe")
     return f.value
+
+
+def fsi_autotune(ctx: Context, pos, mass, n: int = 0, reps: int = 2, stream=None):
+    """Pick the fastest pair-kernel variants on the first n particles; returns them."""
+    N = mass.numel()
+    n = N if n <= 0 else min(n, N)
+    _check(_lib.fsi_autotune(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
+                             int(n), int(reps), _stream(stream)), "fsi_autotune")
+    return fsi_get_tuning(ctx)
+
+
+def fsi_get_tuning(ctx: Context):
+    a, g = _ip(), _ip()
+    _check(_lib.fsi_get_tuning(ctx.handle, C.byref(a), C.byref(g)), "fsi_get_tuning")
+    return int(a.value), int(g.value)
+
+
+def fsi_set_tuning(ctx: Context, ipt_acc: int, ipt_grad: int) -> None:
+    _check(_lib.fsi_set_tuning(ctx.handle, int(ipt_acc), int(ipt_grad)), "fsi_set_tuning")
