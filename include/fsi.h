@@ -75,9 +75,13 @@ typedef struct fsi_params {
     double c;             /* speed of light in N-body units; 0 switches PN1.0 off */
     int split;            /* source-split factor override (0 = automatic) */
     long long timeout_ns; /* budget of every bounded device wait (0 = 2e9 ns) */
+    int symmetric;        /* 1 (default): a set's self-interaction evaluates every unordered
+                             pair once and adds it to both particles (Newton's third law);
+                             0: every ordered pair is evaluated by its receiving particle */
 } fsi_params;
 
-/* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off). */
+/* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,
+ * symmetric self-interaction). */
 void fsi_default_params(fsi_params *p);
 
 /* Create a context on the current CUDA device.  *ctx receives the handle.

@@ -49,16 +49,17 @@ cudaError_t launch_pack(int precision, int N, const double* pos, const double* m
 }
 
 template <int P>
-__global__ void pack_acc_kernel(int N, const double* __restrict__ accg, const int* __restrict__ idx,
+__global__ void pack_acc_kernel(int N, const double* __restrict__ accg,
+                                const double* __restrict__ mass, const int* __restrict__ idx,
                                 int n, void* __restrict__ accrec, double* __restrict__ ac) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const int i = idx_at(idx, k);
     const double x = accg[i], y = accg[(size_t)N + i], z = accg[2 * (size_t)N + i];
     if constexpr (P == FSI_MIXED)
-        reinterpret_cast<float4*>(accrec)[k] = make_float4((float)x, (float)y, (float)z, 0.f);
+        reinterpret_cast<float4*>(accrec)[k] = make_float4((float)x, (float)y, (float)z, (float)mass[i]);
     else
-        reinterpret_cast<D4*>(accrec)[k] = make_d4(x, y, z, 0.0);
+        reinterpret_cast<D4*>(accrec)[k] = make_d4(x, y, z, mass[i]);
     if (ac) {
         ac[k] = x;
         ac[(size_t)n + k] = y;
@@ -66,13 +67,13 @@ __global__ void pack_acc_kernel(int N, const double* __restrict__ accg, const in
     }
 }
 
-cudaError_t launch_pack_acc(int precision, int N, const double* accg, const int* idx, int n,
-                            void* accrec, double* ac, cudaStream_t s) {
+cudaError_t launch_pack_acc(int precision, int N, const double* accg, const double* mass,
+                            const int* idx, int n, void* accrec, double* ac, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (precision == FSI_MIXED)
-        { pack_acc_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(N, accg, idx, n, accrec, ac); note_launch(); }
+        { pack_acc_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(N, accg, mass, idx, n, accrec, ac); note_launch(); }
     else
-        { pack_acc_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(N, accg, idx, n, accrec, ac); note_launch(); }
+        { pack_acc_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(N, accg, mass, idx, n, accrec, ac); note_launch(); }
     return cudaGetLastError();
 }
 

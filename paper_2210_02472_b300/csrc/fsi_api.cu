@@ -63,7 +63,7 @@ struct fsi_ctx {
     int* err_h = nullptr;          // pinned
     int* counts_h = nullptr;       // pinned, 3 ints (HHS partition)
     Buf rec[2], accrec[2], xc, vc, ac, ad, gA, gB, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
-        nbh, apn, pnpart, epart, iota, steps, step0, counts;
+        nbh, apn, pnpart, epart, iota, steps, step0, counts, accum;
     std::vector<Buf> lvS, lvF;
     std::vector<long long> level_counts;
     int max_level_used = 0;
@@ -151,10 +151,38 @@ int timed(fsi_ctx* c, int kind, cudaStream_t s, F&& f) {
     return FSI_OK;
 }
 
+// Source tiles per work item of the symmetric kernel: about 8 items per resident CTA
+// slot, at most 64 tiles each.
+int choose_chunk(const fsi_ctx* c, int n, int ipt) {
+    const long long ntj = (n + kTileJ - 1) / kTileJ;
+    const long long nb = (n + (long long)kThreads * ipt - 1) / ((long long)kThreads * ipt);
+    const long long visits = nb * ntj / 2 + 1;
+    const long long want = 8LL * 2 * c->sm_count;
+    long long ch = visits / want;
+    return (int)std::max(1LL, std::min(64LL, ch));
+}
+
 int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
     if (a.n_i <= 0) return FSI_OK;
     const int prec = c->p.precision;
     const int ipt = c->ipt[prec][kind];
+    if (c->p.symmetric && a.check == CHECK_DIAG && a.irec == a.jrec && a.n_i == a.n_j &&
+        a.iacc == a.jacc) {
+        // self-interaction of one set: every unordered pair once, then the epilogue
+        const int n = a.n_i;
+        CK(ensure(c->accum, 3 * (size_t)n * sizeof(double)));
+        CU(cudaMemsetAsync(c->accum.p, 0, 3 * (size_t)n * sizeof(double), s));
+        const int chunk = choose_chunk(c, n, variant_ipt(ipt));
+        a.err = c->err_d;
+        a.timeout_ns = budget(c);
+        CK(timed(c, kind, s, [&] {
+            return launch_sym_pair(prec, kind, ipt, a.irec, a.iacc, n, a.eps2, chunk,
+                                   P<double>(c->accum), a.err, a.timeout_ns, s);
+        }));
+        a.part = P<double>(c->accum);
+        CK(timed(c, 2, s, [&] { return launch_finalize_p(prec, a, 1, s); }));
+        return FSI_OK;
+    }
     const int ipc = kThreads * variant_ipt(ipt);
     int split = choose_split(c, a.n_i, a.n_j, ipc);
     int jps = (a.n_j + split - 1) / split;
@@ -433,6 +461,7 @@ void fsi_default_params(fsi_params* p) {
     p->c = 0.0;
     p->split = 0;
     p->timeout_ns = 0;
+    p->symmetric = 1;
 }
 
 const char* fsi_last_error(void) { return g_err.c_str(); }
@@ -466,7 +495,7 @@ int fsi_destroy(fsi_ctx* c) {
     Buf* bufs[] = {&c->rec[0], &c->rec[1], &c->accrec[0], &c->accrec[1], &c->xc, &c->vc, &c->ac,
                    &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->mc, &c->bhc, &c->ids[0], &c->ids[1],
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
-                   &c->iota, &c->steps, &c->step0, &c->counts};
+                   &c->iota, &c->steps, &c->step0, &c->counts, &c->accum};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -569,7 +598,7 @@ int fsi_grad(fsi_ctx* c, int N, const double* pos, const double* mass, const dou
     CK(ensure(c->rec[0], pad_tile(nA) * 32));
     CK(ensure(c->accrec[0], pad_tile(nA) * 32));
     CU(launch_pack(prec, N, pos, mass, A, nA, c->rec[0].p, nullptr, s));
-    CU(launch_pack_acc(prec, N, accg, A, nA, c->accrec[0].p, nullptr, s));
+    CU(launch_pack_acc(prec, N, accg, mass, A, nA, c->accrec[0].p, nullptr, s));
     PairArgs a{};
     a.irec = c->rec[0].p;
     a.iacc = c->accrec[0].p;
@@ -587,7 +616,7 @@ int fsi_grad(fsi_ctx* c, int N, const double* pos, const double* mass, const dou
         CK(ensure(c->ids[0], pad_tile(nA) * 4));
         CK(ensure(c->ids[1], pad_tile(nB) * 4));
         CU(launch_pack(prec, N, pos, mass, B, nB, c->rec[1].p, nullptr, s));
-        CU(launch_pack_acc(prec, N, accg, B, nB, c->accrec[1].p, nullptr, s));
+        CU(launch_pack_acc(prec, N, accg, mass, B, nB, c->accrec[1].p, nullptr, s));
         CU(launch_ids(A, nA, (int)pad_tile(nA), P<int>(c->ids[0]), s));
         CU(launch_ids(B, nB, (int)pad_tile(nB), P<int>(c->ids[1]), s));
         a.jrec = c->rec[1].p;

@@ -11,14 +11,14 @@ namespace fsi {
 // that the O(n^2) kernels read contiguous, 16-byte-aligned tiles with bulk copies.
 //
 //  FP64 position record (32 B):  double4 (x, y, z, m)
-//  FP64 accel record    (32 B):  double4 (ax, ay, az, 0)
+//  FP64 accel record    (32 B):  double4 (ax, ay, az, m)
 //  MIXED position record (32 B): float4 (xh, yh, zh, 2.5 m), float4 (xl, yl, zl, -1.5 m)
 //        with xh = fl32(x) and xl = fl32(x - xh): xh + xl carries ~48 bits of x, so a
 //        pair difference (xh_j - xh_i) + (xl_j - xl_i) is accurate to FP32 precision
 //        relative to the separation even when |x| >> |r_ij|.  The two mass multiples
 //        fold the residual correction of the hardware rsqrt into one FMA:
 //        m r^-3 = y^3 (2.5 m - 1.5 m r^2 y^2) to first order in e = 1 - r^2 y^2.
-//  MIXED accel record   (16 B):  float4 (ax, ay, az, 0)
+//  MIXED accel record   (16 B):  float4 (ax, ay, az, m)
 // ---------------------------------------------------------------------------------
 struct alignas(32) D4 { double x, y, z, w; };   // 32-byte aligned FP64 quadruple
 __host__ __device__ __forceinline__ D4 make_d4(double x, double y, double z, double w) {
@@ -160,6 +160,11 @@ cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* sink, cudaSt
 cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int split,
                         cudaStream_t s);
 cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s);
+// Symmetric self-interaction pass (every unordered pair once); adds into accum (3 x n,
+// zeroed by the caller); `chunk` source tiles per work item.
+cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
+                            int n, double eps2, int chunk, double* accum, int* err,
+                            long long timeout_ns, cudaStream_t s);
 // Supported ipt values for (precision, kind): writes up to 8 into out, returns the count.
 int pair_variants(int precision, int kind, int* out);
 int pair_default_ipt(int precision, int kind);
@@ -167,8 +172,8 @@ int variant_ipt(int variant);
 
 cudaError_t launch_pack(int precision, int N, const double* pos, const double* mass,
                         const int* idx, int n, void* rec, double* xc, cudaStream_t s);
-cudaError_t launch_pack_acc(int precision, int N, const double* accg, const int* idx, int n,
-                            void* accrec, double* ac, cudaStream_t s);
+cudaError_t launch_pack_acc(int precision, int N, const double* accg, const double* mass,
+                            const int* idx, int n, void* accrec, double* ac, cudaStream_t s);
 cudaError_t launch_gather3(int N, const double* src, const int* idx, int n, double* dst,
                            cudaStream_t s);
 cudaError_t launch_scatter3(int N, const double* src, const int* idx, int n, double* dst,

@@ -29,6 +29,8 @@
 // overlapping the CTA's own i-range; general lists: every tile, by global id) run a
 // checked loop variant that replaces r^2 by 1 for the self pair (whose separation is
 // exactly 0, so its term vanishes).  All other tiles run the unchecked loop.
+#include <type_traits>
+
 #include "fsi_internal.cuh"
 
 namespace fsi {
@@ -127,22 +129,31 @@ __device__ __forceinline__ void f64_grad_pair(const D4 j, const D4 aj, const F64
     gz = fma(w, bz, fma(s, dz, gz));
 }
 
+// Mass carried by a position record (mixed records hold 2.5 m in FP32).
+template <int P>
+__device__ __forceinline__ double record_mass(const void* rec, int i) {
+    if constexpr (P == FSI_MIXED) return 0.4 * (double)reinterpret_cast<const RecMix*>(rec)[i].hi.w;
+    else return reinterpret_cast<const D4*>(rec)[i].w;
+}
+
 // ---------------------------------------------------------------------------------
 // Epilogue shared by the pair kernel (split == 1) and the finalize kernel.
 template <int P>
+// m_rec: the particle's mass as its position record carries it (used when e.mc is null).
 __device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, double ry,
-                                         double rz, int* err) {
+                                         double rz, double m_rec, int* err) {
     if (!(isfinite(rx) && isfinite(ry) && isfinite(rz))) set_error(err, FSI_ERR_NONFINITE);
     if (e.out) {
         e.out[i] = rx;
         e.out[(size_t)n + i] = ry;
         e.out[2 * (size_t)n + i] = rz;
     }
-    if (e.accrec) {
+    if (e.accrec) {   // accel record (ax, ay, az, m): the mass feeds the symmetric gradient
+        const double m = e.mc ? e.mc[i] : m_rec;
         if (P == FSI_MIXED)
-            reinterpret_cast<float4*>(e.accrec)[i] = make_float4((float)rx, (float)ry, (float)rz, 0.f);
+            reinterpret_cast<float4*>(e.accrec)[i] = make_float4((float)rx, (float)ry, (float)rz, (float)m);
         else
-            reinterpret_cast<D4*>(e.accrec)[i] = make_d4(rx, ry, rz, 0.0);
+            reinterpret_cast<D4*>(e.accrec)[i] = make_d4(rx, ry, rz, m);
     }
     if (e.v) {
         double kx = rx, ky = ry, kz = rz;
@@ -409,7 +420,8 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
             p[(size_t)a.n_i + i] = acc64[u][1];
             p[2 * (size_t)a.n_i + i] = acc64[u][2];
         } else {
-            epilogue<P>(a.epi, i, a.n_i, acc64[u][0], acc64[u][1], acc64[u][2], a.err);
+            epilogue<P>(a.epi, i, a.n_i, acc64[u][0], acc64[u][1], acc64[u][2],
+                        record_mass<P>(a.irec, i), a.err);
         }
     }
 }
@@ -426,7 +438,451 @@ __global__ void finalize_kernel(const PairArgs a, int split) {
         r[1] += p[(size_t)a.n_i + i];
         r[2] += p[2 * (size_t)a.n_i + i];
     }
-    epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], a.err);
+    epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], record_mass<P>(a.irec, i), a.err);
+}
+
+// =================================================================================
+// Symmetric pair kernel: the self-interaction of one set with every unordered pair
+// evaluated once (Newton's third law: the term of j on i and of i on j share the
+// separation, the reciprocal square root and the tidal factor).
+//
+// Work items (blockIdx.x = b * (1 + nchunk) + c): i-block b (256 * I consecutive
+// particles held in registers) against
+//   c = 0   : the tiles of its own block, one-sided (i-side only, self pair excluded
+//             by index) -- every pair inside a block is then evaluated twice, which is
+//             only (256 I)/n of the work;
+//   c >= 1  : chunk c-1 of `chunk` tiles among the tiles above the block, symmetric.
+// Items past the end of the tile range exit at once.  The i-side sums (FP32 per tile,
+// FP64 across tiles) and the j-side sums (FP32 warp reduce-scatter + shared-memory sum
+// over the CTA's warps, per tile) are added to the FP64 accumulator with red.global.add;
+// a finalize kernel then applies the epilogue.
+struct SymArgs {
+    const void* rec;
+    const void* accrec;
+    int n;
+    int chunk;
+    int nchunk;
+    double eps2;
+    double* accum;      // 3 x n, zeroed before the launch
+    int* err;
+    long long timeout_ns;
+};
+
+__device__ __forceinline__ void red_add(double* p, double v) {
+    asm volatile("red.global.add.f64 [%0], %1;" :: "l"(p), "d"(v) : "memory");
+}
+
+// Reduce-scatter of 4 j-groups x 3 components over a warp: on return every lane holds in
+// out[] the warp total of j-group (lane >> 3).
+template <class T>
+__device__ __forceinline__ void reduce_scatter4(const T (&v)[4][3], int lane, T (&out)[3]) {
+    const bool b4 = (lane >> 4) & 1, b3 = (lane >> 3) & 1;
+    T k1[2][3];
+#pragma unroll
+    for (int k = 0; k < 2; ++k)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const T send = b4 ? v[k][q] : v[2 + k][q];
+            const T keep = b4 ? v[2 + k][q] : v[k][q];
+            k1[k][q] = keep + __shfl_xor_sync(0xffffffffu, send, 16);
+        }
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const T send = b3 ? k1[0][q] : k1[1][q];
+        const T keep = b3 ? k1[1][q] : k1[0][q];
+        T r = keep + __shfl_xor_sync(0xffffffffu, send, 8);
+        r += __shfl_xor_sync(0xffffffffu, r, 4);
+        r += __shfl_xor_sync(0xffffffffu, r, 2);
+        r += __shfl_xor_sync(0xffffffffu, r, 1);
+        out[q] = r;
+    }
+}
+
+// i-side state of the symmetric kernel.
+struct SymMixI {
+    float xh, yh, zh, xl, yl, zl;
+    float nA, nB;          // -2.5 m_i, +1.5 m_i  (j-side weight -m_i r^-3, refined)
+    float ax, ay, az, nm;  // gradient: a_i and -m_i
+};
+
+__device__ __forceinline__ void mix_acc_sym(const float4 h, const float4 l, const SymMixI& p,
+                                            float eps2f, float (&fi)[3], float (&fj)[3]) {
+    const float dx = (h.x - p.xh) + (l.x - p.xl);
+    const float dy = (h.y - p.yh) + (l.y - p.yl);
+    const float dz = (h.z - p.zh) + (l.z - p.zl);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2f)));
+    const float y = rsqrt_hw(r2);
+    const float y2 = y * y;
+    const float sres = r2 * y2;
+    const float y3 = y2 * y;
+    const float wi = y3 * fmaf(sres, l.w, h.w);     //  m_j r^-3
+    const float wj = y3 * fmaf(sres, p.nB, p.nA);   // -m_i r^-3
+    fi[0] = fmaf(wi, dx, fi[0]); fi[1] = fmaf(wi, dy, fi[1]); fi[2] = fmaf(wi, dz, fi[2]);
+    fj[0] = fmaf(wj, dx, fj[0]); fj[1] = fmaf(wj, dy, fj[1]); fj[2] = fmaf(wj, dz, fj[2]);
+}
+
+__device__ __forceinline__ void mix_grad_sym(const float4 h, const float4 l, const float4 aj,
+                                             const SymMixI& p, float eps2f,
+                                             float (&gi)[3], float (&gj)[3]) {
+    const float dx = (h.x - p.xh) + (l.x - p.xl);
+    const float dy = (h.y - p.yh) + (l.y - p.yl);
+    const float dz = (h.z - p.zh) + (l.z - p.zl);
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2f)));
+    const float y = rsqrt_hw(r2);
+    const float y2 = y * y;
+    const float sres = r2 * y2;
+    const float r3 = (y2 * y) * fmaf(sres, -1.5f, 2.5f);           // r^-3 (refined)
+    const float bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;
+    const float dot = fmaf(bx, dx, fmaf(by, dy, bz * dz));
+    const float q = r3 * (y2 * fmaf(3.0f, sres, -6.0f));           // -3 r^-5 (refined)
+    const float s = q * dot;
+    // T(d) b = r^-3 b - 3 r^-5 (b.d) d: on i with weight m_j, on j with weight -m_i
+    const float tx = fmaf(r3, bx, s * dx), ty = fmaf(r3, by, s * dy), tz = fmaf(r3, bz, s * dz);
+    gi[0] = fmaf(aj.w, tx, gi[0]); gi[1] = fmaf(aj.w, ty, gi[1]); gi[2] = fmaf(aj.w, tz, gi[2]);
+    gj[0] = fmaf(p.nm, tx, gj[0]); gj[1] = fmaf(p.nm, ty, gj[1]); gj[2] = fmaf(p.nm, tz, gj[2]);
+}
+
+struct SymF64I {
+    double x, y, z, nm;
+    double ax, ay, az;
+};
+
+__device__ __forceinline__ void f64_acc_sym(const D4 j, const SymF64I& p, double eps2,
+                                            double (&fi)[3], double (&fj)[3]) {
+    const double dx = j.x - p.x, dy = j.y - p.y, dz = j.z - p.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double y = rsqrt_f64(r2);
+    const double y3 = (y * y) * y;
+    const double wi = j.w * y3, wj = p.nm * y3;
+    fi[0] = fma(wi, dx, fi[0]); fi[1] = fma(wi, dy, fi[1]); fi[2] = fma(wi, dz, fi[2]);
+    fj[0] = fma(wj, dx, fj[0]); fj[1] = fma(wj, dy, fj[1]); fj[2] = fma(wj, dz, fj[2]);
+}
+
+__device__ __forceinline__ void f64_grad_sym(const D4 j, const D4 aj, const SymF64I& p,
+                                             double eps2, double (&gi)[3], double (&gj)[3]) {
+    const double dx = j.x - p.x, dy = j.y - p.y, dz = j.z - p.z;
+    const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+    const double y = rsqrt_f64(r2);
+    const double y2 = y * y;
+    const double y3 = y2 * y;
+    const double bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;
+    const double dot = fma(bx, dx, fma(by, dy, bz * dz));
+    const double s = (y3 * y2) * (-3.0 * dot);
+    const double tx = fma(y3, bx, s * dx), ty = fma(y3, by, s * dy), tz = fma(y3, bz, s * dz);
+    gi[0] = fma(aj.w, tx, gi[0]); gi[1] = fma(aj.w, ty, gi[1]); gi[2] = fma(aj.w, tz, gi[2]);
+    gj[0] = fma(p.nm, tx, gj[0]); gj[1] = fma(p.nm, ty, gj[1]); gj[2] = fma(p.nm, tz, gj[2]);
+}
+
+template <int P, int KIND>
+struct SymCfg {
+    static constexpr int ACCREC = Cfg<P, KIND>::ACCREC;
+    static constexpr int SB = kTileJ * (kRec + ACCREC);           // one pipeline stage
+    using JT = typename std::conditional<P == FSI_MIXED, float, double>::type;
+    static constexpr int JPART = (kThreads / 32) * kTileJ * 3 * (int)sizeof(JT);
+    static constexpr int SMEM = kStages * SB + JPART;
+};
+
+template <int P, int KIND, int I>
+__global__ void __launch_bounds__(kThreads, 2) sym_pair_kernel(const SymArgs a) {
+    static_assert(kThreads == kTileJ, "an i-block spans I source tiles");
+    using JT = typename SymCfg<P, KIND>::JT;
+    constexpr int ACCREC = SymCfg<P, KIND>::ACCREC;
+    constexpr int SB = SymCfg<P, KIND>::SB;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    JT* jpart = reinterpret_cast<JT*>(smem + kStages * SB);
+
+    const int b = blockIdx.x / (1 + a.nchunk);
+    const int c = blockIdx.x % (1 + a.nchunk);
+    const int ntj = (a.n + kTileJ - 1) / kTileJ;
+    const bool diag = (c == 0);
+    int t0, t1;
+    if (diag) { t0 = b * I; t1 = min((b + 1) * I, ntj); }
+    else { t0 = (b + 1) * I + (c - 1) * a.chunk; t1 = min(t0 + a.chunk, ntj); }
+    if (t0 >= t1) return;                       // uniform: before any barrier
+    const int ntiles = t1 - t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = b * (kThreads * I);
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) mbar_init(&bars[s], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int s = t % kStages;
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n - jt);
+        unsigned char* base = smem + s * SB;
+        mbar_arrive_expect_tx(&bars[s], (uint32_t)cnt * (kRec + ACCREC));
+        bulk_g2s(base, (const unsigned char*)a.rec + (size_t)jt * kRec, (uint32_t)cnt * kRec, &bars[s]);
+        if (ACCREC)
+            bulk_g2s(base + kTileJ * kRec, (const unsigned char*)a.accrec + (size_t)jt * ACCREC,
+                     (uint32_t)cnt * ACCREC, &bars[s]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+
+    double acc64[I][3];
+    bool valid[I];
+    int my_i[I];
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        acc64[u][0] = acc64[u][1] = acc64[u][2] = 0.0;
+        my_i[u] = i0 + u * kThreads + tid;
+        valid[u] = my_i[u] < a.n;
+    }
+
+    bool aborted = false;
+    int t_stop = ntiles;
+    if constexpr (P == FSI_MIXED) {
+        SymMixI pi[I];
+        float f[I][3];
+#pragma unroll
+        for (int u = 0; u < I; ++u) {
+            const int i = min(my_i[u], a.n - 1);
+            const RecMix r = reinterpret_cast<const RecMix*>(a.rec)[i];
+            pi[u].xh = r.hi.x; pi[u].yh = r.hi.y; pi[u].zh = r.hi.z;
+            pi[u].xl = r.lo.x; pi[u].yl = r.lo.y; pi[u].zl = r.lo.z;
+            // an i past the end contributes nothing to the j side
+            pi[u].nA = valid[u] ? -r.hi.w : 0.f;
+            pi[u].nB = valid[u] ? -r.lo.w : 0.f;
+            if constexpr (KIND == KIND_GRAD) {
+                const float4 ai = reinterpret_cast<const float4*>(a.accrec)[i];
+                pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
+                pi[u].nm = valid[u] ? -ai.w : 0.f;
+            } else {
+                pi[u].ax = pi[u].ay = pi[u].az = pi[u].nm = 0.f;
+            }
+            f[u][0] = f[u][1] = f[u][2] = 0.f;
+        }
+        const float eps2f = (float)a.eps2;
+        for (int t = 0; t < ntiles; ++t) {
+            const int s = t % kStages;
+            const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+            const int jt = (t0 + t) * kTileJ;
+            const int cnt = min(kTileJ, a.n - jt);
+            const unsigned char* base = smem + s * SB;
+            const RecMix* rec = reinterpret_cast<const RecMix*>(base);
+            const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
+            if (diag) {
+                // one-sided, self pair excluded by index (reuses the one-sided pair code)
+                MixI q[I];
+#pragma unroll
+                for (int u = 0; u < I; ++u) {
+                    q[u].xh = pi[u].xh; q[u].yh = pi[u].yh; q[u].zh = pi[u].zh;
+                    q[u].xl = pi[u].xl; q[u].yl = pi[u].yl; q[u].zl = pi[u].zl;
+                    q[u].ax = pi[u].ax; q[u].ay = pi[u].ay; q[u].az = pi[u].az;
+                }
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const float4 h = rec[jj].hi;
+                    const float4 l = rec[jj].lo;
+                    if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                        for (int u = 0; u < I; ++u)
+                            mix_acc_pair<true>(h, l, q[u], eps2f, jt + jj == my_i[u], f[u][0], f[u][1], f[u][2]);
+                    } else {
+                        const float4 aj = arec[jj];
+#pragma unroll
+                        for (int u = 0; u < I; ++u)
+                            mix_grad_pair<true>(h, l, aj, q[u], eps2f, jt + jj == my_i[u], f[u][0], f[u][1], f[u][2]);
+                    }
+                }
+            } else {
+                for (int jj = 0; jj < cnt; jj += 4) {
+                    float fj[4][3];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        fj[g][0] = fj[g][1] = fj[g][2] = 0.f;
+                        if (jj + g < cnt) {
+                            const float4 h = rec[jj + g].hi;
+                            const float4 l = rec[jj + g].lo;
+                            if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                                for (int u = 0; u < I; ++u) mix_acc_sym(h, l, pi[u], eps2f, f[u], fj[g]);
+                            } else {
+                                const float4 aj = arec[jj + g];
+#pragma unroll
+                                for (int u = 0; u < I; ++u) mix_grad_sym(h, l, aj, pi[u], eps2f, f[u], fj[g]);
+                            }
+                        }
+                    }
+                    float tot[3];
+                    reduce_scatter4<float>(fj, lane, tot);
+                    const int jl = jj + (lane >> 3);
+                    if ((lane & 7) == 0 && jl < cnt) {
+                        JT* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
+                        dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+                    }
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < I; ++u)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    acc64[u][q] += (double)f[u][q];
+                    f[u][q] = 0.f;
+                }
+            if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+            if (!diag && tid < cnt) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    float sum = 0.f;
+#pragma unroll
+                    for (int w = 0; w < kThreads / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
+                    red_add(a.accum + (size_t)q * a.n + jt + tid, (double)sum);
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+        }
+    } else {
+        SymF64I pi[I];
+#pragma unroll
+        for (int u = 0; u < I; ++u) {
+            const int i = min(my_i[u], a.n - 1);
+            const D4 r = reinterpret_cast<const D4*>(a.rec)[i];
+            pi[u].x = r.x; pi[u].y = r.y; pi[u].z = r.z;
+            pi[u].nm = valid[u] ? -r.w : 0.0;
+            if constexpr (KIND == KIND_GRAD) {
+                const D4 ai = reinterpret_cast<const D4*>(a.accrec)[i];
+                pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
+            } else {
+                pi[u].ax = pi[u].ay = pi[u].az = 0.0;
+            }
+        }
+        for (int t = 0; t < ntiles; ++t) {
+            const int s = t % kStages;
+            const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+            const int jt = (t0 + t) * kTileJ;
+            const int cnt = min(kTileJ, a.n - jt);
+            const unsigned char* base = smem + s * SB;
+            const D4* rec = reinterpret_cast<const D4*>(base);
+            const D4* arec = reinterpret_cast<const D4*>(base + kTileJ * kRec);
+            if (diag) {
+                F64I q[I];
+#pragma unroll
+                for (int u = 0; u < I; ++u) {
+                    q[u].x = pi[u].x; q[u].y = pi[u].y; q[u].z = pi[u].z;
+                    q[u].ax = pi[u].ax; q[u].ay = pi[u].ay; q[u].az = pi[u].az;
+                }
+                for (int jj = 0; jj < cnt; ++jj) {
+                    const D4 r = rec[jj];
+                    if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                        for (int u = 0; u < I; ++u)
+                            f64_acc_pair<true>(r, q[u], a.eps2, jt + jj == my_i[u], acc64[u][0], acc64[u][1], acc64[u][2]);
+                    } else {
+                        const D4 aj = arec[jj];
+#pragma unroll
+                        for (int u = 0; u < I; ++u)
+                            f64_grad_pair<true>(r, aj, q[u], a.eps2, jt + jj == my_i[u], acc64[u][0], acc64[u][1], acc64[u][2]);
+                    }
+                }
+            } else {
+                for (int jj = 0; jj < cnt; jj += 4) {
+                    double fj[4][3];
+#pragma unroll
+                    for (int g = 0; g < 4; ++g) {
+                        fj[g][0] = fj[g][1] = fj[g][2] = 0.0;
+                        if (jj + g < cnt) {
+                            const D4 r = rec[jj + g];
+                            if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                                for (int u = 0; u < I; ++u) f64_acc_sym(r, pi[u], a.eps2, acc64[u], fj[g]);
+                            } else {
+                                const D4 aj = arec[jj + g];
+#pragma unroll
+                                for (int u = 0; u < I; ++u) f64_grad_sym(r, aj, pi[u], a.eps2, acc64[u], fj[g]);
+                            }
+                        }
+                    }
+                    double tot[3];
+                    reduce_scatter4<double>(fj, lane, tot);
+                    const int jl = jj + (lane >> 3);
+                    if ((lane & 7) == 0 && jl < cnt) {
+                        JT* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
+                        dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+                    }
+                }
+            }
+            if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+            if (!diag && tid < cnt) {
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    double sum = 0.0;
+#pragma unroll
+                    for (int w = 0; w < kThreads / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
+                    red_add(a.accum + (size_t)q * a.n + jt + tid, sum);
+                }
+            }
+            __syncthreads();
+            if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+        }
+    }
+
+    if (aborted) {
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int t = t_stop; t < issued; ++t)
+                mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1), a.timeout_ns, nullptr);
+        }
+        __syncthreads();
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        if (!valid[u]) continue;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) red_add(a.accum + (size_t)q * a.n + my_i[u], acc64[u][q]);
+    }
+}
+
+template <int P, int KIND, int I>
+static cudaError_t launch_sym_one(const SymArgs& a, cudaStream_t s) {
+    constexpr int SMEM = SymCfg<P, KIND>::SMEM;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sym_pair_kernel<P, KIND, I>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
+    const long long grid = (long long)nb * (1 + a.nchunk);
+    if (grid > 2147483647LL) return cudaErrorInvalidValue;
+    { sym_pair_kernel<P, KIND, I><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    return cudaGetLastError();
+}
+
+template <int P, int KIND>
+static cudaError_t launch_sym_ipt(int ipt, const SymArgs& a, cudaStream_t s) {
+    switch (ipt) {
+        case 1: return launch_sym_one<P, KIND, 1>(a, s);
+        case 2: return launch_sym_one<P, KIND, 2>(a, s);
+        case 3: return launch_sym_one<P, KIND, 3>(a, s);
+        case 4: return launch_sym_one<P, KIND, 4>(a, s);
+        default: return cudaErrorInvalidValue;
+    }
+}
+
+cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
+                            int n, double eps2, int chunk, double* accum, int* err,
+                            long long timeout_ns, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    SymArgs a;
+    a.rec = rec; a.accrec = accrec; a.n = n; a.eps2 = eps2; a.accum = accum; a.err = err;
+    a.timeout_ns = timeout_ns;
+    const int I = ipt & 15;
+    const int ntj = (n + kTileJ - 1) / kTileJ;
+    a.chunk = chunk > 0 ? chunk : 1;
+    const int above = ntj > I ? ntj - I : 0;       // most tiles above any block (block 0)
+    a.nchunk = (above + a.chunk - 1) / a.chunk;
+    if (precision == FSI_MIXED)
+        return kind == KIND_ACC ? launch_sym_ipt<FSI_MIXED, KIND_ACC>(I, a, s)
+                                : launch_sym_ipt<FSI_MIXED, KIND_GRAD>(I, a, s);
+    return kind == KIND_ACC ? launch_sym_ipt<FSI_FP64, KIND_ACC>(I, a, s)
+                            : launch_sym_ipt<FSI_FP64, KIND_GRAD>(I, a, s);
 }
 
 // ---------------------------------------------------------------------------------

@@ -148,11 +148,45 @@ def test_split_factor_does_not_change_results(F, prec):
     c = inputs.plummer(5000, 11, imf="kroupa")
     outs = []
     for split in (1, 3, 7):
-        with F.Context(prec, split=split) as ctx:
+        with F.Context(prec, split=split, symmetric=False) as ctx:
             outs.append(host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass))))
     for o in outs[1:]:
         e = rel_err(o, outs[0])
         assert e.max() <= (1e-13 if prec == "fp64" else 1e-9)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [700, 4097, 20000])
+def test_symmetric_matches_one_sided(F, prec, n):
+    """Every unordered pair once (Newton's third law) vs every ordered pair: the same sums
+    up to rounding, for every kernel variant."""
+    c = inputs.plummer(n, 41 + n, imf="kroupa")
+    with F.Context(prec, symmetric=False) as ctx:
+        a1, g1 = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
+        a1, g1 = host(a1), host(g1)
+    variants = (2, 3, 4) if prec == "mixed" else (1, 2, 3)
+    with F.Context(prec) as ctx:
+        for v in variants:
+            F.fsi_set_tuning(ctx, v, v)
+            a2, g2 = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
+            a2, g2 = host(a2), host(g2)
+            assert F.fsi_sync_status(ctx) == F.FSI_OK
+            ea, eg = rel_err(a2, a1), rel_err(g2, g1)
+            tol_a = 1e-12 if prec == "fp64" else 2e-6
+            tol_g = 1e-11 if prec == "fp64" else 1e-3
+            assert ea.max() <= tol_a, (v, ea.max())
+            assert np.median(eg) <= tol_g / 10 and np.percentile(eg, 99) <= tol_g, (v, eg.max())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_symmetric_momentum_balance(F, prec):
+    """The symmetric pass applies equal and opposite pair terms: sum_i m_i a_i ~ 0."""
+    c = inputs.plummer(30000, 44, imf="kroupa")
+    with F.Context(prec) as ctx:
+        a = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass)))
+    tot = np.abs((a * c.mass).sum(axis=1)).max()
+    scale = np.abs(a * c.mass).sum()
+    assert tot <= (1e-13 if prec == "fp64" else 1e-7) * scale
 
 
 # ----------------------------------------------------------------------------- grad
