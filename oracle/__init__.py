@@ -76,6 +76,12 @@ def lib():
                                    C.c_double, C.c_double, dp]
         L.or_hhs_interval.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.POINTER(_HHSParams),
                                       C.POINTER(C.c_longlong)]
+        L.or_vjp_acc.argtypes = [C.c_int, dp, dp, ip, C.c_int, C.c_double, dp, C.c_double,
+                                 C.c_double, dp, dp]
+        L.or_vjp_grad.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int, C.c_double, dp, C.c_double,
+                                  dp, dp]
+        L.or_fsi_step_vjp.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int, C.c_double, C.c_double,
+                                      dp, dp, dp, dp, dp]
         L.or_set_threads.argtypes = [C.c_int]
         L.or_get_threads.restype = C.c_int
         _lib = L
@@ -220,3 +226,39 @@ def hhs_interval(pos, vel, mass, tau, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eps2
     if code != OK and not (allow_maxlevel and code == ERR_MAXLEVEL):
         raise OracleError(code, "hhs_interval")
     return pos, vel, counts, code
+
+
+def vjp_acc(pos, mass, u, P=None, eps2=0.0):
+    """(xbar (3, N), mbar (N,)) of the acceleration's VJP with cotangent u (3, N) over P."""
+    pos, mass, u, P = _f64(pos), _f64(mass), _f64(u), _idx(P)
+    N = mass.shape[0]
+    xb = np.zeros((3, N))
+    mb = np.zeros(N)
+    _check(lib().or_vjp_acc(N, _d(pos), _d(mass), _i(P), _n(P, N), float(eps2), _d(u), 1.0, 1.0,
+                            _d(xb), _d(mb)), "vjp_acc")
+    return xb, mb
+
+
+def vjp_grad(pos, mass, acc, w, P=None, eps2=0.0):
+    """(xbar, mbar) of the gradient sum's VJP through r and m (a held fixed)."""
+    pos, mass, acc, w, P = _f64(pos), _f64(mass), _f64(acc), _f64(w), _idx(P)
+    N = mass.shape[0]
+    xb = np.zeros((3, N))
+    mb = np.zeros(N)
+    _check(lib().or_vjp_grad(N, _d(pos), _d(mass), _d(acc), _i(P), _n(P, N), float(eps2), _d(w),
+                             1.0, _d(xb), _d(mb)), "vjp_grad")
+    return xb, mb
+
+
+def fsi_step_vjp(pos0, vel0, mass, h, gx_out, gv_out, P=None, eps2=0.0):
+    """Cotangents (gx_in, gv_in, gm) of one FSI step's input given the output cotangents."""
+    pos0, vel0, mass, P = _f64(pos0), _f64(vel0), _f64(mass), _idx(P)
+    gx_out, gv_out = _f64(gx_out), _f64(gv_out)
+    N = mass.shape[0]
+    gx = np.zeros((3, N))
+    gv = np.zeros((3, N))
+    gm = np.zeros(N)
+    _check(lib().or_fsi_step_vjp(N, _d(pos0), _d(vel0), _d(mass), _i(P), _n(P, N), float(h),
+                                 float(eps2), _d(gx_out), _d(gv_out), _d(gx), _d(gv), _d(gm)),
+           "fsi_step_vjp")
+    return gx, gv, gm

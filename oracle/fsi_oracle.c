@@ -590,3 +590,231 @@ int or_level0_steps(int N, const double *pos, const double *vel, const double *m
     return or_timesteps(N, pos, vel, mass, NULL, N, p->eta_ff, p->eta_fb, p->eta_jerk,
                         p->eps2, step);
 }
+
+/* =============================================================================== *
+ * Adjoint (vector-Jacobian product) of the FSI cycle, hand-derived from the equations
+ * of Sect. 2.1.  Notation for a receiver k and a source j != k of the set:
+ *   d = r_j - r_k,  s^2 = |d|^2 + eps2,  f(d) = d / s^3,
+ *   T(d) = df/dd = I / s^3 - 3 d d^T / s^5             (symmetric, even in d),
+ *   Q(d, b) = d(T(d) b)/dd
+ *           = -3/s^5 (b d^T + d b^T + (d.b) I) + 15 (d.b) d d^T / s^7   (symmetric).
+ * With a_k = sum_j m_j f(d) (Eq. new-newton-acc) and G_k = sum_j m_j T(d)(a_j - a_k)
+ * (Eq. new-grad-acc):
+ *   VJP of a with cotangent u:
+ *     xbar_k = sum_j T(d) (m_k u_j - m_j u_k),   mbar_k = - sum_j u_j . d / s^3
+ *   VJP of G through its explicit dependence on r and m (a held fixed), cotangent w:
+ *     xbar_k = sum_j Q(d, a_j - a_k) (m_k w_j - m_j w_k),
+ *     mbar_k = - sum_j w_j . T(d) (a_j - a_k)
+ *   VJP of G through a (cotangent on a):  abar_k = sum_j T(d) (m_k w_j - m_j w_k).
+ * =============================================================================== */
+
+/* xbar[:, k] += sx * (VJP of acc)_x,  mbar[k] += sm * (VJP of acc)_m  over the set P,
+ * with u a 3 x N array indexed by global id. */
+int or_vjp_acc(int N, const double *pos, const double *mass, const int *Pl, int n,
+               double eps2, const double *u, double sx, double sm, double *xbar,
+               double *mbar)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    const double *UX = u, *UY = u + N, *UZ = u + 2 * (size_t)N;
+    int err = OR_OK;
+    int q;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (q = 0; q < n; ++q) {
+        int k = idx_at(Pl, q);
+        double gx = 0, gy = 0, gz = 0, gm = 0;
+        for (int l = 0; l < n; ++l) {
+            int j = idx_at(Pl, l);
+            if (j == k) continue;
+            double dx = X[j] - X[k], dy = Y[j] - Y[k], dz = Z[j] - Z[k];
+            double s2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (s2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double s = sqrt(s2);
+            double is3 = 1.0 / (s2 * s), is5 = is3 / s2;
+            double cx = mass[k] * UX[j] - mass[j] * UX[k];
+            double cy = mass[k] * UY[j] - mass[j] * UY[k];
+            double cz = mass[k] * UZ[j] - mass[j] * UZ[k];
+            double dc = dx * cx + dy * cy + dz * cz;
+            gx += is3 * cx - 3.0 * is5 * dc * dx;
+            gy += is3 * cy - 3.0 * is5 * dc * dy;
+            gz += is3 * cz - 3.0 * is5 * dc * dz;
+            gm -= (UX[j] * dx + UY[j] * dy + UZ[j] * dz) * is3;
+        }
+        if (xbar) {
+            xbar[k] += sx * gx;
+            xbar[(size_t)N + k] += sx * gy;
+            xbar[2 * (size_t)N + k] += sx * gz;
+        }
+        if (mbar) mbar[k] += sm * gm;
+    }
+    return err;
+}
+
+/* xbar, mbar += scale * (VJP of G through r and m, a held fixed), cotangent w, over P.
+ * acc: the accelerations inside G (3 x N, global id). */
+int or_vjp_grad(int N, const double *pos, const double *mass, const double *acc,
+                const int *Pl, int n, double eps2, const double *w, double scale,
+                double *xbar, double *mbar)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    const double *AX = acc, *AY = acc + N, *AZ = acc + 2 * (size_t)N;
+    const double *WX = w, *WY = w + N, *WZ = w + 2 * (size_t)N;
+    int err = OR_OK;
+    int q;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (q = 0; q < n; ++q) {
+        int k = idx_at(Pl, q);
+        double gx = 0, gy = 0, gz = 0, gm = 0;
+        for (int l = 0; l < n; ++l) {
+            int j = idx_at(Pl, l);
+            if (j == k) continue;
+            double dx = X[j] - X[k], dy = Y[j] - Y[k], dz = Z[j] - Z[k];
+            double s2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (s2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double s = sqrt(s2);
+            double is3 = 1.0 / (s2 * s), is5 = is3 / s2, is7 = is5 / s2;
+            double bx = AX[j] - AX[k], by = AY[j] - AY[k], bz = AZ[j] - AZ[k];
+            double cx = mass[k] * WX[j] - mass[j] * WX[k];
+            double cy = mass[k] * WY[j] - mass[j] * WY[k];
+            double cz = mass[k] * WZ[j] - mass[j] * WZ[k];
+            double db = dx * bx + dy * by + dz * bz;
+            double dc = dx * cx + dy * cy + dz * cz;
+            double bc = bx * cx + by * cy + bz * cz;
+            /* Q(d, b) c */
+            gx += -3.0 * is5 * (bx * dc + dx * bc + db * cx) + 15.0 * is7 * db * dc * dx;
+            gy += -3.0 * is5 * (by * dc + dy * bc + db * cy) + 15.0 * is7 * db * dc * dy;
+            gz += -3.0 * is5 * (bz * dc + dz * bc + db * cz) + 15.0 * is7 * db * dc * dz;
+            /* -w_j . T(d) b */
+            double tbx = is3 * bx - 3.0 * is5 * db * dx;
+            double tby = is3 * by - 3.0 * is5 * db * dy;
+            double tbz = is3 * bz - 3.0 * is5 * db * dz;
+            gm -= WX[j] * tbx + WY[j] * tby + WZ[j] * tbz;
+        }
+        if (xbar) {
+            xbar[k] += scale * gx;
+            xbar[(size_t)N + k] += scale * gy;
+            xbar[2 * (size_t)N + k] += scale * gz;
+        }
+        if (mbar) mbar[k] += scale * gm;
+    }
+    return err;
+}
+
+/* Reverse of one or_fsi_step (PN off) of the set P, h, eps2.  Given the input state
+ * (pos0, vel0) and the cotangents (gx_out, gv_out) of the output state, writes the
+ * cotangents of the input state into gx_in, gv_in (3 x N; entries outside P pass
+ * through) and adds the mass cotangent into gm (N).  The forward intermediates are
+ * recomputed.  The reverse follows the cycle backwards:
+ *   v3 = v2 + h/6 a(x2);  x2 = x1 + h/2 v2;  v2 = v1 + 2h/3 (a(x1) + h^2/24 G(x1));
+ *   x1 = x0 + h/2 v1;     v1 = v0 + h/6 a(x0). */
+int or_fsi_step_vjp(int N, const double *pos0, const double *vel0, const double *mass,
+                    const int *Pl, int n, double h, double eps2,
+                    const double *gx_out, const double *gv_out,
+                    double *gx_in, double *gv_in, double *gm)
+{
+    size_t N3 = 3 * (size_t)N;
+    double *x1 = (double *)malloc(N3 * sizeof(double));
+    double *x2 = (double *)malloc(N3 * sizeof(double));
+    double *v1 = (double *)malloc(N3 * sizeof(double));
+    double *v2 = (double *)malloc(N3 * sizeof(double));
+    double *a0 = (double *)calloc(N3, sizeof(double));
+    double *a1 = (double *)calloc(N3, sizeof(double));
+    double *g1 = (double *)calloc(N3, sizeof(double));
+    double *tmp = (double *)malloc(N3 * sizeof(double));
+    double *X = (double *)malloc(N3 * sizeof(double));
+    double *V = (double *)malloc(N3 * sizeof(double));
+    double *wt = (double *)calloc(N3, sizeof(double));
+    double *ab = (double *)calloc(N3, sizeof(double));
+    double *u = (double *)calloc(N3, sizeof(double));
+    if (!x1 || !x2 || !v1 || !v2 || !a0 || !a1 || !g1 || !tmp || !X || !V || !wt || !ab || !u) {
+        free(x1); free(x2); free(v1); free(v2); free(a0); free(a1); free(g1); free(tmp);
+        free(X); free(V); free(wt); free(ab); free(u);
+        return OR_ERR_NOMEM;
+    }
+    int err;
+    /* forward recompute (global-id arrays) */
+    memcpy(x1, pos0, N3 * sizeof(double));
+    memcpy(v1, vel0, N3 * sizeof(double));
+    err = or_acc(N, pos0, mass, Pl, n, Pl, n, eps2, tmp);
+    if (err == OR_OK) {
+        scatter3(N, Pl, n, tmp, a0);
+        kick(N, v1, Pl, n, tmp, h / 6.0);
+        drift(N, x1, v1, Pl, n, 0.5 * h);
+        double *gg = (double *)malloc(3 * (size_t)(n > 0 ? n : 1) * sizeof(double));
+        if (!gg) err = OR_ERR_NOMEM;
+        else {
+            err = or_accel_grad(N, x1, mass, Pl, n, Pl, n, eps2, tmp, gg);
+            scatter3(N, Pl, n, tmp, a1);
+            scatter3(N, Pl, n, gg, g1);
+            free(gg);
+        }
+    }
+    if (err == OR_OK) {
+        memcpy(v2, v1, N3 * sizeof(double));
+        memcpy(x2, x1, N3 * sizeof(double));
+        for (int q = 0; q < n; ++q) {
+            int k = idx_at(Pl, q);
+            for (int c = 0; c < 3; ++c) {
+                size_t o = (size_t)c * N + k;
+                v2[o] += 2.0 * h / 3.0 * (a1[o] + h * h / 24.0 * g1[o]);
+            }
+        }
+        drift(N, x2, v2, Pl, n, 0.5 * h);
+    }
+    /* reverse */
+    if (err == OR_OK) {
+        memcpy(X, gx_out, N3 * sizeof(double));
+        memcpy(V, gv_out, N3 * sizeof(double));
+        /* v3 = v2 + h/6 a(x2) */
+        err = or_vjp_acc(N, x2, mass, Pl, n, eps2, V, h / 6.0, h / 6.0, X, gm);
+    }
+    if (err == OR_OK) {
+        /* x2 = x1 + h/2 v2 */
+        for (int q = 0; q < n; ++q) {
+            int k = idx_at(Pl, q);
+            for (int c = 0; c < 3; ++c) V[(size_t)c * N + k] += 0.5 * h * X[(size_t)c * N + k];
+        }
+        /* v2 = v1 + 2h/3 a~(x1): cotangent on a~ is wt = 2h/3 V */
+        for (int q = 0; q < n; ++q) {
+            int k = idx_at(Pl, q);
+            for (int c = 0; c < 3; ++c) wt[(size_t)c * N + k] = 2.0 * h / 3.0 * V[(size_t)c * N + k];
+        }
+        double cg = h * h / 24.0;
+        /* abar = cg * (dG/da)^T wt  (same pair form as the acc VJP's position part) */
+        err = or_vjp_acc(N, x1, mass, Pl, n, eps2, wt, cg, 0.0, ab, NULL);
+        if (err == OR_OK) {
+            for (int q = 0; q < n; ++q) {
+                int k = idx_at(Pl, q);
+                for (int c = 0; c < 3; ++c) {
+                    size_t o = (size_t)c * N + k;
+                    u[o] = wt[o] + ab[o];
+                }
+            }
+            err = or_vjp_acc(N, x1, mass, Pl, n, eps2, u, 1.0, 1.0, X, gm);
+        }
+        if (err == OR_OK) err = or_vjp_grad(N, x1, mass, a1, Pl, n, eps2, wt, cg, X, gm);
+    }
+    if (err == OR_OK) {
+        /* x1 = x0 + h/2 v1 */
+        for (int q = 0; q < n; ++q) {
+            int k = idx_at(Pl, q);
+            for (int c = 0; c < 3; ++c) V[(size_t)c * N + k] += 0.5 * h * X[(size_t)c * N + k];
+        }
+        /* v1 = v0 + h/6 a(x0) */
+        err = or_vjp_acc(N, pos0, mass, Pl, n, eps2, V, h / 6.0, h / 6.0, X, gm);
+    }
+    if (err == OR_OK) {
+        memcpy(gx_in, X, N3 * sizeof(double));
+        memcpy(gv_in, V, N3 * sizeof(double));
+    }
+    free(x1); free(x2); free(v1); free(v2); free(a0); free(a1); free(g1); free(tmp);
+    free(X); free(V); free(wt); free(ab); free(u);
+    return err;
+}
