@@ -161,6 +161,25 @@ int fsi_step(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
              const unsigned char *is_bh, const int *idx, int n, double h, int nsteps,
              void *stream);
 
+/* Adjoint of one fsi_step cycle (PN off): given the input state (pos0, vel0; 3 x N) of
+ * a cycle of step h on the set idx (n ids, NULL = all) and the cotangents gx_out, gv_out
+ * (3 x N) of its output state, writes the cotangents of the input state into gx_in,
+ * gv_in (3 x N; entries outside the set are copied from gx_out / gv_out) and ADDS the
+ * mass cotangent into gm (N) so that multi-step products can accumulate.  The cycle's
+ * intermediates are recomputed (context precision); the adjoint pair sums run in FP64:
+ *   VJP of a with cotangent u:   rbar_k = sum_j T(d)(m_k u_j - m_j u_k),
+ *                                mbar_k = -sum_j (u_j . d)/s^3,
+ *   VJP of G (a fixed), cotangent w: rbar_k = sum_j Q(d, a_j - a_k)(m_k w_j - m_j w_k),
+ *                                mbar_k = -sum_j w_j . T(d)(a_j - a_k),
+ * with d = r_j - r_k, s^2 = |d|^2 + eps2, T(d) = I/s^3 - 3 d d^T/s^5 and
+ * Q(d, b) = d(T(d) b)/dd, chained backwards through kick h/6, drift h/2, gradient kick
+ * 2h/3 (Sect. 2.1, Eq. fsi-cycle), drift h/2, kick h/6.  gx_in may alias gx_out and
+ * gv_in may alias gv_out.  Returns FSI_ERR_UNSUPPORTED when fsi_params.c > 0. */
+int fsi_step_vjp(fsi_ctx *ctx, int N, const double *pos0, const double *vel0,
+                 const double *mass, const int *idx, int n, double h,
+                 const double *gx_out, const double *gv_out, double *gx_in, double *gv_in,
+                 double *gm, void *stream);
+
 /* Time steps of the set P against itself (Sect. 3.4): min of the free-fall
  * eta_ff min_j (r^3/(m_i+m_j))^{1/2}, fly-by eta_fb min_j r/|v_ij| and jerk
  * eta_jerk |a_i|/|j_i| criteria (eta's and eps2 from fsi_params).  step_out: n. */

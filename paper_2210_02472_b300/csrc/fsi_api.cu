@@ -65,6 +65,7 @@ struct fsi_ctx {
     Buf rec[2], accrec[2], xc, vc, ac, ad, gA, gB, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
         nbh, apn, pnpart, epart, iota, steps, step0, counts, accum;
     std::vector<Buf> lvS, lvF;
+    Buf vj[24];                     // adjoint work arrays
     std::vector<long long> level_counts;
     int max_level_used = 0;
     int max_level_hit = 0;
@@ -500,6 +501,7 @@ int fsi_destroy(fsi_ctx* c) {
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
     for (auto e : c->ev_pool) cudaEventDestroy(e);
+    for (auto& b : c->vj) if (b.p) cudaFree(b.p);
     for (auto& b : c->lvS) if (b.p) cudaFree(b.p);
     for (auto& b : c->lvF) if (b.p) cudaFree(b.p);
     if (c->err_d) cudaFree(c->err_d);
@@ -770,6 +772,106 @@ int fsi_level_stats(fsi_ctx* c, long long* counts, int max) {
     const int used = std::min<int>((int)c->level_counts.size(), c->max_level_used + 1);
     for (int k = 0; k < max; ++k) counts[k] = k < (int)c->level_counts.size() ? c->level_counts[k] : 0;
     return used;
+}
+
+int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, const double* mass,
+                 const int* idx, int n, double h, const double* gx_out, const double* gv_out,
+                 double* gx_in, double* gv_in, double* gm, void* stream) {
+    CK(check_common(c, N));
+    if (n < 0 || (!idx && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (!pos0 || !vel0 || !mass || !gx_out || !gv_out || !gx_in || !gv_in || !gm)
+        return fail(FSI_ERR_ARG, "NULL array");
+    if (c->p.c > 0.0) return fail(FSI_ERR_UNSUPPORTED, "the adjoint covers the Newtonian FSI cycle (PN off)");
+    const cudaStream_t s = S(stream);
+    const size_t b3 = 3 * (size_t)N * sizeof(double);
+    if (gx_in != gx_out) CU(cudaMemcpyAsync(gx_in, gx_out, b3, cudaMemcpyDeviceToDevice, s));
+    if (gv_in != gv_out) CU(cudaMemcpyAsync(gv_in, gv_out, b3, cudaMemcpyDeviceToDevice, s));
+    if (n == 0) return FSI_OK;
+    const int prec = c->p.precision;
+    const double eps2 = c->p.eps2;
+    const size_t n3 = 3 * (size_t)n * 8;
+    enum { X0, V0, MC, A0, X1, V1, A1, G1, X2, V2, TMP, XB, VB, WT, AB, U, MB, RPOS, RVEC, RACC, NBUF };
+    for (int k = 0; k < NBUF; ++k) {
+        size_t bytes = (k == MC || k == MB) ? (size_t)n * 8 : (k >= RPOS ? (size_t)n * 32 : n3);
+        CK(ensure(c->vj[k], bytes));
+    }
+    auto B = [&](int k) { return P<double>(c->vj[k]); };
+    const double* x0 = pos0;
+    const double* v0 = vel0;
+    const double* mc = mass;
+    if (idx) {
+        CU(launch_gather3(N, pos0, idx, n, B(X0), s));
+        CU(launch_gather3(N, vel0, idx, n, B(V0), s));
+        CU(launch_gather1(N, mass, idx, n, B(MC), s));
+        x0 = B(X0); v0 = B(V0); mc = B(MC);
+    }
+    CK(ensure(c->rec[0], pad_tile(n) * 32));
+    CK(ensure(c->accrec[0], pad_tile(n) * 32));
+    auto acc_at = [&](const double* x, double* out, void* accrec) -> int {
+        CU(launch_pack(prec, n, x, mc, nullptr, n, c->rec[0].p, nullptr, s));
+        PairArgs a{};
+        a.irec = a.jrec = c->rec[0].p;
+        a.n_i = a.n_j = n;
+        a.check = CHECK_DIAG;
+        a.eps2 = eps2;
+        a.epi.out = out;
+        a.epi.accrec = accrec;
+        a.epi.mc = mc;
+        return run_pair(c, KIND_ACC, a, s);
+    };
+    // ---- forward recompute of the cycle's intermediates (compact, FP64 state)
+    CK(acc_at(x0, B(A0), nullptr));
+    CU(launch_lincomb3(n, v0, B(A0), h / 6.0, B(V1), s));
+    CU(launch_lincomb3(n, x0, B(V1), 0.5 * h, B(X1), s));
+    CK(acc_at(B(X1), B(A1), c->accrec[0].p));
+    {
+        PairArgs a{};
+        a.irec = a.jrec = c->rec[0].p;
+        a.iacc = a.jacc = c->accrec[0].p;
+        a.n_i = a.n_j = n;
+        a.check = CHECK_DIAG;
+        a.eps2 = eps2;
+        a.epi.out = B(G1);
+        CK(run_pair(c, KIND_GRAD, a, s));
+    }
+    CU(launch_lincomb3(n, B(A1), B(G1), h * h / 24.0, B(TMP), s));
+    CU(launch_lincomb3(n, B(V1), B(TMP), 2.0 * h / 3.0, B(V2), s));
+    CU(launch_lincomb3(n, B(X1), B(V2), 0.5 * h, B(X2), s));
+    // ---- reverse (FP64 adjoint kernels on FP64 records)
+    CU(launch_gather3(N, gx_out, idx, n, B(XB), s));
+    CU(launch_gather3(N, gv_out, idx, n, B(VB), s));
+    CU(cudaMemsetAsync(B(MB), 0, (size_t)n * 8, s));
+    void* rpos = c->vj[RPOS].p;
+    void* rvec = c->vj[RVEC].p;
+    void* racc = c->vj[RACC].p;
+    auto vjp = [&](int kind, const double* x, const double* vec, double sx, double sm, double* xb,
+                   double* mb) -> int {
+        CU(launch_pack(FSI_FP64, n, x, mc, nullptr, n, rpos, nullptr, s));
+        CU(launch_pack_acc(FSI_FP64, n, vec, mc, nullptr, n, rvec, nullptr, s));
+        CU(launch_vjp_pair(kind, n, rpos, rvec, racc, eps2, sx, sm, xb, mb, c->err_d, c->sm_count, s));
+        return FSI_OK;
+    };
+    // v3 = v2 + h/6 a(x2)
+    CK(vjp(0, B(X2), B(VB), h / 6.0, h / 6.0, B(XB), B(MB)));
+    // x2 = x1 + h/2 v2
+    CU(launch_lincomb3(n, B(VB), B(XB), 0.5 * h, B(VB), s));
+    // v2 = v1 + 2h/3 (a(x1) + h^2/24 G(x1)): cotangent on the gradient acceleration
+    const double cg = h * h / 24.0;
+    CU(launch_lincomb3(n, nullptr, B(VB), 2.0 * h / 3.0, B(WT), s));
+    CU(cudaMemsetAsync(B(AB), 0, n3, s));
+    CK(vjp(0, B(X1), B(WT), cg, 0.0, B(AB), nullptr));               // abar = cg (dG/da)^T w
+    CU(launch_lincomb3(n, B(WT), B(AB), 1.0, B(U), s));               // u = w + abar
+    CK(vjp(0, B(X1), B(U), 1.0, 1.0, B(XB), B(MB)));
+    CU(launch_pack_acc(FSI_FP64, n, B(A1), mc, nullptr, n, racc, nullptr, s));
+    CK(vjp(1, B(X1), B(WT), cg, cg, B(XB), B(MB)));
+    // x1 = x0 + h/2 v1
+    CU(launch_lincomb3(n, B(VB), B(XB), 0.5 * h, B(VB), s));
+    // v1 = v0 + h/6 a(x0)
+    CK(vjp(0, x0, B(VB), h / 6.0, h / 6.0, B(XB), B(MB)));
+    CU(launch_scatter3(N, B(XB), idx, n, gx_in, s));
+    CU(launch_scatter3(N, B(VB), idx, n, gv_in, s));
+    CU(launch_scatter_add1(n, B(MB), idx, gm, s));
+    return FSI_OK;
 }
 
 int fsi_profile(fsi_ctx* c, int enable) {

@@ -214,4 +214,14 @@ cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step
 cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,
                              int* S, int* F, int* counts, cudaStream_t s);
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s);
+// Adjoint pair kernels (FP64): kind 0 = acceleration VJP (vec = cotangent u),
+// kind 1 = gradient-sum VJP through r and m (vec = cotangent w, acc = accelerations).
+// Adds sx * xbar-part into xbar (3 x n) and sm * mbar-part into mbar (n).
+cudaError_t launch_vjp_pair(int kind, int n, const void* rec, const void* vec, const void* acc,
+                            double eps2, double sx, double sm, double* xbar, double* mbar,
+                            int* err, int sm_count, cudaStream_t s);
+cudaError_t launch_lincomb3(int n, const double* a, const double* b, double c, double* out,
+                            cudaStream_t s);
+cudaError_t launch_scatter_add1(int n, const double* src, const int* idx, double* dst,
+                                cudaStream_t s);
 }  // namespace fsi

@@ -38,7 +38,8 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_last_error", "fsi_sync_status", "fsi_accel", "fsi_grad", "fsi_accel_grad",
             "fsi_pn_accel", "fsi_step", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
             "fsi_level_stats", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
-            "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning"]
+            "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
+            "fsi_step_vjp"]
 
 
 class fsi_params(C.Structure):
@@ -73,6 +74,7 @@ _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
 _lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
 _lib.fsi_set_tuning.argtypes = [_vp, _ip, _ip]
+_lib.fsi_step_vjp.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _vp, _vp, _vp, _vp, _vp, _vp]
 
 
 class FsiError(RuntimeError):
@@ -313,3 +315,20 @@ def fsi_get_tuning(ctx: Context):
 
 def fsi_set_tuning(ctx: Context, ipt_acc: int, ipt_grad: int) -> None:
     _check(_lib.fsi_set_tuning(ctx.handle, int(ipt_acc), int(ipt_grad)), "fsi_set_tuning")
+
+
+def fsi_step_vjp(ctx: Context, pos0, vel0, mass, h: float, gx_out, gv_out, idx=None, gm=None,
+                 stream=None):
+    """Cotangents (gx_in, gv_in, gm) of one FSI cycle's input state; gm accumulates."""
+    N = mass.numel()
+    pi, n = _ids(idx, N, "idx")
+    gx_in = torch.empty_like(gx_out)
+    gv_in = torch.empty_like(gv_out)
+    if gm is None:
+        gm = torch.zeros_like(mass)
+    _check(_lib.fsi_step_vjp(ctx.handle, N, _f64(pos0, (3, N), "pos0"), _f64(vel0, (3, N), "vel0"),
+                             _f64(mass, (N,), "mass"), pi, n, float(h),
+                             _f64(gx_out, (3, N), "gx_out"), _f64(gv_out, (3, N), "gv_out"),
+                             _f64(gx_in, (3, N), "gx_in"), _f64(gv_in, (3, N), "gv_in"),
+                             _f64(gm, (N,), "gm"), _stream(stream)), "fsi_step_vjp")
+    return gx_in, gv_in, gm
