@@ -200,6 +200,39 @@ int fsi_energy(fsi_ctx *ctx, int N, const double *pos, const double *vel,
 int fsi_hhs_interval(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
                      const unsigned char *is_bh, double tau, void *stream);
 
+/* ---- batched ensembles ---------------------------------------------------------- */
+typedef struct fsi_batch fsi_batch;
+
+/* Plan the FSI cycles of K independent clusters whose particles are concatenated in one
+ * SoA set: cluster k is [offsets[k], offsets[k+1]) (offsets: host array of K+1 values,
+ * offsets[0] = 0, non-decreasing).  The plan holds the work-item tables (clusters by
+ * decreasing size) and the records of the concatenated set, sized for up to max_steps
+ * cycles per fsi_batch_step (0 = 16).  Synchronous; allocates. */
+int fsi_batch_create(fsi_ctx *ctx, int K, const long long *offsets, int max_steps,
+                     fsi_batch **batch);
+int fsi_batch_destroy(fsi_batch *batch);
+
+/* nsteps FSI cycles of step h (Sect. 2.1, Eq. fsi-cycle) of every cluster on itself, in
+ * place on pos/vel (3 x Ntot, Ntot = offsets[K]), mass (Ntot), in ONE persistent kernel
+ * launch: work items (phase, cluster, block of active particles) are handed out by an
+ * atomic counter and each waits (bounded, fsi_params.timeout_ns) for its cluster's
+ * previous phase.  Consecutive cycles share the closing/opening acceleration pass.
+ * Asynchronous, allocation-free and capturable in a CUDA graph.  Newtonian only
+ * (FSI_ERR_UNSUPPORTED when fsi_params.c > 0); eps2 from fsi_params. */
+int fsi_batch_step(fsi_ctx *ctx, fsi_batch *batch, double *pos, double *vel,
+                   const double *mass, double h, int nsteps, void *stream);
+
+/* Tuning of the batched kernel: active particles per thread (1 or 2) and resident CTAs
+ * per SM (0 = occupancy maximum). */
+int fsi_batch_set_tuning(fsi_ctx *ctx, fsi_batch *batch, int ipt, int ctas_per_sm);
+int fsi_batch_get_tuning(fsi_batch *batch, int *ipt, int *ctas_per_sm);
+
+/* Test hook: during the next fsi_batch_step the items of `cluster` wait for a phase
+ * count that is never reached, so their bounded waits run out and the launch ends with
+ * FSI_ERR_TIMEOUT latched (read by fsi_sync_status) instead of hanging.  The next step
+ * after that runs normally.  That call synchronises the stream. */
+int fsi_batch_inject_stall(fsi_batch *batch, int cluster);
+
 /* Per-level slow-set sizes summed over the visits of the last fsi_hhs_interval.
  * counts: host array of `max` entries.  Returns the number of levels used. */
 int fsi_level_stats(fsi_ctx *ctx, long long *counts, int max);

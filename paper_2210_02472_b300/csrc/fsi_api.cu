@@ -3,6 +3,7 @@
 // The host code only gathers index lists into compact device records, schedules the
 // pair passes and their fused epilogues, and walks the HHS hierarchy; every arithmetic
 // step runs in the kernels of pair_kernels.cu and aux_kernels.cu.
+#include <algorithm>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -447,6 +448,21 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
 
 }  // namespace
 
+// A batch plan: per-variant work-item tables and the records of the concatenated set.
+struct fsi_batch {
+    int K = 0;
+    long long ntot = 0;
+    int max_steps = 0;
+    int ipt = 1;
+    int ctas_per_sm = 2;
+    int stall_cluster = -1;          // test hook (fsi_batch_inject_stall)
+    std::vector<int> nblocks_h[3];   // per ipt (index 1, 2)
+    Buf items[3], nblocks[3];
+    int items_per_phase[3] = {0, 0, 0};
+    Buf rec0, rec1, accrec, ac, done, ctrl;
+    std::vector<long long> off;
+};
+
 // =================================================================================
 extern "C" {
 
@@ -871,6 +887,146 @@ int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, cons
     CU(launch_scatter3(N, B(XB), idx, n, gx_in, s));
     CU(launch_scatter3(N, B(VB), idx, n, gv_in, s));
     CU(launch_scatter_add1(n, B(MB), idx, gm, s));
+    return FSI_OK;
+}
+
+int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps, fsi_batch** out) {
+    if (!c || !offsets || !out || K <= 0) return fail(FSI_ERR_ARG, "bad batch arguments");
+    *out = nullptr;
+    if (offsets[0] != 0) return fail(FSI_ERR_ARG, "offsets[0] must be 0");
+    for (int k = 0; k < K; ++k)
+        if (offsets[k + 1] < offsets[k]) return fail(FSI_ERR_ARG, "offsets must be non-decreasing");
+    const long long ntot = offsets[K];
+    if (ntot <= 0 || ntot > 2000000000LL) return fail(FSI_ERR_ARG, "bad total size %lld", ntot);
+    if (max_steps <= 0) max_steps = 16;
+    fsi_batch* b = new fsi_batch();
+    b->K = K;
+    b->ntot = ntot;
+    b->max_steps = max_steps;
+    b->off.assign(offsets, offsets + K + 1);
+    // clusters by decreasing size: the largest work first within every phase
+    std::vector<int> order(K);
+    for (int k = 0; k < K; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
+    });
+    int rc = FSI_OK;
+    for (int ipt = 1; ipt <= 2 && rc == FSI_OK; ++ipt) {
+        const int bs = batch_block_size(ipt);
+        std::vector<BatchItem> items;
+        b->nblocks_h[ipt].assign(K, 0);
+        for (int k : order) {
+            const int n = (int)(offsets[k + 1] - offsets[k]);
+            const int nb = (n + bs - 1) / bs;
+            b->nblocks_h[ipt][k] = nb;
+            for (int q = 0; q < nb; ++q) items.push_back(BatchItem{k, q, (int)offsets[k], n});
+        }
+        b->items_per_phase[ipt] = (int)items.size();
+        rc = ensure(b->items[ipt], items.size() * sizeof(BatchItem));
+        if (rc == FSI_OK) rc = ensure(b->nblocks[ipt], (size_t)K * sizeof(int));
+        if (rc == FSI_OK &&
+            (cudaMemcpy(b->items[ipt].p, items.data(), items.size() * sizeof(BatchItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(b->nblocks[ipt].p, b->nblocks_h[ipt].data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+            rc = fail(FSI_ERR_CUDA, "batch plan upload failed");
+    }
+    const int nphase = 2 + 3 * max_steps;
+    if (rc == FSI_OK) rc = ensure(b->rec0, (size_t)ntot * 32);
+    if (rc == FSI_OK) rc = ensure(b->rec1, (size_t)ntot * 32);
+    if (rc == FSI_OK) rc = ensure(b->accrec, (size_t)ntot * 32);
+    if (rc == FSI_OK) rc = ensure(b->ac, 3 * (size_t)ntot * 8);
+    if (rc == FSI_OK) rc = ensure(b->done, (size_t)K * nphase * sizeof(int));
+    if (rc == FSI_OK) rc = ensure(b->ctrl, 64);
+    if (rc == FSI_OK) {
+        b->ctas_per_sm = std::max(1, batch_max_ctas_per_sm(c->p.precision, b->ipt));
+        *out = b;
+        return FSI_OK;
+    }
+    fsi_batch_destroy(b);
+    return rc;
+}
+
+int fsi_batch_destroy(fsi_batch* b) {
+    if (!b) return FSI_OK;
+    cudaDeviceSynchronize();
+    Buf* bufs[] = {&b->items[1], &b->items[2], &b->nblocks[1], &b->nblocks[2], &b->rec0, &b->rec1,
+                   &b->accrec, &b->ac, &b->done, &b->ctrl};
+    for (Buf* x : bufs)
+        if (x->p) cudaFree(x->p);
+    delete b;
+    return FSI_OK;
+}
+
+int fsi_batch_set_tuning(fsi_ctx* c, fsi_batch* b, int ipt, int ctas_per_sm) {
+    if (!c || !b) return fail(FSI_ERR_ARG, "NULL argument");
+    if (ipt < 1 || ipt > 2) return fail(FSI_ERR_ARG, "batch particles-per-thread must be 1 or 2");
+    const int mx = std::max(1, batch_max_ctas_per_sm(c->p.precision, ipt));
+    if (ctas_per_sm <= 0 || ctas_per_sm > mx) ctas_per_sm = mx;
+    b->ipt = ipt;
+    b->ctas_per_sm = ctas_per_sm;
+    return FSI_OK;
+}
+
+int fsi_batch_get_tuning(fsi_batch* b, int* ipt, int* ctas_per_sm) {
+    if (!b) return fail(FSI_ERR_ARG, "NULL batch");
+    if (ipt) *ipt = b->ipt;
+    if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    return FSI_OK;
+}
+
+int fsi_batch_inject_stall(fsi_batch* b, int cluster) {
+    if (!b || cluster < 0 || cluster >= b->K) return fail(FSI_ERR_ARG, "bad cluster");
+    b->stall_cluster = cluster;
+    return FSI_OK;
+}
+
+int fsi_batch_step(fsi_ctx* c, fsi_batch* b, double* pos, double* vel, const double* mass,
+                   double h, int nsteps, void* stream) {
+    if (!c || !b) return fail(FSI_ERR_ARG, "NULL argument");
+    if (!pos || !vel || !mass) return fail(FSI_ERR_ARG, "NULL array");
+    if (nsteps <= 0) return FSI_OK;
+    if (nsteps > b->max_steps) return fail(FSI_ERR_ARG, "nsteps %d exceeds the plan's max_steps %d", nsteps, b->max_steps);
+    if (c->p.c > 0.0) return fail(FSI_ERR_UNSUPPORTED, "batched steps are Newtonian (PN off)");
+    const cudaStream_t s = S(stream);
+    const int nphase = 2 + 3 * nsteps;
+    const int ipt = b->ipt;
+    CU(cudaMemsetAsync(b->done.p, 0, (size_t)b->K * nphase * sizeof(int), s));
+    CU(cudaMemsetAsync(b->ctrl.p, 0, 64, s));
+    int* nblocks = P<int>(b->nblocks[ipt]);
+    if (b->stall_cluster >= 0) {
+        // test hook: one cluster waits for a phase count that is never reached
+        const int k = b->stall_cluster;
+        const int bumped = b->nblocks_h[ipt][k] + 1;
+        CU(cudaMemcpy(nblocks + k, &bumped, sizeof(int), cudaMemcpyHostToDevice));
+    }
+    BatchArgs a{};
+    a.items = reinterpret_cast<const BatchItem*>(b->items[ipt].p);
+    a.items_per_phase = b->items_per_phase[ipt];
+    a.nphase = nphase;
+    a.nsteps = nsteps;
+    a.nblocks = nblocks;
+    a.x = pos;
+    a.v = vel;
+    a.m = mass;
+    a.ntot = b->ntot;
+    a.rec0 = b->rec0.p;
+    a.rec1 = b->rec1.p;
+    a.accrec = b->accrec.p;
+    a.ac = P<double>(b->ac);
+    a.done = P<int>(b->done);
+    a.next = P<int>(b->ctrl);
+    a.abort_flag = P<int>(b->ctrl) + 4;
+    a.h = h;
+    a.eps2 = c->p.eps2;
+    a.err = c->err_d;
+    a.timeout_ns = budget(c);
+    const int ctas = c->sm_count * b->ctas_per_sm;
+    CU(launch_batch(c->p.precision, ipt, ctas, a, s));
+    if (b->stall_cluster >= 0) {
+        const int k = b->stall_cluster;
+        CU(cudaMemcpyAsync(nblocks + k, &b->nblocks_h[ipt][k], sizeof(int), cudaMemcpyHostToDevice, s));
+        CU(cudaStreamSynchronize(s));
+        b->stall_cluster = -1;
+    }
     return FSI_OK;
 }
 

@@ -151,6 +151,35 @@ __device__ __forceinline__ float rsqrt_hw(float x) {
 }  // namespace fsi
 
 // ---------------------------------------------------------------------------------
+// Batched ensemble (batch_kernels.cu): one work item = (cluster, i-block) of one phase.
+struct BatchItem {
+    int cluster, block, off, n;
+};
+
+struct BatchArgs {
+    const BatchItem* items;      // items_per_phase entries
+    int items_per_phase;
+    int nphase;
+    int nsteps;
+    const int* nblocks;          // per cluster (index = cluster id)
+    double* x;                   // 3 x Ntot
+    double* v;
+    const double* m;             // Ntot
+    long long ntot;
+    void* rec0;
+    void* rec1;
+    void* accrec;
+    double* ac;                  // 3 x Ntot, FP64 accelerations of the gradient pass
+    int* done;                   // K x nphase, zeroed before the launch
+    int* next;                   // work counter, zeroed
+    int* abort_flag;             // zeroed
+    double h, eps2;
+    int* err;
+    long long timeout_ns;
+};
+
+
+// ---------------------------------------------------------------------------------
 // Host-side launchers (defined in pair_kernels.cu / aux_kernels.cu).
 namespace fsi {
 void note_launch();                 // counts every kernel launch (fsi_launch_count)
@@ -214,6 +243,9 @@ cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step
 cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,
                              int* S, int* F, int* counts, cudaStream_t s);
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s);
+cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, cudaStream_t s);
+int batch_block_size(int ipt);
+int batch_max_ctas_per_sm(int precision, int ipt);
 // Adjoint pair kernels (FP64): kind 0 = acceleration VJP (vec = cotangent u),
 // kind 1 = gradient-sum VJP through r and m (vec = cotangent w, acc = accelerations).
 // Adds sx * xbar-part into xbar (3 x n) and sm * mbar-part into mbar (n).

@@ -32,102 +32,9 @@
 #include <type_traits>
 
 #include "fsi_internal.cuh"
+#include "pair_math.cuh"
 
 namespace fsi {
-
-// ---------------------------------------------------------------------------------
-// Per-pair arithmetic.
-struct MixI {
-    float xh, yh, zh, xl, yl, zl;
-    float ax, ay, az;
-};
-
-template <bool CHK>
-__device__ __forceinline__ void mix_acc_pair(const float4 h, const float4 l, const MixI& p,
-                                             float eps2f, bool self,
-                                             float& fx, float& fy, float& fz) {
-    const float dx = (h.x - p.xh) + (l.x - p.xl);
-    const float dy = (h.y - p.yh) + (l.y - p.yl);
-    const float dz = (h.z - p.zh) + (l.z - p.zl);
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2f)));
-    if (CHK) r2 = self ? 1.0f : r2;
-    const float y = rsqrt_hw(r2);
-    const float y2 = y * y;
-    const float sres = r2 * y2;                      // 1 - e, e = rsqrt residual
-    // m r^-3 = m y^3 (1 - e)^{-3/2} ~ y^3 (2.5 m - 1.5 m (1 - e)); h.w = 2.5 m, l.w = -1.5 m
-    const float w = (y2 * y) * fmaf(sres, l.w, h.w);
-    fx = fmaf(w, dx, fx);
-    fy = fmaf(w, dy, fy);
-    fz = fmaf(w, dz, fz);
-}
-
-template <bool CHK>
-__device__ __forceinline__ void mix_grad_pair(const float4 h, const float4 l, const float4 aj,
-                                              const MixI& p, float eps2f, bool self,
-                                              float& gx, float& gy, float& gz) {
-    const float dx = (h.x - p.xh) + (l.x - p.xl);
-    const float dy = (h.y - p.yh) + (l.y - p.yl);
-    const float dz = (h.z - p.zh) + (l.z - p.zl);
-    float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2f)));
-    if (CHK) r2 = self ? 1.0f : r2;
-    const float y = rsqrt_hw(r2);
-    const float y2 = y * y;
-    const float sres = r2 * y2;                      // 1 - e
-    const float w = (y2 * y) * fmaf(sres, l.w, h.w); // m r^-3
-    const float bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;   // a_ji
-    const float dot = fmaf(bx, dx, fmaf(by, dy, bz * dz));
-    // -3 m r^-5 = -3 w y^2 (1 + e) = w y^2 (3 (1 - e) - 6)
-    const float q = (w * y2) * fmaf(3.0f, sres, -6.0f);
-    const float s = q * dot;
-    gx = fmaf(w, bx, fmaf(s, dx, gx));
-    gy = fmaf(w, by, fmaf(s, dy, gy));
-    gz = fmaf(w, bz, fmaf(s, dz, gz));
-}
-
-__device__ __forceinline__ double rsqrt_f64(double r2) {
-    const double y0 = (double)rsqrt_hw(__double2float_rn(r2));
-    const double t = r2 * y0;
-    const double e = fma(-t, y0, 1.0);
-    const double p = fma(0.375, e, 0.5);
-    return fma(y0 * e, p, y0);
-}
-
-struct F64I {
-    double x, y, z;
-    double ax, ay, az;
-};
-
-template <bool CHK>
-__device__ __forceinline__ void f64_acc_pair(const D4 j, const F64I& p, double eps2,
-                                             bool self, double& fx, double& fy, double& fz) {
-    const double dx = j.x - p.x, dy = j.y - p.y, dz = j.z - p.z;
-    double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-    if (CHK) r2 = self ? 1.0 : r2;
-    const double y = rsqrt_f64(r2);
-    const double y2 = y * y;
-    const double w = j.w * (y2 * y);
-    fx = fma(w, dx, fx);
-    fy = fma(w, dy, fy);
-    fz = fma(w, dz, fz);
-}
-
-template <bool CHK>
-__device__ __forceinline__ void f64_grad_pair(const D4 j, const D4 aj, const F64I& p,
-                                              double eps2, bool self,
-                                              double& gx, double& gy, double& gz) {
-    const double dx = j.x - p.x, dy = j.y - p.y, dz = j.z - p.z;
-    double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
-    if (CHK) r2 = self ? 1.0 : r2;
-    const double y = rsqrt_f64(r2);
-    const double y2 = y * y;
-    const double w = j.w * (y2 * y);
-    const double bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;
-    const double dot = fma(bx, dx, fma(by, dy, bz * dz));
-    const double s = (w * y2) * (-3.0 * dot);
-    gx = fma(w, bx, fma(s, dx, gx));
-    gy = fma(w, by, fma(s, dy, gy));
-    gz = fma(w, bz, fma(s, dz, gz));
-}
 
 // Mass carried by a position record (mixed records hold 2.5 m in FP32).
 template <int P>

@@ -39,7 +39,8 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_pn_accel", "fsi_step", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
             "fsi_level_stats", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
-            "fsi_step_vjp"]
+            "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
+            "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall"]
 
 
 class fsi_params(C.Structure):
@@ -74,6 +75,12 @@ _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
 _lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
 _lib.fsi_set_tuning.argtypes = [_vp, _ip, _ip]
+_lib.fsi_batch_create.argtypes = [_vp, _ip, C.POINTER(C.c_longlong), _ip, C.POINTER(_vp)]
+_lib.fsi_batch_destroy.argtypes = [_vp]
+_lib.fsi_batch_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _dp, _ip, _vp]
+_lib.fsi_batch_set_tuning.argtypes = [_vp, _vp, _ip, _ip]
+_lib.fsi_batch_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
+_lib.fsi_batch_inject_stall.argtypes = [_vp, _ip]
 _lib.fsi_step_vjp.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _vp, _vp, _vp, _vp, _vp, _vp]
 
 
@@ -332,3 +339,59 @@ def fsi_step_vjp(ctx: Context, pos0, vel0, mass, h: float, gx_out, gv_out, idx=N
                              _f64(gx_in, (3, N), "gx_in"), _f64(gv_in, (3, N), "gv_in"),
                              _f64(gm, (N,), "gm"), _stream(stream)), "fsi_step_vjp")
     return gx_in, gv_in, gm
+
+
+class Batch:
+    """A plan for FSI cycles of K independent clusters concatenated in one SoA set."""
+
+    def __init__(self, ctx: Context, offsets, max_steps: int = 16):
+        import numpy as _np
+        off = _np.ascontiguousarray(_np.asarray(offsets, dtype=_np.int64))
+        self.K = int(off.shape[0] - 1)
+        self.ntot = int(off[-1])
+        h = _vp()
+        _check(_lib.fsi_batch_create(ctx.handle, self.K, off.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                     int(max_steps), C.byref(h)), "fsi_batch_create")
+        self.handle = h
+
+    def close(self):
+        if getattr(self, "handle", None):
+            _lib.fsi_batch_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def fsi_batch_create(ctx: Context, offsets, max_steps: int = 16) -> Batch:
+    return Batch(ctx, offsets, max_steps)
+
+
+def fsi_batch_destroy(batch: Batch) -> None:
+    batch.close()
+
+
+def fsi_batch_step(ctx: Context, batch: Batch, pos, vel, mass, h: float, nsteps: int = 1,
+                   stream=None) -> None:
+    N = batch.ntot
+    _check(_lib.fsi_batch_step(ctx.handle, batch.handle, _f64(pos, (3, N), "pos"),
+                               _f64(vel, (3, N), "vel"), _f64(mass, (N,), "mass"), float(h),
+                               int(nsteps), _stream(stream)), "fsi_batch_step")
+
+
+def fsi_batch_set_tuning(ctx: Context, batch: Batch, ipt: int, ctas_per_sm: int = 0) -> None:
+    _check(_lib.fsi_batch_set_tuning(ctx.handle, batch.handle, int(ipt), int(ctas_per_sm)),
+           "fsi_batch_set_tuning")
+
+
+def fsi_batch_get_tuning(batch: Batch):
+    a, b = _ip(), _ip()
+    _check(_lib.fsi_batch_get_tuning(batch.handle, C.byref(a), C.byref(b)), "fsi_batch_get_tuning")
+    return int(a.value), int(b.value)
+
+
+def fsi_batch_inject_stall(batch: Batch, cluster: int) -> None:
+    _check(_lib.fsi_batch_inject_stall(batch.handle, int(cluster)), "fsi_batch_inject_stall")

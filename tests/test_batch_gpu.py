@@ -1,0 +1,96 @@
+"""Batched ensembles (fsi_batch_step, one persistent launch) against the oracle stepping
+each cluster on its own; CUDA-graph capture; the bounded-wait timeout path."""
+import os
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_2210_02472_b300 import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def F():
+    oracle.set_threads(os.cpu_count() or 1)
+    from paper_2210_02472_b300 import fsi
+    return fsi
+
+
+def dev(a, dtype=torch.float64):
+    return torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtype)
+
+
+@pytest.fixture(scope="module")
+def ens():
+    # 24 clusters, N log-uniform in [64, 2048], Kroupa IMF, each in its own Henon units
+    return inputs.ensemble(24, 64, 2048, 77)
+
+
+@pytest.mark.parametrize("prec", ["fp64", "mixed"])
+@pytest.mark.parametrize("ipt", [1, 2])
+def test_batch_matches_oracle_per_cluster(F, ens, prec, ipt):
+    cat, off = ens
+    h, steps = 1e-3, 3
+    rp, rv = cat.pos.copy(), cat.vel.copy()
+    for k in range(len(off) - 1):
+        P = np.arange(off[k], off[k + 1], dtype=np.int32)
+        rp, rv = oracle.fsi_step(rp, rv, cat.mass, h, P=P, steps=steps)
+    with F.Context(prec) as ctx:
+        b = F.Batch(ctx, off, max_steps=4)
+        F.fsi_batch_set_tuning(ctx, b, ipt)
+        p, v = dev(cat.pos), dev(cat.vel)
+        F.fsi_batch_step(ctx, b, p, v, dev(cat.mass), h, steps)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        p, v = p.cpu().numpy(), v.cpu().numpy()
+        b.close()
+    tol = 1e-12 if prec == "fp64" else 1e-9
+    assert np.abs(p - rp).max() <= tol * np.abs(rp).max()
+    assert np.abs(v - rv).max() <= tol * 100 * np.abs(rv).max()
+
+
+def test_batch_graph_capture_replays(F, ens):
+    cat, off = ens
+    h = 1e-3
+    with F.Context("mixed") as ctx:
+        b = F.Batch(ctx, off, max_steps=2)
+        m = dev(cat.mass)
+        p0, v0 = dev(cat.pos), dev(cat.vel)
+        pe, ve = p0.clone(), v0.clone()
+        for _ in range(3):
+            F.fsi_batch_step(ctx, b, pe, ve, m, h, 2)
+        pg, vg = p0.clone(), v0.clone()
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, stream=s):
+            F.fsi_batch_step(ctx, b, pg, vg, m, h, 2, stream=s)
+        for _ in range(3):
+            g.replay()
+        torch.cuda.synchronize()
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        assert torch.allclose(pg, pe, rtol=0, atol=1e-12)
+        assert torch.allclose(vg, ve, rtol=0, atol=1e-10)
+        b.close()
+
+
+def test_batch_bounded_wait_times_out_cleanly(F, ens):
+    """A cluster made to wait for a phase count that never comes: the launch returns with
+    FSI_ERR_TIMEOUT latched, the context stays usable and the next step runs normally."""
+    cat, off = ens
+    with F.Context("mixed", timeout_ns=200_000_000) as ctx:
+        b = F.Batch(ctx, off, max_steps=2)
+        p, v, m = dev(cat.pos), dev(cat.vel), dev(cat.mass)
+        F.fsi_batch_inject_stall(b, 3)
+        F.fsi_batch_step(ctx, b, p, v, m, 1e-3, 1)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_TIMEOUT
+        p, v = dev(cat.pos), dev(cat.vel)
+        F.fsi_batch_step(ctx, b, p, v, m, 1e-3, 1)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        rp, rv = oracle.fsi_step(cat.pos, cat.vel, cat.mass, 1e-3,
+                                 P=np.arange(off[3], off[4], dtype=np.int32))
+        sl = slice(off[3], off[4])
+        assert np.abs(p.cpu().numpy()[:, sl] - rp[:, sl]).max() < 1e-9
+        b.close()
