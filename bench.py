@@ -322,6 +322,193 @@ def run_fsi(args):
     return 0
 
 
+def _timed_events(stream):
+    import torch
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def run_ensemble(args):
+    """512 independent clusters, N log-uniform in [64, 8192], Kroupa IMF, mixed precision:
+    one persistent launch of `--batch-steps` FSI cycles per call, replayed from a CUDA graph."""
+    import torch
+    from paper_2210_02472_b300 import fsi as F
+    torch.cuda.set_device(0)
+    cat, off = inputs.ensemble(512, 64, 8192, inputs.SEED_BASE + 5)
+    sizes = np.diff(off).astype(np.float64)
+    pairs = float((sizes * (sizes - 1)).sum())
+    S = args.batch_steps
+    per_call = pairs * ((1 + 2 * S) * FLOP_ACC + S * FLOP_GRAD) / FLOP_PAIR
+    dev = torch.device("cuda", 0)
+    m = torch.as_tensor(cat.mass).to(dev)
+    ctx = F.Context(args.precision)
+    b = F.Batch(ctx, off, max_steps=S)
+    # autotune: particles per thread x resident CTAs per SM
+    best = None
+    for ipt in (1, 2):
+        for cps in (1, 2, 0):
+            F.fsi_batch_set_tuning(ctx, b, ipt, cps)
+            p, v = torch.as_tensor(cat.pos).to(dev), torch.as_tensor(cat.vel).to(dev)
+            F.fsi_batch_step(ctx, b, p, v, m, 1e-3, S)
+            e0, e1 = _timed_events(None)
+            e0.record()
+            F.fsi_batch_step(ctx, b, p, v, m, 1e-3, S)
+            e1.record()
+            torch.cuda.synchronize()
+            t = e0.elapsed_time(e1)
+            if best is None or t < best[0]:
+                best = (t, F.fsi_batch_get_tuning(b))
+    F.fsi_batch_set_tuning(ctx, b, *best[1])
+    p, v = torch.as_tensor(cat.pos).to(dev), torch.as_tensor(cat.vel).to(dev)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        F.fsi_batch_step(ctx, b, p, v, m, 1e-3, S, stream=s)
+    for _ in range(args.warmup):
+        g.replay()
+    torch.cuda.synchronize()
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    sampler = ClockSampler(0)
+    sampler.start()
+    n0 = F.fsi_launch_count()
+    ms = []
+    for _ in range(args.steps):
+        flush.zero_()
+        e0, e1 = _timed_events(None)
+        e0.record()
+        g.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        ms.append(e0.elapsed_time(e1))
+    clocks = sampler.stop()
+    assert F.fsi_sync_status(ctx) == F.FSI_OK
+    t = sum(ms) / 1e3
+    value = per_call * args.steps / t
+    ach = value * FLOP_PAIR / 1e12
+    peak = fp32_peak_tflops() if args.precision == "mixed" else args.fp64_peak_tflops
+    line = {
+        "metric": "ensemble acc+grad pair interactions/s (512 clusters, N in [64, 8192])",
+        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "ensemble512", "clusters": 512, "n_total": int(off[-1]),
+                   "pairs_per_pass": pairs, "fsi_cycles_per_launch": S,
+                   "launch": "one persistent kernel per call, replayed from a CUDA graph",
+                   "tuning": {"ipt": best[1][0], "ctas_per_sm": best[1][1]},
+                   "l2": "flushed between launches (256 MB write)"},
+        "gpu_launches": (F.fsi_launch_count() - n0),
+        "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
+                     "frac": ach / peak, "traffic": None, "kernel": "batch_kernel"},
+        "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    b.close()
+    ctx.close()
+    return 0
+
+
+def run_vjp(args):
+    """N = 16384 equal-mass Plummer, FP64, 200 FSI steps of h = 1e-3, L = sum |x|^2;
+    gradient w.r.t. (x0, v0, m) by the checkpointed adjoint (every 20 steps), timed
+    against the forward; central finite differences on a few components."""
+    import math
+    import torch
+    from paper_2210_02472_b300 import fsi as F
+    from paper_2210_02472_b300.autodiff import fsi_rollout
+    torch.cuda.set_device(0)
+    c = inputs.workload("plummer16k")
+    dev = torch.device("cuda", 0)
+    h, steps = 1e-3, args.vjp_steps
+    ctx = F.Context("fp64")
+    x = torch.as_tensor(c.pos).to(dev).requires_grad_(True)
+    v = torch.as_tensor(c.vel).to(dev).requires_grad_(True)
+    m = torch.as_tensor(c.mass).to(dev).requires_grad_(True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    p, _ = fsi_rollout(ctx, x, v, m, h, steps, ckpt_every=20)
+    L = (p * p).sum()
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    L.backward()
+    torch.cuda.synchronize()
+    t2 = time.perf_counter()
+    grads = [x.grad.cpu().numpy(), v.grad.cpu().numpy(), m.grad.cpu().numpy()]
+
+    def final(px, pv, pm):
+        P, V = torch.as_tensor(px).to(dev), torch.as_tensor(pv).to(dev)
+        F.fsi_step(ctx, P, V, torch.as_tensor(pm).to(dev), h, nsteps=steps)
+        return P.cpu().numpy()
+
+    rng = np.random.default_rng(20221009)
+    fd = []
+    for t in range(args.fd_components):
+        which = t % 3
+        k, i = int(rng.integers(3)), int(rng.integers(c.n))
+        arrs = [c.pos.copy(), c.vel.copy(), c.mass.copy()]
+        idx = (i,) if which == 2 else (k, i)
+        step = 1e-4 * arrs[2][i] if which == 2 else 1e-6
+        arrs[which][idx] += step
+        fp = final(*arrs)
+        arrs[which][idx] -= 2 * step
+        fm = final(*arrs)
+        d = math.fsum(((fp * fp) - (fm * fm)).ravel()) / (2 * step)
+        an = float(grads[which][idx])
+        fd.append({"var": "xvm"[which], "index": [int(q) for q in idx], "fd": d, "vjp": an,
+                   "rel_diff": abs(d - an) / max(abs(an), 1e-300)})
+    line = {
+        "metric": "adjoint (VJP) of a 200-step FSI rollout: backward / forward time",
+        "value": (t2 - t1) / (t1 - t0), "unit": "ratio", "n_gpus": 1, "steps": 1, "warmup": 0,
+        "ms_per_step": 1e3 * (t2 - t0), "higher_is_better": False, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": "plummer16k", "n": c.n, "steps": steps, "h": h, "ckpt_every": 20,
+                   "loss": "sum |x_final|^2"},
+        "forward_s": t1 - t0, "backward_s": t2 - t1, "finite_differences": fd,
+        "max_rel_diff": max([q["rel_diff"] for q in fd], default=None),
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
+def run_hhs(args):
+    """N = 65536 Plummer with a Kroupa IMF, eps = 0: HHS intervals of tau0 = 1/64."""
+    import torch
+    from paper_2210_02472_b300 import fsi as F
+    torch.cuda.set_device(0)
+    c = inputs.workload("kroupa64k") if not args.n else inputs.plummer(args.n, inputs.SEED_BASE + 2, imf="kroupa")
+    dev = torch.device("cuda", 0)
+    pos, vel = torch.as_tensor(c.pos).to(dev), torch.as_tensor(c.vel).to(dev)
+    mass = torch.as_tensor(c.mass).to(dev)
+    ctx = F.Context(args.precision)
+    e0 = F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum()
+    F.fsi_work_stats(ctx, reset=True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    levels = []
+    for _ in range(args.intervals):
+        code = F.fsi_hhs_interval(ctx, pos, vel, mass, args.tau)
+        levels.append(F.fsi_level_stats(ctx))
+    torch.cuda.synchronize()
+    t = time.perf_counter() - t0
+    acc_p, grad_p = F.fsi_work_stats(ctx)
+    e1 = F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum()
+    inter = (acc_p * FLOP_ACC + grad_p * FLOP_GRAD) / FLOP_PAIR
+    line = {
+        "metric": "HHS acc+grad pair interactions/s (N = 65536 Kroupa, tau0 = 1/64)",
+        "value": inter / t, "unit": UNIT, "n_gpus": 1, "steps": args.intervals, "warmup": 0,
+        "ms_per_step": 1e3 * t / args.intervals, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": "kroupa64k", "n": c.n, "tau": args.tau, "intervals": args.intervals},
+        "level_counts": levels, "rel_energy_error": abs((e1 - e0) / e0),
+        "acc_pairs": acc_p, "grad_pairs": grad_p, "maxlevel_status": code,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -336,9 +523,23 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=1024)
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mode", default="cycle", choices=["cycle", "ensemble", "vjp", "hhs"],
+                    help="cycle: the headline FSI-cycle benchmark; the others measure the "
+                         "ensemble, adjoint and HHS workloads")
+    ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--vjp-steps", type=int, default=200)
+    ap.add_argument("--fd-components", type=int, default=3)
+    ap.add_argument("--intervals", type=int, default=1)
+    ap.add_argument("--tau", type=float, default=1.0 / 64)
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.mode == "ensemble":
+        return run_ensemble(args)
+    if args.mode == "vjp":
+        return run_vjp(args)
+    if args.mode == "hhs":
+        return run_hhs(args)
     return run_fsi(args)
 
 

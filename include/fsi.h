@@ -267,6 +267,11 @@ int fsi_profile(fsi_ctx *ctx, int enable);
  * milliseconds, then clear the record.  launches: host long long[3], ms: host double[3]. */
 int fsi_profile_read(fsi_ctx *ctx, long long *launches, double *ms);
 
+/* Pair-sum work issued by this context: ordered (receiver, source) pairs of the
+ * acceleration passes and of the gradient passes (a symmetric pass counts both
+ * directions), since creation or the last reset (reset != 0 clears after reading). */
+int fsi_work_stats(fsi_ctx *ctx, long long *acc_pairs, long long *grad_pairs, int reset);
+
 /* Number of kernels this library has launched in this process (all contexts). */
 long long fsi_launch_count(void);
 

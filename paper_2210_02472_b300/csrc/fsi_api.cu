@@ -71,6 +71,7 @@ struct fsi_ctx {
     int max_level_used = 0;
     int max_level_hit = 0;
     int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] pair-kernel variant (see pair_variants)
+    long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
     // instrumentation: event pairs around pair-kernel launches
     struct ProfRec { int kind; cudaEvent_t a, b; };
     bool profiling = false;
@@ -166,6 +167,7 @@ int choose_chunk(const fsi_ctx* c, int n, int ipt) {
 
 int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
     if (a.n_i <= 0) return FSI_OK;
+    c->work_pairs[kind] += (long long)a.n_i * (long long)a.n_j;
     const int prec = c->p.precision;
     const int ipt = c->ipt[prec][kind];
     if (c->p.symmetric && a.check == CHECK_DIAG && a.irec == a.jrec && a.n_i == a.n_j &&
@@ -1052,6 +1054,14 @@ int fsi_profile_read(fsi_ctx* c, long long* launches, double* ms) {
 }
 
 long long fsi_launch_count(void) { return g_launches.load(); }
+
+int fsi_work_stats(fsi_ctx* c, long long* acc_pairs, long long* grad_pairs, int reset) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    if (acc_pairs) *acc_pairs = c->work_pairs[KIND_ACC];
+    if (grad_pairs) *grad_pairs = c->work_pairs[KIND_GRAD];
+    if (reset) c->work_pairs[0] = c->work_pairs[1] = 0;
+    return FSI_OK;
+}
 
 int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n, int reps,
                  void* stream) {

@@ -40,7 +40,8 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_level_stats", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
-            "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall"]
+            "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall",
+            "fsi_work_stats"]
 
 
 class fsi_params(C.Structure):
@@ -71,6 +72,7 @@ _lib.fsi_level_stats.argtypes = [_vp, C.POINTER(C.c_longlong), _ip]
 _lib.fsi_profile.argtypes = [_vp, _ip]
 _lib.fsi_profile_read.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
 _lib.fsi_launch_count.restype = C.c_longlong
+_lib.fsi_work_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip]
 _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
 _lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
@@ -395,3 +397,10 @@ def fsi_batch_get_tuning(batch: Batch):
 
 def fsi_batch_inject_stall(batch: Batch, cluster: int) -> None:
     _check(_lib.fsi_batch_inject_stall(batch.handle, int(cluster)), "fsi_batch_inject_stall")
+
+
+def fsi_work_stats(ctx: Context, reset: bool = False):
+    """(acc_pairs, grad_pairs): ordered pairs evaluated by this context's pair passes."""
+    a, g = C.c_longlong(), C.c_longlong()
+    _check(_lib.fsi_work_stats(ctx.handle, C.byref(a), C.byref(g), int(bool(reset))), "fsi_work_stats")
+    return int(a.value), int(g.value)
