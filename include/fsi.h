@@ -78,6 +78,9 @@ typedef struct fsi_params {
     int symmetric;        /* 1 (default): a set's self-interaction evaluates every unordered
                              pair once and adds it to both particles (Newton's third law);
                              0: every ordered pair is evaluated by its receiving particle */
+    int hhs_small_max;    /* HHS: a fast set of at most this many particles (0 = 512, the
+                             maximum) runs its whole recursion inside one CTA; -1 = always
+                             walk the levels from the host */
 } fsi_params;
 
 /* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,
@@ -182,7 +185,9 @@ int fsi_step_vjp(fsi_ctx *ctx, int N, const double *pos0, const double *vel0,
 
 /* Time steps of the set P against itself (Sect. 3.4): min of the free-fall
  * eta_ff min_j (r^3/(m_i+m_j))^{1/2}, fly-by eta_fb min_j r/|v_ij| and jerk
- * eta_jerk |a_i|/|j_i| criteria (eta's and eps2 from fsi_params).  step_out: n. */
+ * eta_jerk |a_i|/|j_i| criteria (eta's and eps2 from fsi_params).  step_out: n.
+ * FSI_FP64: FP64 throughout.  FSI_MIXED: FP32 pair arithmetic (hi/lo separations,
+ * minima of squared ratios), ~1e-6 relative. */
 int fsi_timesteps(fsi_ctx *ctx, int N, const double *pos, const double *vel,
                   const double *mass, const int *P, int n, double *step_out, void *stream);
 

@@ -496,6 +496,84 @@ __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const dou
     step[i] = e;
 }
 
+// Mixed-precision time steps: the same criteria with FP32 pair arithmetic.  Separations
+// come from FP32 hi/lo splits of the FP64 positions (FP32-accurate relative to the
+// separation); the minima are taken over squared quantities (r^6 / (m_i + m_j)^2 and
+// r^2 / |v_ij|^2) so that no division or square root is needed per pair.
+__global__ void timesteps_mixed_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
+                                       const double* __restrict__ mc, double eta_ff, double eta_fb,
+                                       double eta_jerk, double eps2, double* __restrict__ step, int* err) {
+    __shared__ float4 sh[kAuxTile], sl[kAuxTile], sv[kAuxTile];
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ii = min(i, n - 1);
+    const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
+    const float xh = (float)xi, yh = (float)yi, zh = (float)zi;
+    const float xl = (float)(xi - (double)xh), yl = (float)(yi - (double)yh), zl = (float)(zi - (double)zh);
+    const float ui = (float)vc[ii], vi = (float)vc[(size_t)n + ii], wi = (float)vc[2 * (size_t)n + ii];
+    const float mi = (float)mc[ii];
+    const float eps2f = (float)eps2;
+    float ff6 = INFINITY, fb2 = INFINITY;
+    float ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+    bool coincident = false;
+    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
+        __syncthreads();
+        for (int t = threadIdx.x; t < kAuxTile; t += blockDim.x) {
+            const int j = j0 + t;
+            if (j < n) {
+                const double x = xc[j], y = xc[(size_t)n + j], z = xc[2 * (size_t)n + j];
+                const float h0 = (float)x, h1 = (float)y, h2 = (float)z;
+                sh[t] = make_float4(h0, h1, h2, (float)mc[j]);
+                sl[t] = make_float4((float)(x - (double)h0), (float)(y - (double)h1), (float)(z - (double)h2), 0.f);
+                sv[t] = make_float4((float)vc[j], (float)vc[(size_t)n + j], (float)vc[2 * (size_t)n + j], 0.f);
+            }
+        }
+        __syncthreads();
+        const int cnt = min(kAuxTile, n - j0);
+        for (int t = 0; t < cnt; ++t) {
+            const float4 h = sh[t], l = sl[t], v = sv[t];
+            const float dx = (h.x - xh) + (l.x - xl);
+            const float dy = (h.y - yh) + (l.y - yl);
+            const float dz = (h.z - zh) + (l.z - zl);
+            const float du = v.x - ui, dv = v.y - vi, dw = v.z - wi;
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            const bool self = (j0 + t == ii);
+            if (!self && d2 == 0.f) coincident = true;
+            const float d2s = self ? 1.0f : d2;
+            const float s2 = d2s + eps2f;
+            const float y = rsqrt_hw(s2);
+            const float y2 = y * y;
+            const float w = self ? 0.f : h.w * (y2 * y);                       // m_j / s^3
+            const float ms = mi + h.w;
+            const float q_ff = self ? INFINITY : (d2s * d2s) * d2s * __frcp_rn(ms * ms);
+            const float u2 = fmaf(du, du, fmaf(dv, dv, dw * dw));
+            const float q_fb = (self || u2 == 0.f) ? INFINITY : d2s * __frcp_rn(u2);
+            ff6 = fminf(ff6, q_ff);
+            fb2 = fminf(fb2, q_fb);
+            const float rv = fmaf(dx, du, fmaf(dy, dv, dz * dw));
+            const float c3 = -3.0f * rv * y2;
+            ax = fmaf(w, dx, ax); ay = fmaf(w, dy, ay); az = fmaf(w, dz, az);
+            jx = fmaf(w, fmaf(c3, dx, du), jx);
+            jy = fmaf(w, fmaf(c3, dy, dv), jy);
+            jz = fmaf(w, fmaf(c3, dz, dw), jz);
+        }
+    }
+    if (i >= n) return;
+    if (coincident) set_error(err, FSI_ERR_NONFINITE);
+    double e = fmin(eta_ff * sqrt(sqrt((double)ff6)), eta_fb * sqrt((double)fb2));
+    const double jn = sqrt((double)jx * jx + (double)jy * jy + (double)jz * jz);
+    if (jn > 0.0) e = fmin(e, eta_jerk * sqrt((double)ax * ax + (double)ay * ay + (double)az * az) / jn);
+    step[i] = e;
+}
+
+cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
+                                   double eta_ff, double eta_fb, double eta_jerk, double eps2,
+                                   double* step, int* err, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { timesteps_mixed_kernel<<<blocks_for(n, kAuxTile), kAuxTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb,
+                                                                         eta_jerk, eps2, step, err); note_launch(); }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
                              double eta_ff, double eta_fb, double eta_jerk, double eps2,
                              double* step, int* err, cudaStream_t s) {

@@ -67,6 +67,7 @@ struct fsi_ctx {
         nbh, apn, pnpart, epart, iota, steps, step0, counts, accum;
     std::vector<Buf> lvS, lvF;
     Buf vj[24];                     // adjoint work arrays
+    Buf dstats;                     // device HHS stats: level counts (64), work (2), flags
     std::vector<long long> level_counts;
     int max_level_used = 0;
     int max_level_hit = 0;
@@ -401,8 +402,12 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
         vc = P<double>(c->vc);
         mc = P<double>(c->mc);
     }
-    CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
-                        c->err_d, s));
+    if (c->p.precision == FSI_MIXED)
+        CU(launch_timesteps_mixed(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2,
+                                  step, c->err_d, s));
+    else
+        CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
+                            c->err_d, s));
     return FSI_OK;
 }
 
@@ -436,10 +441,30 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
         if (pn) CK(cross_pn_kick(c, N, pos, vel, mass, is_bh, Sids, nS, Fids, nF, 0.5 * tau, s));
         CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, tau / 6.0, 0, 0.0, s));
     }
+    // HHS(F, tau/2): small fast sets recurse inside one CTA, larger ones level by level here
+    const int small_cap = c->p.hhs_small_max == 0 ? small_max()
+                          : std::min(c->p.hhs_small_max, small_max());
+    auto recurse = [&]() -> int {
+        if (nF <= 0) return FSI_OK;
+        if (nF <= small_cap && !pn) {
+            SmallArgs sa{};
+            sa.ids = Fids; sa.n = nF; sa.pos = pos; sa.vel = vel; sa.mass = mass;
+            sa.step0 = P<double>(c->step0); sa.N = N; sa.tau = 0.5 * tau; sa.level = level + 1;
+            sa.max_level = c->p.max_level; sa.eps2 = c->p.eps2; sa.eta_ff = c->p.eta_ff;
+            sa.eta_fb = c->p.eta_fb; sa.eta_jerk = c->p.eta_jerk;
+            unsigned long long* st = P<unsigned long long>(c->dstats);
+            sa.level_counts = st; sa.work = st + 64;
+            sa.maxlevel_hit = reinterpret_cast<int*>(st + 66);
+            sa.err = c->err_d;
+            CU(launch_hhs_small(c->p.precision, sa, s));
+            return FSI_OK;
+        }
+        return hhs_level(c, N, pos, vel, mass, is_bh, Fids, nF, 0.5 * tau, level + 1, s);
+    };
     if (nS > 0) CK(step_core(c, N, pos, vel, mass, is_bh, Sids, nS, 0.5 * tau, 1, s));
-    if (nF > 0) CK(hhs_level(c, N, pos, vel, mass, is_bh, Fids, nF, 0.5 * tau, level + 1, s));
+    CK(recurse());
     if (cross) CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, 2.0 * tau / 3.0, 1, tau, s));
-    if (nF > 0) CK(hhs_level(c, N, pos, vel, mass, is_bh, Fids, nF, 0.5 * tau, level + 1, s));
+    CK(recurse());
     if (nS > 0) CK(step_core(c, N, pos, vel, mass, is_bh, Sids, nS, 0.5 * tau, 1, s));
     if (cross) {
         CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, tau / 6.0, 0, 0.0, s));
@@ -481,6 +506,7 @@ void fsi_default_params(fsi_params* p) {
     p->split = 0;
     p->timeout_ns = 0;
     p->symmetric = 1;
+    p->hhs_small_max = 0;
 }
 
 const char* fsi_last_error(void) { return g_err.c_str(); }
@@ -514,7 +540,7 @@ int fsi_destroy(fsi_ctx* c) {
     Buf* bufs[] = {&c->rec[0], &c->rec[1], &c->accrec[0], &c->accrec[1], &c->xc, &c->vc, &c->ac,
                    &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->mc, &c->bhc, &c->ids[0], &c->ids[1],
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
-                   &c->iota, &c->steps, &c->step0, &c->counts, &c->accum};
+                   &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -777,10 +803,24 @@ int fsi_hhs_interval(fsi_ctx* c, int N, double* pos, double* vel, const double* 
     CK(ensure(c->step0, (size_t)N * 8));
     CK(ensure(c->counts, 16));
     CU(launch_iota(N, P<int>(c->iota), s));
-    c->level_counts.assign(c->p.max_level + 1, 0);
+    CK(ensure(c->dstats, 68 * sizeof(unsigned long long)));
+    CU(cudaMemsetAsync(c->dstats.p, 0, 68 * sizeof(unsigned long long), s));
+    c->level_counts.assign(std::max(c->p.max_level + 1, 64), 0);
     c->max_level_used = 0;
     c->max_level_hit = 0;
     CK(hhs_level(c, N, pos, vel, mass, is_bh, P<int>(c->iota), N, tau, 0, s));
+    {   // merge the statistics of the levels run inside one CTA
+        unsigned long long st[68];
+        CU(cudaMemcpyAsync(st, c->dstats.p, sizeof st, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        for (int k = 0; k < 64; ++k) {
+            c->level_counts[k] += (long long)st[k];
+            if (st[k]) c->max_level_used = std::max(c->max_level_used, k);
+        }
+        c->work_pairs[0] += (long long)st[64];
+        c->work_pairs[1] += (long long)st[65];
+        if (reinterpret_cast<int*>(st + 66)[0]) c->max_level_hit = 1;
+    }
     if (c->max_level_hit) return fail(FSI_ERR_MAXLEVEL, "a particle needed a level deeper than %d", c->p.max_level);
     return FSI_OK;
 }

@@ -179,6 +179,25 @@ struct BatchArgs {
 };
 
 
+// Small-set HHS recursion in one CTA (hhs_small.cu).
+struct SmallArgs {
+    const int* ids;                 // global ids of the set, n entries
+    int n;
+    double* pos;                    // 3 x N
+    double* vel;
+    const double* mass;
+    const double* step0;            // level-0 steps (global id)
+    long long N;
+    double tau;
+    int level;
+    int max_level;
+    double eps2, eta_ff, eta_fb, eta_jerk;
+    unsigned long long* level_counts;   // per level (device)
+    unsigned long long* work;           // [0] acc pairs, [1] grad pairs
+    int* maxlevel_hit;
+    int* err;
+};
+
 // ---------------------------------------------------------------------------------
 // Host-side launchers (defined in pair_kernels.cu / aux_kernels.cu).
 namespace fsi {
@@ -238,11 +257,16 @@ cudaError_t launch_energy(int n, const double* xc, const double* vc, const doubl
 cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
                              double eta_ff, double eta_fb, double eta_jerk, double eps2,
                              double* step, int* err, cudaStream_t s);
+cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
+                                   double eta_ff, double eta_fb, double eta_jerk, double eps2,
+                                   double* step, int* err, cudaStream_t s);
 cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step0, int level0,
                                cudaStream_t s);
 cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,
                              int* S, int* F, int* counts, cudaStream_t s);
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s);
+cudaError_t launch_hhs_small(int precision, const SmallArgs& a, cudaStream_t s);
+int small_max();
 cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, cudaStream_t s);
 int batch_block_size(int ipt);
 int batch_max_ctas_per_sm(int precision, int ipt);

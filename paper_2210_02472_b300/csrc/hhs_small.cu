@@ -1,0 +1,349 @@
+// hhs_small.cu -- the HHS recursion of a small level set inside ONE CTA.
+//
+// Deep HHS levels (Sect. 2.2) hold few particles but are visited 2^level times; walked
+// from the host every visit costs a synchronisation and tens of launches.  Once a fast
+// set F has at most kSmallMax particles, HHS(F, tau) -- time steps against F (min with
+// the level-0 steps), the split S/F, U_SF(tau/6), FSI(S, tau/2), HHS(F', tau/2),
+// U~_SF(2 tau/3), HHS(F', tau/2), FSI(S, tau/2), U_SF(tau/6), recursively -- runs in a
+// single CTA with the set's state in shared memory and an explicit frame stack.  Thread t
+// owns entry t of whichever index list a phase works on; phases are separated by
+// __syncthreads.  The same arithmetic as the large kernels is used (FP64, or FP32 hi/lo
+// separations with FP64 state for the mixed precision).
+#include <type_traits>
+
+#include "fsi_internal.cuh"
+#include "pair_math.cuh"
+
+namespace fsi {
+
+constexpr int kSmallMax = 512;      // particles per set (one thread each)
+constexpr int kSmallDepth = 48;     // recursion frames
+constexpr int kSmallLists = kSmallMax * 40;   // index-list stack entries
+
+struct Frame {
+    int offS, nS, offF, nF;     // index lists in the list stack
+    int offP, nP;               // the frame's own set
+    double tau;
+    int level;
+    int stage;
+};
+
+template <int P>
+struct SmallSmem {
+    double x[3][kSmallMax], v[3][kSmallMax], m[kSmallMax], s0[kSmallMax], st[kSmallMax];
+    double a[3][kSmallMax], g[3][kSmallMax];
+    typename std::conditional<P == FSI_MIXED, RecMix, D4>::type rec[kSmallMax];
+    typename std::conditional<P == FSI_MIXED, float4, D4>::type arec[kSmallMax];
+    unsigned short lists[kSmallLists];      // per frame on the path: its S list then its F list
+    Frame fr[kSmallDepth];
+    int wsum[32];
+    int top, list_top, nS, nF, anyfast;
+};
+
+template <int P>
+__device__ __forceinline__ void write_rec(SmallSmem<P>& S, int k) {
+    if constexpr (P == FSI_MIXED) S.rec[k] = make_mix_rec(S.x[0][k], S.x[1][k], S.x[2][k], S.m[k]);
+    else S.rec[k] = make_d4(S.x[0][k], S.x[1][k], S.x[2][k], S.m[k]);
+}
+
+template <int P>
+__device__ __forceinline__ void write_arec(SmallSmem<P>& S, int k) {
+    if constexpr (P == FSI_MIXED) S.arec[k] = make_float4((float)S.a[0][k], (float)S.a[1][k], (float)S.a[2][k], (float)S.m[k]);
+    else S.arec[k] = make_d4(S.a[0][k], S.a[1][k], S.a[2][k], S.m[k]);
+}
+
+// out[:, A[t]] = sum over B of the acceleration (kind 0) or gradient (kind 1) pair terms
+template <int P, int KIND>
+__device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
+                           const unsigned short* B, int nB, double eps2, double (*out)[kSmallMax],
+                           unsigned long long* work) {
+    const int t = threadIdx.x;
+    if (t == 0 && work) atomicAdd(work + KIND, (unsigned long long)nA * (unsigned long long)nB);
+    if (t >= nA) return;
+    const int k = A[t];
+    double r[3] = {0.0, 0.0, 0.0};
+    if constexpr (P == FSI_MIXED) {
+        const RecMix ri = S.rec[k];
+        MixI p;
+        p.xh = ri.hi.x; p.yh = ri.hi.y; p.zh = ri.hi.z;
+        p.xl = ri.lo.x; p.yl = ri.lo.y; p.zl = ri.lo.z;
+        p.ax = p.ay = p.az = 0.f;
+        if (KIND == 1) { p.ax = S.arec[k].x; p.ay = S.arec[k].y; p.az = S.arec[k].z; }
+        float f[3] = {0.f, 0.f, 0.f};
+        const float eps2f = (float)eps2;
+        for (int q = 0; q < nB; ++q) {
+            const int j = B[q];
+            const RecMix rj = S.rec[j];
+            if (KIND == 0) mix_acc_pair<true>(rj.hi, rj.lo, p, eps2f, j == k, f[0], f[1], f[2]);
+            else mix_grad_pair<true>(rj.hi, rj.lo, S.arec[j], p, eps2f, j == k, f[0], f[1], f[2]);
+            if ((q & 255) == 255) {
+                r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
+                f[0] = f[1] = f[2] = 0.f;
+            }
+        }
+        r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
+    } else {
+        const D4 ri = S.rec[k];
+        F64I p;
+        p.x = ri.x; p.y = ri.y; p.z = ri.z;
+        p.ax = p.ay = p.az = 0.0;
+        if (KIND == 1) { p.ax = S.arec[k].x; p.ay = S.arec[k].y; p.az = S.arec[k].z; }
+        for (int q = 0; q < nB; ++q) {
+            const int j = B[q];
+            if (KIND == 0) f64_acc_pair<true>(S.rec[j], p, eps2, j == k, r[0], r[1], r[2]);
+            else f64_grad_pair<true>(S.rec[j], S.arec[j], p, eps2, j == k, r[0], r[1], r[2]);
+        }
+    }
+    out[0][k] = r[0];
+    out[1][k] = r[1];
+    out[2][k] = r[2];
+}
+
+// FP64 time steps of list L against itself (Sect. 3.4), then min with the level-0 step.
+template <int P>
+__device__ void small_timesteps(SmallSmem<P>& S, const unsigned short* L, int n, const SmallArgs& a) {
+    const int t = threadIdx.x;
+    if (t >= n) return;
+    const int i = L[t];
+    double ff2 = INFINITY, fb = INFINITY, ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+    for (int q = 0; q < n; ++q) {
+        const int j = L[q];
+        if (j == i) continue;
+        const double dx = S.x[0][j] - S.x[0][i], dy = S.x[1][j] - S.x[1][i], dz = S.x[2][j] - S.x[2][i];
+        const double du = S.v[0][j] - S.v[0][i], dv = S.v[1][j] - S.v[1][i], dw = S.v[2][j] - S.v[2][i];
+        const double d2 = dx * dx + dy * dy + dz * dz;
+        if (d2 == 0.0) { set_error(a.err, FSI_ERR_NONFINITE); continue; }
+        const double s2 = d2 + a.eps2;
+        const double d = sqrt(d2);
+        ff2 = fmin(ff2, d2 * d / (S.m[i] + S.m[j]));
+        const double u2 = du * du + dv * dv + dw * dw;
+        if (u2 > 0.0) fb = fmin(fb, d / sqrt(u2));
+        const double sr = sqrt(s2);
+        const double f3 = S.m[j] / (s2 * sr), f5 = f3 / s2;
+        const double rv = dx * du + dy * dv + dz * dw;
+        ax += f3 * dx; ay += f3 * dy; az += f3 * dz;
+        jx += f5 * (s2 * du - 3.0 * rv * dx);
+        jy += f5 * (s2 * dv - 3.0 * rv * dy);
+        jz += f5 * (s2 * dw - 3.0 * rv * dz);
+    }
+    double e = fmin(a.eta_ff * sqrt(ff2), a.eta_fb * fb);
+    const double jn = sqrt(jx * jx + jy * jy + jz * jz);
+    if (jn > 0.0) e = fmin(e, a.eta_jerk * sqrt(ax * ax + ay * ay + az * az) / jn);
+    S.st[i] = fmin(e, S.s0[i]);
+}
+
+template <int P>
+__device__ void small_kick(SmallSmem<P>& S, const unsigned short* L, int n, double w, bool with_grad,
+                           double cg) {
+    const int t = threadIdx.x;
+    if (t >= n) return;
+    const int k = L[t];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S.v[c][k] = fma(w, with_grad ? fma(cg, S.g[c][k], S.a[c][k]) : S.a[c][k], S.v[c][k]);
+}
+
+template <int P>
+__device__ void small_drift(SmallSmem<P>& S, const unsigned short* L, int n, double w) {
+    const int t = threadIdx.x;
+    if (t >= n) return;
+    const int k = L[t];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S.x[c][k] = fma(w, S.v[c][k], S.x[c][k]);
+    write_rec<P>(S, k);
+}
+
+// One FSI cycle of list L on itself (Sect. 2.1, Eq. fsi-cycle).
+template <int P>
+__device__ void small_fsi(SmallSmem<P>& S, const unsigned short* L, int n, double h, const SmallArgs& a) {
+    small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
+    small_kick<P>(S, L, n, h / 6.0, false, 0.0); __syncthreads();
+    small_drift<P>(S, L, n, 0.5 * h); __syncthreads();
+    small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
+    if (threadIdx.x < n) write_arec<P>(S, L[threadIdx.x]);
+    __syncthreads();
+    small_pass<P, 1>(S, L, n, L, n, a.eps2, S.g, a.work); __syncthreads();
+    small_kick<P>(S, L, n, 2.0 * h / 3.0, true, h * h / 24.0); __syncthreads();
+    small_drift<P>(S, L, n, 0.5 * h); __syncthreads();
+    small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
+    small_kick<P>(S, L, n, h / 6.0, false, 0.0); __syncthreads();
+}
+
+// Inter-level kick of S and F (Sect. 2.2); gradient: the gradient acceleration of the
+// same inter-level term with eps = tau.
+template <int P>
+__device__ void small_cross(SmallSmem<P>& S, const unsigned short* Ls, int nS,
+                            const unsigned short* Lf, int nF, double w, bool gradient, double tau,
+                            const SmallArgs& a) {
+    small_pass<P, 0>(S, Ls, nS, Lf, nF, a.eps2, S.a, a.work);
+    __syncthreads();
+    small_pass<P, 0>(S, Lf, nF, Ls, nS, a.eps2, S.a, a.work);
+    __syncthreads();
+    if (gradient) {
+        if (threadIdx.x < nS) write_arec<P>(S, Ls[threadIdx.x]);
+        if (threadIdx.x < nF) write_arec<P>(S, Lf[threadIdx.x]);
+        __syncthreads();
+        small_pass<P, 1>(S, Ls, nS, Lf, nF, a.eps2, S.g, a.work);
+        __syncthreads();
+        small_pass<P, 1>(S, Lf, nF, Ls, nS, a.eps2, S.g, a.work);
+        __syncthreads();
+    }
+    small_kick<P>(S, Ls, nS, w, gradient, tau * tau / 24.0);
+    small_kick<P>(S, Lf, nF, w, gradient, tau * tau / 24.0);
+    __syncthreads();
+}
+
+// Stable split of list L into S = {st >= tau} and F (all slow at max_level).
+template <int P>
+__device__ void small_partition(SmallSmem<P>& S, const unsigned short* L, int n, double tau,
+                                bool force_slow, unsigned short* outS, unsigned short* outF) {
+    const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const bool valid = t < n;
+    const int k = valid ? L[t] : 0;
+    const bool wants_fast = valid && S.st[k] < tau;
+    const bool slow = valid && (force_slow || !wants_fast);
+    const unsigned bs = __ballot_sync(0xffffffffu, slow);
+    const unsigned bv = __ballot_sync(0xffffffffu, valid);
+    if (lane == 0) S.wsum[wid] = __popc(bs);
+    if (t == 0) S.anyfast = 0;
+    __syncthreads();
+    if (force_slow && wants_fast) S.anyfast = 1;
+    int before = 0, total = 0;
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) {
+        if (w < wid) before += S.wsum[w];
+        total += S.wsum[w];
+    }
+    const unsigned lm = (1u << lane) - 1u;
+    const int rs = before + __popc(bs & lm);
+    const int rv = t - rs;                              // valid entries before me that are fast
+    (void)bv;
+    if (slow) outS[rs] = (unsigned short)k;
+    else if (valid) outF[rv] = (unsigned short)k;
+    if (t == 0) { S.nS = total; S.nF = n - total; }
+    __syncthreads();
+}
+
+template <int P>
+__global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs a) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    SmallSmem<P>& S = *reinterpret_cast<SmallSmem<P>*>(smem_raw);
+    const int t = threadIdx.x;
+    const int n = a.n;
+    const long long N = a.N;
+    if (t < n) {
+        const int i = a.ids[t];
+        for (int c = 0; c < 3; ++c) {
+            S.x[c][t] = a.pos[c * N + i];
+            S.v[c][t] = a.vel[c * N + i];
+        }
+        S.m[t] = a.mass[i];
+        S.s0[t] = a.step0[i];
+        write_rec<P>(S, t);
+        S.lists[t] = (unsigned short)t;                 // the root's set
+    }
+    if (t == 0) {
+        S.top = 0;
+        S.list_top = n;
+        Frame f;
+        f.offP = 0; f.nP = n; f.tau = a.tau; f.level = a.level; f.stage = 0;
+        f.offS = f.nS = f.offF = f.nF = 0;
+        S.fr[0] = f;
+    }
+    __syncthreads();
+    while (true) {
+        const int top = S.top;
+        if (top < 0) break;
+        Frame f = S.fr[top];
+        if (f.stage == 0) {
+            const unsigned short* L = S.lists + f.offP;
+            small_timesteps<P>(S, L, f.nP, a);
+            __syncthreads();
+            // S goes to [lt, lt + nS), F first to [lt + nP, ...) and is then moved down to
+            // [lt + nS, lt + nP): the frame's lists take exactly nP entries.
+            const int lt = S.list_top;
+            const bool room = lt + 2 * f.nP <= kSmallLists;
+            const bool stop = f.level >= a.max_level || !room;
+            small_partition<P>(S, L, f.nP, f.tau, stop, S.lists + lt, S.lists + lt + f.nP);
+            const int nS = S.nS, nF = S.nF;
+            if (t < nF) S.lists[lt + nS + t] = S.lists[lt + f.nP + t];
+            if (t == 0) {
+                if (stop && S.anyfast) {
+                    atomicExch(a.maxlevel_hit, 1);
+                    if (!room) set_error(a.err, FSI_ERR_MAXLEVEL);
+                }
+                atomicAdd(a.level_counts + f.level, (unsigned long long)nS);
+            }
+            __syncthreads();
+            f.offS = lt; f.nS = nS; f.offF = lt + nS; f.nF = nF;
+            const unsigned short* Ls = S.lists + f.offS;
+            const unsigned short* Lf = S.lists + f.offF;
+            if (nS > 0 && nF > 0) small_cross<P>(S, Ls, nS, Lf, nF, f.tau / 6.0, false, 0.0, a);
+            if (nS > 0) small_fsi<P>(S, Ls, nS, 0.5 * f.tau, a);
+            f.stage = 1;
+        } else if (f.stage == 1) {
+            const unsigned short* Ls = S.lists + f.offS;
+            const unsigned short* Lf = S.lists + f.offF;
+            if (f.nS > 0 && f.nF > 0) small_cross<P>(S, Ls, f.nS, Lf, f.nF, 2.0 * f.tau / 3.0, true, f.tau, a);
+            f.stage = 2;
+        } else {
+            const unsigned short* Ls = S.lists + f.offS;
+            const unsigned short* Lf = S.lists + f.offF;
+            if (f.nS > 0) small_fsi<P>(S, Ls, f.nS, 0.5 * f.tau, a);
+            if (f.nS > 0 && f.nF > 0) small_cross<P>(S, Ls, f.nS, Lf, f.nF, f.tau / 6.0, false, 0.0, a);
+            f.stage = 3;
+        }
+        __syncthreads();
+        if (t == 0) {
+            if (f.stage == 3) {
+                // done: pop, and give the list space back to the parent
+                S.top = top - 1;
+                S.list_top = f.offS;
+            } else {
+                // after stage 0 and after stage 1: HHS(F, tau/2)
+                S.fr[top] = f;
+                S.list_top = f.offS + f.nS + f.nF;
+                if (f.nF > 0) {
+                    if (top + 1 < kSmallDepth) {
+                        Frame c;
+                        c.offP = f.offF; c.nP = f.nF; c.tau = 0.5 * f.tau; c.level = f.level + 1;
+                        c.stage = 0; c.offS = c.nS = c.offF = c.nF = 0;
+                        S.fr[top + 1] = c;
+                        S.top = top + 1;
+                    } else {
+                        set_error(a.err, FSI_ERR_MAXLEVEL);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (t < n) {
+        const int i = a.ids[t];
+        for (int c = 0; c < 3; ++c) {
+            a.pos[c * N + i] = S.x[c][t];
+            a.vel[c * N + i] = S.v[c][t];
+        }
+    }
+}
+
+size_t small_smem_bytes(int precision) {
+    return precision == FSI_MIXED ? sizeof(SmallSmem<FSI_MIXED>) : sizeof(SmallSmem<FSI_FP64>);
+}
+
+int small_max() { return kSmallMax; }
+
+cudaError_t launch_hhs_small(int precision, const SmallArgs& a, cudaStream_t s) {
+    const size_t smem = small_smem_bytes(precision);
+    static bool attr[2] = {false, false};
+    if (!attr[precision]) {
+        cudaError_t e = precision == FSI_MIXED
+            ? cudaFuncSetAttribute(hhs_small_kernel<FSI_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
+            : cudaFuncSetAttribute(hhs_small_kernel<FSI_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        attr[precision] = true;
+    }
+    if (precision == FSI_MIXED) { hhs_small_kernel<FSI_MIXED><<<1, kSmallMax, smem, s>>>(a); note_launch(); }
+    else { hhs_small_kernel<FSI_FP64><<<1, kSmallMax, smem, s>>>(a); note_launch(); }
+    return cudaGetLastError();
+}
+
+}  // namespace fsi

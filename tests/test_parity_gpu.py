@@ -360,12 +360,23 @@ def test_timesteps_and_energy(F):
     assert abs(e[0] / T - 1) < 1e-13 and abs(e[1] / W - 1) < 1e-12
 
 
+def test_timesteps_mixed(F):
+    c = inputs.plummer(3000, 23, imf="kroupa")
+    ref = oracle.timesteps(c.pos, c.vel, c.mass)
+    with F.Context("mixed") as ctx:
+        s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+    assert np.abs(s / ref - 1).max() < 2e-5
+
+
 @pytest.mark.parametrize("prec", PRECS)
-def test_hhs_interval(F, prec):
-    c = inputs.plummer(160, 22, imf="kroupa")
+@pytest.mark.parametrize("small", [0, -1, 64])
+def test_hhs_interval(F, prec, small):
+    """One HHS interval against the oracle: the levels walked from the host (small = -1),
+    run inside one CTA once the fast set has <= 512 particles (0), or a mix (64)."""
+    c = inputs.plummer(600, 22, imf="kroupa")
     tau = 1.0 / 16
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
-    with F.Context(prec) as ctx:
+    with F.Context(prec, hhs_small_max=small) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
