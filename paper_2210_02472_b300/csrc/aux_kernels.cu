@@ -2,6 +2,7 @@
 // record packing (gather), scatter, kick/drift, PN1.0 pair kicks, time steps, energy,
 // set checks.
 #include "fsi_internal.cuh"
+#include "pair_math.cuh"
 
 namespace fsi {
 
@@ -442,8 +443,8 @@ cudaError_t launch_pn_pairs(int N, const double* pos, const double* vel, const d
 // memory in plain cooperative tiles.
 constexpr int kAuxTile = 128;
 
-// Time steps (Sect. 3.4): min over j of eta_ff (r^3/(m_i+m_j))^{1/2} and eta_fb r/|v_ij|,
-// and eta_jerk |a|/|j| with a and the jerk from the softened kernel.
+// Time steps (Sect. 3.4), FP64: thread per i, sources through shared memory, the
+// division-free pair update of step_pair (pair_math.cuh).
 __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
                                  const double* __restrict__ mc, double eta_ff, double eta_fb,
                                  double eta_jerk, double eps2, double* __restrict__ step, int* err) {
@@ -454,8 +455,9 @@ __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const dou
     const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
     const double ui = vc[ii], vi = vc[(size_t)n + ii], wi = vc[2 * (size_t)n + ii];
     const double mi = mc[ii];
-    double ff2 = INFINITY, fb = INFINITY;
-    double ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
+    StepAcc<double> acc;
+    acc.init();
+    bool coincident = false;
     for (int j0 = 0; j0 < n; j0 += kAuxTile) {
         __syncthreads();
         for (int t = threadIdx.x; t < kAuxTile; t += blockDim.x) {
@@ -471,107 +473,18 @@ __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const dou
         for (int t = 0; t < cnt; ++t) {
             if (j0 + t == ii) continue;
             const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
-            const double du = su[t] - ui, dv = sv[t] - vi, dw = sw[t] - wi;
             const double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 == 0.0) { coincident = true; continue; }
             const double s2 = d2 + eps2;
-            if (d2 == 0.0) { if (i < n) set_error(err, FSI_ERR_NONFINITE); continue; }
-            const double d = sqrt(d2);
-            ff2 = fmin(ff2, d2 * d / (mi + sm[t]));
-            const double u2 = du * du + dv * dv + dw * dw;
-            if (u2 > 0.0) fb = fmin(fb, d / sqrt(u2));
-            const double sr = sqrt(s2);
-            const double f3 = sm[t] / (s2 * sr);
-            const double f5 = f3 / s2;
-            const double rv = dx * du + dy * dv + dz * dw;
-            ax += f3 * dx; ay += f3 * dy; az += f3 * dz;
-            jx += f5 * (s2 * du - 3.0 * rv * dx);
-            jy += f5 * (s2 * dv - 3.0 * rv * dy);
-            jz += f5 * (s2 * dw - 3.0 * rv * dz);
-        }
-    }
-    if (i >= n) return;
-    double e = fmin(eta_ff * sqrt(ff2), eta_fb * fb);
-    const double jn = sqrt(jx * jx + jy * jy + jz * jz);
-    if (jn > 0.0) e = fmin(e, eta_jerk * sqrt(ax * ax + ay * ay + az * az) / jn);
-    step[i] = e;
-}
-
-// Mixed-precision time steps: the same criteria with FP32 pair arithmetic.  Separations
-// come from FP32 hi/lo splits of the FP64 positions (FP32-accurate relative to the
-// separation); the minima are taken over squared quantities (r^6 / (m_i + m_j)^2 and
-// r^2 / |v_ij|^2) so that no division or square root is needed per pair.
-__global__ void timesteps_mixed_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
-                                       const double* __restrict__ mc, double eta_ff, double eta_fb,
-                                       double eta_jerk, double eps2, double* __restrict__ step, int* err) {
-    __shared__ float4 sh[kAuxTile], sl[kAuxTile], sv[kAuxTile];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ii = min(i, n - 1);
-    const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
-    const float xh = (float)xi, yh = (float)yi, zh = (float)zi;
-    const float xl = (float)(xi - (double)xh), yl = (float)(yi - (double)yh), zl = (float)(zi - (double)zh);
-    const float ui = (float)vc[ii], vi = (float)vc[(size_t)n + ii], wi = (float)vc[2 * (size_t)n + ii];
-    const float mi = (float)mc[ii];
-    const float eps2f = (float)eps2;
-    float ff6 = INFINITY, fb2 = INFINITY;
-    float ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
-    bool coincident = false;
-    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < kAuxTile; t += blockDim.x) {
-            const int j = j0 + t;
-            if (j < n) {
-                const double x = xc[j], y = xc[(size_t)n + j], z = xc[2 * (size_t)n + j];
-                const float h0 = (float)x, h1 = (float)y, h2 = (float)z;
-                sh[t] = make_float4(h0, h1, h2, (float)mc[j]);
-                sl[t] = make_float4((float)(x - (double)h0), (float)(y - (double)h1), (float)(z - (double)h2), 0.f);
-                sv[t] = make_float4((float)vc[j], (float)vc[(size_t)n + j], (float)vc[2 * (size_t)n + j], 0.f);
-            }
-        }
-        __syncthreads();
-        const int cnt = min(kAuxTile, n - j0);
-        for (int t = 0; t < cnt; ++t) {
-            const float4 h = sh[t], l = sl[t], v = sv[t];
-            const float dx = (h.x - xh) + (l.x - xl);
-            const float dy = (h.y - yh) + (l.y - yl);
-            const float dz = (h.z - zh) + (l.z - zl);
-            const float du = v.x - ui, dv = v.y - vi, dw = v.z - wi;
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            const bool self = (j0 + t == ii);
-            if (!self && d2 == 0.f) coincident = true;
-            const float d2s = self ? 1.0f : d2;
-            const float s2 = d2s + eps2f;
-            const float y = rsqrt_hw(s2);
-            const float y2 = y * y;
-            const float w = self ? 0.f : h.w * (y2 * y);                       // m_j / s^3
-            const float ms = mi + h.w;
-            const float q_ff = self ? INFINITY : (d2s * d2s) * d2s * __frcp_rn(ms * ms);
-            const float u2 = fmaf(du, du, fmaf(dv, dv, dw * dw));
-            const float q_fb = (self || u2 == 0.f) ? INFINITY : d2s * __frcp_rn(u2);
-            ff6 = fminf(ff6, q_ff);
-            fb2 = fminf(fb2, q_fb);
-            const float rv = fmaf(dx, du, fmaf(dy, dv, dz * dw));
-            const float c3 = -3.0f * rv * y2;
-            ax = fmaf(w, dx, ax); ay = fmaf(w, dy, ay); az = fmaf(w, dz, az);
-            jx = fmaf(w, fmaf(c3, dx, du), jx);
-            jy = fmaf(w, fmaf(c3, dy, dv), jy);
-            jz = fmaf(w, fmaf(c3, dz, dw), jz);
+            const double y0 = (double)rsqrt_hw(__double2float_rn(s2));
+            const double e0 = fma(-s2 * y0, y0, 1.0);
+            const double y = fma(y0 * e0, fma(0.375, e0, 0.5), y0);
+            step_pair<double>(acc, dx, dy, dz, su[t] - ui, sv[t] - vi, sw[t] - wi, d2, sm[t], mi + sm[t], y);
         }
     }
     if (i >= n) return;
     if (coincident) set_error(err, FSI_ERR_NONFINITE);
-    double e = fmin(eta_ff * sqrt(sqrt((double)ff6)), eta_fb * sqrt((double)fb2));
-    const double jn = sqrt((double)jx * jx + (double)jy * jy + (double)jz * jz);
-    if (jn > 0.0) e = fmin(e, eta_jerk * sqrt((double)ax * ax + (double)ay * ay + (double)az * az) / jn);
-    step[i] = e;
-}
-
-cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
-                                   double eta_ff, double eta_fb, double eta_jerk, double eps2,
-                                   double* step, int* err, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    { timesteps_mixed_kernel<<<blocks_for(n, kAuxTile), kAuxTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb,
-                                                                         eta_jerk, eps2, step, err); note_launch(); }
-    return cudaGetLastError();
+    step[i] = step_finish<double>(acc, eta_ff, eta_fb, eta_jerk);
 }
 
 cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
@@ -582,6 +495,87 @@ cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const do
                                                                   eta_jerk, eps2, step, err); note_launch(); }
     return cudaGetLastError();
 }
+
+// Mixed-precision time steps: the same criteria with FP32 pair arithmetic on the mixed
+// position records (hi/lo separations, FP32-accurate relative to the separation) and FP32
+// velocity records (vx, vy, vz, m); two receivers per thread.
+constexpr int kStepIpt = 2;
+
+__global__ void __launch_bounds__(kAuxTile) timesteps_mixed_kernel(
+    int n, const RecMix* __restrict__ rec, const float4* __restrict__ vrec, double eta_ff,
+    double eta_fb, double eta_jerk, double eps2, double* __restrict__ step, int* err) {
+    __shared__ RecMix sr[kAuxTile];
+    __shared__ float4 sv[kAuxTile];
+    const int base = blockIdx.x * (kAuxTile * kStepIpt);
+    float xh[kStepIpt], yh[kStepIpt], zh[kStepIpt], xl[kStepIpt], yl[kStepIpt], zl[kStepIpt];
+    float ui[kStepIpt], vi[kStepIpt], wi[kStepIpt], mi[kStepIpt];
+    int me[kStepIpt];
+    StepAcc<float> acc[kStepIpt];
+#pragma unroll
+    for (int u = 0; u < kStepIpt; ++u) {
+        me[u] = base + u * kAuxTile + threadIdx.x;
+        const int ii = min(me[u], n - 1);
+        const RecMix r = rec[ii];
+        const float4 v = vrec[ii];
+        xh[u] = r.hi.x; yh[u] = r.hi.y; zh[u] = r.hi.z;
+        xl[u] = r.lo.x; yl[u] = r.lo.y; zl[u] = r.lo.z;
+        ui[u] = v.x; vi[u] = v.y; wi[u] = v.z; mi[u] = v.w;
+        acc[u].init();
+    }
+    const float eps2f = (float)eps2;
+    bool coincident = false;
+    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
+        __syncthreads();
+        if (j0 + threadIdx.x < n) {
+            sr[threadIdx.x] = rec[j0 + threadIdx.x];
+            sv[threadIdx.x] = vrec[j0 + threadIdx.x];
+        }
+        __syncthreads();
+        const int cnt = min(kAuxTile, n - j0);
+        for (int t = 0; t < cnt; ++t) {
+            const float4 h = sr[t].hi, l = sr[t].lo, v = sv[t];
+#pragma unroll
+            for (int u = 0; u < kStepIpt; ++u) {
+                const float dx = (h.x - xh[u]) + (l.x - xl[u]);
+                const float dy = (h.y - yh[u]) + (l.y - yl[u]);
+                const float dz = (h.z - zh[u]) + (l.z - zl[u]);
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                const bool self = (j0 + t == me[u]);
+                coincident |= (!self && d2 == 0.f);
+                if (self || d2 == 0.f) continue;
+                const float y = rsqrt_f32_refined(d2 + eps2f);
+                step_pair<float>(acc[u], dx, dy, dz, v.x - ui[u], v.y - vi[u], v.z - wi[u], d2, v.w,
+                                 mi[u] + v.w, y);
+            }
+        }
+    }
+    if (coincident) set_error(err, FSI_ERR_NONFINITE);
+#pragma unroll
+    for (int u = 0; u < kStepIpt; ++u)
+        if (me[u] < n) step[me[u]] = step_finish<float>(acc[u], eta_ff, eta_fb, eta_jerk);
+}
+
+// FP32 velocity records (vx, vy, vz, m) of a compact set.
+__global__ void pack_vel_kernel(int n, const double* __restrict__ vc, const double* __restrict__ mc,
+                                float4* __restrict__ out) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k < n) out[k] = make_float4((float)vc[k], (float)vc[(size_t)n + k], (float)vc[2 * (size_t)n + k], (float)mc[k]);
+}
+
+cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
+                                   double eta_ff, double eta_fb, double eta_jerk, double eps2,
+                                   void* rec_ws, void* vrec_ws, double* step, int* err,
+                                   cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { pack_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, mc, nullptr, n, rec_ws, nullptr); note_launch(); }
+    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, reinterpret_cast<float4*>(vrec_ws)); note_launch(); }
+    { timesteps_mixed_kernel<<<blocks_for(n, kAuxTile * kStepIpt), kAuxTile, 0, s>>>(
+        n, reinterpret_cast<const RecMix*>(rec_ws), reinterpret_cast<const float4*>(vrec_ws), eta_ff,
+        eta_fb, eta_jerk, eps2, step, err); note_launch(); }
+    return cudaGetLastError();
+}
+
+
 
 // Energy: per-CTA partial sums of the kinetic energy and of -1/2 sum_i sum_{j != i}
 // m_i m_j / sqrt(r^2 + eps2), reduced in a fixed order by energy_finish_kernel.
@@ -607,7 +601,9 @@ __global__ void energy_kernel(int n, const double* __restrict__ xc, const double
             const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
             const double r2 = dx * dx + dy * dy + dz * dz + eps2;
             if (r2 == 0.0) { if (i < n) set_error(err, FSI_ERR_NONFINITE); continue; }
-            w += sm[t] / sqrt(r2);
+            const double y0 = (double)rsqrt_hw(__double2float_rn(r2));
+            const double e0 = fma(-r2 * y0, y0, 1.0);
+            w = fma(sm[t], fma(y0 * e0, fma(0.375, e0, 0.5), y0), w);
         }
     }
     double kin = 0.0;

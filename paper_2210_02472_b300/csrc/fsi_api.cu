@@ -402,9 +402,12 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
         vc = P<double>(c->vc);
         mc = P<double>(c->mc);
     }
-    if (c->p.precision == FSI_MIXED)
+    if (c->p.precision == FSI_MIXED) {
+        CK(ensure(c->rec[1], pad_tile(n) * 32));
+        CK(ensure(c->accrec[1], pad_tile(n) * 32));
         CU(launch_timesteps_mixed(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2,
-                                  step, c->err_d, s));
+                                  c->rec[1].p, c->accrec[1].p, step, c->err_d, s));
+    }
     else
         CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
                             c->err_d, s));

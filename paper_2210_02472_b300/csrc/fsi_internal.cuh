@@ -257,9 +257,11 @@ cudaError_t launch_energy(int n, const double* xc, const double* vc, const doubl
 cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
                              double eta_ff, double eta_fb, double eta_jerk, double eps2,
                              double* step, int* err, cudaStream_t s);
+// rec_ws, vrec_ws: workspace of >= 32 n and 16 n bytes (mixed records, FP32 velocities)
 cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
                                    double eta_ff, double eta_fb, double eta_jerk, double eps2,
-                                   double* step, int* err, cudaStream_t s);
+                                   void* rec_ws, void* vrec_ws, double* step, int* err,
+                                   cudaStream_t s);
 cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step0, int level0,
                                cudaStream_t s);
 cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,

@@ -34,6 +34,7 @@ struct SmallSmem {
     double a[3][kSmallMax], g[3][kSmallMax];
     typename std::conditional<P == FSI_MIXED, RecMix, D4>::type rec[kSmallMax];
     typename std::conditional<P == FSI_MIXED, float4, D4>::type arec[kSmallMax];
+    float4 vf[kSmallMax];                   // FP32 (vx, vy, vz, m) for the mixed time steps
     unsigned short lists[kSmallLists];      // per frame on the path: its S list then its F list
     Frame fr[kSmallDepth];
     int wsum[32];
@@ -99,36 +100,54 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
     out[2][k] = r[2];
 }
 
-// FP64 time steps of list L against itself (Sect. 3.4), then min with the level-0 step.
+// Time steps of list L against itself (Sect. 3.4; FP32 pair arithmetic for the mixed
+// precision, FP64 otherwise), then the min with the level-0 step.
 template <int P>
 __device__ void small_timesteps(SmallSmem<P>& S, const unsigned short* L, int n, const SmallArgs& a) {
     const int t = threadIdx.x;
     if (t >= n) return;
     const int i = L[t];
-    double ff2 = INFINITY, fb = INFINITY, ax = 0, ay = 0, az = 0, jx = 0, jy = 0, jz = 0;
-    for (int q = 0; q < n; ++q) {
-        const int j = L[q];
-        if (j == i) continue;
-        const double dx = S.x[0][j] - S.x[0][i], dy = S.x[1][j] - S.x[1][i], dz = S.x[2][j] - S.x[2][i];
-        const double du = S.v[0][j] - S.v[0][i], dv = S.v[1][j] - S.v[1][i], dw = S.v[2][j] - S.v[2][i];
-        const double d2 = dx * dx + dy * dy + dz * dz;
-        if (d2 == 0.0) { set_error(a.err, FSI_ERR_NONFINITE); continue; }
-        const double s2 = d2 + a.eps2;
-        const double d = sqrt(d2);
-        ff2 = fmin(ff2, d2 * d / (S.m[i] + S.m[j]));
-        const double u2 = du * du + dv * dv + dw * dw;
-        if (u2 > 0.0) fb = fmin(fb, d / sqrt(u2));
-        const double sr = sqrt(s2);
-        const double f3 = S.m[j] / (s2 * sr), f5 = f3 / s2;
-        const double rv = dx * du + dy * dv + dz * dw;
-        ax += f3 * dx; ay += f3 * dy; az += f3 * dz;
-        jx += f5 * (s2 * du - 3.0 * rv * dx);
-        jy += f5 * (s2 * dv - 3.0 * rv * dy);
-        jz += f5 * (s2 * dw - 3.0 * rv * dz);
+    bool coincident = false;
+    double e;
+    if constexpr (P == FSI_MIXED) {
+        const RecMix ri = S.rec[i];
+        const float4 vi = S.vf[i];
+        const float eps2f = (float)a.eps2;
+        StepAcc<float> acc;
+        acc.init();
+        for (int q = 0; q < n; ++q) {
+            const int j = L[q];
+            if (j == i) continue;
+            const RecMix rj = S.rec[j];
+            const float4 vj = S.vf[j];
+            const float dx = (rj.hi.x - ri.hi.x) + (rj.lo.x - ri.lo.x);
+            const float dy = (rj.hi.y - ri.hi.y) + (rj.lo.y - ri.lo.y);
+            const float dz = (rj.hi.z - ri.hi.z) + (rj.lo.z - ri.lo.z);
+            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (d2 == 0.f) { coincident = true; continue; }
+            step_pair<float>(acc, dx, dy, dz, vj.x - vi.x, vj.y - vi.y, vj.z - vi.z, d2, vj.w,
+                             vi.w + vj.w, rsqrt_f32_refined(d2 + eps2f));
+        }
+        e = step_finish<float>(acc, a.eta_ff, a.eta_fb, a.eta_jerk);
+    } else {
+        StepAcc<double> acc;
+        acc.init();
+        for (int q = 0; q < n; ++q) {
+            const int j = L[q];
+            if (j == i) continue;
+            const double dx = S.x[0][j] - S.x[0][i], dy = S.x[1][j] - S.x[1][i], dz = S.x[2][j] - S.x[2][i];
+            const double d2 = dx * dx + dy * dy + dz * dz;
+            if (d2 == 0.0) { coincident = true; continue; }
+            const double s2 = d2 + a.eps2;
+            const double y0 = (double)rsqrt_hw(__double2float_rn(s2));
+            const double e0 = fma(-s2 * y0, y0, 1.0);
+            const double y = fma(y0 * e0, fma(0.375, e0, 0.5), y0);
+            step_pair<double>(acc, dx, dy, dz, S.v[0][j] - S.v[0][i], S.v[1][j] - S.v[1][i],
+                              S.v[2][j] - S.v[2][i], d2, S.m[j], S.m[i] + S.m[j], y);
+        }
+        e = step_finish<double>(acc, a.eta_ff, a.eta_fb, a.eta_jerk);
     }
-    double e = fmin(a.eta_ff * sqrt(ff2), a.eta_fb * fb);
-    const double jn = sqrt(jx * jx + jy * jy + jz * jz);
-    if (jn > 0.0) e = fmin(e, a.eta_jerk * sqrt(ax * ax + ay * ay + az * az) / jn);
+    if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
     S.st[i] = fmin(e, S.s0[i]);
 }
 
@@ -140,6 +159,7 @@ __device__ void small_kick(SmallSmem<P>& S, const unsigned short* L, int n, doub
     const int k = L[t];
 #pragma unroll
     for (int c = 0; c < 3; ++c) S.v[c][k] = fma(w, with_grad ? fma(cg, S.g[c][k], S.a[c][k]) : S.a[c][k], S.v[c][k]);
+    if constexpr (P == FSI_MIXED) S.vf[k] = make_float4((float)S.v[0][k], (float)S.v[1][k], (float)S.v[2][k], (float)S.m[k]);
 }
 
 template <int P>
@@ -238,6 +258,7 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
         S.m[t] = a.mass[i];
         S.s0[t] = a.step0[i];
         write_rec<P>(S, t);
+        S.vf[t] = make_float4((float)S.v[0][t], (float)S.v[1][t], (float)S.v[2][t], (float)S.m[t]);
         S.lists[t] = (unsigned short)t;                 // the root's set
     }
     if (t == 0) {

@@ -105,3 +105,58 @@ __device__ __forceinline__ void f64_grad_pair(const D4 j, const D4 aj, const F64
 }
 
 }  // namespace fsi
+
+namespace fsi {
+
+// ---------------------------------------------------------------------------------
+// Time-step pair update (Sect. 3.4), division-free: the free-fall minimum of
+// r^3 / (m_i + m_j) is tracked as the minimum of r^6 / (m_i + m_j)^2 and the fly-by
+// minimum of r / |v_ij| as that of r^2 / |v_ij|^2, each as a (numerator, denominator)
+// pair compared by cross-multiplication; a_i and the jerk j_i use the softened kernel.
+template <class T>
+struct StepAcc {
+    T ffn, ffd, fbn, fbd;
+    T ax, ay, az, jx, jy, jz;
+    __device__ __forceinline__ void init() {
+        ffn = fbn = (T)INFINITY;
+        ffd = fbd = (T)1;
+        ax = ay = az = jx = jy = jz = (T)0;
+    }
+};
+
+// d = r_j - r_i, u = v_j - v_i, ms = m_i + m_j, y = 1/sqrt(|d|^2 + eps2) (refined).
+template <class T>
+__device__ __forceinline__ void step_pair(StepAcc<T>& s, T dx, T dy, T dz, T du, T dv, T dw,
+                                          T d2, T mj, T ms, T y) {
+    const T num = d2 * d2 * d2, den = ms * ms;
+    if (num * s.ffd < s.ffn * den) { s.ffn = num; s.ffd = den; }
+    const T u2 = du * du + dv * dv + dw * dw;
+    if (u2 > (T)0 && d2 * s.fbd < s.fbn * u2) { s.fbn = d2; s.fbd = u2; }
+    const T y2 = y * y;
+    const T w = mj * (y2 * y);
+    const T rv = dx * du + dy * dv + dz * dw;
+    const T c3 = (T)(-3) * rv * y2;
+    s.ax += w * dx; s.ay += w * dy; s.az += w * dz;
+    s.jx += w * (c3 * dx + du);
+    s.jy += w * (c3 * dy + dv);
+    s.jz += w * (c3 * dz + dw);
+}
+
+template <class T>
+__device__ __forceinline__ double step_finish(const StepAcc<T>& s, double eta_ff, double eta_fb,
+                                              double eta_jerk) {
+    double e = INFINITY;
+    if (isfinite((double)s.ffn)) e = eta_ff * sqrt(sqrt((double)s.ffn / (double)s.ffd));
+    if (isfinite((double)s.fbn)) e = fmin(e, eta_fb * sqrt((double)s.fbn / (double)s.fbd));
+    const double jn = sqrt((double)s.jx * s.jx + (double)s.jy * s.jy + (double)s.jz * s.jz);
+    if (jn > 0.0)
+        e = fmin(e, eta_jerk * sqrt((double)s.ax * s.ax + (double)s.ay * s.ay + (double)s.az * s.az) / jn);
+    return e;
+}
+
+__device__ __forceinline__ float rsqrt_f32_refined(float r2) {
+    const float y = rsqrt_hw(r2);
+    return y * fmaf(-0.5f * r2, y * y, 1.5f);
+}
+
+}  // namespace fsi
