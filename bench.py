@@ -476,18 +476,21 @@ def run_hhs(args):
     import torch
     from paper_2210_02472_b300 import fsi as F
     torch.cuda.set_device(0)
-    c = inputs.workload("kroupa64k") if not args.n else inputs.plummer(args.n, inputs.SEED_BASE + 2, imf="kroupa")
+    wl = args.workload if args.workload != "kroupa1m_bh16" or args.hhs_pn else "kroupa64k"
+    c = inputs.workload(wl) if not args.n else inputs.plummer(args.n, inputs.SEED_BASE + 2, imf="kroupa")
     dev = torch.device("cuda", 0)
     pos, vel = torch.as_tensor(c.pos).to(dev), torch.as_tensor(c.vel).to(dev)
     mass = torch.as_tensor(c.mass).to(dev)
-    ctx = F.Context(args.precision)
+    bh = torch.as_tensor(c.is_bh.astype(np.uint8)).to(dev)
+    cl = 1e4 if args.hhs_pn else 0.0
+    ctx = F.Context(args.precision, c=cl)
     e0 = F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum()
     F.fsi_work_stats(ctx, reset=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     levels = []
     for _ in range(args.intervals):
-        code = F.fsi_hhs_interval(ctx, pos, vel, mass, args.tau)
+        code = F.fsi_hhs_interval(ctx, pos, vel, mass, args.tau, is_bh=bh if cl > 0 else None)
         levels.append(F.fsi_level_stats(ctx))
     torch.cuda.synchronize()
     t = time.perf_counter() - t0
@@ -495,12 +498,12 @@ def run_hhs(args):
     e1 = F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum()
     inter = (acc_p * FLOP_ACC + grad_p * FLOP_GRAD) / FLOP_PAIR
     line = {
-        "metric": "HHS acc+grad pair interactions/s (N = 65536 Kroupa, tau0 = 1/64)",
+        "metric": f"HHS acc+grad pair interactions/s ({wl}, tau0 = {args.tau:g})",
         "value": inter / t, "unit": UNIT, "n_gpus": 1, "steps": args.intervals, "warmup": 0,
         "ms_per_step": 1e3 * t / args.intervals, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": "kroupa64k", "n": c.n, "tau": args.tau, "intervals": args.intervals},
+        "config": {"workload": wl, "n": c.n, "tau": args.tau, "intervals": args.intervals, "c": cl},
         "level_counts": levels, "rel_energy_error": abs((e1 - e0) / e0),
         "acc_pairs": acc_p, "grad_pairs": grad_p, "maxlevel_status": code,
     }
@@ -531,6 +534,7 @@ def main():
     ap.add_argument("--fd-components", type=int, default=3)
     ap.add_argument("--intervals", type=int, default=1)
     ap.add_argument("--tau", type=float, default=1.0 / 64)
+    ap.add_argument("--hhs-pn", action="store_true", help="HHS mode: PN1.0 on (c = 1e4)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

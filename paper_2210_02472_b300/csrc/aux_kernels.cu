@@ -252,33 +252,6 @@ cudaError_t launch_axpy3(int n, double* v, const double* a, double w, cudaStream
     return cudaGetLastError();
 }
 
-// ---------------------------------------------------------------------------------
-// PN1.0 pair acceleration (two-body 1PN EIH, harmonic coordinates), body i due to j:
-//   n = (x_i - x_j)/r,
-//   a = m_j/(c^2 r^2) { n [ -v_i^2 - 2 v_j^2 + 4 v_i.v_j + 1.5 (n.v_j)^2 + 5 m_i/r + 4 m_j/r ]
-//                      + (v_i - v_j) [ 4 n.v_i - 3 n.v_j ] }
-__device__ __forceinline__ void pn_pair(double xi, double yi, double zi, double vxi, double vyi,
-                                        double vzi, double mi, double xj, double yj, double zj,
-                                        double vxj, double vyj, double vzj, double mj, double ic2,
-                                        double& ax, double& ay, double& az, int* err) {
-    const double rx = xi - xj, ry = yi - yj, rz = zi - zj;
-    const double r2 = rx * rx + ry * ry + rz * rz;
-    if (r2 == 0.0) { set_error(err, FSI_ERR_NONFINITE); return; }
-    const double ir = 1.0 / sqrt(r2);
-    const double nx = rx * ir, ny = ry * ir, nz = rz * ir;
-    const double vi2 = vxi * vxi + vyi * vyi + vzi * vzi;
-    const double vj2 = vxj * vxj + vyj * vyj + vzj * vzj;
-    const double vivj = vxi * vxj + vyi * vyj + vzi * vzj;
-    const double nvi = nx * vxi + ny * vyi + nz * vzi;
-    const double nvj = nx * vxj + ny * vyj + nz * vzj;
-    const double cn = -vi2 - 2.0 * vj2 + 4.0 * vivj + 1.5 * nvj * nvj + (5.0 * mi + 4.0 * mj) * ir;
-    const double cv = 4.0 * nvi - 3.0 * nvj;
-    const double pre = mj * ic2 * ir * ir;
-    ax += pre * (cn * nx + cv * (vxi - vxj));
-    ay += pre * (cn * ny + cv * (vyi - vyj));
-    az += pre * (cn * nz + cv * (vzi - vzj));
-}
-
 // Ordered list of the black holes of a compact set (single CTA, warp-ballot scan).
 constexpr int kMaxBH = kMaxBHList;
 
@@ -439,6 +412,124 @@ cudaError_t launch_pn_pairs(int N, const double* pos, const double* vel, const d
 }
 
 // ---------------------------------------------------------------------------------
+// PN1.0 kicks between two disjoint sets of global ids (the slow-fast pairs of an HHS
+// level), through the black-hole sublists: for i in A, the terms of the black holes j of
+// B (pn_list_from_bh) plus, for a black hole i of A, the terms of every non-black-hole j
+// of B (pn_list_bh_from_all + finish).
+
+// Positions k of list L whose particle is a black hole, in list order (single CTA).
+__global__ void bh_sublist_kernel(int n, const int* __restrict__ L, const unsigned char* __restrict__ is_bh,
+                                  int* __restrict__ out, int* __restrict__ count, int* err) {
+    __shared__ int warp_tot[32];
+    __shared__ int base;
+    if (threadIdx.x == 0) base = 0;
+    __syncthreads();
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int k0 = 0; k0 < n; k0 += blockDim.x) {
+        const int k = k0 + threadIdx.x;
+        const bool f = k < n && is_bh[L[k]];
+        const unsigned b = __ballot_sync(0xffffffffu, f);
+        if (lane == 0) warp_tot[wid] = __popc(b);
+        __syncthreads();
+        int off = base;
+        for (int w = 0; w < wid; ++w) off += warp_tot[w];
+        off += __popc(b & ((1u << lane) - 1u));
+        if (f) {
+            if (off < kMaxBH) out[off] = k;
+            else set_error(err, FSI_ERR_UNSUPPORTED);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0)
+            for (int w = 0; w < nw; ++w) base += warp_tot[w];
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) *count = min(base, kMaxBH);
+}
+
+__global__ void pn_list_from_bh_kernel(long long N, const double* __restrict__ pos, const double* __restrict__ vel,
+                                       const double* __restrict__ mass, const int* __restrict__ A, int nA,
+                                       const int* __restrict__ B, const int* __restrict__ Bbh,
+                                       const int* __restrict__ nBbh, double ic2, double* __restrict__ out,
+                                       int* err) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= nA) return;
+    const int i = A[k];
+    const double xi = pos[i], yi = pos[N + i], zi = pos[2 * N + i];
+    const double ui = vel[i], vi = vel[N + i], wi = vel[2 * N + i];
+    double ax = 0, ay = 0, az = 0;
+    const int nb = *nBbh;
+    for (int q = 0; q < nb; ++q) {
+        const int j = B[Bbh[q]];
+        if (j == i) continue;
+        pn_pair(xi, yi, zi, ui, vi, wi, mass[i], pos[j], pos[N + j], pos[2 * N + j], vel[j], vel[N + j],
+                vel[2 * N + j], mass[j], ic2, ax, ay, az, err);
+    }
+    out[k] = ax;
+    out[(size_t)nA + k] = ay;
+    out[2 * (size_t)nA + k] = az;
+}
+
+__global__ void pn_list_bh_from_all_kernel(long long N, const double* __restrict__ pos, const double* __restrict__ vel,
+                                           const double* __restrict__ mass, const unsigned char* __restrict__ is_bh,
+                                           const int* __restrict__ A, const int* __restrict__ Abh,
+                                           const int* __restrict__ nAbh, const int* __restrict__ B, int nB,
+                                           double ic2, double* __restrict__ part, int* err) {
+    __shared__ double red[3][kB];
+    for (int b = blockIdx.y; b < *nAbh; b += gridDim.y) {
+        const int i = A[Abh[b]];
+        const double xi = pos[i], yi = pos[N + i], zi = pos[2 * N + i];
+        const double ui = vel[i], vi = vel[N + i], wi = vel[2 * N + i];
+        double sx = 0, sy = 0, sz = 0;
+        for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nB; q += gridDim.x * blockDim.x) {
+            const int j = B[q];
+            if (is_bh[j]) continue;
+            pn_pair(xi, yi, zi, ui, vi, wi, mass[i], pos[j], pos[N + j], pos[2 * N + j], vel[j],
+                    vel[N + j], vel[2 * N + j], mass[j], ic2, sx, sy, sz, err);
+        }
+        red[0][threadIdx.x] = sx; red[1][threadIdx.x] = sy; red[2][threadIdx.x] = sz;
+        __syncthreads();
+        for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+            if (threadIdx.x < w)
+                for (int c = 0; c < 3; ++c) red[c][threadIdx.x] += red[c][threadIdx.x + w];
+            __syncthreads();
+        }
+        if (threadIdx.x == 0)
+            for (int c = 0; c < 3; ++c) part[((size_t)b * 3 + c) * kPnCtas + blockIdx.x] = red[c][0];
+        __syncthreads();
+    }
+}
+
+__global__ void pn_list_bh_finish_kernel(const int* __restrict__ Abh, const int* __restrict__ nAbh, int nA,
+                                         const double* __restrict__ part, double* __restrict__ out) {
+    const int b = blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= *nAbh) return;
+    const int k = Abh[b];
+    for (int c = 0; c < 3; ++c) {
+        double s = 0;
+        for (int q = 0; q < kPnCtas; ++q) s += part[((size_t)b * 3 + c) * kPnCtas + q];
+        out[(size_t)c * nA + k] += s;
+    }
+}
+
+cudaError_t launch_pn_cross(long long N, const double* pos, const double* vel, const double* mass,
+                            const unsigned char* is_bh, double c, const int* A, int nA, const int* B,
+                            int nB, int* Abh, int* nAbh, int* Bbh, int* nBbh, double* outA,
+                            double* outB, double* part, int* err, cudaStream_t s) {
+    if (nA <= 0 || nB <= 0) return cudaSuccess;
+    const double ic2 = 1.0 / (c * c);
+    { bh_sublist_kernel<<<1, 1024, 0, s>>>(nA, A, is_bh, Abh, nAbh, err); note_launch(); }
+    { bh_sublist_kernel<<<1, 1024, 0, s>>>(nB, B, is_bh, Bbh, nBbh, err); note_launch(); }
+    { pn_list_from_bh_kernel<<<blocks_for(nA), kB, 0, s>>>(N, pos, vel, mass, A, nA, B, Bbh, nBbh, ic2, outA, err); note_launch(); }
+    { pn_list_from_bh_kernel<<<blocks_for(nB), kB, 0, s>>>(N, pos, vel, mass, B, nB, A, Abh, nAbh, ic2, outB, err); note_launch(); }
+    const dim3 g(kPnCtas, 32);
+    { pn_list_bh_from_all_kernel<<<g, kB, 0, s>>>(N, pos, vel, mass, is_bh, A, Abh, nAbh, B, nB, ic2, part, err); note_launch(); }
+    { pn_list_bh_finish_kernel<<<blocks_for(kMaxBH), kB, 0, s>>>(Abh, nAbh, nA, part, outA); note_launch(); }
+    { pn_list_bh_from_all_kernel<<<g, kB, 0, s>>>(N, pos, vel, mass, is_bh, B, Bbh, nBbh, A, nA, ic2, part, err); note_launch(); }
+    { pn_list_bh_finish_kernel<<<blocks_for(kMaxBH), kB, 0, s>>>(Bbh, nBbh, nB, part, outB); note_launch(); }
+    return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------------
 // Small O(n^2) FP64 loops (time steps, energy): thread per i, sources through shared
 // memory in plain cooperative tiles.
 constexpr int kAuxTile = 128;
@@ -540,8 +631,9 @@ __global__ void __launch_bounds__(kAuxTile) timesteps_mixed_kernel(
                 const float dy = (h.y - yh[u]) + (l.y - yl[u]);
                 const float dz = (h.z - zh[u]) + (l.z - zl[u]);
                 const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                const bool self = (j0 + t == me[u]);
-                coincident |= (!self && d2 == 0.f);
+                // lanes past the end hold a copy of particle n-1: compare clamped indices
+                const bool self = (j0 + t == min(me[u], n - 1));
+                coincident |= (!self && d2 == 0.f && me[u] < n);
                 if (self || d2 == 0.f) continue;
                 const float y = rsqrt_f32_refined(d2 + eps2f);
                 step_pair<float>(acc[u], dx, dy, dz, v.x - ui[u], v.y - vi[u], v.z - wi[u], d2, v.w,

@@ -244,7 +244,7 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     if (pn) {
         CK(ensure(c->ad, 3 * (size_t)n * 8));
         CK(ensure(c->apn, 3 * (size_t)n * 8));
-        CK(ensure(c->bhlist, kMaxBHList * 4));
+        CK(ensure(c->bhlist, 2 * kMaxBHList * 4));
         CK(ensure(c->nbh, 16));
         CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
         if (idx) {
@@ -376,10 +376,13 @@ int cross_pn_kick(fsi_ctx* c, int N, const double* pos, double* vel, const doubl
                   double w, cudaStream_t s) {
     CK(ensure(c->tA, 3 * (size_t)nS * 8));
     CK(ensure(c->tB, 3 * (size_t)nF * 8));
-    CU(launch_pn_pairs(N, pos, vel, mass, is_bh, c->p.c, Sids, nS, Fids, nF, P<double>(c->tA),
-                       c->err_d, s));
-    CU(launch_pn_pairs(N, pos, vel, mass, is_bh, c->p.c, Fids, nF, Sids, nS, P<double>(c->tB),
-                       c->err_d, s));
+    CK(ensure(c->bhlist, 2 * kMaxBHList * 4));
+    CK(ensure(c->nbh, 16));
+    CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
+    int* bl = P<int>(c->bhlist);
+    int* nb = P<int>(c->nbh);
+    CU(launch_pn_cross(N, pos, vel, mass, is_bh, c->p.c, Sids, nS, Fids, nF, bl, nb, bl + kMaxBHList,
+                       nb + 1, P<double>(c->tA), P<double>(c->tB), P<double>(c->pnpart), c->err_d, s));
     CU(launch_scatter_axpy3(N, P<double>(c->tA), Sids, nS, w, vel, s));
     CU(launch_scatter_axpy3(N, P<double>(c->tB), Fids, nF, w, vel, s));
     return FSI_OK;
@@ -449,7 +452,7 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
                           : std::min(c->p.hhs_small_max, small_max());
     auto recurse = [&]() -> int {
         if (nF <= 0) return FSI_OK;
-        if (nF <= small_cap && !pn) {
+        if (nF <= small_cap) {
             SmallArgs sa{};
             sa.ids = Fids; sa.n = nF; sa.pos = pos; sa.vel = vel; sa.mass = mass;
             sa.step0 = P<double>(c->step0); sa.N = N; sa.tau = 0.5 * tau; sa.level = level + 1;
@@ -459,6 +462,8 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
             sa.level_counts = st; sa.work = st + 64;
             sa.maxlevel_hit = reinterpret_cast<int*>(st + 66);
             sa.err = c->err_d;
+            sa.is_bh = is_bh;
+            sa.c = c->p.c;
             CU(launch_hhs_small(c->p.precision, sa, s));
             return FSI_OK;
         }
@@ -578,7 +583,7 @@ int fsi_reserve(fsi_ctx* c, int N, int n) {
     for (Buf* b : b3) CK(ensure(*b, 3 * (size_t)n * 8));
     CK(ensure(c->mc, (size_t)n * 8));
     CK(ensure(c->bhc, (size_t)n));
-    CK(ensure(c->bhlist, kMaxBHList * 4));
+    CK(ensure(c->bhlist, 2 * kMaxBHList * 4));
     CK(ensure(c->nbh, 16));
     CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
     CK(ensure(c->part, (size_t)64 * 3 * n * 8));

@@ -196,6 +196,8 @@ struct SmallArgs {
     unsigned long long* work;           // [0] acc pairs, [1] grad pairs
     int* maxlevel_hit;
     int* err;
+    const unsigned char* is_bh;     // PN1.0 pair flags (global id), used when c > 0
+    double c;
 };
 
 // ---------------------------------------------------------------------------------
@@ -248,6 +250,13 @@ cudaError_t launch_bh_list(int n, const unsigned char* bhc, int* bh_list, int* n
 cudaError_t launch_pn(int n, const double* xc, const double* vc, const double* mc,
                       const unsigned char* bhc, double c, const int* bh_list, const int* n_bh,
                       int max_bh, double* apn, double* part, int* err, cudaStream_t s);
+// PN1.0 accelerations of the pairs between disjoint id lists A and B (pairs with a black
+// hole): outA (3 x nA) and outB (3 x nB) overwritten.  Abh/Bbh: kMaxBHList ints each,
+// nAbh/nBbh: one int each (workspace); part: kMaxBHList * 3 * kPnPartCtas doubles.
+cudaError_t launch_pn_cross(long long N, const double* pos, const double* vel, const double* mass,
+                            const unsigned char* is_bh, double c, const int* A, int nA, const int* B,
+                            int nB, int* Abh, int* nAbh, int* Bbh, int* nBbh, double* outA,
+                            double* outB, double* part, int* err, cudaStream_t s);
 cudaError_t launch_pn_pairs(int N, const double* pos, const double* vel, const double* mass,
                             const unsigned char* is_bh, double c, const int* A, int nA,
                             const int* B, int nB, double* out, int* err, cudaStream_t s);

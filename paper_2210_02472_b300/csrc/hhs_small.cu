@@ -35,6 +35,7 @@ struct SmallSmem {
     typename std::conditional<P == FSI_MIXED, RecMix, D4>::type rec[kSmallMax];
     typename std::conditional<P == FSI_MIXED, float4, D4>::type arec[kSmallMax];
     float4 vf[kSmallMax];                   // FP32 (vx, vy, vz, m) for the mixed time steps
+    unsigned char bh[kSmallMax];            // black-hole flags (PN1.0 pairs)
     unsigned short lists[kSmallLists];      // per frame on the path: its S list then its F list
     Frame fr[kSmallDepth];
     int wsum[32];
@@ -172,9 +173,61 @@ __device__ void small_drift(SmallSmem<P>& S, const unsigned short* L, int n, dou
     write_rec<P>(S, k);
 }
 
-// One FSI cycle of list L on itself (Sect. 2.1, Eq. fsi-cycle).
+// PN1.0 accelerations (into g) of list A from list B, pairs with a black hole, j != i.
+template <int P>
+__device__ void small_pn(SmallSmem<P>& S, const unsigned short* A, int nA, const unsigned short* B,
+                         int nB, const SmallArgs& a) {
+    const int t = threadIdx.x;
+    if (t >= nA) return;
+    const int i = A[t];
+    const double ic2 = 1.0 / (a.c * a.c);
+    double px = 0, py = 0, pz = 0;
+    for (int q = 0; q < nB; ++q) {
+        const int j = B[q];
+        if (j == i || (!S.bh[i] && !S.bh[j])) continue;
+        pn_pair(S.x[0][i], S.x[1][i], S.x[2][i], S.v[0][i], S.v[1][i], S.v[2][i], S.m[i], S.x[0][j],
+                S.x[1][j], S.x[2][j], S.v[0][j], S.v[1][j], S.v[2][j], S.m[j], ic2, px, py, pz, a.err);
+    }
+    S.g[0][i] = px;
+    S.g[1][i] = py;
+    S.g[2][i] = pz;
+}
+
+template <int P>
+__device__ void small_kick_g(SmallSmem<P>& S, const unsigned short* L, int n, double w) {
+    const int t = threadIdx.x;
+    if (t >= n) return;
+    const int k = L[t];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) S.v[c][k] = fma(w, S.g[c][k], S.v[c][k]);
+    if constexpr (P == FSI_MIXED) S.vf[k] = make_float4((float)S.v[0][k], (float)S.v[1][k], (float)S.v[2][k], (float)S.m[k]);
+}
+
+// PN1.0 kick of weight w: within list L (B == nullptr) or between disjoint L and B; all PN
+// accelerations from the velocities at the start of the kick (Sect. 3.9).
+template <int P>
+__device__ void small_pn_kick(SmallSmem<P>& S, const unsigned short* L, int n, const unsigned short* B,
+                              int nB, double w, const SmallArgs& a) {
+    if (!(a.c > 0.0)) return;
+    if (B == nullptr) {
+        small_pn<P>(S, L, n, L, n, a);
+        __syncthreads();
+        small_kick_g<P>(S, L, n, w);
+    } else {
+        small_pn<P>(S, L, n, B, nB, a);
+        small_pn<P>(S, B, nB, L, n, a);
+        __syncthreads();
+        small_kick_g<P>(S, L, n, w);
+        small_kick_g<P>(S, B, nB, w);
+    }
+    __syncthreads();
+}
+
+// One FSI cycle of list L on itself (Sect. 2.1, Eq. fsi-cycle), wrapped in PN1.0
+// half-kicks when c > 0 (Sect. 3.9).
 template <int P>
 __device__ void small_fsi(SmallSmem<P>& S, const unsigned short* L, int n, double h, const SmallArgs& a) {
+    small_pn_kick<P>(S, L, n, nullptr, 0, 0.5 * h, a);
     small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
     small_kick<P>(S, L, n, h / 6.0, false, 0.0); __syncthreads();
     small_drift<P>(S, L, n, 0.5 * h); __syncthreads();
@@ -186,6 +239,7 @@ __device__ void small_fsi(SmallSmem<P>& S, const unsigned short* L, int n, doubl
     small_drift<P>(S, L, n, 0.5 * h); __syncthreads();
     small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
     small_kick<P>(S, L, n, h / 6.0, false, 0.0); __syncthreads();
+    small_pn_kick<P>(S, L, n, nullptr, 0, 0.5 * h, a);
 }
 
 // Inter-level kick of S and F (Sect. 2.2); gradient: the gradient acceleration of the
@@ -259,6 +313,7 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
         S.s0[t] = a.step0[i];
         write_rec<P>(S, t);
         S.vf[t] = make_float4((float)S.v[0][t], (float)S.v[1][t], (float)S.v[2][t], (float)S.m[t]);
+        S.bh[t] = (a.c > 0.0 && a.is_bh) ? a.is_bh[i] : 0;
         S.lists[t] = (unsigned short)t;                 // the root's set
     }
     if (t == 0) {
@@ -297,7 +352,10 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
             f.offS = lt; f.nS = nS; f.offF = lt + nS; f.nF = nF;
             const unsigned short* Ls = S.lists + f.offS;
             const unsigned short* Lf = S.lists + f.offF;
-            if (nS > 0 && nF > 0) small_cross<P>(S, Ls, nS, Lf, nF, f.tau / 6.0, false, 0.0, a);
+            if (nS > 0 && nF > 0) {
+                small_pn_kick<P>(S, Ls, nS, Lf, nF, 0.5 * f.tau, a);
+                small_cross<P>(S, Ls, nS, Lf, nF, f.tau / 6.0, false, 0.0, a);
+            }
             if (nS > 0) small_fsi<P>(S, Ls, nS, 0.5 * f.tau, a);
             f.stage = 1;
         } else if (f.stage == 1) {
@@ -309,7 +367,10 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
             const unsigned short* Ls = S.lists + f.offS;
             const unsigned short* Lf = S.lists + f.offF;
             if (f.nS > 0) small_fsi<P>(S, Ls, f.nS, 0.5 * f.tau, a);
-            if (f.nS > 0 && f.nF > 0) small_cross<P>(S, Ls, f.nS, Lf, f.nF, f.tau / 6.0, false, 0.0, a);
+            if (f.nS > 0 && f.nF > 0) {
+                small_cross<P>(S, Ls, f.nS, Lf, f.nF, f.tau / 6.0, false, 0.0, a);
+                small_pn_kick<P>(S, Ls, f.nS, Lf, f.nF, 0.5 * f.tau, a);
+            }
             f.stage = 3;
         }
         __syncthreads();

@@ -160,3 +160,34 @@ __device__ __forceinline__ float rsqrt_f32_refined(float r2) {
 }
 
 }  // namespace fsi
+
+namespace fsi {
+
+// ---------------------------------------------------------------------------------
+// PN1.0 pair acceleration (two-body 1PN EIH, harmonic coordinates), body i due to j:
+//   n = (x_i - x_j)/r,
+//   a = m_j/(c^2 r^2) { n [ -v_i^2 - 2 v_j^2 + 4 v_i.v_j + 1.5 (n.v_j)^2 + 5 m_i/r + 4 m_j/r ]
+//                      + (v_i - v_j) [ 4 n.v_i - 3 n.v_j ] }
+__device__ __forceinline__ void pn_pair(double xi, double yi, double zi, double vxi, double vyi,
+                                        double vzi, double mi, double xj, double yj, double zj,
+                                        double vxj, double vyj, double vzj, double mj, double ic2,
+                                        double& ax, double& ay, double& az, int* err) {
+    const double rx = xi - xj, ry = yi - yj, rz = zi - zj;
+    const double r2 = rx * rx + ry * ry + rz * rz;
+    if (r2 == 0.0) { set_error(err, FSI_ERR_NONFINITE); return; }
+    const double ir = 1.0 / sqrt(r2);
+    const double nx = rx * ir, ny = ry * ir, nz = rz * ir;
+    const double vi2 = vxi * vxi + vyi * vyi + vzi * vzi;
+    const double vj2 = vxj * vxj + vyj * vyj + vzj * vzj;
+    const double vivj = vxi * vxj + vyi * vyj + vzi * vzj;
+    const double nvi = nx * vxi + ny * vyi + nz * vzi;
+    const double nvj = nx * vxj + ny * vyj + nz * vzj;
+    const double cn = -vi2 - 2.0 * vj2 + 4.0 * vivj + 1.5 * nvj * nvj + (5.0 * mi + 4.0 * mj) * ir;
+    const double cv = 4.0 * nvi - 3.0 * nvj;
+    const double pre = mj * ic2 * ir * ir;
+    ax += pre * (cn * nx + cv * (vxi - vxj));
+    ay += pre * (cn * ny + cv * (vyi - vyj));
+    az += pre * (cn * nz + cv * (vzi - vzj));
+}
+
+}  // namespace fsi

@@ -355,6 +355,7 @@ def test_timesteps_and_energy(F):
         e = host(F.fsi_energy(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
         P = inputs.random_subset(1500, 400, 7)
         sp = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
     assert np.abs(s / ref - 1).max() < 1e-12
     assert np.abs(sp / oracle.timesteps(c.pos, c.vel, c.mass, P) - 1).max() < 1e-12
     assert abs(e[0] / T - 1) < 1e-13 and abs(e[1] / W - 1) < 1e-12
@@ -365,6 +366,7 @@ def test_timesteps_mixed(F):
     ref = oracle.timesteps(c.pos, c.vel, c.mass)
     with F.Context("mixed") as ctx:
         s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
     assert np.abs(s / ref - 1).max() < 2e-5
 
 
@@ -382,11 +384,44 @@ def test_hhs_interval(F, prec, small):
         lv = F.fsi_level_stats(ctx)
         p, v = host(p), host(v)
         assert code == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
     used = np.nonzero(counts)[0].max() + 1
     assert lv[:used] == list(counts[:used])
     tol = 1e-11 if prec == "fp64" else 1e-7
     assert np.abs(p - rp).max() <= tol
     assert np.abs(v - rv).max() <= tol * 100
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("small", [0, -1])
+def test_hhs_interval_with_pn(F, prec, small):
+    """HHS with the PN1.0 pair term (4 black holes, c = 30): S-S half-kicks around every
+    FSI(S, .) step and S-F kicks with the opening and closing U_SF."""
+    c = inputs.plummer(500, 26, imf="kroupa", n_bh=4)
+    tau, cl = 1.0 / 16, 30.0
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, c=cl, is_bh=c.is_bh)
+    with F.Context(prec, c=cl, hhs_small_max=small) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau, is_bh=dev(c.is_bh, torch.uint8))
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    if prec == "fp64":
+        assert np.abs(p - rp).max() <= 1e-11
+        assert np.abs(v - rv).max() <= 1e-9
+    else:
+        # The close black-hole encounters here are chaotic: in the FP64 oracle itself a
+        # relative perturbation of 1e-9 (1e-7) of the initial positions changes the final
+        # velocity of the most sensitive particle by 9e-6 (1.3e-3) of its speed within
+        # this one interval.  The mixed path's ~1e-7 force errors are amplified the same
+        # way, so its bound is 1e-3 of max(|v|, 1); the FP64 path shows no amplification
+        # of its ~1e-16 differences beyond the bound above.
+        assert np.abs(p - rp).max() <= 1e-5
+        sp = np.maximum(np.linalg.norm(rv, axis=0), 1.0)
+        assert (np.abs(v - rv).max(axis=0) / sp).max() <= 1e-3
 
 
 # ----------------------------------------------------------------------------- full size
