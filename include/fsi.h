@@ -260,6 +260,27 @@ int fsi_autotune(fsi_ctx *ctx, int N, const double *pos, const double *mass, int
 int fsi_get_tuning(fsi_ctx *ctx, int *ipt_acc, int *ipt_grad);
 int fsi_set_tuning(fsi_ctx *ctx, int ipt_acc, int ipt_grad);
 
+/* ---- context-free, allocation-free variant ------------------------------------------- */
+
+/* The paper has no counterpart: this entry point exists for callers that cannot allocate
+ * device memory -- code under a host framework that owns every device allocation, or
+ * code that must not allocate inside a region that will be captured into a CUDA graph.
+ * It computes the same Newtonian accelerations as fsi_accel with an FP64 context for the
+ * self-interaction of all N particles (A = B = all):
+ *   acc_out[:, i] = sum_{j != i} m_j (r_j - r_i) / (|r_j - r_i|^2 + eps2)^{3/2},
+ * pos: 3 x N, mass: N, acc_out: 3 x N, all device pointers owned by the caller.
+ * It calls no allocating routine.  Its scratch (packed source records and split partial
+ * sums) is a fixed array in the library's device image, 4 MiB on every GPU that loads the
+ * library, held until the process exits.  Limit: N <= 32768; larger N returns FSI_ERR_ARG
+ * with a message in fsi_last_error, and nothing is launched.  All calls share the array:
+ * each call rewrites every scratch byte it reads (nothing needs clearing), and calls that
+ * overlap on the GPU (unordered streams) race on it.  The first call on a device looks
+ * the array's device address up (cudaGetSymbolAddress) and caches it; make that first
+ * call before any stream capture.  Device-side errors (non-finite results) are not
+ * latched anywhere: check the outputs.  Asynchronous on `stream`. */
+int fsi_accel_noalloc(int N, const double *pos, const double *mass, double eps2,
+                      double *acc_out, void *stream);
+
 /* ---- instrumentation ------------------------------------------------------------ */
 
 /* Start (enable = 1) or stop (0) recording a CUDA event pair around every pair-kernel

@@ -21,6 +21,11 @@ std::atomic<long long> g_launches{0};
 
 void fsi::note_launch() { g_launches.fetch_add(1, std::memory_order_relaxed); }
 
+namespace fsi {
+// Records a host-side error message for fsi_last_error (used by the context-free entry point).
+int set_last_error(int code, const char* msg);
+}
+
 namespace {
 
 thread_local std::string g_err = "";
@@ -497,6 +502,8 @@ struct fsi_batch {
     Buf rec0, rec1, accrec, ac, done, ctrl;
     std::vector<long long> off;
 };
+
+int fsi::set_last_error(int code, const char* msg) { return fail(code, "%s", msg); }
 
 // =================================================================================
 extern "C" {

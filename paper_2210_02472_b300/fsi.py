@@ -41,7 +41,7 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall",
-            "fsi_work_stats"]
+            "fsi_work_stats", "fsi_accel_noalloc"]
 
 
 class fsi_params(C.Structure):
@@ -72,6 +72,7 @@ _lib.fsi_level_stats.argtypes = [_vp, C.POINTER(C.c_longlong), _ip]
 _lib.fsi_profile.argtypes = [_vp, _ip]
 _lib.fsi_profile_read.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
 _lib.fsi_launch_count.restype = C.c_longlong
+_lib.fsi_accel_noalloc.argtypes = [_ip, _vp, _vp, _dp, _vp, _vp]
 _lib.fsi_work_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip]
 _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
@@ -406,3 +407,16 @@ def fsi_work_stats(ctx: Context, reset: bool = False):
     a, g = C.c_longlong(), C.c_longlong()
     _check(_lib.fsi_work_stats(ctx.handle, C.byref(a), C.byref(g), int(bool(reset))), "fsi_work_stats")
     return int(a.value), int(g.value)
+
+
+def fsi_accel_noalloc(pos, mass, eps2: float = 0.0, out=None, stream=None):
+    """FP64 accelerations of all N particles with no context and no device allocation by
+    the library (fixed 4 MiB scratch in the library; N <= 32768).  `out` (3, N) must be
+    supplied by callers that cannot allocate; otherwise it is created here with torch."""
+    N = mass.numel()
+    if out is None:
+        out = torch.empty((3, N), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_accel_noalloc(N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
+                                  float(eps2), _f64(out, (3, N), "out"), _stream(stream)),
+           "fsi_accel_noalloc")
+    return out
