@@ -152,6 +152,24 @@ def dist_init():
     return rank, ws, local, None
 
 
+def reduce_max(value: float, dist, device=None) -> float:
+    """Max of a per-rank float over all ranks (identity without a process group).  Uses a
+    CPU tensor with gloo and a device tensor with NCCL."""
+    if dist is None:
+        return float(value)
+    import torch
+    on_cpu = dist.get_backend() == "gloo" or device is None
+    t = torch.tensor([float(value)], dtype=torch.float64,
+                     device="cpu" if on_cpu else device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(units_per_rank: float, world_size: int, t_max: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return units_per_rank * world_size / t_max
+
+
 def run_reference(args):
     rank, ws, local, dist = dist_init()
     if rank != 0:
@@ -244,13 +262,9 @@ def run_fsi(args):
     if F.fsi_sync_status(ctx) != F.FSI_OK:
         raise SystemExit("device error in the timed region")
     step_ms = [a.elapsed_time(b) for a, b in ev]
-    t_dev = sum(step_ms) / 1e3
-    if dist:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = reduce_max(sum(step_ms) / 1e3, dist, dev)
     inter = step_interactions(N) * args.steps
-    value = inter * ws / t_dev
+    value = job_value(inter, ws, t_dev)
 
     # ---- end to end through the C ABI with host buffers (pinned), copies timed
     hpos = torch.as_tensor(c.pos).pin_memory()
@@ -269,12 +283,8 @@ def run_fsi(args):
         opos.copy_(pos, non_blocking=True)
         ovel.copy_(vel, non_blocking=True)
     torch.cuda.synchronize()
-    t_e2e = time.perf_counter() - t0
-    if dist:
-        tt = torch.tensor([t_e2e], dtype=torch.float64, device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
-    e2e_value = step_interactions(N) * e2e_steps * ws / t_e2e
+    t_e2e = reduce_max(time.perf_counter() - t0, dist, dev)
+    e2e_value = job_value(step_interactions(N) * e2e_steps, ws, t_e2e)
     bytes_io = 2 * 3 * N * 8
 
     # ---- roofline of the dominant pair kernel (FP32 pipe bound for the mixed path)
