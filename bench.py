@@ -224,7 +224,11 @@ def run_fsi(args):
     cl = 1e4
     ctx = F.Context(args.precision, c=cl)
     F.fsi_reserve(ctx, N, N)
-    tuning = F.fsi_autotune(ctx, pos, mass, n=min(N, 1 << 18))   # variant per kernel kind
+    if args.tuning:
+        tuning = tuple(int(x) for x in args.tuning.split(","))
+        F.fsi_set_tuning(ctx, *tuning)
+    else:
+        tuning = F.fsi_autotune(ctx, pos, mass, n=min(N, 1 << 18))   # variant per kernel kind
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
@@ -294,8 +298,11 @@ def run_fsi(args):
     achieved = (float(N) * (N - 1) * kinds[dom]) / (ms / nl / 1e3) / 1e12
     peak_mhz = SM_MAX_MHZ
     peak = fp32_peak_tflops(peak_mhz) if args.precision == "mixed" else args.fp64_peak_tflops
+    var = tuning[0 if dom == "acc" else 1]
+    kname = (f"sym_mixed_v2_kernel<{dom}, I={var & 15}>" if var & 32 else
+             f"sym_pair_kernel<{args.precision}, {dom}, I={var & 15}>")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": f"pair_kernel<{args.precision},{dom}>",
+                "frac": achieved / peak, "traffic": None, "kernel": kname,
                 "peak_basis": ("148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"
                                if args.precision == "mixed" else "FP64 FMA probe"),
                 "per_kernel_ms": {k: prof[k][1] / max(prof[k][0], 1) for k in prof},
@@ -536,6 +543,8 @@ def main():
     ap.add_argument("--ref-rows", type=int, default=1024)
     ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--tuning", default="", help="fixed pair-kernel variants 'acc,grad' "
+                    "(see fsi_set_tuning); default: autotune on a 2^18 sample")
     ap.add_argument("--mode", default="cycle", choices=["cycle", "ensemble", "vjp", "hhs"],
                     help="cycle: the headline FSI-cycle benchmark; the others measure the "
                          "ensemble, adjoint and HHS workloads")

@@ -245,18 +245,21 @@ int fsi_level_stats(fsi_ctx *ctx, long long *counts, int max);
 /* ---- tuning ----------------------------------------------------------------------- */
 
 /* Autotuner: times every built variant of the acceleration and gradient pair kernels
- * (context precision) on the first n particles of pos/mass as one self-interacting set,
+ * (context precision; the symmetric kernels when fsi_params.symmetric, else the
+ * one-sided ones) on the first n particles of pos/mass as one self-interacting set,
  * `reps` timed launches each after one warm-up, and keeps the fastest in the context.
- * A variant is the number of active particles each thread holds in registers (1-4),
- * plus 16 for mixed kernels that carry their per-tile partial sums as float-float
- * pairs (FP32 pipe) instead of adding them in FP64.  Synchronous.  (The source-split
- * factor is chosen per launch from the grid's wave count, or fixed by
- * fsi_params.split.) */
+ * A variant is the number of active particles each thread holds in registers (low 4
+ * bits, 1-6); one-sided mixed kernels add 16 to carry their per-tile partial sums as
+ * float-float pairs instead of FP64; symmetric mixed kernels add 32 for the second form
+ * (FP64 sums in shared memory, select-free source reduce-scatter).  Synchronous.  (The
+ * source-split factor of one-sided passes is chosen per launch from the wave count, or
+ * fixed by fsi_params.split.) */
 int fsi_autotune(fsi_ctx *ctx, int N, const double *pos, const double *mass, int n, int reps,
                  void *stream);
 
-/* Read / set the pair-kernel variants (acc, grad) of the context precision.
- * fsi_set_tuning rejects variants the library was not built with (FSI_ERR_ARG). */
+/* Read / set the pair-kernel variants (acc, grad) of the context precision and mode
+ * (symmetric or one-sided).  fsi_set_tuning rejects variants the library was not built
+ * with (FSI_ERR_ARG). */
 int fsi_get_tuning(fsi_ctx *ctx, int *ipt_acc, int *ipt_grad);
 int fsi_set_tuning(fsi_ctx *ctx, int ipt_acc, int ipt_grad);
 

@@ -76,7 +76,8 @@ struct fsi_ctx {
     std::vector<long long> level_counts;
     int max_level_used = 0;
     int max_level_hit = 0;
-    int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] pair-kernel variant (see pair_variants)
+    int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] one-sided kernel variant (pair_variants)
+    int symv[2][2] = {{2, 2}, {4, 2}};  // [precision][kind] symmetric kernel variant (sym_variants)
     long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
     // instrumentation: event pairs around pair-kernel launches
     struct ProfRec { int kind; cudaEvent_t a, b; };
@@ -180,13 +181,14 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
         a.iacc == a.jacc) {
         // self-interaction of one set: every unordered pair once, then the epilogue
         const int n = a.n_i;
+        const int sv = c->symv[prec][kind];
         CK(ensure(c->accum, 3 * (size_t)n * sizeof(double)));
         CU(cudaMemsetAsync(c->accum.p, 0, 3 * (size_t)n * sizeof(double), s));
-        const int chunk = choose_chunk(c, n, variant_ipt(ipt));
+        const int chunk = choose_chunk(c, n, variant_ipt(sv));
         a.err = c->err_d;
         a.timeout_ns = budget(c);
         CK(timed(c, kind, s, [&] {
-            return launch_sym_pair(prec, kind, ipt, a.irec, a.iacc, n, a.eps2, chunk,
+            return launch_sym_pair(prec, kind, sv, a.irec, a.iacc, n, a.eps2, chunk,
                                    P<double>(c->accum), a.err, a.timeout_ns, s);
         }));
         a.part = P<double>(c->accum);
@@ -1135,13 +1137,14 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
     const bool was = c->profiling;
     c->profiling = false;
     int rc = FSI_OK;
+    int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
     for (int kind = 0; kind < 2 && rc == FSI_OK; ++kind) {
         int cand[8];
-        const int nc = pair_variants(prec, kind, cand);
+        const int nc = c->p.symmetric ? sym_variants(prec, kind, cand) : pair_variants(prec, kind, cand);
         float best = 3.4e38f;
-        int best_ipt = c->ipt[prec][kind];
+        int best_ipt = table[prec][kind];
         for (int v = 0; v < nc && rc == FSI_OK; ++v) {
-            c->ipt[prec][kind] = cand[v];
+            table[prec][kind] = cand[v];
             PairArgs a{};
             a.irec = a.jrec = c->rec[0].p;
             a.iacc = a.jacc = c->accrec[0].p;
@@ -1162,7 +1165,7 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
             cudaEventElapsedTime(&ms, e0, e1);
             if (ms < best) { best = ms; best_ipt = cand[v]; }
         }
-        c->ipt[prec][kind] = best_ipt;
+        table[prec][kind] = best_ipt;
     }
     c->profiling = was;
     cudaEventDestroy(e0);
@@ -1172,8 +1175,9 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
 
 int fsi_get_tuning(fsi_ctx* c, int* ipt_acc, int* ipt_grad) {
     if (!c) return fail(FSI_ERR_ARG, "NULL context");
-    if (ipt_acc) *ipt_acc = c->ipt[c->p.precision][KIND_ACC];
-    if (ipt_grad) *ipt_grad = c->ipt[c->p.precision][KIND_GRAD];
+    int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
+    if (ipt_acc) *ipt_acc = table[c->p.precision][KIND_ACC];
+    if (ipt_grad) *ipt_grad = table[c->p.precision][KIND_GRAD];
     return FSI_OK;
 }
 
@@ -1183,13 +1187,14 @@ int fsi_set_tuning(fsi_ctx* c, int ipt_acc, int ipt_grad) {
     const int prec = c->p.precision;
     for (int kind = 0; kind < 2; ++kind) {
         const int want = kind == KIND_ACC ? ipt_acc : ipt_grad;
-        const int nc = pair_variants(prec, kind, cand);
+        const int nc = c->p.symmetric ? sym_variants(prec, kind, cand) : pair_variants(prec, kind, cand);
         bool ok = false;
         for (int v = 0; v < nc; ++v) ok |= cand[v] == want;
-        if (!ok) return fail(FSI_ERR_ARG, "unsupported particles-per-thread %d", want);
+        if (!ok) return fail(FSI_ERR_ARG, "unsupported kernel variant %d", want);
     }
-    c->ipt[prec][KIND_ACC] = ipt_acc;
-    c->ipt[prec][KIND_GRAD] = ipt_grad;
+    int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
+    table[prec][KIND_ACC] = ipt_acc;
+    table[prec][KIND_GRAD] = ipt_grad;
     return FSI_OK;
 }
 

@@ -218,6 +218,9 @@ cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, c
 // Supported ipt values for (precision, kind): writes up to 8 into out, returns the count.
 int pair_variants(int precision, int kind, int* out);
 int pair_default_ipt(int precision, int kind);
+// Variants of the symmetric kernels: active particles per thread (low 4 bits), + 32 for the
+// mixed second form (FP64 sums in shared memory, select-free reduce-scatter).
+int sym_variants(int precision, int kind, int* out);
 int variant_ipt(int variant);
 
 cudaError_t launch_pack(int precision, int N, const double* pos, const double* mass,

@@ -745,6 +745,211 @@ __global__ void __launch_bounds__(kThreads, 2) sym_pair_kernel(const SymArgs a) 
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Symmetric mixed kernel, second form (autotuned against the first):
+//  - the FP64 per-particle sums live in shared memory (one slot per thread and particle),
+//    so a thread can hold up to 6 active particles in registers;
+//  - inside each group of 4 sources, lane l visits source (g XOR (l >> 3)) at step g, so
+//    after the pair loop slot s of lane l holds the partial of source s ^ (l >> 3); the
+//    warp reduce-scatter then needs no selects: at the xor-16 level every lane keeps slots
+//    0, 1 and sends 2, 3, at the xor-8 level keeps slot 0 and sends 1, and three butterfly
+//    levels finish; lane l ends with the total of source l >> 3.  The 4 sources read at one
+//    step are 4 consecutive records, so the shared-memory loads stay conflict-free.
+template <int KIND, int I>
+__global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs a) {
+    static_assert(kThreads == kTileJ, "an i-block spans I source tiles");
+    constexpr int ACCREC = SymCfg<FSI_MIXED, KIND>::ACCREC;
+    constexpr int SB = SymCfg<FSI_MIXED, KIND>::SB;
+    constexpr int JPART = SymCfg<FSI_MIXED, KIND>::JPART;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    float* jpart = reinterpret_cast<float*>(smem + kStages * SB);
+    double* acc_s = reinterpret_cast<double*>(smem + kStages * SB + JPART);   // [I][3][kThreads]
+
+    const int b = blockIdx.x / (1 + a.nchunk);
+    const int c = blockIdx.x % (1 + a.nchunk);
+    const int ntj = (a.n + kTileJ - 1) / kTileJ;
+    const bool diag = (c == 0);
+    int t0, t1;
+    if (diag) { t0 = b * I; t1 = min((b + 1) * I, ntj); }
+    else { t0 = (b + 1) * I + (c - 1) * a.chunk; t1 = min(t0 + a.chunk, ntj); }
+    if (t0 >= t1) return;
+    const int ntiles = t1 - t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, L = lane >> 3;
+    const int i0 = b * (kThreads * I);
+
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int st = t % kStages;
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n - jt);
+        unsigned char* base = smem + st * SB;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC));
+        bulk_g2s(base, (const unsigned char*)a.rec + (size_t)jt * kRec, (uint32_t)cnt * kRec, &bars[st]);
+        if (ACCREC)
+            bulk_g2s(base + kTileJ * kRec, (const unsigned char*)a.accrec + (size_t)jt * ACCREC,
+                     (uint32_t)cnt * ACCREC, &bars[st]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+
+    SymMixI pi[I];
+    float f[I][3];
+    int my_i[I];
+    bool valid[I];
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        my_i[u] = i0 + u * kThreads + tid;
+        valid[u] = my_i[u] < a.n;
+        const int i = min(my_i[u], a.n - 1);
+        const RecMix r = reinterpret_cast<const RecMix*>(a.rec)[i];
+        pi[u].xh = r.hi.x; pi[u].yh = r.hi.y; pi[u].zh = r.hi.z;
+        pi[u].xl = r.lo.x; pi[u].yl = r.lo.y; pi[u].zl = r.lo.z;
+        pi[u].nA = valid[u] ? -r.hi.w : 0.f;
+        pi[u].nB = valid[u] ? -r.lo.w : 0.f;
+        if constexpr (KIND == KIND_GRAD) {
+            const float4 ai = reinterpret_cast<const float4*>(a.accrec)[i];
+            pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
+            pi[u].nm = valid[u] ? -ai.w : 0.f;
+        } else {
+            pi[u].ax = pi[u].ay = pi[u].az = pi[u].nm = 0.f;
+        }
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            f[u][q] = 0.f;
+            acc_s[(u * 3 + q) * kThreads + tid] = 0.0;
+        }
+    }
+    const float eps2f = (float)a.eps2;
+    bool aborted = false;
+    int t_stop = ntiles;
+    for (int t = 0; t < ntiles; ++t) {
+        const int st = t % kStages;
+        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n - jt);
+        const unsigned char* base = smem + st * SB;
+        const RecMix* rec = reinterpret_cast<const RecMix*>(base);
+        const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
+        if (diag) {
+            MixI q[I];
+#pragma unroll
+            for (int u = 0; u < I; ++u) {
+                q[u].xh = pi[u].xh; q[u].yh = pi[u].yh; q[u].zh = pi[u].zh;
+                q[u].xl = pi[u].xl; q[u].yl = pi[u].yl; q[u].zl = pi[u].zl;
+                q[u].ax = pi[u].ax; q[u].ay = pi[u].ay; q[u].az = pi[u].az;
+            }
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 h = rec[jj].hi;
+                const float4 l = rec[jj].lo;
+                if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                    for (int u = 0; u < I; ++u)
+                        mix_acc_pair<true>(h, l, q[u], eps2f, jt + jj == my_i[u], f[u][0], f[u][1], f[u][2]);
+                } else {
+                    const float4 aj = arec[jj];
+#pragma unroll
+                    for (int u = 0; u < I; ++u)
+                        mix_grad_pair<true>(h, l, aj, q[u], eps2f, jt + jj == my_i[u], f[u][0], f[u][1], f[u][2]);
+                }
+            }
+        } else {
+            for (int jj = 0; jj < cnt; jj += 4) {
+                float fj[4][3];
+#pragma unroll
+                for (int g = 0; g < 4; ++g) {
+                    fj[g][0] = fj[g][1] = fj[g][2] = 0.f;
+                    const int jg = jj + (g ^ L);
+                    if (jg < cnt) {
+                        const float4 h = rec[jg].hi;
+                        const float4 l = rec[jg].lo;
+                        if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                            for (int u = 0; u < I; ++u) mix_acc_sym(h, l, pi[u], eps2f, f[u], fj[g]);
+                        } else {
+                            const float4 aj = arec[jg];
+#pragma unroll
+                            for (int u = 0; u < I; ++u) mix_grad_sym(h, l, aj, pi[u], eps2f, f[u], fj[g]);
+                        }
+                    }
+                }
+                float tot[3];
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float k0 = fj[0][q] + __shfl_xor_sync(0xffffffffu, fj[2][q], 16);
+                    const float k1 = fj[1][q] + __shfl_xor_sync(0xffffffffu, fj[3][q], 16);
+                    float r = k0 + __shfl_xor_sync(0xffffffffu, k1, 8);
+                    r += __shfl_xor_sync(0xffffffffu, r, 4);
+                    r += __shfl_xor_sync(0xffffffffu, r, 2);
+                    r += __shfl_xor_sync(0xffffffffu, r, 1);
+                    tot[q] = r;
+                }
+                const int jl = jj + L;
+                if ((lane & 7) == 0 && jl < cnt) {
+                    float* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
+                    dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+                }
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < I; ++u)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                acc_s[(u * 3 + q) * kThreads + tid] += (double)f[u][q];
+                f[u][q] = 0.f;
+            }
+        if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+        if (!diag && tid < cnt) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float sum = 0.f;
+#pragma unroll
+                for (int w = 0; w < kThreads / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
+                red_add(a.accum + (size_t)q * a.n + jt + tid, (double)sum);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+    }
+    if (aborted) {
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int t = t_stop; t < issued; ++t)
+                mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1), a.timeout_ns, nullptr);
+        }
+        __syncthreads();
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        if (!valid[u]) continue;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+            red_add(a.accum + (size_t)q * a.n + my_i[u], acc_s[(u * 3 + q) * kThreads + tid]);
+    }
+}
+
+template <int KIND, int I>
+static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
+    constexpr int SMEM = SymCfg<FSI_MIXED, KIND>::SMEM + I * 3 * kThreads * (int)sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sym_mixed_v2_kernel<KIND, I>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
+    const long long grid = (long long)nb * (1 + a.nchunk);
+    if (grid > 2147483647LL) return cudaErrorInvalidValue;
+    { sym_mixed_v2_kernel<KIND, I><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    return cudaGetLastError();
+}
+
 template <int P, int KIND, int I>
 static cudaError_t launch_sym_one(const SymArgs& a, cudaStream_t s) {
     constexpr int SMEM = SymCfg<P, KIND>::SMEM;
@@ -785,6 +990,16 @@ cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, c
     a.chunk = chunk > 0 ? chunk : 1;
     const int above = ntj > I ? ntj - I : 0;       // most tiles above any block (block 0)
     a.nchunk = (above + a.chunk - 1) / a.chunk;
+    if (precision == FSI_MIXED && (ipt & 32)) {
+        switch (I * 2 + kind) {
+            case 4 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 4>(a, s);
+            case 5 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 5>(a, s);
+            case 6 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 6>(a, s);
+            case 4 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 4>(a, s);
+            case 5 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 5>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (precision == FSI_MIXED)
         return kind == KIND_ACC ? launch_sym_ipt<FSI_MIXED, KIND_ACC>(I, a, s)
                                 : launch_sym_ipt<FSI_MIXED, KIND_GRAD>(I, a, s);
@@ -829,6 +1044,19 @@ int pair_variants(int precision, int kind, int* out) {
     if (precision == FSI_MIXED) {
         for (int ipt = 2; ipt <= 4; ++ipt) out[n++] = ipt;
         for (int ipt = 2; ipt <= 4; ++ipt) out[n++] = 16 + ipt;
+    } else {
+        out[n++] = 1; out[n++] = 2; out[n++] = 3;
+    }
+    return n;
+}
+
+int sym_variants(int precision, int kind, int* out) {
+    int n = 0;
+    if (precision == FSI_MIXED) {
+        for (int ipt = 2; ipt <= 4; ++ipt) out[n++] = ipt;
+        out[n++] = 32 + 4;
+        out[n++] = 32 + 5;
+        if (kind == KIND_ACC) out[n++] = 32 + 6;
     } else {
         out[n++] = 1; out[n++] = 2; out[n++] = 3;
     }

@@ -164,10 +164,12 @@ def test_symmetric_matches_one_sided(F, prec, n):
     with F.Context(prec, symmetric=False) as ctx:
         a1, g1 = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
         a1, g1 = host(a1), host(g1)
-    variants = (2, 3, 4) if prec == "mixed" else (1, 2, 3)
+    variants = ((2, 2), (3, 3), (4, 4), (36, 36), (37, 37), (38, 37)) if prec == "mixed" \
+        else ((1, 1), (2, 2), (3, 3))
     with F.Context(prec) as ctx:
-        for v in variants:
-            F.fsi_set_tuning(ctx, v, v)
+        for va, vg in variants:
+            F.fsi_set_tuning(ctx, va, vg)
+            v = (va, vg)
             a2, g2 = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
             a2, g2 = host(a2), host(g2)
             assert F.fsi_sync_status(ctx) == F.FSI_OK
