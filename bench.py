@@ -250,6 +250,7 @@ def run_fsi(args):
     torch.cuda.synchronize()
     sampler.start()
     F.fsi_profile(ctx, True)
+    F.fsi_far_stats(ctx, reset=True)
     n0 = F.fsi_launch_count()
     t0 = time.perf_counter()
     for k in range(args.steps):
@@ -263,6 +264,7 @@ def run_fsi(args):
     clocks = sampler.stop()
     prof = F.fsi_profile_read(ctx)
     F.fsi_profile(ctx, False)
+    far_v, near_v = F.fsi_far_stats(ctx)
     if F.fsi_sync_status(ctx) != F.FSI_OK:
         raise SystemExit("device error in the timed region")
     step_ms = [a.elapsed_time(b) for a, b in ev]
@@ -299,8 +301,8 @@ def run_fsi(args):
     peak_mhz = SM_MAX_MHZ
     peak = fp32_peak_tflops(peak_mhz) if args.precision == "mixed" else args.fp64_peak_tflops
     var = tuning[0 if dom == "acc" else 1]
-    kname = (f"sym_mixed_v2_kernel<{dom}, I={var & 15}>" if var & 32 else
-             f"sym_pair_kernel<{args.precision}, {dom}, I={var & 15}>")
+    kname = (f"sym_mixed_v2_kernel<{dom}, I={var & 15}{', far' if var & 64 else ''}>" if var & 32
+             else f"sym_pair_kernel<{args.precision}, {dom}, I={var & 15}>")
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": None, "kernel": kname,
                 "peak_basis": ("148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"
@@ -320,6 +322,8 @@ def run_fsi(args):
                    "step": "one FSI cycle of all N + PN1.0 half-kicks (3 acc + 1 grad pair passes)",
                    "c": cl, "h": h, "l2": "flushed between steps (256 MB write)",
                    "tuning": {"acc_variant": tuning[0], "grad_variant": tuning[1]},
+                   "far_tile_visits": {"far": far_v, "near": near_v,
+                                       "far_fraction": far_v / max(far_v + near_v, 1)},
                    "parallelism": f"replicas x{ws}"},
         "wall_s": wall, "gpu_launches": launches,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": bytes_io,

@@ -81,6 +81,11 @@ typedef struct fsi_params {
     int hhs_small_max;    /* HHS: a fast set of at most this many particles (0 = 512, the
                              maximum) runs its whole recursion inside one CTA; -1 = always
                              walk the levels from the host */
+    int order_min;        /* mixed + symmetric with a far-tile kernel variant selected (see
+                             fsi_autotune): fsi_step puts a set of at least this many
+                             particles in Morton order for the duration of the call (0 =
+                             32768; -1 = never).  The order only changes which pairs take
+                             the far-tile arithmetic and the summation order. */
 } fsi_params;
 
 /* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,
@@ -251,9 +256,14 @@ int fsi_level_stats(fsi_ctx *ctx, long long *counts, int max);
  * A variant is the number of active particles each thread holds in registers (low 4
  * bits, 1-6); one-sided mixed kernels add 16 to carry their per-tile partial sums as
  * float-float pairs instead of FP64; symmetric mixed kernels add 32 for the second form
- * (FP64 sums in shared memory, select-free source reduce-scatter).  Synchronous.  (The
- * source-split factor of one-sided passes is chosen per launch from the wave count, or
- * fixed by fsi_params.split.) */
+ * (FP64 sums in shared memory, select-free source reduce-scatter) and 96 for the second
+ * form with the far-tile path: for a warp of 32 I consecutive particles and a 32-record
+ * source sub-tile of centre C and radius R whose gap is at least 4 R, the separation is
+ * formed as (C - x_i) + (x_j - C) from FP32 values relative to C (3 additions instead of
+ * 9; relative error of d at most about 3 u (1 + 1/3), u = 2^-24).  When n >= the order
+ * threshold (fsi_params.order_min), the set is timed in Morton order, as fsi_step runs
+ * it.  Synchronous.  (The source-split factor of one-sided passes is chosen per launch
+ * from the wave count, or fixed by fsi_params.split.) */
 int fsi_autotune(fsi_ctx *ctx, int N, const double *pos, const double *mass, int n, int reps,
                  void *stream);
 
@@ -300,6 +310,13 @@ int fsi_profile_read(fsi_ctx *ctx, long long *launches, double *ms);
  * acceleration passes and of the gradient passes (a symmetric pass counts both
  * directions), since creation or the last reset (reset != 0 clears after reading). */
 int fsi_work_stats(fsi_ctx *ctx, long long *acc_pairs, long long *grad_pairs, int reset);
+
+/* Far-tile statistics of the symmetric mixed kernel (variants >= 96): (warp, 32-record
+ * source sub-tile) visits that took the far-tile separation and that took the hi/lo
+ * separation, since creation or the last reset (reset != 0 clears after reading).
+ * Synchronises `stream`. */
+int fsi_far_stats(fsi_ctx *ctx, long long *far_visits, long long *near_visits, int reset,
+                  void *stream);
 
 /* Number of kernels this library has launched in this process (all contexts). */
 long long fsi_launch_count(void);

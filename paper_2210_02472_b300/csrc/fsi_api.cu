@@ -4,6 +4,7 @@
 // pair passes and their fused epilogues, and walks the HHS hierarchy; every arithmetic
 // step runs in the kernels of pair_kernels.cu and aux_kernels.cu.
 #include <algorithm>
+#include <climits>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -79,6 +80,10 @@ struct fsi_ctx {
     int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] one-sided kernel variant (pair_variants)
     int symv[2][2] = {{2, 2}, {4, 2}};  // [precision][kind] symmetric kernel variant (sym_variants)
     long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
+    // far-tile path of the symmetric mixed kernel: while far_n > 0, the records of the set
+    // being stepped (n = far_n) have valid masses in rel[].w (step_core, autotune)
+    Buf rel, sub, ordws, ordperm, ordlist, farstats;
+    int far_n = 0;
     // instrumentation: event pairs around pair-kernel launches
     struct ProfRec { int kind; cudaEvent_t a, b; };
     bool profiling = false;
@@ -161,6 +166,82 @@ int timed(fsi_ctx* c, int kind, cudaStream_t s, F&& f) {
     return FSI_OK;
 }
 
+// Far-tile test of the symmetric mixed kernel: the gap between a warp's particles and a
+// sub-tile centre must be at least (kFarKappa + 1) R, so that every source of the
+// sub-tile is at least kFarKappa times its offset from the centre away from every
+// particle of the warp.
+constexpr float kFarKappa = 3.0f;
+// Sets of at least this many particles are put in Morton order by step_core when the
+// symmetric mixed far-tile kernel is selected (order_min = 0).
+constexpr int kOrderMinDefault = 32768;
+
+int order_threshold(const fsi_ctx* c) {
+    if (c->p.order_min < 0) return INT_MAX;
+    return c->p.order_min > 0 ? c->p.order_min : kOrderMinDefault;
+}
+
+bool far_selected(const fsi_ctx* c) {
+    return c->p.precision == FSI_MIXED && c->p.symmetric &&
+           ((c->symv[FSI_MIXED][KIND_ACC] & 64) || (c->symv[FSI_MIXED][KIND_GRAD] & 64));
+}
+
+// Morton order of a set: ordlist[k] = member at sorted position k (global index).
+// pos rows have leading dimension N; idx (nullable, then n == N) lists the members.
+int order_set(fsi_ctx* c, int N, const double* pos, const int* idx, int n, cudaStream_t s) {
+    const double* xs = pos;
+    long long ld = N;
+    if (idx) {
+        CK(ensure(c->xc, 3 * (size_t)n * 8));
+        CU(launch_gather3(N, pos, idx, n, P<double>(c->xc), s));
+        xs = P<double>(c->xc);
+        ld = n;
+    }
+    CK(ensure(c->ordperm, (size_t)n * 4));
+    CK(ensure(c->ordlist, (size_t)n * 4));
+    const size_t wsb = morton_workspace_bytes(n);
+    CK(ensure(c->ordws, wsb));
+    CU(launch_morton_order(n, xs, ld, P<int>(c->ordperm), c->ordws.p, c->ordws.bytes, s));
+    CU(launch_compose(idx, P<int>(c->ordperm), n, P<int>(c->ordlist), s));
+    return FSI_OK;
+}
+
+// Far-tile set-up for the set list (nullable) of n members: masses into rel[].w.
+int far_setup(fsi_ctx* c, const double* mass, const int* list, int n, cudaStream_t s) {
+    CK(ensure(c->rel, pad_tile(n) * 16));
+    CK(ensure(c->sub, (pad_tile(n) / 32) * 16));
+    CU(launch_rel_mass(mass, list, n, c->rel.p, s));
+    c->far_n = n;
+    return FSI_OK;
+}
+
+struct FarGuard {
+    fsi_ctx* c;
+    ~FarGuard() { c->far_n = 0; }
+};
+
+// Same-set passes of fsi_accel / fsi_grad / fsi_accel_grad with the far-tile kernel: the
+// set runs in Morton order (list = ordlist) with outputs in workspace rows, and unsort()
+// scatters each output back to the caller's order.
+struct SameSetOrder {
+    bool on = false;
+    const int* list = nullptr;
+    int begin(fsi_ctx* c, int N, const double* pos, const double* mass, const int* A, int n,
+              cudaStream_t s) {
+        list = A;
+        on = far_selected(c) && n >= order_threshold(c);
+        if (!on) return FSI_OK;
+        CK(order_set(c, N, pos, A, n, s));
+        list = P<int>(c->ordlist);
+        CK(far_setup(c, mass, list, n, s));
+        return FSI_OK;
+    }
+    // out[:, perm[k]] = sorted[:, k]  (both 3 x n)
+    int unsort(fsi_ctx* c, const double* sorted, int n, double* out, cudaStream_t s) {
+        CU(launch_scatter3(n, sorted, P<int>(c->ordperm), n, out, s));
+        return FSI_OK;
+    }
+};
+
 // Source tiles per work item of the symmetric kernel: about 8 items per resident CTA
 // slot, at most 64 tiles each.
 int choose_chunk(const fsi_ctx* c, int n, int ipt) {
@@ -187,9 +268,23 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
         const int chunk = choose_chunk(c, n, variant_ipt(sv));
         a.err = c->err_d;
         a.timeout_ns = budget(c);
+        SymFar far{};
+        const SymFar* farp = nullptr;
+        if (prec == FSI_MIXED && (sv & 64) && c->far_n == n) {
+            if (!c->farstats.p) {
+                CK(ensure(c->farstats, 2 * sizeof(unsigned long long)));
+                CU(cudaMemsetAsync(c->farstats.p, 0, 2 * sizeof(unsigned long long), s));
+            }
+            CU(launch_subtiles(n, a.irec, c->rel.p, c->sub.p, s));
+            far.rel = c->rel.p;
+            far.sub = c->sub.p;
+            far.k2 = (kFarKappa + 1.0f) * (kFarKappa + 1.0f);
+            far.stats = P<unsigned long long>(c->farstats);
+            farp = &far;
+        }
         CK(timed(c, kind, s, [&] {
             return launch_sym_pair(prec, kind, sv, a.irec, a.iacc, n, a.eps2, chunk,
-                                   P<double>(c->accum), a.err, a.timeout_ns, s);
+                                   P<double>(c->accum), a.err, a.timeout_ns, farp, s);
         }));
         a.part = P<double>(c->accum);
         CK(timed(c, 2, s, [&] { return launch_finalize_p(prec, a, 1, s); }));
@@ -233,6 +328,13 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     CK(ensure(c->rec[1], pad_tile(n) * 32));
     CK(ensure(c->accrec[0], pad_tile(n) * 32));
     CK(ensure(c->ac, 3 * (size_t)n * 8));
+    FarGuard far_guard{c};
+    const bool far = far_selected(c) && n >= order_threshold(c);
+    if (far) {
+        CK(order_set(c, N, pos, idx, n, s));
+        idx = P<int>(c->ordlist);
+        CK(far_setup(c, mass, idx, n, s));
+    }
     double* xc = pos;
     double* vc = vel;
     const double* mc = mass;
@@ -524,6 +626,7 @@ void fsi_default_params(fsi_params* p) {
     p->timeout_ns = 0;
     p->symmetric = 1;
     p->hhs_small_max = 0;
+    p->order_min = 0;
 }
 
 const char* fsi_last_error(void) { return g_err.c_str(); }
@@ -557,7 +660,8 @@ int fsi_destroy(fsi_ctx* c) {
     Buf* bufs[] = {&c->rec[0], &c->rec[1], &c->accrec[0], &c->accrec[1], &c->xc, &c->vc, &c->ac,
                    &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->mc, &c->bhc, &c->ids[0], &c->ids[1],
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
-                   &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats};
+                   &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
+                   &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -597,6 +701,17 @@ int fsi_reserve(fsi_ctx* c, int N, int n) {
     CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
     CK(ensure(c->part, (size_t)64 * 3 * n * 8));
     CK(ensure(c->epart, (size_t)(energy_blocks(n) * 2 + 2) * 8));
+    CK(ensure(c->accum, 3 * (size_t)n * 8));
+    // spatial ordering and far-tile inputs of the symmetric mixed kernel
+    CK(ensure(c->rel, pad_tile(n) * 16));
+    CK(ensure(c->sub, (pad_tile(n) / 32) * 16));
+    CK(ensure(c->ordperm, (size_t)n * 4));
+    CK(ensure(c->ordlist, (size_t)n * 4));
+    CK(ensure(c->ordws, morton_workspace_bytes(n)));
+    if (!c->farstats.p) {
+        CK(ensure(c->farstats, 2 * sizeof(unsigned long long)));
+        CU(cudaMemset(c->farstats.p, 0, 2 * sizeof(unsigned long long)));
+    }
     CU(cudaDeviceSynchronize());
     return FSI_OK;
 }
@@ -622,16 +737,22 @@ int fsi_accel(fsi_ctx* c, int N, const double* pos, const double* mass, const in
     const int prec = c->p.precision;
     const bool same = (A == B) && (nA == nB);
     CK(ensure(c->rec[0], pad_tile(nA) * 32));
-    CU(launch_pack(prec, N, pos, mass, A, nA, c->rec[0].p, nullptr, s));
+    FarGuard far_guard{c};
+    SameSetOrder ord;
+    if (same) CK(ord.begin(c, N, pos, mass, A, nA, s));
+    if (ord.on) CK(ensure(c->tA, 3 * (size_t)nA * 8));
+    CU(launch_pack(prec, N, pos, mass, ord.on ? ord.list : A, nA, c->rec[0].p, nullptr, s));
     PairArgs a{};
     a.irec = c->rec[0].p;
     a.n_i = nA;
     a.n_j = nB;
     a.eps2 = eps2;
-    a.epi.out = acc_out;
+    a.epi.out = ord.on ? P<double>(c->tA) : acc_out;
     if (same) {
         a.jrec = c->rec[0].p;
         a.check = CHECK_DIAG;
+        CK(run_pair(c, KIND_ACC, a, s));
+        return ord.on ? ord.unsort(c, P<double>(c->tA), nA, acc_out, s) : FSI_OK;
     } else {
         CK(ensure(c->rec[1], pad_tile(nB) * 32));
         CK(ensure(c->ids[0], pad_tile(nA) * 4));
@@ -660,19 +781,25 @@ int fsi_grad(fsi_ctx* c, int N, const double* pos, const double* mass, const dou
     const bool same = (A == B) && (nA == nB);
     CK(ensure(c->rec[0], pad_tile(nA) * 32));
     CK(ensure(c->accrec[0], pad_tile(nA) * 32));
-    CU(launch_pack(prec, N, pos, mass, A, nA, c->rec[0].p, nullptr, s));
-    CU(launch_pack_acc(prec, N, accg, mass, A, nA, c->accrec[0].p, nullptr, s));
+    FarGuard far_guard{c};
+    SameSetOrder ord;
+    if (same) CK(ord.begin(c, N, pos, mass, A, nA, s));
+    if (ord.on) CK(ensure(c->tA, 3 * (size_t)nA * 8));
+    CU(launch_pack(prec, N, pos, mass, ord.on ? ord.list : A, nA, c->rec[0].p, nullptr, s));
+    CU(launch_pack_acc(prec, N, accg, mass, ord.on ? ord.list : A, nA, c->accrec[0].p, nullptr, s));
     PairArgs a{};
     a.irec = c->rec[0].p;
     a.iacc = c->accrec[0].p;
     a.n_i = nA;
     a.n_j = nB;
     a.eps2 = eps2;
-    a.epi.out = grad_out;
+    a.epi.out = ord.on ? P<double>(c->tA) : grad_out;
     if (same) {
         a.jrec = a.irec;
         a.jacc = a.iacc;
         a.check = CHECK_DIAG;
+        CK(run_pair(c, KIND_GRAD, a, s));
+        return ord.on ? ord.unsort(c, P<double>(c->tA), nA, grad_out, s) : FSI_OK;
     } else {
         CK(ensure(c->rec[1], pad_tile(nB) * 32));
         CK(ensure(c->accrec[1], pad_tile(nB) * 32));
@@ -705,20 +832,30 @@ int fsi_accel_grad(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     const bool same = (A == B) && (nA == nB);
     CK(ensure(c->rec[0], pad_tile(nA) * 32));
     CK(ensure(c->accrec[0], pad_tile(nA) * 32));
-    CU(launch_pack(prec, N, pos, mass, A, nA, c->rec[0].p, nullptr, s));
+    FarGuard far_guard{c};
+    SameSetOrder ord;
+    if (same) CK(ord.begin(c, N, pos, mass, A, nA, s));
+    CU(launch_pack(prec, N, pos, mass, ord.on ? ord.list : A, nA, c->rec[0].p, nullptr, s));
     if (same) {
+        if (ord.on) {
+            CK(ensure(c->tA, 3 * (size_t)nA * 8));
+            CK(ensure(c->tB, 3 * (size_t)nA * 8));
+        }
         PairArgs a{};
         a.irec = a.jrec = c->rec[0].p;
         a.n_i = a.n_j = nA;
         a.check = CHECK_DIAG;
         a.eps2 = eps2;
-        a.epi.out = acc_out;
+        a.epi.out = ord.on ? P<double>(c->tA) : acc_out;
         a.epi.accrec = c->accrec[0].p;
         CK(run_pair(c, KIND_ACC, a, s));
         a.iacc = a.jacc = c->accrec[0].p;
         a.epi = Epi{};
-        a.epi.out = grad_out;
-        return run_pair(c, KIND_GRAD, a, s);
+        a.epi.out = ord.on ? P<double>(c->tB) : grad_out;
+        CK(run_pair(c, KIND_GRAD, a, s));
+        if (!ord.on) return FSI_OK;
+        CK(ord.unsort(c, P<double>(c->tA), nA, acc_out, s));
+        return ord.unsort(c, P<double>(c->tB), nA, grad_out, s);
     }
     if (!A || !B) return fail(FSI_ERR_ARG, "a NULL (all-particle) list overlaps any other list");
     CK(ensure(c->mark, (size_t)N));
@@ -1130,7 +1267,15 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
     CK(ensure(c->rec[0], pad_tile(n) * 32));
     CK(ensure(c->accrec[0], pad_tile(n) * 32));
     CK(ensure(c->tA, 3 * (size_t)n * 8));
-    CU(launch_pack(prec, N, pos, mass, nullptr, n, c->rec[0].p, nullptr, s));
+    FarGuard far_guard{c};
+    const int* list = nullptr;
+    if (prec == FSI_MIXED && c->p.symmetric && n >= order_threshold(c)) {
+        // the far-tile variants are timed as step_core runs them: set in Morton order
+        CK(order_set(c, N, pos, nullptr, n, s));
+        list = P<int>(c->ordlist);
+        CK(far_setup(c, mass, list, n, s));
+    }
+    CU(launch_pack(prec, N, pos, mass, list, n, c->rec[0].p, nullptr, s));
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
@@ -1139,7 +1284,7 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
     int rc = FSI_OK;
     int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
     for (int kind = 0; kind < 2 && rc == FSI_OK; ++kind) {
-        int cand[8];
+        int cand[16];
         const int nc = c->p.symmetric ? sym_variants(prec, kind, cand) : pair_variants(prec, kind, cand);
         float best = 3.4e38f;
         int best_ipt = table[prec][kind];
@@ -1183,7 +1328,7 @@ int fsi_get_tuning(fsi_ctx* c, int* ipt_acc, int* ipt_grad) {
 
 int fsi_set_tuning(fsi_ctx* c, int ipt_acc, int ipt_grad) {
     if (!c) return fail(FSI_ERR_ARG, "NULL context");
-    int cand[8];
+    int cand[16];
     const int prec = c->p.precision;
     for (int kind = 0; kind < 2; ++kind) {
         const int want = kind == KIND_ACC ? ipt_acc : ipt_grad;
@@ -1195,6 +1340,21 @@ int fsi_set_tuning(fsi_ctx* c, int ipt_acc, int ipt_grad) {
     int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
     table[prec][KIND_ACC] = ipt_acc;
     table[prec][KIND_GRAD] = ipt_grad;
+    return FSI_OK;
+}
+
+int fsi_far_stats(fsi_ctx* c, long long* far_visits, long long* near_visits, int reset,
+                  void* stream) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    unsigned long long st[2] = {0, 0};
+    const cudaStream_t s = S(stream);
+    if (c->farstats.p) {
+        CU(cudaMemcpyAsync(st, c->farstats.p, sizeof st, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (reset) CU(cudaMemsetAsync(c->farstats.p, 0, sizeof st, s));
+    }
+    if (far_visits) *far_visits = (long long)st[0];
+    if (near_visits) *near_visits = (long long)st[1];
     return FSI_OK;
 }
 

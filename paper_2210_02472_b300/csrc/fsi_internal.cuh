@@ -212,16 +212,35 @@ cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int
 cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s);
 // Symmetric self-interaction pass (every unordered pair once); adds into accum (3 x n,
 // zeroed by the caller); `chunk` source tiles per work item.
+// Far-tile inputs of the symmetric mixed kernel (second form with bit 64 in its variant):
+// rel[k] = (x_k - C, y_k - C, z_k - C, m_k) in FP32 with C the centre of k's 32-record
+// sub-tile, sub[k / 32] = (C, R), R >= max |rel.xyz| over the sub-tile (launch_subtiles);
+// a warp takes the far form for a sub-tile when the gap between its particles' box and C
+// is at least sqrt(k2) R.  stats (nullable): += [far, near] sub-tile visits.
+struct SymFar {
+    const void* rel;
+    const void* sub;
+    float k2;
+    unsigned long long* stats;
+};
 cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
                             int n, double eps2, int chunk, double* accum, int* err,
-                            long long timeout_ns, cudaStream_t s);
-// Supported ipt values for (precision, kind): writes up to 8 into out, returns the count.
+                            long long timeout_ns, const SymFar* far, cudaStream_t s);
+// Supported ipt values for (precision, kind): writes up to 16 into out, returns the count.
 int pair_variants(int precision, int kind, int* out);
 int pair_default_ipt(int precision, int kind);
 // Variants of the symmetric kernels: active particles per thread (low 4 bits), + 32 for the
 // mixed second form (FP64 sums in shared memory, select-free reduce-scatter).
 int sym_variants(int precision, int kind, int* out);
 int variant_ipt(int variant);
+
+// Spatial ordering and far-tile inputs (order_kernels.cu).
+size_t morton_workspace_bytes(int n);
+cudaError_t launch_morton_order(int n, const double* xc, long long ld, int* perm, void* ws,
+                                size_t ws_bytes, cudaStream_t s);
+cudaError_t launch_compose(const int* idx, const int* perm, int n, int* list, cudaStream_t s);
+cudaError_t launch_rel_mass(const double* mass, const int* idx, int n, void* rel, cudaStream_t s);
+cudaError_t launch_subtiles(int n, const void* rec, void* rel, void* sub, cudaStream_t s);
 
 cudaError_t launch_pack(int precision, int N, const double* pos, const double* mass,
                         const int* idx, int n, void* rec, double* xc, cudaStream_t s);

@@ -373,6 +373,11 @@ struct SymArgs {
     double* accum;      // 3 x n, zeroed before the launch
     int* err;
     long long timeout_ns;
+    // far-tile path of the second form (null rel: never taken), see SymFar
+    const float4* rel;
+    const float4* sub;
+    float far_k2;
+    unsigned long long* far_stats;
 };
 
 __device__ __forceinline__ void red_add(double* p, double v) {
@@ -444,6 +449,42 @@ __device__ __forceinline__ void mix_grad_sym(const float4 h, const float4 l, con
     const float q = r3 * (y2 * fmaf(3.0f, sres, -6.0f));           // -3 r^-5 (refined)
     const float s = q * dot;
     // T(d) b = r^-3 b - 3 r^-5 (b.d) d: on i with weight m_j, on j with weight -m_i
+    const float tx = fmaf(r3, bx, s * dx), ty = fmaf(r3, by, s * dy), tz = fmaf(r3, bz, s * dz);
+    gi[0] = fmaf(aj.w, tx, gi[0]); gi[1] = fmaf(aj.w, ty, gi[1]); gi[2] = fmaf(aj.w, tz, gi[2]);
+    gj[0] = fmaf(p.nm, tx, gj[0]); gj[1] = fmaf(p.nm, ty, gj[1]); gj[2] = fmaf(p.nm, tz, gj[2]);
+}
+
+// Far-tile forms.  r = (x_j - C, y_j - C, z_j - C, m_j) is the source relative to the
+// centre C of its 32-record sub-tile, rounded once to FP32; D = (C - xh_i) - xl_i.  Then
+// d = D + r.xyz costs 3 additions instead of 9, with error at most about
+// 3 u (|d| + |r.xyz|) (u = 2^-24): the far test keeps |r.xyz| <= |d| / kappa.
+__device__ __forceinline__ void mix_acc_sym_far(const float4 r, const float (&D)[3], float nmi,
+                                                float eps2f, float (&fi)[3], float (&fj)[3]) {
+    const float dx = D[0] + r.x, dy = D[1] + r.y, dz = D[2] + r.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2f)));
+    const float y = rsqrt_hw(r2);
+    const float y2 = y * y;
+    const float sres = r2 * y2;
+    const float r3 = (y2 * y) * fmaf(sres, -1.5f, 2.5f);           // r^-3 (refined)
+    const float wi = r3 * r.w;                                       //  m_j r^-3
+    const float wj = r3 * nmi;                                       // -m_i r^-3
+    fi[0] = fmaf(wi, dx, fi[0]); fi[1] = fmaf(wi, dy, fi[1]); fi[2] = fmaf(wi, dz, fi[2]);
+    fj[0] = fmaf(wj, dx, fj[0]); fj[1] = fmaf(wj, dy, fj[1]); fj[2] = fmaf(wj, dz, fj[2]);
+}
+
+__device__ __forceinline__ void mix_grad_sym_far(const float4 r, const float4 aj, const float (&D)[3],
+                                                 const SymMixI& p, float eps2f,
+                                                 float (&gi)[3], float (&gj)[3]) {
+    const float dx = D[0] + r.x, dy = D[1] + r.y, dz = D[2] + r.z;
+    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, eps2f)));
+    const float y = rsqrt_hw(r2);
+    const float y2 = y * y;
+    const float sres = r2 * y2;
+    const float r3 = (y2 * y) * fmaf(sres, -1.5f, 2.5f);
+    const float bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;
+    const float dot = fmaf(bx, dx, fmaf(by, dy, bz * dz));
+    const float q = r3 * (y2 * fmaf(3.0f, sres, -6.0f));
+    const float s = q * dot;
     const float tx = fmaf(r3, bx, s * dx), ty = fmaf(r3, by, s * dy), tz = fmaf(r3, bz, s * dz);
     gi[0] = fmaf(aj.w, tx, gi[0]); gi[1] = fmaf(aj.w, ty, gi[1]); gi[2] = fmaf(aj.w, tz, gi[2]);
     gj[0] = fmaf(p.nm, tx, gj[0]); gj[1] = fmaf(p.nm, ty, gj[1]); gj[2] = fmaf(p.nm, tz, gj[2]);
@@ -749,20 +790,30 @@ __global__ void __launch_bounds__(kThreads, 2) sym_pair_kernel(const SymArgs a) 
 // Symmetric mixed kernel, second form (autotuned against the first):
 //  - the FP64 per-particle sums live in shared memory (one slot per thread and particle),
 //    so a thread can hold up to 6 active particles in registers;
+//  - warp w holds the 32 I consecutive particles i0 + 32 I w + 32 u + lane (u < I), so
+//    that a warp's particles are close in space when the set is in spatial order;
 //  - inside each group of 4 sources, lane l visits source (g XOR (l >> 3)) at step g, so
 //    after the pair loop slot s of lane l holds the partial of source s ^ (l >> 3); the
 //    warp reduce-scatter then needs no selects: at the xor-16 level every lane keeps slots
 //    0, 1 and sends 2, 3, at the xor-8 level keeps slot 0 and sends 1, and three butterfly
 //    levels finish; lane l ends with the total of source l >> 3.  The 4 sources read at one
 //    step are 4 consecutive records, so the shared-memory loads stay conflict-free.
-template <int KIND, int I>
+//  - FAR: each stage also holds the tile's relative records and its 8 sub-tile centres;
+//    a warp whose box of particles is far from a 32-record sub-tile (gap to the centre
+//    >= (kappa + 1) R, R the sub-tile radius) takes the 3-addition separation
+//    (mix_*_sym_far) for the whole sub-tile.  The test is warp-uniform, so the two loops
+//    never diverge inside a warp.
+template <int KIND, int I, bool FAR>
 __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs a) {
     static_assert(kThreads == kTileJ, "an i-block spans I source tiles");
     constexpr int ACCREC = SymCfg<FSI_MIXED, KIND>::ACCREC;
-    constexpr int SB = SymCfg<FSI_MIXED, KIND>::SB;
+    constexpr int RELB = FAR ? 16 : 0;
+    constexpr int SUBB = FAR ? (kTileJ / 32) * 16 : 0;
+    constexpr int SB = kTileJ * (kRec + ACCREC + RELB) + SUBB;
     constexpr int JPART = SymCfg<FSI_MIXED, KIND>::JPART;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ float wbox[FAR ? kThreads / 32 : 1][6];
     float* jpart = reinterpret_cast<float*>(smem + kStages * SB);
     double* acc_s = reinterpret_cast<double*>(smem + kStages * SB + JPART);   // [I][3][kThreads]
 
@@ -777,6 +828,7 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
     const int ntiles = t1 - t0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, L = lane >> 3;
     const int i0 = b * (kThreads * I);
+    const bool far_on = FAR && a.rel != nullptr && !diag;
 
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
@@ -787,12 +839,20 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
         const int st = t % kStages;
         const int jt = (t0 + t) * kTileJ;
         const int cnt = min(kTileJ, a.n - jt);
+        const int nsub = (cnt + 31) >> 5;
         unsigned char* base = smem + st * SB;
-        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC));
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC) +
+                                             (far_on ? (uint32_t)(cnt * 16 + nsub * 16) : 0u));
         bulk_g2s(base, (const unsigned char*)a.rec + (size_t)jt * kRec, (uint32_t)cnt * kRec, &bars[st]);
         if (ACCREC)
             bulk_g2s(base + kTileJ * kRec, (const unsigned char*)a.accrec + (size_t)jt * ACCREC,
                      (uint32_t)cnt * ACCREC, &bars[st]);
+        if (far_on) {
+            bulk_g2s(base + kTileJ * (kRec + ACCREC), (const unsigned char*)(a.rel + jt),
+                     (uint32_t)cnt * 16, &bars[st]);
+            bulk_g2s(base + kTileJ * (kRec + ACCREC + RELB), (const unsigned char*)(a.sub + jt / 32),
+                     (uint32_t)nsub * 16, &bars[st]);
+        }
     };
     if (tid == 0)
         for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
@@ -803,7 +863,7 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
     bool valid[I];
 #pragma unroll
     for (int u = 0; u < I; ++u) {
-        my_i[u] = i0 + u * kThreads + tid;
+        my_i[u] = i0 + warp * (32 * I) + u * 32 + lane;
         valid[u] = my_i[u] < a.n;
         const int i = min(my_i[u], a.n - 1);
         const RecMix r = reinterpret_cast<const RecMix*>(a.rec)[i];
@@ -816,7 +876,8 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
             pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
             pi[u].nm = valid[u] ? -ai.w : 0.f;
         } else {
-            pi[u].ax = pi[u].ay = pi[u].az = pi[u].nm = 0.f;
+            pi[u].ax = pi[u].ay = pi[u].az = 0.f;
+            pi[u].nm = (far_on && valid[u]) ? -a.rel[i].w : 0.f;    // -m_i for the far form
         }
 #pragma unroll
         for (int q = 0; q < 3; ++q) {
@@ -824,7 +885,28 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
             acc_s[(u * 3 + q) * kThreads + tid] = 0.0;
         }
     }
+    if (far_on) {
+        // box of the warp's particles (FP32 high parts)
+        float bl[3] = {pi[0].xh, pi[0].yh, pi[0].zh}, bh[3] = {pi[0].xh, pi[0].yh, pi[0].zh};
+#pragma unroll
+        for (int u = 1; u < I; ++u) {
+            bl[0] = fminf(bl[0], pi[u].xh); bl[1] = fminf(bl[1], pi[u].yh); bl[2] = fminf(bl[2], pi[u].zh);
+            bh[0] = fmaxf(bh[0], pi[u].xh); bh[1] = fmaxf(bh[1], pi[u].yh); bh[2] = fmaxf(bh[2], pi[u].zh);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                bl[q] = fminf(bl[q], __shfl_xor_sync(0xffffffffu, bl[q], o));
+                bh[q] = fmaxf(bh[q], __shfl_xor_sync(0xffffffffu, bh[q], o));
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { wbox[FAR ? warp : 0][q] = bl[q]; wbox[FAR ? warp : 0][3 + q] = bh[q]; }
+        __syncwarp();
+    }
     const float eps2f = (float)a.eps2;
+    unsigned far_visits = 0, near_visits = 0;
     bool aborted = false;
     int t_stop = ntiles;
     for (int t = 0; t < ntiles; ++t) {
@@ -835,6 +917,8 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
         const unsigned char* base = smem + st * SB;
         const RecMix* rec = reinterpret_cast<const RecMix*>(base);
         const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
+        const float4* rel_s = reinterpret_cast<const float4*>(base + kTileJ * (kRec + ACCREC));
+        const float4* sub_s = reinterpret_cast<const float4*>(base + kTileJ * (kRec + ACCREC + RELB));
         if (diag) {
             MixI q[I];
 #pragma unroll
@@ -858,22 +942,49 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
                 }
             }
         } else {
-            for (int jj = 0; jj < cnt; jj += 4) {
+            unsigned fmask = 0;
+            if (far_on) {
+                bool fr = false;
+                if (lane < ((cnt + 31) >> 5)) {
+                    const float4 sb = sub_s[lane];
+                    const float* wb = wbox[FAR ? warp : 0];
+                    const float gx = fmaxf(0.f, fmaxf(wb[0] - sb.x, sb.x - wb[3]));
+                    const float gy = fmaxf(0.f, fmaxf(wb[1] - sb.y, sb.y - wb[4]));
+                    const float gz = fmaxf(0.f, fmaxf(wb[2] - sb.z, sb.z - wb[5]));
+                    fr = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= a.far_k2 * (sb.w * sb.w);
+                }
+                fmask = __ballot_sync(0xffffffffu, fr);
+            }
+            // one group of 4 sources; FG selects the far form
+            auto group = [&](int jj, auto fg, const float (&D)[I][3]) {
+                constexpr bool FG = decltype(fg)::value;
                 float fj[4][3];
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     fj[g][0] = fj[g][1] = fj[g][2] = 0.f;
                     const int jg = jj + (g ^ L);
                     if (jg < cnt) {
-                        const float4 h = rec[jg].hi;
-                        const float4 l = rec[jg].lo;
-                        if constexpr (KIND == KIND_ACC) {
+                        if constexpr (FG) {
+                            const float4 r = rel_s[jg];
+                            if constexpr (KIND == KIND_ACC) {
 #pragma unroll
-                            for (int u = 0; u < I; ++u) mix_acc_sym(h, l, pi[u], eps2f, f[u], fj[g]);
+                                for (int u = 0; u < I; ++u) mix_acc_sym_far(r, D[u], pi[u].nm, eps2f, f[u], fj[g]);
+                            } else {
+                                const float4 aj = arec[jg];
+#pragma unroll
+                                for (int u = 0; u < I; ++u) mix_grad_sym_far(r, aj, D[u], pi[u], eps2f, f[u], fj[g]);
+                            }
                         } else {
-                            const float4 aj = arec[jg];
+                            const float4 h = rec[jg].hi;
+                            const float4 l = rec[jg].lo;
+                            if constexpr (KIND == KIND_ACC) {
 #pragma unroll
-                            for (int u = 0; u < I; ++u) mix_grad_sym(h, l, aj, pi[u], eps2f, f[u], fj[g]);
+                                for (int u = 0; u < I; ++u) mix_acc_sym(h, l, pi[u], eps2f, f[u], fj[g]);
+                            } else {
+                                const float4 aj = arec[jg];
+#pragma unroll
+                                for (int u = 0; u < I; ++u) mix_grad_sym(h, l, aj, pi[u], eps2f, f[u], fj[g]);
+                            }
                         }
                     }
                 }
@@ -892,6 +1003,25 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
                 if ((lane & 7) == 0 && jl < cnt) {
                     float* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
                     dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+                }
+            };
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                const int jend = min(cnt, k0 + 32);
+                if (FAR && ((fmask >> (k0 >> 5)) & 1u)) {
+                    const float4 C = sub_s[k0 >> 5];
+                    float D[I][3];
+#pragma unroll
+                    for (int u = 0; u < I; ++u) {
+                        D[u][0] = (C.x - pi[u].xh) - pi[u].xl;
+                        D[u][1] = (C.y - pi[u].yh) - pi[u].yl;
+                        D[u][2] = (C.z - pi[u].zh) - pi[u].zl;
+                    }
+                    for (int jj = k0; jj < jend; jj += 4) group(jj, std::true_type{}, D);
+                    ++far_visits;
+                } else {
+                    float D0[I][3];
+                    for (int jj = k0; jj < jend; jj += 4) group(jj, std::false_type{}, D0);
+                    ++near_visits;
                 }
             }
         }
@@ -924,6 +1054,10 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
         __syncthreads();
         return;
     }
+    if (FAR && a.far_stats && lane == 0 && !diag) {
+        atomicAdd(a.far_stats, (unsigned long long)far_visits);
+        atomicAdd(a.far_stats + 1, (unsigned long long)near_visits);
+    }
 #pragma unroll
     for (int u = 0; u < I; ++u) {
         if (!valid[u]) continue;
@@ -933,12 +1067,14 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
     }
 }
 
-template <int KIND, int I>
+template <int KIND, int I, bool FAR>
 static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
-    constexpr int SMEM = SymCfg<FSI_MIXED, KIND>::SMEM + I * 3 * kThreads * (int)sizeof(double);
+    constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + (FAR ? 16 : 0)) +
+                       (FAR ? (kTileJ / 32) * 16 : 0);
+    constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + I * 3 * kThreads * (int)sizeof(double);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sym_mixed_v2_kernel<KIND, I>,
+        cudaError_t e = cudaFuncSetAttribute(sym_mixed_v2_kernel<KIND, I, FAR>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
@@ -946,7 +1082,7 @@ static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
     const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
     const long long grid = (long long)nb * (1 + a.nchunk);
     if (grid > 2147483647LL) return cudaErrorInvalidValue;
-    { sym_mixed_v2_kernel<KIND, I><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    { sym_mixed_v2_kernel<KIND, I, FAR><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
     return cudaGetLastError();
 }
 
@@ -980,23 +1116,38 @@ static cudaError_t launch_sym_ipt(int ipt, const SymArgs& a, cudaStream_t s) {
 
 cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
                             int n, double eps2, int chunk, double* accum, int* err,
-                            long long timeout_ns, cudaStream_t s) {
+                            long long timeout_ns, const SymFar* far, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    SymArgs a;
+    SymArgs a{};
     a.rec = rec; a.accrec = accrec; a.n = n; a.eps2 = eps2; a.accum = accum; a.err = err;
     a.timeout_ns = timeout_ns;
+    if (far && (ipt & 64)) {
+        a.rel = reinterpret_cast<const float4*>(far->rel);
+        a.sub = reinterpret_cast<const float4*>(far->sub);
+        a.far_k2 = far->k2;
+        a.far_stats = far->stats;
+    }
     const int I = ipt & 15;
     const int ntj = (n + kTileJ - 1) / kTileJ;
     a.chunk = chunk > 0 ? chunk : 1;
     const int above = ntj > I ? ntj - I : 0;       // most tiles above any block (block 0)
     a.nchunk = (above + a.chunk - 1) / a.chunk;
+    if (precision == FSI_MIXED && (ipt & 64)) {
+        switch (I * 2 + kind) {
+            case 4 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 4, true>(a, s);
+            case 5 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 5, true>(a, s);
+            case 3 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 3, true>(a, s);
+            case 4 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 4, true>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (precision == FSI_MIXED && (ipt & 32)) {
         switch (I * 2 + kind) {
-            case 4 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 4>(a, s);
-            case 5 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 5>(a, s);
-            case 6 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 6>(a, s);
-            case 4 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 4>(a, s);
-            case 5 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 5>(a, s);
+            case 4 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 4, false>(a, s);
+            case 5 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 5, false>(a, s);
+            case 6 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 6, false>(a, s);
+            case 4 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 4, false>(a, s);
+            case 5 * 2 + KIND_GRAD: return launch_sym_v2<KIND_GRAD, 5, false>(a, s);
             default: return cudaErrorInvalidValue;
         }
     }
@@ -1057,6 +1208,9 @@ int sym_variants(int precision, int kind, int* out) {
         out[n++] = 32 + 4;
         out[n++] = 32 + 5;
         if (kind == KIND_ACC) out[n++] = 32 + 6;
+        // second form with the far-tile path
+        if (kind == KIND_ACC) { out[n++] = 96 + 4; out[n++] = 96 + 5; }
+        else { out[n++] = 96 + 3; out[n++] = 96 + 4; }
     } else {
         out[n++] = 1; out[n++] = 2; out[n++] = 3;
     }

@@ -41,14 +41,14 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall",
-            "fsi_work_stats", "fsi_accel_noalloc"]
+            "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats"]
 
 
 class fsi_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("eps2", C.c_double), ("eta_ff", C.c_double),
                 ("eta_fb", C.c_double), ("eta_jerk", C.c_double), ("max_level", C.c_int),
                 ("c", C.c_double), ("split", C.c_int), ("timeout_ns", C.c_longlong),
-                ("symmetric", C.c_int), ("hhs_small_max", C.c_int)]
+                ("symmetric", C.c_int), ("hhs_small_max", C.c_int), ("order_min", C.c_int)]
 
 
 _vp, _ip, _dp = C.c_void_p, C.c_int, C.c_double
@@ -74,6 +74,7 @@ _lib.fsi_profile_read.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_do
 _lib.fsi_launch_count.restype = C.c_longlong
 _lib.fsi_accel_noalloc.argtypes = [_ip, _vp, _vp, _dp, _vp, _vp]
 _lib.fsi_work_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip]
+_lib.fsi_far_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip, _vp]
 _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
 _lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
@@ -137,7 +138,7 @@ class Context:
     def __init__(self, precision: str = "fp64", eps2: float = 0.0, eta_ff: float = 0.2,
                  eta_fb: float = 0.2, eta_jerk: float = 0.1, max_level: int = 40,
                  c: float = 0.0, split: int = 0, timeout_ns: int = 0, symmetric: bool = True,
-                 hhs_small_max: int = 0):
+                 hhs_small_max: int = 0, order_min: int = 0):
         p = fsi_params()
         _lib.fsi_default_params(C.byref(p))
         p.precision = {"fp64": FSI_FP64, "mixed": FSI_MIXED}[precision]
@@ -145,6 +146,7 @@ class Context:
         p.max_level, p.c, p.split, p.timeout_ns = max_level, c, split, timeout_ns
         p.symmetric = int(bool(symmetric))
         p.hhs_small_max = int(hhs_small_max)
+        p.order_min = int(order_min)
         self.params = p
         self.precision = precision
         h = _vp()
@@ -407,6 +409,15 @@ def fsi_work_stats(ctx: Context, reset: bool = False):
     a, g = C.c_longlong(), C.c_longlong()
     _check(_lib.fsi_work_stats(ctx.handle, C.byref(a), C.byref(g), int(bool(reset))), "fsi_work_stats")
     return int(a.value), int(g.value)
+
+
+def fsi_far_stats(ctx: Context, reset: bool = False, stream=None):
+    """(far_visits, near_visits): (warp, source sub-tile) visits of the symmetric mixed
+    far-tile kernel that took the far-tile / the hi-lo separation."""
+    f, n = C.c_longlong(), C.c_longlong()
+    _check(_lib.fsi_far_stats(ctx.handle, C.byref(f), C.byref(n), int(bool(reset)), _stream(stream)),
+           "fsi_far_stats")
+    return int(f.value), int(n.value)
 
 
 def fsi_accel_noalloc(pos, mass, eps2: float = 0.0, out=None, stream=None):
