@@ -44,6 +44,12 @@ FLOP_ACC, FLOP_GRAD = 20, 36
 FLOP_PAIR = FLOP_ACC + FLOP_GRAD
 SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 CPU_ROWS = 4096
+# DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
+# kernel, from one one-pass ncu capture of this benchmark's own workload (`--tuning 101,100
+# --steps 1 --warmup 3`, mean of the cycle's three acceleration launches).  Keyed by
+# (kernel label, workload, N); a kernel changed since the capture must drop its entry, and
+# any other configuration reports null.
+DRAM_TRAFFIC = {("sym_mixed_v2_kernel<acc, I=5, far>", "kroupa1m_bh16", 1048592): 201.9e6}
 
 
 def step_interactions(n: int) -> float:
@@ -303,8 +309,11 @@ def run_fsi(args):
     var = tuning[0 if dom == "acc" else 1]
     kname = (f"sym_mixed_v2_kernel<{dom}, I={var & 15}{', far' if var & 64 else ''}>" if var & 32
              else f"sym_pair_kernel<{args.precision}, {dom}, I={var & 15}>")
+    traffic = DRAM_TRAFFIC.get((kname, args.workload if not args.n else "", N))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": kname,
+                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                "traffic_basis": ("DRAM bytes per launch, one ncu capture of this workload"
+                                  if traffic else None),
                 "peak_basis": ("148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"
                                if args.precision == "mixed" else "FP64 FMA probe"),
                 "per_kernel_ms": {k: prof[k][1] / max(prof[k][0], 1) for k in prof},

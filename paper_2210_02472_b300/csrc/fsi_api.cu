@@ -78,7 +78,7 @@ struct fsi_ctx {
     int max_level_used = 0;
     int max_level_hit = 0;
     int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] one-sided kernel variant (pair_variants)
-    int symv[2][2] = {{2, 2}, {4, 2}};  // [precision][kind] symmetric kernel variant (sym_variants)
+    int symv[2][2] = {{2, 2}, {101, 100}};  // [precision][kind] symmetric kernel variant (sym_variants)
     long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
     // far-tile path of the symmetric mixed kernel: while far_n > 0, the records of the set
     // being stepped (n = far_n) have valid masses in rel[].w (step_core, autotune)

@@ -62,26 +62,37 @@ __device__ __forceinline__ unsigned spread10(unsigned v) {      // 10 bits -> ev
     return v;
 }
 
-__global__ void morton_kernel(int n, const double* __restrict__ xc, long long ld, const double* __restrict__ part,
-                              int nparts, unsigned* __restrict__ key, int* __restrict__ idx) {
-    __shared__ double box[6];
-    if (threadIdx.x < 6) {
-        const bool is_lo = threadIdx.x < 3;
-        double v = is_lo ? INFINITY : -INFINITY;
-        for (int b = 0; b < nparts; ++b) {
-            const double q = part[b * 6 + threadIdx.x];
-            v = is_lo ? fmin(v, q) : fmax(v, q);
+// box[0..5] = (min x, y, z, max x, y, z) from the per-block partials (one warp).
+__global__ void bbox_finish_kernel(const double* __restrict__ part, int nparts, double* __restrict__ box) {
+    const int lane = threadIdx.x;
+    double v[6] = {INFINITY, INFINITY, INFINITY, -INFINITY, -INFINITY, -INFINITY};
+    for (int b = lane; b < nparts; b += 32)
+        for (int q = 0; q < 6; ++q) v[q] = q < 3 ? fmin(v[q], part[b * 6 + q]) : fmax(v[q], part[b * 6 + q]);
+    for (int o = 16; o > 0; o >>= 1)
+        for (int q = 0; q < 6; ++q) {
+            const double w = __shfl_xor_sync(0xffffffffu, v[q], o);
+            v[q] = q < 3 ? fmin(v[q], w) : fmax(v[q], w);
         }
-        box[threadIdx.x] = v;
+    if (lane == 0)
+        for (int q = 0; q < 6; ++q) box[q] = v[q];
+}
+
+__global__ void morton_kernel(int n, const double* __restrict__ xc, long long ld,
+                              const double* __restrict__ gbox, unsigned* __restrict__ key,
+                              int* __restrict__ idx) {
+    __shared__ double lo[3], sc[3];        // box corner, 1024 / extent (0 for a flat axis)
+    if (threadIdx.x < 3) {
+        const double ext = gbox[3 + threadIdx.x] - gbox[threadIdx.x];
+        lo[threadIdx.x] = gbox[threadIdx.x];
+        sc[threadIdx.x] = ext > 0.0 ? 1024.0 / ext : 0.0;
     }
     __syncthreads();
     const int k = blockIdx.x * kOB + threadIdx.x;
     if (k >= n) return;
     unsigned code = 0;
     for (int c = 0; c < 3; ++c) {
-        const double ext = box[3 + c] - box[c];
-        const double s = ext > 0.0 ? (xc[(size_t)c * ld + k] - box[c]) / ext : 0.0;
-        const unsigned q = (unsigned)fmin(1023.0, fmax(0.0, s * 1024.0));
+        const double s = (xc[(size_t)c * ld + k] - lo[c]) * sc[c];
+        const unsigned q = (unsigned)fmin(1023.0, fmax(0.0, s));
         code |= spread10(q) << c;
     }
     key[k] = code;
@@ -256,7 +267,8 @@ size_t morton_workspace_bytes(int n) {
     const long long m = (long long)kRadixBins * nb;
     const long long nc = (m + kScanChunk - 1) / kScanChunk;
     auto r = [](size_t b) { return (b + 255) & ~size_t(255); };
-    return 3 * r((size_t)n * 4) + 2 * r((size_t)m * 4) + r((size_t)nparts * 6 * 8) + r((size_t)nc * 4);
+    return 3 * r((size_t)n * 4) + 2 * r((size_t)m * 4) + r((size_t)nparts * 6 * 8) + r(6 * 8) +
+           r((size_t)nc * 4);
 }
 
 // perm[k] = index (into the set) of the particle at sorted position k.  xc: 3 rows of
@@ -274,12 +286,14 @@ cudaError_t launch_morton_order(int n, const double* xc, long long ld, int* perm
     int* offs = reinterpret_cast<int*>(take((size_t)kRadixBins * nb * 4));
     const int nparts = std::min(nb, 1024);
     double* part = reinterpret_cast<double*>(take((size_t)nparts * 6 * 8));
+    double* box = reinterpret_cast<double*>(take(6 * 8));
     const int m = kRadixBins * nb;
     const int nc = (m + kScanChunk - 1) / kScanChunk;
     int* sums = reinterpret_cast<int*>(take((size_t)nc * 4));
     if ((size_t)(p - reinterpret_cast<unsigned char*>(ws)) > ws_bytes) return cudaErrorInvalidValue;
     { bbox_partial_kernel<<<nparts, kOB, 0, s>>>(n, xc, ld, part); note_launch(); }
-    { morton_kernel<<<nb, kOB, 0, s>>>(n, xc, ld, part, nparts, k0, perm); note_launch(); }
+    { bbox_finish_kernel<<<1, 32, 0, s>>>(part, nparts, box); note_launch(); }
+    { morton_kernel<<<nb, kOB, 0, s>>>(n, xc, ld, box, k0, perm); note_launch(); }
     unsigned* kin = k0;
     unsigned* kout = k1;
     int* iin = perm;

@@ -955,15 +955,17 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
                 }
                 fmask = __ballot_sync(0xffffffffu, fr);
             }
-            // one group of 4 sources; FG selects the far form
-            auto group = [&](int jj, auto fg, const float (&D)[I][3]) {
+            // one group of 4 sources; FG selects the far form, FULL drops the bounds check
+            // (a full 32-record sub-tile)
+            auto group = [&](int jj, auto fg, auto full, const float (&D)[I][3]) {
                 constexpr bool FG = decltype(fg)::value;
+                constexpr bool FULL = decltype(full)::value;
                 float fj[4][3];
 #pragma unroll
                 for (int g = 0; g < 4; ++g) {
                     fj[g][0] = fj[g][1] = fj[g][2] = 0.f;
                     const int jg = jj + (g ^ L);
-                    if (jg < cnt) {
+                    if (FULL || jg < cnt) {
                         if constexpr (FG) {
                             const float4 r = rel_s[jg];
                             if constexpr (KIND == KIND_ACC) {
@@ -1000,14 +1002,20 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
                     tot[q] = r;
                 }
                 const int jl = jj + L;
-                if ((lane & 7) == 0 && jl < cnt) {
+                if ((lane & 7) == 0 && (FULL || jl < cnt)) {
                     float* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
                     dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
                 }
             };
             for (int k0 = 0; k0 < cnt; k0 += 32) {
                 const int jend = min(cnt, k0 + 32);
-                if (FAR && ((fmask >> (k0 >> 5)) & 1u)) {
+                if (jend - k0 < 32) {
+                    // the ragged end of the last tile: checked hi/lo form
+                    float D0[I][3];
+                    for (int jj = k0; jj < jend; jj += 4)
+                        group(jj, std::false_type{}, std::false_type{}, D0);
+                    ++near_visits;
+                } else if (FAR && ((fmask >> (k0 >> 5)) & 1u)) {
                     const float4 C = sub_s[k0 >> 5];
                     float D[I][3];
 #pragma unroll
@@ -1016,11 +1024,11 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
                         D[u][1] = (C.y - pi[u].yh) - pi[u].yl;
                         D[u][2] = (C.z - pi[u].zh) - pi[u].zl;
                     }
-                    for (int jj = k0; jj < jend; jj += 4) group(jj, std::true_type{}, D);
+                    for (int jj = k0; jj < jend; jj += 4) group(jj, std::true_type{}, std::true_type{}, D);
                     ++far_visits;
                 } else {
                     float D0[I][3];
-                    for (int jj = k0; jj < jend; jj += 4) group(jj, std::false_type{}, D0);
+                    for (int jj = k0; jj < jend; jj += 4) group(jj, std::false_type{}, std::true_type{}, D0);
                     ++near_visits;
                 }
             }
