@@ -253,6 +253,9 @@ int fsi_level_stats(fsi_ctx *ctx, long long *counts, int max);
  * (context precision; the symmetric kernels when fsi_params.symmetric, else the
  * one-sided ones) on the first n particles of pos/mass as one self-interacting set,
  * `reps` timed launches each after one warm-up, and keeps the fastest in the context.
+ * Symmetric variants are kept per set-size class (n < 32768, 32768 <= n < 196608,
+ * n >= 196608: small sets are latency-bound and favour few particles per thread); each
+ * class that n reaches is tuned on the first min(n, 8192), min(n, 65536) and n particles.
  * A variant is the number of active particles each thread holds in registers (low 4
  * bits, 1-6); one-sided mixed kernels add 16 to carry their per-tile partial sums as
  * float-float pairs instead of FP64; symmetric mixed kernels add 32 for the second form
@@ -268,9 +271,11 @@ int fsi_autotune(fsi_ctx *ctx, int N, const double *pos, const double *mass, int
                  void *stream);
 
 /* Read / set the pair-kernel variants (acc, grad) of the context precision and mode
- * (symmetric or one-sided).  fsi_set_tuning rejects variants the library was not built
- * with (FSI_ERR_ARG). */
+ * (symmetric or one-sided).  fsi_get_tuning reads the largest size class,
+ * fsi_get_tuning_for the class of a set of n particles; fsi_set_tuning sets every class
+ * and rejects variants the library was not built with (FSI_ERR_ARG). */
 int fsi_get_tuning(fsi_ctx *ctx, int *ipt_acc, int *ipt_grad);
+int fsi_get_tuning_for(fsi_ctx *ctx, int n, int *ipt_acc, int *ipt_grad);
 int fsi_set_tuning(fsi_ctx *ctx, int ipt_acc, int ipt_grad);
 
 /* ---- context-free, allocation-free variant ------------------------------------------- */

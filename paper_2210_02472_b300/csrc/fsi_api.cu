@@ -62,6 +62,12 @@ struct Buf {
 
 }  // namespace
 
+// Set-size classes of the symmetric variant table: the fastest kernel differs between
+// small sets (latency-bound, few CTAs: fewest particles per thread wins) and large ones.
+constexpr int kSymClasses = 3;
+constexpr int kSymClassMin[kSymClasses] = {0, 32768, 196608};
+inline int sym_class(int n) { return n >= kSymClassMin[2] ? 2 : (n >= kSymClassMin[1] ? 1 : 0); }
+
 struct fsi_ctx {
     fsi_params p;
     int device = 0;
@@ -78,7 +84,8 @@ struct fsi_ctx {
     int max_level_used = 0;
     int max_level_hit = 0;
     int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] one-sided kernel variant (pair_variants)
-    int symv[2][2] = {{2, 2}, {101, 100}};  // [precision][kind] symmetric kernel variant (sym_variants)
+    // [precision][kind][size class] symmetric kernel variant (sym_variants)
+    int symv[2][2][kSymClasses] = {{{2, 2, 2}, {2, 2, 2}}, {{2, 100, 101}, {2, 99, 100}}};
     long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
     // far-tile path of the symmetric mixed kernel: while far_n > 0, the records of the set
     // being stepped (n = far_n) have valid masses in rel[].w (step_core, autotune)
@@ -180,9 +187,11 @@ int order_threshold(const fsi_ctx* c) {
     return c->p.order_min > 0 ? c->p.order_min : kOrderMinDefault;
 }
 
-bool far_selected(const fsi_ctx* c) {
+// Does a set of n particles run a far-tile kernel (and so want Morton order)?
+bool far_selected(const fsi_ctx* c, int n) {
+    const int k = sym_class(n);
     return c->p.precision == FSI_MIXED && c->p.symmetric &&
-           ((c->symv[FSI_MIXED][KIND_ACC] & 64) || (c->symv[FSI_MIXED][KIND_GRAD] & 64));
+           ((c->symv[FSI_MIXED][KIND_ACC][k] & 64) || (c->symv[FSI_MIXED][KIND_GRAD][k] & 64));
 }
 
 // Morton order of a set: ordlist[k] = member at sorted position k (global index).
@@ -228,7 +237,7 @@ struct SameSetOrder {
     int begin(fsi_ctx* c, int N, const double* pos, const double* mass, const int* A, int n,
               cudaStream_t s) {
         list = A;
-        on = far_selected(c) && n >= order_threshold(c);
+        on = far_selected(c, n) && n >= order_threshold(c);
         if (!on) return FSI_OK;
         CK(order_set(c, N, pos, A, n, s));
         list = P<int>(c->ordlist);
@@ -262,7 +271,7 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
         a.iacc == a.jacc) {
         // self-interaction of one set: every unordered pair once, then the epilogue
         const int n = a.n_i;
-        const int sv = c->symv[prec][kind];
+        const int sv = c->symv[prec][kind][sym_class(n)];
         CK(ensure(c->accum, 3 * (size_t)n * sizeof(double)));
         CU(cudaMemsetAsync(c->accum.p, 0, 3 * (size_t)n * sizeof(double), s));
         const int chunk = choose_chunk(c, n, variant_ipt(sv));
@@ -329,7 +338,7 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     CK(ensure(c->accrec[0], pad_tile(n) * 32));
     CK(ensure(c->ac, 3 * (size_t)n * 8));
     FarGuard far_guard{c};
-    const bool far = far_selected(c) && n >= order_threshold(c);
+    const bool far = far_selected(c, n) && n >= order_threshold(c);
     if (far) {
         CK(order_set(c, N, pos, idx, n, s));
         idx = P<int>(c->ordlist);
@@ -1257,12 +1266,15 @@ int fsi_work_stats(fsi_ctx* c, long long* acc_pairs, long long* grad_pairs, int 
     return FSI_OK;
 }
 
-int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n, int reps,
-                 void* stream) {
-    CK(check_common(c, N));
-    if (n <= 0 || n > N || !pos || !mass) return fail(FSI_ERR_ARG, "bad autotune arguments");
-    if (reps <= 0) reps = 2;
-    const cudaStream_t s = S(stream);
+}  // extern "C"
+
+namespace {
+
+// Time every candidate variant of both kinds on the first n particles as one set and keep
+// the fastest in *slot(kind).
+template <class Slot>
+int tune_set(fsi_ctx* c, int N, const double* pos, const double* mass, int n, int reps,
+             cudaStream_t s, Slot slot) {
     const int prec = c->p.precision;
     CK(ensure(c->rec[0], pad_tile(n) * 32));
     CK(ensure(c->accrec[0], pad_tile(n) * 32));
@@ -1279,17 +1291,15 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    const bool was = c->profiling;
-    c->profiling = false;
     int rc = FSI_OK;
-    int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
     for (int kind = 0; kind < 2 && rc == FSI_OK; ++kind) {
         int cand[16];
         const int nc = c->p.symmetric ? sym_variants(prec, kind, cand) : pair_variants(prec, kind, cand);
         float best = 3.4e38f;
-        int best_ipt = table[prec][kind];
+        int& cur = slot(kind);
+        int best_v = cur;
         for (int v = 0; v < nc && rc == FSI_OK; ++v) {
-            table[prec][kind] = cand[v];
+            cur = cand[v];
             PairArgs a{};
             a.irec = a.jrec = c->rec[0].p;
             a.iacc = a.jacc = c->accrec[0].p;
@@ -1308,21 +1318,63 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
             }
             float ms = 0.f;
             cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; best_ipt = cand[v]; }
+            if (ms < best) { best = ms; best_v = cand[v]; }
         }
-        table[prec][kind] = best_ipt;
+        cur = best_v;
     }
-    c->profiling = was;
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     return rc;
 }
 
+}  // namespace
+
+extern "C" {
+
+int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n, int reps,
+                 void* stream) {
+    CK(check_common(c, N));
+    if (n <= 0 || n > N || !pos || !mass) return fail(FSI_ERR_ARG, "bad autotune arguments");
+    if (reps <= 0) reps = 2;
+    const cudaStream_t s = S(stream);
+    const int prec = c->p.precision;
+    const bool was = c->profiling;
+    c->profiling = false;
+    int rc = FSI_OK;
+    if (!c->p.symmetric) {
+        rc = tune_set(c, N, pos, mass, n, reps, s, [&](int kind) -> int& { return c->ipt[prec][kind]; });
+    } else {
+        // one sample per size class that n reaches: 8192 (or n), 65536 (or n), n
+        for (int k = 0; k < kSymClasses && rc == FSI_OK; ++k) {
+            const int hi = k + 1 < kSymClasses ? kSymClassMin[k + 1] : INT_MAX;
+            if (n < kSymClassMin[k]) break;
+            int m = k == 0 ? std::min(n, 8192) : k == 1 ? std::min(n, 65536) : n;
+            m = std::min(std::max(m, kSymClassMin[k]), hi - 1);
+            if (m > n) break;
+            rc = tune_set(c, N, pos, mass, m, reps, s,
+                          [&](int kind) -> int& { return c->symv[prec][kind][k]; });
+        }
+    }
+    c->profiling = was;
+    return rc;
+}
+
 int fsi_get_tuning(fsi_ctx* c, int* ipt_acc, int* ipt_grad) {
     if (!c) return fail(FSI_ERR_ARG, "NULL context");
-    int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
-    if (ipt_acc) *ipt_acc = table[c->p.precision][KIND_ACC];
-    if (ipt_grad) *ipt_grad = table[c->p.precision][KIND_GRAD];
+    const int prec = c->p.precision;
+    const int k = kSymClasses - 1;
+    if (ipt_acc) *ipt_acc = c->p.symmetric ? c->symv[prec][KIND_ACC][k] : c->ipt[prec][KIND_ACC];
+    if (ipt_grad) *ipt_grad = c->p.symmetric ? c->symv[prec][KIND_GRAD][k] : c->ipt[prec][KIND_GRAD];
+    return FSI_OK;
+}
+
+int fsi_get_tuning_for(fsi_ctx* c, int n, int* ipt_acc, int* ipt_grad) {
+    if (!c) return fail(FSI_ERR_ARG, "NULL context");
+    if (n < 0) return fail(FSI_ERR_ARG, "negative set size");
+    const int prec = c->p.precision;
+    const int k = sym_class(n);
+    if (ipt_acc) *ipt_acc = c->p.symmetric ? c->symv[prec][KIND_ACC][k] : c->ipt[prec][KIND_ACC];
+    if (ipt_grad) *ipt_grad = c->p.symmetric ? c->symv[prec][KIND_GRAD][k] : c->ipt[prec][KIND_GRAD];
     return FSI_OK;
 }
 
@@ -1337,9 +1389,15 @@ int fsi_set_tuning(fsi_ctx* c, int ipt_acc, int ipt_grad) {
         for (int v = 0; v < nc; ++v) ok |= cand[v] == want;
         if (!ok) return fail(FSI_ERR_ARG, "unsupported kernel variant %d", want);
     }
-    int (*table)[2] = c->p.symmetric ? c->symv : c->ipt;
-    table[prec][KIND_ACC] = ipt_acc;
-    table[prec][KIND_GRAD] = ipt_grad;
+    if (c->p.symmetric) {
+        for (int k = 0; k < kSymClasses; ++k) {
+            c->symv[prec][KIND_ACC][k] = ipt_acc;
+            c->symv[prec][KIND_GRAD][k] = ipt_grad;
+        }
+    } else {
+        c->ipt[prec][KIND_ACC] = ipt_acc;
+        c->ipt[prec][KIND_GRAD] = ipt_grad;
+    }
     return FSI_OK;
 }
 

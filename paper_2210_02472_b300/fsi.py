@@ -41,7 +41,7 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall",
-            "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats"]
+            "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for"]
 
 
 class fsi_params(C.Structure):
@@ -78,6 +78,7 @@ _lib.fsi_far_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longl
 _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
 _lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
+_lib.fsi_get_tuning_for.argtypes = [_vp, _ip, C.POINTER(_ip), C.POINTER(_ip)]
 _lib.fsi_set_tuning.argtypes = [_vp, _ip, _ip]
 _lib.fsi_batch_create.argtypes = [_vp, _ip, C.POINTER(C.c_longlong), _ip, C.POINTER(_vp)]
 _lib.fsi_batch_destroy.argtypes = [_vp]
@@ -318,12 +319,20 @@ def fsi_autotune(ctx: Context, pos, mass, n: int = 0, reps: int = 2, stream=None
     n = N if n <= 0 else min(n, N)
     _check(_lib.fsi_autotune(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
                              int(n), int(reps), _stream(stream)), "fsi_autotune")
-    return fsi_get_tuning(ctx)
+    return fsi_get_tuning_for(ctx, n)
 
 
 def fsi_get_tuning(ctx: Context):
+    """(acc, grad) variants of the largest set-size class."""
     a, g = _ip(), _ip()
     _check(_lib.fsi_get_tuning(ctx.handle, C.byref(a), C.byref(g)), "fsi_get_tuning")
+    return int(a.value), int(g.value)
+
+
+def fsi_get_tuning_for(ctx: Context, n: int):
+    """(acc, grad) variants a set of n particles runs."""
+    a, g = _ip(), _ip()
+    _check(_lib.fsi_get_tuning_for(ctx.handle, int(n), C.byref(a), C.byref(g)), "fsi_get_tuning_for")
     return int(a.value), int(g.value)
 
 

@@ -213,3 +213,19 @@ def test_autotune_times_far_variants_in_order(F, cluster):
         a = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass)))
         assert F.fsi_sync_status(ctx) == F.FSI_OK
     assert (np.abs(a[:, rows] - ref_a).max(axis=0) / sa).max() <= 1e-6
+
+
+def test_size_class_tuning_tables(F):
+    """Symmetric variants are kept per set-size class (< 32768, < 196608, larger):
+    mixed defaults are the first form with 2 particles per thread for small sets and the
+    far-tile second form above; fsi_set_tuning fixes every class."""
+    with F.Context("mixed") as ctx:
+        assert F.fsi_get_tuning_for(ctx, 1000) == (2, 2)
+        assert F.fsi_get_tuning_for(ctx, 40000) == (100, 99)
+        assert F.fsi_get_tuning_for(ctx, 1 << 20) == (101, 100)
+        assert F.fsi_get_tuning(ctx) == (101, 100)
+        F.fsi_set_tuning(ctx, 36, 36)
+        for n in (10, 40000, 1 << 20):
+            assert F.fsi_get_tuning_for(ctx, n) == (36, 36)
+    with F.Context("fp64") as ctx:
+        assert F.fsi_get_tuning_for(ctx, 1000) == (2, 2)
