@@ -45,11 +45,13 @@ FLOP_PAIR = FLOP_ACC + FLOP_GRAD
 SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
 CPU_ROWS = 4096
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
-# kernel, from one one-pass ncu capture of this benchmark's own workload (`--tuning 101,100
-# --steps 1 --warmup 3`, mean of the cycle's three acceleration launches).  Keyed by
+# kernel, from one one-pass ncu capture of this benchmark's own workload (`--tuning A,G
+# --steps 1 --warmup 3` with the kernel's variant, mean of the cycle's three acceleration
+# launches).  Keyed by
 # (kernel label, workload, N); a kernel changed since the capture must drop its entry, and
 # any other configuration reports null.
-DRAM_TRAFFIC = {("sym_mixed_v2_kernel<acc, I=5, far>", "kroupa1m_bh16", 1048592): 201.9e6}
+DRAM_TRAFFIC = {("sym_mixed_v2_kernel<acc, I=5, far>", "kroupa1m_bh16", 1048592): 201.9e6,
+                ("sym_mixed_x2_kernel<acc, I=6, MINB=2>", "kroupa1m_bh16", 1048592): 256.3e6}
 
 
 def step_interactions(n: int) -> float:
@@ -234,7 +236,7 @@ def run_fsi(args):
         tuning = tuple(int(x) for x in args.tuning.split(","))
         F.fsi_set_tuning(ctx, *tuning)
     else:
-        tuning = F.fsi_autotune(ctx, pos, mass, n=min(N, 1 << 18))   # variant per kernel kind
+        tuning = F.fsi_autotune(ctx, pos, mass, n=N, reps=1)   # variant per kernel kind
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)   # 256 MB > L2
     stream = torch.cuda.current_stream()
 
@@ -307,8 +309,12 @@ def run_fsi(args):
     peak_mhz = SM_MAX_MHZ
     peak = fp32_peak_tflops(peak_mhz) if args.precision == "mixed" else args.fp64_peak_tflops
     var = tuning[0 if dom == "acc" else 1]
-    kname = (f"sym_mixed_v2_kernel<{dom}, I={var & 15}{', far' if var & 64 else ''}>" if var & 32
-             else f"sym_pair_kernel<{args.precision}, {dom}, I={var & 15}>")
+    if var & 128:
+        kname = f"sym_mixed_x2_kernel<{dom}, I={var & 15}, MINB={1 if var & 16 else 2}>"
+    elif var & 32:
+        kname = f"sym_mixed_v2_kernel<{dom}, I={var & 15}{', far' if var & 64 else ''}>"
+    else:
+        kname = f"sym_pair_kernel<{args.precision}, {dom}, I={var & 15}>"
     traffic = DRAM_TRAFFIC.get((kname, args.workload if not args.n else "", N))
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": kname,
@@ -542,6 +548,91 @@ def run_hhs(args):
     return 0
 
 
+def probe_peak_tflops(F, mode: int) -> float:
+    """FMA throughput of this GPU measured by the library's probe (0: FP32, 1: FP64,
+    2: packed FP32x2): best of 3 launches of 8 CTAs per SM."""
+    import torch
+    blocks = 148 * 8
+    iters = 400 if mode == 1 else 20000
+    sink = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
+    F.fsi_fma_probe(mode, blocks, iters, sink)
+    best = 0.0
+    for _ in range(3):
+        e0, e1 = _timed_events(None)
+        e0.record()
+        fl = F.fsi_fma_probe(mode, blocks, iters, sink)
+        e1.record()
+        torch.cuda.synchronize()
+        best = max(best, fl / (e0.elapsed_time(e1) / 1e3) / 1e12)
+    return best
+
+
+def run_accgrad(args):
+    """One same-set acceleration pass plus one force-gradient pass over all N(N-1) ordered
+    pairs (fsi_accel_grad), the north star's acc+grad measurement, in either precision;
+    each pass against the FMA peak of its pipe measured by the probe in the same run."""
+    import torch
+    from paper_2210_02472_b300 import fsi as F
+    torch.cuda.set_device(0)
+    c = inputs.workload(args.workload)
+    if args.n:
+        c = inputs.plummer(args.n, inputs.SEED_BASE + 3, imf="kroupa", n_bh=16)
+    N = c.n
+    dev = torch.device("cuda", 0)
+    pos = torch.as_tensor(c.pos).to(dev)
+    mass = torch.as_tensor(c.mass).to(dev)
+    ctx = F.Context(args.precision)
+    if args.tuning:
+        F.fsi_set_tuning(ctx, *(int(x) for x in args.tuning.split(",")))
+    tuning = F.fsi_get_tuning_for(ctx, N)
+    # warm-up on a 2^16 subset (same kernels), then the full set
+    sub = torch.arange(0, min(N, 65536), dtype=torch.int32, device=dev)
+    for _ in range(max(1, args.warmup)):
+        F.fsi_accel_grad(ctx, pos, None, mass, sub, sub)
+    torch.cuda.synchronize()
+    peak_fp32 = probe_peak_tflops(F, 0)
+    peak_fp64 = probe_peak_tflops(F, 1)
+    sampler = ClockSampler(0)
+    sampler.start()
+    F.fsi_profile(ctx, True)
+    e0, e1 = _timed_events(None)
+    e0.record()
+    for _ in range(args.steps):
+        F.fsi_accel_grad(ctx, pos, None, mass)
+    e1.record()
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = F.fsi_profile_read(ctx)
+    F.fsi_profile(ctx, False)
+    assert F.fsi_sync_status(ctx) == F.FSI_OK
+    t = e0.elapsed_time(e1) / 1e3
+    pairs = float(N) * (N - 1)
+    value = pairs * args.steps / t
+    peak = peak_fp32 if args.precision == "mixed" else peak_fp64
+    kern = {}
+    for k, fl in (("acc", FLOP_ACC), ("grad", FLOP_GRAD)):
+        nl, ms = prof[k]
+        ach = pairs * fl / (ms / nl / 1e3) / 1e12
+        kern[k] = {"ms_per_launch": ms / nl, "launches": nl, "achieved_tflops": ach,
+                   "frac_of_probe_peak": ach / peak,
+                   "frac_of_nominal_fp32": ach / fp32_peak_tflops() if args.precision == "mixed" else None}
+    line = {
+        "metric": f"acc+grad pair interactions/s at N={N} ({args.precision}, one acc + one grad pass)",
+        "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
+        "data": "synthetic",
+        "config": {"workload": args.workload if not args.n else f"plummer_kroupa_bh16_{N}", "n": N,
+                   "precision": args.precision, "tuning": list(tuning),
+                   "flops": "acc pair 20, grad pair 36"},
+        "probe_peaks_tflops": {"fp32": peak_fp32, "fp64": peak_fp64},
+        "kernels": kern, "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -558,9 +649,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning", default="", help="fixed pair-kernel variants 'acc,grad' "
                     "(see fsi_set_tuning); default: autotune on a 2^18 sample")
-    ap.add_argument("--mode", default="cycle", choices=["cycle", "ensemble", "vjp", "hhs"],
+    ap.add_argument("--mode", default="cycle", choices=["cycle", "ensemble", "vjp", "hhs", "accgrad"],
                     help="cycle: the headline FSI-cycle benchmark; the others measure the "
-                         "ensemble, adjoint and HHS workloads")
+                         "ensemble, adjoint and HHS workloads and one acc + grad pass")
     ap.add_argument("--batch-steps", type=int, default=10)
     ap.add_argument("--vjp-steps", type=int, default=200)
     ap.add_argument("--fd-components", type=int, default=3)
@@ -576,6 +667,8 @@ def main():
         return run_vjp(args)
     if args.mode == "hhs":
         return run_hhs(args)
+    if args.mode == "accgrad":
+        return run_accgrad(args)
     return run_fsi(args)
 
 

@@ -326,10 +326,11 @@ int fsi_far_stats(fsi_ctx *ctx, long long *far_visits, long long *near_visits, i
 /* Number of kernels this library has launched in this process (all contexts). */
 long long fsi_launch_count(void);
 
-/* FP32 (fp64 = 0) or FP64 (fp64 = 1) fused multiply-add throughput probe: launches
- * `blocks` CTAs of 256 threads, each thread running 8 independent FMA chains for
- * `iters` iterations, writing one value per thread to sink (device, blocks*256 entries of
- * the probe's type).  *flops receives the nominal flop count (2 per FMA).  Time it with
+/* FP32 (fp64 = 0), FP64 (fp64 = 1) or packed FP32x2 (fp64 = 2, fma.rn.f32x2) fused
+ * multiply-add throughput probe: launches `blocks` CTAs of 256 threads, each thread
+ * running 8 independent FMA chains for `iters` iterations, writing one value per thread
+ * to sink (device, blocks*256 entries of the probe's scalar type: float for 0 and 2).
+ * *flops receives the nominal flop count (2 per FMA, 4 per packed FMA).  Time it with
  * CUDA events on `stream`.  The paper has no counterpart: it measures the pipe peaks
  * that the pair kernels' roofline fractions are quoted against. */
 int fsi_fma_probe(int fp64, int blocks, int iters, void *sink, double *flops, void *stream);

@@ -85,7 +85,7 @@ struct fsi_ctx {
     int max_level_hit = 0;
     int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] one-sided kernel variant (pair_variants)
     // [precision][kind][size class] symmetric kernel variant (sym_variants)
-    int symv[2][2][kSymClasses] = {{{2, 2, 2}, {2, 2, 2}}, {{2, 100, 101}, {2, 99, 100}}};
+    int symv[2][2][kSymClasses] = {{{2, 2, 2}, {2, 2, 2}}, {{2, 228, 230}, {2, 228, 246}}};
     long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
     // far-tile path of the symmetric mixed kernel: while far_n > 0, the records of the set
     // being stepped (n = far_n) have valid masses in rel[].w (step_core, autotune)
@@ -1417,9 +1417,10 @@ int fsi_far_stats(fsi_ctx* c, long long* far_visits, long long* near_visits, int
 }
 
 int fsi_fma_probe(int fp64, int blocks, int iters, void* sink, double* flops, void* stream) {
-    if (blocks <= 0 || iters <= 0 || !sink) return fail(FSI_ERR_ARG, "bad probe arguments");
+    if (blocks <= 0 || iters <= 0 || !sink || fp64 < 0 || fp64 > 2)
+        return fail(FSI_ERR_ARG, "bad probe arguments");
     CU(launch_fma_probe(fp64, blocks, iters, sink, S(stream)));
-    if (flops) *flops = (double)blocks * 256.0 * (double)iters * 4.0 * 8.0 * 2.0;
+    if (flops) *flops = (double)blocks * 256.0 * (double)iters * 4.0 * 8.0 * (fp64 == 2 ? 4.0 : 2.0);
     return FSI_OK;
 }
 

@@ -1075,6 +1075,464 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
     }
 }
 
+// ---------------------------------------------------------------------------------
+// Symmetric mixed kernel, packed form: the second form's work decomposition with the pair
+// arithmetic on packed FP32 pairs (add/mul/fma.rn.f32x2, sm_100 and later).  The pair
+// kernels are bound by instruction issue (every FP32 instruction, MUFU, shuffle and
+// shared-memory load takes an issue slot); one packed instruction does two FP32 lane
+// operations, so the FP32 pipe, not issue, becomes the limit.
+//  - a thread's I particles (I even) form I/2 packed pairs (particles 2p, 2p+1 in the
+//    low / high half); every source value is broadcast into both halves;
+//  - per source, the j-side partials of the two halves are added once (one FP32 add per
+//    component) before the warp reduce-scatter of the second form;
+//  - the per-pair arithmetic is the second form's, operation for operation, so each
+//    half rounds exactly as the scalar code does; only the order of the j-side sums
+//    differs.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ void set_half(float2& d, int h, float v) {
+    if (h) d.y = v;
+    else d.x = v;
+}
+__device__ __forceinline__ float2 rsqrt2(float2 v) { return make_float2(rsqrt_hw(v.x), rsqrt_hw(v.y)); }
+
+// Float-float accumulation of two sums at once: (hi, lo) += v by the TwoSum of Knuth
+// (six FP32 operations, exact error term; s - a formed as fma(a, -1, s), one rounding),
+// acc = (hi_0, hi_1, lo_0, lo_1).  Keeps ~48 bits across source tiles without FP64
+// instructions (the B300 FP64 unit issues ~1/64 of the FP32 rate).
+__device__ __forceinline__ void ff_add2(float4& acc, const float2 v) {
+    const float2 m1 = bc2(-1.0f);
+    const float2 hi = make_float2(acc.x, acc.y);
+    const float2 s = __fadd2_rn(hi, v);
+    const float2 bb = __ffma2_rn(hi, m1, s);                  // s - hi
+    const float2 e1 = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, hi);   // hi - (s - bb)
+    const float2 e2 = __ffma2_rn(bb, m1, v);                  // v - bb
+    const float2 lo = __fadd2_rn(make_float2(acc.z, acc.w), __fadd2_rn(e1, e2));
+    acc = make_float4(s.x, s.y, lo.x, lo.y);
+}
+
+// i-side state of a packed pair of particles (low half: particle 2p, high half: 2p+1).
+struct X2I {
+    float2 nxh, nyh, nzh, nxl, nyl, nzl;   // -xh, -yh, -zh, -xl, -yl, -zl
+    float2 nA, nB;                         // -2.5 m_i, +1.5 m_i (near acc j-side weight)
+    float2 nm;                             // -m_i
+    float2 nax, nay, naz;                  // gradient: -a_i
+};
+
+// hi/lo separation of a source from both particles of a pair.
+__device__ __forceinline__ void x2_sep_near(const float4 h, const float4 l, const X2I& p,
+                                            float2& dx, float2& dy, float2& dz) {
+    dx = __fadd2_rn(__fadd2_rn(bc2(h.x), p.nxh), __fadd2_rn(bc2(l.x), p.nxl));
+    dy = __fadd2_rn(__fadd2_rn(bc2(h.y), p.nyh), __fadd2_rn(bc2(l.y), p.nyl));
+    dz = __fadd2_rn(__fadd2_rn(bc2(h.z), p.nzh), __fadd2_rn(bc2(l.z), p.nzl));
+}
+
+// y = r^-1 (hardware), y2 = y^2, sres = r^2 y^2 (= 1 - e), y3 = y^3.
+__device__ __forceinline__ void x2_geom(float2 dx, float2 dy, float2 dz, float2 eps2, float2& y2,
+                                        float2& sres, float2& y3) {
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    const float2 y = rsqrt2(r2);
+    y2 = __fmul2_rn(y, y);
+    sres = __fmul2_rn(r2, y2);
+    y3 = __fmul2_rn(y2, y);
+}
+
+__device__ __forceinline__ void x2_acc_acc(float2 wi, float2 wj, float2 dx, float2 dy, float2 dz,
+                                           float2 (&fi)[3], float2 (&fj)[3]) {
+    fi[0] = __ffma2_rn(wi, dx, fi[0]); fi[1] = __ffma2_rn(wi, dy, fi[1]); fi[2] = __ffma2_rn(wi, dz, fi[2]);
+    fj[0] = __ffma2_rn(wj, dx, fj[0]); fj[1] = __ffma2_rn(wj, dy, fj[1]); fj[2] = __ffma2_rn(wj, dz, fj[2]);
+}
+
+__device__ __forceinline__ void x2_acc_near(const float4 h, const float4 l, const X2I& p, float2 eps2,
+                                            float2 (&fi)[3], float2 (&fj)[3]) {
+    float2 dx, dy, dz, y2, sres, y3;
+    x2_sep_near(h, l, p, dx, dy, dz);
+    x2_geom(dx, dy, dz, eps2, y2, sres, y3);
+    const float2 wi = __fmul2_rn(y3, __ffma2_rn(sres, bc2(l.w), bc2(h.w)));   //  m_j r^-3
+    const float2 wj = __fmul2_rn(y3, __ffma2_rn(sres, p.nB, p.nA));           // -m_i r^-3
+    x2_acc_acc(wi, wj, dx, dy, dz, fi, fj);
+}
+
+__device__ __forceinline__ void x2_acc_far(const float4 r, const float2 (&D)[3], const X2I& p,
+                                           float2 eps2, float2 (&fi)[3], float2 (&fj)[3]) {
+    const float2 dx = __fadd2_rn(D[0], bc2(r.x)), dy = __fadd2_rn(D[1], bc2(r.y)),
+                 dz = __fadd2_rn(D[2], bc2(r.z));
+    float2 y2, sres, y3;
+    x2_geom(dx, dy, dz, eps2, y2, sres, y3);
+    const float2 r3 = __fmul2_rn(y3, __ffma2_rn(sres, bc2(-1.5f), bc2(2.5f)));
+    const float2 wi = __fmul2_rn(r3, bc2(r.w));
+    const float2 wj = __fmul2_rn(r3, p.nm);
+    x2_acc_acc(wi, wj, dx, dy, dz, fi, fj);
+}
+
+// T(d) b = r^-3 b - 3 r^-5 (b.d) d with b = a_j - a_i; on i with weight m_j, on j with -m_i.
+__device__ __forceinline__ void x2_grad_tail(float2 dx, float2 dy, float2 dz, float2 y2, float2 sres,
+                                             float2 y3, const float4 aj, const X2I& p,
+                                             float2 (&gi)[3], float2 (&gj)[3]) {
+    const float2 r3 = __fmul2_rn(y3, __ffma2_rn(sres, bc2(-1.5f), bc2(2.5f)));   // r^-3 (refined)
+    const float2 bx = __fadd2_rn(bc2(aj.x), p.nax), by = __fadd2_rn(bc2(aj.y), p.nay),
+                 bz = __fadd2_rn(bc2(aj.z), p.naz);
+    const float2 dot = __ffma2_rn(bx, dx, __ffma2_rn(by, dy, __fmul2_rn(bz, dz)));
+    const float2 q = __fmul2_rn(r3, __fmul2_rn(y2, __ffma2_rn(bc2(3.0f), sres, bc2(-6.0f))));
+    const float2 s = __fmul2_rn(q, dot);
+    const float2 tx = __ffma2_rn(r3, bx, __fmul2_rn(s, dx)), ty = __ffma2_rn(r3, by, __fmul2_rn(s, dy)),
+                 tz = __ffma2_rn(r3, bz, __fmul2_rn(s, dz));
+    const float2 mj = bc2(aj.w);
+    gi[0] = __ffma2_rn(mj, tx, gi[0]); gi[1] = __ffma2_rn(mj, ty, gi[1]); gi[2] = __ffma2_rn(mj, tz, gi[2]);
+    gj[0] = __ffma2_rn(p.nm, tx, gj[0]); gj[1] = __ffma2_rn(p.nm, ty, gj[1]); gj[2] = __ffma2_rn(p.nm, tz, gj[2]);
+}
+
+__device__ __forceinline__ void x2_grad_near(const float4 h, const float4 l, const float4 aj, const X2I& p,
+                                             float2 eps2, float2 (&gi)[3], float2 (&gj)[3]) {
+    float2 dx, dy, dz, y2, sres, y3;
+    x2_sep_near(h, l, p, dx, dy, dz);
+    x2_geom(dx, dy, dz, eps2, y2, sres, y3);
+    x2_grad_tail(dx, dy, dz, y2, sres, y3, aj, p, gi, gj);
+}
+
+__device__ __forceinline__ void x2_grad_far(const float4 r, const float4 aj, const float2 (&D)[3],
+                                            const X2I& p, float2 eps2, float2 (&gi)[3], float2 (&gj)[3]) {
+    const float2 dx = __fadd2_rn(D[0], bc2(r.x)), dy = __fadd2_rn(D[1], bc2(r.y)),
+                 dz = __fadd2_rn(D[2], bc2(r.z));
+    float2 y2, sres, y3;
+    x2_geom(dx, dy, dz, eps2, y2, sres, y3);
+    x2_grad_tail(dx, dy, dz, y2, sres, y3, aj, p, gi, gj);
+}
+
+// One group of 4 sources of the packed kernel (lane l visits source jj + (g ^ (l >> 3)) at
+// step g); FG selects the far form, FULL drops the bounds check (a full 32-record sub-tile).
+// The j-side totals of the group are left in jpart (one row per warp).
+template <int KIND, int NP, bool FG, bool FULL>
+__device__ __forceinline__ void x2_group(int jj, int cnt, int lane, int warp, const RecMix* rec,
+                                         const float4* arec, const float4* rel_s,
+                                         const X2I (&pp)[NP], const float2 (&D)[NP][3],
+                                         float2 eps2, float2 (&f)[NP][3], float* jpart) {
+    const int L = lane >> 3;
+    float fj[4][3];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        fj[g][0] = fj[g][1] = fj[g][2] = 0.f;
+        const int jg = jj + (g ^ L);
+        if (FULL || jg < cnt) {
+            float2 pj[3];
+            pj[0] = make_float2(0.f, 0.f);
+            pj[1] = make_float2(0.f, 0.f);
+            pj[2] = make_float2(0.f, 0.f);
+            if constexpr (FG) {
+                const float4 r = rel_s[jg];
+                if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) x2_acc_far(r, D[p], pp[p], eps2, f[p], pj);
+                } else {
+                    const float4 aj = arec[jg];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) x2_grad_far(r, aj, D[p], pp[p], eps2, f[p], pj);
+                }
+            } else {
+                const float4 h = rec[jg].hi;
+                const float4 l = rec[jg].lo;
+                if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) x2_acc_near(h, l, pp[p], eps2, f[p], pj);
+                } else {
+                    const float4 aj = arec[jg];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) x2_grad_near(h, l, aj, pp[p], eps2, f[p], pj);
+                }
+            }
+            fj[g][0] = pj[0].x + pj[0].y;
+            fj[g][1] = pj[1].x + pj[1].y;
+            fj[g][2] = pj[2].x + pj[2].y;
+        }
+    }
+    float tot[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const float k0 = fj[0][q] + __shfl_xor_sync(0xffffffffu, fj[2][q], 16);
+        const float k1 = fj[1][q] + __shfl_xor_sync(0xffffffffu, fj[3][q], 16);
+        float r = k0 + __shfl_xor_sync(0xffffffffu, k1, 8);
+        r += __shfl_xor_sync(0xffffffffu, r, 4);
+        r += __shfl_xor_sync(0xffffffffu, r, 2);
+        r += __shfl_xor_sync(0xffffffffu, r, 1);
+        tot[q] = r;
+    }
+    const int jl = jj + L;
+    if ((lane & 7) == 0 && (FULL || jl < cnt)) {
+        float* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
+        dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+    }
+}
+
+template <int KIND, int I, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymArgs a) {
+    static_assert(kThreads == kTileJ, "an i-block spans I source tiles");
+    static_assert(I % 2 == 0, "particles are handled in packed pairs");
+    constexpr int NP = I / 2;
+    constexpr int ACCREC = SymCfg<FSI_MIXED, KIND>::ACCREC;
+    constexpr int RELB = 16;
+    constexpr int SUBB = (kTileJ / 32) * 16;
+    constexpr int SB = kTileJ * (kRec + ACCREC + RELB) + SUBB;
+    constexpr int JPART = SymCfg<FSI_MIXED, KIND>::JPART;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ float wbox[kThreads / 32][6];
+    float* jpart = reinterpret_cast<float*>(smem + kStages * SB);
+    // i-side sums across tiles as float-float pairs: acc_s[(p * 3 + q) * kThreads + tid] =
+    // (hi of 2p, hi of 2p+1, lo of 2p, lo of 2p+1) for component q
+    float4* acc_s = reinterpret_cast<float4*>(smem + kStages * SB + JPART);
+
+    const int b = blockIdx.x / (1 + a.nchunk);
+    const int c = blockIdx.x % (1 + a.nchunk);
+    const int ntj = (a.n + kTileJ - 1) / kTileJ;
+    const bool diag = (c == 0);
+    int t0, t1;
+    if (diag) { t0 = b * I; t1 = min((b + 1) * I, ntj); }
+    else { t0 = (b + 1) * I + (c - 1) * a.chunk; t1 = min(t0 + a.chunk, ntj); }
+    if (t0 >= t1) return;
+    const int ntiles = t1 - t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = b * (kThreads * I);
+    const bool far_on = a.rel != nullptr && !diag;
+
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int st = t % kStages;
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n - jt);
+        const int nsub = (cnt + 31) >> 5;
+        unsigned char* base = smem + st * SB;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC) +
+                                             (far_on ? (uint32_t)(cnt * 16 + nsub * 16) : 0u));
+        bulk_g2s(base, (const unsigned char*)a.rec + (size_t)jt * kRec, (uint32_t)cnt * kRec, &bars[st]);
+        if (ACCREC)
+            bulk_g2s(base + kTileJ * kRec, (const unsigned char*)a.accrec + (size_t)jt * ACCREC,
+                     (uint32_t)cnt * ACCREC, &bars[st]);
+        if (far_on) {
+            bulk_g2s(base + kTileJ * (kRec + ACCREC), (const unsigned char*)(a.rel + jt),
+                     (uint32_t)cnt * 16, &bars[st]);
+            bulk_g2s(base + kTileJ * (kRec + ACCREC + RELB), (const unsigned char*)(a.sub + jt / 32),
+                     (uint32_t)nsub * 16, &bars[st]);
+        }
+    };
+    if (tid == 0)
+        for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+
+    X2I pp[NP];
+    float2 f[NP][3];
+    const int ib = i0 + warp * (32 * I) + lane;     // particle u of this thread: ib + 32 u
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        const bool valid = ib + 32 * u < a.n;
+        const int i = min(ib + 32 * u, a.n - 1);
+        const RecMix r = reinterpret_cast<const RecMix*>(a.rec)[i];
+        float nm = 0.f, nax = 0.f, nay = 0.f, naz = 0.f;
+        if constexpr (KIND == KIND_GRAD) {
+            const float4 ai = reinterpret_cast<const float4*>(a.accrec)[i];
+            nax = -ai.x; nay = -ai.y; naz = -ai.z;
+            nm = valid ? -ai.w : 0.f;
+        } else {
+            nm = (far_on && valid) ? -a.rel[i].w : 0.f;    // -m_i for the far form
+        }
+        const int h = u & 1;
+        X2I& q = pp[u >> 1];
+        set_half(q.nxh, h, -r.hi.x); set_half(q.nyh, h, -r.hi.y); set_half(q.nzh, h, -r.hi.z);
+        set_half(q.nxl, h, -r.lo.x); set_half(q.nyl, h, -r.lo.y); set_half(q.nzl, h, -r.lo.z);
+        set_half(q.nA, h, valid ? -r.hi.w : 0.f);
+        set_half(q.nB, h, valid ? -r.lo.w : 0.f);
+        set_half(q.nm, h, nm);
+        set_half(q.nax, h, nax); set_half(q.nay, h, nay); set_half(q.naz, h, naz);
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        f[p][0] = f[p][1] = f[p][2] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc_s[(p * 3 + q) * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    if (far_on) {
+        // box of the warp's particles (FP32 high parts)
+        float bl[3] = {-pp[0].nxh.x, -pp[0].nyh.x, -pp[0].nzh.x};
+        float bh[3] = {bl[0], bl[1], bl[2]};
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            bl[0] = fminf(bl[0], -fmaxf(pp[p].nxh.x, pp[p].nxh.y));
+            bl[1] = fminf(bl[1], -fmaxf(pp[p].nyh.x, pp[p].nyh.y));
+            bl[2] = fminf(bl[2], -fmaxf(pp[p].nzh.x, pp[p].nzh.y));
+            bh[0] = fmaxf(bh[0], -fminf(pp[p].nxh.x, pp[p].nxh.y));
+            bh[1] = fmaxf(bh[1], -fminf(pp[p].nyh.x, pp[p].nyh.y));
+            bh[2] = fmaxf(bh[2], -fminf(pp[p].nzh.x, pp[p].nzh.y));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                bl[q] = fminf(bl[q], __shfl_xor_sync(0xffffffffu, bl[q], o));
+                bh[q] = fmaxf(bh[q], __shfl_xor_sync(0xffffffffu, bh[q], o));
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { wbox[warp][q] = bl[q]; wbox[warp][3 + q] = bh[q]; }
+        __syncwarp();
+    }
+    const float eps2f = (float)a.eps2;
+    const float2 eps2 = bc2(eps2f);
+    unsigned far_visits = 0, near_visits = 0;
+    bool aborted = false;
+    int t_stop = ntiles;
+    for (int t = 0; t < ntiles; ++t) {
+        const int st = t % kStages;
+        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n - jt);
+        const unsigned char* base = smem + st * SB;
+        const RecMix* rec = reinterpret_cast<const RecMix*>(base);
+        const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
+        const float4* rel_s = reinterpret_cast<const float4*>(base + kTileJ * (kRec + ACCREC));
+        const float4* sub_s = reinterpret_cast<const float4*>(base + kTileJ * (kRec + ACCREC + RELB));
+        if (diag) {
+            // the block's own tiles: one-sided scalar loop with the self pair excluded by index
+            MixI q[I];
+            float fs[I][3];
+#pragma unroll
+            for (int u = 0; u < I; ++u) {
+                const X2I& s = pp[u >> 1];
+                const bool hi = (u & 1) != 0;
+                q[u].xh = -(hi ? s.nxh.y : s.nxh.x); q[u].yh = -(hi ? s.nyh.y : s.nyh.x);
+                q[u].zh = -(hi ? s.nzh.y : s.nzh.x); q[u].xl = -(hi ? s.nxl.y : s.nxl.x);
+                q[u].yl = -(hi ? s.nyl.y : s.nyl.x); q[u].zl = -(hi ? s.nzl.y : s.nzl.x);
+                q[u].ax = -(hi ? s.nax.y : s.nax.x); q[u].ay = -(hi ? s.nay.y : s.nay.x);
+                q[u].az = -(hi ? s.naz.y : s.naz.x);
+                fs[u][0] = fs[u][1] = fs[u][2] = 0.f;
+            }
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 h = rec[jj].hi;
+                const float4 l = rec[jj].lo;
+                if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                    for (int u = 0; u < I; ++u)
+                        mix_acc_pair<true>(h, l, q[u], eps2f, jt + jj == ib + 32 * u, fs[u][0], fs[u][1], fs[u][2]);
+                } else {
+                    const float4 aj = arec[jj];
+#pragma unroll
+                    for (int u = 0; u < I; ++u)
+                        mix_grad_pair<true>(h, l, aj, q[u], eps2f, jt + jj == ib + 32 * u, fs[u][0], fs[u][1], fs[u][2]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q)
+                    ff_add2(acc_s[(p * 3 + q) * kThreads + tid], make_float2(fs[2 * p][q], fs[2 * p + 1][q]));
+        } else {
+            unsigned fmask = 0;
+            if (far_on) {
+                bool fr = false;
+                if (lane < ((cnt + 31) >> 5)) {
+                    const float4 sb = sub_s[lane];
+                    const float* wb = wbox[warp];
+                    const float gx = fmaxf(0.f, fmaxf(wb[0] - sb.x, sb.x - wb[3]));
+                    const float gy = fmaxf(0.f, fmaxf(wb[1] - sb.y, sb.y - wb[4]));
+                    const float gz = fmaxf(0.f, fmaxf(wb[2] - sb.z, sb.z - wb[5]));
+                    fr = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= a.far_k2 * (sb.w * sb.w);
+                }
+                fmask = __ballot_sync(0xffffffffu, fr);
+            }
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                const int jend = min(cnt, k0 + 32);
+                if (jend - k0 < 32) {
+                    // the ragged end of the last tile: checked hi/lo form
+                    float2 D0[NP][3];
+                    for (int jj = k0; jj < jend; jj += 4)
+                        x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D0, eps2, f, jpart);
+                    ++near_visits;
+                } else if ((fmask >> (k0 >> 5)) & 1u) {
+                    const float4 C = sub_s[k0 >> 5];
+                    float2 D[NP][3];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p) {
+                        D[p][0] = __fadd2_rn(__fadd2_rn(bc2(C.x), pp[p].nxh), pp[p].nxl);
+                        D[p][1] = __fadd2_rn(__fadd2_rn(bc2(C.y), pp[p].nyh), pp[p].nyl);
+                        D[p][2] = __fadd2_rn(__fadd2_rn(bc2(C.z), pp[p].nzh), pp[p].nzl);
+                    }
+                    for (int jj = k0; jj < jend; jj += 4)
+                        x2_group<KIND, NP, true, true>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D, eps2, f, jpart);
+                    ++far_visits;
+                } else {
+                    float2 D0[NP][3];
+                    for (int jj = k0; jj < jend; jj += 4)
+                        x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D0, eps2, f, jpart);
+                    ++near_visits;
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    ff_add2(acc_s[(p * 3 + q) * kThreads + tid], f[p][q]);
+                    f[p][q] = make_float2(0.f, 0.f);
+                }
+        }
+        if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+        if (!diag && tid < cnt) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float sum = 0.f;
+#pragma unroll
+                for (int w = 0; w < kThreads / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
+                red_add(a.accum + (size_t)q * a.n + jt + tid, (double)sum);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+    }
+    if (aborted) {
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int t = t_stop; t < issued; ++t)
+                mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1), a.timeout_ns, nullptr);
+        }
+        __syncthreads();
+        return;
+    }
+    if (a.far_stats && lane == 0 && !diag) {
+        atomicAdd(a.far_stats, (unsigned long long)far_visits);
+        atomicAdd(a.far_stats + 1, (unsigned long long)near_visits);
+    }
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        if (ib + 32 * u >= a.n) continue;
+#pragma unroll
+        for (int q = 0; q < 3; ++q)
+        {
+            const float4 v = acc_s[((u >> 1) * 3 + q) * kThreads + tid];
+            const double sum = (u & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
+            red_add(a.accum + (size_t)q * a.n + ib + 32 * u, sum);
+        }
+    }
+}
+
+// MINB: resident CTAs per SM the register budget is sized for (2: 128 registers per
+// thread, 1: 255).
+template <int KIND, int I, int MINB>
+static cudaError_t launch_sym_x2(const SymArgs& a, cudaStream_t s) {
+    constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + 16) + (kTileJ / 32) * 16;
+    constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + I * 3 * kThreads * (int)sizeof(double);
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(sym_mixed_x2_kernel<KIND, I, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
+    const long long grid = (long long)nb * (1 + a.nchunk);
+    if (grid > 2147483647LL) return cudaErrorInvalidValue;
+    { sym_mixed_x2_kernel<KIND, I, MINB><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    return cudaGetLastError();
+}
+
 template <int KIND, int I, bool FAR>
 static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
     constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + (FAR ? 16 : 0)) +
@@ -1140,6 +1598,20 @@ cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, c
     a.chunk = chunk > 0 ? chunk : 1;
     const int above = ntj > I ? ntj - I : 0;       // most tiles above any block (block 0)
     a.nchunk = (above + a.chunk - 1) / a.chunk;
+    if (precision == FSI_MIXED && (ipt & 128)) {
+        // packed form; bit 16 selects the one-CTA-per-SM register budget
+        switch ((ipt & 16 ? 64 : 0) + I * 2 + kind) {
+            case 4 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 4, 2>(a, s);
+            case 6 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 6, 2>(a, s);
+            case 4 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 4, 2>(a, s);
+            case 6 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 6, 2>(a, s);
+            case 64 + 6 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 6, 1>(a, s);
+            case 64 + 6 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 6, 1>(a, s);
+            case 64 + 8 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 8, 1>(a, s);
+            case 64 + 8 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 8, 1>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (precision == FSI_MIXED && (ipt & 64)) {
         switch (I * 2 + kind) {
             case 4 * 2 + KIND_ACC: return launch_sym_v2<KIND_ACC, 4, true>(a, s);
@@ -1219,6 +1691,11 @@ int sym_variants(int precision, int kind, int* out) {
         // second form with the far-tile path
         if (kind == KIND_ACC) { out[n++] = 96 + 4; out[n++] = 96 + 5; }
         else { out[n++] = 96 + 3; out[n++] = 96 + 4; }
+        // packed FP32x2 form (far-tile path included)
+        out[n++] = 224 + 4;
+        out[n++] = 224 + 6;
+        out[n++] = 240 + 6;     // one CTA per SM (255 registers)
+        out[n++] = 240 + 8;
     } else {
         out[n++] = 1; out[n++] = 2; out[n++] = 3;
     }

@@ -19,8 +19,29 @@ __global__ void __launch_bounds__(256) fma_probe_kernel(int iters, T* sink) {
     sink[blockIdx.x * blockDim.x + threadIdx.x] = a0 + a1 + a2 + a3 + a4 + a5 + a6 + a7;
 }
 
+// Packed FP32 form: fma.rn.f32x2 (two FP32 FMAs per instruction, sm_100 and later).
+__global__ void __launch_bounds__(256) fma2_probe_kernel(int iters, float* sink) {
+    const float t = (float)threadIdx.x * 1e-3f;
+    float2 a[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) a[k] = make_float2(t + (float)k, t - (float)k);
+    const float2 b = make_float2(0.999999f, 0.999998f), c = make_float2(1e-7f, 2e-7f);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int k = 0; k < 8; ++k) a[k] = __ffma2_rn(a[k], b, c);
+    }
+    float r = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) r += a[k].x + a[k].y;
+    sink[blockIdx.x * blockDim.x + threadIdx.x] = r;
+}
+
 cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* sink, cudaStream_t s) {
-    if (fp64)
+    if (fp64 == 2)
+        { fma2_probe_kernel<<<blocks, 256, 0, s>>>(iters, reinterpret_cast<float*>(sink)); note_launch(); }
+    else if (fp64)
         { fma_probe_kernel<double><<<blocks, 256, 0, s>>>(iters, reinterpret_cast<double*>(sink)); note_launch(); }
     else
         { fma_probe_kernel<float><<<blocks, 256, 0, s>>>(iters, reinterpret_cast<float*>(sink)); note_launch(); }

@@ -305,10 +305,11 @@ def fsi_launch_count() -> int:
     return int(_lib.fsi_launch_count())
 
 
-def fsi_fma_probe(fp64: bool, blocks: int, iters: int, sink: torch.Tensor, stream=None) -> float:
-    """Enqueue the FMA throughput probe; returns its nominal flop count."""
+def fsi_fma_probe(fp64: int, blocks: int, iters: int, sink: torch.Tensor, stream=None) -> float:
+    """Enqueue the FMA throughput probe (0: FP32, 1: FP64, 2: packed FP32x2); returns its
+    nominal flop count."""
     f = C.c_double()
-    _check(_lib.fsi_fma_probe(int(bool(fp64)), int(blocks), int(iters), sink.data_ptr(),
+    _check(_lib.fsi_fma_probe(int(fp64), int(blocks), int(iters), sink.data_ptr(),
                               C.byref(f), _stream(stream)), "fsi_fma_probe")
     return f.value
 

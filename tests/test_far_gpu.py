@@ -1,4 +1,5 @@
-"""Far-tile path of the symmetric mixed kernel (variants 96 + I) and the Morton ordering
+"""Far-tile path of the symmetric mixed kernels (second form: variants 96 + I; packed FP32x2
+form: 224 + I, 240 + I) and the Morton ordering
 that feeds it, against the FP64 oracle and against the hi/lo (near) form.
 
 A far pair forms d = (C - x_i) + (x_j - C) from FP32 values relative to the centre C of
@@ -22,7 +23,7 @@ from paper_2210_02472_b300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FAR_VARIANTS = [(101, 100), (100, 99)]
+FAR_VARIANTS = [(101, 100), (100, 99), (228, 228), (230, 230), (246, 246), (248, 248)]
 
 
 @pytest.fixture(scope="module")
@@ -218,12 +219,12 @@ def test_autotune_times_far_variants_in_order(F, cluster):
 def test_size_class_tuning_tables(F):
     """Symmetric variants are kept per set-size class (< 32768, < 196608, larger):
     mixed defaults are the first form with 2 particles per thread for small sets and the
-    far-tile second form above; fsi_set_tuning fixes every class."""
+    packed FP32x2 form (far-tile path included) above; fsi_set_tuning fixes every class."""
     with F.Context("mixed") as ctx:
         assert F.fsi_get_tuning_for(ctx, 1000) == (2, 2)
-        assert F.fsi_get_tuning_for(ctx, 40000) == (100, 99)
-        assert F.fsi_get_tuning_for(ctx, 1 << 20) == (101, 100)
-        assert F.fsi_get_tuning(ctx) == (101, 100)
+        assert F.fsi_get_tuning_for(ctx, 40000) == (228, 228)
+        assert F.fsi_get_tuning_for(ctx, 1 << 20) == (230, 246)
+        assert F.fsi_get_tuning(ctx) == (230, 246)
         F.fsi_set_tuning(ctx, 36, 36)
         for n in (10, 40000, 1 << 20):
             assert F.fsi_get_tuning_for(ctx, n) == (36, 36)
