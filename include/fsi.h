@@ -86,6 +86,13 @@ typedef struct fsi_params {
                              particles in Morton order for the duration of the call (0 =
                              32768; -1 = never).  The order only changes which pairs take
                              the far-tile arithmetic and the summation order. */
+    double eta_grad;      /* gradient time-step parameter eta_nabla (Sect. 3.4, Eqs. dt-nabla1
+                             and dt-nabla2): eps = eta (|v_i| / |g'_i|)^{1/3} and
+                             eps = eta (|a_i| / |g'_i|)^{1/2}, g'_i = G_i / 24 from the
+                             set's own accelerations (one extra acc + grad pass per
+                             time-step assignment); 0 (default) = off */
+    double eta_va;        /* velocity-per-acceleration time-step parameter (Sect. 3.4, Eq.
+                             vel-acc-crit): eps = eta |v_i| / |a_i|; 0 (default) = off */
 } fsi_params;
 
 /* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,
@@ -190,7 +197,10 @@ int fsi_step_vjp(fsi_ctx *ctx, int N, const double *pos0, const double *vel0,
 
 /* Time steps of the set P against itself (Sect. 3.4): min of the free-fall
  * eta_ff min_j (r^3/(m_i+m_j))^{1/2}, fly-by eta_fb min_j r/|v_ij| and jerk
- * eta_jerk |a_i|/|j_i| criteria (eta's and eps2 from fsi_params).  step_out: n.
+ * eta_jerk |a_i|/|j_i| criteria (eta's and eps2 from fsi_params), and, when
+ * fsi_params.eta_grad / eta_va are > 0, the gradient criteria (Eqs. dt-nabla1, dt-nabla2)
+ * and the velocity-per-acceleration criterion (Eq. vel-acc-crit) from the set's own
+ * accelerations and force-gradient sums (one extra acc + grad pass).  step_out: n.
  * FSI_FP64: FP64 throughout.  FSI_MIXED: FP32 pair arithmetic (hi/lo separations,
  * minima of squared ratios), ~1e-6 relative. */
 int fsi_timesteps(fsi_ctx *ctx, int N, const double *pos, const double *vel,

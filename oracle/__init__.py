@@ -50,7 +50,13 @@ class _HHSParams(C.Structure):
     _fields_ = [("eta_ff", C.c_double), ("eta_fb", C.c_double), ("eta_jerk", C.c_double),
                 ("eps2", C.c_double), ("c", C.c_double),
                 ("is_bh", C.POINTER(C.c_ubyte)), ("max_level", C.c_int),
-                ("fixed_steps", C.POINTER(C.c_double))]
+                ("fixed_steps", C.POINTER(C.c_double)),
+                ("eta_grad", C.c_double), ("eta_va", C.c_double)]
+
+
+class _StepParams(C.Structure):
+    _fields_ = [("eta_ff", C.c_double), ("eta_fb", C.c_double), ("eta_jerk", C.c_double),
+                ("eta_grad", C.c_double), ("eta_va", C.c_double)]
 
 
 class _ForceParams(C.Structure):
@@ -74,6 +80,8 @@ def lib():
                                   C.POINTER(_ForceParams)]
         L.or_timesteps.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int, C.c_double, C.c_double,
                                    C.c_double, C.c_double, dp]
+        L.or_timesteps_all.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int,
+                                       C.POINTER(_StepParams), C.c_double, dp]
         L.or_hhs_interval.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.POINTER(_HHSParams),
                                       C.POINTER(C.c_longlong)]
         L.or_vjp_acc.argtypes = [C.c_int, dp, dp, ip, C.c_int, C.c_double, dp, C.c_double,
@@ -191,18 +199,28 @@ def fsi_step(pos, vel, mass, h, P=None, eps2=0.0, c=0.0, is_bh=None, steps=1):
     return pos, vel
 
 
-def timesteps(pos, vel, mass, P=None, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eps2=0.0):
+def timesteps(pos, vel, mass, P=None, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eps2=0.0,
+              eta_grad=0.0, eta_va=0.0):
+    """Time steps of the set P against itself (Sect. 3.4): free fall, fly-by and jerk, plus
+    the gradient (eta_grad > 0) and velocity-per-acceleration (eta_va > 0) criteria."""
     pos, vel, mass, P = _f64(pos), _f64(vel), _f64(mass), _idx(P)
     N = mass.shape[0]
     n = _n(P, N)
     out = np.zeros(n)
+    if eta_grad > 0 or eta_va > 0:
+        sp = _StepParams(float(eta_ff), float(eta_fb), float(eta_jerk), float(eta_grad),
+                         float(eta_va))
+        _check(lib().or_timesteps_all(N, _d(pos), _d(vel), _d(mass), _i(P), n, C.byref(sp),
+                                      float(eps2), _d(out)), "timesteps_all")
+        return out
     _check(lib().or_timesteps(N, _d(pos), _d(vel), _d(mass), _i(P), n, float(eta_ff),
                               float(eta_fb), float(eta_jerk), float(eps2), _d(out)), "timesteps")
     return out
 
 
 def hhs_interval(pos, vel, mass, tau, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eps2=0.0,
-                 c=0.0, is_bh=None, max_level=40, allow_maxlevel=False, fixed_steps=None):
+                 c=0.0, is_bh=None, max_level=40, allow_maxlevel=False, fixed_steps=None,
+                 eta_grad=0.0, eta_va=0.0):
     """Return (pos, vel, level_counts, status) after one HHS interval of length tau.
 
     fixed_steps (N,) forces every particle's time step at every level (a frozen
@@ -211,7 +229,7 @@ def hhs_interval(pos, vel, mass, tau, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eps2
     pos, vel, mass = _f64(pos).copy(), _f64(vel).copy(), _f64(mass)
     N = mass.shape[0]
     p = _HHSParams(float(eta_ff), float(eta_fb), float(eta_jerk), float(eps2), float(c),
-                   None, int(max_level), None)
+                   None, int(max_level), None, float(eta_grad), float(eta_va))
     fs = None
     if fixed_steps is not None:
         fs = _f64(fixed_steps)

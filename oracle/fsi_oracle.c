@@ -374,6 +374,11 @@ int or_fsi_step(int N, double *pos, double *vel, const double *mass,
     return err;
 }
 
+/* Time-step parameters (Sect. 3.4): eta_grad and eta_va switch their criteria off at 0. */
+typedef struct {
+    double eta_ff, eta_fb, eta_jerk, eta_grad, eta_va;
+} or_step_params;
+
 /* ------------------------------------------------------------------------------- *
  * Time steps of the listed set against itself (Sect. 3.4):
  *   free fall  eps_ff = eta_ff min_{j != i} ( |r_ij|^3 / (G (m_i + m_j)) )^{1/2},
@@ -384,9 +389,10 @@ int or_fsi_step(int N, double *pos, double *vel, const double *mass,
  * fly-by bound and a zero jerk gives no jerk bound (both +inf).  The free-fall and
  * fly-by distances are unsoftened; a_i and j_i use the softened kernel of the force.
  * ------------------------------------------------------------------------------- */
-int or_timesteps(int N, const double *pos, const double *vel, const double *mass,
-                 const int *P, int n, double eta_ff, double eta_fb, double eta_jerk,
-                 double eps2, double *step)
+static int steps_ff_fb_jerk(int N, const double *pos, const double *vel,
+                            const double *mass, const int *P, int n, double eta_ff,
+                            double eta_fb, double eta_jerk, double eps2, double *step,
+                            double *acc)
 {
     const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
     const double *VX = vel, *VY = vel + N, *VZ = vel + 2 * (size_t)N;
@@ -435,7 +441,88 @@ int or_timesteps(int N, const double *pos, const double *vel, const double *mass
             if (ej < e) e = ej;
         }
         step[k] = e;
+        if (acc) {
+            acc[k] = ax;
+            acc[(size_t)n + k] = ay;
+            acc[2 * (size_t)n + k] = az;
+        }
     }
+    return err;
+}
+
+int or_timesteps(int N, const double *pos, const double *vel, const double *mass,
+                 const int *P, int n, double eta_ff, double eta_fb, double eta_jerk,
+                 double eps2, double *step)
+{
+    return steps_ff_fb_jerk(N, pos, vel, mass, P, n, eta_ff, eta_fb, eta_jerk, eps2, step,
+                            NULL);
+}
+
+/* ------------------------------------------------------------------------------- *
+ * Every time-step criterion of Sect. 3.4 for the listed set against itself: the free-fall,
+ * fly-by and jerk steps above, then, when switched on (parameter > 0),
+ *   velocity per acceleration (Eq. vel-acc-crit)   eps = eta_va |v_i| / |a_i|,
+ *   gradient, first form      (Eq. dt-nabla1)      eps = eta_grad (|v_i| / |g'_i|)^{1/3},
+ *   gradient, second form     (Eq. dt-nabla2)      eps = eta_grad (|a_i| / |g'_i|)^{1/2},
+ * where a_i is the acceleration from the set, g'_i the gradient acceleration of the FSI
+ * gradient kick written as a~_i = a_i + eps^2 g'_i, i.e. g'_i = G_i / 24 with G_i the
+ * force-gradient sum of Eq. new-grad-acc evaluated with the set's own accelerations, and
+ * v_i the particle's velocity in the simulation frame.  |a_i| = 0 gives no
+ * velocity-per-acceleration bound and |g'_i| = 0 no gradient bound.  The step is the
+ * minimum over the criteria in use.
+ * ------------------------------------------------------------------------------- */
+int or_timesteps_all(int N, const double *pos, const double *vel, const double *mass,
+                     const int *P, int n, const or_step_params *sp, double eps2, double *step)
+{
+    int extra = sp->eta_grad > 0.0 || sp->eta_va > 0.0;
+    double *a = NULL, *field = NULL, *G = NULL;
+    if (extra) {
+        a = (double *)malloc(3 * (size_t)n * sizeof(double));
+        field = (double *)calloc(3 * (size_t)N, sizeof(double));
+        G = (double *)malloc(3 * (size_t)n * sizeof(double));
+        if (!a || !field || !G) { free(a); free(field); free(G); return OR_ERR_NOMEM; }
+    }
+    int err = steps_ff_fb_jerk(N, pos, vel, mass, P, n, sp->eta_ff, sp->eta_fb, sp->eta_jerk,
+                               eps2, step, a);
+    if (err == OR_OK && extra) {
+        /* the set's accelerations as a global-id field, then G_i from those (Sect. 2.1) */
+        for (int k = 0; k < n; ++k) {
+            int i = idx_at(P, k);
+            for (int q = 0; q < 3; ++q) field[(size_t)q * N + i] = a[(size_t)q * n + k];
+        }
+        err = or_grad(N, pos, mass, field, P, n, P, n, eps2, G);
+    }
+    if (err == OR_OK && extra) {
+        for (int k = 0; k < n; ++k) {
+            int i = idx_at(P, k);
+            double an = 0.0, gn = 0.0, vn = 0.0;
+            for (int q = 0; q < 3; ++q) {
+                double aq = a[(size_t)q * n + k], gq = G[(size_t)q * n + k] / 24.0;
+                double vq = vel[(size_t)q * N + i];
+                an += aq * aq;
+                gn += gq * gq;
+                vn += vq * vq;
+            }
+            an = sqrt(an);
+            gn = sqrt(gn);
+            vn = sqrt(vn);
+            double e = step[k];
+            if (sp->eta_va > 0.0 && an > 0.0) {
+                double t = sp->eta_va * vn / an;
+                if (t < e) e = t;
+            }
+            if (sp->eta_grad > 0.0 && gn > 0.0) {
+                double t1 = sp->eta_grad * cbrt(vn / gn);
+                double t2 = sp->eta_grad * sqrt(an / gn);
+                if (t1 < e) e = t1;
+                if (t2 < e) e = t2;
+            }
+            step[k] = e;
+        }
+    }
+    free(a);
+    free(field);
+    free(G);
     return err;
 }
 
@@ -459,7 +546,14 @@ typedef struct {
     const unsigned char *is_bh;
     int max_level;
     const double *fixed_steps;   /* if non-NULL: eps_i = fixed_steps[i] at every level */
+    double eta_grad, eta_va;     /* gradient and velocity/acceleration criteria (0 = off) */
 } or_hhs_params;
+
+static or_step_params hhs_step_params(const or_hhs_params *p)
+{
+    or_step_params sp = {p->eta_ff, p->eta_fb, p->eta_jerk, p->eta_grad, p->eta_va};
+    return sp;
+}
 
 typedef struct {
     int N;
@@ -517,9 +611,10 @@ static int hhs_level(hhs_ctx *c, const int *P, int n, double tau, int level)
     int err = OR_OK;
     if (p->fixed_steps)
         for (int k = 0; k < n; ++k) st[k] = p->fixed_steps[P[k]];
-    else
-        err = or_timesteps(N, c->pos, c->vel, c->mass, P, n, p->eta_ff, p->eta_fb,
-                           p->eta_jerk, p->eps2, st);
+    else {
+        or_step_params sp = hhs_step_params(p);
+        err = or_timesteps_all(N, c->pos, c->vel, c->mass, P, n, &sp, p->eps2, st);
+    }
     int nS = 0, nF = 0;
     if (err == OR_OK) {
         for (int k = 0; k < n; ++k) {
@@ -587,8 +682,8 @@ int or_hhs_interval(int N, double *pos, double *vel, const double *mass, double 
 int or_level0_steps(int N, const double *pos, const double *vel, const double *mass,
                     const or_hhs_params *p, double *step)
 {
-    return or_timesteps(N, pos, vel, mass, NULL, N, p->eta_ff, p->eta_fb, p->eta_jerk,
-                        p->eps2, step);
+    or_step_params sp = hhs_step_params(p);
+    return or_timesteps_all(N, pos, vel, mass, NULL, N, &sp, p->eps2, step);
 }
 
 /* =============================================================================== *

@@ -587,6 +587,45 @@ cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const do
     return cudaGetLastError();
 }
 
+// Gradient and velocity-per-acceleration time steps (Sect. 3.4, Eqs. dt-nabla1,
+// dt-nabla2, vel-acc-crit) of a compact set from its velocities v, accelerations a and
+// force-gradient sums G (3 x n each, G without the eps^2/24 factor):
+//   g' = G / 24 (a~ = a + eps^2 g'),  eps = min(eta_va |v|/|a|, eta_grad (|v|/|g'|)^{1/3},
+//   eta_grad (|a|/|g'|)^{1/2}), each only when its parameter is > 0 and its denominator
+//   is non-zero; step[k] takes the min with it.
+__global__ void grad_steps_kernel(int n, const double* __restrict__ v, const double* __restrict__ a,
+                                  const double* __restrict__ G, double eta_grad, double eta_va,
+                                  double* __restrict__ step) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= n) return;
+    double vn = 0.0, an = 0.0, gn = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double vq = v[(size_t)q * n + k], aq = a[(size_t)q * n + k];
+        const double gq = G[(size_t)q * n + k] * (1.0 / 24.0);
+        vn = fma(vq, vq, vn);
+        an = fma(aq, aq, an);
+        gn = fma(gq, gq, gn);
+    }
+    vn = sqrt(vn);
+    an = sqrt(an);
+    gn = sqrt(gn);
+    double e = step[k];
+    if (eta_va > 0.0 && an > 0.0) e = fmin(e, eta_va * vn / an);
+    if (eta_grad > 0.0 && gn > 0.0) {
+        e = fmin(e, eta_grad * cbrt(vn / gn));
+        e = fmin(e, eta_grad * sqrt(an / gn));
+    }
+    step[k] = e;
+}
+
+cudaError_t launch_grad_steps(int n, const double* vc, const double* a, const double* G,
+                              double eta_grad, double eta_va, double* step, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { grad_steps_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, a, G, eta_grad, eta_va, step); note_launch(); }
+    return cudaGetLastError();
+}
+
 // Mixed-precision time steps: the same criteria with FP32 pair arithmetic on the mixed
 // position records (hi/lo separations, FP32-accurate relative to the separation) and FP32
 // velocity records (vx, vy, vz, m); two receivers per thread.

@@ -532,6 +532,30 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     else
         CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
                             c->err_d, s));
+    if (c->p.eta_grad > 0.0 || c->p.eta_va > 0.0) {
+        // gradient and velocity-per-acceleration criteria (Sect. 3.4): a and G of the set
+        // from itself, G with the set's own accelerations, then the min into step
+        const int prec = c->p.precision;
+        CK(ensure(c->rec[0], pad_tile(n) * 32));
+        CK(ensure(c->accrec[0], pad_tile(n) * 32));
+        CK(ensure(c->tA, 3 * (size_t)n * 8));
+        CK(ensure(c->tB, 3 * (size_t)n * 8));
+        CU(launch_pack(prec, N, pos, mass, Pids, n, c->rec[0].p, nullptr, s));
+        PairArgs a{};
+        a.irec = a.jrec = c->rec[0].p;
+        a.n_i = a.n_j = n;
+        a.check = CHECK_DIAG;
+        a.eps2 = c->p.eps2;
+        a.epi.out = P<double>(c->tA);
+        a.epi.accrec = c->accrec[0].p;
+        CK(run_pair(c, KIND_ACC, a, s));
+        a.iacc = a.jacc = c->accrec[0].p;
+        a.epi = Epi{};
+        a.epi.out = P<double>(c->tB);
+        CK(run_pair(c, KIND_GRAD, a, s));
+        CU(launch_grad_steps(n, vc, P<double>(c->tA), P<double>(c->tB), c->p.eta_grad, c->p.eta_va,
+                             step, s));
+    }
     return FSI_OK;
 }
 
@@ -576,6 +600,7 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
             sa.step0 = P<double>(c->step0); sa.N = N; sa.tau = 0.5 * tau; sa.level = level + 1;
             sa.max_level = c->p.max_level; sa.eps2 = c->p.eps2; sa.eta_ff = c->p.eta_ff;
             sa.eta_fb = c->p.eta_fb; sa.eta_jerk = c->p.eta_jerk;
+            sa.eta_grad = c->p.eta_grad; sa.eta_va = c->p.eta_va;
             unsigned long long* st = P<unsigned long long>(c->dstats);
             sa.level_counts = st; sa.work = st + 64;
             sa.maxlevel_hit = reinterpret_cast<int*>(st + 66);
@@ -636,6 +661,8 @@ void fsi_default_params(fsi_params* p) {
     p->symmetric = 1;
     p->hhs_small_max = 0;
     p->order_min = 0;
+    p->eta_grad = 0.0;
+    p->eta_va = 0.0;
 }
 
 const char* fsi_last_error(void) { return g_err.c_str(); }
@@ -647,6 +674,8 @@ int fsi_create(fsi_ctx** out, const fsi_params* p) {
     if (p) q = *p;
     else fsi_default_params(&q);
     if (!valid_prec(q.precision)) return fail(FSI_ERR_ARG, "unknown precision %d", q.precision);
+    if (!(q.eta_grad >= 0.0) || !(q.eta_va >= 0.0))
+        return fail(FSI_ERR_ARG, "eta_grad and eta_va must be >= 0 (0 = off)");
     fsi_ctx* c = new fsi_ctx();
     c->p = q;
     if (cudaGetDevice(&c->device) != cudaSuccess ||
@@ -688,6 +717,8 @@ int fsi_destroy(fsi_ctx* c) {
 int fsi_set_params(fsi_ctx* c, const fsi_params* p) {
     if (!c || !p) return fail(FSI_ERR_ARG, "NULL argument");
     if (!valid_prec(p->precision)) return fail(FSI_ERR_ARG, "unknown precision %d", p->precision);
+    if (!(p->eta_grad >= 0.0) || !(p->eta_va >= 0.0))
+        return fail(FSI_ERR_ARG, "eta_grad and eta_va must be >= 0 (0 = off)");
     c->p = *p;
     return FSI_OK;
 }

@@ -192,6 +192,7 @@ struct SmallArgs {
     int level;
     int max_level;
     double eps2, eta_ff, eta_fb, eta_jerk;
+    double eta_grad, eta_va;        // gradient / velocity-per-acceleration criteria (0 = off)
     unsigned long long* level_counts;   // per level (device)
     unsigned long long* work;           // [0] acc pairs, [1] grad pairs
     int* maxlevel_hit;
@@ -289,6 +290,10 @@ cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const do
                              double eta_ff, double eta_fb, double eta_jerk, double eps2,
                              double* step, int* err, cudaStream_t s);
 // rec_ws, vrec_ws: workspace of >= 32 n and 16 n bytes (mixed records, FP32 velocities)
+// step[k] = min(step[k], gradient and velocity-per-acceleration steps) from the set's
+// velocities vc, accelerations a and force-gradient sums G (all 3 x n).
+cudaError_t launch_grad_steps(int n, const double* vc, const double* a, const double* G,
+                              double eta_grad, double eta_va, double* step, cudaStream_t s);
 cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
                                    double eta_ff, double eta_fb, double eta_jerk, double eps2,
                                    void* rec_ws, void* vrec_ws, double* step, int* err,

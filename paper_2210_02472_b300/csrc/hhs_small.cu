@@ -152,6 +152,34 @@ __device__ void small_timesteps(SmallSmem<P>& S, const unsigned short* L, int n,
     S.st[i] = fmin(e, S.s0[i]);
 }
 
+// Gradient and velocity-per-acceleration steps (Sect. 3.4) of list L from its own a and
+// G (in S.a, S.g): st = min(st, eta_va |v|/|a|, eta_grad (|v|/|g'|)^{1/3},
+// eta_grad (|a|/|g'|)^{1/2}), g' = G / 24.
+template <int P>
+__device__ void small_grad_steps(SmallSmem<P>& S, const unsigned short* L, int n, const SmallArgs& a) {
+    const int t = threadIdx.x;
+    if (t >= n) return;
+    const int k = L[t];
+    double vn = 0.0, an = 0.0, gn = 0.0;
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        const double gq = S.g[q][k] * (1.0 / 24.0);
+        vn = fma(S.v[q][k], S.v[q][k], vn);
+        an = fma(S.a[q][k], S.a[q][k], an);
+        gn = fma(gq, gq, gn);
+    }
+    vn = sqrt(vn);
+    an = sqrt(an);
+    gn = sqrt(gn);
+    double e = S.st[k];
+    if (a.eta_va > 0.0 && an > 0.0) e = fmin(e, a.eta_va * vn / an);
+    if (a.eta_grad > 0.0 && gn > 0.0) {
+        e = fmin(e, a.eta_grad * cbrt(vn / gn));
+        e = fmin(e, a.eta_grad * sqrt(an / gn));
+    }
+    S.st[k] = e;
+}
+
 template <int P>
 __device__ void small_kick(SmallSmem<P>& S, const unsigned short* L, int n, double w, bool with_grad,
                            double cg) {
@@ -333,6 +361,17 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
             const unsigned short* L = S.lists + f.offP;
             small_timesteps<P>(S, L, f.nP, a);
             __syncthreads();
+            if (a.eta_grad > 0.0 || a.eta_va > 0.0) {
+                // a and G of the level set from itself, then the gradient criteria
+                small_pass<P, 0>(S, L, f.nP, L, f.nP, a.eps2, S.a, a.work);
+                __syncthreads();
+                if (t < f.nP) write_arec<P>(S, L[t]);
+                __syncthreads();
+                small_pass<P, 1>(S, L, f.nP, L, f.nP, a.eps2, S.g, a.work);
+                __syncthreads();
+                small_grad_steps<P>(S, L, f.nP, a);
+                __syncthreads();
+            }
             // S goes to [lt, lt + nS), F first to [lt + nP, ...) and is then moved down to
             // [lt + nS, lt + nP): the frame's lists take exactly nP entries.
             const int lt = S.list_top;

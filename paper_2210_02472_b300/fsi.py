@@ -48,7 +48,8 @@ class fsi_params(C.Structure):
     _fields_ = [("precision", C.c_int), ("eps2", C.c_double), ("eta_ff", C.c_double),
                 ("eta_fb", C.c_double), ("eta_jerk", C.c_double), ("max_level", C.c_int),
                 ("c", C.c_double), ("split", C.c_int), ("timeout_ns", C.c_longlong),
-                ("symmetric", C.c_int), ("hhs_small_max", C.c_int), ("order_min", C.c_int)]
+                ("symmetric", C.c_int), ("hhs_small_max", C.c_int), ("order_min", C.c_int),
+                ("eta_grad", C.c_double), ("eta_va", C.c_double)]
 
 
 _vp, _ip, _dp = C.c_void_p, C.c_int, C.c_double
@@ -139,7 +140,8 @@ class Context:
     def __init__(self, precision: str = "fp64", eps2: float = 0.0, eta_ff: float = 0.2,
                  eta_fb: float = 0.2, eta_jerk: float = 0.1, max_level: int = 40,
                  c: float = 0.0, split: int = 0, timeout_ns: int = 0, symmetric: bool = True,
-                 hhs_small_max: int = 0, order_min: int = 0):
+                 hhs_small_max: int = 0, order_min: int = 0, eta_grad: float = 0.0,
+                 eta_va: float = 0.0):
         p = fsi_params()
         _lib.fsi_default_params(C.byref(p))
         p.precision = {"fp64": FSI_FP64, "mixed": FSI_MIXED}[precision]
@@ -148,6 +150,7 @@ class Context:
         p.symmetric = int(bool(symmetric))
         p.hhs_small_max = int(hhs_small_max)
         p.order_min = int(order_min)
+        p.eta_grad, p.eta_va = float(eta_grad), float(eta_va)
         self.params = p
         self.precision = precision
         h = _vp()

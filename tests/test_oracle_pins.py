@@ -274,6 +274,52 @@ def test_timesteps_circular_binary_all_criteria_agree():
         assert np.allclose(s, tff, rtol=1e-13)
 
 
+def test_gradient_and_velocity_acceleration_steps_circular_binary():
+    """Sect. 3.4 criteria on a circular binary (COM frame, separation a, M = m1 + m2),
+    from the two-body closed forms |a_1| = m2/a^2, |G_1| = 2 m2 M / a^5 (g' = G/24),
+    |v_1| = (m2/M) (M/a)^{1/2} (and 1 <-> 2):
+      velocity per acceleration  eta a^{3/2} M^{-1/2},
+      gradient, first form       eta 12^{1/3} a^{3/2} M^{-1/2}  (the smaller of the two),
+      gradient, second form      eta (12 a^3 / M)^{1/2}  (isolated by a large common
+                                 velocity along z, which raises the other two)."""
+    m1, m2, a = 0.7, 0.3, 0.9
+    M = m1 + m2
+    pos, vel = kepler.binary(m1, m2, a, 0.0)
+    m = np.array([m1, m2])
+    off = dict(eta_ff=1e30, eta_fb=1e30, eta_jerk=1e30)
+    s_va = oracle.timesteps(pos, vel, m, eta_va=1.0, **off)
+    assert np.allclose(s_va, a ** 1.5 / math.sqrt(M), rtol=1e-13)
+    s_g = oracle.timesteps(pos, vel, m, eta_grad=1.0, **off)
+    assert np.allclose(s_g, 12 ** (1 / 3) * a ** 1.5 / math.sqrt(M), rtol=1e-13)
+    vz = vel.copy()
+    vz[2] += 50.0
+    s_g2 = oracle.timesteps(pos, vz, m, eta_grad=1.0, **off)
+    assert np.allclose(s_g2, math.sqrt(12 * a ** 3 / M), rtol=1e-13)
+    # the first gradient form with that velocity: eta (|v_i| 12 a^5 / (m_j M))^{1/3}
+    vn = np.linalg.norm(vz, axis=0)
+    first = (vn * 12 * a ** 5 / (m[::-1] * M)) ** (1 / 3)
+    assert np.all(first > s_g2)
+    s_min = oracle.timesteps(pos, vz, m, eta_grad=1.0, eta_va=1.0, **off)
+    assert np.allclose(s_min, np.minimum(s_g2, vn * a ** 2 / m[::-1]), rtol=1e-13)
+
+
+def test_gradient_steps_only_shrink_steps_and_deepen_the_hierarchy():
+    """Adding criteria can only lower a particle's step (the step is a minimum), so an
+    HHS interval with them keeps no more particles on the top level; the interval still
+    conserves momentum (Sect. 2.2)."""
+    c = inputs.plummer(200, 27, imf="kroupa")
+    base = oracle.timesteps(c.pos, c.vel, c.mass)
+    more = oracle.timesteps(c.pos, c.vel, c.mass, eta_grad=0.1, eta_va=0.1)
+    assert np.all(more <= base) and np.any(more < base)
+    tau = 1.0 / 32
+    _, _, n0, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    p1, v1, n1, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, eta_grad=0.1, eta_va=0.1)
+    assert n1[0] <= n0[0]
+    P0 = (c.mass * c.vel).sum(axis=1)
+    P1 = (c.mass * v1).sum(axis=1)
+    assert np.abs(P1 - P0).max() <= 1e-14 * np.abs(c.mass * c.vel).sum()
+
+
 def test_timesteps_jerk_is_time_derivative_of_acc():
     """The jerk criterion's j_i equals d/dt a_i(x + t v): with eta_ff = eta_fb = inf the
     step is eta |a| / |j| with j from a central difference of the oracle's acc."""

@@ -374,6 +374,51 @@ def test_timesteps_mixed(F):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+def test_timesteps_gradient_criteria(F, prec):
+    """Gradient (Eqs. dt-nabla1/2) and velocity-per-acceleration (Eq. vel-acc-crit)
+    criteria on top of free fall, fly-by and jerk, for the whole set and a subset."""
+    c = inputs.plummer(2000, 24, imf="kroupa")
+    P = inputs.random_subset(2000, 500, 8)
+    kw = dict(eta_grad=0.1, eta_va=0.05)
+    ref = oracle.timesteps(c.pos, c.vel, c.mass, **kw)
+    refp = oracle.timesteps(c.pos, c.vel, c.mass, P, **kw)
+    base = oracle.timesteps(c.pos, c.vel, c.mass)
+    assert np.mean(ref < base) > 0.1        # the new criteria set many of the steps
+    with F.Context(prec, **kw) as ctx:
+        s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+        sp = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    assert np.abs(s / ref - 1).max() < tol
+    assert np.abs(sp / refp - 1).max() < tol
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("small", [0, -1])
+def test_hhs_interval_gradient_criteria(F, prec, small):
+    """One HHS interval with the gradient and velocity-per-acceleration criteria on, the
+    levels walked from the host (small = -1) or recursed inside one CTA (0)."""
+    c = inputs.plummer(600, 22, imf="kroupa")
+    tau = 1.0 / 16
+    kw = dict(eta_grad=0.1, eta_va=0.1)
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, **kw)
+    _, _, counts0, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    assert not np.array_equal(counts, counts0)      # the criteria change the hierarchy
+    with F.Context(prec, hhs_small_max=small, **kw) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("small", [0, -1, 64])
 def test_hhs_interval(F, prec, small):
     """One HHS interval against the oracle: the levels walked from the host (small = -1),
