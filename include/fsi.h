@@ -220,6 +220,22 @@ int fsi_energy(fsi_ctx *ctx, int N, const double *pos, const double *vel,
 int fsi_hhs_interval(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
                      const unsigned char *is_bh, double tau, void *stream);
 
+/* One HHS interval with adaptive energy-error restarts (Sect. 3.12): the state is saved
+ * (device copies in the context workspace) and E = T + W (fsi_energy) taken; after the
+ * interval, if |Delta E / E| > eta_restart, the saved state is restored and the interval
+ * re-run with eta_ff, eta_fb, eta_jerk, eta_grad and eta_va all lowered by 50 % per
+ * consecutive restart.  An attempt is accepted when its error is within eta_restart, when
+ * it is larger than the previous attempt's (the current result is kept), or after
+ * max_restarts restarts; the context's parameters are unchanged afterwards.  *restarts
+ * (host, may be NULL) receives the number of restarts, *rel_err (host, may be NULL) the
+ * accepted attempt's |Delta E / E|; fsi_level_stats reports the accepted attempt's
+ * levels.  Synchronous.  Returns like fsi_hhs_interval; FSI_ERR_ARG for eta_restart < 0
+ * or max_restarts < 0. */
+int fsi_hhs_interval_restart(fsi_ctx *ctx, int N, double *pos, double *vel,
+                             const double *mass, const unsigned char *is_bh, double tau,
+                             double eta_restart, int max_restarts, int *restarts,
+                             double *rel_err, void *stream);
+
 /* ---- batched ensembles ---------------------------------------------------------- */
 typedef struct fsi_batch fsi_batch;
 

@@ -84,6 +84,9 @@ def lib():
                                        C.POINTER(_StepParams), C.c_double, dp]
         L.or_hhs_interval.argtypes = [C.c_int, dp, dp, dp, C.c_double, C.POINTER(_HHSParams),
                                       C.POINTER(C.c_longlong)]
+        L.or_hhs_interval_restart.argtypes = [C.c_int, dp, dp, dp, C.c_double,
+                                              C.POINTER(_HHSParams), C.c_double, C.c_int,
+                                              C.POINTER(C.c_longlong), ip, dp]
         L.or_vjp_acc.argtypes = [C.c_int, dp, dp, ip, C.c_int, C.c_double, dp, C.c_double,
                                  C.c_double, dp, dp]
         L.or_vjp_grad.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int, C.c_double, dp, C.c_double,
@@ -244,6 +247,27 @@ def hhs_interval(pos, vel, mass, tau, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eps2
     if code != OK and not (allow_maxlevel and code == ERR_MAXLEVEL):
         raise OracleError(code, "hhs_interval")
     return pos, vel, counts, code
+
+
+def hhs_interval_restart(pos, vel, mass, tau, eta_restart, max_restarts=8, eta_ff=0.2,
+                         eta_fb=0.2, eta_jerk=0.1, eps2=0.0, eta_grad=0.0, eta_va=0.0,
+                         max_level=40):
+    """One HHS interval with adaptive energy-error restarts (Sect. 3.12).
+    Returns (pos, vel, level_counts, restarts, rel_err, status)."""
+    pos, vel, mass = _f64(pos).copy(), _f64(vel).copy(), _f64(mass)
+    N = mass.shape[0]
+    p = _HHSParams(float(eta_ff), float(eta_fb), float(eta_jerk), float(eps2), 0.0,
+                   None, int(max_level), None, float(eta_grad), float(eta_va))
+    counts = np.zeros(max_level + 1, dtype=np.int64)
+    k = C.c_int()
+    e = C.c_double()
+    code = lib().or_hhs_interval_restart(N, _d(pos), _d(vel), _d(mass), float(tau), C.byref(p),
+                                         float(eta_restart), int(max_restarts),
+                                         counts.ctypes.data_as(C.POINTER(C.c_longlong)),
+                                         C.byref(k), C.byref(e))
+    if code not in (OK, ERR_MAXLEVEL):
+        raise OracleError(code, "hhs_interval_restart")
+    return pos, vel, counts, k.value, e.value, code
 
 
 def vjp_acc(pos, mass, u, P=None, eps2=0.0):

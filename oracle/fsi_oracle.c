@@ -678,6 +678,58 @@ int or_hhs_interval(int N, double *pos, double *vel, const double *mass, double 
     return err;
 }
 
+/* ------------------------------------------------------------------------------- *
+ * Adaptive energy-error restarts (Sect. 3.12) around one HHS interval: the state is
+ * saved before the interval; if the relative error of the energy E = T + W against its
+ * value at the start exceeds eta_restart, the saved state is restored and the interval
+ * re-run with every time-step accuracy parameter lowered by 50 % per consecutive restart
+ * (eta * 2^-k on attempt k).  An attempt is accepted when its error is within the
+ * tolerance, when its error is larger than the previous attempt's ("the energy error
+ * starts to increase again": the current result is kept), or after max_restarts
+ * restarts.  The caller's parameters stand for the next interval.  *restarts receives the
+ * number of restarts, *rel_err the accepted attempt's |Delta E / E|, level_counts its
+ * level histogram.  Returns the accepted attempt's status (OR_ERR_MAXLEVEL included).
+ * ------------------------------------------------------------------------------- */
+int or_hhs_interval_restart(int N, double *pos, double *vel, const double *mass, double tau,
+                            const or_hhs_params *p, double eta_restart, int max_restarts,
+                            long long *level_counts, int *restarts, double *rel_err)
+{
+    size_t bytes = 3 * (size_t)N * sizeof(double);
+    double *x0 = (double *)malloc(bytes), *v0 = (double *)malloc(bytes);
+    if (!x0 || !v0) { free(x0); free(v0); return OR_ERR_NOMEM; }
+    memcpy(x0, pos, bytes);
+    memcpy(v0, vel, bytes);
+    double t0, w0;
+    int err = or_energy(N, pos, vel, mass, NULL, N, p->eps2, &t0, &w0);
+    double E0 = t0 + w0, prev = INFINITY, e = INFINITY;
+    int k = 0;
+    for (; err == OR_OK; ++k) {
+        or_hhs_params q = *p;
+        double f = ldexp(1.0, -k);
+        q.eta_ff *= f; q.eta_fb *= f; q.eta_jerk *= f; q.eta_grad *= f; q.eta_va *= f;
+        if (k > 0) {
+            memcpy(pos, x0, bytes);
+            memcpy(vel, v0, bytes);
+        }
+        int st = or_hhs_interval(N, pos, vel, mass, tau, &q, level_counts);
+        if (st != OR_OK && st != OR_ERR_MAXLEVEL) { err = st; break; }
+        double t1, w1;
+        err = or_energy(N, pos, vel, mass, NULL, N, p->eps2, &t1, &w1);
+        if (err != OR_OK) break;
+        e = fabs((t1 + w1 - E0) / E0);
+        if (e <= eta_restart || (k > 0 && e > prev) || k >= max_restarts) {
+            err = st;
+            break;
+        }
+        prev = e;
+    }
+    *restarts = k;
+    *rel_err = e;
+    free(x0);
+    free(v0);
+    return err;
+}
+
 /* Time steps of the level-0 set as the interval would assign them (for tests). */
 int or_level0_steps(int N, const double *pos, const double *vel, const double *mass,
                     const or_hhs_params *p, double *step)

@@ -5,6 +5,7 @@
 // step runs in the kernels of pair_kernels.cu and aux_kernels.cu.
 #include <algorithm>
 #include <climits>
+#include <cmath>
 #include <atomic>
 #include <cstdarg>
 #include <cstdio>
@@ -76,7 +77,7 @@ struct fsi_ctx {
     int* err_h = nullptr;          // pinned
     int* counts_h = nullptr;       // pinned, 3 ints (HHS partition)
     Buf rec[2], accrec[2], xc, vc, ac, ad, gA, gB, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
-        nbh, apn, pnpart, epart, iota, steps, step0, counts, accum;
+        nbh, apn, pnpart, epart, iota, steps, step0, counts, accum, eout, snapx, snapv;
     std::vector<Buf> lvS, lvF;
     Buf vj[24];                     // adjoint work arrays
     Buf dstats;                     // device HHS stats: level counts (64), work (2), flags
@@ -699,7 +700,8 @@ int fsi_destroy(fsi_ctx* c) {
                    &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->mc, &c->bhc, &c->ids[0], &c->ids[1],
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
                    &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
-                   &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats};
+                   &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
+                   &c->eout, &c->snapx, &c->snapv};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -986,13 +988,13 @@ int fsi_energy(fsi_ctx* c, int N, const double* pos, const double* vel, const do
     return FSI_OK;
 }
 
-int fsi_hhs_interval(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
-                     const unsigned char* is_bh, double tau, void* stream) {
-    CK(check_common(c, N));
-    if (!pos || !vel || !mass) return fail(FSI_ERR_ARG, "NULL array");
-    if (!(tau > 0.0)) return fail(FSI_ERR_ARG, "tau must be positive");
-    if (c->p.c > 0.0 && !is_bh) return fail(FSI_ERR_ARG, "PN on (c > 0) needs is_bh");
-    const cudaStream_t s = S(stream);
+}  // extern "C"
+
+namespace {
+
+// One HHS interval (arguments checked by the caller); FSI_OK or FSI_ERR_MAXLEVEL.
+int hhs_interval_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                      const unsigned char* is_bh, double tau, cudaStream_t s) {
     CK(ensure(c->iota, (size_t)N * 4));
     CK(ensure(c->step0, (size_t)N * 8));
     CK(ensure(c->counts, 16));
@@ -1015,8 +1017,87 @@ int fsi_hhs_interval(fsi_ctx* c, int N, double* pos, double* vel, const double* 
         c->work_pairs[1] += (long long)st[65];
         if (reinterpret_cast<int*>(st + 66)[0]) c->max_level_hit = 1;
     }
-    if (c->max_level_hit) return fail(FSI_ERR_MAXLEVEL, "a particle needed a level deeper than %d", c->p.max_level);
+    return c->max_level_hit ? FSI_ERR_MAXLEVEL : FSI_OK;
+}
+
+// E = T + W of all N particles, FP64 (synchronous).
+int total_energy(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+                 cudaStream_t s, double* E) {
+    CK(ensure(c->eout, 2 * sizeof(double)));
+    CK(fsi_energy(c, N, pos, vel, mass, nullptr, N, P<double>(c->eout), s));
+    double h[2];
+    CU(cudaMemcpyAsync(h, c->eout.p, sizeof h, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    *E = h[0] + h[1];
     return FSI_OK;
+}
+
+int check_hhs_args(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+                   const unsigned char* is_bh, double tau) {
+    CK(check_common(c, N));
+    if (!pos || !vel || !mass) return fail(FSI_ERR_ARG, "NULL array");
+    if (!(tau > 0.0)) return fail(FSI_ERR_ARG, "tau must be positive");
+    if (c->p.c > 0.0 && !is_bh) return fail(FSI_ERR_ARG, "PN on (c > 0) needs is_bh");
+    return FSI_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int fsi_hhs_interval(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                     const unsigned char* is_bh, double tau, void* stream) {
+    CK(check_hhs_args(c, N, pos, vel, mass, is_bh, tau));
+    const int st = hhs_interval_core(c, N, pos, vel, mass, is_bh, tau, S(stream));
+    if (st == FSI_ERR_MAXLEVEL)
+        return fail(FSI_ERR_MAXLEVEL, "a particle needed a level deeper than %d", c->p.max_level);
+    return st;
+}
+
+int fsi_hhs_interval_restart(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                             const unsigned char* is_bh, double tau, double eta_restart,
+                             int max_restarts, int* restarts, double* rel_err, void* stream) {
+    CK(check_hhs_args(c, N, pos, vel, mass, is_bh, tau));
+    if (!(eta_restart >= 0.0) || max_restarts < 0)
+        return fail(FSI_ERR_ARG, "eta_restart must be >= 0 and max_restarts >= 0");
+    const cudaStream_t s = S(stream);
+    const size_t bytes = 3 * (size_t)N * sizeof(double);
+    CK(ensure(c->snapx, bytes));
+    CK(ensure(c->snapv, bytes));
+    CU(cudaMemcpyAsync(c->snapx.p, pos, bytes, cudaMemcpyDeviceToDevice, s));
+    CU(cudaMemcpyAsync(c->snapv.p, vel, bytes, cudaMemcpyDeviceToDevice, s));
+    double E0 = 0.0;
+    CK(total_energy(c, N, pos, vel, mass, s, &E0));
+    const fsi_params keep = c->p;
+    double prev = INFINITY, e = INFINITY;
+    int k = 0, st = FSI_OK;
+    for (;; ++k) {
+        // attempt k: every time-step accuracy parameter lowered by 50 % per restart
+        const double f = std::ldexp(1.0, -k);
+        c->p.eta_ff = keep.eta_ff * f;
+        c->p.eta_fb = keep.eta_fb * f;
+        c->p.eta_jerk = keep.eta_jerk * f;
+        c->p.eta_grad = keep.eta_grad * f;
+        c->p.eta_va = keep.eta_va * f;
+        if (k > 0) {
+            CU(cudaMemcpyAsync(pos, c->snapx.p, bytes, cudaMemcpyDeviceToDevice, s));
+            CU(cudaMemcpyAsync(vel, c->snapv.p, bytes, cudaMemcpyDeviceToDevice, s));
+        }
+        st = hhs_interval_core(c, N, pos, vel, mass, is_bh, tau, s);
+        if (st != FSI_OK && st != FSI_ERR_MAXLEVEL) break;
+        double E1 = 0.0;
+        const int re = total_energy(c, N, pos, vel, mass, s, &E1);
+        if (re != FSI_OK) { st = re; break; }
+        e = std::fabs((E1 - E0) / E0);
+        if (e <= eta_restart || (k > 0 && e > prev) || k >= max_restarts) break;
+        prev = e;
+    }
+    c->p = keep;
+    if (restarts) *restarts = k;
+    if (rel_err) *rel_err = e;
+    if (st == FSI_ERR_MAXLEVEL)
+        return fail(FSI_ERR_MAXLEVEL, "a particle needed a level deeper than %d", c->p.max_level);
+    return st;
 }
 
 int fsi_level_stats(fsi_ctx* c, long long* counts, int max) {

@@ -37,7 +37,7 @@ FSI_MIXED = 1
 EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params", "fsi_reserve",
             "fsi_last_error", "fsi_sync_status", "fsi_accel", "fsi_grad", "fsi_accel_grad",
             "fsi_pn_accel", "fsi_step", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
-            "fsi_level_stats", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
+            "fsi_level_stats", "fsi_hhs_interval_restart", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall",
@@ -70,6 +70,8 @@ _lib.fsi_timesteps.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
 _lib.fsi_energy.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
 _lib.fsi_hhs_interval.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp]
 _lib.fsi_level_stats.argtypes = [_vp, C.POINTER(C.c_longlong), _ip]
+_lib.fsi_hhs_interval_restart.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _dp, _ip,
+                                          C.POINTER(_ip), C.POINTER(_dp), _vp]
 _lib.fsi_profile.argtypes = [_vp, _ip]
 _lib.fsi_profile_read.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_double)]
 _lib.fsi_launch_count.restype = C.c_longlong
@@ -282,6 +284,23 @@ def fsi_hhs_interval(ctx: Context, pos, vel, mass, tau: float, is_bh=None, strea
     if code not in (FSI_OK, FSI_ERR_MAXLEVEL):
         raise FsiError(code, "fsi_hhs_interval")
     return int(code)
+
+
+def fsi_hhs_interval_restart(ctx: Context, pos, vel, mass, tau: float, eta_restart: float,
+                             max_restarts: int = 8, is_bh=None, stream=None):
+    """One HHS interval with adaptive energy-error restarts, in place; returns
+    (status, restarts, |dE/E| of the accepted attempt)."""
+    N = mass.numel()
+    k = C.c_int()
+    e = C.c_double()
+    code = _lib.fsi_hhs_interval_restart(ctx.handle, N, _f64(pos, (3, N), "pos"),
+                                         _f64(vel, (3, N), "vel"), _f64(mass, (N,), "mass"),
+                                         _u8(is_bh, N, "is_bh"), float(tau), float(eta_restart),
+                                         int(max_restarts), C.byref(k), C.byref(e),
+                                         _stream(stream))
+    if code not in (FSI_OK, FSI_ERR_MAXLEVEL):
+        raise FsiError(code, "fsi_hhs_interval_restart")
+    return int(code), int(k.value), float(e.value)
 
 
 def fsi_level_stats(ctx: Context, max_levels: int = 64):

@@ -458,3 +458,58 @@ def test_pn_periapsis_advance_rate(m2):
     dw = (math.remainder(w1 - w0, 2 * math.pi)) / norb
     expect = 6 * math.pi * m.sum() / (c * c * a0 * (1 - e0 * e0))
     assert dw == pytest.approx(expect, rel=0.02)
+
+
+# ----------------------------------------------------------------------------- restarts
+def _restart_reference(c, tau, k, **kw):
+    """The interval re-run as attempt k of the restart procedure: every eta times 2^-k."""
+    f = 0.5 ** k
+    eta = {n: kw.get(n, d) * f for n, d in (("eta_ff", 0.2), ("eta_fb", 0.2), ("eta_jerk", 0.1),
+                                           ("eta_grad", 0.0), ("eta_va", 0.0))}
+    p, v, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, allow_maxlevel=True, **eta)
+    E0 = sum(oracle.energy(c.pos, c.vel, c.mass))
+    return p, v, counts, abs((sum(oracle.energy(p, v, c.mass)) - E0) / E0)
+
+
+def test_restart_within_tolerance_is_the_plain_interval():
+    c = inputs.plummer(300, 28, imf="kroupa")
+    p, v, counts, k, e, _ = oracle.hhs_interval_restart(c.pos, c.vel, c.mass, 1 / 16, 1.0)
+    rp, rv, rc, re = _restart_reference(c, 1 / 16, 0)
+    assert k == 0 and e == re
+    assert np.array_equal(p, rp) and np.array_equal(v, rv) and np.array_equal(counts, rc)
+
+
+def test_restart_halves_every_accuracy_parameter_per_restart():
+    """Sect. 3.12: each consecutive restart lowers every time-step parameter by 50 %, until
+    the energy error is within the tolerance; the accepted state is the interval run from
+    the saved state with the parameters times 2^-k."""
+    c = inputs.plummer(300, 28, imf="kroupa")
+    kw = dict(eta_grad=0.1, eta_va=0.2)
+    errs = [_restart_reference(c, 1 / 16, k, **kw)[3] for k in range(3)]
+    assert errs[0] > errs[1] > errs[2]
+    tol = (errs[1] * errs[2]) ** 0.5            # attempts 0 and 1 fail, attempt 2 passes
+    p, v, counts, k, e, _ = oracle.hhs_interval_restart(c.pos, c.vel, c.mass, 1 / 16, tol, **kw)
+    rp, rv, rc, re = _restart_reference(c, 1 / 16, 2, **kw)
+    assert k == 2 and e == re
+    assert np.array_equal(p, rp) and np.array_equal(v, rv) and np.array_equal(counts, rc)
+
+
+def test_restart_keeps_the_current_result_when_the_error_grows():
+    """A 24-body cluster whose error grows when the steps are halved (1.7e-5 -> 3.3e-5):
+    with a 1e-6 tolerance the first restart's result is accepted."""
+    c = inputs.plummer(24, 304, imf="kroupa")
+    e0, e1 = (_restart_reference(c, 1 / 8, k)[3] for k in (0, 1))
+    assert e1 > 1.5 * e0 > 1e-6
+    p, v, counts, k, e, _ = oracle.hhs_interval_restart(c.pos, c.vel, c.mass, 1 / 8, 1e-6)
+    rp, rv, _, re = _restart_reference(c, 1 / 8, 1)
+    assert k == 1 and e == re
+    assert np.array_equal(p, rp) and np.array_equal(v, rv)
+
+
+def test_restart_stops_after_max_restarts():
+    c = inputs.plummer(300, 28, imf="kroupa")
+    p, v, counts, k, e, _ = oracle.hhs_interval_restart(c.pos, c.vel, c.mass, 1 / 16, 0.0,
+                                                        max_restarts=3)
+    rp, rv, _, re = _restart_reference(c, 1 / 16, 3)
+    assert k == 3 and e == re
+    assert np.array_equal(p, rp) and np.array_equal(v, rv)

@@ -440,6 +440,50 @@ def test_hhs_interval(F, prec, small):
     assert np.abs(v - rv).max() <= tol * 100
 
 
+RESTART_CASES = {
+    # name: (N, seed, tau, tolerance or None (between attempts 1 and 2), max_restarts, etas)
+    "halve": (300, 28, 1 / 16, None, 8, dict(eta_grad=0.1, eta_va=0.2)),
+    "grows": (24, 304, 1 / 8, 1e-6, 8, {}),
+    "cap": (300, 28, 1 / 16, 0.0, 3, {}),
+}
+
+
+@pytest.mark.parametrize("case", sorted(RESTART_CASES))
+def test_hhs_interval_restart(F, case):
+    """Adaptive energy-error restarts (Sect. 3.12) through the C ABI against the oracle's
+    procedure: the same number of restarts (every time-step parameter halved per restart),
+    the same accepted state and energy error.  "halve": two restarts reach the tolerance;
+    "grows": the first restart's error is larger, so its result is kept; "cap": a zero
+    tolerance stops after max_restarts."""
+    n, seed, tau, tol, cap, kw = RESTART_CASES[case]
+    c = inputs.plummer(n, seed, imf="kroupa")
+    if tol is None:
+        E0 = sum(oracle.energy(c.pos, c.vel, c.mass))
+        errs = []
+        for k in (1, 2):
+            f = 0.5 ** k
+            eta = dict(eta_ff=0.2 * f, eta_fb=0.2 * f, eta_jerk=0.1 * f,
+                       **{q: w * f for q, w in kw.items()})
+            p, v, _, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, **eta)
+            errs.append(abs((sum(oracle.energy(p, v, c.mass)) - E0) / E0))
+        tol = (errs[0] * errs[1]) ** 0.5
+    rp, rv, counts, rk, re, _ = oracle.hhs_interval_restart(c.pos, c.vel, c.mass, tau, tol,
+                                                            max_restarts=cap, **kw)
+    with F.Context("fp64", **kw) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code, k, e = F.fsi_hhs_interval_restart(ctx, p, v, dev(c.mass), tau, tol, cap)
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert k == rk, (k, rk)
+    assert abs(e - re) <= 1e-13 + 1e-6 * re, (e, re)
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    assert np.abs(p - rp).max() <= 1e-10
+    assert np.abs(v - rv).max() <= 1e-8
+
+
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("small", [0, -1])
 def test_hhs_interval_with_pn(F, prec, small):
