@@ -507,8 +507,22 @@ def run_vjp(args):
     return 0
 
 
+# The softened equal-mass long run of Sect. 5.2 in Henon units: 161000 stars of 0.5 Msun
+# (M = 80500 Msun), half-mass radius 3.1 pc, softening length 1e-3 pc, interval 1e-3 Myr,
+# eta 0.2 (free fall, fly-by) and 0.1 (jerk, gradient).  Plummer: r_h = a / (2^{2/3} - 1)^{1/2}
+# with a = 3 pi / 16, so the length unit is 3.1 pc / r_h and the time unit
+# (L^3 / (G M))^{1/2} with G = 4.4985e-3 pc^3 / (Msun Myr^2).
+SOFT_RH_NB = (3.0 * math.pi / 16.0) / math.sqrt(2.0 ** (2.0 / 3.0) - 1.0)
+SOFT_LUNIT_PC = 3.1 / SOFT_RH_NB
+SOFT_TUNIT_MYR = math.sqrt(SOFT_LUNIT_PC ** 3 / (4.4985e-3 * 80500.0))
+SOFT_EPS = 1e-3 / SOFT_LUNIT_PC
+SOFT_TAU = 1e-3 / SOFT_TUNIT_MYR
+
+
 def run_hhs(args):
-    """N = 65536 Plummer with a Kroupa IMF, eps = 0: HHS intervals of tau0 = 1/64."""
+    """HHS intervals: N = 65536 Plummer with a Kroupa IMF, eps = 0, tau0 = 1/64 (default);
+    with --workload plummer161k the softened equal-mass long run (Sect. 5.2 setup), which
+    reports the energy error of every interval."""
     import torch
     from paper_2210_02472_b300 import fsi as F
     torch.cuda.set_device(0)
@@ -519,28 +533,45 @@ def run_hhs(args):
     mass = torch.as_tensor(c.mass).to(dev)
     bh = torch.as_tensor(c.is_bh.astype(np.uint8)).to(dev)
     cl = 1e4 if args.hhs_pn else 0.0
-    ctx = F.Context(args.precision, c=cl)
-    e0 = F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum()
+    soft = wl == "plummer161k"
+    tau = SOFT_TAU if soft else args.tau
+    kw = dict(eps2=SOFT_EPS ** 2, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eta_grad=0.1) if soft else {}
+    ctx = F.Context(args.precision, c=cl, **kw)
+    energy = lambda: float(F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum())
+    e0 = energy()
     F.fsi_work_stats(ctx, reset=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    levels = []
+    levels, per_interval, t_int = [], [], 0.0
+    ek = e0
     for _ in range(args.intervals):
-        code = F.fsi_hhs_interval(ctx, pos, vel, mass, args.tau, is_bh=bh if cl > 0 else None)
+        ti = time.perf_counter()
+        code = F.fsi_hhs_interval(ctx, pos, vel, mass, tau, is_bh=bh if cl > 0 else None)
         levels.append(F.fsi_level_stats(ctx))
+        if soft:
+            torch.cuda.synchronize()
+            t_int += time.perf_counter() - ti
+            e = energy()                 # outside the interval timing
+            per_interval.append(abs((e - ek) / ek))
+            ek = e
     torch.cuda.synchronize()
-    t = time.perf_counter() - t0
+    t = t_int if soft else time.perf_counter() - t0
     acc_p, grad_p = F.fsi_work_stats(ctx)
-    e1 = F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum()
+    e1 = energy()
     inter = (acc_p * FLOP_ACC + grad_p * FLOP_GRAD) / FLOP_PAIR
     line = {
-        "metric": f"HHS acc+grad pair interactions/s ({wl}, tau0 = {args.tau:g})",
+        "metric": f"HHS acc+grad pair interactions/s ({wl}, tau0 = {tau:g})",
         "value": inter / t, "unit": UNIT, "n_gpus": 1, "steps": args.intervals, "warmup": 0,
         "ms_per_step": 1e3 * t / args.intervals, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
-        "config": {"workload": wl, "n": c.n, "tau": args.tau, "intervals": args.intervals, "c": cl},
+        "config": {"workload": wl, "n": c.n, "tau": tau, "intervals": args.intervals, "c": cl,
+                   **({"eps2": SOFT_EPS ** 2, "eta": "ff 0.2, fb 0.2, jerk 0.1, gradient 0.1",
+                       "units": f"length {SOFT_LUNIT_PC:.4f} pc, time {SOFT_TUNIT_MYR:.4f} Myr"}
+                      if soft else {})},
         "level_counts": levels, "rel_energy_error": abs((e1 - e0) / e0),
+        "rel_energy_error_per_interval": per_interval or None,
+        "mean_rel_energy_error_per_interval": float(np.mean(per_interval)) if per_interval else None,
         "acc_pairs": acc_p, "grad_pairs": grad_p, "maxlevel_status": code,
     }
     print(json.dumps(line), flush=True)

@@ -212,4 +212,6 @@ def workload(name: str) -> Cluster:
         return plummer(1 << 20, SEED_BASE + 3, imf="kroupa", n_bh=16)
     if name == "plummer16k":       # 16384 equal-mass stars
         return plummer(16384, SEED_BASE + 4, imf="equal")
+    if name == "plummer161k":      # 161000 equal-mass stars (the softened long-run cluster)
+        return plummer(161000, SEED_BASE + 6, imf="equal")
     raise KeyError(name)
