@@ -87,6 +87,11 @@ def lib():
         L.or_hhs_interval_restart.argtypes = [C.c_int, dp, dp, dp, C.c_double,
                                               C.POINTER(_HHSParams), C.c_double, C.c_int,
                                               C.POINTER(C.c_longlong), ip, dp]
+        L.or_acc_sub.argtypes = [C.c_int, dp, dp, ip, ip, C.c_int, ip, C.c_int, C.c_double, dp]
+        L.or_grad_sub.argtypes = [C.c_int, dp, dp, ip, dp, ip, C.c_int, ip, C.c_int, C.c_double,
+                                  dp]
+        L.or_fsi_step_sub.argtypes = [C.c_int, dp, dp, dp, ip, ip, C.c_int, ip, C.c_int,
+                                      C.c_double, C.c_double]
         L.or_vjp_acc.argtypes = [C.c_int, dp, dp, ip, C.c_int, C.c_double, dp, C.c_double,
                                  C.c_double, dp, dp]
         L.or_vjp_grad.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int, C.c_double, dp, C.c_double,
@@ -268,6 +273,52 @@ def hhs_interval_restart(pos, vel, mass, tau, eta_restart, max_restarts=8, eta_f
     if code not in (OK, ERR_MAXLEVEL):
         raise OracleError(code, "hhs_interval_restart")
     return pos, vel, counts, k.value, e.value, code
+
+
+def subsystem_ids(N, pairs):
+    """sub (N,) int32: the pair index of each member of `pairs` ((n_pairs, 2) global ids),
+    -1 for single particles."""
+    sub = np.full(N, -1, dtype=np.int32)
+    for s, (i, j) in enumerate(np.asarray(pairs, dtype=np.int64).reshape(-1, 2)):
+        sub[i] = sub[j] = s
+    return sub
+
+
+def acc_sub(pos, mass, pairs, A=None, B=None, eps2=0.0):
+    """acc(A <- B) without the pairs inside one subsystem (Algorithm 1)."""
+    pos, mass, A, B = _f64(pos), _f64(mass), _idx(A), _idx(B)
+    N = mass.shape[0]
+    sub = subsystem_ids(N, pairs)
+    nA = _n(A, N)
+    out = np.zeros((3, nA))
+    _check(lib().or_acc_sub(N, _d(pos), _d(mass), _i(sub), _i(A), nA, _i(B), _n(B, N),
+                            float(eps2), _d(out)), "acc_sub")
+    return out
+
+
+def grad_sub(pos, mass, pairs, accg, A=None, B=None, eps2=0.0):
+    """grad(A <- B) without intra-subsystem pairs; accg (3, N) global-id field."""
+    pos, mass, accg, A, B = _f64(pos), _f64(mass), _f64(accg), _idx(A), _idx(B)
+    N = mass.shape[0]
+    sub = subsystem_ids(N, pairs)
+    nA = _n(A, N)
+    out = np.zeros((3, nA))
+    _check(lib().or_grad_sub(N, _d(pos), _d(mass), _i(sub), _d(accg), _i(A), nA, _i(B),
+                             _n(B, N), float(eps2), _d(out)), "grad_sub")
+    return out
+
+
+def fsi_step_sub(pos, vel, mass, pairs, h, P=None, eps2=0.0, steps=1):
+    """FSI cycles with binary subsystems (Sect. 2.3, Algorithm 1); returns (pos, vel)."""
+    pos, vel, mass, P = _f64(pos).copy(), _f64(vel).copy(), _f64(mass), _idx(P)
+    N = mass.shape[0]
+    pr = np.ascontiguousarray(np.asarray(pairs, dtype=np.int32).reshape(-1))
+    sub = subsystem_ids(N, pairs)
+    for _ in range(steps):
+        _check(lib().or_fsi_step_sub(N, _d(pos), _d(vel), _d(mass), _i(sub), _i(pr),
+                                     int(pr.shape[0] // 2), _i(P), _n(P, N), float(h),
+                                     float(eps2)), "fsi_step_sub")
+    return pos, vel
 
 
 def vjp_acc(pos, mass, u, P=None, eps2=0.0):

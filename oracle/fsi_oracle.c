@@ -32,6 +32,7 @@
 #define OR_ERR_NOMEM (-2)
 #define OR_ERR_COINCIDENT (-4)
 #define OR_ERR_MAXLEVEL (-6)
+#define OR_PI 3.14159265358979323846
 
 /* ------------------------------------------------------------------------------- */
 static int or_threads = 1;
@@ -371,6 +372,216 @@ int or_fsi_step(int N, double *pos, double *vel, const double *mass,
     free(a);
     free(g);
     free(a3);
+    return err;
+}
+
+/* =============================================================================== *
+ * FSI with subsystems (Sect. 2.3, Algorithm 1), kernel side: the splitting
+ * H = T' + U' + sum_s H_S^s with U' = U minus the intra-subsystem potentials.  The kicks
+ * use accelerations and gradient sums that ignore every pair inside one subsystem; the
+ * drifts move only the single particles; each subsystem is advanced by its own
+ * Hamiltonian H_S (its members' kinetic energy plus their mutual potential) for eps/2
+ * twice per cycle.  Subsystems here are isolated bound binaries, whose H_S flow is the
+ * exact two-body (Kepler) motion: the centre of mass moves on a straight line and the
+ * relative orbit follows Kepler's equation (Sect. 3.11).
+ * sub[i] (N entries, global id) is the subsystem of particle i, -1 for a single.
+ * =============================================================================== */
+static int same_subsystem(const int *sub, int i, int j)
+{
+    return sub && sub[i] >= 0 && sub[i] == sub[j];
+}
+
+/* acc(A <- B) without intra-subsystem pairs (plain definition, as or_acc). */
+int or_acc_sub(int N, const double *pos, const double *mass, const int *sub,
+               const int *A, int nA, const int *B, int nB, double eps2, double *acc)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    int err = OR_OK;
+    int k;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (k = 0; k < nA; ++k) {
+        int i = idx_at(A, k);
+        double ax = 0.0, ay = 0.0, az = 0.0;
+        for (int l = 0; l < nB; ++l) {
+            int j = idx_at(B, l);
+            if (j == i || same_subsystem(sub, i, j)) continue;
+            double dx = X[j] - X[i], dy = Y[j] - Y[i], dz = Z[j] - Z[i];
+            double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double f = mass[j] / (r2 * sqrt(r2));
+            ax += f * dx; ay += f * dy; az += f * dz;
+        }
+        acc[k] = ax;
+        acc[(size_t)nA + k] = ay;
+        acc[2 * (size_t)nA + k] = az;
+    }
+    return err;
+}
+
+/* grad(A <- B) without intra-subsystem pairs; accg is a 3 x N global-id field. */
+int or_grad_sub(int N, const double *pos, const double *mass, const int *sub,
+                const double *accg, const int *A, int nA, const int *B, int nB, double eps2,
+                double *grad)
+{
+    const double *X = pos, *Y = pos + N, *Z = pos + 2 * (size_t)N;
+    const double *AX = accg, *AY = accg + N, *AZ = accg + 2 * (size_t)N;
+    int err = OR_OK;
+    int k;
+#pragma omp parallel for schedule(dynamic, 16) num_threads(or_threads)
+    for (k = 0; k < nA; ++k) {
+        int i = idx_at(A, k);
+        double gx = 0.0, gy = 0.0, gz = 0.0;
+        for (int l = 0; l < nB; ++l) {
+            int j = idx_at(B, l);
+            if (j == i || same_subsystem(sub, i, j)) continue;
+            double dx = X[j] - X[i], dy = Y[j] - Y[i], dz = Z[j] - Z[i];
+            double r2 = dx * dx + dy * dy + dz * dz + eps2;
+            if (r2 == 0.0) {
+#pragma omp atomic write
+                err = OR_ERR_COINCIDENT;
+                continue;
+            }
+            double bx = AX[j] - AX[i], by = AY[j] - AY[i], bz = AZ[j] - AZ[i];
+            double r = sqrt(r2);
+            double f = mass[j] / (r2 * r2 * r);
+            double adotr = bx * dx + by * dy + bz * dz;
+            gx += f * (r2 * bx - 3.0 * adotr * dx);
+            gy += f * (r2 * by - 3.0 * adotr * dy);
+            gz += f * (r2 * bz - 3.0 * adotr * dz);
+        }
+        grad[k] = gx;
+        grad[(size_t)nA + k] = gy;
+        grad[2 * (size_t)nA + k] = gz;
+    }
+    return err;
+}
+
+/* Kepler's equation M = E - e sin E (Sect. 3.11): the cubic first approximation in
+ * s = sin(E/3) (arcsin expanded to third order; the real root of
+ * (1 - e) s + (1/6 + 4e/3) s^3 = M/3), then Newton-Raphson with a bisection fallback,
+ * until two consecutive iterates differ by less than tol. */
+static double kepler_solve(double M, double e, double tol)
+{
+    double twopi = 2.0 * OR_PI;
+    double k = floor((M + OR_PI) / twopi);
+    double Mr = M - k * twopi;
+    double sgn = Mr >= 0.0 ? 1.0 : -1.0;
+    double Ma = fabs(Mr);
+    double c3 = 1.0 / 6.0 + 4.0 * e / 3.0;
+    double p = (1.0 - e) / c3, q = (Ma / 3.0) / c3;
+    double s;
+    if (p > 0.0) {
+        double al = 2.0 * sqrt(p / 3.0);
+        s = al * sinh(asinh(4.0 * q / (al * al * al)) / 3.0);
+    } else {
+        s = cbrt(q);
+    }
+    if (s > 1.0) s = 1.0;
+    double E = 3.0 * asin(s);
+    double lo = 0.0, hi = OR_PI;
+    for (int it = 0; it < 200; ++it) {
+        double f = E - e * sin(E) - Ma;
+        if (f > 0.0) { if (E < hi) hi = E; }
+        else if (E > lo) lo = E;
+        double En = E - f / (1.0 - e * cos(E));
+        if (!(En >= lo && En <= hi)) En = 0.5 * (lo + hi);
+        double d = fabs(En - E);
+        E = En;
+        if (d < tol) break;
+    }
+    return sgn * E + k * twopi;
+}
+
+/* Exact two-body motion of particles i, j over time t (bound orbits only). */
+static int kepler_drift(int N, double *pos, double *vel, const double *mass, int i, int j,
+                        double t)
+{
+    double mi = mass[i], mj = mass[j], mu = mi + mj;
+    double R[3], V[3], r0[3], v0[3];
+    for (int q = 0; q < 3; ++q) {
+        size_t oi = (size_t)q * N + i, oj = (size_t)q * N + j;
+        R[q] = (mi * pos[oi] + mj * pos[oj]) / mu;
+        V[q] = (mi * vel[oi] + mj * vel[oj]) / mu;
+        r0[q] = pos[oj] - pos[oi];
+        v0[q] = vel[oj] - vel[oi];
+    }
+    double r0n = sqrt(r0[0] * r0[0] + r0[1] * r0[1] + r0[2] * r0[2]);
+    double v02 = v0[0] * v0[0] + v0[1] * v0[1] + v0[2] * v0[2];
+    double rv = r0[0] * v0[0] + r0[1] * v0[1] + r0[2] * v0[2];
+    double inva = 2.0 / r0n - v02 / mu;
+    if (!(inva > 0.0)) return OR_ERR_ARG;           /* unbound: not a binary */
+    double a = 1.0 / inva;
+    double n = sqrt(mu * inva * inva * inva);
+    double ec = 1.0 - r0n / a;                      /* e cos E0 */
+    double es = rv / sqrt(mu * a);                  /* e sin E0 */
+    double e = sqrt(ec * ec + es * es);
+    double E0 = atan2(es, ec);
+    double M0 = E0 - es;
+    double E1 = kepler_solve(M0 + n * t, e, 1e-15);
+    double dE = E1 - E0;
+    double f = 1.0 - (a / r0n) * (1.0 - cos(dE));
+    double g = t - (dE - sin(dE)) / n;
+    double r1[3];
+    for (int q = 0; q < 3; ++q) r1[q] = f * r0[q] + g * v0[q];
+    double r1n = sqrt(r1[0] * r1[0] + r1[1] * r1[1] + r1[2] * r1[2]);
+    double fd = -sqrt(mu * a) * sin(dE) / (r0n * r1n);
+    double gd = 1.0 - (a / r1n) * (1.0 - cos(dE));
+    for (int q = 0; q < 3; ++q) {
+        double v1 = fd * r0[q] + gd * v0[q];
+        double Rq = R[q] + V[q] * t;
+        size_t oi = (size_t)q * N + i, oj = (size_t)q * N + j;
+        pos[oi] = Rq - (mj / mu) * r1[q];
+        pos[oj] = Rq + (mi / mu) * r1[q];
+        vel[oi] = V[q] - (mj / mu) * v1;
+        vel[oj] = V[q] + (mi / mu) * v1;
+    }
+    return OR_OK;
+}
+
+/* One FSI cycle of set P with the binary subsystems listed in pairs (n_pairs pairs of
+ * global ids, members of P; sub must mark them: sub[pairs[2s]] = sub[pairs[2s+1]] = s and
+ * -1 for every other particle), Algorithm 1:
+ *   kick eps/6 (a'), subsystems eps/2, drift singles eps/2, kick 2eps/3 (a' + eps^2/24 G'),
+ *   subsystems eps/2, drift singles eps/2, kick eps/6 (a'),
+ * where a' and G' ignore the intra-subsystem pairs (G' from the a' of the same term). */
+int or_fsi_step_sub(int N, double *pos, double *vel, const double *mass, const int *sub,
+                    const int *pairs, int n_pairs, const int *P, int n, double h, double eps2)
+{
+    if (n <= 0) return OR_OK;
+    double *a = (double *)malloc(3 * (size_t)n * sizeof(double));
+    double *g = (double *)malloc(3 * (size_t)n * sizeof(double));
+    double *field = (double *)calloc(3 * (size_t)N, sizeof(double));
+    if (!a || !g || !field) { free(a); free(g); free(field); return OR_ERR_NOMEM; }
+    int err = OR_OK;
+    for (int half = 0; half < 2 && err == OR_OK; ++half) {
+        /* opening kick eps/6 (half 0) or gradient kick 2 eps/3 (half 1) */
+        err = or_acc_sub(N, pos, mass, sub, P, n, P, n, eps2, a);
+        if (err == OR_OK && half == 1) {
+            for (int k = 0; k < n; ++k)
+                for (int q = 0; q < 3; ++q) field[(size_t)q * N + idx_at(P, k)] = a[(size_t)q * n + k];
+            err = or_grad_sub(N, pos, mass, sub, field, P, n, P, n, eps2, g);
+            if (err == OR_OK)
+                for (size_t q = 0; q < 3 * (size_t)n; ++q) a[q] += (h * h / 24.0) * g[q];
+        }
+        if (err != OR_OK) break;
+        kick(N, vel, P, n, a, half == 0 ? h / 6.0 : 2.0 * h / 3.0);
+        for (int s = 0; s < n_pairs && err == OR_OK; ++s)
+            err = kepler_drift(N, pos, vel, mass, pairs[2 * s], pairs[2 * s + 1], 0.5 * h);
+        for (int k = 0; k < n && err == OR_OK; ++k) {
+            int i = idx_at(P, k);
+            if (sub[i] >= 0) continue;
+            for (int q = 0; q < 3; ++q) pos[(size_t)q * N + i] += 0.5 * h * vel[(size_t)q * N + i];
+        }
+    }
+    if (err == OR_OK) err = or_acc_sub(N, pos, mass, sub, P, n, P, n, eps2, a);
+    if (err == OR_OK) kick(N, vel, P, n, a, h / 6.0);
+    free(a);
+    free(g);
+    free(field);
     return err;
 }
 
