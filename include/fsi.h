@@ -195,6 +195,21 @@ int fsi_step_vjp(fsi_ctx *ctx, int N, const double *pos0, const double *vel0,
                  const double *gx_out, const double *gv_out, double *gx_in, double *gv_in,
                  double *gm, void *stream);
 
+/* nsteps FSI cycles of the set idx (NULL = all N, then n == N) with binary subsystems
+ * (Sect. 2.3, Algorithm 1), in place: kick eps/6, subsystems eps/2, drift of the single
+ * particles eps/2, gradient kick 2 eps/3 (a + eps^2/24 G), subsystems eps/2, drift eps/2,
+ * kick eps/6, where every acceleration and gradient sum ignores the pair inside a
+ * subsystem.  pairs: device int array of 2 x n_pairs global ids, binary s =
+ * (pairs[2s], pairs[2s+1]); both members must be in the set and in no other binary
+ * (else FSI_ERR_ARG is latched on the device).  A binary's subsystem flow is its exact
+ * two-body motion over eps/2 (Kepler's equation, FP64); an unbound pair latches
+ * FSI_ERR_UNSUPPORTED (regularised and secular subsystem integrators are not part of
+ * this library).  Newtonian only: FSI_ERR_UNSUPPORTED when fsi_params.c > 0.  Masked
+ * passes take the one-sided pair kernel in the context's precision. */
+int fsi_step_sub(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
+                 const int *idx, int n, const int *pairs, int n_pairs, double h, int nsteps,
+                 void *stream);
+
 /* Time steps of the set P against itself (Sect. 3.4): min of the free-fall
  * eta_ff min_j (r^3/(m_i+m_j))^{1/2}, fly-by eta_fb min_j r/|v_ij| and jerk
  * eta_jerk |a_i|/|j_i| criteria (eta's and eps2 from fsi_params), and, when

@@ -77,7 +77,8 @@ struct fsi_ctx {
     int* err_h = nullptr;          // pinned
     int* counts_h = nullptr;       // pinned, 3 ints (HHS partition)
     Buf rec[2], accrec[2], xc, vc, ac, ad, gA, gB, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
-        nbh, apn, pnpart, epart, iota, steps, step0, counts, accum, eout, snapx, snapv;
+        nbh, apn, pnpart, epart, iota, steps, step0, counts, accum, eout, snapx, snapv,
+        subwhere, subkey, subppos;
     std::vector<Buf> lvS, lvF;
     Buf vj[24];                     // adjoint work arrays
     Buf dstats;                     // device HHS stats: level counts (64), work (2), flags
@@ -701,7 +702,7 @@ int fsi_destroy(fsi_ctx* c) {
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
                    &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
                    &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
-                   &c->eout, &c->snapx, &c->snapv};
+                   &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -948,6 +949,91 @@ int fsi_step(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     if (n == 0 || nsteps == 0) return FSI_OK;
     if (!pos || !vel || !mass) return fail(FSI_ERR_ARG, "NULL array");
     return step_core(c, N, pos, vel, mass, is_bh, idx, n, h, nsteps, S(stream));
+}
+
+int fsi_step_sub(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                 const int* idx, int n, const int* pairs, int n_pairs, double h, int nsteps,
+                 void* stream) {
+    CK(check_common(c, N));
+    if (!pos || !vel || !mass) return fail(FSI_ERR_ARG, "NULL array");
+    if (n < 0 || (!idx && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (n_pairs < 0 || (n_pairs > 0 && !pairs) || 2LL * n_pairs > n)
+        return fail(FSI_ERR_ARG, "bad binary list (%d pairs for %d particles)", n_pairs, n);
+    if (nsteps < 0) return fail(FSI_ERR_ARG, "nsteps must be >= 0");
+    if (c->p.c > 0.0) return fail(FSI_ERR_UNSUPPORTED, "subsystem steps are Newtonian (PN off)");
+    if (n == 0 || nsteps == 0) return FSI_OK;
+    if ((long long)N + n_pairs > INT_MAX) return fail(FSI_ERR_ARG, "N + n_pairs overflows the keys");
+    const cudaStream_t s = S(stream);
+    const int prec = c->p.precision;
+    CK(ensure(c->rec[0], pad_tile(n) * 32));
+    CK(ensure(c->accrec[0], pad_tile(n) * 32));
+    CK(ensure(c->ac, 3 * (size_t)n * 8));
+    CK(ensure(c->subwhere, (size_t)N * 4));
+    CK(ensure(c->subkey, (size_t)((n + 3) & ~3) * 4));
+    CK(ensure(c->subppos, (size_t)std::max(1, 2 * n_pairs) * 4));
+    int* key = P<int>(c->subkey);
+    int* ppos = P<int>(c->subppos);
+    CU(launch_sub_keys(n, idx, N, pairs, n_pairs, P<int>(c->subwhere), key, ppos, c->err_d, s));
+    double* xc = pos;
+    double* vc = vel;
+    const double* mc = mass;
+    if (idx) {
+        CK(ensure(c->xc, 3 * (size_t)n * 8));
+        CK(ensure(c->vc, 3 * (size_t)n * 8));
+        CK(ensure(c->mc, (size_t)n * 8));
+        xc = P<double>(c->xc);
+        vc = P<double>(c->vc);
+        CU(launch_gather3(N, pos, idx, n, xc, s));
+        CU(launch_gather3(N, vel, idx, n, vc, s));
+        CU(launch_gather1(N, mass, idx, n, P<double>(c->mc), s));
+        mc = P<double>(c->mc);
+    }
+    // a masked pass over the set: sources whose key equals the receiver's add nothing
+    auto pass = [&](int kind, double ck, double cg) -> int {
+        PairArgs a{};
+        a.irec = a.jrec = c->rec[0].p;
+        a.n_i = a.n_j = n;
+        a.check = CHECK_IDS;
+        a.iid = a.jid = key;
+        a.eps2 = c->p.eps2;
+        a.epi.mc = mc;
+        if (kind == KIND_ACC) {
+            a.epi.out = P<double>(c->ac);
+            a.epi.accrec = c->accrec[0].p;
+        } else {
+            a.iacc = a.jacc = c->accrec[0].p;
+            a.epi.base = P<double>(c->ac);
+            a.epi.c_grad = cg;
+        }
+        if (ck != 0.0) {
+            a.epi.v = vc;
+            a.epi.c_kick = ck;
+        }
+        return run_pair(c, kind, a, s);
+    };
+    // subsystems for t, then the single particles drift t; records repacked
+    auto flow = [&](double t) -> int {
+        CU(launch_kepler_pairs(n_pairs, ppos, n, xc, vc, mc, t, c->err_d, s));
+        CU(launch_drift_singles(n, xc, vc, key, N, t, s));
+        CU(launch_pack(prec, n, xc, mc, nullptr, n, c->rec[0].p, nullptr, s));
+        return FSI_OK;
+    };
+    CU(launch_pack(prec, n, xc, mc, nullptr, n, c->rec[0].p, nullptr, s));
+    for (int k = 0; k < nsteps; ++k) {
+        // Algorithm 1: kick eps/6, H_S + drift eps/2, gradient kick 2 eps/3, H_S + drift
+        // eps/2, kick eps/6; all accelerations without intra-subsystem pairs
+        CK(pass(KIND_ACC, h / 6.0, 0.0));
+        CK(flow(0.5 * h));
+        CK(pass(KIND_ACC, 0.0, 0.0));
+        CK(pass(KIND_GRAD, 2.0 * h / 3.0, h * h / 24.0));
+        CK(flow(0.5 * h));
+        CK(pass(KIND_ACC, h / 6.0, 0.0));
+    }
+    if (idx) {
+        CU(launch_scatter3(N, xc, idx, n, pos, s));
+        CU(launch_scatter3(N, vc, idx, n, vel, s));
+    }
+    return FSI_OK;
 }
 
 int fsi_timesteps(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,

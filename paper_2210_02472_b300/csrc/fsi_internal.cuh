@@ -264,6 +264,15 @@ cudaError_t launch_kick_drift(int precision, int n, double* xc, double* vc, cons
                               double c_kick, double c_drift, const double* mc, void* rec_out,
                               cudaStream_t s);
 cudaError_t launch_axpy3(int n, double* v, const double* a, double w, cudaStream_t s);
+// FSI with binary subsystems (subsys_kernels.cu): keys of the set (global id for singles,
+// N + s for both members of binary s) and the members' set positions; the exact two-body
+// flow of every binary over time t; the drift of the single particles.
+cudaError_t launch_sub_keys(int n, const int* idx, int N, const int* pairs, int n_pairs,
+                            int* where, int* key, int* ppos, int* err, cudaStream_t s);
+cudaError_t launch_kepler_pairs(int n_pairs, const int* ppos, int n, double* x, double* v,
+                                const double* m, double t, int* err, cudaStream_t s);
+cudaError_t launch_drift_singles(int n, double* x, const double* v, const int* key, int N, double w,
+                                 cudaStream_t s);
 cudaError_t launch_axpby3(int n, const double* a, const double* g, double c, double* out,
                           cudaStream_t s);
 constexpr int kMaxBHList = 1024;   // black holes per set handled by the PN kernels

@@ -30,7 +30,8 @@ __device__ __forceinline__ void mix_acc_pair(const float4 h, const float4 l, con
     const float y2 = y * y;
     const float sres = r2 * y2;                      // 1 - e, e = rsqrt residual
     // m r^-3 = m y^3 (1 - e)^{-3/2} ~ y^3 (2.5 m - 1.5 m (1 - e)); h.w = 2.5 m, l.w = -1.5 m
-    const float w = (y2 * y) * fmaf(sres, l.w, h.w);
+    float w = (y2 * y) * fmaf(sres, l.w, h.w);
+    if (CHK) w = self ? 0.0f : w;                    // excluded pair (self, or masked)
     fx = fmaf(w, dx, fx);
     fy = fmaf(w, dy, fy);
     fz = fmaf(w, dz, fz);
@@ -48,7 +49,8 @@ __device__ __forceinline__ void mix_grad_pair(const float4 h, const float4 l, co
     const float y = rsqrt_hw(r2);
     const float y2 = y * y;
     const float sres = r2 * y2;                      // 1 - e
-    const float w = (y2 * y) * fmaf(sres, l.w, h.w); // m r^-3
+    float w = (y2 * y) * fmaf(sres, l.w, h.w);       // m r^-3
+    if (CHK) w = self ? 0.0f : w;                    // excluded pair (self, or masked)
     const float bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;   // a_ji
     const float dot = fmaf(bx, dx, fmaf(by, dy, bz * dz));
     // -3 m r^-5 = -3 w y^2 (1 + e) = w y^2 (3 (1 - e) - 6)
@@ -80,7 +82,8 @@ __device__ __forceinline__ void f64_acc_pair(const D4 j, const F64I& p, double e
     if (CHK) r2 = self ? 1.0 : r2;
     const double y = rsqrt_f64(r2);
     const double y2 = y * y;
-    const double w = j.w * (y2 * y);
+    double w = j.w * (y2 * y);
+    if (CHK) w = self ? 0.0 : w;                     // excluded pair (self, or masked)
     fx = fma(w, dx, fx);
     fy = fma(w, dy, fy);
     fz = fma(w, dz, fz);
@@ -95,7 +98,8 @@ __device__ __forceinline__ void f64_grad_pair(const D4 j, const D4 aj, const F64
     if (CHK) r2 = self ? 1.0 : r2;
     const double y = rsqrt_f64(r2);
     const double y2 = y * y;
-    const double w = j.w * (y2 * y);
+    double w = j.w * (y2 * y);
+    if (CHK) w = self ? 0.0 : w;                     // excluded pair (self, or masked)
     const double bx = aj.x - p.ax, by = aj.y - p.ay, bz = aj.z - p.az;
     const double dot = fma(bx, dx, fma(by, dy, bz * dz));
     const double s = (w * y2) * (-3.0 * dot);

@@ -37,7 +37,7 @@ FSI_MIXED = 1
 EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params", "fsi_reserve",
             "fsi_last_error", "fsi_sync_status", "fsi_accel", "fsi_grad", "fsi_accel_grad",
             "fsi_pn_accel", "fsi_step", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
-            "fsi_level_stats", "fsi_hhs_interval_restart", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
+            "fsi_level_stats", "fsi_hhs_interval_restart", "fsi_step_sub", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall",
@@ -70,6 +70,7 @@ _lib.fsi_timesteps.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
 _lib.fsi_energy.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
 _lib.fsi_hhs_interval.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp]
 _lib.fsi_level_stats.argtypes = [_vp, C.POINTER(C.c_longlong), _ip]
+_lib.fsi_step_sub.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _ip, _vp]
 _lib.fsi_hhs_interval_restart.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _dp, _ip,
                                           C.POINTER(_ip), C.POINTER(_dp), _vp]
 _lib.fsi_profile.argtypes = [_vp, _ip]
@@ -284,6 +285,23 @@ def fsi_hhs_interval(ctx: Context, pos, vel, mass, tau: float, is_bh=None, strea
     if code not in (FSI_OK, FSI_ERR_MAXLEVEL):
         raise FsiError(code, "fsi_hhs_interval")
     return int(code)
+
+
+def fsi_step_sub(ctx: Context, pos, vel, mass, pairs, h: float, nsteps: int = 1, idx=None,
+                 stream=None) -> None:
+    """nsteps FSI cycles with binary subsystems (Algorithm 1), in place; pairs: int32
+    device tensor of shape (n_pairs, 2) holding global ids."""
+    N = mass.numel()
+    pi, n = _ids(idx, N, "idx")
+    if pairs is None or pairs.numel() == 0:
+        pp, npairs = None, 0
+    else:
+        if pairs.dtype != torch.int32 or not pairs.is_cuda or not pairs.is_contiguous():
+            raise TypeError("pairs must be a contiguous int32 CUDA tensor of shape (n_pairs, 2)")
+        pp, npairs = pairs.data_ptr(), pairs.numel() // 2
+    _check(_lib.fsi_step_sub(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                             _f64(mass, (N,), "mass"), pi, n, pp, int(npairs), float(h),
+                             int(nsteps), _stream(stream)), "fsi_step_sub")
 
 
 def fsi_hhs_interval_restart(ctx: Context, pos, vel, mass, tau: float, eta_restart: float,

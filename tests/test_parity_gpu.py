@@ -24,6 +24,7 @@ import torch
 
 import oracle
 from paper_2210_02472_b300 import inputs
+from tests import kepler
 
 pytestmark = pytest.mark.gpu
 
@@ -564,3 +565,67 @@ def test_full_size_mixed_grad_sampled_rows(F, big):
     scale = grad_scale(big.pos, big.mass, accg, rows, np.arange(big.n))
     e = np.abs(got[:, rows] - ref).max(axis=0) / scale
     assert e.max() <= 1e-5, e.max()
+
+
+# ----------------------------------------------------------------------------- subsystems
+def _cluster_with_binaries(n, seed, n_bin):
+    """A Plummer cluster in which particles 2s, 2s+1 (s < n_bin) are re-placed as bound
+    binaries (a = 1e-3 .. 5e-3, e up to 0.9, at apoapsis, random orientation) centred on
+    particle 2s with its velocity."""
+    c = inputs.plummer(n, seed, imf="kroupa")
+    rng = np.random.default_rng(seed + 1)
+    pos, vel = c.pos.copy(), c.vel.copy()
+    pairs = []
+    for s in range(n_bin):
+        i, j = 2 * s, 2 * s + 1
+        mi, mj = c.mass[i], c.mass[j]
+        bp, bv = kepler.binary(mi, mj, rng.uniform(1e-3, 5e-3), rng.uniform(0.0, 0.9))
+        R = rng.standard_normal((3, 3))
+        Q, _ = np.linalg.qr(R)
+        centre, cv = c.pos[:, i], c.vel[:, i]
+        pos[:, [i, j]] = centre[:, None] + Q @ bp
+        vel[:, [i, j]] = cv[:, None] + Q @ bv
+        pairs.append([i, j])
+    return pos, vel, c.mass, np.array(pairs, dtype=np.int32)
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("subset", [False, True])
+def test_fsi_step_with_binary_subsystems(F, prec, subset):
+    """Algorithm 1 through the C ABI against the oracle: 12 binaries in a 700-particle
+    cluster (masked one-sided passes, exact two-body subsystem flow), 4 cycles; on a subset
+    the other particles must not move."""
+    pos, vel, m, pairs = _cluster_with_binaries(700, 41, 12)
+    h = 2e-4
+    P = None
+    if subset:
+        rest = inputs.random_subset(700 - 24, 300, 42) + 24
+        P = np.sort(np.concatenate([np.arange(24), rest])).astype(np.int32)
+    rp, rv = oracle.fsi_step_sub(pos, vel, m, pairs, h, P=P, steps=4)
+    with F.Context(prec) as ctx:
+        p, v = dev(pos), dev(vel)
+        F.fsi_step_sub(ctx, p, v, dev(m), dev(pairs, torch.int32), h, nsteps=4, idx=ids(P))
+        p, v = host(p), host(v)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    if prec == "fp64":
+        assert np.abs(p - rp).max() <= 1e-13
+        assert np.abs(v - rv).max() <= 1e-11 * np.abs(rv).max()
+    else:
+        assert np.abs(p - rp).max() <= 1e-10
+        assert np.abs(v - rv).max() <= 1e-6 * np.abs(rv).max()
+    if subset:
+        others = np.setdiff1d(np.arange(700), P)
+        assert np.array_equal(p[:, others], pos[:, others])
+
+
+def test_fsi_step_sub_rejects_bad_binaries(F):
+    """A particle in two binaries is reported on the device; PN on is unsupported."""
+    pos, vel, m, pairs = _cluster_with_binaries(64, 43, 2)
+    bad = np.array([[0, 1], [1, 2]], dtype=np.int32)
+    with F.Context("fp64") as ctx:
+        p, v = dev(pos), dev(vel)
+        F.fsi_step_sub(ctx, p, v, dev(m), dev(bad, torch.int32), 1e-4)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_ARG
+    with F.Context("fp64", c=100.0) as ctx:
+        with pytest.raises(F.FsiError):
+            F.fsi_step_sub(ctx, dev(pos), dev(vel), dev(m), dev(pairs, torch.int32), 1e-4)
