@@ -24,7 +24,7 @@ def nvcc() -> str:
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> Path:
     srcs = [CSRC / s for s in SOURCES]
-    deps = srcs + [CSRC / "fsi_internal.cuh", CSRC / "pair_math.cuh", INCLUDE / "fsi.h"]
+    deps = srcs + [CSRC / "fsi_internal.cuh", CSRC / "pair_math.cuh", CSRC / "sym_x2.cuh", INCLUDE / "fsi.h"]
     if not force and LIB.exists() and all(LIB.stat().st_mtime >= d.stat().st_mtime for d in deps):
         return LIB
     objdir = PKG / "_build"

@@ -23,6 +23,7 @@
 
 #include "fsi_internal.cuh"
 #include "pair_math.cuh"
+#include "sym_x2.cuh"
 
 namespace fsi {
 
@@ -141,6 +142,10 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
             if constexpr (P == FSI_MIXED) {
                 MixI pi[I];
                 float f[I][3];
+                // I = 2: the two particles as one packed pair for the tiles without the
+                // self pair (fma.rn.f32x2 arithmetic, same rounding per half)
+                X2I pp;
+                float2 f2[3];
 #pragma unroll
                 for (int u = 0; u < I; ++u) {
                     const long long i = it.off + min(myl[u], it.n - 1);
@@ -153,7 +158,16 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
                         pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
                     }
                     f[u][0] = f[u][1] = f[u][2] = 0.f;
+                    if constexpr (I == 2) {
+                        set_half(pp.nxh, u, -pi[u].xh); set_half(pp.nyh, u, -pi[u].yh);
+                        set_half(pp.nzh, u, -pi[u].zh); set_half(pp.nxl, u, -pi[u].xl);
+                        set_half(pp.nyl, u, -pi[u].yl); set_half(pp.nzl, u, -pi[u].zl);
+                        set_half(pp.nax, u, -pi[u].ax); set_half(pp.nay, u, -pi[u].ay);
+                        set_half(pp.naz, u, -pi[u].az);
+                    }
                 }
+                f2[0] = f2[1] = f2[2] = make_float2(0.f, 0.f);
+                const float2 eps2x = bc2((float)a.eps2);
                 const float eps2f = (float)a.eps2;
                 for (int j0 = 0; j0 < it.n; j0 += kBatchTile) {
                     const int cnt = min(kBatchTile, it.n - j0);
@@ -168,7 +182,14 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
                     const RecMix* rec = reinterpret_cast<const RecMix*>(sm_rec);
                     const float4* arec = reinterpret_cast<const float4*>(sm_acc);
                     const bool chk = j0 < ib + kBatchThreads * I && j0 + cnt > ib;
-                    if (!chk) {
+                    if (!chk && I == 2) {
+                        if (!grad) {
+                            for (int jj = 0; jj < cnt; ++jj) x2_acc_one(rec[jj].hi, rec[jj].lo, pp, eps2x, f2);
+                        } else {
+                            for (int jj = 0; jj < cnt; ++jj)
+                                x2_grad_one(rec[jj].hi, rec[jj].lo, arec[jj], pp, eps2x, f2);
+                        }
+                    } else if (!chk) {
                         for (int jj = 0; jj < cnt; ++jj) {
                             const float4 hh = rec[jj].hi, ll = rec[jj].lo;
                             if (!grad) {
@@ -197,6 +218,14 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
                     for (int u = 0; u < I; ++u)
 #pragma unroll
                         for (int q = 0; q < 3; ++q) { acc64[u][q] += (double)f[u][q]; f[u][q] = 0.f; }
+                    if constexpr (I == 2) {
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            acc64[0][q] += (double)f2[q].x;
+                            acc64[1][q] += (double)f2[q].y;
+                            f2[q] = make_float2(0.f, 0.f);
+                        }
+                    }
                 }
             } else {
                 F64I pi[I];
@@ -297,6 +326,388 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
             atomicAdd(a.done + (size_t)it.cluster * a.nphase + p, 1);
         }
     }
+}
+
+// =================================================================================
+// Symmetric persistent ensemble kernel (mixed precision).  The same phase machinery as
+// batch_kernel, but every pair pass is split into
+//   a sum phase:   items (cluster, i-block of 1024 particles, source tiles [t0, t1));
+//                  off-diagonal tiles evaluate each unordered pair once with the packed
+//                  symmetric arithmetic (sym_x2.cuh: i-side in registers, source side by
+//                  the warp reduce-scatter), the block's own tiles one-sided with the self
+//                  pair excluded; both sides are added into the FP64 accumulator accum
+//                  (red.global.add);
+//   an apply phase: items (cluster, block): the pass's epilogue from accum, which it
+//                  clears for the next pass.
+// A sum item of a cluster waits for the previous apply (or pack) phase of that cluster,
+// an apply item for all sum items of its pass.  Source tiles stream through a 3-stage
+// shared-memory ring filled by cp.async.bulk on mbarriers whose phase parity follows a
+// running per-CTA tile count; every wait is bounded as in batch_kernel.
+namespace {
+constexpr int kBSNP = kBatchSymI / 2;                                // packed pairs per thread
+constexpr int kBSBlock = kBatchThreads * kBatchSymI;                 // particles per block
+constexpr int kBSStage = kBatchTile * (32 + 16);                     // record + accel record
+constexpr int kBSJpart = (kBatchThreads / 32) * kBatchTile * 3 * 4;
+constexpr int kBSAccS = kBSNP * 3 * kBatchThreads * 16;
+constexpr int kBSSmem = kStages * kBSStage + kBSJpart + kBSAccS;
+static_assert(kBatchTile == kTileJ && kBatchThreads == kThreads, "tile sizes of sym_x2.cuh");
+}  // namespace
+
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.global;" ::: "memory");
+}
+
+// Epilogue of one particle (global index i) of a pass with role 1..4 from its pair sum r3.
+template <int P>
+__device__ __forceinline__ void batch_apply(const BatchArgs& a, int role, bool last_acc, long long i,
+                                            const double (&r3)[3], void* rout) {
+    const long long N = a.ntot;
+    const double h = a.h;
+    if (!(isfinite(r3[0]) && isfinite(r3[1]) && isfinite(r3[2]))) set_error(a.err, FSI_ERR_NONFINITE);
+    if (role == 2) {
+        const double mi = a.m[i];
+#pragma unroll
+        for (int q = 0; q < 3; ++q) __stcg(a.ac + q * N + i, r3[q]);
+        if constexpr (P == FSI_MIXED)
+            __stcg(reinterpret_cast<float4*>(a.accrec) + i, make_float4((float)r3[0], (float)r3[1], (float)r3[2], (float)mi));
+        else {
+            double2* q = reinterpret_cast<double2*>(reinterpret_cast<D4*>(a.accrec) + i);
+            __stcg(q, make_double2(r3[0], r3[1]));
+            __stcg(q + 1, make_double2(r3[2], mi));
+        }
+        return;
+    }
+    double ck = 0.0, cd = 0.0;
+    if (role == 1) { ck = h / 6.0; cd = 0.5 * h; }
+    if (role == 3) { ck = 2.0 * h / 3.0; cd = 0.5 * h; }
+    if (role == 4) { ck = last_acc ? h / 6.0 : h / 3.0; cd = last_acc ? 0.0 : 0.5 * h; }
+    double xv[3], vv[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        double kq = r3[q];
+        if (role == 3) kq = fma(h * h / 24.0, r3[q], __ldcg(a.ac + q * N + i));
+        vv[q] = fma(ck, kq, __ldcg(a.v + q * N + i));
+        __stcg(a.v + q * N + i, vv[q]);
+        xv[q] = __ldcg(a.x + q * N + i);
+        if (cd != 0.0) {
+            xv[q] = fma(cd, vv[q], xv[q]);
+            __stcg(a.x + q * N + i, xv[q]);
+        }
+    }
+    if (cd != 0.0) {
+        const double mi = a.m[i];
+        if constexpr (P == FSI_MIXED) {
+            const RecMix r = make_mix_rec(xv[0], xv[1], xv[2], mi);
+            RecMix* o = reinterpret_cast<RecMix*>(rout) + i;
+            __stcg(&o->hi, r.hi);
+            __stcg(&o->lo, r.lo);
+        } else {
+            double2* o = reinterpret_cast<double2*>(reinterpret_cast<D4*>(rout) + i);
+            __stcg(o, make_double2(xv[0], xv[1]));
+            __stcg(o + 1, make_double2(xv[2], mi));
+        }
+    }
+}
+
+// One sum item: block `it.block` of cluster it.cluster against its source tiles [t0, t1).
+// g: the CTA's running tile count (advanced by the item's tiles).  Returns false if a wait
+// timed out (the caller leaves the kernel).
+template <int KIND>
+__device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const void* rin,
+                               double* __restrict__ accum, unsigned char* smem, uint64_t* bars,
+                               float* jpart, float4* acc_s, unsigned& g) {
+    constexpr int I = kBatchSymI, NP = kBSNP;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const long long N = a.ntot;
+    const RecMix* R = reinterpret_cast<const RecMix*>(rin) + it.off;
+    const float4* AR = reinterpret_cast<const float4*>(a.accrec) + it.off;
+    const bool diag = (it.t0 == it.block * I);
+    const int ntiles = it.t1 - it.t0;
+    auto issue = [&](int tl) {
+        const unsigned gg = g + (unsigned)tl;
+        const int st = (int)(gg % kStages);
+        const int jt = (it.t0 + tl) * kBatchTile;
+        const int cnt = min(kBatchTile, it.n - jt);
+        unsigned char* base = smem + st * kBSStage;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (32u + (KIND == KIND_GRAD ? 16u : 0u)));
+        bulk_g2s(base, R + jt, (uint32_t)cnt * 32u, &bars[st]);
+        if (KIND == KIND_GRAD) bulk_g2s(base + kBatchTile * 32, AR + jt, (uint32_t)cnt * 16u, &bars[st]);
+    };
+    if (tid == 0) {
+        fence_proxy_async();            // records written by generic stores of earlier phases
+        for (int tl = 0; tl < min(kStages, ntiles); ++tl) issue(tl);
+    }
+    // i-side state: warp w holds the 32 I consecutive particles i0 + 32 I w + 32 u + lane
+    const int ib = it.block * kBSBlock + warp * (32 * I) + lane;
+    X2I pp[NP];
+    float2 f[NP][3];
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        const bool valid = ib + 32 * u < it.n;
+        const int ic = min(ib + 32 * u, it.n - 1);
+        RecMix r;
+        r.hi = __ldcg(&R[ic].hi);
+        r.lo = __ldcg(&R[ic].lo);
+        float nm = 0.f, nax = 0.f, nay = 0.f, naz = 0.f;
+        if constexpr (KIND == KIND_GRAD) {
+            const float4 ai = __ldcg(AR + ic);
+            nax = -ai.x; nay = -ai.y; naz = -ai.z;
+            nm = valid ? -ai.w : 0.f;
+        }
+        const int h = u & 1;
+        X2I& q = pp[u >> 1];
+        set_half(q.nxh, h, -r.hi.x); set_half(q.nyh, h, -r.hi.y); set_half(q.nzh, h, -r.hi.z);
+        set_half(q.nxl, h, -r.lo.x); set_half(q.nyl, h, -r.lo.y); set_half(q.nzl, h, -r.lo.z);
+        set_half(q.nA, h, valid ? -r.hi.w : 0.f);
+        set_half(q.nB, h, valid ? -r.lo.w : 0.f);
+        set_half(q.nm, h, nm);
+        set_half(q.nax, h, nax); set_half(q.nay, h, nay); set_half(q.naz, h, naz);
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        f[p][0] = f[p][1] = f[p][2] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc_s[(p * 3 + q) * kBatchThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float eps2f = (float)a.eps2;
+    const float2 eps2 = bc2(eps2f);
+    bool ok_all = true;
+    int t_stop = ntiles;
+    for (int tl = 0; tl < ntiles; ++tl) {
+        const unsigned gg = g + (unsigned)tl;
+        const int st = (int)(gg % kStages);
+        const bool ok = mbar_wait_bounded(&bars[st], (gg / kStages) & 1u, a.timeout_ns, a.err);
+        const int jt = (it.t0 + tl) * kBatchTile;
+        const int cnt = min(kBatchTile, it.n - jt);
+        const unsigned char* base = smem + st * kBSStage;
+        const RecMix* rec = reinterpret_cast<const RecMix*>(base);
+        const float4* arec = reinterpret_cast<const float4*>(base + kBatchTile * 32);
+        if (diag) {
+            // the block's own tiles: one-sided (packed), self pair excluded by index
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 h = rec[jj].hi;
+                const float4 l = rec[jj].lo;
+                const int j = jt + jj;
+                if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        x2_acc_one_chk(h, l, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
+                } else {
+                    const float4 aj = arec[jj];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        x2_grad_one_chk(h, l, aj, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ff_add2(acc_s[(p * 3 + c) * kBatchThreads + tid], f[p][c]);
+                    f[p][c] = make_float2(0.f, 0.f);
+                }
+        } else {
+            float2 D0[NP][3];
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                const int jend = min(cnt, k0 + 32);
+                if (jend - k0 < 32) {
+                    for (int jj = k0; jj < jend; jj += 4)
+                        x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+                } else {
+                    for (int jj = k0; jj < jend; jj += 4)
+                        x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+                }
+            }
+#pragma unroll
+            for (int p = 0; p < NP; ++p)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    ff_add2(acc_s[(p * 3 + c) * kBatchThreads + tid], f[p][c]);
+                    f[p][c] = make_float2(0.f, 0.f);
+                }
+        }
+        if (__syncthreads_or(!ok)) { ok_all = false; t_stop = tl; break; }
+        if (!diag && tid < cnt) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float sum = 0.f;
+#pragma unroll
+                for (int w = 0; w < kBatchThreads / 32; ++w) sum += jpart[((size_t)w * kBatchTile + tid) * 3 + c];
+                red_add(accum + (size_t)c * N + it.off + jt + tid, (double)sum);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && tl + kStages < ntiles) issue(tl + kStages);
+    }
+    if (!ok_all) {
+        // let every copy still in flight land (bounded) before the CTA leaves
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int tl = t_stop; tl < issued; ++tl) {
+                const unsigned gg = g + (unsigned)tl;
+                mbar_wait_bounded(&bars[gg % kStages], (gg / kStages) & 1u, a.timeout_ns, nullptr);
+            }
+        }
+        __syncthreads();
+        return false;
+    }
+    g += (unsigned)ntiles;
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        if (ib + 32 * u >= it.n) continue;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float4 s = acc_s[((u >> 1) * 3 + c) * kBatchThreads + tid];
+            const double sum = (u & 1) ? (double)s.y + (double)s.w : (double)s.x + (double)s.z;
+            red_add(accum + (size_t)c * N + it.off + ib + 32 * u, sum);
+        }
+    }
+    return true;
+}
+
+__global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
+    const BatchArgs a, const BatchSymItem* __restrict__ sitems, int nS, const int* __restrict__ nsum,
+    double* __restrict__ accum) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ int s_item, s_flag;
+    float* jpart = reinterpret_cast<float*>(smem + kStages * kBSStage);
+    float4* acc_s = reinterpret_cast<float4*>(smem + kStages * kBSStage + kBSJpart);
+    const int tid = threadIdx.x;
+    const long long N = a.ntot;
+    const int nA = a.items_per_phase;
+    const int npass = 1 + 3 * a.nsteps;
+    const long long total = (long long)nA + (long long)npass * (long long)(nS + nA);
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    unsigned g = 0;
+    while (true) {
+        if (tid == 0) {
+            long long t = atomicAdd(a.next, 1);
+            if (t >= total || ld_acquire(a.abort_flag)) t = -1;
+            s_item = (int)t;
+        }
+        __syncthreads();
+        const int t = s_item;
+        __syncthreads();
+        if (t < 0) return;
+        int phase, pass = -1, r = t;
+        bool is_sum = false;
+        if (t >= nA) {
+            const int tt = t - nA;
+            pass = tt / (nS + nA);
+            r = tt % (nS + nA);
+            is_sum = r < nS;
+            if (!is_sum) r -= nS;
+            phase = 1 + 2 * pass + (is_sum ? 0 : 1);
+        } else {
+            phase = 0;
+        }
+        const int cluster = is_sum ? sitems[r].cluster : a.items[r].cluster;
+        if (phase > 0) {
+            // wait until the previous phase of this cluster is complete: a sum phase has
+            // odd index, the pack and apply phases even
+            if (tid == 0) {
+                const int* cnt = a.done + (size_t)cluster * a.nphase + (phase - 1);
+                const int need = ((phase - 1) & 1) ? nsum[cluster] : a.nblocks[cluster];
+                int flag = 0;
+                if (ld_acquire(cnt) < need) {
+                    const long long t0 = global_ns();
+                    while (ld_acquire(cnt) < need) {
+                        if (ld_acquire(a.abort_flag)) { flag = 1; break; }
+                        if (global_ns() - t0 > a.timeout_ns) {
+                            set_error(a.err, FSI_ERR_TIMEOUT);
+                            atomicExch(a.abort_flag, 1);
+                            flag = 1;
+                            break;
+                        }
+                        __nanosleep(64);
+                    }
+                }
+                __threadfence();
+                s_flag = flag;
+            }
+            __syncthreads();
+            if (s_flag) return;
+        }
+        const int role = phase == 0 ? 0 : (pass == 0 ? 1 : 2 + (pass - 1) % 3);
+        if (phase == 0) {
+            // pack the block's records from x
+            const BatchItem it = a.items[r];
+#pragma unroll
+            for (int u = 0; u < kBatchSymI; ++u) {
+                const int il = it.block * kBSBlock + u * kBatchThreads + tid;
+                if (il < it.n) {
+                    const long long i = it.off + il;
+                    const RecMix rr = make_mix_rec(a.x[i], a.x[N + i], a.x[2 * N + i], a.m[i]);
+                    RecMix* o = reinterpret_cast<RecMix*>(a.rec0) + i;
+                    __stcg(&o->hi, rr.hi);
+                    __stcg(&o->lo, rr.lo);
+                }
+            }
+        } else if (is_sum) {
+            const BatchSymItem it = sitems[r];
+            // roles 1 and 4 read rec0, 2 and 3 read rec1
+            const void* rin = (role == 1 || role == 4) ? a.rec0 : a.rec1;
+            const bool ok = role == 3
+                ? batch_sum_item<KIND_GRAD>(a, it, rin, accum, smem, bars, jpart, acc_s, g)
+                : batch_sum_item<KIND_ACC>(a, it, rin, accum, smem, bars, jpart, acc_s, g);
+            if (!ok) {
+                if (tid == 0) atomicExch(a.abort_flag, 1);
+                return;
+            }
+        } else {
+            const BatchItem it = a.items[r];
+            const bool last_acc = (role == 4) && (pass == npass - 1);
+            void* rout = (role == 3) ? a.rec0 : a.rec1;
+#pragma unroll
+            for (int u = 0; u < kBatchSymI; ++u) {
+                const int il = it.block * kBSBlock + u * kBatchThreads + tid;
+                if (il >= it.n) continue;
+                const long long i = it.off + il;
+                double r3[3];
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    r3[c] = __ldcg(accum + c * N + i);
+                    __stcg(accum + c * N + i, 0.0);
+                }
+                batch_apply<FSI_MIXED>(a, role, last_acc, i, r3, rout);
+            }
+        }
+        // signal completion of this item (release); the proxy fence orders this thread's
+        // generic stores before the bulk copies (async proxy) of later items
+        fence_proxy_async();
+        __syncthreads();
+        if (tid == 0) {
+            __threadfence();
+            atomicAdd(a.done + (size_t)cluster * a.nphase + phase, 1);
+        }
+    }
+}
+
+cudaError_t launch_batch_sym(int ctas, const BatchArgs& a, const BatchSymItem* sitems,
+                             int sitems_per_phase, const int* nsum, double* accum,
+                             cudaStream_t s) {
+    static bool attr = false;
+    if (!attr) {
+        cudaError_t e = cudaFuncSetAttribute(batch_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSSmem);
+        if (e != cudaSuccess) return e;
+        attr = true;
+    }
+    { batch_sym_kernel<<<ctas, kBatchThreads, kBSSmem, s>>>(a, sitems, sitems_per_phase, nsum, accum); note_launch(); }
+    return cudaGetLastError();
+}
+
+int batch_sym_max_ctas_per_sm() {
+    if (cudaFuncSetAttribute(batch_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSSmem) != cudaSuccess)
+        return 0;
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_sym_kernel, kBatchThreads, kBSSmem) != cudaSuccess)
+        return 0;
+    return nb;
 }
 
 cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, cudaStream_t s) {

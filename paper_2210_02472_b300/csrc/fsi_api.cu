@@ -636,9 +636,12 @@ struct fsi_batch {
     int ipt = 1;
     int ctas_per_sm = 2;
     int stall_cluster = -1;          // test hook (fsi_batch_inject_stall)
-    std::vector<int> nblocks_h[3];   // per ipt (index 1, 2)
-    Buf items[3], nblocks[3];
-    int items_per_phase[3] = {0, 0, 0};
+    // per particles-per-thread variant (index 1, 2: one-sided; kBatchSymI: symmetric)
+    std::vector<int> nblocks_h[kBatchSymI + 1];
+    Buf items[kBatchSymI + 1], nblocks[kBatchSymI + 1];
+    int items_per_phase[kBatchSymI + 1] = {};
+    Buf sitems, nsum, accum;         // symmetric form: sum items, sum items per cluster
+    int sitems_per_phase = 0;
     Buf rec0, rec1, accrec, ac, done, ctrl;
     std::vector<long long> off;
 };
@@ -1314,7 +1317,8 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
         return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
     });
     int rc = FSI_OK;
-    for (int ipt = 1; ipt <= 2 && rc == FSI_OK; ++ipt) {
+    for (int ipt : {1, 2, kBatchSymI}) {
+        if (rc != FSI_OK) break;
         const int bs = batch_block_size(ipt);
         std::vector<BatchItem> items;
         b->nblocks_h[ipt].assign(K, 0);
@@ -1332,7 +1336,39 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
              cudaMemcpy(b->nblocks[ipt].p, b->nblocks_h[ipt].data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
             rc = fail(FSI_ERR_CUDA, "batch plan upload failed");
     }
-    const int nphase = 2 + 3 * max_steps;
+    if (rc == FSI_OK && c->p.precision == FSI_MIXED) {
+        // symmetric form: per cluster (largest first) and block, the block's own tiles, then
+        // chunks of kBatchSymChunk source tiles above it
+        constexpr int kBatchSymChunk = 4;
+        const int bs = batch_block_size(kBatchSymI);
+        std::vector<BatchSymItem> sit;
+        std::vector<int> nsum(K, 0);
+        for (int k : order) {
+            const int n = (int)(offsets[k + 1] - offsets[k]);
+            const int ntj = (n + 255) / 256;
+            const int nb = (n + bs - 1) / bs;
+            for (int q = 0; q < nb; ++q) {
+                const int own0 = q * kBatchSymI, own1 = std::min((q + 1) * kBatchSymI, ntj);
+                sit.push_back(BatchSymItem{k, q, (int)offsets[k], n, own0, own1});
+                for (int t0 = own1; t0 < ntj; t0 += kBatchSymChunk)
+                    sit.push_back(BatchSymItem{k, q, (int)offsets[k], n, t0, std::min(t0 + kBatchSymChunk, ntj)});
+            }
+            int cnt = 0;
+            for (size_t z = 0; z < sit.size(); ++z) cnt += sit[z].cluster == k;
+            nsum[k] = cnt;
+        }
+        b->sitems_per_phase = (int)sit.size();
+        rc = ensure(b->sitems, sit.size() * sizeof(BatchSymItem));
+        if (rc == FSI_OK) rc = ensure(b->nsum, (size_t)K * sizeof(int));
+        if (rc == FSI_OK) rc = ensure(b->accum, 3 * (size_t)ntot * sizeof(double));
+        if (rc == FSI_OK &&
+            (cudaMemcpy(b->sitems.p, sit.data(), sit.size() * sizeof(BatchSymItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(b->nsum.p, nsum.data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+            rc = fail(FSI_ERR_CUDA, "batch plan upload failed");
+    }
+    // phases: one-sided form 2 + 3 S (pack, first pass, 3 per step); symmetric form
+    // 1 + 2 (1 + 3 S) (pack, then a sum and an apply phase per pass)
+    const int nphase = 3 + 6 * max_steps;
     if (rc == FSI_OK) rc = ensure(b->rec0, (size_t)ntot * 32);
     if (rc == FSI_OK) rc = ensure(b->rec1, (size_t)ntot * 32);
     if (rc == FSI_OK) rc = ensure(b->accrec, (size_t)ntot * 32);
@@ -1351,7 +1387,8 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
 int fsi_batch_destroy(fsi_batch* b) {
     if (!b) return FSI_OK;
     cudaDeviceSynchronize();
-    Buf* bufs[] = {&b->items[1], &b->items[2], &b->nblocks[1], &b->nblocks[2], &b->rec0, &b->rec1,
+    Buf* bufs[] = {&b->items[1], &b->items[2], &b->items[kBatchSymI], &b->nblocks[1], &b->nblocks[2],
+                   &b->nblocks[kBatchSymI], &b->sitems, &b->nsum, &b->accum, &b->rec0, &b->rec1,
                    &b->accrec, &b->ac, &b->done, &b->ctrl};
     for (Buf* x : bufs)
         if (x->p) cudaFree(x->p);
@@ -1361,8 +1398,12 @@ int fsi_batch_destroy(fsi_batch* b) {
 
 int fsi_batch_set_tuning(fsi_ctx* c, fsi_batch* b, int ipt, int ctas_per_sm) {
     if (!c || !b) return fail(FSI_ERR_ARG, "NULL argument");
-    if (ipt < 1 || ipt > 2) return fail(FSI_ERR_ARG, "batch particles-per-thread must be 1 or 2");
-    const int mx = std::max(1, batch_max_ctas_per_sm(c->p.precision, ipt));
+    if (ipt != 1 && ipt != 2 && ipt != kBatchSymI)
+        return fail(FSI_ERR_ARG, "batch variant must be 1, 2 (one-sided) or %d (symmetric)", kBatchSymI);
+    if (ipt == kBatchSymI && c->p.precision != FSI_MIXED)
+        return fail(FSI_ERR_ARG, "the symmetric batch form is mixed precision");
+    const int mx = std::max(1, ipt == kBatchSymI ? batch_sym_max_ctas_per_sm()
+                                                 : batch_max_ctas_per_sm(c->p.precision, ipt));
     if (ctas_per_sm <= 0 || ctas_per_sm > mx) ctas_per_sm = mx;
     b->ipt = ipt;
     b->ctas_per_sm = ctas_per_sm;
@@ -1390,8 +1431,10 @@ int fsi_batch_step(fsi_ctx* c, fsi_batch* b, double* pos, double* vel, const dou
     if (nsteps > b->max_steps) return fail(FSI_ERR_ARG, "nsteps %d exceeds the plan's max_steps %d", nsteps, b->max_steps);
     if (c->p.c > 0.0) return fail(FSI_ERR_UNSUPPORTED, "batched steps are Newtonian (PN off)");
     const cudaStream_t s = S(stream);
-    const int nphase = 2 + 3 * nsteps;
     const int ipt = b->ipt;
+    const bool sym = ipt == kBatchSymI;
+    if (sym && c->p.precision != FSI_MIXED) return fail(FSI_ERR_ARG, "the symmetric batch form is mixed precision");
+    const int nphase = sym ? 3 + 6 * nsteps : 2 + 3 * nsteps;
     CU(cudaMemsetAsync(b->done.p, 0, (size_t)b->K * nphase * sizeof(int), s));
     CU(cudaMemsetAsync(b->ctrl.p, 0, 64, s));
     int* nblocks = P<int>(b->nblocks[ipt]);
@@ -1423,7 +1466,13 @@ int fsi_batch_step(fsi_ctx* c, fsi_batch* b, double* pos, double* vel, const dou
     a.err = c->err_d;
     a.timeout_ns = budget(c);
     const int ctas = c->sm_count * b->ctas_per_sm;
-    CU(launch_batch(c->p.precision, ipt, ctas, a, s));
+    if (sym) {
+        CU(cudaMemsetAsync(b->accum.p, 0, 3 * (size_t)b->ntot * sizeof(double), s));
+        CU(launch_batch_sym(ctas, a, reinterpret_cast<const BatchSymItem*>(b->sitems.p),
+                            b->sitems_per_phase, P<int>(b->nsum), P<double>(b->accum), s));
+    } else {
+        CU(launch_batch(c->p.precision, ipt, ctas, a, s));
+    }
     if (b->stall_cluster >= 0) {
         const int k = b->stall_cluster;
         CU(cudaMemcpyAsync(nblocks + k, &b->nblocks_h[ipt][k], sizeof(int), cudaMemcpyHostToDevice, s));

@@ -156,6 +156,12 @@ struct BatchItem {
     int cluster, block, off, n;
 };
 
+// Symmetric form (mixed precision): a sum item is (cluster, i-block, source tiles
+// [t0, t1) of the cluster); t0 == block * I marks the block's own tiles (one-sided).
+struct BatchSymItem {
+    int cluster, block, off, n, t0, t1;
+};
+
 struct BatchArgs {
     const BatchItem* items;      // items_per_phase entries
     int items_per_phase;
@@ -315,6 +321,14 @@ cudaError_t launch_iota(int n, int* ids, cudaStream_t s);
 cudaError_t launch_hhs_small(int precision, const SmallArgs& a, cudaStream_t s);
 int small_max();
 cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, cudaStream_t s);
+// Symmetric persistent ensemble kernel (mixed precision): phases pack, then per pair pass
+// a sum phase (sitems, red.add into accum) and an apply phase (items: epilogue, accum
+// cleared).  nsum: sum items per cluster.
+cudaError_t launch_batch_sym(int ctas, const BatchArgs& a, const BatchSymItem* sitems,
+                             int sitems_per_phase, const int* nsum, double* accum,
+                             cudaStream_t s);
+constexpr int kBatchSymI = 4;      // particles per thread of the symmetric ensemble kernel
+int batch_sym_max_ctas_per_sm();
 int batch_block_size(int ipt);
 int batch_max_ctas_per_sm(int precision, int ipt);
 // Adjoint pair kernels (FP64): kind 0 = acceleration VJP (vec = cotangent u),

@@ -61,6 +61,131 @@ __device__ __forceinline__ void mix_grad_pair(const float4 h, const float4 l, co
     gz = fmaf(w, bz, fmaf(s, dz, gz));
 }
 
+// ---------------------------------------------------------------------------------
+// Packed FP32 pairs (add/mul/fma.rn.f32x2, sm_100 and later): two receivers per
+// instruction, each half rounding exactly as the scalar form above.
+__device__ __forceinline__ float2 bc2(float v) { return make_float2(v, v); }
+__device__ __forceinline__ void set_half(float2& d, int h, float v) {
+    if (h) d.y = v;
+    else d.x = v;
+}
+__device__ __forceinline__ float2 rsqrt2(float2 v) { return make_float2(rsqrt_hw(v.x), rsqrt_hw(v.y)); }
+
+// Float-float accumulation of two sums at once: (hi, lo) += v by the TwoSum of Knuth
+// (six FP32 operations, exact error term; s - a formed as fma(a, -1, s), one rounding),
+// acc = (hi_0, hi_1, lo_0, lo_1).  Keeps ~48 bits across source tiles without FP64
+// instructions (the B300 FP64 unit issues ~1/64 of the FP32 rate).
+__device__ __forceinline__ void ff_add2(float4& acc, const float2 v) {
+    const float2 m1 = bc2(-1.0f);
+    const float2 hi = make_float2(acc.x, acc.y);
+    const float2 s = __fadd2_rn(hi, v);
+    const float2 bb = __ffma2_rn(hi, m1, s);                  // s - hi
+    const float2 e1 = __ffma2_rn(__ffma2_rn(bb, m1, s), m1, hi);   // hi - (s - bb)
+    const float2 e2 = __ffma2_rn(bb, m1, v);                  // v - bb
+    const float2 lo = __fadd2_rn(make_float2(acc.z, acc.w), __fadd2_rn(e1, e2));
+    acc = make_float4(s.x, s.y, lo.x, lo.y);
+}
+
+// i-side state of a packed pair of particles (low half: particle 2p, high half: 2p+1).
+struct X2I {
+    float2 nxh, nyh, nzh, nxl, nyl, nzl;   // -xh, -yh, -zh, -xl, -yl, -zl
+    float2 nA, nB;                         // -2.5 m_i, +1.5 m_i (near acc j-side weight)
+    float2 nm;                             // -m_i
+    float2 nax, nay, naz;                  // gradient: -a_i
+};
+
+// hi/lo separation of a source from both particles of a pair.
+__device__ __forceinline__ void x2_sep_near(const float4 h, const float4 l, const X2I& p,
+                                            float2& dx, float2& dy, float2& dz) {
+    dx = __fadd2_rn(__fadd2_rn(bc2(h.x), p.nxh), __fadd2_rn(bc2(l.x), p.nxl));
+    dy = __fadd2_rn(__fadd2_rn(bc2(h.y), p.nyh), __fadd2_rn(bc2(l.y), p.nyl));
+    dz = __fadd2_rn(__fadd2_rn(bc2(h.z), p.nzh), __fadd2_rn(bc2(l.z), p.nzl));
+}
+
+// y = r^-1 (hardware), y2 = y^2, sres = r^2 y^2 (= 1 - e), y3 = y^3.
+__device__ __forceinline__ void x2_geom(float2 dx, float2 dy, float2 dz, float2 eps2, float2& y2,
+                                        float2& sres, float2& y3) {
+    const float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    const float2 y = rsqrt2(r2);
+    y2 = __fmul2_rn(y, y);
+    sres = __fmul2_rn(r2, y2);
+    y3 = __fmul2_rn(y2, y);
+}
+
+// One-sided packed terms of source j on both particles of a pair (the pair's particles
+// must differ from j): acceleration f += m_j r^-3 d and gradient g += m_j T(d)(a_j - a_i),
+// operation for operation mix_acc_pair / mix_grad_pair.
+__device__ __forceinline__ void x2_acc_one(const float4 h, const float4 l, const X2I& p, float2 eps2,
+                                           float2 (&f)[3]) {
+    float2 dx, dy, dz, y2, sres, y3;
+    x2_sep_near(h, l, p, dx, dy, dz);
+    x2_geom(dx, dy, dz, eps2, y2, sres, y3);
+    const float2 w = __fmul2_rn(y3, __ffma2_rn(sres, bc2(l.w), bc2(h.w)));    // m_j r^-3
+    f[0] = __ffma2_rn(w, dx, f[0]);
+    f[1] = __ffma2_rn(w, dy, f[1]);
+    f[2] = __ffma2_rn(w, dz, f[2]);
+}
+
+__device__ __forceinline__ void x2_grad_one(const float4 h, const float4 l, const float4 aj, const X2I& p,
+                                            float2 eps2, float2 (&g)[3]) {
+    float2 dx, dy, dz, y2, sres, y3;
+    x2_sep_near(h, l, p, dx, dy, dz);
+    x2_geom(dx, dy, dz, eps2, y2, sres, y3);
+    const float2 w = __fmul2_rn(y3, __ffma2_rn(sres, bc2(l.w), bc2(h.w)));    // m_j r^-3
+    const float2 bx = __fadd2_rn(bc2(aj.x), p.nax), by = __fadd2_rn(bc2(aj.y), p.nay),
+                 bz = __fadd2_rn(bc2(aj.z), p.naz);
+    const float2 dot = __ffma2_rn(bx, dx, __ffma2_rn(by, dy, __fmul2_rn(bz, dz)));
+    const float2 q = __fmul2_rn(__fmul2_rn(w, y2), __ffma2_rn(bc2(3.0f), sres, bc2(-6.0f)));
+    const float2 s = __fmul2_rn(q, dot);
+    g[0] = __ffma2_rn(w, bx, __ffma2_rn(s, dx, g[0]));
+    g[1] = __ffma2_rn(w, by, __ffma2_rn(s, dy, g[1]));
+    g[2] = __ffma2_rn(w, bz, __ffma2_rn(s, dz, g[2]));
+}
+
+// The same with a source that may be one of the pair's particles (self_lo / self_hi): as
+// in the checked scalar forms, r^2 is replaced by 1 and the weight by 0 for that half.
+__device__ __forceinline__ void x2_geom_chk(float2 dx, float2 dy, float2 dz, float2 eps2, bool self_lo,
+                                            bool self_hi, float2& y2, float2& sres, float2& y3) {
+    float2 r2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __ffma2_rn(dz, dz, eps2)));
+    r2.x = self_lo ? 1.0f : r2.x;
+    r2.y = self_hi ? 1.0f : r2.y;
+    const float2 y = rsqrt2(r2);
+    y2 = __fmul2_rn(y, y);
+    sres = __fmul2_rn(r2, y2);
+    y3 = __fmul2_rn(y2, y);
+}
+
+__device__ __forceinline__ void x2_acc_one_chk(const float4 h, const float4 l, const X2I& p, float2 eps2,
+                                               bool self_lo, bool self_hi, float2 (&f)[3]) {
+    float2 dx, dy, dz, y2, sres, y3;
+    x2_sep_near(h, l, p, dx, dy, dz);
+    x2_geom_chk(dx, dy, dz, eps2, self_lo, self_hi, y2, sres, y3);
+    float2 w = __fmul2_rn(y3, __ffma2_rn(sres, bc2(l.w), bc2(h.w)));          // m_j r^-3
+    w.x = self_lo ? 0.0f : w.x;
+    w.y = self_hi ? 0.0f : w.y;
+    f[0] = __ffma2_rn(w, dx, f[0]);
+    f[1] = __ffma2_rn(w, dy, f[1]);
+    f[2] = __ffma2_rn(w, dz, f[2]);
+}
+
+__device__ __forceinline__ void x2_grad_one_chk(const float4 h, const float4 l, const float4 aj, const X2I& p,
+                                                float2 eps2, bool self_lo, bool self_hi, float2 (&g)[3]) {
+    float2 dx, dy, dz, y2, sres, y3;
+    x2_sep_near(h, l, p, dx, dy, dz);
+    x2_geom_chk(dx, dy, dz, eps2, self_lo, self_hi, y2, sres, y3);
+    float2 w = __fmul2_rn(y3, __ffma2_rn(sres, bc2(l.w), bc2(h.w)));          // m_j r^-3
+    w.x = self_lo ? 0.0f : w.x;
+    w.y = self_hi ? 0.0f : w.y;
+    const float2 bx = __fadd2_rn(bc2(aj.x), p.nax), by = __fadd2_rn(bc2(aj.y), p.nay),
+                 bz = __fadd2_rn(bc2(aj.z), p.naz);
+    const float2 dot = __ffma2_rn(bx, dx, __ffma2_rn(by, dy, __fmul2_rn(bz, dz)));
+    const float2 q = __fmul2_rn(__fmul2_rn(w, y2), __ffma2_rn(bc2(3.0f), sres, bc2(-6.0f)));
+    const float2 s = __fmul2_rn(q, dot);
+    g[0] = __ffma2_rn(w, bx, __ffma2_rn(s, dx, g[0]));
+    g[1] = __ffma2_rn(w, by, __ffma2_rn(s, dy, g[1]));
+    g[2] = __ffma2_rn(w, bz, __ffma2_rn(s, dz, g[2]));
+}
+
 __device__ __forceinline__ double rsqrt_f64(double r2) {
     const double y0 = (double)rsqrt_hw(__double2float_rn(r2));
     const double t = r2 * y0;

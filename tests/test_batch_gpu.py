@@ -30,8 +30,11 @@ def ens():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("ipt", [1, 2])
+@pytest.mark.parametrize("ipt", [1, 2, 4])
 def test_batch_matches_oracle_per_cluster(F, ens, prec, ipt):
+    """ipt 1, 2: one-sided form; 4: symmetric form (mixed precision only)."""
+    if ipt == 4 and prec == "fp64":
+        pytest.skip("the symmetric batch form is mixed precision")
     cat, off = ens
     h, steps = 1e-3, 3
     rp, rv = cat.pos.copy(), cat.vel.copy()
@@ -51,11 +54,13 @@ def test_batch_matches_oracle_per_cluster(F, ens, prec, ipt):
     assert np.abs(v - rv).max() <= tol * 100 * np.abs(rv).max()
 
 
-def test_batch_graph_capture_replays(F, ens):
+@pytest.mark.parametrize("ipt", [1, 4])
+def test_batch_graph_capture_replays(F, ens, ipt):
     cat, off = ens
     h = 1e-3
     with F.Context("mixed") as ctx:
         b = F.Batch(ctx, off, max_steps=2)
+        F.fsi_batch_set_tuning(ctx, b, ipt)
         m = dev(cat.mass)
         p0, v0 = dev(cat.pos), dev(cat.vel)
         pe, ve = p0.clone(), v0.clone()
@@ -76,12 +81,14 @@ def test_batch_graph_capture_replays(F, ens):
         b.close()
 
 
-def test_batch_bounded_wait_times_out_cleanly(F, ens):
+@pytest.mark.parametrize("ipt", [1, 4])
+def test_batch_bounded_wait_times_out_cleanly(F, ens, ipt):
     """A cluster made to wait for a phase count that never comes: the launch returns with
     FSI_ERR_TIMEOUT latched, the context stays usable and the next step runs normally."""
     cat, off = ens
     with F.Context("mixed", timeout_ns=200_000_000) as ctx:
         b = F.Batch(ctx, off, max_steps=2)
+        F.fsi_batch_set_tuning(ctx, b, ipt)
         p, v, m = dev(cat.pos), dev(cat.vel), dev(cat.mass)
         F.fsi_batch_inject_stall(b, 3)
         F.fsi_batch_step(ctx, b, p, v, m, 1e-3, 1)
@@ -94,3 +101,24 @@ def test_batch_bounded_wait_times_out_cleanly(F, ens):
         sl = slice(off[3], off[4])
         assert np.abs(p.cpu().numpy()[:, sl] - rp[:, sl]).max() < 1e-9
         b.close()
+
+
+def test_batch_symmetric_form_larger_clusters(F):
+    """Clusters of 2000-5000 particles (2-5 blocks of 1024): the symmetric form's
+    off-diagonal source chunks and ragged tiles against the oracle stepping each cluster."""
+    cat, off = inputs.ensemble(5, 2000, 5000, 78)
+    h, steps = 1e-3, 2
+    rp, rv = cat.pos.copy(), cat.vel.copy()
+    for k in range(len(off) - 1):
+        P = np.arange(off[k], off[k + 1], dtype=np.int32)
+        rp, rv = oracle.fsi_step(rp, rv, cat.mass, h, P=P, steps=steps)
+    with F.Context("mixed") as ctx:
+        b = F.Batch(ctx, off, max_steps=2)
+        F.fsi_batch_set_tuning(ctx, b, 4)
+        p, v = dev(cat.pos), dev(cat.vel)
+        F.fsi_batch_step(ctx, b, p, v, dev(cat.mass), h, steps)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        p, v = p.cpu().numpy(), v.cpu().numpy()
+        b.close()
+    assert np.abs(p - rp).max() <= 1e-9 * np.abs(rp).max()
+    assert np.abs(v - rv).max() <= 1e-7 * np.abs(rv).max()
