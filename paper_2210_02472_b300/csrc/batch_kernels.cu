@@ -332,11 +332,11 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
 // Symmetric persistent ensemble kernel (mixed precision).  The same phase machinery as
 // batch_kernel, but every pair pass is split into
 //   a sum phase:   items (cluster, i-block of 1024 particles, source tiles [t0, t1));
-//                  off-diagonal tiles evaluate each unordered pair once with the packed
-//                  symmetric arithmetic (sym_x2.cuh: i-side in registers, source side by
-//                  the warp reduce-scatter), the block's own tiles one-sided with the self
-//                  pair excluded; both sides are added into the FP64 accumulator accum
-//                  (red.global.add);
+//                  every unordered pair is evaluated once with the packed symmetric
+//                  arithmetic (sym_x2.cuh: i-side in registers, source side by the warp
+//                  reduce-scatter), except the pairs inside one warp's 128 particles
+//                  (one-sided, self pair excluded); both sides are added into the FP64
+//                  accumulator accum (red.global.add);
 //   an apply phase: items (cluster, block): the pass's epilogue from accum, which it
 //                  clears for the next pass.
 // A sum item of a cluster waits for the previous apply (or pack) phase of that cluster,
@@ -483,20 +483,43 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
         const RecMix* rec = reinterpret_cast<const RecMix*>(base);
         const float4* arec = reinterpret_cast<const float4*>(base + kBatchTile * 32);
         if (diag) {
-            // the block's own tiles: one-sided (packed), self pair excluded by index
-            for (int jj = 0; jj < cnt; ++jj) {
-                const float4 h = rec[jj].hi;
-                const float4 l = rec[jj].lo;
-                const int j = jt + jj;
-                if constexpr (KIND == KIND_ACC) {
+            // the block's own tiles, each unordered pair once: warp w holds the block's
+            // 32-record sub-tiles 4w .. 4w+3; a sub-tile above that range is evaluated
+            // symmetrically, one inside it one-sided (self pair excluded by index), one
+            // below it not at all (its pairs with warp w come from the warp that holds it)
+            float2 D0[NP][3];
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                const int jend = min(cnt, k0 + 32);
+                const int sub = 8 * tl + (k0 >> 5);                // sub-tile within the block
+                if (sub > 4 * warp + 3) {
+                    if (jend - k0 < 32) {
+                        for (int jj = k0; jj < jend; jj += 4)
+                            x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+                    } else {
+                        for (int jj = k0; jj < jend; jj += 4)
+                            x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+                    }
+                    continue;
+                }
+                if (k0 + lane < jend) {
+                    float* dst = jpart + ((size_t)warp * kBatchTile + k0 + lane) * 3;
+                    dst[0] = dst[1] = dst[2] = 0.f;
+                }
+                if (sub < 4 * warp) continue;
+                for (int jj = k0; jj < jend; ++jj) {
+                    const float4 h = rec[jj].hi;
+                    const float4 l = rec[jj].lo;
+                    const int j = jt + jj;
+                    if constexpr (KIND == KIND_ACC) {
 #pragma unroll
-                    for (int p = 0; p < NP; ++p)
-                        x2_acc_one_chk(h, l, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
-                } else {
-                    const float4 aj = arec[jj];
+                        for (int p = 0; p < NP; ++p)
+                            x2_acc_one_chk(h, l, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
+                    } else {
+                        const float4 aj = arec[jj];
 #pragma unroll
-                    for (int p = 0; p < NP; ++p)
-                        x2_grad_one_chk(h, l, aj, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
+                        for (int p = 0; p < NP; ++p)
+                            x2_grad_one_chk(h, l, aj, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
+                    }
                 }
             }
 #pragma unroll
@@ -527,7 +550,7 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
                 }
         }
         if (__syncthreads_or(!ok)) { ok_all = false; t_stop = tl; break; }
-        if (!diag && tid < cnt) {
+        if (tid < cnt) {
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float sum = 0.f;
