@@ -693,6 +693,12 @@ __global__ void pack_vel_kernel(int n, const double* __restrict__ vc, const doub
     if (k < n) out[k] = make_float4((float)vc[k], (float)vc[(size_t)n + k], (float)vc[2 * (size_t)n + k], (float)mc[k]);
 }
 
+cudaError_t launch_pack_vel(int n, const double* vc, const double* mc, void* vrec, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, reinterpret_cast<float4*>(vrec)); note_launch(); }
+    return cudaGetLastError();
+}
+
 cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
                                    double eta_ff, double eta_fb, double eta_jerk, double eps2,
                                    void* rec_ws, void* vrec_ws, double* step, int* err,

@@ -65,6 +65,9 @@ struct Buf {
 
 // Set-size classes of the symmetric variant table: the fastest kernel differs between
 // small sets (latency-bound, few CTAs: fewest particles per thread wins) and large ones.
+// One-sided passes with at least this many receivers (mixed: the packed form) form the
+// second class of the one-sided variant table.
+constexpr int kOneSidedLarge = 16384;
 constexpr int kSymClasses = 3;
 constexpr int kSymClassMin[kSymClasses] = {0, 32768, 196608};
 inline int sym_class(int n) { return n >= kSymClassMin[2] ? 2 : (n >= kSymClassMin[1] ? 1 : 0); }
@@ -78,14 +81,16 @@ struct fsi_ctx {
     int* counts_h = nullptr;       // pinned, 3 ints (HHS partition)
     Buf rec[2], accrec[2], xc, vc, ac, ad, gA, gB, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
         nbh, apn, pnpart, epart, iota, steps, step0, counts, accum, eout, snapx, snapv,
-        subwhere, subkey, subppos;
+        subwhere, subkey, subppos, stpart;
     std::vector<Buf> lvS, lvF;
     Buf vj[24];                     // adjoint work arrays
     Buf dstats;                     // device HHS stats: level counts (64), work (2), flags
     std::vector<long long> level_counts;
     int max_level_used = 0;
     int max_level_hit = 0;
-    int ipt[2][2] = {{2, 2}, {4, 2}};   // [precision][kind] one-sided kernel variant (pair_variants)
+    // [precision][kind][receivers >= kOneSidedLarge] one-sided kernel variant (pair_variants):
+    // mixed sets of many receivers take the packed FP32x2 form
+    int ipt[2][2][2] = {{{2, 2}, {2, 2}}, {{4, 36}, {2, 36}}};
     // [precision][kind][size class] symmetric kernel variant (sym_variants)
     int symv[2][2][kSymClasses] = {{{2, 2, 2}, {2, 2, 2}}, {{2, 228, 230}, {2, 228, 246}}};
     long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
@@ -268,7 +273,7 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
     if (a.n_i <= 0) return FSI_OK;
     c->work_pairs[kind] += (long long)a.n_i * (long long)a.n_j;
     const int prec = c->p.precision;
-    const int ipt = c->ipt[prec][kind];
+    const int ipt = c->ipt[prec][kind][a.n_i >= kOneSidedLarge];
     if (c->p.symmetric && a.check == CHECK_DIAG && a.irec == a.jrec && a.n_i == a.n_j &&
         a.iacc == a.jacc) {
         // self-interaction of one set: every unordered pair once, then the epilogue
@@ -528,8 +533,11 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     if (c->p.precision == FSI_MIXED) {
         CK(ensure(c->rec[1], pad_tile(n) * 32));
         CK(ensure(c->accrec[1], pad_tile(n) * 32));
-        CU(launch_timesteps_mixed(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2,
-                                  c->rec[1].p, c->accrec[1].p, step, c->err_d, s));
+        CK(ensure(c->stpart, steps_x2_part_bytes(n, c->sm_count)));
+        CU(launch_pack(FSI_MIXED, n, xc, mc, nullptr, n, c->rec[1].p, nullptr, s));
+        CU(launch_pack_vel(n, vc, mc, c->accrec[1].p, s));
+        CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
+                           c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c), c->sm_count, s));
     }
     else
         CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
@@ -705,7 +713,7 @@ int fsi_destroy(fsi_ctx* c) {
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
                    &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
                    &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
-                   &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos};
+                   &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos, &c->stpart};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -1589,7 +1597,10 @@ int fsi_autotune(fsi_ctx* c, int N, const double* pos, const double* mass, int n
     c->profiling = false;
     int rc = FSI_OK;
     if (!c->p.symmetric) {
-        rc = tune_set(c, N, pos, mass, n, reps, s, [&](int kind) -> int& { return c->ipt[prec][kind]; });
+        rc = tune_set(c, N, pos, mass, n, reps, s,
+                      [&](int kind) -> int& { return c->ipt[prec][kind][n >= kOneSidedLarge]; });
+        for (int kind = 0; kind < 2; ++kind)      // the sampled size stands for both classes
+            c->ipt[prec][kind][n < kOneSidedLarge] = c->ipt[prec][kind][n >= kOneSidedLarge];
     } else {
         // one sample per size class that n reaches: 8192 (or n), 65536 (or n), n
         for (int k = 0; k < kSymClasses && rc == FSI_OK; ++k) {
@@ -1610,8 +1621,8 @@ int fsi_get_tuning(fsi_ctx* c, int* ipt_acc, int* ipt_grad) {
     if (!c) return fail(FSI_ERR_ARG, "NULL context");
     const int prec = c->p.precision;
     const int k = kSymClasses - 1;
-    if (ipt_acc) *ipt_acc = c->p.symmetric ? c->symv[prec][KIND_ACC][k] : c->ipt[prec][KIND_ACC];
-    if (ipt_grad) *ipt_grad = c->p.symmetric ? c->symv[prec][KIND_GRAD][k] : c->ipt[prec][KIND_GRAD];
+    if (ipt_acc) *ipt_acc = c->p.symmetric ? c->symv[prec][KIND_ACC][k] : c->ipt[prec][KIND_ACC][1];
+    if (ipt_grad) *ipt_grad = c->p.symmetric ? c->symv[prec][KIND_GRAD][k] : c->ipt[prec][KIND_GRAD][1];
     return FSI_OK;
 }
 
@@ -1620,8 +1631,9 @@ int fsi_get_tuning_for(fsi_ctx* c, int n, int* ipt_acc, int* ipt_grad) {
     if (n < 0) return fail(FSI_ERR_ARG, "negative set size");
     const int prec = c->p.precision;
     const int k = sym_class(n);
-    if (ipt_acc) *ipt_acc = c->p.symmetric ? c->symv[prec][KIND_ACC][k] : c->ipt[prec][KIND_ACC];
-    if (ipt_grad) *ipt_grad = c->p.symmetric ? c->symv[prec][KIND_GRAD][k] : c->ipt[prec][KIND_GRAD];
+    const int big = n >= kOneSidedLarge;
+    if (ipt_acc) *ipt_acc = c->p.symmetric ? c->symv[prec][KIND_ACC][k] : c->ipt[prec][KIND_ACC][big];
+    if (ipt_grad) *ipt_grad = c->p.symmetric ? c->symv[prec][KIND_GRAD][k] : c->ipt[prec][KIND_GRAD][big];
     return FSI_OK;
 }
 
@@ -1642,8 +1654,10 @@ int fsi_set_tuning(fsi_ctx* c, int ipt_acc, int ipt_grad) {
             c->symv[prec][KIND_GRAD][k] = ipt_grad;
         }
     } else {
-        c->ipt[prec][KIND_ACC] = ipt_acc;
-        c->ipt[prec][KIND_GRAD] = ipt_grad;
+        for (int b = 0; b < 2; ++b) {
+            c->ipt[prec][KIND_ACC][b] = ipt_acc;
+            c->ipt[prec][KIND_GRAD][b] = ipt_grad;
+        }
     }
     return FSI_OK;
 }

@@ -309,6 +309,13 @@ cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const do
 // velocities vc, accelerations a and force-gradient sums G (all 3 x n).
 cudaError_t launch_grad_steps(int n, const double* vc, const double* a, const double* G,
                               double eta_grad, double eta_va, double* step, cudaStream_t s);
+// FP32 velocity records (vx, vy, vz, m) of a compact set.
+cudaError_t launch_pack_vel(int n, const double* vc, const double* mc, void* vrec, cudaStream_t s);
+// Mixed time steps with packed FP32 pairs (steps_x2.cu); part: steps_x2_part_bytes bytes.
+size_t steps_x2_part_bytes(int n, int sm_count);
+cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
+                            double eta_fb, double eta_jerk, float* part, double* step, int* err,
+                            long long timeout_ns, int sm_count, cudaStream_t s);
 cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
                                    double eta_ff, double eta_fb, double eta_jerk, double eps2,
                                    void* rec_ws, void* vrec_ws, double* step, int* err,

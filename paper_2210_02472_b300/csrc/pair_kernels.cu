@@ -103,9 +103,10 @@ constexpr int kRec = 32;
 
 __host__ __device__ constexpr int stage_bytes(int accrec) { return kTileJ * (kRec + accrec + 4); }
 
-// P: precision; KIND: acc or grad; I: active particles per thread; FF (mixed only): the
+// P: precision; KIND: acc or grad; I: active particles per thread; FF (mixed only): 1 = the
 // per-tile FP32 partial sums are accumulated as float-float pairs by TwoSum (FP32 pipe)
-// instead of FP64 additions (FP64 pipe, 1/64 of the FP32 rate on B300).
+// instead of FP64 additions (FP64 pipe, 1/64 of the FP32 rate on B300); 2 = the tiles
+// without the self pair run packed FP32x2 arithmetic on pairs of active particles (I even).
 template <int P, int KIND, int I, int FF>
 __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const PairArgs a) {
     constexpr int ACCREC = Cfg<P, KIND>::ACCREC;
@@ -159,6 +160,9 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
         MixI pi[I];
         float f[I][3];
         float hi[I][3], lo[I][3];   // float-float running sums (FF variant)
+        constexpr int NP = (FF == 2) ? I / 2 : 1;
+        X2I pp[NP];                 // packed pairs of active particles (FF == 2)
+        float2 f2[NP][3];
 #pragma unroll
         for (int u = 0; u < I; ++u) {
             const int i = min(i0 + u * kThreads + tid, max(a.n_i - 1, 0));
@@ -174,7 +178,17 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
             f[u][0] = f[u][1] = f[u][2] = 0.f;
 #pragma unroll
             for (int q = 0; q < 3; ++q) hi[u][q] = lo[u][q] = 0.f;
+            if constexpr (FF == 2) {
+                X2I& q = pp[u >> 1];
+                const int h = u & 1;
+                set_half(q.nxh, h, -pi[u].xh); set_half(q.nyh, h, -pi[u].yh); set_half(q.nzh, h, -pi[u].zh);
+                set_half(q.nxl, h, -pi[u].xl); set_half(q.nyl, h, -pi[u].yl); set_half(q.nzl, h, -pi[u].zl);
+                set_half(q.nax, h, -pi[u].ax); set_half(q.nay, h, -pi[u].ay); set_half(q.naz, h, -pi[u].az);
+            }
         }
+#pragma unroll
+        for (int p = 0; p < NP; ++p) f2[p][0] = f2[p][1] = f2[p][2] = make_float2(0.f, 0.f);
+        const float2 eps2x = bc2((float)a.eps2);
         const float eps2f = (float)a.eps2;
         for (int t = 0; t < ntiles; ++t) {
             const int s = t % kStages;
@@ -186,7 +200,18 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
             const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
             const int* jidt = reinterpret_cast<const int*>(base + kTileJ * (kRec + ACCREC));
             const bool chk = use_ids || (a.check == CHECK_DIAG && jt < i0 + kThreads * I && jt + cnt > i0);
-            if (!chk) {
+            if (FF == 2 && !chk) {
+                for (int jj = 0; jj < cnt; ++jj) {
+                    if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) x2_acc_one(rec[jj].hi, rec[jj].lo, pp[p], eps2x, f2[p]);
+                    } else {
+                        const float4 aj = arec[jj];
+#pragma unroll
+                        for (int p = 0; p < NP; ++p) x2_grad_one(rec[jj].hi, rec[jj].lo, aj, pp[p], eps2x, f2[p]);
+                    }
+                }
+            } else if (!chk) {
 #pragma unroll 2
                 for (int jj = 0; jj < cnt; ++jj) {
                     const float4 h = rec[jj].hi;
@@ -219,11 +244,21 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
                     }
                 }
             }
+            if constexpr (FF == 2) {
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        f[2 * p][q] += f2[p][q].x;
+                        f[2 * p + 1][q] += f2[p][q].y;
+                        f2[p][q] = make_float2(0.f, 0.f);
+                    }
+            }
 #pragma unroll
             for (int u = 0; u < I; ++u) {
 #pragma unroll
                 for (int q = 0; q < 3; ++q) {
-                    if constexpr (FF) {
+                    if constexpr (FF == 1) {
                         // error-free transformation (Knuth's TwoSum): hi + f = s + e exactly
                         const float sum = hi[u][q] + f[u][q];
                         const float bb = sum - hi[u][q];
@@ -239,7 +274,7 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
             if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
             if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
         }
-        if constexpr (FF) {
+        if constexpr (FF == 1) {
 #pragma unroll
             for (int u = 0; u < I; ++u)
 #pragma unroll
@@ -1490,6 +1525,9 @@ static cudaError_t launch_variant(int v, const PairArgs& a, int split, cudaStrea
         case 16 + 2: return launch_one<P, KIND, 2, 1>(a, split, s);
         case 16 + 3: return launch_one<P, KIND, 3, 1>(a, split, s);
         case 16 + 4: return launch_one<P, KIND, 4, 1>(a, split, s);
+        case 32 + 4:
+            if constexpr (P == FSI_MIXED) return launch_one<P, KIND, 4, 2>(a, split, s);
+            else return cudaErrorInvalidValue;
         default: return cudaErrorInvalidValue;
     }
 }
@@ -1500,6 +1538,7 @@ int pair_variants(int precision, int kind, int* out) {
     if (precision == FSI_MIXED) {
         for (int ipt = 2; ipt <= 4; ++ipt) out[n++] = ipt;
         for (int ipt = 2; ipt <= 4; ++ipt) out[n++] = 16 + ipt;
+        out[n++] = 32 + 4;      // packed FP32x2 (two pairs of active particles per thread)
     } else {
         out[n++] = 1; out[n++] = 2; out[n++] = 3;
     }

@@ -1,0 +1,290 @@
+// steps_x2.cu -- time steps of a set against itself (Sect. 3.4) in the mixed precision,
+// with packed FP32 pairs (add/mul/fma.rn.f32x2).
+//
+// For receiver i over every other member j of the set (d = x_j - x_i, u = v_j - v_i):
+//   free fall  eps_ff = eta_ff min_j (r^3 / (m_i + m_j))^{1/2},  r = |d| (unsoftened),
+//   fly-by     eps_fb = eta_fb min_j r / |u|,
+//   jerk       eps_j  = eta_jerk |a_i| / |j_i|,  a_i and j_i with the softened kernel,
+// eps_i the minimum of the three (no partner: +inf; |u| = 0 and |j| = 0 give no bound).
+// The minima are tracked as r^3 / (m_i + m_j) and r^2 / |u|^2 with the hardware reciprocal;
+// a and j accumulate in FP32 (only the ratio |a| / |j| is needed).
+//
+// Work decomposition: CTAs of 256 threads hold 4 receivers per thread (two packed pairs);
+// sources stream through a 3-stage shared-memory ring of 256 records (position record
+// 32 B + velocity record 16 B) filled by cp.async.bulk on mbarriers with bounded waits.
+// When the receiver blocks alone cannot fill the GPU, blockIdx.y splits the sources and a
+// finalize kernel combines the per-split minima and sums.
+#include <algorithm>
+
+#include "fsi_internal.cuh"
+#include "pair_math.cuh"
+
+namespace fsi {
+
+namespace {
+constexpr int kStI = 4;                          // receivers per thread
+constexpr int kStNP = kStI / 2;
+constexpr int kStThreads = 256;
+constexpr int kStTile = 256;                     // sources per stage
+constexpr int kStStage = kStTile * (32 + 16);
+constexpr int kStSmem = kStages * kStStage;
+constexpr int kStPart = 8;                       // ff, fb, ax, ay, az, jx, jy, jz
+}  // namespace
+
+__device__ __forceinline__ float2 rcp2(float2 v) {
+    float2 r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(v.x));
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(v.y));
+    return r;
+}
+
+struct StepX2I {
+    float2 nxh, nyh, nzh, nxl, nyl, nzl;   // -position splits of the two receivers
+    float2 nu, nv, nw;                     // -velocities
+    float2 m;                              // masses
+};
+
+struct StepX2Acc {
+    float2 ff, fb, ax, ay, az, jx, jy, jz;
+};
+
+// Source j (position record h/l, velocity record vj = (vx, vy, vz, m)) on both receivers
+// of a pair.  CHK: the source may be one of them (self_lo / self_hi), which is skipped.
+template <bool CHK, bool SOFT>
+__device__ __forceinline__ void step_pair_x2(const float4 h, const float4 l, const float4 vj,
+                                             const StepX2I& p, float2 eps2, bool self_lo,
+                                             bool self_hi, StepX2Acc& s, bool& coincident) {
+    const float2 dx = __fadd2_rn(__fadd2_rn(bc2(h.x), p.nxh), __fadd2_rn(bc2(l.x), p.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(bc2(h.y), p.nyh), __fadd2_rn(bc2(l.y), p.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(bc2(h.z), p.nzh), __fadd2_rn(bc2(l.z), p.nzl));
+    float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    if (CHK) {
+        d2.x = self_lo ? 1.0f : d2.x;
+        d2.y = self_hi ? 1.0f : d2.y;
+    }
+    coincident |= (d2.x == 0.0f) | (d2.y == 0.0f);
+    const float2 ux = __fadd2_rn(bc2(vj.x), p.nu), uy = __fadd2_rn(bc2(vj.y), p.nv),
+                 uz = __fadd2_rn(bc2(vj.z), p.nw);
+    const float2 u2 = __ffma2_rn(ux, ux, __ffma2_rn(uy, uy, __fmul2_rn(uz, uz)));
+    const float2 s2 = SOFT ? __fadd2_rn(d2, eps2) : d2;
+    float2 y = rsqrt2(s2);
+    // one Newton step of the hardware reciprocal square root: y (3 - s2 y^2) / 2
+    y = __fmul2_rn(y, __ffma2_rn(__fmul2_rn(s2, bc2(-0.5f)), __fmul2_rn(y, y), bc2(1.5f)));
+    const float2 y2 = __fmul2_rn(y, y);
+    float2 w = __fmul2_rn(bc2(vj.w), __fmul2_rn(y2, y));                   // m_j / s^3
+    const float2 r = __fmul2_rn(d2, SOFT ? rsqrt2(d2) : y);               // |d|
+    float2 tff = __fmul2_rn(__fmul2_rn(d2, r), rcp2(__fadd2_rn(bc2(vj.w), p.m)));
+    float2 tfb = __fmul2_rn(d2, rcp2(u2));
+    if (CHK) {
+        tff.x = self_lo ? INFINITY : tff.x; tff.y = self_hi ? INFINITY : tff.y;
+        tfb.x = self_lo ? INFINITY : tfb.x; tfb.y = self_hi ? INFINITY : tfb.y;
+        w.x = self_lo ? 0.0f : w.x;
+        w.y = self_hi ? 0.0f : w.y;
+    }
+    s.ff.x = fminf(s.ff.x, tff.x); s.ff.y = fminf(s.ff.y, tff.y);
+    s.fb.x = fminf(s.fb.x, tfb.x); s.fb.y = fminf(s.fb.y, tfb.y);
+    const float2 rv = __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz)));
+    const float2 c3 = __fmul2_rn(__fmul2_rn(rv, y2), bc2(-3.0f));
+    s.ax = __ffma2_rn(w, dx, s.ax); s.ay = __ffma2_rn(w, dy, s.ay); s.az = __ffma2_rn(w, dz, s.az);
+    s.jx = __ffma2_rn(w, __ffma2_rn(c3, dx, ux), s.jx);
+    s.jy = __ffma2_rn(w, __ffma2_rn(c3, dy, uy), s.jy);
+    s.jz = __ffma2_rn(w, __ffma2_rn(c3, dz, uz), s.jz);
+}
+
+__device__ __forceinline__ double step_from(float ff, float fb, float ax, float ay, float az,
+                                            float jx, float jy, float jz, double eta_ff,
+                                            double eta_fb, double eta_jerk) {
+    double e = INFINITY;
+    if (isfinite(ff)) e = eta_ff * sqrt((double)ff);
+    if (isfinite(fb)) e = fmin(e, eta_fb * sqrt((double)fb));
+    const double jn = sqrt((double)jx * jx + (double)jy * jy + (double)jz * jz);
+    if (jn > 0.0) e = fmin(e, eta_jerk * sqrt((double)ax * ax + (double)ay * ay + (double)az * az) / jn);
+    return e;
+}
+
+struct StepX2Args {
+    int n;
+    const RecMix* rec;
+    const float4* vrec;
+    float eps2;
+    double eta_ff, eta_fb, eta_jerk;
+    int j_per_split;
+    float* part;            // split > 1: [split][kStPart][n]
+    double* step;
+    int* err;
+    long long timeout_ns;
+};
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kStThreads, 2) steps_x2_kernel(const StepX2Args a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    const int tid = threadIdx.x;
+    const int i0 = blockIdx.x * (kStThreads * kStI);
+    const int js = blockIdx.y * a.j_per_split;
+    const int je = min(a.n, js + a.j_per_split);
+    const int ntiles = max(0, (je - js + kStTile - 1) / kStTile);
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int st = t % kStages;
+        const int jt = js + t * kStTile;
+        const int cnt = min(kStTile, je - jt);
+        unsigned char* base = smem + st * kStStage;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * 48u);
+        bulk_g2s(base, a.rec + jt, (uint32_t)cnt * 32u, &bars[st]);
+        bulk_g2s(base + kStTile * 32, a.vrec + jt, (uint32_t)cnt * 16u, &bars[st]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+    // receivers: i0 + u * 256 + tid, u = 0..3; pair p holds u = 2p (low) and 2p + 1 (high)
+    StepX2I pp[kStNP];
+    StepX2Acc acc[kStNP];
+    // lanes past the end hold a copy of particle n - 1 and use its index for the self test
+    int me[kStI];
+#pragma unroll
+    for (int u = 0; u < kStI; ++u) {
+        const int i = min(i0 + u * kStThreads + tid, a.n - 1);
+        me[u] = i;
+        const RecMix r = a.rec[i];
+        const float4 v = a.vrec[i];
+        const int h = u & 1;
+        StepX2I& q = pp[u >> 1];
+        set_half(q.nxh, h, -r.hi.x); set_half(q.nyh, h, -r.hi.y); set_half(q.nzh, h, -r.hi.z);
+        set_half(q.nxl, h, -r.lo.x); set_half(q.nyl, h, -r.lo.y); set_half(q.nzl, h, -r.lo.z);
+        set_half(q.nu, h, -v.x); set_half(q.nv, h, -v.y); set_half(q.nw, h, -v.z);
+        set_half(q.m, h, v.w);
+    }
+#pragma unroll
+    for (int p = 0; p < kStNP; ++p) {
+        acc[p].ff = acc[p].fb = bc2(INFINITY);
+        acc[p].ax = acc[p].ay = acc[p].az = acc[p].jx = acc[p].jy = acc[p].jz = bc2(0.0f);
+    }
+    const float2 eps2 = bc2(a.eps2);
+    bool coincident = false, aborted = false;
+    int t_stop = ntiles;
+    for (int t = 0; t < ntiles; ++t) {
+        const int st = t % kStages;
+        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+        const int jt = js + t * kStTile;
+        const int cnt = min(kStTile, je - jt);
+        const unsigned char* base = smem + st * kStStage;
+        const RecMix* rec = reinterpret_cast<const RecMix*>(base);
+        const float4* vr = reinterpret_cast<const float4*>(base + kStTile * 32);
+        const bool chk = jt < i0 + kStThreads * kStI && jt + cnt > i0;
+        if (!chk) {
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 h = rec[jj].hi, l = rec[jj].lo, v = vr[jj];
+#pragma unroll
+                for (int p = 0; p < kStNP; ++p)
+                    step_pair_x2<false, SOFT>(h, l, v, pp[p], eps2, false, false, acc[p], coincident);
+            }
+        } else {
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 h = rec[jj].hi, l = rec[jj].lo, v = vr[jj];
+                const int j = jt + jj;
+#pragma unroll
+                for (int p = 0; p < kStNP; ++p)
+                    step_pair_x2<true, SOFT>(h, l, v, pp[p], eps2, j == me[2 * p], j == me[2 * p + 1],
+                                             acc[p], coincident);
+            }
+        }
+        if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+        if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+    }
+    if (aborted) {
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int t = t_stop; t < issued; ++t)
+                mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1), a.timeout_ns, nullptr);
+        }
+        __syncthreads();
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < kStI; ++u) {
+        const int i = i0 + u * kStThreads + tid;
+        if (i >= a.n) continue;
+        if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
+        const StepX2Acc& s = acc[u >> 1];
+        const bool hi = (u & 1) != 0;
+        const float v[kStPart] = {hi ? s.ff.y : s.ff.x, hi ? s.fb.y : s.fb.x, hi ? s.ax.y : s.ax.x,
+                                  hi ? s.ay.y : s.ay.x, hi ? s.az.y : s.az.x, hi ? s.jx.y : s.jx.x,
+                                  hi ? s.jy.y : s.jy.x, hi ? s.jz.y : s.jz.x};
+        if (gridDim.y > 1) {
+#pragma unroll
+            for (int k = 0; k < kStPart; ++k) a.part[((size_t)blockIdx.y * kStPart + k) * a.n + i] = v[k];
+        } else {
+            if (!(isfinite(v[2]) && isfinite(v[3]) && isfinite(v[4]))) set_error(a.err, FSI_ERR_NONFINITE);
+            a.step[i] = step_from(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], a.eta_ff, a.eta_fb, a.eta_jerk);
+        }
+    }
+}
+
+// Combine the per-split partials: minima of the ratios, sums of a and j (fixed order).
+__global__ void steps_x2_finalize_kernel(const StepX2Args a, int split) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.n) return;
+    float v[kStPart];
+#pragma unroll
+    for (int k = 0; k < kStPart; ++k) v[k] = a.part[(size_t)k * a.n + i];
+    for (int s = 1; s < split; ++s) {
+        const float* q = a.part + (size_t)s * kStPart * a.n + i;
+        v[0] = fminf(v[0], q[0]);
+        v[1] = fminf(v[1], q[(size_t)a.n]);
+#pragma unroll
+        for (int k = 2; k < kStPart; ++k) v[k] += q[(size_t)k * a.n];
+    }
+    if (!(isfinite(v[2]) && isfinite(v[3]) && isfinite(v[4]))) set_error(a.err, FSI_ERR_NONFINITE);
+    a.step[i] = step_from(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], a.eta_ff, a.eta_fb, a.eta_jerk);
+}
+
+size_t steps_x2_part_bytes(int n, int sm_count) {
+    const int nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
+    const int want = (2 * sm_count + nb - 1) / nb;
+    const int split = std::max(1, std::min(want, (n + kStTile - 1) / kStTile));
+    return split > 1 ? (size_t)split * kStPart * (size_t)n * sizeof(float) : 0;
+}
+
+// rec, vrec: the set's mixed position records and FP32 velocity records (vx, vy, vz, m),
+// 16-byte aligned, n entries each.  part: steps_x2_part_bytes(n, sm_count) bytes.
+cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
+                            double eta_fb, double eta_jerk, float* part, double* step, int* err,
+                            long long timeout_ns, int sm_count, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    static bool attr[2] = {false, false};
+    const bool soft = eps2 > 0.0;
+    if (!attr[soft]) {
+        cudaError_t e = soft ? cudaFuncSetAttribute(steps_x2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem)
+                             : cudaFuncSetAttribute(steps_x2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem);
+        if (e != cudaSuccess) return e;
+        attr[soft] = true;
+    }
+    const int nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
+    const int want = (2 * sm_count + nb - 1) / nb;
+    int split = std::max(1, std::min(want, (n + kStTile - 1) / kStTile));
+    int jps = (n + split - 1) / split;
+    jps = (jps + kStTile - 1) / kStTile * kStTile;
+    split = (n + jps - 1) / jps;
+    StepX2Args a{};
+    a.n = n;
+    a.rec = reinterpret_cast<const RecMix*>(rec);
+    a.vrec = reinterpret_cast<const float4*>(vrec);
+    a.eps2 = (float)eps2;
+    a.eta_ff = eta_ff; a.eta_fb = eta_fb; a.eta_jerk = eta_jerk;
+    a.j_per_split = jps;
+    a.part = part;
+    a.step = step;
+    a.err = err;
+    a.timeout_ns = timeout_ns;
+    dim3 grid(nb, split);
+    if (soft) { steps_x2_kernel<true><<<grid, kStThreads, kStSmem, s>>>(a); note_launch(); }
+    else { steps_x2_kernel<false><<<grid, kStThreads, kStSmem, s>>>(a); note_launch(); }
+    if (split > 1) { steps_x2_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, split); note_launch(); }
+    return cudaGetLastError();
+}
+
+}  // namespace fsi

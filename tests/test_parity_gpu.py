@@ -634,3 +634,35 @@ def test_fsi_step_sub_rejects_bad_binaries(F):
     with F.Context("fp64", c=100.0) as ctx:
         with pytest.raises(F.FsiError):
             F.fsi_step_sub(ctx, dev(pos), dev(vel), dev(m), dev(pairs, torch.int32), 1e-4)
+
+
+@pytest.mark.parametrize("general", [False, True])
+def test_one_sided_packed_variant(F, general):
+    """The one-sided pair kernel's packed FP32x2 variant (36: two pairs of active particles
+    per thread) against the oracle: the same set (self pairs in the checked tiles) and
+    disjoint lists (every tile packed)."""
+    n = 3001
+    c = inputs.plummer(n, 61, imf="kroupa")
+    if general:
+        A = inputs.random_subset(n, 1200, 62)
+        B = np.setdiff1d(np.arange(n), A).astype(np.int32)
+    else:
+        A = B = None
+    ra, rg = oracle.accel_grad(c.pos, c.mass, A, B)
+    with F.Context("mixed", symmetric=False) as ctx:
+        F.fsi_set_tuning(ctx, 36, 36)
+        Ad = ids(A)
+        Bd = Ad if A is None else ids(B)
+        a, g = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass), Ad, Bd)
+        a, g = host(a), host(g)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    Aa = np.arange(n) if A is None else A
+    Ba = np.arange(n) if B is None else B
+    assert_close(a, ra, "mixed", scale=abs_scale(c.pos, c.mass, Aa, Ba))
+    accg = np.zeros((3, n))
+    if general:
+        accg[:, A] = oracle.acc(c.pos, c.mass, A, B)
+        accg[:, B] = oracle.acc(c.pos, c.mass, B, A)
+    else:
+        accg = oracle.acc(c.pos, c.mass)
+    assert_grad_close(g, rg, "mixed", grad_scale(c.pos, c.mass, accg, Aa, Ba))
