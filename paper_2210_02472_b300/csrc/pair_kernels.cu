@@ -4,7 +4,7 @@
 // and the force-gradient sum of the gradient kick (Sect. 2.1, Eq. new-grad-acc), each in
 // two precisions:
 //
-//  FP64  : every pair term in FP64.  The reciprocal square root is seeded by the FP32
+//  FP64  : every pair term in FP64.  The reciprocal square root is seeded by the FP64
 //          hardware approximation and refined in FP64 by the second-order series of
 //          (1 - e)^{-1/2}:  y = y0 (1 + e/2 + 3 e^2 / 8),  e = 1 - r^2 y0^2
 //          (a Householder-type step; error ~ (5/16) e^3 ~ 1e-21, below FP64 rounding).

@@ -1,6 +1,6 @@
 // pair_math.cuh -- per-pair arithmetic shared by the pair kernels (one-sided form).
 //
-// FP64: every operation in FP64; the reciprocal square root is seeded by the FP32
+// FP64: every operation in FP64; the reciprocal square root is seeded by the FP64
 // hardware approximation and refined by the second-order series of (1 - e)^{-1/2},
 // y = y0 (1 + e/2 + 3 e^2/8) with e = 1 - r^2 y0^2.
 // MIXED: separations from FP32 hi/lo position splits, FP32 arithmetic with the rsqrt
@@ -186,8 +186,12 @@ __device__ __forceinline__ void x2_grad_one_chk(const float4 h, const float4 l, 
     g[2] = __ffma2_rn(w, bz, __ffma2_rn(s, dz, g[2]));
 }
 
+// FP64 reciprocal square root: the hardware FP64 approximation (no conversion to and from
+// FP32 on the FP64 pipe, and the whole FP64 exponent range) refined by the second-order
+// step of (1 - e)^{-1/2} above.
 __device__ __forceinline__ double rsqrt_f64(double r2) {
-    const double y0 = (double)rsqrt_hw(__double2float_rn(r2));
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(r2));
     const double t = r2 * y0;
     const double e = fma(-t, y0, 1.0);
     const double p = fma(0.375, e, 0.5);
