@@ -567,9 +567,7 @@ __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const dou
             const double d2 = dx * dx + dy * dy + dz * dz;
             if (d2 == 0.0) { coincident = true; continue; }
             const double s2 = d2 + eps2;
-            const double y0 = (double)rsqrt_hw(__double2float_rn(s2));
-            const double e0 = fma(-s2 * y0, y0, 1.0);
-            const double y = fma(y0 * e0, fma(0.375, e0, 0.5), y0);
+            const double y = rsqrt_f64(s2);
             step_pair<double>(acc, dx, dy, dz, su[t] - ui, sv[t] - vi, sw[t] - wi, d2, sm[t], mi + sm[t], y);
         }
     }
@@ -738,9 +736,7 @@ __global__ void energy_kernel(int n, const double* __restrict__ xc, const double
             const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
             const double r2 = dx * dx + dy * dy + dz * dz + eps2;
             if (r2 == 0.0) { if (i < n) set_error(err, FSI_ERR_NONFINITE); continue; }
-            const double y0 = (double)rsqrt_hw(__double2float_rn(r2));
-            const double e0 = fma(-r2 * y0, y0, 1.0);
-            w = fma(sm[t], fma(y0 * e0, fma(0.375, e0, 0.5), y0), w);
+            w = fma(sm[t], rsqrt_f64(r2), w);
         }
     }
     double kin = 0.0;

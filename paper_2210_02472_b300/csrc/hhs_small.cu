@@ -140,9 +140,7 @@ __device__ void small_timesteps(SmallSmem<P>& S, const unsigned short* L, int n,
             const double d2 = dx * dx + dy * dy + dz * dz;
             if (d2 == 0.0) { coincident = true; continue; }
             const double s2 = d2 + a.eps2;
-            const double y0 = (double)rsqrt_hw(__double2float_rn(s2));
-            const double e0 = fma(-s2 * y0, y0, 1.0);
-            const double y = fma(y0 * e0, fma(0.375, e0, 0.5), y0);
+            const double y = rsqrt_f64(s2);
             step_pair<double>(acc, dx, dy, dz, S.v[0][j] - S.v[0][i], S.v[1][j] - S.v[1][i],
                               S.v[2][j] - S.v[2][i], d2, S.m[j], S.m[i] + S.m[j], y);
         }

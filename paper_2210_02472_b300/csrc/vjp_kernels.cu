@@ -25,7 +25,8 @@ constexpr int kVjpThreads = 128;
 constexpr int kVjpTile = 128;
 
 __device__ __forceinline__ double vjp_rsqrt(double r2) {
-    const double y0 = (double)rsqrt_hw(__double2float_rn(r2));
+    double y0;
+    asm("rsqrt.approx.ftz.f64 %0, %1;" : "=d"(y0) : "d"(r2));
     const double t = r2 * y0;
     const double e = fma(-t, y0, 1.0);
     return fma(y0 * e, fma(0.375, e, 0.5), y0);
