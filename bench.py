@@ -51,7 +51,7 @@ CPU_ROWS = 4096
 # (kernel label, workload, N); a kernel changed since the capture must drop its entry, and
 # any other configuration reports null.
 DRAM_TRAFFIC = {("sym_mixed_v2_kernel<acc, I=5, far>", "kroupa1m_bh16", 1048592): 201.9e6,
-                ("sym_mixed_x2_kernel<acc, I=6, MINB=2>", "kroupa1m_bh16", 1048592): 258.0e6}
+                ("sym_mixed_x2_kernel<acc, I=6, MINB=2>", "kroupa1m_bh16", 1048592): 256.5e6}
 
 
 def step_interactions(n: int) -> float:

@@ -54,6 +54,16 @@ __device__ __forceinline__ void write_arec(SmallSmem<P>& S, int k) {
     else S.arec[k] = make_d4(S.a[0][k], S.a[1][k], S.a[2][k], S.m[k]);
 }
 
+// Threads per receiver of a pass with nA receivers: the largest power of two (<= 32) that
+// still fits nA groups into the CTA.  Deep levels hold few particles, so their passes are
+// latency-bound; a group of G consecutive lanes splits the sources of one receiver and
+// reduces its partials with a butterfly of shuffles (a fixed order).
+__device__ __forceinline__ int group_size(int nA) {
+    int g = 1;
+    while (g < 32 && 2 * g * nA <= kSmallMax) g *= 2;
+    return g;
+}
+
 // out[:, A[t]] = sum over B of the acceleration (kind 0) or gradient (kind 1) pair terms
 template <int P, int KIND>
 __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
@@ -61,93 +71,117 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
                            unsigned long long* work) {
     const int t = threadIdx.x;
     if (t == 0 && work) atomicAdd(work + KIND, (unsigned long long)nA * (unsigned long long)nB);
-    if (t >= nA) return;
-    const int k = A[t];
+    const int G = group_size(nA);
+    const int slot = t / G, g = t % G;
+    const bool active = slot < nA;
+    const int k = active ? A[slot] : 0;
     double r[3] = {0.0, 0.0, 0.0};
-    if constexpr (P == FSI_MIXED) {
-        const RecMix ri = S.rec[k];
-        MixI p;
-        p.xh = ri.hi.x; p.yh = ri.hi.y; p.zh = ri.hi.z;
-        p.xl = ri.lo.x; p.yl = ri.lo.y; p.zl = ri.lo.z;
-        p.ax = p.ay = p.az = 0.f;
-        if (KIND == 1) { p.ax = S.arec[k].x; p.ay = S.arec[k].y; p.az = S.arec[k].z; }
-        float f[3] = {0.f, 0.f, 0.f};
-        const float eps2f = (float)eps2;
-        for (int q = 0; q < nB; ++q) {
-            const int j = B[q];
-            const RecMix rj = S.rec[j];
-            if (KIND == 0) mix_acc_pair<true>(rj.hi, rj.lo, p, eps2f, j == k, f[0], f[1], f[2]);
-            else mix_grad_pair<true>(rj.hi, rj.lo, S.arec[j], p, eps2f, j == k, f[0], f[1], f[2]);
-            if ((q & 255) == 255) {
-                r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
-                f[0] = f[1] = f[2] = 0.f;
+    if (active) {
+        if constexpr (P == FSI_MIXED) {
+            const RecMix ri = S.rec[k];
+            MixI p;
+            p.xh = ri.hi.x; p.yh = ri.hi.y; p.zh = ri.hi.z;
+            p.xl = ri.lo.x; p.yl = ri.lo.y; p.zl = ri.lo.z;
+            p.ax = p.ay = p.az = 0.f;
+            if (KIND == 1) { p.ax = S.arec[k].x; p.ay = S.arec[k].y; p.az = S.arec[k].z; }
+            float f[3] = {0.f, 0.f, 0.f};
+            const float eps2f = (float)eps2;
+            int cnt = 0;
+            for (int q = g; q < nB; q += G) {
+                const int j = B[q];
+                const RecMix rj = S.rec[j];
+                if (KIND == 0) mix_acc_pair<true>(rj.hi, rj.lo, p, eps2f, j == k, f[0], f[1], f[2]);
+                else mix_grad_pair<true>(rj.hi, rj.lo, S.arec[j], p, eps2f, j == k, f[0], f[1], f[2]);
+                if (++cnt == 256) {
+                    r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
+                    f[0] = f[1] = f[2] = 0.f;
+                    cnt = 0;
+                }
+            }
+            r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
+        } else {
+            const D4 ri = S.rec[k];
+            F64I p;
+            p.x = ri.x; p.y = ri.y; p.z = ri.z;
+            p.ax = p.ay = p.az = 0.0;
+            if (KIND == 1) { p.ax = S.arec[k].x; p.ay = S.arec[k].y; p.az = S.arec[k].z; }
+            for (int q = g; q < nB; q += G) {
+                const int j = B[q];
+                if (KIND == 0) f64_acc_pair<true>(S.rec[j], p, eps2, j == k, r[0], r[1], r[2]);
+                else f64_grad_pair<true>(S.rec[j], S.arec[j], p, eps2, j == k, r[0], r[1], r[2]);
             }
         }
-        r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
-    } else {
-        const D4 ri = S.rec[k];
-        F64I p;
-        p.x = ri.x; p.y = ri.y; p.z = ri.z;
-        p.ax = p.ay = p.az = 0.0;
-        if (KIND == 1) { p.ax = S.arec[k].x; p.ay = S.arec[k].y; p.az = S.arec[k].z; }
-        for (int q = 0; q < nB; ++q) {
-            const int j = B[q];
-            if (KIND == 0) f64_acc_pair<true>(S.rec[j], p, eps2, j == k, r[0], r[1], r[2]);
-            else f64_grad_pair<true>(S.rec[j], S.arec[j], p, eps2, j == k, r[0], r[1], r[2]);
-        }
     }
-    out[0][k] = r[0];
-    out[1][k] = r[1];
-    out[2][k] = r[2];
+    // every lane of the warp takes part in the reduction of its group
+    for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+        for (int q = 0; q < 3; ++q) r[q] += __shfl_xor_sync(0xffffffffu, r[q], o);
+    if (active && g == 0) {
+        out[0][k] = r[0];
+        out[1][k] = r[1];
+        out[2][k] = r[2];
+    }
 }
 
 // Time steps of list L against itself (Sect. 3.4; FP32 pair arithmetic for the mixed
 // precision, FP64 otherwise), then the min with the level-0 step.
 template <int P>
 __device__ void small_timesteps(SmallSmem<P>& S, const unsigned short* L, int n, const SmallArgs& a) {
+    using T = typename std::conditional<P == FSI_MIXED, float, double>::type;
     const int t = threadIdx.x;
-    if (t >= n) return;
-    const int i = L[t];
+    const int G = group_size(n);
+    const int slot = t / G, g = t % G;
+    const bool active = slot < n;
+    const int i = active ? L[slot] : 0;
     bool coincident = false;
-    double e;
-    if constexpr (P == FSI_MIXED) {
-        const RecMix ri = S.rec[i];
-        const float4 vi = S.vf[i];
-        const float eps2f = (float)a.eps2;
-        StepAcc<float> acc;
-        acc.init();
-        for (int q = 0; q < n; ++q) {
-            const int j = L[q];
-            if (j == i) continue;
-            const RecMix rj = S.rec[j];
-            const float4 vj = S.vf[j];
-            const float dx = (rj.hi.x - ri.hi.x) + (rj.lo.x - ri.lo.x);
-            const float dy = (rj.hi.y - ri.hi.y) + (rj.lo.y - ri.lo.y);
-            const float dz = (rj.hi.z - ri.hi.z) + (rj.lo.z - ri.lo.z);
-            const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (d2 == 0.f) { coincident = true; continue; }
-            step_pair<float>(acc, dx, dy, dz, vj.x - vi.x, vj.y - vi.y, vj.z - vi.z, d2, vj.w,
-                             vi.w + vj.w, rsqrt_f32_refined(d2 + eps2f));
+    StepAcc<T> acc;
+    acc.init();
+    if (active) {
+        if constexpr (P == FSI_MIXED) {
+            const RecMix ri = S.rec[i];
+            const float4 vi = S.vf[i];
+            const float eps2f = (float)a.eps2;
+            for (int q = g; q < n; q += G) {
+                const int j = L[q];
+                if (j == i) continue;
+                const RecMix rj = S.rec[j];
+                const float4 vj = S.vf[j];
+                const float dx = (rj.hi.x - ri.hi.x) + (rj.lo.x - ri.lo.x);
+                const float dy = (rj.hi.y - ri.hi.y) + (rj.lo.y - ri.lo.y);
+                const float dz = (rj.hi.z - ri.hi.z) + (rj.lo.z - ri.lo.z);
+                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+                if (d2 == 0.f) { coincident = true; continue; }
+                step_pair<float>(acc, dx, dy, dz, vj.x - vi.x, vj.y - vi.y, vj.z - vi.z, d2, vj.w,
+                                 vi.w + vj.w, rsqrt_f32_refined(d2 + eps2f));
+            }
+        } else {
+            for (int q = g; q < n; q += G) {
+                const int j = L[q];
+                if (j == i) continue;
+                const double dx = S.x[0][j] - S.x[0][i], dy = S.x[1][j] - S.x[1][i], dz = S.x[2][j] - S.x[2][i];
+                const double d2 = dx * dx + dy * dy + dz * dz;
+                if (d2 == 0.0) { coincident = true; continue; }
+                const double y = rsqrt_f64(d2 + a.eps2);
+                step_pair<double>(acc, dx, dy, dz, S.v[0][j] - S.v[0][i], S.v[1][j] - S.v[1][i],
+                                  S.v[2][j] - S.v[2][i], d2, S.m[j], S.m[i] + S.m[j], y);
+            }
         }
-        e = step_finish<float>(acc, a.eta_ff, a.eta_fb, a.eta_jerk);
-    } else {
-        StepAcc<double> acc;
-        acc.init();
-        for (int q = 0; q < n; ++q) {
-            const int j = L[q];
-            if (j == i) continue;
-            const double dx = S.x[0][j] - S.x[0][i], dy = S.x[1][j] - S.x[1][i], dz = S.x[2][j] - S.x[2][i];
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 == 0.0) { coincident = true; continue; }
-            const double s2 = d2 + a.eps2;
-            const double y = rsqrt_f64(s2);
-            step_pair<double>(acc, dx, dy, dz, S.v[0][j] - S.v[0][i], S.v[1][j] - S.v[1][i],
-                              S.v[2][j] - S.v[2][i], d2, S.m[j], S.m[i] + S.m[j], y);
-        }
-        e = step_finish<double>(acc, a.eta_ff, a.eta_fb, a.eta_jerk);
+    }
+    // reduce the group: minima as (numerator, denominator) pairs, sums of a and j
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        const T ffn = __shfl_xor_sync(0xffffffffu, acc.ffn, o), ffd = __shfl_xor_sync(0xffffffffu, acc.ffd, o);
+        const T fbn = __shfl_xor_sync(0xffffffffu, acc.fbn, o), fbd = __shfl_xor_sync(0xffffffffu, acc.fbd, o);
+        if (ffn * acc.ffd < acc.ffn * ffd) { acc.ffn = ffn; acc.ffd = ffd; }
+        if (fbn * acc.fbd < acc.fbn * fbd) { acc.fbn = fbn; acc.fbd = fbd; }
+        acc.ax += __shfl_xor_sync(0xffffffffu, acc.ax, o);
+        acc.ay += __shfl_xor_sync(0xffffffffu, acc.ay, o);
+        acc.az += __shfl_xor_sync(0xffffffffu, acc.az, o);
+        acc.jx += __shfl_xor_sync(0xffffffffu, acc.jx, o);
+        acc.jy += __shfl_xor_sync(0xffffffffu, acc.jy, o);
+        acc.jz += __shfl_xor_sync(0xffffffffu, acc.jz, o);
     }
     if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
-    S.st[i] = fmin(e, S.s0[i]);
+    if (active && g == 0) S.st[i] = fmin(step_finish<T>(acc, a.eta_ff, a.eta_fb, a.eta_jerk), S.s0[i]);
 }
 
 // Gradient and velocity-per-acceleration steps (Sect. 3.4) of list L from its own a and
