@@ -378,21 +378,23 @@ def run_ensemble(args):
     m = torch.as_tensor(cat.mass).to(dev)
     ctx = F.Context(args.precision)
     b = F.Batch(ctx, off, max_steps=S)
-    # autotune: particles per thread x resident CTAs per SM
+    # autotune: particles per thread x resident CTAs per SM (or fixed by --batch-tuning)
     best = None
-    for ipt in ((1, 2, 4) if args.precision == "mixed" else (1, 2)):   # 4: symmetric form
-        for cps in (1, 2, 0):
-            F.fsi_batch_set_tuning(ctx, b, ipt, cps)
-            p, v = torch.as_tensor(cat.pos).to(dev), torch.as_tensor(cat.vel).to(dev)
-            F.fsi_batch_step(ctx, b, p, v, m, 1e-3, S)
-            e0, e1 = _timed_events(None)
-            e0.record()
-            F.fsi_batch_step(ctx, b, p, v, m, 1e-3, S)
-            e1.record()
-            torch.cuda.synchronize()
-            t = e0.elapsed_time(e1)
-            if best is None or t < best[0]:
-                best = (t, F.fsi_batch_get_tuning(b))
+    fixed = [tuple(int(x) for x in args.batch_tuning.split(","))] if args.batch_tuning else None
+    combos = fixed or [(ipt, cps) for ipt in ((1, 2, 4) if args.precision == "mixed" else (1, 2))
+                       for cps in (1, 2, 0)]                       # ipt 4: symmetric form
+    for ipt, cps in combos:
+        F.fsi_batch_set_tuning(ctx, b, ipt, cps)
+        p, v = torch.as_tensor(cat.pos).to(dev), torch.as_tensor(cat.vel).to(dev)
+        F.fsi_batch_step(ctx, b, p, v, m, 1e-3, S)
+        e0, e1 = _timed_events(None)
+        e0.record()
+        F.fsi_batch_step(ctx, b, p, v, m, 1e-3, S)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1)
+        if best is None or t < best[0]:
+            best = (t, F.fsi_batch_get_tuning(b))
     F.fsi_batch_set_tuning(ctx, b, *best[1])
     p, v = torch.as_tensor(cat.pos).to(dev), torch.as_tensor(cat.vel).to(dev)
     s = torch.cuda.Stream()
@@ -686,6 +688,8 @@ def main():
                     help="cycle: the headline FSI-cycle benchmark; the others measure the "
                          "ensemble, adjoint and HHS workloads and one acc + grad pass")
     ap.add_argument("--batch-steps", type=int, default=10)
+    ap.add_argument("--batch-tuning", default="", help="ensemble mode: fixed 'ipt,ctas_per_sm' "
+                    "(ipt 4 = symmetric form) instead of the autotuning sweep")
     ap.add_argument("--vjp-steps", type=int, default=200)
     ap.add_argument("--fd-components", type=int, default=3)
     ap.add_argument("--intervals", type=int, default=1)
