@@ -1347,7 +1347,7 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
     if (rc == FSI_OK && c->p.precision == FSI_MIXED) {
         // symmetric form: per cluster (largest first) and block, the block's own tiles, then
         // chunks of kBatchSymChunk source tiles above it
-        constexpr int kBatchSymChunk = 4;
+        constexpr int kBatchSymChunk = 8;
         const int bs = batch_block_size(kBatchSymI);
         std::vector<BatchSymItem> sit;
         std::vector<int> nsum(K, 0);
