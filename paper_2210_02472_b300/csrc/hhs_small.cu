@@ -8,7 +8,10 @@
 // single CTA with the set's state in shared memory and an explicit frame stack.  Thread t
 // owns entry t of whichever index list a phase works on; phases are separated by
 // __syncthreads.  The same arithmetic as the large kernels is used (FP64, or FP32 hi/lo
-// separations with FP64 state for the mixed precision).
+// separations with FP64 state for the mixed precision).  In the mixed precision the pass
+// sums are float-float pairs (hi, lo) and reach FP64 only in the per-particle kicks: the
+// B300 FP64 unit issues about 1/70 of the FP32 rate, and a pass with G lanes per receiver
+// would otherwise spend G FP64 reductions on every receiver.
 #include <type_traits>
 
 #include "fsi_internal.cuh"
@@ -28,10 +31,31 @@ struct Frame {
     int stage;
 };
 
+// Pass sums: FP64, or float-float (hi, lo) in the mixed precision (value hi + lo).
+template <int P>
+using SumT = typename std::conditional<P == FSI_MIXED, float2, double>::type;
+
+__device__ __forceinline__ double to_f64(double v) { return v; }
+__device__ __forceinline__ double to_f64(float2 v) { return (double)v.x + (double)v.y; }
+__device__ __forceinline__ void from_f64(double& d, double v) { d = v; }
+__device__ __forceinline__ void from_f64(float2& d, double v) {
+    const float h = (float)v;
+    d = make_float2(h, (float)(v - (double)h));
+}
+
+// (hi, lo) += v, TwoSum of Knuth (exact rounding error of hi + v into lo).
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
 template <int P>
 struct SmallSmem {
     double x[3][kSmallMax], v[3][kSmallMax], m[kSmallMax], s0[kSmallMax], st[kSmallMax];
-    double a[3][kSmallMax], g[3][kSmallMax];
+    SumT<P> a[3][kSmallMax], g[3][kSmallMax];
     typename std::conditional<P == FSI_MIXED, RecMix, D4>::type rec[kSmallMax];
     typename std::conditional<P == FSI_MIXED, float4, D4>::type arec[kSmallMax];
     float4 vf[kSmallMax];                   // FP32 (vx, vy, vz, m) for the mixed time steps
@@ -48,9 +72,29 @@ __device__ __forceinline__ void write_rec(SmallSmem<P>& S, int k) {
     else S.rec[k] = make_d4(S.x[0][k], S.x[1][k], S.x[2][k], S.m[k]);
 }
 
+// After a drift: new hi/lo position splits, the mass constants kept.
+template <int P>
+__device__ __forceinline__ void write_rec_pos(SmallSmem<P>& S, int k) {
+    if constexpr (P == FSI_MIXED) {
+        RecMix r = S.rec[k];
+        const float xh = (float)S.x[0][k], yh = (float)S.x[1][k], zh = (float)S.x[2][k];
+        r.hi.x = xh; r.hi.y = yh; r.hi.z = zh;
+        r.lo.x = (float)(S.x[0][k] - (double)xh);
+        r.lo.y = (float)(S.x[1][k] - (double)yh);
+        r.lo.z = (float)(S.x[2][k] - (double)zh);
+        S.rec[k] = r;
+    } else {
+        write_rec<P>(S, k);
+    }
+}
+
+// Source accelerations of a gradient pass (FP32 record in the mixed precision: the
+// rounded float-float sum, no FP64 instruction).
 template <int P>
 __device__ __forceinline__ void write_arec(SmallSmem<P>& S, int k) {
-    if constexpr (P == FSI_MIXED) S.arec[k] = make_float4((float)S.a[0][k], (float)S.a[1][k], (float)S.a[2][k], (float)S.m[k]);
+    if constexpr (P == FSI_MIXED)
+        S.arec[k] = make_float4(S.a[0][k].x + S.a[0][k].y, S.a[1][k].x + S.a[1][k].y,
+                                S.a[2][k].x + S.a[2][k].y, S.vf[k].w);
     else S.arec[k] = make_d4(S.a[0][k], S.a[1][k], S.a[2][k], S.m[k]);
 }
 
@@ -67,7 +111,7 @@ __device__ __forceinline__ int group_size(int nA) {
 // out[:, A[t]] = sum over B of the acceleration (kind 0) or gradient (kind 1) pair terms
 template <int P, int KIND>
 __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
-                           const unsigned short* B, int nB, double eps2, double (*out)[kSmallMax],
+                           const unsigned short* B, int nB, double eps2, SumT<P> (*out)[kSmallMax],
                            unsigned long long* work) {
     const int t = threadIdx.x;
     if (t == 0 && work) atomicAdd(work + KIND, (unsigned long long)nA * (unsigned long long)nB);
@@ -75,9 +119,10 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
     const int slot = t / G, g = t % G;
     const bool active = slot < nA;
     const int k = active ? A[slot] : 0;
-    double r[3] = {0.0, 0.0, 0.0};
-    if (active) {
-        if constexpr (P == FSI_MIXED) {
+    if constexpr (P == FSI_MIXED) {
+        // FP32 partial sums over runs of 256 sources, float-float across runs and lanes
+        float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
+        if (active) {
             const RecMix ri = S.rec[k];
             MixI p;
             p.xh = ri.hi.x; p.yh = ri.hi.y; p.zh = ri.hi.z;
@@ -93,13 +138,35 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
                 if (KIND == 0) mix_acc_pair<true>(rj.hi, rj.lo, p, eps2f, j == k, f[0], f[1], f[2]);
                 else mix_grad_pair<true>(rj.hi, rj.lo, S.arec[j], p, eps2f, j == k, f[0], f[1], f[2]);
                 if (++cnt == 256) {
-                    r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
-                    f[0] = f[1] = f[2] = 0.f;
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) { ff_acc(sh[c], sl[c], f[c]); f[c] = 0.f; }
                     cnt = 0;
                 }
             }
-            r[0] += f[0]; r[1] += f[1]; r[2] += f[2];
-        } else {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ff_acc(sh[c], sl[c], f[c]);
+        }
+        // every lane of the warp takes part in the reduction of its group
+        for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh[c], o);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl[c], o);
+                ff_acc(sh[c], sl[c], oh);
+                sl[c] = __fadd_rn(sl[c], ol);
+            }
+        if (active && g == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float h = 0.f, l = 0.f;                  // renormalised: h = fl(hi + lo)
+                ff_acc(h, l, sh[c]);
+                ff_acc(h, l, sl[c]);
+                out[c][k] = make_float2(h, l);
+            }
+        }
+    } else {
+        double r[3] = {0.0, 0.0, 0.0};
+        if (active) {
             const D4 ri = S.rec[k];
             F64I p;
             p.x = ri.x; p.y = ri.y; p.z = ri.z;
@@ -111,15 +178,14 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
                 else f64_grad_pair<true>(S.rec[j], S.arec[j], p, eps2, j == k, r[0], r[1], r[2]);
             }
         }
-    }
-    // every lane of the warp takes part in the reduction of its group
-    for (int o = G >> 1; o > 0; o >>= 1)
+        for (int o = G >> 1; o > 0; o >>= 1)
 #pragma unroll
-        for (int q = 0; q < 3; ++q) r[q] += __shfl_xor_sync(0xffffffffu, r[q], o);
-    if (active && g == 0) {
-        out[0][k] = r[0];
-        out[1][k] = r[1];
-        out[2][k] = r[2];
+            for (int q = 0; q < 3; ++q) r[q] += __shfl_xor_sync(0xffffffffu, r[q], o);
+        if (active && g == 0) {
+            out[0][k] = r[0];
+            out[1][k] = r[1];
+            out[2][k] = r[2];
+        }
     }
 }
 
@@ -195,9 +261,10 @@ __device__ void small_grad_steps(SmallSmem<P>& S, const unsigned short* L, int n
     double vn = 0.0, an = 0.0, gn = 0.0;
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-        const double gq = S.g[q][k] * (1.0 / 24.0);
+        const double gq = to_f64(S.g[q][k]) * (1.0 / 24.0);
+        const double aq = to_f64(S.a[q][k]);
         vn = fma(S.v[q][k], S.v[q][k], vn);
-        an = fma(S.a[q][k], S.a[q][k], an);
+        an = fma(aq, aq, an);
         gn = fma(gq, gq, gn);
     }
     vn = sqrt(vn);
@@ -219,8 +286,15 @@ __device__ void small_kick(SmallSmem<P>& S, const unsigned short* L, int n, doub
     if (t >= n) return;
     const int k = L[t];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) S.v[c][k] = fma(w, with_grad ? fma(cg, S.g[c][k], S.a[c][k]) : S.a[c][k], S.v[c][k]);
-    if constexpr (P == FSI_MIXED) S.vf[k] = make_float4((float)S.v[0][k], (float)S.v[1][k], (float)S.v[2][k], (float)S.m[k]);
+    for (int c = 0; c < 3; ++c) {
+        const double ac = to_f64(S.a[c][k]);
+        S.v[c][k] = fma(w, with_grad ? fma(cg, to_f64(S.g[c][k]), ac) : ac, S.v[c][k]);
+    }
+    if constexpr (P == FSI_MIXED) {
+        float4 u = S.vf[k];                     // the mass (w) is kept
+        u.x = (float)S.v[0][k]; u.y = (float)S.v[1][k]; u.z = (float)S.v[2][k];
+        S.vf[k] = u;
+    }
 }
 
 template <int P>
@@ -230,7 +304,7 @@ __device__ void small_drift(SmallSmem<P>& S, const unsigned short* L, int n, dou
     const int k = L[t];
 #pragma unroll
     for (int c = 0; c < 3; ++c) S.x[c][k] = fma(w, S.v[c][k], S.x[c][k]);
-    write_rec<P>(S, k);
+    write_rec_pos<P>(S, k);
 }
 
 // PN1.0 accelerations (into g) of list A from list B, pairs with a black hole, j != i.
@@ -248,9 +322,9 @@ __device__ void small_pn(SmallSmem<P>& S, const unsigned short* A, int nA, const
         pn_pair(S.x[0][i], S.x[1][i], S.x[2][i], S.v[0][i], S.v[1][i], S.v[2][i], S.m[i], S.x[0][j],
                 S.x[1][j], S.x[2][j], S.v[0][j], S.v[1][j], S.v[2][j], S.m[j], ic2, px, py, pz, a.err);
     }
-    S.g[0][i] = px;
-    S.g[1][i] = py;
-    S.g[2][i] = pz;
+    from_f64(S.g[0][i], px);
+    from_f64(S.g[1][i], py);
+    from_f64(S.g[2][i], pz);
 }
 
 template <int P>
@@ -259,8 +333,12 @@ __device__ void small_kick_g(SmallSmem<P>& S, const unsigned short* L, int n, do
     if (t >= n) return;
     const int k = L[t];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) S.v[c][k] = fma(w, S.g[c][k], S.v[c][k]);
-    if constexpr (P == FSI_MIXED) S.vf[k] = make_float4((float)S.v[0][k], (float)S.v[1][k], (float)S.v[2][k], (float)S.m[k]);
+    for (int c = 0; c < 3; ++c) S.v[c][k] = fma(w, to_f64(S.g[c][k]), S.v[c][k]);
+    if constexpr (P == FSI_MIXED) {
+        float4 u = S.vf[k];
+        u.x = (float)S.v[0][k]; u.y = (float)S.v[1][k]; u.z = (float)S.v[2][k];
+        S.vf[k] = u;
+    }
 }
 
 // PN1.0 kick of weight w: within list L (B == nullptr) or between disjoint L and B; all PN
