@@ -540,7 +540,8 @@ def run_hhs(args):
     soft = wl == "plummer161k"
     tau = SOFT_TAU if soft else args.tau
     kw = dict(eps2=SOFT_EPS ** 2, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eta_grad=0.1) if soft else {}
-    ctx = F.Context(args.precision, c=cl, **kw)
+    ctx = F.Context(args.precision, c=cl, wide_ctas=args.wide_ctas,
+                    hhs_small_max=args.hhs_small_max, **kw)
     energy = lambda: float(F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum())
     e0 = energy()
     F.fsi_work_stats(ctx, reset=True)
@@ -570,6 +571,7 @@ def run_hhs(args):
         "vs_baseline": None, "dtype": "f32+f64" if args.precision == "mixed" else "f64",
         "data": "synthetic",
         "config": {"workload": wl, "n": c.n, "tau": tau, "intervals": args.intervals, "c": cl,
+                   "wide_ctas": args.wide_ctas, "hhs_small_max": args.hhs_small_max,
                    **({"eps2": SOFT_EPS ** 2, "eta": "ff 0.2, fb 0.2, jerk 0.1, gradient 0.1",
                        "units": f"length {SOFT_LUNIT_PC:.4f} pc, time {SOFT_TUNIT_MYR:.4f} Myr"}
                       if soft else {})},
@@ -695,6 +697,9 @@ def main():
     ap.add_argument("--intervals", type=int, default=1)
     ap.add_argument("--tau", type=float, default=1.0 / 64)
     ap.add_argument("--hhs-pn", action="store_true", help="HHS mode: PN1.0 on (c = 1e4)")
+    ap.add_argument("--wide-ctas", type=int, default=0, help="HHS mode: fsi_params.wide_ctas "
+                    "(0 = 32, -1 = tiled passes only)")
+    ap.add_argument("--hhs-small-max", type=int, default=0, help="HHS mode: fsi_params.hhs_small_max")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

@@ -78,9 +78,9 @@ typedef struct fsi_params {
     int symmetric;        /* 1 (default): a set's self-interaction evaluates every unordered
                              pair once and adds it to both particles (Newton's third law);
                              0: every ordered pair is evaluated by its receiving particle */
-    int hhs_small_max;    /* HHS: a fast set of at most this many particles (0 = 512, the
-                             maximum) runs its whole recursion inside one CTA; -1 = always
-                             walk the levels from the host */
+    int hhs_small_max;    /* HHS: a fast set of at most this many particles (0 = 256; the
+                             maximum is 512) runs its whole recursion inside one CTA; -1 =
+                             always walk the levels from the host */
     int order_min;        /* mixed + symmetric with a far-tile kernel variant selected (see
                              fsi_autotune): fsi_step puts a set of at least this many
                              particles in Morton order for the duration of the call (0 =
@@ -93,6 +93,10 @@ typedef struct fsi_params {
                              time-step assignment); 0 (default) = off */
     double eta_va;        /* velocity-per-acceleration time-step parameter (Sect. 3.4, Eq.
                              vel-acc-crit): eps = eta |v_i| / |a_i|; 0 (default) = off */
+    int wide_ctas;        /* a pair pass (acc or grad, unmasked) whose tiled form would run
+                             fewer CTAs than this takes the wide form instead: up to 32
+                             lanes per receiver splitting its sources (0 = 32; -1 =
+                             never).  Only the summation order differs. */
 } fsi_params;
 
 /* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,

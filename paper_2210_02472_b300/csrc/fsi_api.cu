@@ -135,6 +135,12 @@ size_t pad_tile(int n) { return (size_t)((n + kTileJ - 1) / kTileJ) * kTileJ; }
 
 // Source-split factor: the smallest S whose CTA count (i-blocks x S) fills the resident
 // slots of the GPU (2 CTAs/SM) to >= 90 % in the last wave, keeping >= 4 tiles per slice.
+// Default size cap of a fast set whose HHS recursion runs inside one CTA (the kernel holds
+// up to 512): with the wide pair passes for the host-walked small levels, sets of 257 to
+// 512 particles are faster walked from the host (one HHS interval of 65536 particles,
+// mixed: 279.6 ms at 512, 269.5 ms at 256 and 128).
+constexpr int kSmallCapDefault = 256;
+
 int choose_split(const fsi_ctx* c, int n_i, int n_j, int ipc) {
     const int ctas = (n_i + ipc - 1) / ipc;
     const int max_s = std::max(1, std::min(64, n_j / (4 * kTileJ)));
@@ -269,11 +275,55 @@ int choose_chunk(const fsi_ctx* c, int n, int ipt) {
     return (int)std::max(1LL, std::min(64LL, ch));
 }
 
+// Wide form of a pass (lanes per receiver 2^lg, source slices split) when its tiled
+// form would run fewer CTAs than wide_ctas (0: kWideCtasDefault): each lane keeps >= 8
+// sources, and the slices aim at 16 resident warps per SM with >= 32 sources per lane.
+// Measured on one HHS interval of 65536 particles (mixed): the wide form is faster
+// below ~32 tiled CTAs and slower for the mid-size passes above (L1 loads of every
+// source record per lane, where the tiled form broadcasts a staged tile).
+constexpr int kWideCtasDefault = 32;
+
+bool wide_plan(const fsi_ctx* c, int n_i, int n_j, int ipc, int& lg, int& split) {
+    if (c->p.wide_ctas < 0) return false;
+    const long long limit = c->p.wide_ctas > 0 ? c->p.wide_ctas : kWideCtasDefault;
+    const long long tiled = (long long)((n_i + ipc - 1) / ipc) * choose_split(c, n_i, n_j, ipc);
+    if (tiled >= limit) return false;
+    lg = 5;
+    while (lg > 0 && (8LL << lg) > n_j) --lg;
+    const long long warps = (((long long)n_i << lg) + 31) / 32;
+    const long long want = 16LL * c->sm_count;
+    long long sp = (want + warps - 1) / warps;
+    sp = std::min(sp, std::max(1LL, (long long)n_j / (32LL << lg)));
+    split = (int)std::max(1LL, std::min(64LL, sp));
+    return true;
+}
+
+int run_wide(fsi_ctx* c, int kind, PairArgs a, int lg, int split, cudaStream_t s) {
+    const int prec = c->p.precision;
+    const int jps = (a.n_j + split - 1) / split;
+    split = std::max(1, (a.n_j + jps - 1) / jps);
+    a.j_per_split = std::max(1, jps);
+    a.err = c->err_d;
+    if (split > 1) {
+        CK(ensure(c->part, (size_t)split * 3 * a.n_i * sizeof(double)));
+        a.part = P<double>(c->part);
+    }
+    const bool diag = a.check == CHECK_DIAG;
+    CK(timed(c, kind, s, [&] { return launch_wide_pair(prec, kind, diag, a, lg, split, s); }));
+    if (split > 1) CK(timed(c, 2, s, [&] { return launch_finalize_p(prec, a, split, s); }));
+    return FSI_OK;
+}
+
 int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
     if (a.n_i <= 0) return FSI_OK;
     c->work_pairs[kind] += (long long)a.n_i * (long long)a.n_j;
     const int prec = c->p.precision;
     const int ipt = c->ipt[prec][kind][a.n_i >= kOneSidedLarge];
+    if (a.check == CHECK_NONE || a.check == CHECK_DIAG) {
+        int lg = 0, split = 1;
+        if (wide_plan(c, a.n_i, a.n_j, kThreads * variant_ipt(ipt), lg, split))
+            return run_wide(c, kind, a, lg, split, s);
+    }
     if (c->p.symmetric && a.check == CHECK_DIAG && a.irec == a.jrec && a.n_i == a.n_j &&
         a.iacc == a.jacc) {
         // self-interaction of one set: every unordered pair once, then the epilogue
@@ -600,7 +650,7 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
         CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, tau / 6.0, 0, 0.0, s));
     }
     // HHS(F, tau/2): small fast sets recurse inside one CTA, larger ones level by level here
-    const int small_cap = c->p.hhs_small_max == 0 ? small_max()
+    const int small_cap = c->p.hhs_small_max == 0 ? std::min(kSmallCapDefault, small_max())
                           : std::min(c->p.hhs_small_max, small_max());
     auto recurse = [&]() -> int {
         if (nF <= 0) return FSI_OK;
@@ -676,6 +726,7 @@ void fsi_default_params(fsi_params* p) {
     p->order_min = 0;
     p->eta_grad = 0.0;
     p->eta_va = 0.0;
+    p->wide_ctas = 0;
 }
 
 const char* fsi_last_error(void) { return g_err.c_str(); }

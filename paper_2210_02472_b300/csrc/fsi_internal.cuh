@@ -217,6 +217,10 @@ cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* sink, cudaSt
 cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int split,
                         cudaStream_t s);
 cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s);
+// Wide one-sided pass (2^lg lanes per receiver, split source slices); split == 1 applies
+// the epilogue itself, split > 1 writes a.part for launch_finalize_p.
+cudaError_t launch_wide_pair(int precision, int kind, bool diag, const PairArgs& a, int lg,
+                             int split, cudaStream_t s);
 // Symmetric self-interaction pass (every unordered pair once); adds into accum (3 x n,
 // zeroed by the caller); `chunk` source tiles per work item.
 // Far-tile inputs of the symmetric mixed kernel (second form with bit 64 in its variant):

@@ -43,15 +43,6 @@ __device__ __forceinline__ void from_f64(float2& d, double v) {
     d = make_float2(h, (float)(v - (double)h));
 }
 
-// (hi, lo) += v, TwoSum of Knuth (exact rounding error of hi + v into lo).
-__device__ __forceinline__ void ff_acc(float& hi, float& lo, float v) {
-    const float s = __fadd_rn(hi, v);
-    const float bb = __fsub_rn(s, hi);
-    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
-    hi = s;
-    lo = __fadd_rn(lo, e);
-}
-
 template <int P>
 struct SmallSmem {
     double x[3][kSmallMax], v[3][kSmallMax], m[kSmallMax], s0[kSmallMax], st[kSmallMax];

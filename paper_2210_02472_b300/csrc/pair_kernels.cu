@@ -385,6 +385,104 @@ __global__ void finalize_kernel(const PairArgs a, int split) {
 }
 
 // =================================================================================
+// Wide one-sided kernel: passes too small for the tiled form to fill the GPU (the deep
+// HHS levels, the cross-level kicks of small sets).  G = 2^lg consecutive lanes (G <= 32,
+// so a group never straddles a warp) share one receiver and stride over its sources;
+// blockIdx.y splits the source range as in the tiled form.  The set is small, so source
+// records are read through L1 without staging.  Mixed: FP32 partial sums over runs of
+// 256 sources per lane, float-float (TwoSum) across runs and lanes, no FP64 instruction
+// before the epilogue; FP64: FP64 throughout.  DIAG: same list on both sides, the self
+// pair excluded by index.
+template <int P, int KIND, bool DIAG>
+__global__ void __launch_bounds__(kThreads) wide_pair_kernel(const PairArgs a, int lg) {
+    const int G = 1 << lg;
+    const long long gt = (long long)blockIdx.x * kThreads + threadIdx.x;
+    const int slot = (int)(gt >> lg);
+    const int g = (int)(gt & (G - 1));
+    const bool active = slot < a.n_i;
+    const int i = active ? slot : a.n_i - 1;
+    const int js = blockIdx.y * a.j_per_split;
+    const int je = min(a.n_j, js + a.j_per_split);
+    double r[3];
+    if constexpr (P == FSI_MIXED) {
+        const RecMix ri = reinterpret_cast<const RecMix*>(a.irec)[i];
+        MixI p;
+        p.xh = ri.hi.x; p.yh = ri.hi.y; p.zh = ri.hi.z;
+        p.xl = ri.lo.x; p.yl = ri.lo.y; p.zl = ri.lo.z;
+        p.ax = p.ay = p.az = 0.f;
+        if constexpr (KIND == KIND_GRAD) {
+            const float4 ai = reinterpret_cast<const float4*>(a.iacc)[i];
+            p.ax = ai.x; p.ay = ai.y; p.az = ai.z;
+        }
+        const RecMix* J = reinterpret_cast<const RecMix*>(a.jrec);
+        const float4* JA = reinterpret_cast<const float4*>(a.jacc);
+        const float eps2f = (float)a.eps2;
+        float sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f}, f[3] = {0.f, 0.f, 0.f};
+        if (active) {
+            int cnt = 0;
+            for (int j = js + g; j < je; j += G) {
+                const RecMix rj = J[j];
+                if constexpr (KIND == KIND_ACC)
+                    mix_acc_pair<DIAG>(rj.hi, rj.lo, p, eps2f, j == i, f[0], f[1], f[2]);
+                else
+                    mix_grad_pair<DIAG>(rj.hi, rj.lo, JA[j], p, eps2f, j == i, f[0], f[1], f[2]);
+                if (++cnt == 256) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) { ff_acc(sh[c], sl[c], f[c]); f[c] = 0.f; }
+                    cnt = 0;
+                }
+            }
+#pragma unroll
+            for (int c = 0; c < 3; ++c) ff_acc(sh[c], sl[c], f[c]);
+        }
+        // every lane of the warp takes part (inactive lanes add zeros)
+        for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                const float oh = __shfl_xor_sync(0xffffffffu, sh[c], o);
+                const float ol = __shfl_xor_sync(0xffffffffu, sl[c], o);
+                ff_acc(sh[c], sl[c], oh);
+                sl[c] = __fadd_rn(sl[c], ol);
+            }
+        if (!active || g != 0) return;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = (double)sh[c] + (double)sl[c];
+    } else {
+        const D4 ri = reinterpret_cast<const D4*>(a.irec)[i];
+        F64I p;
+        p.x = ri.x; p.y = ri.y; p.z = ri.z;
+        p.ax = p.ay = p.az = 0.0;
+        if constexpr (KIND == KIND_GRAD) {
+            const D4 ai = reinterpret_cast<const D4*>(a.iacc)[i];
+            p.ax = ai.x; p.ay = ai.y; p.az = ai.z;
+        }
+        const D4* J = reinterpret_cast<const D4*>(a.jrec);
+        const D4* JA = reinterpret_cast<const D4*>(a.jacc);
+        r[0] = r[1] = r[2] = 0.0;
+        if (active) {
+            for (int j = js + g; j < je; j += G) {
+                if constexpr (KIND == KIND_ACC)
+                    f64_acc_pair<DIAG>(J[j], p, a.eps2, j == i, r[0], r[1], r[2]);
+                else
+                    f64_grad_pair<DIAG>(J[j], JA[j], p, a.eps2, j == i, r[0], r[1], r[2]);
+            }
+        }
+        for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
+        if (!active || g != 0) return;
+    }
+    if (gridDim.y == 1) {
+        epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], record_mass<P>(a.irec, i), a.err);
+    } else {
+        double* part = a.part + (size_t)blockIdx.y * 3 * a.n_i;
+        part[i] = r[0];
+        part[(size_t)a.n_i + i] = r[1];
+        part[2 * (size_t)a.n_i + i] = r[2];
+    }
+}
+
+// =================================================================================
 // Symmetric pair kernel: the self-interaction of one set with every unordered pair
 // evaluated once (Newton's third law: the term of j on i and of i on j share the
 // separation, the reciprocal square root and the tidal factor).
@@ -1581,6 +1679,26 @@ cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int
     if (ipt >= 16) return cudaErrorInvalidValue;
     return kind == KIND_ACC ? launch_variant<FSI_FP64, KIND_ACC>(ipt, a, split, s)
                             : launch_variant<FSI_FP64, KIND_GRAD>(ipt, a, split, s);
+}
+
+template <int P, int KIND>
+cudaError_t launch_wide_t(bool diag, const PairArgs& a, int lg, int split, cudaStream_t s) {
+    const long long threads = (long long)a.n_i << lg;
+    const dim3 grid((unsigned)((threads + kThreads - 1) / kThreads), (unsigned)split);
+    if (diag) { wide_pair_kernel<P, KIND, true><<<grid, kThreads, 0, s>>>(a, lg); note_launch(); }
+    else { wide_pair_kernel<P, KIND, false><<<grid, kThreads, 0, s>>>(a, lg); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_pair(int precision, int kind, bool diag, const PairArgs& a, int lg,
+                             int split, cudaStream_t s) {
+    if (a.n_i <= 0) return cudaSuccess;
+    if (lg < 0 || lg > 5 || split < 1 || split > 65535) return cudaErrorInvalidValue;
+    if (precision == FSI_MIXED)
+        return kind == KIND_ACC ? launch_wide_t<FSI_MIXED, KIND_ACC>(diag, a, lg, split, s)
+                                : launch_wide_t<FSI_MIXED, KIND_GRAD>(diag, a, lg, split, s);
+    return kind == KIND_ACC ? launch_wide_t<FSI_FP64, KIND_ACC>(diag, a, lg, split, s)
+                            : launch_wide_t<FSI_FP64, KIND_GRAD>(diag, a, lg, split, s);
 }
 
 cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s) {

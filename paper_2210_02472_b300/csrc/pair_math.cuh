@@ -86,6 +86,16 @@ __device__ __forceinline__ void ff_add2(float4& acc, const float2 v) {
     acc = make_float4(s.x, s.y, lo.x, lo.y);
 }
 
+// Scalar float-float accumulation: (hi, lo) += v, TwoSum of Knuth (the exact rounding
+// error of hi + v goes into lo).
+__device__ __forceinline__ void ff_acc(float& hi, float& lo, float v) {
+    const float s = __fadd_rn(hi, v);
+    const float bb = __fsub_rn(s, hi);
+    const float e = __fadd_rn(__fsub_rn(hi, __fsub_rn(s, bb)), __fsub_rn(v, bb));
+    hi = s;
+    lo = __fadd_rn(lo, e);
+}
+
 // i-side state of a packed pair of particles (low half: particle 2p, high half: 2p+1).
 struct X2I {
     float2 nxh, nyh, nzh, nxl, nyl, nzl;   // -xh, -yh, -zh, -xl, -yl, -zl

@@ -86,12 +86,18 @@ def assert_close(got, ref, prec, what="", scale=None):
 
 
 # ----------------------------------------------------------------------------- acc
+# wide_ctas: 0 = default choice (small passes take the wide form), -1 = the tiled forms
+# only, 1 << 30 = the wide form for every unmasked pass (n = 2100: two source slices).
+WIDE = [0, -1, 1 << 30]
+
+
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("n", [2, 3, 255, 1024, 3001])
-def test_accel_same_set(F, prec, n):
+@pytest.mark.parametrize("n", [2, 3, 255, 1024, 2100, 3001])
+@pytest.mark.parametrize("wide", WIDE)
+def test_accel_same_set(F, prec, n, wide):
     c = inputs.plummer(n, 100 + n, imf="kroupa")
     ref = oracle.acc(c.pos, c.mass)
-    with F.Context(prec) as ctx:
+    with F.Context(prec, wide_ctas=wide) as ctx:
         got = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass)))
         assert F.fsi_sync_status(ctx) == F.FSI_OK
     assert_close(got, ref, prec, f"n={n}", abs_scale(c.pos, c.mass))
@@ -149,7 +155,7 @@ def test_split_factor_does_not_change_results(F, prec):
     c = inputs.plummer(5000, 11, imf="kroupa")
     outs = []
     for split in (1, 3, 7):
-        with F.Context(prec, split=split, symmetric=False) as ctx:
+        with F.Context(prec, split=split, symmetric=False, wide_ctas=-1) as ctx:
             outs.append(host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass))))
     for o in outs[1:]:
         e = rel_err(o, outs[0])
@@ -162,13 +168,23 @@ def test_symmetric_matches_one_sided(F, prec, n):
     """Every unordered pair once (Newton's third law) vs every ordered pair: the same sums
     up to rounding, for every kernel variant."""
     c = inputs.plummer(n, 41 + n, imf="kroupa")
-    with F.Context(prec, symmetric=False) as ctx:
+    with F.Context(prec, symmetric=False, wide_ctas=-1) as ctx:
         a1, g1 = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
         a1, g1 = host(a1), host(g1)
+    with F.Context(prec, wide_ctas=1 << 30) as ctx:          # the wide form
+        aw, gw = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
+        aw, gw = host(aw), host(gw)
+    if prec == "fp64":
+        assert rel_err(aw, a1).max() <= 1e-12
+    else:   # both forms within 1e-6 S_i of the exact sums (S_i = sum m_j / r_ij^2)
+        sc = abs_scale(c.pos, c.mass)
+        assert (np.abs(aw - a1).max(axis=0) / sc).max() <= 2e-6
+    eg = rel_err(gw, g1)
+    assert np.median(eg) <= (1e-12 if prec == "fp64" else 1e-4)
     variants = ((2, 2), (3, 3), (4, 4), (36, 36), (37, 37), (38, 37), (228, 228), (230, 230), (246, 246), (248, 248)) \
         if prec == "mixed" \
         else ((1, 1), (2, 2), (3, 3))
-    with F.Context(prec) as ctx:
+    with F.Context(prec, wide_ctas=-1) as ctx:
         for va, vg in variants:
             F.fsi_set_tuning(ctx, va, vg)
             v = (va, vg)
@@ -216,7 +232,8 @@ def assert_grad_close(got, ref, prec, scale):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("general", [False, True])
-def test_grad_given_field(F, prec, general):
+@pytest.mark.parametrize("wide", WIDE)
+def test_grad_given_field(F, prec, general, wide):
     n = 1500
     c = inputs.plummer(n, 12, imf="kroupa")
     accg = inputs.random_field(n, 13)
@@ -226,7 +243,7 @@ def test_grad_given_field(F, prec, general):
     else:
         A = B = None
     ref = oracle.grad(c.pos, c.mass, accg, A, B)
-    with F.Context(prec) as ctx:
+    with F.Context(prec, wide_ctas=wide) as ctx:
         Ad = ids(A)
         Bd = Ad if (A is None and B is None) else ids(B)
         got = host(F.fsi_grad(ctx, dev(c.pos), dev(c.mass), dev(accg), Ad, Bd))
@@ -421,13 +438,15 @@ def test_hhs_interval_gradient_criteria(F, prec, small):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("small", [0, -1, 64])
-def test_hhs_interval(F, prec, small):
+@pytest.mark.parametrize("wide", [0, -1])
+def test_hhs_interval(F, prec, small, wide):
     """One HHS interval against the oracle: the levels walked from the host (small = -1),
-    run inside one CTA once the fast set has <= 512 particles (0), or a mix (64)."""
+    run inside one CTA once the fast set has <= 512 particles (0), or a mix (64); the
+    host-walked passes in the wide form where it is chosen (wide = 0) or tiled only (-1)."""
     c = inputs.plummer(600, 22, imf="kroupa")
     tau = 1.0 / 16
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
-    with F.Context(prec, hhs_small_max=small) as ctx:
+    with F.Context(prec, hhs_small_max=small, wide_ctas=wide) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
