@@ -283,9 +283,13 @@ int choose_chunk(const fsi_ctx* c, int n, int ipt) {
 // source record per lane, where the tiled form broadcasts a staged tile).
 constexpr int kWideCtasDefault = 32;
 
+int wide_limit(const fsi_ctx* c) {
+    return c->p.wide_ctas < 0 ? 0 : (c->p.wide_ctas > 0 ? c->p.wide_ctas : kWideCtasDefault);
+}
+
 bool wide_plan(const fsi_ctx* c, int n_i, int n_j, int ipc, int& lg, int& split) {
     if (c->p.wide_ctas < 0) return false;
-    const long long limit = c->p.wide_ctas > 0 ? c->p.wide_ctas : kWideCtasDefault;
+    const long long limit = wide_limit(c);
     const long long tiled = (long long)((n_i + ipc - 1) / ipc) * choose_split(c, n_i, n_j, ipc);
     if (tiled >= limit) return false;
     lg = 5;
@@ -587,7 +591,8 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
         CU(launch_pack(FSI_MIXED, n, xc, mc, nullptr, n, c->rec[1].p, nullptr, s));
         CU(launch_pack_vel(n, vc, mc, c->accrec[1].p, s));
         CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
-                           c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c), c->sm_count, s));
+                           c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c), c->sm_count,
+                           wide_limit(c), s));
     }
     else
         CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,

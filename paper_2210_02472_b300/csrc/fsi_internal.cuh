@@ -319,7 +319,7 @@ cudaError_t launch_pack_vel(int n, const double* vc, const double* mc, void* vre
 size_t steps_x2_part_bytes(int n, int sm_count);
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                             double eta_fb, double eta_jerk, float* part, double* step, int* err,
-                            long long timeout_ns, int sm_count, cudaStream_t s);
+                            long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s);
 cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
                                    double eta_ff, double eta_fb, double eta_jerk, double eps2,
                                    void* rec_ws, void* vrec_ws, double* step, int* err,

@@ -31,12 +31,13 @@ constexpr int kStSmem = kStages * kStStage;
 constexpr int kStPart = 8;                       // ff, fb, ax, ay, az, jx, jy, jz
 }  // namespace
 
-__device__ __forceinline__ float2 rcp2(float2 v) {
-    float2 r;
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.x) : "f"(v.x));
-    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r.y) : "f"(v.y));
+__device__ __forceinline__ float rcp_hw(float v) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(v));
     return r;
 }
+
+__device__ __forceinline__ float2 rcp2(float2 v) { return make_float2(rcp_hw(v.x), rcp_hw(v.y)); }
 
 struct StepX2I {
     float2 nxh, nyh, nzh, nxl, nyl, nzl;   // -position splits of the two receivers
@@ -242,6 +243,71 @@ __global__ void steps_x2_finalize_kernel(const StepX2Args a, int split) {
     a.step[i] = step_from(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], a.eta_ff, a.eta_fb, a.eta_jerk);
 }
 
+// Wide form for sets too small for the tiled kernel to fill the GPU: 2^lg lanes per
+// receiver stride over the sources (records read through L1), then combine their minima
+// and sums by shuffles.  Per pair the arithmetic of step_pair_x2 on one receiver.
+template <bool SOFT>
+__global__ void __launch_bounds__(kStThreads) steps_wide_kernel(const StepX2Args a, int lg) {
+    const int G = 1 << lg;
+    const long long gt = (long long)blockIdx.x * kStThreads + threadIdx.x;
+    const int slot = (int)(gt >> lg);
+    const int g = (int)(gt & (G - 1));
+    const bool active = slot < a.n;
+    const int i = active ? slot : a.n - 1;
+    float ff = INFINITY, fb = INFINITY, ax = 0.f, ay = 0.f, az = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
+    bool coincident = false;
+    if (active) {
+        const RecMix ri = a.rec[i];
+        const float4 vi = a.vrec[i];
+        for (int j = g; j < a.n; j += G) {
+            const RecMix rj = a.rec[j];
+            const float4 vj = a.vrec[j];
+            const bool self = j == i;
+            const float dx = (rj.hi.x - ri.hi.x) + (rj.lo.x - ri.lo.x);
+            const float dy = (rj.hi.y - ri.hi.y) + (rj.lo.y - ri.lo.y);
+            const float dz = (rj.hi.z - ri.hi.z) + (rj.lo.z - ri.lo.z);
+            float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            d2 = self ? 1.0f : d2;
+            coincident |= d2 == 0.0f;
+            const float ux = vj.x - vi.x, uy = vj.y - vi.y, uz = vj.z - vi.z;
+            const float u2 = fmaf(ux, ux, fmaf(uy, uy, uz * uz));
+            const float s2 = SOFT ? d2 + a.eps2 : d2;
+            float y = rsqrt_hw(s2);
+            y = y * fmaf(s2 * -0.5f, y * y, 1.5f);
+            const float y2 = y * y;
+            float w = vj.w * (y2 * y);
+            const float r = d2 * (SOFT ? rsqrt_hw(d2) : y);
+            float tff = (d2 * r) * rcp_hw(vj.w + vi.w);
+            float tfb = d2 * rcp_hw(u2);
+            tff = self ? INFINITY : tff;
+            tfb = self ? INFINITY : tfb;
+            w = self ? 0.0f : w;
+            ff = fminf(ff, tff);
+            fb = fminf(fb, tfb);
+            const float rv = fmaf(dx, ux, fmaf(dy, uy, dz * uz));
+            const float c3 = (rv * y2) * -3.0f;
+            ax = fmaf(w, dx, ax); ay = fmaf(w, dy, ay); az = fmaf(w, dz, az);
+            jx = fmaf(w, fmaf(c3, dx, ux), jx);
+            jy = fmaf(w, fmaf(c3, dy, uy), jy);
+            jz = fmaf(w, fmaf(c3, dz, uz), jz);
+        }
+    }
+    if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
+    for (int o = G >> 1; o > 0; o >>= 1) {
+        ff = fminf(ff, __shfl_xor_sync(0xffffffffu, ff, o));
+        fb = fminf(fb, __shfl_xor_sync(0xffffffffu, fb, o));
+        ax += __shfl_xor_sync(0xffffffffu, ax, o);
+        ay += __shfl_xor_sync(0xffffffffu, ay, o);
+        az += __shfl_xor_sync(0xffffffffu, az, o);
+        jx += __shfl_xor_sync(0xffffffffu, jx, o);
+        jy += __shfl_xor_sync(0xffffffffu, jy, o);
+        jz += __shfl_xor_sync(0xffffffffu, jz, o);
+    }
+    if (!active || g != 0) return;
+    if (!(isfinite(ax) && isfinite(ay) && isfinite(az))) set_error(a.err, FSI_ERR_NONFINITE);
+    a.step[i] = step_from(ff, fb, ax, ay, az, jx, jy, jz, a.eta_ff, a.eta_fb, a.eta_jerk);
+}
+
 size_t steps_x2_part_bytes(int n, int sm_count) {
     const int nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
     const int want = (2 * sm_count + nb - 1) / nb;
@@ -251,12 +317,35 @@ size_t steps_x2_part_bytes(int n, int sm_count) {
 
 // rec, vrec: the set's mixed position records and FP32 velocity records (vx, vy, vz, m),
 // 16-byte aligned, n entries each.  part: steps_x2_part_bytes(n, sm_count) bytes.
+// wide_ctas: a set whose tiled launch would run fewer CTAs takes steps_wide_kernel.
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                             double eta_fb, double eta_jerk, float* part, double* step, int* err,
-                            long long timeout_ns, int sm_count, cudaStream_t s) {
+                            long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    static bool attr[2] = {false, false};
     const bool soft = eps2 > 0.0;
+    {
+        // tiled CTAs this set would get; below wide_ctas the wide form runs instead
+        const long long nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
+        const long long want = (2LL * sm_count + nb - 1) / nb;
+        const long long tiled = nb * std::max(1LL, std::min(want, (long long)(n + kStTile - 1) / kStTile));
+        if (tiled < wide_ctas) {
+            int lg = 5;
+            while (lg > 0 && (8 << lg) > n) --lg;
+            StepX2Args a{};
+            a.n = n;
+            a.rec = reinterpret_cast<const RecMix*>(rec);
+            a.vrec = reinterpret_cast<const float4*>(vrec);
+            a.eps2 = (float)eps2;
+            a.eta_ff = eta_ff; a.eta_fb = eta_fb; a.eta_jerk = eta_jerk;
+            a.step = step;
+            a.err = err;
+            const unsigned grid = (unsigned)((((long long)n << lg) + kStThreads - 1) / kStThreads);
+            if (soft) { steps_wide_kernel<true><<<grid, kStThreads, 0, s>>>(a, lg); note_launch(); }
+            else { steps_wide_kernel<false><<<grid, kStThreads, 0, s>>>(a, lg); note_launch(); }
+            return cudaGetLastError();
+        }
+    }
+    static bool attr[2] = {false, false};
     if (!attr[soft]) {
         cudaError_t e = soft ? cudaFuncSetAttribute(steps_x2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem)
                              : cudaFuncSetAttribute(steps_x2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem);

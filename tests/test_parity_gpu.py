@@ -382,13 +382,24 @@ def test_timesteps_and_energy(F):
     assert abs(e[0] / T - 1) < 1e-13 and abs(e[1] / W - 1) < 1e-12
 
 
-def test_timesteps_mixed(F):
-    c = inputs.plummer(3000, 23, imf="kroupa")
-    ref = oracle.timesteps(c.pos, c.vel, c.mass)
-    with F.Context("mixed") as ctx:
+@pytest.mark.parametrize("n", [2, 3, 257, 3000])
+@pytest.mark.parametrize("wide", WIDE)
+@pytest.mark.parametrize("eps2", [0.0, 1e-4])
+def test_timesteps_mixed(F, n, wide, eps2):
+    """Mixed time steps against the oracle: the tiled packed kernel, the wide form (small
+    sets by default, every set with wide = 1 << 30), softened and not, and a subset."""
+    c = inputs.plummer(n, 23 + n, imf="kroupa")
+    ref = oracle.timesteps(c.pos, c.vel, c.mass, eps2=eps2)
+    P = inputs.random_subset(n, max(1, n // 3), 9)
+    refp = oracle.timesteps(c.pos, c.vel, c.mass, P, eps2=eps2)
+    with F.Context("mixed", eps2=eps2, wide_ctas=wide) as ctx:
         s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+        sp = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P)))
         assert F.fsi_sync_status(ctx) == F.FSI_OK
-    assert np.abs(s / ref - 1).max() < 2e-5
+    for got, want in ((s, ref), (sp, refp)):
+        fin = np.isfinite(want)                 # a lone particle has no bound: +inf
+        assert np.array_equal(np.isfinite(got), fin)
+        assert np.all(np.abs(got[fin] / want[fin] - 1) < 2e-5)
 
 
 @pytest.mark.parametrize("prec", PRECS)
