@@ -542,6 +542,8 @@ def run_hhs(args):
     kw = dict(eps2=SOFT_EPS ** 2, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eta_grad=0.1) if soft else {}
     ctx = F.Context(args.precision, c=cl, wide_ctas=args.wide_ctas,
                     hhs_small_max=args.hhs_small_max, **kw)
+    if args.tuning:
+        F.fsi_set_tuning(ctx, *[int(v) for v in args.tuning.split(",")])
     energy = lambda: float(F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum())
     e0 = energy()
     F.fsi_work_stats(ctx, reset=True)
@@ -572,6 +574,7 @@ def run_hhs(args):
         "data": "synthetic",
         "config": {"workload": wl, "n": c.n, "tau": tau, "intervals": args.intervals, "c": cl,
                    "wide_ctas": args.wide_ctas, "hhs_small_max": args.hhs_small_max,
+                   "tuning": args.tuning or "default",
                    **({"eps2": SOFT_EPS ** 2, "eta": "ff 0.2, fb 0.2, jerk 0.1, gradient 0.1",
                        "units": f"length {SOFT_LUNIT_PC:.4f} pc, time {SOFT_TUNIT_MYR:.4f} Myr"}
                       if soft else {})},
