@@ -673,6 +673,69 @@ def run_accgrad(args):
     return 0
 
 
+def run_update(args):
+    """The fused kick/drift update (fsi_kick_drift, FP64) on a state larger than L2:
+    N = --update-n particles (default 2^25: x, v and a are 805 MB each), every particle
+    (contiguous SoA rows) and a sorted half of them through an id list (the gather/scatter
+    pattern of a level set).  Algorithmic bytes: read a, v, x and write v, x (120 B per
+    particle) + 4 B per id; reported against the measured HBM copy bandwidth.  Each case
+    times max(--steps, 400) launches."""
+    import torch
+    from paper_2210_02472_b300 import fsi as F
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    N = args.update_n
+    g = torch.Generator(device=dev)
+    g.manual_seed(inputs.SEED_BASE + 7)
+    pos = torch.rand((3, N), dtype=torch.float64, device=dev, generator=g)
+    vel = torch.rand((3, N), dtype=torch.float64, device=dev, generator=g)
+    acc_all = torch.rand((3, N), dtype=torch.float64, device=dev, generator=g)
+    keep = torch.rand(N, device=dev, generator=g) < 0.5
+    ids = torch.nonzero(keep).flatten().to(torch.int32).contiguous()
+    acc_ids = torch.rand((3, ids.numel()), dtype=torch.float64, device=dev, generator=g)
+    ctx = F.Context("fp64")
+    peaks = measured_peaks()
+    hbm = float(peaks.get("hbm_gbs") or 6400.0)
+    res = {}
+    sampler = ClockSampler(0)
+    steps = max(args.steps, 400)        # >= ~0.25 s timed, so the 200 ms clock samples see it
+    for name, idx, acc, bpp in (("all", None, acc_all, 120.0), ("ids", ids, acc_ids, 124.0)):
+        n = N if idx is None else idx.numel()
+        for _ in range(max(3, args.warmup)):
+            F.fsi_kick_drift(ctx, pos, vel, acc, 1e-9, 1e-9, idx=idx)
+        torch.cuda.synchronize()
+        if name == "all":
+            sampler.start()
+        e0, e1 = _timed_events(None)
+        e0.record()
+        for _ in range(steps):
+            F.fsi_kick_drift(ctx, pos, vel, acc, 1e-9, 1e-9, idx=idx)
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) / 1e3 / steps
+        gbs = bpp * n / t / 1e9
+        res[name] = {"n": n, "ms_per_launch": 1e3 * t, "particles_per_s": n / t,
+                     "achieved_gbs": gbs, "frac_of_measured_hbm": gbs / hbm}
+    clocks = sampler.stop()
+    assert F.fsi_sync_status(ctx) == F.FSI_OK
+    a = res["all"]
+    line = {
+        "metric": f"kick+drift particle updates/s (N = {N}, FP64 state, contiguous)",
+        "value": a["particles_per_s"], "unit": "particles/s", "n_gpus": 1, "steps": steps,
+        "warmup": max(3, args.warmup), "ms_per_step": a["ms_per_launch"], "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": f"state_{N}", "n": N, "bytes_per_particle": "120 (124 with ids)",
+                   "l2": "inputs 805 MB per array, > L2"},
+        "roofline": {"bound": "hbm", "achieved": a["achieved_gbs"], "peak": hbm, "unit": "GB/s",
+                     "frac": a["frac_of_measured_hbm"], "traffic": None,
+                     "peak_source": "MEASURED_PEAKS.json hbm_gbs" if peaks.get("hbm_gbs") else "fallback"},
+        "id_list": res["ids"], "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -689,7 +752,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--tuning", default="", help="fixed pair-kernel variants 'acc,grad' "
                     "(see fsi_set_tuning); default: autotune on a 2^18 sample")
-    ap.add_argument("--mode", default="cycle", choices=["cycle", "ensemble", "vjp", "hhs", "accgrad"],
+    ap.add_argument("--mode", default="cycle",
+                    choices=["cycle", "ensemble", "vjp", "hhs", "accgrad", "update"],
                     help="cycle: the headline FSI-cycle benchmark; the others measure the "
                          "ensemble, adjoint and HHS workloads and one acc + grad pass")
     ap.add_argument("--batch-steps", type=int, default=10)
@@ -698,6 +762,8 @@ def main():
     ap.add_argument("--vjp-steps", type=int, default=200)
     ap.add_argument("--fd-components", type=int, default=3)
     ap.add_argument("--intervals", type=int, default=1)
+    ap.add_argument("--update-n", type=int, default=1 << 25,
+                    help="update mode: particles in the state (default 2^25)")
     ap.add_argument("--tau", type=float, default=1.0 / 64)
     ap.add_argument("--hhs-pn", action="store_true", help="HHS mode: PN1.0 on (c = 1e4)")
     ap.add_argument("--wide-ctas", type=int, default=0, help="HHS mode: fsi_params.wide_ctas "
@@ -714,6 +780,8 @@ def main():
         return run_hhs(args)
     if args.mode == "accgrad":
         return run_accgrad(args)
+    if args.mode == "update":
+        return run_update(args)
     return run_fsi(args)
 
 

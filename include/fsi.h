@@ -180,6 +180,18 @@ int fsi_step(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
              const unsigned char *is_bh, const int *idx, int n, double h, int nsteps,
              void *stream);
 
+/* Kick then drift of the set idx with given accelerations (the kinetic and potential
+ * factors of Sect. 2.1, Eq. fsi-cycle, applied on their own): for k < n, i = idx[k]
+ * (idx NULL: i = k and n <= N),
+ *   vel[:, i] += c_kick * acc[:, k],   then   pos[:, i] += c_drift * vel[:, i],
+ * every operation an FP64 FMA.  pos, vel: 3 x N device arrays, updated in place; acc:
+ * 3 x n compact device rows (NULL: drift only); idx: n device ids in [0, N) without
+ * repeats (not checked: a repeated id races).  HBM-bound: 120 B per particle moved
+ * (124 B with idx).  Asynchronous on `stream`; FSI_ERR_ARG for a NULL state array or a
+ * bad n. */
+int fsi_kick_drift(fsi_ctx *ctx, int N, double *pos, double *vel, const double *acc,
+                   const int *idx, int n, double c_kick, double c_drift, void *stream);
+
 /* Adjoint of one fsi_step cycle (PN off): given the input state (pos0, vel0; 3 x N) of
  * a cycle of step h on the set idx (n ids, NULL = all) and the cotangents gx_out, gv_out
  * (3 x N) of its output state, writes the cotangents of the input state into gx_in,

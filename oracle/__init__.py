@@ -98,6 +98,7 @@ def lib():
                                   dp, dp]
         L.or_fsi_step_vjp.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int, C.c_double, C.c_double,
                                       dp, dp, dp, dp, dp]
+        L.or_kick_drift.argtypes = [C.c_int, dp, dp, dp, ip, C.c_int, C.c_double, C.c_double]
         L.or_set_threads.argtypes = [C.c_int]
         L.or_get_threads.restype = C.c_int
         _lib = L
@@ -204,6 +205,18 @@ def fsi_step(pos, vel, mass, h, P=None, eps2=0.0, c=0.0, is_bh=None, steps=1):
     for _ in range(steps):
         _check(lib().or_fsi_step(N, _d(pos), _d(vel), _d(mass), _i(P), _n(P, N), float(h),
                                  C.byref(fp)), "fsi_step")
+    return pos, vel
+
+
+def kick_drift(pos, vel, acc, c_kick, c_drift, P=None):
+    """Return (pos, vel) after v_i += c_kick a_k, then x_i += c_drift v_i for i = P[k]
+    (copies; acc: 3 x n compact rows or None for a drift only)."""
+    pos, vel, P = _f64(pos).copy(), _f64(vel).copy(), _idx(P)
+    N = pos.shape[1]
+    n = _n(P, N)
+    a = None if acc is None else _f64(acc)
+    _check(lib().or_kick_drift(N, _d(pos), _d(vel), None if a is None else _d(a), _i(P), n,
+                               float(c_kick), float(c_drift)), "kick_drift")
     return pos, vel
 
 

@@ -336,6 +336,28 @@ static int pn_kick(int N, const double *pos, double *vel, const double *mass,
 }
 
 /* ------------------------------------------------------------------------------- *
+ * Kick then drift of the listed set with given accelerations (the kinetic and potential
+ * factors of Eq. fsi-cycle applied on their own): for k < n, i = P[k] (P NULL: i = k),
+ *   v_i <- v_i + c_kick a_k,   then   x_i <- x_i + c_drift v_i.
+ * acc: 3 x n compact rows (NULL: drift only).
+ * ------------------------------------------------------------------------------- */
+int or_kick_drift(int N, double *pos, double *vel, const double *acc, const int *P, int n,
+                  double c_kick, double c_drift) {
+    if (N < 0 || n < 0 || (!P && n > N)) return OR_ERR_ARG;
+    for (int k = 0; k < n; ++k) {
+        const int i = P ? P[k] : k;
+        if (i < 0 || i >= N) return OR_ERR_ARG;
+        for (int c = 0; c < 3; ++c) {
+            double v = vel[(size_t)c * N + i];
+            if (acc) v = v + c_kick * acc[(size_t)c * n + k];
+            vel[(size_t)c * N + i] = v;
+            pos[(size_t)c * N + i] = pos[(size_t)c * N + i] + c_drift * v;
+        }
+    }
+    return OR_OK;
+}
+
+/* ------------------------------------------------------------------------------- *
  * One FSI cycle of step h on the listed set, interacting with itself only
  * (Sect. 2.1, Eq. fsi-cycle):
  *   kick h/6 with a;  drift h/2;  kick 2h/3 with a~ = a + (h^2/24) G;  drift h/2;

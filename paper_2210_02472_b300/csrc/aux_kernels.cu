@@ -1,6 +1,8 @@
 // aux_kernels.cu -- O(n) and small O(n^2) kernels around the pair passes:
 // record packing (gather), scatter, kick/drift, PN1.0 pair kicks, time steps, energy,
 // set checks.
+#include <algorithm>
+
 #include "fsi_internal.cuh"
 #include "pair_math.cuh"
 
@@ -236,6 +238,36 @@ cudaError_t launch_kick_drift(int precision, int n, double* xc, double* vc, cons
         { kick_drift_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, mc, rec_out); note_launch(); }
     else
         { kick_drift_kernel<FSI_FP64><<<blocks_for(n), kB, 0, s>>>(n, xc, vc, ac, c_kick, c_drift, mc, rec_out); note_launch(); }
+    return cudaGetLastError();
+}
+
+// Kick then drift of a listed set in the global SoA state (grid-stride):
+//   v[:, i] += c_kick a[:, k];  x[:, i] += c_drift v[:, i];  i = idx[k] (idx null: i = k).
+__global__ void kick_drift_ids_kernel(long long N, double* __restrict__ pos,
+                                      double* __restrict__ vel, const double* __restrict__ acc,
+                                      const int* __restrict__ idx, int n, double c_kick,
+                                      double c_drift) {
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n;
+         k += (long long)gridDim.x * blockDim.x) {
+        const long long i = idx ? (long long)idx[k] : k;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double v = vel[c * N + i];
+            if (acc) v = fma(c_kick, acc[c * (long long)n + k], v);
+            vel[c * N + i] = v;
+            pos[c * N + i] = fma(c_drift, v, pos[c * N + i]);
+        }
+    }
+}
+
+cudaError_t launch_kick_drift_ids(long long N, double* pos, double* vel, const double* acc,
+                                  const int* idx, int n, double c_kick, double c_drift,
+                                  int sm_count, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    // 8 CTAs of 256 per SM (full occupancy at <= 32 registers), at most one per 256 ids
+    const long long want = (long long)sm_count * 8;
+    const int grid = (int)std::min<long long>(want, (n + kB - 1) / kB);
+    { kick_drift_ids_kernel<<<grid, kB, 0, s>>>(N, pos, vel, acc, idx, n, c_kick, c_drift); note_launch(); }
     return cudaGetLastError();
 }
 

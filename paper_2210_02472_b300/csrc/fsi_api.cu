@@ -1018,6 +1018,16 @@ int fsi_step(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     return step_core(c, N, pos, vel, mass, is_bh, idx, n, h, nsteps, S(stream));
 }
 
+int fsi_kick_drift(fsi_ctx* c, int N, double* pos, double* vel, const double* acc,
+                   const int* idx, int n, double c_kick, double c_drift, void* stream) {
+    CK(check_common(c, N));
+    if (n < 0 || (!idx && n > N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (n == 0) return FSI_OK;
+    if (!pos || !vel) return fail(FSI_ERR_ARG, "NULL array");
+    CU(launch_kick_drift_ids(N, pos, vel, acc, idx, n, c_kick, c_drift, c->sm_count, S(stream)));
+    return FSI_OK;
+}
+
 int fsi_step_sub(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
                  const int* idx, int n, const int* pairs, int n_pairs, double h, int nsteps,
                  void* stream) {

@@ -216,6 +216,10 @@ cudaError_t launch_fma_probe(int fp64, int blocks, int iters, void* sink, cudaSt
 // accumulates its tile partials as float-float pairs (see pair_variants).
 cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int split,
                         cudaStream_t s);
+// fsi_kick_drift's kernel (global SoA state, optional id list).
+cudaError_t launch_kick_drift_ids(long long N, double* pos, double* vel, const double* acc,
+                                  const int* idx, int n, double c_kick, double c_drift,
+                                  int sm_count, cudaStream_t s);
 cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaStream_t s);
 // Wide one-sided pass (2^lg lanes per receiver, split source slices); split == 1 applies
 // the epilogue itself, split > 1 writes a.part for launch_finalize_p.

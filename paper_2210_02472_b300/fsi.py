@@ -36,7 +36,7 @@ FSI_MIXED = 1
 
 EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params", "fsi_reserve",
             "fsi_last_error", "fsi_sync_status", "fsi_accel", "fsi_grad", "fsi_accel_grad",
-            "fsi_pn_accel", "fsi_step", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
+            "fsi_pn_accel", "fsi_step", "fsi_kick_drift", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
             "fsi_level_stats", "fsi_hhs_interval_restart", "fsi_step_sub", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
@@ -66,6 +66,7 @@ _lib.fsi_grad.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp,
 _lib.fsi_accel_grad.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp, _vp, _vp]
 _lib.fsi_pn_accel.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp, _ip, _vp, _ip, _vp, _vp]
 _lib.fsi_step.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _vp, _ip, _dp, _ip, _vp]
+_lib.fsi_kick_drift.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _dp, _vp]
 _lib.fsi_timesteps.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
 _lib.fsi_energy.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
 _lib.fsi_hhs_interval.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp]
@@ -252,6 +253,18 @@ def fsi_step(ctx: Context, pos, vel, mass, h: float, nsteps: int = 1, is_bh=None
     _check(_lib.fsi_step(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
                          _f64(mass, (N,), "mass"), _u8(is_bh, N, "is_bh"), pi, n, float(h),
                          int(nsteps), _stream(stream)), "fsi_step")
+
+
+def fsi_kick_drift(ctx: Context, pos, vel, acc, c_kick: float, c_drift: float, idx=None,
+                   stream=None) -> None:
+    """In place: vel[:, i] += c_kick acc[:, k], then pos[:, i] += c_drift vel[:, i] for
+    i = idx[k] (all particles when idx is None); acc (3, n) or None for a drift only."""
+    N = pos.shape[1]
+    pi, n = _ids(idx, N, "idx")
+    pa = None if acc is None else _f64(acc, (3, n), "acc")
+    _check(_lib.fsi_kick_drift(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                               pa, pi, n, float(c_kick), float(c_drift), _stream(stream)),
+           "fsi_kick_drift")
 
 
 def fsi_timesteps(ctx: Context, pos, vel, mass, P=None, out=None, stream=None):

@@ -586,3 +586,44 @@ def test_subsystem_step_is_fourth_order_and_conserves_momentum():
         assert np.abs((m * v).sum(axis=1) - (m * vel).sum(axis=1)).max() <= 1e-15
     for r in (errs[0] / errs[1], errs[1] / errs[2]):
         assert 12.0 < r < 20.0, errs
+
+
+# ----------------------------------------------------------------------------- kick / drift
+def test_kick_drift_exact_dyadic_closed_form():
+    """v' = v + c_k a and x' = x + c_d v' on dyadic numbers, where every operation is
+    exact: the oracle must reproduce the closed form bit for bit, only on the listed ids."""
+    pos = np.array([[1.5, -2.0, 0.75], [0.25, 4.0, -1.0], [3.0, 0.5, 2.0]])
+    vel = np.array([[0.25, 1.0, -0.5], [-0.75, 0.0, 2.0], [0.5, -1.5, 0.125]])
+    P = np.array([2, 0], dtype=np.int32)
+    acc = np.array([[-2.0, 4.0], [1.0, 0.5], [0.0, -8.0]])     # rows for ids 2, 0
+    ck, cd = 0.5, 0.125
+    p, v = oracle.kick_drift(pos, vel, acc, ck, cd, P)
+    ev, ex = vel.copy(), pos.copy()
+    for k, i in enumerate(P):
+        ev[:, i] = vel[:, i] + ck * acc[:, k]
+        ex[:, i] = pos[:, i] + cd * ev[:, i]
+    assert np.array_equal(v, ev) and np.array_equal(p, ex)
+    assert v[0, 2] == -0.5 - 1.0 and p[0, 2] == 0.75 + 0.125 * -1.5
+    assert np.array_equal(p[:, 1], pos[:, 1]) and np.array_equal(v[:, 1], vel[:, 1])
+    # drift only: x + c_d v
+    p2, v2 = oracle.kick_drift(pos, vel, None, 0.0, 0.25)
+    assert np.array_equal(v2, vel) and np.array_equal(p2, pos + 0.25 * vel)
+
+
+def test_fsi_cycle_is_its_kick_and_drift_factors():
+    """Eq. fsi-cycle as a product of kicks and drifts: kick h/6 (a), drift h/2, kick 2h/3
+    with a + (h^2/24) G, drift h/2, kick h/6 (a), each a from the current positions,
+    composed from the oracle's kick_drift, acc and grad, equals the oracle's fsi_step."""
+    c = inputs.plummer(40, 31, imf="kroupa")
+    h = 1e-3
+    x, v = c.pos.copy(), c.vel.copy()
+    a = np.asarray(oracle.acc(x, c.mass))
+    x, v = oracle.kick_drift(x, v, a, h / 6, h / 2)
+    a = np.asarray(oracle.acc(x, c.mass))
+    G = np.asarray(oracle.grad(x, c.mass, a))
+    x, v = oracle.kick_drift(x, v, a + h * h / 24 * G, 2 * h / 3, h / 2)
+    a = np.asarray(oracle.acc(x, c.mass))
+    x, v = oracle.kick_drift(x, v, a, h / 6, 0.0)
+    rp, rv = oracle.fsi_step(c.pos, c.vel, c.mass, h)
+    assert np.abs(x - rp).max() <= 1e-15 * np.abs(rp).max()
+    assert np.abs(v - rv).max() <= 1e-14 * np.abs(rv).max()

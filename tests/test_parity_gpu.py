@@ -366,6 +366,41 @@ def test_pn_accel_pairs(F):
     assert_close(got, ref, "fp64")
 
 
+# ----------------------------------------------------------------------------- kick / drift
+@pytest.mark.parametrize("case", ["all", "ids", "drift", "empty"])
+def test_kick_drift_matches_oracle(F, case):
+    """fsi_kick_drift against the oracle's kick/drift: every particle, a sorted id subset,
+    a drift without kick, no ids.  FP64 FMAs against separate roundings: <= 2 ulp."""
+    N = 5003
+    c = inputs.plummer(N, 27)
+    rng = np.random.default_rng(28)
+    P = {"all": None, "ids": np.sort(inputs.random_subset(N, 1777, 29)).astype(np.int32),
+         "drift": None, "empty": np.zeros(0, np.int32)}[case]
+    n = N if P is None else len(P)
+    acc = None if case == "drift" else rng.standard_normal((3, n))
+    ck, cd = 0.3, 0.7
+    rp, rv = oracle.kick_drift(c.pos, c.vel, acc, ck, cd, P)
+    with F.Context("fp64") as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        F.fsi_kick_drift(ctx, p, v, None if acc is None else dev(acc), ck, cd,
+                         idx=None if P is None else dev(P, torch.int32))
+        p, v = host(p), host(v)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    # one FMA against a product and a sum rounded apart: |dv| <= u (|v'| + |c_k a|) per
+    # entry, and dx <= u (|x'| + |c_d v'|) + c_d |dv|  (u = 2^-53; bounds taken at 4 u)
+    u = 4 * 2.0 ** -53
+    A = np.zeros_like(c.vel)
+    if acc is not None:
+        A[:, slice(None) if P is None else P] = np.abs(ck * acc)
+    bv = u * (np.abs(rv) + A)
+    assert np.all(np.abs(v - rv) <= bv)
+    assert np.all(np.abs(p - rp) <= u * (np.abs(rp) + cd * np.abs(rv)) + cd * bv)
+    if P is not None:
+        others = np.setdiff1d(np.arange(N), P)
+        assert np.array_equal(p[:, others], c.pos[:, others])
+        assert np.array_equal(v[:, others], c.vel[:, others])
+
+
 # ----------------------------------------------------------------------------- misc
 def test_timesteps_and_energy(F):
     c = inputs.plummer(1500, 21, imf="kroupa")
