@@ -410,6 +410,7 @@ def run_ensemble(args):
     flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     sampler = ClockSampler(0)
     sampler.start()
+    F.fsi_batch_stats(b, reset=True)
     ms = []
     for _ in range(args.steps):
         flush.zero_()
@@ -420,8 +421,14 @@ def run_ensemble(args):
         torch.cuda.synchronize()
         ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
+    wait_ns, life_ns, ctas = F.fsi_batch_stats(b)
     assert F.fsi_sync_status(ctx) == F.FSI_OK
     t = sum(ms) / 1e3
+    # idle: CTA time spent waiting for other CTAs' phases, plus CTAs out of work before the
+    # launch ended, over the launch's whole CTA capacity (CTAs x elapsed time)
+    cap_ns = ctas * t * 1e9
+    idle = {"fraction": 1.0 - (life_ns - wait_ns) / cap_ns, "phase_waits": wait_ns / cap_ns,
+            "tail": 1.0 - life_ns / cap_ns, "ctas": ctas}
     value = per_call * args.steps / t
     ach = value * FLOP_PAIR / 1e12
     peak = fp32_peak_tflops() if args.precision == "mixed" else args.fp64_peak_tflops
@@ -440,6 +447,7 @@ def run_ensemble(args):
         "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": ach / peak, "traffic": None,
                      "kernel": "batch_sym_kernel" if best[1][0] == 4 else "batch_kernel"},
+        "idle": idle,
         "clocks": clocks,
     }
     print(json.dumps(line), flush=True)

@@ -294,6 +294,15 @@ int fsi_batch_step(fsi_ctx *ctx, fsi_batch *batch, double *pos, double *vel,
 int fsi_batch_set_tuning(fsi_ctx *ctx, fsi_batch *batch, int ipt, int ctas_per_sm);
 int fsi_batch_get_tuning(fsi_batch *batch, int *ipt, int *ctas_per_sm);
 
+/* Idle accounting of the batch's persistent launches since the last reset (load balance
+ * across clusters of uneven size): *wait_ns = time the CTAs spent waiting for other CTAs'
+ * phases, *life_ns = summed CTA lifetimes (start to leaving the work loop), *ctas = CTAs
+ * of the last launch.  With the launches' summed elapsed time T, the idle fraction is
+ * 1 - (life_ns - wait_ns) / (ctas T): waits inside CTAs plus CTAs out of work before the
+ * launch ends.  Synchronises the device; reset != 0 zeroes the counters after reading. */
+int fsi_batch_stats(fsi_batch *batch, long long *wait_ns, long long *life_ns, int *ctas,
+                    int reset);
+
 /* Test hook: during the next fsi_batch_step the items of `cluster` wait for a phase
  * count that is never reached, so their bounded waits run out and the launch ends with
  * FSI_ERR_TIMEOUT latched (read by fsi_sync_status) instead of hanging.  The next step

@@ -59,6 +59,16 @@ __device__ __forceinline__ int phase_role(int p) {
     return 2 + (p - 2) % 3;
 }
 
+// Idle accounting (fsi_batch_stats): thread 0 of every CTA adds the time it spent waiting
+// for other CTAs' phases and its lifetime when it leaves the persistent loop.
+__device__ __forceinline__ void batch_stats_exit(const BatchArgs& a, long long t_start,
+                                                 long long waited) {
+    if (threadIdx.x == 0 && a.stats) {
+        atomicAdd(a.stats, (unsigned long long)waited);
+        atomicAdd(a.stats + 1, (unsigned long long)(global_ns() - t_start));
+    }
+}
+
 template <int P, int I>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs a) {
     constexpr int JREC = 32;
@@ -68,6 +78,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
     __shared__ int s_item, s_flag;
     const int tid = threadIdx.x;
     const long long N = a.ntot;
+    const long long t_start = global_ns();
+    long long waited = 0;
 
     while (true) {
         if (tid == 0) {
@@ -78,7 +90,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
         __syncthreads();
         const int t = s_item;
         __syncthreads();
-        if (t < 0) return;
+        if (t < 0) { batch_stats_exit(a, t_start, waited); return; }
         const int p = t / a.items_per_phase;
         const BatchItem it = a.items[t % a.items_per_phase];
         const int role = phase_role(p);
@@ -100,12 +112,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
                         }
                         __nanosleep(64);
                     }
+                    waited += global_ns() - t0;
                 }
                 __threadfence();
                 s_flag = flag;
             }
             __syncthreads();
-            if (s_flag) return;
+            if (s_flag) { batch_stats_exit(a, t_start, waited); return; }
         }
         const int ib = it.block * (kBatchThreads * I);        // first i of the block (local)
         // ---- phase 0: pack records of the block from x
@@ -598,6 +611,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
     float4* acc_s = reinterpret_cast<float4*>(smem + kStages * kBSStage + kBSJpart);
     const int tid = threadIdx.x;
     const long long N = a.ntot;
+    const long long t_start = global_ns();
+    long long waited = 0;
     const int nA = a.items_per_phase;
     const int npass = 1 + 3 * a.nsteps;
     const long long total = (long long)nA + (long long)npass * (long long)(nS + nA);
@@ -616,7 +631,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
         __syncthreads();
         const int t = s_item;
         __syncthreads();
-        if (t < 0) return;
+        if (t < 0) { batch_stats_exit(a, t_start, waited); return; }
         int phase, pass = -1, r = t;
         bool is_sum = false;
         if (t >= nA) {
@@ -649,12 +664,13 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
                         }
                         __nanosleep(64);
                     }
+                    waited += global_ns() - t0;
                 }
                 __threadfence();
                 s_flag = flag;
             }
             __syncthreads();
-            if (s_flag) return;
+            if (s_flag) { batch_stats_exit(a, t_start, waited); return; }
         }
         const int role = phase == 0 ? 0 : (pass == 0 ? 1 : 2 + (pass - 1) % 3);
         if (phase == 0) {
@@ -680,6 +696,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
                 : batch_sum_item<KIND_ACC>(a, it, rin, accum, smem, bars, jpart, acc_s, g);
             if (!ok) {
                 if (tid == 0) atomicExch(a.abort_flag, 1);
+                batch_stats_exit(a, t_start, waited);
                 return;
             }
         } else {

@@ -706,6 +706,8 @@ struct fsi_batch {
     Buf sitems, nsum, accum;         // symmetric form: sum items, sum items per cluster
     int sitems_per_phase = 0;
     Buf rec0, rec1, accrec, ac, done, ctrl;
+    Buf stats;                       // idle accounting: wait ns, CTA lifetime ns
+    int last_ctas = 0;
     std::vector<long long> off;
 };
 
@@ -1449,6 +1451,9 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
     if (rc == FSI_OK) rc = ensure(b->ac, 3 * (size_t)ntot * 8);
     if (rc == FSI_OK) rc = ensure(b->done, (size_t)K * nphase * sizeof(int));
     if (rc == FSI_OK) rc = ensure(b->ctrl, 64);
+    if (rc == FSI_OK) rc = ensure(b->stats, 2 * sizeof(unsigned long long));
+    if (rc == FSI_OK && cudaMemset(b->stats.p, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+        rc = fail(FSI_ERR_CUDA, "batch counters");
     if (rc == FSI_OK) {
         b->ctas_per_sm = std::max(1, batch_max_ctas_per_sm(c->p.precision, b->ipt));
         *out = b;
@@ -1463,7 +1468,7 @@ int fsi_batch_destroy(fsi_batch* b) {
     cudaDeviceSynchronize();
     Buf* bufs[] = {&b->items[1], &b->items[2], &b->items[kBatchSymI], &b->nblocks[1], &b->nblocks[2],
                    &b->nblocks[kBatchSymI], &b->sitems, &b->nsum, &b->accum, &b->rec0, &b->rec1,
-                   &b->accrec, &b->ac, &b->done, &b->ctrl};
+                   &b->accrec, &b->ac, &b->done, &b->ctrl, &b->stats};
     for (Buf* x : bufs)
         if (x->p) cudaFree(x->p);
     delete b;
@@ -1488,6 +1493,20 @@ int fsi_batch_get_tuning(fsi_batch* b, int* ipt, int* ctas_per_sm) {
     if (!b) return fail(FSI_ERR_ARG, "NULL batch");
     if (ipt) *ipt = b->ipt;
     if (ctas_per_sm) *ctas_per_sm = b->ctas_per_sm;
+    return FSI_OK;
+}
+
+int fsi_batch_stats(fsi_batch* b, long long* wait_ns, long long* life_ns, int* ctas, int reset) {
+    if (!b) return fail(FSI_ERR_ARG, "NULL batch");
+    unsigned long long st[2] = {0, 0};
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(st, b->stats.p, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(FSI_ERR_CUDA, "batch counters read");
+    if (reset && cudaMemset(b->stats.p, 0, sizeof st) != cudaSuccess)
+        return fail(FSI_ERR_CUDA, "batch counters reset");
+    if (wait_ns) *wait_ns = (long long)st[0];
+    if (life_ns) *life_ns = (long long)st[1];
+    if (ctas) *ctas = b->last_ctas;
     return FSI_OK;
 }
 
@@ -1535,11 +1554,13 @@ int fsi_batch_step(fsi_ctx* c, fsi_batch* b, double* pos, double* vel, const dou
     a.done = P<int>(b->done);
     a.next = P<int>(b->ctrl);
     a.abort_flag = P<int>(b->ctrl) + 4;
+    a.stats = P<unsigned long long>(b->stats);
     a.h = h;
     a.eps2 = c->p.eps2;
     a.err = c->err_d;
     a.timeout_ns = budget(c);
     const int ctas = c->sm_count * b->ctas_per_sm;
+    b->last_ctas = ctas;
     if (sym) {
         CU(cudaMemsetAsync(b->accum.p, 0, 3 * (size_t)b->ntot * sizeof(double), s));
         CU(launch_batch_sym(ctas, a, reinterpret_cast<const BatchSymItem*>(b->sitems.p),

@@ -176,6 +176,7 @@ struct BatchArgs {
     void* rec1;
     void* accrec;
     double* ac;                  // 3 x Ntot, FP64 accelerations of the gradient pass
+    unsigned long long* stats;   // [0] += wait ns, [1] += CTA lifetime ns (may be null)
     int* done;                   // K x nphase, zeroed before the launch
     int* next;                   // work counter, zeroed
     int* abort_flag;             // zeroed

@@ -40,7 +40,7 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_level_stats", "fsi_hhs_interval_restart", "fsi_step_sub", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
-            "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall",
+            "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall", "fsi_batch_stats",
             "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for"]
 
 
@@ -91,6 +91,8 @@ _lib.fsi_batch_step.argtypes = [_vp, _vp, _vp, _vp, _vp, _dp, _ip, _vp]
 _lib.fsi_batch_set_tuning.argtypes = [_vp, _vp, _ip, _ip]
 _lib.fsi_batch_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
 _lib.fsi_batch_inject_stall.argtypes = [_vp, _ip]
+_lib.fsi_batch_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
+                                 C.POINTER(_ip), _ip]
 _lib.fsi_step_vjp.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _vp, _vp, _vp, _vp, _vp, _vp]
 
 
@@ -462,6 +464,15 @@ def fsi_batch_get_tuning(batch: Batch):
     a, b = _ip(), _ip()
     _check(_lib.fsi_batch_get_tuning(batch.handle, C.byref(a), C.byref(b)), "fsi_batch_get_tuning")
     return int(a.value), int(b.value)
+
+
+def fsi_batch_stats(batch: Batch, reset: bool = False):
+    """(wait_ns, life_ns, ctas) of the batch's launches since the last reset: the CTAs'
+    summed waits for other CTAs' phases, their summed lifetimes, CTAs per launch."""
+    w, l, n = C.c_longlong(), C.c_longlong(), _ip()
+    _check(_lib.fsi_batch_stats(batch.handle, C.byref(w), C.byref(l), C.byref(n), int(bool(reset))),
+           "fsi_batch_stats")
+    return int(w.value), int(l.value), int(n.value)
 
 
 def fsi_batch_inject_stall(batch: Batch, cluster: int) -> None:

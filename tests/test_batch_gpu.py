@@ -122,3 +122,31 @@ def test_batch_symmetric_form_larger_clusters(F):
         b.close()
     assert np.abs(p - rp).max() <= 1e-9 * np.abs(rp).max()
     assert np.abs(v - rv).max() <= 1e-7 * np.abs(rv).max()
+
+
+@pytest.mark.parametrize("ipt", [1, 4])
+def test_batch_idle_counters(F, ens, ipt):
+    """fsi_batch_stats: the CTAs' summed lifetimes fit inside CTAs x elapsed time, their
+    phase waits inside their lifetimes, and a reset zeroes both."""
+    cat, off = ens
+    with F.Context("mixed") as ctx:
+        b = F.Batch(ctx, off, max_steps=2)
+        F.fsi_batch_set_tuning(ctx, b, ipt)
+        m, p, v = dev(cat.mass), dev(cat.pos), dev(cat.vel)
+        F.fsi_batch_step(ctx, b, p, v, m, 1e-3, 2)
+        F.fsi_batch_stats(b, reset=True)
+        assert F.fsi_batch_stats(b)[:2] == (0, 0)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        F.fsi_batch_step(ctx, b, p, v, m, 1e-3, 2)
+        e1.record()
+        torch.cuda.synchronize()
+        wait_ns, life_ns, ctas = F.fsi_batch_stats(b, reset=True)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        ipt_now, cps = F.fsi_batch_get_tuning(b)
+        b.close()
+    nsm = torch.cuda.get_device_properties(0).multi_processor_count
+    assert ctas == nsm * cps
+    elapsed_ns = e0.elapsed_time(e1) * 1e6
+    assert 0 < life_ns <= ctas * elapsed_ns * 1.01
+    assert 0 <= wait_ns <= life_ns
