@@ -717,15 +717,21 @@ __global__ void __launch_bounds__(kAuxTile) timesteps_mixed_kernel(
 }
 
 // FP32 velocity records (vx, vy, vz, m) of a compact set.
-__global__ void pack_vel_kernel(int n, const double* __restrict__ vc, const double* __restrict__ mc,
+// FP32 velocity records (vx, vy, vz, m) of a set: entry k from particle idx[k] of the
+// 3 x ld velocity rows (idx null: particle k).
+__global__ void pack_vel_kernel(long long ld, const double* __restrict__ v,
+                                const double* __restrict__ m, const int* __restrict__ idx, int n,
                                 float4* __restrict__ out) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n) out[k] = make_float4((float)vc[k], (float)vc[(size_t)n + k], (float)vc[2 * (size_t)n + k], (float)mc[k]);
+    if (k >= n) return;
+    const long long i = idx ? (long long)idx[k] : k;
+    out[k] = make_float4((float)v[i], (float)v[ld + i], (float)v[2 * ld + i], (float)m[i]);
 }
 
-cudaError_t launch_pack_vel(int n, const double* vc, const double* mc, void* vrec, cudaStream_t s) {
+cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const int* idx, int n,
+                            void* vrec, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, reinterpret_cast<float4*>(vrec)); note_launch(); }
+    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(N, vel, mass, idx, n, reinterpret_cast<float4*>(vrec)); note_launch(); }
     return cudaGetLastError();
 }
 
@@ -735,7 +741,7 @@ cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, co
                                    cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     { pack_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, mc, nullptr, n, rec_ws, nullptr); note_launch(); }
-    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, reinterpret_cast<float4*>(vrec_ws)); note_launch(); }
+    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, nullptr, n, reinterpret_cast<float4*>(vrec_ws)); note_launch(); }
     { timesteps_mixed_kernel<<<blocks_for(n, kAuxTile * kStepIpt), kAuxTile, 0, s>>>(
         n, reinterpret_cast<const RecMix*>(rec_ws), reinterpret_cast<const float4*>(vrec_ws), eta_ff,
         eta_fb, eta_jerk, eps2, step, err); note_launch(); }
@@ -887,20 +893,6 @@ __global__ void iota_kernel(int n, int* ids) {
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     { iota_kernel<<<blocks_for(n), kB, 0, s>>>(n, ids); note_launch(); }
-    return cudaGetLastError();
-}
-
-// out = a + c * g  (3 x n), elementwise
-__global__ void axpby3_kernel(int n3, const double* __restrict__ a, const double* __restrict__ g,
-                              double c, double* __restrict__ out) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k < n3) out[k] = fma(c, g[k], a[k]);
-}
-
-cudaError_t launch_axpby3(int n, const double* a, const double* g, double c, double* out,
-                          cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    { axpby3_kernel<<<blocks_for(3LL * n), kB, 0, s>>>(3 * n, a, g, c, out); note_launch(); }
     return cudaGetLastError();
 }
 

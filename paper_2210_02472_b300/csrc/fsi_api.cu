@@ -79,7 +79,7 @@ struct fsi_ctx {
     int* err_d = nullptr;
     int* err_h = nullptr;          // pinned
     int* counts_h = nullptr;       // pinned, 3 ints (HHS partition)
-    Buf rec[2], accrec[2], xc, vc, ac, ad, gA, gB, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
+    Buf rec[2], accrec[2], xc, vc, ac, ad, tA, tB, mc, bhc, ids[2], part, mark, bhlist,
         nbh, apn, pnpart, epart, iota, steps, step0, counts, accum, eout, snapx, snapv,
         subwhere, subkey, subppos, stpart;
     std::vector<Buf> lvS, lvF;
@@ -409,7 +409,11 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     double* vc = vel;
     const double* mc = mass;
     const unsigned char* bhc = is_bh;
-    if (idx) {
+    // Without PN every update of x and v happens in a pass epilogue, which reaches the
+    // global state through the id list; the PN kernels work on a compact copy.
+    const bool compact = idx && pn;
+    const int* eids = (idx && !pn) ? idx : nullptr;
+    if (compact) {
         CK(ensure(c->xc, 3 * (size_t)n * 8));
         CK(ensure(c->vc, 3 * (size_t)n * 8));
         CK(ensure(c->mc, (size_t)n * 8));
@@ -419,7 +423,7 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
         CU(launch_gather1(N, mass, idx, n, P<double>(c->mc), s));
         mc = P<double>(c->mc);
     }
-    CU(launch_pack(prec, N, pos, mass, idx, n, c->rec[0].p, idx ? xc : nullptr, s));
+    CU(launch_pack(prec, N, pos, mass, idx, n, c->rec[0].p, compact ? xc : nullptr, s));
     if (pn) {
         CK(ensure(c->ad, 3 * (size_t)n * 8));
         CK(ensure(c->apn, 3 * (size_t)n * 8));
@@ -454,6 +458,8 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
             a.epi.c_drift = cd;
             a.epi.rec_out = rout;
             a.epi.mc = mc;
+            a.epi.ids = eids;
+            a.epi.ld = N;
         }
         return run_pair(c, KIND_ACC, a, s);
     };
@@ -472,6 +478,8 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
         a.epi.c_drift = cd;
         a.epi.rec_out = rout;
         a.epi.mc = mc;
+        a.epi.ids = eids;
+        a.epi.ld = N;
         return run_pair(c, KIND_GRAD, a, s);
     };
     void* r0 = c->rec[0].p;
@@ -493,7 +501,7 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
             }
         }
     }
-    if (idx) {
+    if (compact) {
         CU(launch_scatter3(N, xc, idx, n, pos, s));
         CU(launch_scatter3(N, vc, idx, n, vel, s));
     }
@@ -515,37 +523,47 @@ int cross_kick(fsi_ctx* c, int N, const double* pos, double* vel, const double* 
     CK(ensure(c->tB, 3 * (size_t)nF * 8));
     CU(launch_pack(prec, N, pos, mass, Sids, nS, c->rec[0].p, nullptr, s));
     CU(launch_pack(prec, N, pos, mass, Fids, nF, c->rec[1].p, nullptr, s));
+    // the kicks land on the global velocities through the id lists in the pass epilogues:
+    // v += w a (acc passes), or v += w (a + (eps^2/24) G) (grad passes, a from tA / tB)
+    auto kick = [&](Epi& e, const int* ids, double* base) {
+        e.v = vel;
+        e.ids = ids;
+        e.ld = N;
+        e.c_kick = w;
+        if (base) {
+            e.base = base;
+            e.c_grad = eps * eps / 24.0;
+        }
+    };
     PairArgs a{};
     a.check = CHECK_NONE;
     a.eps2 = c->p.eps2;
     a.irec = c->rec[0].p; a.jrec = c->rec[1].p; a.n_i = nS; a.n_j = nF;
-    a.epi.out = P<double>(c->tA);
-    a.epi.accrec = gradient ? c->accrec[0].p : nullptr;
-    CK(run_pair(c, KIND_ACC, a, s));
     PairArgs b{};
     b.check = CHECK_NONE;
     b.eps2 = c->p.eps2;
     b.irec = c->rec[1].p; b.jrec = c->rec[0].p; b.n_i = nF; b.n_j = nS;
-    b.epi.out = P<double>(c->tB);
-    b.epi.accrec = gradient ? c->accrec[1].p : nullptr;
+    if (gradient) {
+        a.epi.out = P<double>(c->tA);
+        a.epi.accrec = c->accrec[0].p;
+        b.epi.out = P<double>(c->tB);
+        b.epi.accrec = c->accrec[1].p;
+    } else {
+        kick(a.epi, Sids, nullptr);
+        kick(b.epi, Fids, nullptr);
+    }
+    CK(run_pair(c, KIND_ACC, a, s));
     CK(run_pair(c, KIND_ACC, b, s));
     if (gradient) {
-        CK(ensure(c->gA, 3 * (size_t)nS * 8));
-        CK(ensure(c->gB, 3 * (size_t)nF * 8));
         a.iacc = c->accrec[0].p; a.jacc = c->accrec[1].p;
         a.epi = Epi{};
-        a.epi.out = P<double>(c->gA);
+        kick(a.epi, Sids, P<double>(c->tA));
         CK(run_pair(c, KIND_GRAD, a, s));
         b.iacc = c->accrec[1].p; b.jacc = c->accrec[0].p;
         b.epi = Epi{};
-        b.epi.out = P<double>(c->gB);
+        kick(b.epi, Fids, P<double>(c->tB));
         CK(run_pair(c, KIND_GRAD, b, s));
-        const double cg = eps * eps / 24.0;
-        CU(launch_axpby3(nS, P<double>(c->tA), P<double>(c->gA), cg, P<double>(c->tA), s));
-        CU(launch_axpby3(nF, P<double>(c->tB), P<double>(c->gB), cg, P<double>(c->tB), s));
     }
-    CU(launch_scatter_axpy3(N, P<double>(c->tA), Sids, nS, w, vel, s));
-    CU(launch_scatter_axpy3(N, P<double>(c->tB), Fids, nF, w, vel, s));
     return FSI_OK;
 }
 
@@ -573,7 +591,11 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     const double* xc = pos;
     const double* vc = vel;
     const double* mc = mass;
-    if (Pids) {
+    const bool mixed = c->p.precision == FSI_MIXED;
+    const bool crit = c->p.eta_grad > 0.0 || c->p.eta_va > 0.0;
+    // compact copies for the FP64 kernel and the gradient criteria; the mixed kernel packs
+    // its records straight from the global arrays through the id list
+    if (Pids && (!mixed || crit)) {
         CK(ensure(c->xc, 3 * (size_t)n * 8));
         CK(ensure(c->vc, 3 * (size_t)n * 8));
         CK(ensure(c->mc, (size_t)n * 8));
@@ -584,12 +606,12 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
         vc = P<double>(c->vc);
         mc = P<double>(c->mc);
     }
-    if (c->p.precision == FSI_MIXED) {
+    if (mixed) {
         CK(ensure(c->rec[1], pad_tile(n) * 32));
         CK(ensure(c->accrec[1], pad_tile(n) * 32));
         CK(ensure(c->stpart, steps_x2_part_bytes(n, c->sm_count)));
-        CU(launch_pack(FSI_MIXED, n, xc, mc, nullptr, n, c->rec[1].p, nullptr, s));
-        CU(launch_pack_vel(n, vc, mc, c->accrec[1].p, s));
+        CU(launch_pack(FSI_MIXED, N, pos, mass, Pids, n, c->rec[1].p, nullptr, s));
+        CU(launch_pack_vel(N, vel, mass, Pids, n, c->accrec[1].p, s));
         CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
                            c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c), c->sm_count,
                            wide_limit(c), s));
@@ -767,7 +789,7 @@ int fsi_destroy(fsi_ctx* c) {
     if (!c) return FSI_OK;
     cudaDeviceSynchronize();
     Buf* bufs[] = {&c->rec[0], &c->rec[1], &c->accrec[0], &c->accrec[1], &c->xc, &c->vc, &c->ac,
-                   &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->mc, &c->bhc, &c->ids[0], &c->ids[1],
+                   &c->ad, &c->tA, &c->tB, &c->mc, &c->bhc, &c->ids[0], &c->ids[1],
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
                    &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
                    &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
@@ -804,7 +826,7 @@ int fsi_reserve(fsi_ctx* c, int N, int n) {
         CK(ensure(c->accrec[k], pt));
         CK(ensure(c->ids[k], pad_tile(n) * 4));
     }
-    Buf* b3[] = {&c->xc, &c->vc, &c->ac, &c->ad, &c->gA, &c->gB, &c->tA, &c->tB, &c->apn};
+    Buf* b3[] = {&c->xc, &c->vc, &c->ac, &c->ad, &c->tA, &c->tB, &c->apn};
     for (Buf* b : b3) CK(ensure(*b, 3 * (size_t)n * 8));
     CK(ensure(c->mc, (size_t)n * 8));
     CK(ensure(c->bhc, (size_t)n));

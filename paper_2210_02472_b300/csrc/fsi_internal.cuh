@@ -52,13 +52,15 @@ enum Check { CHECK_NONE = 0, CHECK_DIAG = 1, CHECK_IDS = 2 };
 //   accrec  : if non-null, the accel record of i is written there (acc pass feeding grad)
 struct Epi {
     double* out;
-    double* x;          // compact 3 x n_i, FP64 master positions (may be null)
-    double* v;          // compact 3 x n_i
+    double* x;          // FP64 master positions, 3 x n_i compact or global (ids) (may be null)
+    double* v;          // velocities, 3 x n_i compact or global (ids)
     const double* base; // compact 3 x n_i (grad pass: a_i), may be null
     double c_kick, c_grad, c_drift;
     void* rec_out;      // position records for the next pass
-    const double* mc;   // compact FP64 masses (needed when rec_out is written)
+    const double* mc;   // FP64 masses, compact or global (ids) (needed when rec_out is written)
     void* accrec;       // accel records (FP64: RecF64-like double4; MIXED: float4)
+    const int* ids;     // non-null: x, v, mc are global arrays (rows of ld), entry i at ids[i]
+    long long ld;
 };
 
 struct PairArgs {
@@ -288,8 +290,6 @@ cudaError_t launch_kepler_pairs(int n_pairs, const int* ppos, int n, double* x, 
                                 const double* m, double t, int* err, cudaStream_t s);
 cudaError_t launch_drift_singles(int n, double* x, const double* v, const int* key, int N, double w,
                                  cudaStream_t s);
-cudaError_t launch_axpby3(int n, const double* a, const double* g, double c, double* out,
-                          cudaStream_t s);
 constexpr int kMaxBHList = 1024;   // black holes per set handled by the PN kernels
 constexpr int kPnPartCtas = 64;    // CTAs per black hole in the PN reduction
 cudaError_t launch_bh_list(int n, const unsigned char* bhc, int* bh_list, int* n_bh, int* err,
@@ -319,7 +319,9 @@ cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const do
 cudaError_t launch_grad_steps(int n, const double* vc, const double* a, const double* G,
                               double eta_grad, double eta_va, double* step, cudaStream_t s);
 // FP32 velocity records (vx, vy, vz, m) of a compact set.
-cudaError_t launch_pack_vel(int n, const double* vc, const double* mc, void* vrec, cudaStream_t s);
+// FP32 velocity records (vx, vy, vz, m) of the set idx (null: the first n) of 3 x N rows.
+cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const int* idx, int n,
+                            void* vrec, cudaStream_t s);
 // Mixed time steps with packed FP32 pairs (steps_x2.cu); part: steps_x2_part_bytes bytes.
 size_t steps_x2_part_bytes(int n, int sm_count);
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,

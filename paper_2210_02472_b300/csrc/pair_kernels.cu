@@ -56,8 +56,11 @@ __device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, 
         e.out[(size_t)n + i] = ry;
         e.out[2 * (size_t)n + i] = rz;
     }
+    // state entry of particle i: compact (row length n) or global through the id list
+    const size_t gi = e.ids ? (size_t)e.ids[i] : (size_t)i;
+    const size_t L = e.ids ? (size_t)e.ld : (size_t)n;
     if (e.accrec) {   // accel record (ax, ay, az, m): the mass feeds the symmetric gradient
-        const double m = e.mc ? e.mc[i] : m_rec;
+        const double m = e.mc ? e.mc[gi] : m_rec;
         if (P == FSI_MIXED)
             reinterpret_cast<float4*>(e.accrec)[i] = make_float4((float)rx, (float)ry, (float)rz, (float)m);
         else
@@ -70,24 +73,24 @@ __device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, 
             ky = fma(e.c_grad, ry, e.base[(size_t)n + i]);
             kz = fma(e.c_grad, rz, e.base[2 * (size_t)n + i]);
         }
-        const double vx = fma(e.c_kick, kx, e.v[i]);
-        const double vy = fma(e.c_kick, ky, e.v[(size_t)n + i]);
-        const double vz = fma(e.c_kick, kz, e.v[2 * (size_t)n + i]);
-        e.v[i] = vx;
-        e.v[(size_t)n + i] = vy;
-        e.v[2 * (size_t)n + i] = vz;
+        const double vx = fma(e.c_kick, kx, e.v[gi]);
+        const double vy = fma(e.c_kick, ky, e.v[L + gi]);
+        const double vz = fma(e.c_kick, kz, e.v[2 * L + gi]);
+        e.v[gi] = vx;
+        e.v[L + gi] = vy;
+        e.v[2 * L + gi] = vz;
         if (e.x && e.c_drift != 0.0) {
-            const double x = fma(e.c_drift, vx, e.x[i]);
-            const double y = fma(e.c_drift, vy, e.x[(size_t)n + i]);
-            const double z = fma(e.c_drift, vz, e.x[2 * (size_t)n + i]);
-            e.x[i] = x;
-            e.x[(size_t)n + i] = y;
-            e.x[2 * (size_t)n + i] = z;
+            const double x = fma(e.c_drift, vx, e.x[gi]);
+            const double y = fma(e.c_drift, vy, e.x[L + gi]);
+            const double z = fma(e.c_drift, vz, e.x[2 * L + gi]);
+            e.x[gi] = x;
+            e.x[L + gi] = y;
+            e.x[2 * L + gi] = z;
             if (e.rec_out) {
                 if constexpr (P == FSI_MIXED)
-                    reinterpret_cast<RecMix*>(e.rec_out)[i] = make_mix_rec(x, y, z, e.mc[i]);
+                    reinterpret_cast<RecMix*>(e.rec_out)[i] = make_mix_rec(x, y, z, e.mc[gi]);
                 else
-                    reinterpret_cast<D4*>(e.rec_out)[i] = make_d4(x, y, z, e.mc[i]);
+                    reinterpret_cast<D4*>(e.rec_out)[i] = make_d4(x, y, z, e.mc[gi]);
             }
         }
     }
