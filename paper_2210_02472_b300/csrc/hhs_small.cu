@@ -7,11 +7,14 @@
 // U~_SF(2 tau/3), HHS(F', tau/2), FSI(S, tau/2), U_SF(tau/6), recursively -- runs in a
 // single CTA with the set's state in shared memory and an explicit frame stack.  Thread t
 // owns entry t of whichever index list a phase works on; phases are separated by
-// __syncthreads.  The same arithmetic as the large kernels is used (FP64, or FP32 hi/lo
-// separations with FP64 state for the mixed precision).  In the mixed precision the pass
-// sums are float-float pairs (hi, lo) and reach FP64 only in the per-particle kicks: the
-// B300 FP64 unit issues about 1/70 of the FP32 rate, and a pass with G lanes per receiver
-// would otherwise spend G FP64 reductions on every receiver.
+// __syncthreads.  The same pair arithmetic as the large kernels is used (FP64, or FP32
+// hi/lo separations for the mixed precision).  In the mixed precision the pass sums, and
+// the positions and velocities themselves, are float-float pairs (hi, lo) (about 48
+// significant bits) updated by FP32 operations, and the kick and drift weights are derived
+// from the level's tau in float-float arithmetic: the B300 FP64 unit issues about 1/70 of
+// the FP32 rate, so one FP64 warp instruction costs as much as ~70 FP32 ones, and FP64
+// partial sums, kicks, drifts and weight divisions made the deep levels FP64-bound.  FP64
+// remains for loading and storing the state, the time-step comparisons and PN pairs.
 #include <type_traits>
 
 #include "fsi_internal.cuh"
@@ -26,7 +29,8 @@ constexpr int kSmallLists = kSmallMax * 40;   // index-list stack entries
 struct Frame {
     int offS, nS, offF, nF;     // index lists in the list stack
     int offP, nP;               // the frame's own set
-    double tau;
+    double tau;                 // the level's interval (time-step comparisons)
+    float2 tauf;                // the same as a float-float pair (mixed-precision weights)
     int level;
     int stage;
 };
@@ -43,9 +47,72 @@ __device__ __forceinline__ void from_f64(float2& d, double v) {
     d = make_float2(h, (float)(v - (double)h));
 }
 
+// State (x, v) and kick / drift weights: FP64, or float-float in the mixed precision;
+// gradient-kick coefficients eps^2/24: FP64 or FP32 (they scale a correction of relative
+// size (eps^2/24) |G| / |a| and are rounded once).
+template <int P>
+using StT = SumT<P>;
+template <int P>
+using CgT = typename std::conditional<P == FSI_MIXED, float, double>::type;
+
+// Float-float arithmetic on normalised pairs (|lo| <= ulp(hi) / 2), FP32 operations only:
+// TwoSum (Knuth) and the FMA-based exact product, each renormalised by FastTwoSum
+// (Dekker).  Relative error of one sum or product ~ 2^-47.
+__device__ __forceinline__ float2 ff_norm(float h, float e) {
+    const float s = __fadd_rn(h, e);
+    return make_float2(s, __fsub_rn(e, __fsub_rn(s, h)));
+}
+__device__ __forceinline__ float2 ff_add(float2 a, float2 b) {
+    const float s = __fadd_rn(a.x, b.x);
+    const float bb = __fsub_rn(s, a.x);
+    float e = __fadd_rn(__fsub_rn(a.x, __fsub_rn(s, bb)), __fsub_rn(b.x, bb));
+    e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+    return ff_norm(s, e);
+}
+__device__ __forceinline__ float2 ff_mul(float2 a, float2 b) {
+    const float p = __fmul_rn(a.x, b.x);
+    float e = fmaf(a.x, b.x, -p);
+    e = fmaf(a.x, b.y, fmaf(a.y, b.x, e));
+    return ff_norm(p, e);
+}
+// a / d for a small integer d (exact in FP32): two quotient digits and the exact remainder
+__device__ __forceinline__ float2 ff_div(float2 a, float d) {
+    const float q1 = __fdiv_rn(a.x, d);
+    const float r = __fadd_rn(fmaf(-q1, d, a.x), a.y);
+    return ff_norm(q1, __fdiv_rn(r, d));
+}
+
+// v + w a (the kick and drift updates)
+__device__ __forceinline__ double axpy(double w, double a, double v) { return fma(w, a, v); }
+__device__ __forceinline__ float2 axpy(float2 w, float2 a, float2 v) { return ff_add(v, ff_mul(w, a)); }
+// a + c g (the gradient-kick acceleration)
+__device__ __forceinline__ double grad_acc(double a, double c, double g) { return fma(c, g, a); }
+__device__ __forceinline__ float2 grad_acc(float2 a, float c, float2 g) {
+    return ff_add(a, make_float2(__fmul_rn(c, g.x), 0.0f));
+}
+
+// Weights from a step h: h/2, h/6, 2h/3 and the gradient coefficient h^2/24.
+__device__ __forceinline__ double w_half(double h) { return 0.5 * h; }
+__device__ __forceinline__ float2 w_half(float2 h) { return make_float2(0.5f * h.x, 0.5f * h.y); }
+__device__ __forceinline__ double w_sixth(double h) { return h / 6.0; }
+__device__ __forceinline__ float2 w_sixth(float2 h) { return ff_div(h, 6.0f); }
+__device__ __forceinline__ double w_two_thirds(double h) { return 2.0 * h / 3.0; }
+__device__ __forceinline__ float2 w_two_thirds(float2 h) {
+    return ff_div(make_float2(2.0f * h.x, 2.0f * h.y), 3.0f);
+}
+__device__ __forceinline__ double w_cg(double h) { return h * h / 24.0; }
+__device__ __forceinline__ float w_cg(float2 h) { return __fdiv_rn(__fmul_rn(h.x, h.x), 24.0f); }
+
+template <int P>
+__device__ __forceinline__ StT<P> frame_tau(const Frame& f) {
+    if constexpr (P == FSI_MIXED) return f.tauf;
+    else return f.tau;
+}
+
 template <int P>
 struct SmallSmem {
-    double x[3][kSmallMax], v[3][kSmallMax], m[kSmallMax], s0[kSmallMax], st[kSmallMax];
+    StT<P> x[3][kSmallMax], v[3][kSmallMax];
+    double m[kSmallMax], s0[kSmallMax], st[kSmallMax];
     SumT<P> a[3][kSmallMax], g[3][kSmallMax];
     typename std::conditional<P == FSI_MIXED, RecMix, D4>::type rec[kSmallMax];
     typename std::conditional<P == FSI_MIXED, float4, D4>::type arec[kSmallMax];
@@ -57,25 +124,28 @@ struct SmallSmem {
     int top, list_top, nS, nF, anyfast;
 };
 
-template <int P>
-__device__ __forceinline__ void write_rec(SmallSmem<P>& S, int k) {
-    if constexpr (P == FSI_MIXED) S.rec[k] = make_mix_rec(S.x[0][k], S.x[1][k], S.x[2][k], S.m[k]);
-    else S.rec[k] = make_d4(S.x[0][k], S.x[1][k], S.x[2][k], S.m[k]);
-}
-
-// After a drift: new hi/lo position splits, the mass constants kept.
+// Position record of particle k from its state.  Mixed: the record's hi/lo splits are the
+// float-float position itself; the mass constants (2.5 m, -1.5 m) are written at the load
+// and kept.
 template <int P>
 __device__ __forceinline__ void write_rec_pos(SmallSmem<P>& S, int k) {
     if constexpr (P == FSI_MIXED) {
         RecMix r = S.rec[k];
-        const float xh = (float)S.x[0][k], yh = (float)S.x[1][k], zh = (float)S.x[2][k];
-        r.hi.x = xh; r.hi.y = yh; r.hi.z = zh;
-        r.lo.x = (float)(S.x[0][k] - (double)xh);
-        r.lo.y = (float)(S.x[1][k] - (double)yh);
-        r.lo.z = (float)(S.x[2][k] - (double)zh);
+        r.hi.x = S.x[0][k].x; r.hi.y = S.x[1][k].x; r.hi.z = S.x[2][k].x;
+        r.lo.x = S.x[0][k].y; r.lo.y = S.x[1][k].y; r.lo.z = S.x[2][k].y;
         S.rec[k] = r;
     } else {
-        write_rec<P>(S, k);
+        S.rec[k] = make_d4(S.x[0][k], S.x[1][k], S.x[2][k], S.m[k]);
+    }
+}
+
+// FP32 velocity record (vx, vy, vz, m) of the mixed time steps, mass kept.
+template <int P>
+__device__ __forceinline__ void write_vf(SmallSmem<P>& S, int k) {
+    if constexpr (P == FSI_MIXED) {
+        float4 u = S.vf[k];
+        u.x = S.v[0][k].x; u.y = S.v[1][k].x; u.z = S.v[2][k].x;
+        S.vf[k] = u;
     }
 }
 
@@ -238,7 +308,21 @@ __device__ void small_timesteps(SmallSmem<P>& S, const unsigned short* L, int n,
         acc.jz += __shfl_xor_sync(0xffffffffu, acc.jz, o);
     }
     if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
-    if (active && g == 0) S.st[i] = fmin(step_finish<T>(acc, a.eta_ff, a.eta_fb, a.eta_jerk), S.s0[i]);
+    if constexpr (P == FSI_MIXED) {
+        // the group leaders park their FP32 sums in the pass-sum storage (free until the
+        // next pass), then thread t finishes receiver t: the FP64 finish runs on n / 32 full
+        // warps instead of one warp per receiver with a single active lane
+        StepAcc<T>* sacc = reinterpret_cast<StepAcc<T>*>(&S.a[0][0]);
+        static_assert(sizeof(StepAcc<T>) * kSmallMax <= sizeof(S.a) + sizeof(S.g), "step sums");
+        if (active && g == 0) sacc[slot] = acc;
+        __syncthreads();
+        if (t < n) {
+            const int k = L[t];
+            S.st[k] = fmin(step_finish<T>(sacc[t], a.eta_ff, a.eta_fb, a.eta_jerk), S.s0[k]);
+        }
+    } else {
+        if (active && g == 0) S.st[i] = fmin(step_finish<T>(acc, a.eta_ff, a.eta_fb, a.eta_jerk), S.s0[i]);
+    }
 }
 
 // Gradient and velocity-per-acceleration steps (Sect. 3.4) of list L from its own a and
@@ -254,7 +338,8 @@ __device__ void small_grad_steps(SmallSmem<P>& S, const unsigned short* L, int n
     for (int q = 0; q < 3; ++q) {
         const double gq = to_f64(S.g[q][k]) * (1.0 / 24.0);
         const double aq = to_f64(S.a[q][k]);
-        vn = fma(S.v[q][k], S.v[q][k], vn);
+        const double vq = to_f64(S.v[q][k]);
+        vn = fma(vq, vq, vn);
         an = fma(aq, aq, an);
         gn = fma(gq, gq, gn);
     }
@@ -271,30 +356,26 @@ __device__ void small_grad_steps(SmallSmem<P>& S, const unsigned short* L, int n
 }
 
 template <int P>
-__device__ void small_kick(SmallSmem<P>& S, const unsigned short* L, int n, double w, bool with_grad,
-                           double cg) {
+__device__ void small_kick(SmallSmem<P>& S, const unsigned short* L, int n, StT<P> w, bool with_grad,
+                           CgT<P> cg) {
     const int t = threadIdx.x;
     if (t >= n) return;
     const int k = L[t];
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        const double ac = to_f64(S.a[c][k]);
-        S.v[c][k] = fma(w, with_grad ? fma(cg, to_f64(S.g[c][k]), ac) : ac, S.v[c][k]);
+        const SumT<P> ac = with_grad ? grad_acc(S.a[c][k], cg, S.g[c][k]) : S.a[c][k];
+        S.v[c][k] = axpy(w, ac, S.v[c][k]);
     }
-    if constexpr (P == FSI_MIXED) {
-        float4 u = S.vf[k];                     // the mass (w) is kept
-        u.x = (float)S.v[0][k]; u.y = (float)S.v[1][k]; u.z = (float)S.v[2][k];
-        S.vf[k] = u;
-    }
+    write_vf<P>(S, k);
 }
 
 template <int P>
-__device__ void small_drift(SmallSmem<P>& S, const unsigned short* L, int n, double w) {
+__device__ void small_drift(SmallSmem<P>& S, const unsigned short* L, int n, StT<P> w) {
     const int t = threadIdx.x;
     if (t >= n) return;
     const int k = L[t];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) S.x[c][k] = fma(w, S.v[c][k], S.x[c][k]);
+    for (int c = 0; c < 3; ++c) S.x[c][k] = axpy(w, S.v[c][k], S.x[c][k]);
     write_rec_pos<P>(S, k);
 }
 
@@ -310,8 +391,10 @@ __device__ void small_pn(SmallSmem<P>& S, const unsigned short* A, int nA, const
     for (int q = 0; q < nB; ++q) {
         const int j = B[q];
         if (j == i || (!S.bh[i] && !S.bh[j])) continue;
-        pn_pair(S.x[0][i], S.x[1][i], S.x[2][i], S.v[0][i], S.v[1][i], S.v[2][i], S.m[i], S.x[0][j],
-                S.x[1][j], S.x[2][j], S.v[0][j], S.v[1][j], S.v[2][j], S.m[j], ic2, px, py, pz, a.err);
+        pn_pair(to_f64(S.x[0][i]), to_f64(S.x[1][i]), to_f64(S.x[2][i]), to_f64(S.v[0][i]),
+                to_f64(S.v[1][i]), to_f64(S.v[2][i]), S.m[i], to_f64(S.x[0][j]), to_f64(S.x[1][j]),
+                to_f64(S.x[2][j]), to_f64(S.v[0][j]), to_f64(S.v[1][j]), to_f64(S.v[2][j]), S.m[j],
+                ic2, px, py, pz, a.err);
     }
     from_f64(S.g[0][i], px);
     from_f64(S.g[1][i], py);
@@ -319,24 +402,20 @@ __device__ void small_pn(SmallSmem<P>& S, const unsigned short* A, int nA, const
 }
 
 template <int P>
-__device__ void small_kick_g(SmallSmem<P>& S, const unsigned short* L, int n, double w) {
+__device__ void small_kick_g(SmallSmem<P>& S, const unsigned short* L, int n, StT<P> w) {
     const int t = threadIdx.x;
     if (t >= n) return;
     const int k = L[t];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) S.v[c][k] = fma(w, to_f64(S.g[c][k]), S.v[c][k]);
-    if constexpr (P == FSI_MIXED) {
-        float4 u = S.vf[k];
-        u.x = (float)S.v[0][k]; u.y = (float)S.v[1][k]; u.z = (float)S.v[2][k];
-        S.vf[k] = u;
-    }
+    for (int c = 0; c < 3; ++c) S.v[c][k] = axpy(w, S.g[c][k], S.v[c][k]);
+    write_vf<P>(S, k);
 }
 
 // PN1.0 kick of weight w: within list L (B == nullptr) or between disjoint L and B; all PN
 // accelerations from the velocities at the start of the kick (Sect. 3.9).
 template <int P>
 __device__ void small_pn_kick(SmallSmem<P>& S, const unsigned short* L, int n, const unsigned short* B,
-                              int nB, double w, const SmallArgs& a) {
+                              int nB, StT<P> w, const SmallArgs& a) {
     if (!(a.c > 0.0)) return;
     if (B == nullptr) {
         small_pn<P>(S, L, n, L, n, a);
@@ -355,27 +434,29 @@ __device__ void small_pn_kick(SmallSmem<P>& S, const unsigned short* L, int n, c
 // One FSI cycle of list L on itself (Sect. 2.1, Eq. fsi-cycle), wrapped in PN1.0
 // half-kicks when c > 0 (Sect. 3.9).
 template <int P>
-__device__ void small_fsi(SmallSmem<P>& S, const unsigned short* L, int n, double h, const SmallArgs& a) {
-    small_pn_kick<P>(S, L, n, nullptr, 0, 0.5 * h, a);
+__device__ void small_fsi(SmallSmem<P>& S, const unsigned short* L, int n, StT<P> h, const SmallArgs& a) {
+    const StT<P> h2 = w_half(h), h6 = w_sixth(h), h23 = w_two_thirds(h);
+    const CgT<P> cg = w_cg(h);
+    small_pn_kick<P>(S, L, n, nullptr, 0, h2, a);
     small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
-    small_kick<P>(S, L, n, h / 6.0, false, 0.0); __syncthreads();
-    small_drift<P>(S, L, n, 0.5 * h); __syncthreads();
+    small_kick<P>(S, L, n, h6, false, cg); __syncthreads();
+    small_drift<P>(S, L, n, h2); __syncthreads();
     small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
     if (threadIdx.x < n) write_arec<P>(S, L[threadIdx.x]);
     __syncthreads();
     small_pass<P, 1>(S, L, n, L, n, a.eps2, S.g, a.work); __syncthreads();
-    small_kick<P>(S, L, n, 2.0 * h / 3.0, true, h * h / 24.0); __syncthreads();
-    small_drift<P>(S, L, n, 0.5 * h); __syncthreads();
+    small_kick<P>(S, L, n, h23, true, cg); __syncthreads();
+    small_drift<P>(S, L, n, h2); __syncthreads();
     small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
-    small_kick<P>(S, L, n, h / 6.0, false, 0.0); __syncthreads();
-    small_pn_kick<P>(S, L, n, nullptr, 0, 0.5 * h, a);
+    small_kick<P>(S, L, n, h6, false, cg); __syncthreads();
+    small_pn_kick<P>(S, L, n, nullptr, 0, h2, a);
 }
 
 // Inter-level kick of S and F (Sect. 2.2); gradient: the gradient acceleration of the
 // same inter-level term with eps = tau.
 template <int P>
 __device__ void small_cross(SmallSmem<P>& S, const unsigned short* Ls, int nS,
-                            const unsigned short* Lf, int nF, double w, bool gradient, double tau,
+                            const unsigned short* Lf, int nF, StT<P> w, bool gradient, CgT<P> cg,
                             const SmallArgs& a) {
     small_pass<P, 0>(S, Ls, nS, Lf, nF, a.eps2, S.a, a.work);
     __syncthreads();
@@ -390,8 +471,8 @@ __device__ void small_cross(SmallSmem<P>& S, const unsigned short* Ls, int nS,
         small_pass<P, 1>(S, Lf, nF, Ls, nS, a.eps2, S.g, a.work);
         __syncthreads();
     }
-    small_kick<P>(S, Ls, nS, w, gradient, tau * tau / 24.0);
-    small_kick<P>(S, Lf, nF, w, gradient, tau * tau / 24.0);
+    small_kick<P>(S, Ls, nS, w, gradient, cg);
+    small_kick<P>(S, Lf, nF, w, gradient, cg);
     __syncthreads();
 }
 
@@ -435,13 +516,21 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
     if (t < n) {
         const int i = a.ids[t];
         for (int c = 0; c < 3; ++c) {
-            S.x[c][t] = a.pos[c * N + i];
-            S.v[c][t] = a.vel[c * N + i];
+            from_f64(S.x[c][t], a.pos[c * N + i]);
+            from_f64(S.v[c][t], a.vel[c * N + i]);
         }
-        S.m[t] = a.mass[i];
+        const double m = a.mass[i];
+        S.m[t] = m;
         S.s0[t] = a.step0[i];
-        write_rec<P>(S, t);
-        S.vf[t] = make_float4((float)S.v[0][t], (float)S.v[1][t], (float)S.v[2][t], (float)S.m[t]);
+        if constexpr (P == FSI_MIXED) {
+            RecMix r;
+            r.hi.w = (float)(2.5 * m);
+            r.lo.w = (float)(-1.5 * m);
+            S.rec[t] = r;
+        }
+        write_rec_pos<P>(S, t);
+        S.vf[t] = make_float4((float)to_f64(S.v[0][t]), (float)to_f64(S.v[1][t]),
+                              (float)to_f64(S.v[2][t]), (float)m);
         S.bh[t] = (a.c > 0.0 && a.is_bh) ? a.is_bh[i] : 0;
         S.lists[t] = (unsigned short)t;                 // the root's set
     }
@@ -450,6 +539,7 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
         S.list_top = n;
         Frame f;
         f.offP = 0; f.nP = n; f.tau = a.tau; f.level = a.level; f.stage = 0;
+        from_f64(f.tauf, a.tau);
         f.offS = f.nS = f.offF = f.nF = 0;
         S.fr[0] = f;
     }
@@ -458,6 +548,7 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
         const int top = S.top;
         if (top < 0) break;
         Frame f = S.fr[top];
+        const StT<P> ft = frame_tau<P>(f);
         if (f.stage == 0) {
             const unsigned short* L = S.lists + f.offP;
             small_timesteps<P>(S, L, f.nP, a);
@@ -493,23 +584,24 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
             const unsigned short* Ls = S.lists + f.offS;
             const unsigned short* Lf = S.lists + f.offF;
             if (nS > 0 && nF > 0) {
-                small_pn_kick<P>(S, Ls, nS, Lf, nF, 0.5 * f.tau, a);
-                small_cross<P>(S, Ls, nS, Lf, nF, f.tau / 6.0, false, 0.0, a);
+                small_pn_kick<P>(S, Ls, nS, Lf, nF, w_half(ft), a);
+                small_cross<P>(S, Ls, nS, Lf, nF, w_sixth(ft), false, w_cg(ft), a);
             }
-            if (nS > 0) small_fsi<P>(S, Ls, nS, 0.5 * f.tau, a);
+            if (nS > 0) small_fsi<P>(S, Ls, nS, w_half(ft), a);
             f.stage = 1;
         } else if (f.stage == 1) {
             const unsigned short* Ls = S.lists + f.offS;
             const unsigned short* Lf = S.lists + f.offF;
-            if (f.nS > 0 && f.nF > 0) small_cross<P>(S, Ls, f.nS, Lf, f.nF, 2.0 * f.tau / 3.0, true, f.tau, a);
+            if (f.nS > 0 && f.nF > 0)
+                small_cross<P>(S, Ls, f.nS, Lf, f.nF, w_two_thirds(ft), true, w_cg(ft), a);
             f.stage = 2;
         } else {
             const unsigned short* Ls = S.lists + f.offS;
             const unsigned short* Lf = S.lists + f.offF;
-            if (f.nS > 0) small_fsi<P>(S, Ls, f.nS, 0.5 * f.tau, a);
+            if (f.nS > 0) small_fsi<P>(S, Ls, f.nS, w_half(ft), a);
             if (f.nS > 0 && f.nF > 0) {
-                small_cross<P>(S, Ls, f.nS, Lf, f.nF, f.tau / 6.0, false, 0.0, a);
-                small_pn_kick<P>(S, Ls, f.nS, Lf, f.nF, 0.5 * f.tau, a);
+                small_cross<P>(S, Ls, f.nS, Lf, f.nF, w_sixth(ft), false, w_cg(ft), a);
+                small_pn_kick<P>(S, Ls, f.nS, Lf, f.nF, w_half(ft), a);
             }
             f.stage = 3;
         }
@@ -527,6 +619,7 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
                     if (top + 1 < kSmallDepth) {
                         Frame c;
                         c.offP = f.offF; c.nP = f.nF; c.tau = 0.5 * f.tau; c.level = f.level + 1;
+                        c.tauf = make_float2(0.5f * f.tauf.x, 0.5f * f.tauf.y);
                         c.stage = 0; c.offS = c.nS = c.offF = c.nF = 0;
                         S.fr[top + 1] = c;
                         S.top = top + 1;
@@ -541,8 +634,8 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
     if (t < n) {
         const int i = a.ids[t];
         for (int c = 0; c < 3; ++c) {
-            a.pos[c * N + i] = S.x[c][t];
-            a.vel[c * N + i] = S.v[c][t];
+            a.pos[c * N + i] = to_f64(S.x[c][t]);
+            a.vel[c * N + i] = to_f64(S.v[c][t]);
         }
     }
 }
