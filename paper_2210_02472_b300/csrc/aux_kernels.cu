@@ -51,6 +51,41 @@ cudaError_t launch_pack(int precision, int N, const double* pos, const double* m
     return cudaGetLastError();
 }
 
+// Two packings in one launch (the slow and fast sets of a cross-level kick): CTAs
+// [0, ctas_a) pack list A into rec_a, the others list B into rec_b.
+template <int P>
+__global__ void pack2_kernel(int N, const double* __restrict__ pos, const double* __restrict__ mass,
+                             const int* __restrict__ ida, int na, void* __restrict__ rec_a,
+                             const int* __restrict__ idb, int nb, void* __restrict__ rec_b,
+                             int ctas_a) {
+    const bool first = (int)blockIdx.x < ctas_a;
+    const int k = (first ? blockIdx.x : blockIdx.x - ctas_a) * blockDim.x + threadIdx.x;
+    const int n = first ? na : nb;
+    if (k >= n) return;
+    const int i = idx_at(first ? ida : idb, k);
+    void* rec = first ? rec_a : rec_b;
+    const double x = pos[i], y = pos[(size_t)N + i], z = pos[2 * (size_t)N + i];
+    if constexpr (P == FSI_MIXED)
+        reinterpret_cast<RecMix*>(rec)[k] = make_mix_rec(x, y, z, mass[i]);
+    else
+        reinterpret_cast<D4*>(rec)[k] = make_d4(x, y, z, mass[i]);
+}
+
+cudaError_t launch_pack2(int precision, int N, const double* pos, const double* mass,
+                         const int* ida, int na, void* rec_a, const int* idb, int nb, void* rec_b,
+                         cudaStream_t s) {
+    if (na <= 0 || nb <= 0) {
+        cudaError_t e = launch_pack(precision, N, pos, mass, ida, na, rec_a, nullptr, s);
+        return e != cudaSuccess ? e : launch_pack(precision, N, pos, mass, idb, nb, rec_b, nullptr, s);
+    }
+    const int ca = (na + kB - 1) / kB, cb = (nb + kB - 1) / kB;
+    if (precision == FSI_MIXED)
+        { pack2_kernel<FSI_MIXED><<<ca + cb, kB, 0, s>>>(N, pos, mass, ida, na, rec_a, idb, nb, rec_b, ca); note_launch(); }
+    else
+        { pack2_kernel<FSI_FP64><<<ca + cb, kB, 0, s>>>(N, pos, mass, ida, na, rec_a, idb, nb, rec_b, ca); note_launch(); }
+    return cudaGetLastError();
+}
+
 template <int P>
 __global__ void pack_acc_kernel(int N, const double* __restrict__ accg,
                                 const double* __restrict__ mass, const int* __restrict__ idx,

@@ -318,6 +318,30 @@ int run_wide(fsi_ctx* c, int kind, PairArgs a, int lg, int split, cudaStream_t s
     return FSI_OK;
 }
 
+int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s);
+
+// The two directions of a cross-level pass (independent, unmasked): one launch when both
+// take the wide form with a single source slice, else one pass after the other.
+int run_pair2(fsi_ctx* c, int kind, PairArgs a, PairArgs b, cudaStream_t s) {
+    const int prec = c->p.precision;
+    if (a.n_i > 0 && b.n_i > 0 && a.check == CHECK_NONE && b.check == CHECK_NONE) {
+        const int ipa = kThreads * variant_ipt(c->ipt[prec][kind][a.n_i >= kOneSidedLarge]);
+        const int ipb = kThreads * variant_ipt(c->ipt[prec][kind][b.n_i >= kOneSidedLarge]);
+        int lga = 0, lgb = 0, spa = 1, spb = 1;
+        if (wide_plan(c, a.n_i, a.n_j, ipa, lga, spa) && wide_plan(c, b.n_i, b.n_j, ipb, lgb, spb) &&
+            spa == 1 && spb == 1) {
+            c->work_pairs[kind] += (long long)a.n_i * a.n_j + (long long)b.n_i * b.n_j;
+            a.err = b.err = c->err_d;
+            a.j_per_split = std::max(1, a.n_j);
+            b.j_per_split = std::max(1, b.n_j);
+            CK(timed(c, kind, s, [&] { return launch_wide_pair2(prec, kind, a, b, lga, lgb, s); }));
+            return FSI_OK;
+        }
+    }
+    CK(run_pair(c, kind, a, s));
+    return run_pair(c, kind, b, s);
+}
+
 int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
     if (a.n_i <= 0) return FSI_OK;
     c->work_pairs[kind] += (long long)a.n_i * (long long)a.n_j;
@@ -521,8 +545,7 @@ int cross_kick(fsi_ctx* c, int N, const double* pos, double* vel, const double* 
     CK(ensure(c->accrec[1], pad_tile(nF) * 32));
     CK(ensure(c->tA, 3 * (size_t)nS * 8));
     CK(ensure(c->tB, 3 * (size_t)nF * 8));
-    CU(launch_pack(prec, N, pos, mass, Sids, nS, c->rec[0].p, nullptr, s));
-    CU(launch_pack(prec, N, pos, mass, Fids, nF, c->rec[1].p, nullptr, s));
+    CU(launch_pack2(prec, N, pos, mass, Sids, nS, c->rec[0].p, Fids, nF, c->rec[1].p, s));
     // the kicks land on the global velocities through the id lists in the pass epilogues:
     // v += w a (acc passes), or v += w (a + (eps^2/24) G) (grad passes, a from tA / tB)
     auto kick = [&](Epi& e, const int* ids, double* base) {
@@ -552,17 +575,15 @@ int cross_kick(fsi_ctx* c, int N, const double* pos, double* vel, const double* 
         kick(a.epi, Sids, nullptr);
         kick(b.epi, Fids, nullptr);
     }
-    CK(run_pair(c, KIND_ACC, a, s));
-    CK(run_pair(c, KIND_ACC, b, s));
+    CK(run_pair2(c, KIND_ACC, a, b, s));
     if (gradient) {
         a.iacc = c->accrec[0].p; a.jacc = c->accrec[1].p;
         a.epi = Epi{};
         kick(a.epi, Sids, P<double>(c->tA));
-        CK(run_pair(c, KIND_GRAD, a, s));
         b.iacc = c->accrec[1].p; b.jacc = c->accrec[0].p;
         b.epi = Epi{};
         kick(b.epi, Fids, P<double>(c->tB));
-        CK(run_pair(c, KIND_GRAD, b, s));
+        CK(run_pair2(c, KIND_GRAD, a, b, s));
     }
     return FSI_OK;
 }

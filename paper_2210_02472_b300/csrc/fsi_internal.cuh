@@ -228,6 +228,9 @@ cudaError_t launch_finalize_p(int precision, const PairArgs& a, int split, cudaS
 // the epilogue itself, split > 1 writes a.part for launch_finalize_p.
 cudaError_t launch_wide_pair(int precision, int kind, bool diag, const PairArgs& a, int lg,
                              int split, cudaStream_t s);
+// Two unmasked wide passes (one source slice each) in one launch; each applies its epilogue.
+cudaError_t launch_wide_pair2(int precision, int kind, const PairArgs& a, const PairArgs& b,
+                              int lga, int lgb, cudaStream_t s);
 // Symmetric self-interaction pass (every unordered pair once); adds into accum (3 x n,
 // zeroed by the caller); `chunk` source tiles per work item.
 // Far-tile inputs of the symmetric mixed kernel (second form with bit 64 in its variant):
@@ -260,6 +263,10 @@ cudaError_t launch_compose(const int* idx, const int* perm, int n, int* list, cu
 cudaError_t launch_rel_mass(const double* mass, const int* idx, int n, void* rel, cudaStream_t s);
 cudaError_t launch_subtiles(int n, const void* rec, void* rel, void* sub, cudaStream_t s);
 
+// launch_pack of two id lists (no compact copies) in one launch.
+cudaError_t launch_pack2(int precision, int N, const double* pos, const double* mass,
+                         const int* ida, int na, void* rec_a, const int* idb, int nb, void* rec_b,
+                         cudaStream_t s);
 cudaError_t launch_pack(int precision, int N, const double* pos, const double* mass,
                         const int* idx, int n, void* rec, double* xc, cudaStream_t s);
 cudaError_t launch_pack_acc(int precision, int N, const double* accg, const double* mass,

@@ -396,15 +396,16 @@ __global__ void finalize_kernel(const PairArgs a, int split) {
 // 256 sources per lane, float-float (TwoSum) across runs and lanes, no FP64 instruction
 // before the epilogue; FP64: FP64 throughout.  DIAG: same list on both sides, the self
 // pair excluded by index.
+// One CTA of a wide pass: receiver block bx, source slice by of ny.
 template <int P, int KIND, bool DIAG>
-__global__ void __launch_bounds__(kThreads) wide_pair_kernel(const PairArgs a, int lg) {
+__device__ __forceinline__ void wide_pair_body(const PairArgs& a, int lg, int bx, int by, int ny) {
     const int G = 1 << lg;
-    const long long gt = (long long)blockIdx.x * kThreads + threadIdx.x;
+    const long long gt = (long long)bx * kThreads + threadIdx.x;
     const int slot = (int)(gt >> lg);
     const int g = (int)(gt & (G - 1));
     const bool active = slot < a.n_i;
     const int i = active ? slot : a.n_i - 1;
-    const int js = blockIdx.y * a.j_per_split;
+    const int js = by * a.j_per_split;
     const int je = min(a.n_j, js + a.j_per_split);
     double r[3];
     if constexpr (P == FSI_MIXED) {
@@ -475,14 +476,28 @@ __global__ void __launch_bounds__(kThreads) wide_pair_kernel(const PairArgs a, i
             for (int c = 0; c < 3; ++c) r[c] += __shfl_xor_sync(0xffffffffu, r[c], o);
         if (!active || g != 0) return;
     }
-    if (gridDim.y == 1) {
+    if (ny == 1) {
         epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], record_mass<P>(a.irec, i), a.err);
     } else {
-        double* part = a.part + (size_t)blockIdx.y * 3 * a.n_i;
+        double* part = a.part + (size_t)by * 3 * a.n_i;
         part[i] = r[0];
         part[(size_t)a.n_i + i] = r[1];
         part[2 * (size_t)a.n_i + i] = r[2];
     }
+}
+
+template <int P, int KIND, bool DIAG>
+__global__ void __launch_bounds__(kThreads) wide_pair_kernel(const PairArgs a, int lg) {
+    wide_pair_body<P, KIND, DIAG>(a, lg, blockIdx.x, blockIdx.y, gridDim.y);
+}
+
+// Two independent unmasked passes in one launch (the two directions of a cross-level
+// kick, one source slice each): CTAs [0, ctas_a) run a, the others b.
+template <int P, int KIND>
+__global__ void __launch_bounds__(kThreads) wide_pair2_kernel(const PairArgs a, const PairArgs b,
+                                                              int lga, int lgb, int ctas_a) {
+    if ((int)blockIdx.x < ctas_a) wide_pair_body<P, KIND, false>(a, lga, blockIdx.x, 0, 1);
+    else wide_pair_body<P, KIND, false>(b, lgb, blockIdx.x - ctas_a, 0, 1);
 }
 
 // =================================================================================
@@ -1691,6 +1706,25 @@ cudaError_t launch_wide_t(bool diag, const PairArgs& a, int lg, int split, cudaS
     if (diag) { wide_pair_kernel<P, KIND, true><<<grid, kThreads, 0, s>>>(a, lg); note_launch(); }
     else { wide_pair_kernel<P, KIND, false><<<grid, kThreads, 0, s>>>(a, lg); note_launch(); }
     return cudaGetLastError();
+}
+
+template <int P, int KIND>
+cudaError_t launch_wide2_t(const PairArgs& a, const PairArgs& b, int lga, int lgb, cudaStream_t s) {
+    const long long ca = (((long long)a.n_i << lga) + kThreads - 1) / kThreads;
+    const long long cb = (((long long)b.n_i << lgb) + kThreads - 1) / kThreads;
+    { wide_pair2_kernel<P, KIND><<<(unsigned)(ca + cb), kThreads, 0, s>>>(a, b, lga, lgb, (int)ca); note_launch(); }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wide_pair2(int precision, int kind, const PairArgs& a, const PairArgs& b,
+                              int lga, int lgb, cudaStream_t s) {
+    if (a.n_i <= 0 || b.n_i <= 0) return cudaErrorInvalidValue;
+    if (lga < 0 || lga > 5 || lgb < 0 || lgb > 5) return cudaErrorInvalidValue;
+    if (precision == FSI_MIXED)
+        return kind == KIND_ACC ? launch_wide2_t<FSI_MIXED, KIND_ACC>(a, b, lga, lgb, s)
+                                : launch_wide2_t<FSI_MIXED, KIND_GRAD>(a, b, lga, lgb, s);
+    return kind == KIND_ACC ? launch_wide2_t<FSI_FP64, KIND_ACC>(a, b, lga, lgb, s)
+                            : launch_wide2_t<FSI_FP64, KIND_GRAD>(a, b, lga, lgb, s);
 }
 
 cudaError_t launch_wide_pair(int precision, int kind, bool diag, const PairArgs& a, int lg,
