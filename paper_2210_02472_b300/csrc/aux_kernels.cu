@@ -753,20 +753,23 @@ __global__ void __launch_bounds__(kAuxTile) timesteps_mixed_kernel(
 
 // FP32 velocity records (vx, vy, vz, m) of a compact set.
 // FP32 velocity records (vx, vy, vz, m) of a set: entry k from particle idx[k] of the
-// 3 x ld velocity rows (idx null: particle k).
+// 3 x ld velocity rows (idx null: particle k); with pos, also its mixed position record.
 __global__ void pack_vel_kernel(long long ld, const double* __restrict__ v,
                                 const double* __restrict__ m, const int* __restrict__ idx, int n,
-                                float4* __restrict__ out) {
+                                float4* __restrict__ out, const double* __restrict__ pos,
+                                RecMix* __restrict__ rec) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= n) return;
     const long long i = idx ? (long long)idx[k] : k;
     out[k] = make_float4((float)v[i], (float)v[ld + i], (float)v[2 * ld + i], (float)m[i]);
+    if (pos) rec[k] = make_mix_rec(pos[i], pos[ld + i], pos[2 * ld + i], m[i]);
 }
 
 cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const int* idx, int n,
-                            void* vrec, cudaStream_t s) {
+                            void* vrec, const double* pos, void* rec, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
-    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(N, vel, mass, idx, n, reinterpret_cast<float4*>(vrec)); note_launch(); }
+    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(N, vel, mass, idx, n, reinterpret_cast<float4*>(vrec),
+                                                   pos, reinterpret_cast<RecMix*>(rec)); note_launch(); }
     return cudaGetLastError();
 }
 
@@ -776,7 +779,7 @@ cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, co
                                    cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     { pack_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, mc, nullptr, n, rec_ws, nullptr); note_launch(); }
-    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, nullptr, n, reinterpret_cast<float4*>(vrec_ws)); note_launch(); }
+    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, nullptr, n, reinterpret_cast<float4*>(vrec_ws), nullptr, nullptr); note_launch(); }
     { timesteps_mixed_kernel<<<blocks_for(n, kAuxTile * kStepIpt), kAuxTile, 0, s>>>(
         n, reinterpret_cast<const RecMix*>(rec_ws), reinterpret_cast<const float4*>(vrec_ws), eta_ff,
         eta_fb, eta_jerk, eps2, step, err); note_launch(); }
@@ -862,28 +865,14 @@ cudaError_t launch_energy(int n, const double* xc, const double* vc, const doubl
 
 // ---------------------------------------------------------------------------------
 // HHS helpers.
-// step[k] = min(step[k], step0[ids[k]]) at deeper levels; step0[ids[k]] = step[k] at level 0.
-__global__ void level_steps_kernel(int n, const int* __restrict__ ids, double* __restrict__ step,
-                                   double* __restrict__ step0, int level0) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
-    const int i = ids[k];
-    if (level0) step0[i] = step[k];
-    else step[k] = fmin(step[k], step0[i]);
-}
-
-cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step0, int level0,
-                               cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    { level_steps_kernel<<<blocks_for(n), kB, 0, s>>>(n, ids, step, step0, level0); note_launch(); }
-    return cudaGetLastError();
-}
-
 // Stable partition of ids by (step >= tau) into S (slow) and F (fast), single CTA scan.
 // counts[0] = |S|, counts[1] = |F|, counts[2] = 1 if some particle wanted a step < tau
-// at the deepest level (force_slow).
-__global__ void partition_kernel(int n, const int* __restrict__ ids, const double* __restrict__ step,
-                                 double tau, int force_slow, int* __restrict__ S, int* __restrict__ F,
+// at the deepest level (force_slow).  With step0 the level-step rule is applied first:
+// at level 0 the steps are recorded (step0[id] = step), deeper down a step is the min
+// with the recorded one.
+__global__ void partition_kernel(int n, const int* __restrict__ ids, double* __restrict__ step,
+                                 double* __restrict__ step0, int level0, double tau, int force_slow,
+                                 int* __restrict__ S, int* __restrict__ F,
                                  int* __restrict__ counts) {
     __shared__ int wS[32], wF[32];
     __shared__ int baseS, baseF, anyfast;
@@ -893,7 +882,13 @@ __global__ void partition_kernel(int n, const int* __restrict__ ids, const doubl
     for (int k0 = 0; k0 < n; k0 += blockDim.x) {
         const int k = k0 + threadIdx.x;
         const bool valid = k < n;
-        const bool fastw = valid && step[k] < tau;
+        double st = valid ? step[k] : 0.0;
+        if (valid && step0) {
+            const int i = ids[k];
+            if (level0) step0[i] = st;
+            else { st = fmin(st, step0[i]); step[k] = st; }
+        }
+        const bool fastw = valid && st < tau;
         const bool slow = valid && (force_slow || !fastw);
         const bool fast = valid && !slow;
         if (fastw && force_slow) anyfast = 1;
@@ -914,9 +909,9 @@ __global__ void partition_kernel(int n, const int* __restrict__ ids, const doubl
     if (threadIdx.x == 0) { counts[0] = baseS; counts[1] = baseF; counts[2] = anyfast; }
 }
 
-cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,
-                             int* S, int* F, int* counts, cudaStream_t s) {
-    { partition_kernel<<<1, 1024, 0, s>>>(n, ids, step, tau, force_slow, S, F, counts); note_launch(); }
+cudaError_t launch_partition(int n, const int* ids, double* step, double* step0, int level0,
+                             double tau, int force_slow, int* S, int* F, int* counts, cudaStream_t s) {
+    { partition_kernel<<<1, 1024, 0, s>>>(n, ids, step, step0, level0, tau, force_slow, S, F, counts); note_launch(); }
     return cudaGetLastError();
 }
 

@@ -631,8 +631,7 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
         CK(ensure(c->rec[1], pad_tile(n) * 32));
         CK(ensure(c->accrec[1], pad_tile(n) * 32));
         CK(ensure(c->stpart, steps_x2_part_bytes(n, c->sm_count)));
-        CU(launch_pack(FSI_MIXED, N, pos, mass, Pids, n, c->rec[1].p, nullptr, s));
-        CU(launch_pack_vel(N, vel, mass, Pids, n, c->accrec[1].p, s));
+        CU(launch_pack_vel(N, vel, mass, Pids, n, c->accrec[1].p, pos, c->rec[1].p, s));
         CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
                            c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c), c->sm_count,
                            wide_limit(c), s));
@@ -680,11 +679,12 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     CK(ensure(c->lvS[level], (size_t)n * 4));
     CK(ensure(c->lvF[level], (size_t)n * 4));
     CK(timesteps_core(c, N, pos, vel, mass, Pids, n, P<double>(c->steps), s));
-    CU(launch_level_steps(n, Pids, P<double>(c->steps), P<double>(c->step0), level == 0, s));
     const int force_slow = level >= c->p.max_level;
     int* Sids = P<int>(c->lvS[level]);
     int* Fids = P<int>(c->lvF[level]);
-    CU(launch_partition(n, Pids, P<double>(c->steps), tau, force_slow, Sids, Fids, P<int>(c->counts), s));
+    // level-step rule (record at level 0, min deeper down) fused into the partition
+    CU(launch_partition(n, Pids, P<double>(c->steps), P<double>(c->step0), level == 0, tau, force_slow,
+                        Sids, Fids, P<int>(c->counts), s));
     CU(cudaMemcpyAsync(c->counts_h, c->counts.p, 3 * sizeof(int), cudaMemcpyDeviceToHost, s));
     CU(cudaStreamSynchronize(s));
     const int nS = c->counts_h[0], nF = c->counts_h[1];

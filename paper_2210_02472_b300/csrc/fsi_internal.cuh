@@ -326,9 +326,10 @@ cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const do
 cudaError_t launch_grad_steps(int n, const double* vc, const double* a, const double* G,
                               double eta_grad, double eta_va, double* step, cudaStream_t s);
 // FP32 velocity records (vx, vy, vz, m) of a compact set.
-// FP32 velocity records (vx, vy, vz, m) of the set idx (null: the first n) of 3 x N rows.
+// FP32 velocity records (vx, vy, vz, m) of the set idx (null: the first n) of 3 x N rows;
+// with pos non-null also the mixed position records into rec.
 cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const int* idx, int n,
-                            void* vrec, cudaStream_t s);
+                            void* vrec, const double* pos, void* rec, cudaStream_t s);
 // Mixed time steps with packed FP32 pairs (steps_x2.cu); part: steps_x2_part_bytes bytes.
 size_t steps_x2_part_bytes(int n, int sm_count);
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
@@ -338,10 +339,8 @@ cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, co
                                    double eta_ff, double eta_fb, double eta_jerk, double eps2,
                                    void* rec_ws, void* vrec_ws, double* step, int* err,
                                    cudaStream_t s);
-cudaError_t launch_level_steps(int n, const int* ids, double* step, double* step0, int level0,
-                               cudaStream_t s);
-cudaError_t launch_partition(int n, const int* ids, const double* step, double tau, int force_slow,
-                             int* S, int* F, int* counts, cudaStream_t s);
+cudaError_t launch_partition(int n, const int* ids, double* step, double* step0, int level0,
+                             double tau, int force_slow, int* S, int* F, int* counts, cudaStream_t s);
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s);
 cudaError_t launch_hhs_small(int precision, const SmallArgs& a, cudaStream_t s);
 int small_max();
