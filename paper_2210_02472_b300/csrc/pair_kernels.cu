@@ -29,6 +29,7 @@
 // overlapping the CTA's own i-range; general lists: every tile, by global id) run a
 // checked loop variant that replaces r^2 by 1 for the self pair (whose separation is
 // exactly 0, so its term vanishes).  All other tiles run the unchecked loop.
+#include <algorithm>
 #include <type_traits>
 
 #include "fsi_internal.cuh"
@@ -1487,6 +1488,197 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
             red_add(a.accum + (size_t)q * a.n + ib + 32 * u, sum);
         }
     }
+}
+
+// =================================================================================
+// Bipartite packed symmetric kernel: the two directions of a cross-level pass (Sect. 2.2,
+// S <- F and F <- S of disjoint sets) with every S-F pair evaluated once and added to both
+// particles (Newton's third law; for the gradient, the inter-level accelerations a_S of
+// S <- F and a_F of F <- S make the pair term antisymmetric up to the masses).  Work
+// items (blockIdx.x = b * nchunk + c): i-block b of 256 I particles of S in registers
+// against chunk c of `chunk` source tiles of F.  Hi/lo (near) form only: the sets are in
+// no spatial order.  Both sides are added into FP64 accumulators (red.global.add); two
+// finalize launches then apply the epilogues.
+struct CrossArgs {
+    const void* irec; const void* iacc;   // S: position / accel records, n_i
+    const void* jrec; const void* jacc;   // F: position / accel records, n_j
+    int n_i, n_j;
+    int chunk, nchunk;
+    double eps2;
+    double* acc_i;      // 3 x n_i, zeroed before the launch
+    double* acc_j;      // 3 x n_j, zeroed before the launch
+    int* err;
+    long long timeout_ns;
+};
+
+template <int KIND, int I, int MINB>
+__global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const CrossArgs a) {
+    static_assert(I % 2 == 0, "particles are handled in packed pairs");
+    constexpr int NP = I / 2;
+    constexpr int ACCREC = SymCfg<FSI_MIXED, KIND>::ACCREC;
+    constexpr int SB = kTileJ * (kRec + ACCREC);
+    constexpr int JPART = SymCfg<FSI_MIXED, KIND>::JPART;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    float* jpart = reinterpret_cast<float*>(smem + kStages * SB);
+    float4* acc_s = reinterpret_cast<float4*>(smem + kStages * SB + JPART);
+
+    const int b = blockIdx.x / a.nchunk;
+    const int c = blockIdx.x % a.nchunk;
+    const int ntj = (a.n_j + kTileJ - 1) / kTileJ;
+    const int t0 = c * a.chunk;
+    const int t1 = min(t0 + a.chunk, ntj);
+    if (t0 >= t1) return;                       // uniform: before any barrier
+    const int ntiles = t1 - t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = b * (kThreads * I);
+
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int st = t % kStages;
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n_j - jt);
+        unsigned char* base = smem + st * SB;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC));
+        bulk_g2s(base, (const unsigned char*)a.jrec + (size_t)jt * kRec, (uint32_t)cnt * kRec, &bars[st]);
+        if (ACCREC)
+            bulk_g2s(base + kTileJ * kRec, (const unsigned char*)a.jacc + (size_t)jt * ACCREC,
+                     (uint32_t)cnt * ACCREC, &bars[st]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+
+    X2I pp[NP];
+    float2 f[NP][3];
+    const int ib = i0 + warp * (32 * I) + lane;     // particle u of this thread: ib + 32 u
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        const bool valid = ib + 32 * u < a.n_i;
+        const int i = min(ib + 32 * u, a.n_i - 1);
+        const RecMix r = reinterpret_cast<const RecMix*>(a.irec)[i];
+        float nm = 0.f, nax = 0.f, nay = 0.f, naz = 0.f;
+        if constexpr (KIND == KIND_GRAD) {
+            const float4 ai = reinterpret_cast<const float4*>(a.iacc)[i];
+            nax = -ai.x; nay = -ai.y; naz = -ai.z;
+            nm = valid ? -ai.w : 0.f;
+        }
+        const int h = u & 1;
+        X2I& q = pp[u >> 1];
+        set_half(q.nxh, h, -r.hi.x); set_half(q.nyh, h, -r.hi.y); set_half(q.nzh, h, -r.hi.z);
+        set_half(q.nxl, h, -r.lo.x); set_half(q.nyl, h, -r.lo.y); set_half(q.nzl, h, -r.lo.z);
+        // a receiver past the end contributes nothing to the source side
+        set_half(q.nA, h, valid ? -r.hi.w : 0.f);
+        set_half(q.nB, h, valid ? -r.lo.w : 0.f);
+        set_half(q.nm, h, nm);
+        set_half(q.nax, h, nax); set_half(q.nay, h, nay); set_half(q.naz, h, naz);
+    }
+#pragma unroll
+    for (int p = 0; p < NP; ++p) {
+        f[p][0] = f[p][1] = f[p][2] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int q = 0; q < 3; ++q) acc_s[(p * 3 + q) * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    const float2 eps2 = bc2((float)a.eps2);
+    float2 D0[NP][3];                           // unused by the near form
+    bool aborted = false;
+    int t_stop = ntiles;
+    for (int t = 0; t < ntiles; ++t) {
+        const int st = t % kStages;
+        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n_j - jt);
+        const unsigned char* base = smem + st * SB;
+        const RecMix* rec = reinterpret_cast<const RecMix*>(base);
+        const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            const int jend = min(cnt, k0 + 32);
+            if (jend - k0 < 32) {
+                for (int jj = k0; jj < jend; jj += 4)
+                    x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+            } else {
+                for (int jj = k0; jj < jend; jj += 4)
+                    x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                ff_add2(acc_s[(p * 3 + q) * kThreads + tid], f[p][q]);
+                f[p][q] = make_float2(0.f, 0.f);
+            }
+        if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+        if (tid < cnt) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                float sum = 0.f;
+#pragma unroll
+                for (int w = 0; w < kThreads / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
+                red_add(a.acc_j + (size_t)q * a.n_j + jt + tid, (double)sum);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+    }
+    if (aborted) {
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int t = t_stop; t < issued; ++t)
+                mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1), a.timeout_ns, nullptr);
+        }
+        __syncthreads();
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        if (ib + 32 * u >= a.n_i) continue;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) {
+            const float4 v = acc_s[((u >> 1) * 3 + q) * kThreads + tid];
+            const double sum = (u & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
+            red_add(a.acc_i + (size_t)q * a.n_i + ib + 32 * u, sum);
+        }
+    }
+}
+
+template <int KIND>
+static cudaError_t launch_cross_x2_t(const CrossArgs& a, cudaStream_t s) {
+    constexpr int I = 4;
+    constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC);
+    constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + (I / 2) * 3 * kThreads * 16;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(cross_mixed_x2_kernel<KIND, I, 2>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long nb = (a.n_i + kThreads * I - 1) / (kThreads * I);
+    const long long grid = nb * a.nchunk;
+    if (grid <= 0 || grid > 2147483647LL) return cudaErrorInvalidValue;
+    { cross_mixed_x2_kernel<KIND, I, 2><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    return cudaGetLastError();
+}
+
+int cross_block_size() { return kThreads * 4; }
+
+cudaError_t launch_cross_pair(int kind, const void* irec, const void* iacc, int n_i,
+                              const void* jrec, const void* jacc, int n_j, double eps2, int chunk,
+                              double* acc_i, double* acc_j, int* err, long long timeout_ns,
+                              cudaStream_t s) {
+    if (n_i <= 0 || n_j <= 0) return cudaErrorInvalidValue;
+    CrossArgs a{};
+    a.irec = irec; a.iacc = iacc; a.jrec = jrec; a.jacc = jacc;
+    a.n_i = n_i; a.n_j = n_j;
+    const int ntj = (n_j + kTileJ - 1) / kTileJ;
+    a.chunk = std::max(1, std::min(chunk, ntj));
+    a.nchunk = (ntj + a.chunk - 1) / a.chunk;
+    a.eps2 = eps2; a.acc_i = acc_i; a.acc_j = acc_j; a.err = err; a.timeout_ns = timeout_ns;
+    return kind == KIND_ACC ? launch_cross_x2_t<KIND_ACC>(a, s) : launch_cross_x2_t<KIND_GRAD>(a, s);
 }
 
 // MINB: resident CTAs per SM the register budget is sized for (2: 128 registers per
