@@ -657,11 +657,16 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     if (mixed) {
         CK(ensure(c->rec[1], pad_tile(n) * 32));
         CK(ensure(c->accrec[1], pad_tile(n) * 32));
-        CK(ensure(c->stpart, steps_x2_part_bytes(n, c->sm_count)));
+        const bool sym = c->p.symmetric && n >= steps_sym_min_n();
+        CK(ensure(c->stpart, sym ? steps_sym_work_bytes(n) : steps_x2_part_bytes(n, c->sm_count)));
         CU(launch_pack_vel(N, vel, mass, Pids, n, c->accrec[1].p, pos, c->rec[1].p, s));
-        CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
-                           c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c), c->sm_count,
-                           wide_limit(c), s));
+        if (sym)
+            CU(launch_steps_sym(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
+                                c->p.eta_jerk, c->stpart.p, step, c->err_d, budget(c), c->sm_count, s));
+        else
+            CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
+                               c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c),
+                               c->sm_count, wide_limit(c), s));
     }
     else
         CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,

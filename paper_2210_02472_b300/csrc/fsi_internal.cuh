@@ -340,6 +340,13 @@ cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const 
                             void* vrec, const double* pos, void* rec, cudaStream_t s);
 // Mixed time steps with packed FP32 pairs (steps_x2.cu); part: steps_x2_part_bytes bytes.
 size_t steps_x2_part_bytes(int n, int sm_count);
+// Symmetric mixed time steps (every unordered pair once) for sets of at least
+// steps_sym_min_n() particles; work: steps_sym_work_bytes(n) bytes (8-byte aligned).
+size_t steps_sym_work_bytes(int n);
+int steps_sym_min_n();
+cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
+                             double eta_fb, double eta_jerk, void* work, double* step, int* err,
+                             long long timeout_ns, int sm_count, cudaStream_t s);
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                             double eta_fb, double eta_jerk, float* part, double* step, int* err,
                             long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s);

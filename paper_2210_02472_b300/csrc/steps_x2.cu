@@ -18,6 +18,7 @@
 
 #include "fsi_internal.cuh"
 #include "pair_math.cuh"
+#include "sym_x2.cuh"
 
 namespace fsi {
 
@@ -306,6 +307,333 @@ __global__ void __launch_bounds__(kStThreads) steps_wide_kernel(const StepX2Args
     if (!active || g != 0) return;
     if (!(isfinite(ax) && isfinite(ay) && isfinite(az))) set_error(a.err, FSI_ERR_NONFINITE);
     a.step[i] = step_from(ff, fb, ax, ay, az, jx, jy, jz, a.eta_ff, a.eta_fb, a.eta_jerk);
+}
+
+// =================================================================================
+// Symmetric form: every unordered pair of the set once.  The pair quantities are
+// symmetric (r^3 / (m_i + m_j), r^2 / |u|^2, and r.u, hence c3) or flip sign with
+// d -> -d, u -> -u (the a and j terms), so the term of i on j is the term of j on i with
+// m_i in place of m_j and the opposite sign.  Work items (blockIdx.x = b * (1 + nchunk) +
+// c): block b of 1024 receivers (4 per thread) against c = 0: its own 4 tiles, one-sided
+// with the self pair excluded by index, or c >= 1: chunk c - 1 of the tiles above it, both
+// sides.  The source side of a group of 4 sources is reduced across the warp (lane
+// permutation and shuffles: minima by fminf, sums by adds), across the CTA's warps in
+// shared memory, then into the set's accumulators: minima as float bits by atomicMin
+// (non-negative floats order as unsigned integers), sums by red.global.add.f64.  The
+// receiver side goes to the same accumulators at the end of the item; a finalize kernel
+// turns them into steps.
+namespace {
+constexpr int kSsBlock = kStThreads * kStI;                       // receivers per block
+constexpr int kSsQ = 8;                                           // ff, fb, ax..az, jx..jz
+constexpr int kSsJpart = (kStThreads / 32) * kStTile * kSsQ * 4;   // per-warp source rows
+constexpr int kSsSmem = kStages * kStStage + kSsJpart;
+}  // namespace
+
+struct StepSymArgs {
+    int n;
+    const RecMix* rec;
+    const float4* vrec;
+    float eps2;
+    int chunk, nchunk;
+    unsigned* mins;         // 2 x n: float bits of the ff and fb minima (+inf to start)
+    double* sums;           // 6 x n: a and j sums (0 to start)
+    int* err;
+    long long timeout_ns;
+};
+
+// Source j on both receivers of a packed pair (all receivers valid, j none of them):
+// receiver side into s, source side into pj (a_j, j_j per half) and the running minima.
+template <bool SOFT>
+__device__ __forceinline__ void step_pair_sym(const float4 h, const float4 l, const float4 vj,
+                                              const StepX2I& p, float2 nmi, float2 eps2,
+                                              StepX2Acc& s, float2 (&pj)[6], float& jff, float& jfb,
+                                              bool& coincident) {
+    const float2 dx = __fadd2_rn(__fadd2_rn(bc2(h.x), p.nxh), __fadd2_rn(bc2(l.x), p.nxl));
+    const float2 dy = __fadd2_rn(__fadd2_rn(bc2(h.y), p.nyh), __fadd2_rn(bc2(l.y), p.nyl));
+    const float2 dz = __fadd2_rn(__fadd2_rn(bc2(h.z), p.nzh), __fadd2_rn(bc2(l.z), p.nzl));
+    const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
+    coincident |= (d2.x == 0.0f) | (d2.y == 0.0f);
+    const float2 ux = __fadd2_rn(bc2(vj.x), p.nu), uy = __fadd2_rn(bc2(vj.y), p.nv),
+                 uz = __fadd2_rn(bc2(vj.z), p.nw);
+    const float2 u2 = __ffma2_rn(ux, ux, __ffma2_rn(uy, uy, __fmul2_rn(uz, uz)));
+    const float2 s2 = SOFT ? __fadd2_rn(d2, eps2) : d2;
+    float2 y = rsqrt2(s2);
+    y = __fmul2_rn(y, __ffma2_rn(__fmul2_rn(s2, bc2(-0.5f)), __fmul2_rn(y, y), bc2(1.5f)));
+    const float2 y2 = __fmul2_rn(y, y);
+    const float2 y3 = __fmul2_rn(y2, y);
+    const float2 wi = __fmul2_rn(bc2(vj.w), y3);                       //  m_j / s^3
+    const float2 wj = __fmul2_rn(nmi, y3);                             // -m_i / s^3
+    const float2 r = __fmul2_rn(d2, SOFT ? rsqrt2(d2) : y);           // |d|
+    const float2 tff = __fmul2_rn(__fmul2_rn(d2, r), rcp2(__fadd2_rn(bc2(vj.w), p.m)));
+    const float2 tfb = __fmul2_rn(d2, rcp2(u2));
+    s.ff.x = fminf(s.ff.x, tff.x); s.ff.y = fminf(s.ff.y, tff.y);
+    s.fb.x = fminf(s.fb.x, tfb.x); s.fb.y = fminf(s.fb.y, tfb.y);
+    jff = fminf(jff, fminf(tff.x, tff.y));
+    jfb = fminf(jfb, fminf(tfb.x, tfb.y));
+    const float2 rv = __ffma2_rn(dx, ux, __ffma2_rn(dy, uy, __fmul2_rn(dz, uz)));
+    const float2 c3 = __fmul2_rn(__fmul2_rn(rv, y2), bc2(-3.0f));
+    const float2 tx = __ffma2_rn(c3, dx, ux), ty = __ffma2_rn(c3, dy, uy), tz = __ffma2_rn(c3, dz, uz);
+    s.ax = __ffma2_rn(wi, dx, s.ax); s.ay = __ffma2_rn(wi, dy, s.ay); s.az = __ffma2_rn(wi, dz, s.az);
+    s.jx = __ffma2_rn(wi, tx, s.jx); s.jy = __ffma2_rn(wi, ty, s.jy); s.jz = __ffma2_rn(wi, tz, s.jz);
+    pj[0] = __ffma2_rn(wj, dx, pj[0]); pj[1] = __ffma2_rn(wj, dy, pj[1]); pj[2] = __ffma2_rn(wj, dz, pj[2]);
+    pj[3] = __ffma2_rn(wj, tx, pj[3]); pj[4] = __ffma2_rn(wj, ty, pj[4]); pj[5] = __ffma2_rn(wj, tz, pj[5]);
+}
+
+// A group of 4 sources (lane l takes source jj + (g ^ (l >> 3)) at step g), then the
+// warp's source-side totals of the group into jpart (row per warp, 8 values per source).
+template <bool SOFT, bool FULL>
+__device__ __forceinline__ void steps_sym_group(int jj, int cnt, int lane, int warp,
+                                                const RecMix* rec, const float4* vr,
+                                                const StepX2I (&pp)[kStNP], const float2 (&nmi)[kStNP],
+                                                float2 eps2, StepX2Acc (&acc)[kStNP], float* jpart,
+                                                bool& coincident) {
+    const int L = lane >> 3;
+    float fj[4][kSsQ];
+#pragma unroll
+    for (int g = 0; g < 4; ++g) {
+        fj[g][0] = fj[g][1] = INFINITY;
+#pragma unroll
+        for (int q = 2; q < kSsQ; ++q) fj[g][q] = 0.f;
+        const int jg = jj + (g ^ L);
+        if (FULL || jg < cnt) {
+            const float4 h = rec[jg].hi, l = rec[jg].lo, v = vr[jg];
+            float2 pj[6];
+#pragma unroll
+            for (int q = 0; q < 6; ++q) pj[q] = make_float2(0.f, 0.f);
+            float jff = INFINITY, jfb = INFINITY;
+#pragma unroll
+            for (int p = 0; p < kStNP; ++p)
+                step_pair_sym<SOFT>(h, l, v, pp[p], nmi[p], eps2, acc[p], pj, jff, jfb, coincident);
+            fj[g][0] = jff;
+            fj[g][1] = jfb;
+#pragma unroll
+            for (int q = 0; q < 6; ++q) fj[g][2 + q] = pj[q].x + pj[q].y;
+        }
+    }
+#pragma unroll
+    for (int q = 0; q < kSsQ; ++q) {
+        float r;
+        if (q < 2) {
+            const float k0 = fminf(fj[0][q], __shfl_xor_sync(0xffffffffu, fj[2][q], 16));
+            const float k1 = fminf(fj[1][q], __shfl_xor_sync(0xffffffffu, fj[3][q], 16));
+            r = fminf(k0, __shfl_xor_sync(0xffffffffu, k1, 8));
+            r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 4));
+            r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 2));
+            r = fminf(r, __shfl_xor_sync(0xffffffffu, r, 1));
+        } else {
+            const float k0 = fj[0][q] + __shfl_xor_sync(0xffffffffu, fj[2][q], 16);
+            const float k1 = fj[1][q] + __shfl_xor_sync(0xffffffffu, fj[3][q], 16);
+            r = k0 + __shfl_xor_sync(0xffffffffu, k1, 8);
+            r += __shfl_xor_sync(0xffffffffu, r, 4);
+            r += __shfl_xor_sync(0xffffffffu, r, 2);
+            r += __shfl_xor_sync(0xffffffffu, r, 1);
+        }
+        fj[0][q] = r;
+    }
+    const int jl = jj + L;
+    if ((lane & 7) == 0 && (FULL || jl < cnt)) {
+        float* dst = jpart + ((size_t)warp * kStTile + jl) * kSsQ;
+#pragma unroll
+        for (int q = 0; q < kSsQ; ++q) dst[q] = fj[0][q];
+    }
+}
+
+__device__ __forceinline__ void steps_sym_put(const StepSymArgs& a, int i, float ff, float fb,
+                                              const float (&sum)[6]) {
+    atomicMin(a.mins + i, __float_as_uint(ff));
+    atomicMin(a.mins + (size_t)a.n + i, __float_as_uint(fb));
+#pragma unroll
+    for (int q = 0; q < 6; ++q) red_add(a.sums + (size_t)q * a.n + i, (double)sum[q]);
+}
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kStThreads, 1) steps_sym_kernel(const StepSymArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    float* jpart = reinterpret_cast<float*>(smem + kStages * kStStage);
+    const int b = blockIdx.x / (1 + a.nchunk);
+    const int c = blockIdx.x % (1 + a.nchunk);
+    const int ntj = (a.n + kStTile - 1) / kStTile;
+    const bool diag = (c == 0);
+    int t0, t1;
+    if (diag) { t0 = b * kStI; t1 = min((b + 1) * kStI, ntj); }
+    else { t0 = (b + 1) * kStI + (c - 1) * a.chunk; t1 = min(t0 + a.chunk, ntj); }
+    if (t0 >= t1) return;                       // uniform: before any barrier
+    const int ntiles = t1 - t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = b * kSsBlock;
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int st = t % kStages;
+        const int jt = (t0 + t) * kStTile;
+        const int cnt = min(kStTile, a.n - jt);
+        unsigned char* base = smem + st * kStStage;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * 48u);
+        bulk_g2s(base, a.rec + jt, (uint32_t)cnt * 32u, &bars[st]);
+        bulk_g2s(base + kStTile * 32, a.vrec + jt, (uint32_t)cnt * 16u, &bars[st]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+    // receivers of this thread: ib + 32 u (u = 0..3); packed pair p holds u = 2p, 2p + 1
+    const int ib = i0 + warp * (32 * kStI) + lane;
+    StepX2I pp[kStNP];
+    float2 nmi[kStNP];
+    StepX2Acc acc[kStNP];
+    int me[kStI];
+#pragma unroll
+    for (int u = 0; u < kStI; ++u) {
+        const int i = min(ib + 32 * u, a.n - 1);
+        me[u] = i;
+        const RecMix r = a.rec[i];
+        const float4 v = a.vrec[i];
+        const int h = u & 1;
+        StepX2I& q = pp[u >> 1];
+        set_half(q.nxh, h, -r.hi.x); set_half(q.nyh, h, -r.hi.y); set_half(q.nzh, h, -r.hi.z);
+        set_half(q.nxl, h, -r.lo.x); set_half(q.nyl, h, -r.lo.y); set_half(q.nzl, h, -r.lo.z);
+        set_half(q.nu, h, -v.x); set_half(q.nv, h, -v.y); set_half(q.nw, h, -v.z);
+        set_half(q.m, h, v.w);
+        set_half(nmi[u >> 1], h, -v.w);
+    }
+#pragma unroll
+    for (int p = 0; p < kStNP; ++p) {
+        acc[p].ff = acc[p].fb = bc2(INFINITY);
+        acc[p].ax = acc[p].ay = acc[p].az = acc[p].jx = acc[p].jy = acc[p].jz = bc2(0.0f);
+    }
+    const float2 eps2 = bc2(a.eps2);
+    bool coincident = false, aborted = false;
+    int t_stop = ntiles;
+    for (int t = 0; t < ntiles; ++t) {
+        const int st = t % kStages;
+        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+        const int jt = (t0 + t) * kStTile;
+        const int cnt = min(kStTile, a.n - jt);
+        const unsigned char* base = smem + st * kStStage;
+        const RecMix* rec = reinterpret_cast<const RecMix*>(base);
+        const float4* vr = reinterpret_cast<const float4*>(base + kStTile * 32);
+        if (diag) {
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 h = rec[jj].hi, l = rec[jj].lo, v = vr[jj];
+                const int j = jt + jj;
+#pragma unroll
+                for (int p = 0; p < kStNP; ++p)
+                    step_pair_x2<true, SOFT>(h, l, v, pp[p], eps2, j == me[2 * p], j == me[2 * p + 1],
+                                             acc[p], coincident);
+            }
+        } else {
+            // blocks with tiles above them are full: every receiver is valid
+            for (int k0 = 0; k0 < cnt; k0 += 32) {
+                const int jend = min(cnt, k0 + 32);
+                if (jend - k0 < 32) {
+                    for (int jj = k0; jj < jend; jj += 4)
+                        steps_sym_group<SOFT, false>(jj, cnt, lane, warp, rec, vr, pp, nmi, eps2, acc, jpart, coincident);
+                } else {
+                    for (int jj = k0; jj < jend; jj += 4)
+                        steps_sym_group<SOFT, true>(jj, cnt, lane, warp, rec, vr, pp, nmi, eps2, acc, jpart, coincident);
+                }
+            }
+        }
+        if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+        if (!diag && tid < cnt) {
+            float ff = INFINITY, fb = INFINITY, sum[6] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+            for (int w = 0; w < kStThreads / 32; ++w) {
+                const float* row = jpart + ((size_t)w * kStTile + tid) * kSsQ;
+                ff = fminf(ff, row[0]);
+                fb = fminf(fb, row[1]);
+#pragma unroll
+                for (int q = 0; q < 6; ++q) sum[q] += row[2 + q];
+            }
+            steps_sym_put(a, jt + tid, ff, fb, sum);
+        }
+        __syncthreads();
+        if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+    }
+    if (aborted) {
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int t = t_stop; t < issued; ++t)
+                mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1), a.timeout_ns, nullptr);
+        }
+        __syncthreads();
+        return;
+    }
+    if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
+#pragma unroll
+    for (int u = 0; u < kStI; ++u) {
+        const int i = ib + 32 * u;
+        if (i >= a.n) continue;
+        const StepX2Acc& sa = acc[u >> 1];
+        const bool hi = (u & 1) != 0;
+        const float sum[6] = {hi ? sa.ax.y : sa.ax.x, hi ? sa.ay.y : sa.ay.x, hi ? sa.az.y : sa.az.x,
+                              hi ? sa.jx.y : sa.jx.x, hi ? sa.jy.y : sa.jy.x, hi ? sa.jz.y : sa.jz.x};
+        steps_sym_put(a, i, hi ? sa.ff.y : sa.ff.x, hi ? sa.fb.y : sa.fb.x, sum);
+    }
+}
+
+__global__ void steps_sym_init_kernel(int n, unsigned* mins, double* sums) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    mins[i] = mins[(size_t)n + i] = 0x7f800000u;      // +inf
+#pragma unroll
+    for (int q = 0; q < 6; ++q) sums[(size_t)q * n + i] = 0.0;
+}
+
+__global__ void steps_sym_finalize_kernel(int n, const unsigned* mins, const double* sums,
+                                          double eta_ff, double eta_fb, double eta_jerk,
+                                          double* step, int* err) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const float ff = __uint_as_float(mins[i]), fb = __uint_as_float(mins[(size_t)n + i]);
+    float v[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) v[q] = (float)sums[(size_t)q * n + i];
+    if (!(isfinite(v[0]) && isfinite(v[1]) && isfinite(v[2]))) set_error(err, FSI_ERR_NONFINITE);
+    step[i] = step_from(ff, fb, v[0], v[1], v[2], v[3], v[4], v[5], eta_ff, eta_fb, eta_jerk);
+}
+
+size_t steps_sym_work_bytes(int n) { return (size_t)n * (2 * sizeof(unsigned) + 6 * sizeof(double)); }
+int steps_sym_min_n() { return 4 * kSsBlock; }
+
+// work: steps_sym_work_bytes(n) bytes, 8-byte aligned.
+cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
+                             double eta_fb, double eta_jerk, void* work, double* step, int* err,
+                             long long timeout_ns, int sm_count, cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    static bool attr[2] = {false, false};
+    const bool soft = eps2 > 0.0;
+    if (!attr[soft]) {
+        cudaError_t e = soft ? cudaFuncSetAttribute(steps_sym_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSsSmem)
+                             : cudaFuncSetAttribute(steps_sym_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSsSmem);
+        if (e != cudaSuccess) return e;
+        attr[soft] = true;
+    }
+    StepSymArgs a{};
+    a.n = n;
+    a.rec = reinterpret_cast<const RecMix*>(rec);
+    a.vrec = reinterpret_cast<const float4*>(vrec);
+    a.eps2 = (float)eps2;
+    a.sums = reinterpret_cast<double*>(work);
+    a.mins = reinterpret_cast<unsigned*>(a.sums + 6 * (size_t)n);
+    a.err = err;
+    a.timeout_ns = timeout_ns;
+    const long long ntj = (n + kStTile - 1) / kStTile;
+    const long long nb = (n + kSsBlock - 1) / kSsBlock;
+    // about 8 items per resident CTA, at most 64 tiles each
+    const long long visits = nb * ntj / 2 + 1;
+    a.chunk = (int)std::max(1LL, std::min(64LL, visits / (8LL * sm_count)));
+    const long long above = ntj > kStI ? ntj - kStI : 0;
+    a.nchunk = (int)((above + a.chunk - 1) / a.chunk);
+    const long long grid = nb * (1 + a.nchunk);
+    if (grid > 2147483647LL) return cudaErrorInvalidValue;
+    { steps_sym_init_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, a.mins, a.sums); note_launch(); }
+    if (soft) { steps_sym_kernel<true><<<(unsigned)grid, kStThreads, kSsSmem, s>>>(a); note_launch(); }
+    else { steps_sym_kernel<false><<<(unsigned)grid, kStThreads, kSsSmem, s>>>(a); note_launch(); }
+    { steps_sym_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, a.mins, a.sums, eta_ff, eta_fb, eta_jerk, step, err); note_launch(); }
+    return cudaGetLastError();
 }
 
 size_t steps_x2_part_bytes(int n, int sm_count) {

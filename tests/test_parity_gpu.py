@@ -417,17 +417,22 @@ def test_timesteps_and_energy(F):
     assert abs(e[0] / T - 1) < 1e-13 and abs(e[1] / W - 1) < 1e-12
 
 
-@pytest.mark.parametrize("n", [2, 3, 257, 3000])
+@pytest.mark.parametrize("n", [2, 3, 257, 3000, 4096, 13001])
 @pytest.mark.parametrize("wide", WIDE)
 @pytest.mark.parametrize("eps2", [0.0, 1e-4])
-def test_timesteps_mixed(F, n, wide, eps2):
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_timesteps_mixed(F, n, wide, eps2, symmetric):
     """Mixed time steps against the oracle: the tiled packed kernel, the wide form (small
-    sets by default, every set with wide = 1 << 30), softened and not, and a subset."""
+    sets by default, every set with wide = 1 << 30), the symmetric kernel (sets of >= 4096
+    with symmetric = True; 13001: a ragged last tile and block), softened and not, and a
+    subset."""
+    if n >= 4096 and wide == 1 << 30:
+        pytest.skip("the always-wide context is covered at the smaller sizes")
     c = inputs.plummer(n, 23 + n, imf="kroupa")
     ref = oracle.timesteps(c.pos, c.vel, c.mass, eps2=eps2)
     P = inputs.random_subset(n, max(1, n // 3), 9)
     refp = oracle.timesteps(c.pos, c.vel, c.mass, P, eps2=eps2)
-    with F.Context("mixed", eps2=eps2, wide_ctas=wide) as ctx:
+    with F.Context("mixed", eps2=eps2, wide_ctas=wide, symmetric=symmetric) as ctx:
         s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
         sp = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P)))
         assert F.fsi_sync_status(ctx) == F.FSI_OK
