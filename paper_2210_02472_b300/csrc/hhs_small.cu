@@ -149,16 +149,6 @@ __device__ __forceinline__ void write_vf(SmallSmem<P>& S, int k) {
     }
 }
 
-// Source accelerations of a gradient pass (FP32 record in the mixed precision: the
-// rounded float-float sum, no FP64 instruction).
-template <int P>
-__device__ __forceinline__ void write_arec(SmallSmem<P>& S, int k) {
-    if constexpr (P == FSI_MIXED)
-        S.arec[k] = make_float4(S.a[0][k].x + S.a[0][k].y, S.a[1][k].x + S.a[1][k].y,
-                                S.a[2][k].x + S.a[2][k].y, S.vf[k].w);
-    else S.arec[k] = make_d4(S.a[0][k], S.a[1][k], S.a[2][k], S.m[k]);
-}
-
 // Threads per receiver of a pass with nA receivers: the largest power of two (<= 32) that
 // still fits nA groups into the CTA.  Deep levels hold few particles, so their passes are
 // latency-bound; a group of G consecutive lanes splits the sources of one receiver and
@@ -170,9 +160,61 @@ __device__ __forceinline__ int group_size(int nA) {
 }
 
 // out[:, A[t]] = sum over B of the acceleration (kind 0) or gradient (kind 1) pair terms
+// What a pass does with the sum of receiver k, in its group's leader lane: store it in
+// out, write k's acceleration record (an acc pass that feeds a gradient pass), and / or
+// kick v_k with weight w by the sum (acc) or by a + cg G with a from S.a (gradient).
+// No pass reads velocities, so a kick needs no barrier before the next pass.
+template <int P>
+struct PassOut {
+    SumT<P> (*out)[kSmallMax];
+    bool arec;
+    bool kick;
+    StT<P> w;
+    CgT<P> cg;
+};
+
+template <int P>
+__device__ __forceinline__ PassOut<P> pass_store(SumT<P> (*out)[kSmallMax], bool arec) {
+    PassOut<P> o{};
+    o.out = out;
+    o.arec = arec;
+    return o;
+}
+
+template <int P>
+__device__ __forceinline__ PassOut<P> pass_kick(StT<P> w, CgT<P> cg) {
+    PassOut<P> o{};
+    o.kick = true;
+    o.w = w;
+    o.cg = cg;
+    return o;
+}
+
+template <int P, int KIND>
+__device__ __forceinline__ void pass_leader(SmallSmem<P>& S, int k, const SumT<P> (&sum)[3],
+                                            const PassOut<P>& o) {
+    if (o.out)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o.out[c][k] = sum[c];
+    if (o.arec) {
+        if constexpr (P == FSI_MIXED)
+            S.arec[k] = make_float4(sum[0].x + sum[0].y, sum[1].x + sum[1].y, sum[2].x + sum[2].y, S.vf[k].w);
+        else
+            S.arec[k] = make_d4(sum[0], sum[1], sum[2], S.m[k]);
+    }
+    if (o.kick) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const SumT<P> ac = KIND == 1 ? grad_acc(S.a[c][k], o.cg, sum[c]) : sum[c];
+            S.v[c][k] = axpy(o.w, ac, S.v[c][k]);
+        }
+        write_vf<P>(S, k);
+    }
+}
+
 template <int P, int KIND>
 __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
-                           const unsigned short* B, int nB, double eps2, SumT<P> (*out)[kSmallMax],
+                           const unsigned short* B, int nB, double eps2, const PassOut<P>& o,
                            unsigned long long* work) {
     const int t = threadIdx.x;
     if (t == 0 && work) atomicAdd(work + KIND, (unsigned long long)nA * (unsigned long long)nB);
@@ -217,13 +259,15 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
                 sl[c] = __fadd_rn(sl[c], ol);
             }
         if (active && g == 0) {
+            SumT<P> sum[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 float h = 0.f, l = 0.f;                  // renormalised: h = fl(hi + lo)
                 ff_acc(h, l, sh[c]);
                 ff_acc(h, l, sl[c]);
-                out[c][k] = make_float2(h, l);
+                sum[c] = make_float2(h, l);
             }
+            pass_leader<P, KIND>(S, k, sum, o);
         }
     } else {
         double r[3] = {0.0, 0.0, 0.0};
@@ -243,9 +287,8 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
 #pragma unroll
             for (int q = 0; q < 3; ++q) r[q] += __shfl_xor_sync(0xffffffffu, r[q], o);
         if (active && g == 0) {
-            out[0][k] = r[0];
-            out[1][k] = r[1];
-            out[2][k] = r[2];
+            const SumT<P> sum[3] = {r[0], r[1], r[2]};
+            pass_leader<P, KIND>(S, k, sum, o);
         }
     }
 }
@@ -356,20 +399,6 @@ __device__ void small_grad_steps(SmallSmem<P>& S, const unsigned short* L, int n
 }
 
 template <int P>
-__device__ void small_kick(SmallSmem<P>& S, const unsigned short* L, int n, StT<P> w, bool with_grad,
-                           CgT<P> cg) {
-    const int t = threadIdx.x;
-    if (t >= n) return;
-    const int k = L[t];
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const SumT<P> ac = with_grad ? grad_acc(S.a[c][k], cg, S.g[c][k]) : S.a[c][k];
-        S.v[c][k] = axpy(w, ac, S.v[c][k]);
-    }
-    write_vf<P>(S, k);
-}
-
-template <int P>
 __device__ void small_drift(SmallSmem<P>& S, const unsigned short* L, int n, StT<P> w) {
     const int t = threadIdx.x;
     if (t >= n) return;
@@ -438,17 +467,12 @@ __device__ void small_fsi(SmallSmem<P>& S, const unsigned short* L, int n, StT<P
     const StT<P> h2 = w_half(h), h6 = w_sixth(h), h23 = w_two_thirds(h);
     const CgT<P> cg = w_cg(h);
     small_pn_kick<P>(S, L, n, nullptr, 0, h2, a);
-    small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
-    small_kick<P>(S, L, n, h6, false, cg); __syncthreads();
+    small_pass<P, 0>(S, L, n, L, n, a.eps2, pass_kick<P>(h6, cg), a.work); __syncthreads();
     small_drift<P>(S, L, n, h2); __syncthreads();
-    small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
-    if (threadIdx.x < n) write_arec<P>(S, L[threadIdx.x]);
-    __syncthreads();
-    small_pass<P, 1>(S, L, n, L, n, a.eps2, S.g, a.work); __syncthreads();
-    small_kick<P>(S, L, n, h23, true, cg); __syncthreads();
+    small_pass<P, 0>(S, L, n, L, n, a.eps2, pass_store<P>(S.a, true), a.work); __syncthreads();
+    small_pass<P, 1>(S, L, n, L, n, a.eps2, pass_kick<P>(h23, cg), a.work); __syncthreads();
     small_drift<P>(S, L, n, h2); __syncthreads();
-    small_pass<P, 0>(S, L, n, L, n, a.eps2, S.a, a.work); __syncthreads();
-    small_kick<P>(S, L, n, h6, false, cg); __syncthreads();
+    small_pass<P, 0>(S, L, n, L, n, a.eps2, pass_kick<P>(h6, cg), a.work); __syncthreads();
     small_pn_kick<P>(S, L, n, nullptr, 0, h2, a);
 }
 
@@ -458,21 +482,18 @@ template <int P>
 __device__ void small_cross(SmallSmem<P>& S, const unsigned short* Ls, int nS,
                             const unsigned short* Lf, int nF, StT<P> w, bool gradient, CgT<P> cg,
                             const SmallArgs& a) {
-    small_pass<P, 0>(S, Ls, nS, Lf, nF, a.eps2, S.a, a.work);
-    __syncthreads();
-    small_pass<P, 0>(S, Lf, nF, Ls, nS, a.eps2, S.a, a.work);
-    __syncthreads();
-    if (gradient) {
-        if (threadIdx.x < nS) write_arec<P>(S, Ls[threadIdx.x]);
-        if (threadIdx.x < nF) write_arec<P>(S, Lf[threadIdx.x]);
+    // the two directions touch disjoint velocities and read only records: one phase each
+    if (!gradient) {
+        small_pass<P, 0>(S, Ls, nS, Lf, nF, a.eps2, pass_kick<P>(w, cg), a.work);
+        small_pass<P, 0>(S, Lf, nF, Ls, nS, a.eps2, pass_kick<P>(w, cg), a.work);
         __syncthreads();
-        small_pass<P, 1>(S, Ls, nS, Lf, nF, a.eps2, S.g, a.work);
-        __syncthreads();
-        small_pass<P, 1>(S, Lf, nF, Ls, nS, a.eps2, S.g, a.work);
-        __syncthreads();
+        return;
     }
-    small_kick<P>(S, Ls, nS, w, gradient, cg);
-    small_kick<P>(S, Lf, nF, w, gradient, cg);
+    small_pass<P, 0>(S, Ls, nS, Lf, nF, a.eps2, pass_store<P>(S.a, true), a.work);
+    small_pass<P, 0>(S, Lf, nF, Ls, nS, a.eps2, pass_store<P>(S.a, true), a.work);
+    __syncthreads();
+    small_pass<P, 1>(S, Ls, nS, Lf, nF, a.eps2, pass_kick<P>(w, cg), a.work);
+    small_pass<P, 1>(S, Lf, nF, Ls, nS, a.eps2, pass_kick<P>(w, cg), a.work);
     __syncthreads();
 }
 
@@ -555,11 +576,9 @@ __global__ void __launch_bounds__(kSmallMax, 1) hhs_small_kernel(const SmallArgs
             __syncthreads();
             if (a.eta_grad > 0.0 || a.eta_va > 0.0) {
                 // a and G of the level set from itself, then the gradient criteria
-                small_pass<P, 0>(S, L, f.nP, L, f.nP, a.eps2, S.a, a.work);
+                small_pass<P, 0>(S, L, f.nP, L, f.nP, a.eps2, pass_store<P>(S.a, true), a.work);
                 __syncthreads();
-                if (t < f.nP) write_arec<P>(S, L[t]);
-                __syncthreads();
-                small_pass<P, 1>(S, L, f.nP, L, f.nP, a.eps2, S.g, a.work);
+                small_pass<P, 1>(S, L, f.nP, L, f.nP, a.eps2, pass_store<P>(S.g, false), a.work);
                 __syncthreads();
                 small_grad_steps<P>(S, L, f.nP, a);
                 __syncthreads();
