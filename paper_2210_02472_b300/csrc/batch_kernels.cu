@@ -497,14 +497,19 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
         const float4* arec = reinterpret_cast<const float4*>(base + kBatchTile * 32);
         if (diag) {
             // the block's own tiles, each unordered pair once: warp w holds the block's
-            // 32-record sub-tiles 4w .. 4w+3; a sub-tile above that range is evaluated
-            // symmetrically, one inside it one-sided (self pair excluded by index), one
-            // below it not at all (its pairs with warp w come from the warp that holds it)
+            // 32-record sub-tiles 4w .. 4w+3 (group w); the pairs of groups w and v != w
+            // are evaluated symmetrically by w when (v - w) mod 8 is 1, 2 or 3, or 4 with
+            // w < 4 (by v otherwise), so every warp takes 3 or 4 of the 7 other groups;
+            // its own group one-sided (self pair excluded by index).  A warp past the end of
+            // the cluster holds copies of its last particle and takes no pairs: that
+            // particle's pairs belong to the warp that holds it
+            const bool wvalid = it.block * kBSBlock + warp * (32 * I) < it.n;
             float2 D0[NP][3];
             for (int k0 = 0; k0 < cnt; k0 += 32) {
                 const int jend = min(cnt, k0 + 32);
                 const int sub = 8 * tl + (k0 >> 5);                // sub-tile within the block
-                if (sub > 4 * warp + 3) {
+                const int dv = ((sub >> 2) - warp) & 7;
+                if (wvalid && dv >= 1 && (dv <= 3 || (dv == 4 && warp < 4))) {
                     if (jend - k0 < 32) {
                         for (int jj = k0; jj < jend; jj += 4)
                             x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
@@ -518,7 +523,7 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
                     float* dst = jpart + ((size_t)warp * kBatchTile + k0 + lane) * 3;
                     dst[0] = dst[1] = dst[2] = 0.f;
                 }
-                if (sub < 4 * warp) continue;
+                if (dv != 0) continue;
                 for (int jj = k0; jj < jend; ++jj) {
                     const float4 h = rec[jj].hi;
                     const float4 l = rec[jj].lo;
