@@ -691,67 +691,6 @@ cudaError_t launch_grad_steps(int n, const double* vc, const double* a, const do
     return cudaGetLastError();
 }
 
-// Mixed-precision time steps: the same criteria with FP32 pair arithmetic on the mixed
-// position records (hi/lo separations, FP32-accurate relative to the separation) and FP32
-// velocity records (vx, vy, vz, m); two receivers per thread.
-constexpr int kStepIpt = 2;
-
-__global__ void __launch_bounds__(kAuxTile) timesteps_mixed_kernel(
-    int n, const RecMix* __restrict__ rec, const float4* __restrict__ vrec, double eta_ff,
-    double eta_fb, double eta_jerk, double eps2, double* __restrict__ step, int* err) {
-    __shared__ RecMix sr[kAuxTile];
-    __shared__ float4 sv[kAuxTile];
-    const int base = blockIdx.x * (kAuxTile * kStepIpt);
-    float xh[kStepIpt], yh[kStepIpt], zh[kStepIpt], xl[kStepIpt], yl[kStepIpt], zl[kStepIpt];
-    float ui[kStepIpt], vi[kStepIpt], wi[kStepIpt], mi[kStepIpt];
-    int me[kStepIpt];
-    StepAcc<float> acc[kStepIpt];
-#pragma unroll
-    for (int u = 0; u < kStepIpt; ++u) {
-        me[u] = base + u * kAuxTile + threadIdx.x;
-        const int ii = min(me[u], n - 1);
-        const RecMix r = rec[ii];
-        const float4 v = vrec[ii];
-        xh[u] = r.hi.x; yh[u] = r.hi.y; zh[u] = r.hi.z;
-        xl[u] = r.lo.x; yl[u] = r.lo.y; zl[u] = r.lo.z;
-        ui[u] = v.x; vi[u] = v.y; wi[u] = v.z; mi[u] = v.w;
-        acc[u].init();
-    }
-    const float eps2f = (float)eps2;
-    bool coincident = false;
-    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
-        __syncthreads();
-        if (j0 + threadIdx.x < n) {
-            sr[threadIdx.x] = rec[j0 + threadIdx.x];
-            sv[threadIdx.x] = vrec[j0 + threadIdx.x];
-        }
-        __syncthreads();
-        const int cnt = min(kAuxTile, n - j0);
-        for (int t = 0; t < cnt; ++t) {
-            const float4 h = sr[t].hi, l = sr[t].lo, v = sv[t];
-#pragma unroll
-            for (int u = 0; u < kStepIpt; ++u) {
-                const float dx = (h.x - xh[u]) + (l.x - xl[u]);
-                const float dy = (h.y - yh[u]) + (l.y - yl[u]);
-                const float dz = (h.z - zh[u]) + (l.z - zl[u]);
-                const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-                // lanes past the end hold a copy of particle n-1: compare clamped indices
-                const bool self = (j0 + t == min(me[u], n - 1));
-                coincident |= (!self && d2 == 0.f && me[u] < n);
-                if (self || d2 == 0.f) continue;
-                const float y = rsqrt_f32_refined(d2 + eps2f);
-                step_pair<float>(acc[u], dx, dy, dz, v.x - ui[u], v.y - vi[u], v.z - wi[u], d2, v.w,
-                                 mi[u] + v.w, y);
-            }
-        }
-    }
-    if (coincident) set_error(err, FSI_ERR_NONFINITE);
-#pragma unroll
-    for (int u = 0; u < kStepIpt; ++u)
-        if (me[u] < n) step[me[u]] = step_finish<float>(acc[u], eta_ff, eta_fb, eta_jerk);
-}
-
-// FP32 velocity records (vx, vy, vz, m) of a compact set.
 // FP32 velocity records (vx, vy, vz, m) of a set: entry k from particle idx[k] of the
 // 3 x ld velocity rows (idx null: particle k); with pos, also its mixed position record.
 __global__ void pack_vel_kernel(long long ld, const double* __restrict__ v,
@@ -772,21 +711,6 @@ cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const 
                                                    pos, reinterpret_cast<RecMix*>(rec)); note_launch(); }
     return cudaGetLastError();
 }
-
-cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
-                                   double eta_ff, double eta_fb, double eta_jerk, double eps2,
-                                   void* rec_ws, void* vrec_ws, double* step, int* err,
-                                   cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    { pack_kernel<FSI_MIXED><<<blocks_for(n), kB, 0, s>>>(n, xc, mc, nullptr, n, rec_ws, nullptr); note_launch(); }
-    { pack_vel_kernel<<<blocks_for(n), kB, 0, s>>>(n, vc, mc, nullptr, n, reinterpret_cast<float4*>(vrec_ws), nullptr, nullptr); note_launch(); }
-    { timesteps_mixed_kernel<<<blocks_for(n, kAuxTile * kStepIpt), kAuxTile, 0, s>>>(
-        n, reinterpret_cast<const RecMix*>(rec_ws), reinterpret_cast<const float4*>(vrec_ws), eta_ff,
-        eta_fb, eta_jerk, eps2, step, err); note_launch(); }
-    return cudaGetLastError();
-}
-
-
 
 // Energy: per-CTA partial sums of the kinetic energy and of -1/2 sum_i sum_{j != i}
 // m_i m_j / sqrt(r^2 + eps2), reduced in a fixed order by energy_finish_kernel.

@@ -350,10 +350,6 @@ cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double ep
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                             double eta_fb, double eta_jerk, float* part, double* step, int* err,
                             long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s);
-cudaError_t launch_timesteps_mixed(int n, const double* xc, const double* vc, const double* mc,
-                                   double eta_ff, double eta_fb, double eta_jerk, double eps2,
-                                   void* rec_ws, void* vrec_ws, double* step, int* err,
-                                   cudaStream_t s);
 cudaError_t launch_partition(int n, const int* ids, double* step, double* step0, int level0,
                              double tau, int force_slow, int* S, int* F, int* counts, cudaStream_t s);
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s);

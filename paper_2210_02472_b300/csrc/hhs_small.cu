@@ -214,7 +214,7 @@ __device__ __forceinline__ void pass_leader(SmallSmem<P>& S, int k, const SumT<P
 
 template <int P, int KIND>
 __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
-                           const unsigned short* B, int nB, double eps2, const PassOut<P>& o,
+                           const unsigned short* B, int nB, double eps2, const PassOut<P>& po,
                            unsigned long long* work) {
     const int t = threadIdx.x;
     if (t == 0 && work) atomicAdd(work + KIND, (unsigned long long)nA * (unsigned long long)nB);
@@ -267,7 +267,7 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
                 ff_acc(h, l, sl[c]);
                 sum[c] = make_float2(h, l);
             }
-            pass_leader<P, KIND>(S, k, sum, o);
+            pass_leader<P, KIND>(S, k, sum, po);
         }
     } else {
         double r[3] = {0.0, 0.0, 0.0};
@@ -288,7 +288,7 @@ __device__ void small_pass(SmallSmem<P>& S, const unsigned short* A, int nA,
             for (int q = 0; q < 3; ++q) r[q] += __shfl_xor_sync(0xffffffffu, r[q], o);
         if (active && g == 0) {
             const SumT<P> sum[3] = {r[0], r[1], r[2]};
-            pass_leader<P, KIND>(S, k, sum, o);
+            pass_leader<P, KIND>(S, k, sum, po);
         }
     }
 }
