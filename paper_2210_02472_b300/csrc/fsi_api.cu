@@ -888,7 +888,8 @@ int fsi_reserve(fsi_ctx* c, int N, int n) {
     CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
     CK(ensure(c->part, (size_t)64 * 3 * n * 8));
     CK(ensure(c->epart, (size_t)(energy_blocks(n) * 2 + 2) * 8));
-    CK(ensure(c->accum, 3 * (size_t)n * 8));
+    CK(ensure(c->accum, 3 * (size_t)n * 8));      // also both sides of a bipartite pass
+    CK(ensure(c->stpart, std::max(steps_x2_part_bytes(n, c->sm_count), steps_sym_work_bytes(n))));
     // spatial ordering and far-tile inputs of the symmetric mixed kernel
     CK(ensure(c->rel, pad_tile(n) * 16));
     CK(ensure(c->sub, (pad_tile(n) / 32) * 16));
