@@ -24,8 +24,11 @@ def dev(a, dtype=torch.float64):
     return torch.as_tensor(np.ascontiguousarray(a)).to("cuda", dtype)
 
 
-@pytest.mark.parametrize("n,subset", [(300, False), (1000, False), (700, True)])
+@pytest.mark.parametrize("n,subset", [(300, False), (1000, False), (700, True), (2500, False),
+                                      (7000, True)])
 def test_step_vjp_matches_oracle(F, n, subset):
+    """One cycle's adjoint against the oracle's hand-derived adjoint; sets of >= 2048
+    particles (2500, and the 2333 of 7000) take the symmetric adjoint pair kernels."""
     c = inputs.plummer(n, 61 + n, imf="kroupa")
     h = 1e-3
     rng = np.random.default_rng(3)
