@@ -194,6 +194,15 @@ int fsi_step(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
 int fsi_kick_drift(fsi_ctx *ctx, int N, double *pos, double *vel, const double *acc,
                    const int *idx, int n, double c_kick, double c_drift, void *stream);
 
+/* One FSI cycle (PN off) of the set idx exactly as fsi_step with nsteps = 1 (the set kept
+ * in its own order), also writing the cycle's intermediates for fsi_step_vjp_rec: a0 =
+ * a(x0), a1 = a(x1) and g1 = G(x1) (Sect. 2.1, Eq. fsi-cycle; x1 = the positions after the
+ * first drift), each 3 x n compact device rows in the order of idx.  FSI_ERR_UNSUPPORTED
+ * when fsi_params.c > 0. */
+int fsi_step_record(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
+                    const int *idx, int n, double h, double *a0, double *a1, double *g1,
+                    void *stream);
+
 /* Adjoint of one fsi_step cycle (PN off): given the input state (pos0, vel0; 3 x N) of
  * a cycle of step h on the set idx (n ids, NULL = all) and the cotangents gx_out, gv_out
  * (3 x N) of its output state, writes the cotangents of the input state into gx_in,
@@ -212,6 +221,14 @@ int fsi_step_vjp(fsi_ctx *ctx, int N, const double *pos0, const double *vel0,
                  const double *mass, const int *idx, int n, double h,
                  const double *gx_out, const double *gv_out, double *gx_in, double *gv_in,
                  double *gm, void *stream);
+
+/* fsi_step_vjp given the cycle's intermediates a0, a1, g1 as written by fsi_step_record
+ * for the same input state, instead of recomputing them (three pair passes fewer). */
+int fsi_step_vjp_rec(fsi_ctx *ctx, int N, const double *pos0, const double *vel0,
+                     const double *mass, const int *idx, int n, double h, const double *a0,
+                     const double *a1, const double *g1, const double *gx_out,
+                     const double *gv_out, double *gx_in, double *gv_in, double *gm,
+                     void *stream);
 
 /* nsteps FSI cycles of the set idx (NULL = all N, then n == N) with binary subsystems
  * (Sect. 2.3, Algorithm 1), in place: kick eps/6, subsystems eps/2, drift of the single

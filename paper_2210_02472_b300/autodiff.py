@@ -2,8 +2,10 @@
 
 The forward passes call ``fsi_step`` and the backward passes the hand-written adjoint
 ``fsi_step_vjp`` of the CUDA library; no arithmetic of the method runs here.  Rollouts
-keep the state every ``ckpt_every`` steps and recompute each segment's intermediate
-states during the backward pass (memory O(steps / ckpt_every + ckpt_every) states).
+keep the state every ``ckpt_every`` steps and recompute each segment during the backward
+pass with ``fsi_step_record``, keeping every cycle's input state and intermediates
+(a(x0), a(x1), G(x1)) for ``fsi_step_vjp_rec`` (memory O(steps / ckpt_every + ckpt_every)
+states).
 """
 from __future__ import annotations
 
@@ -60,11 +62,11 @@ class FSIRollout(torch.autograd.Function):
             p, v = ctx.ckpts[s][0].clone(), ctx.ckpts[s][1].clone()
             k = min(ctx.every, ctx.steps - s * ctx.every)
             states = []
-            for _ in range(k):                      # recompute the segment's inputs
-                states.append((p.clone(), v.clone()))
-                F.fsi_step(fctx, p, v, m, h, nsteps=1)
-            for (p0, v0) in reversed(states):
-                gx, gv, gm = F.fsi_step_vjp(fctx, p0, v0, m, h, gx, gv, gm=gm)
+            for _ in range(k):                      # recompute the segment, recording
+                p0, v0 = p.clone(), v.clone()
+                states.append((p0, v0, F.fsi_step_record(fctx, p, v, m, h)))
+            for (p0, v0, rec) in reversed(states):
+                gx, gv, gm = F.fsi_step_vjp_rec(fctx, p0, v0, m, h, rec, gx, gv, gm=gm)
         return gx, gv, gm, None, None, None, None
 
 

@@ -438,19 +438,29 @@ int check_common(fsi_ctx* c, int N) {
 
 // ---------------------------------------------------------------------------------
 // FSI cycles of a set on itself (compact buffers; see fsi_step in fsi.h).
+// Intermediates of one recorded FSI cycle (compact 3 x n, in the order of the set's ids):
+// a(x0), a(x1) and G(x1) with x1 the positions after the first drift.
+struct StepRecord {
+    double* a0;
+    double* a1;
+    double* g1;
+};
+
 int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
               const unsigned char* is_bh, const int* idx, int n, double h, int nsteps,
-              cudaStream_t s) {
+              cudaStream_t s, const StepRecord* record = nullptr) {
     if (n <= 0 || nsteps <= 0) return FSI_OK;
     const int prec = c->p.precision;
     const bool pn = c->p.c > 0.0;
     if (pn && !is_bh) return fail(FSI_ERR_ARG, "PN on (c > 0) needs is_bh");
+    if (record && (pn || nsteps != 1)) return fail(FSI_ERR_ARG, "a recorded step is one Newtonian cycle");
     CK(ensure(c->rec[0], pad_tile(n) * 32));
     CK(ensure(c->rec[1], pad_tile(n) * 32));
     CK(ensure(c->accrec[0], pad_tile(n) * 32));
     CK(ensure(c->ac, 3 * (size_t)n * 8));
     FarGuard far_guard{c};
-    const bool far = far_selected(c, n) && n >= order_threshold(c);
+    // a recorded cycle keeps the set's own order (its intermediates are returned in it)
+    const bool far = !record && far_selected(c, n) && n >= order_threshold(c);
     if (far) {
         CK(order_set(c, N, pos, idx, n, s));
         idx = P<int>(c->ordlist);
@@ -536,11 +546,34 @@ int step_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
     void* r0 = c->rec[0].p;
     void* r1 = c->rec[1].p;
     if (pn) CK(pn_kick(0.5 * h));
-    CK(acc_pass(r0, r1, h / 6.0, 0.5 * h, nullptr, nullptr));
+    CK(acc_pass(r0, r1, h / 6.0, 0.5 * h, record ? record->a0 : nullptr, nullptr));
     for (int k = 0; k < nsteps; ++k) {
         const bool last = (k == nsteps - 1);
-        CK(acc_pass(r1, nullptr, 0.0, 0.0, P<double>(c->ac), c->accrec[0].p));
-        CK(grad_pass(r1, r0, 2.0 * h / 3.0, h * h / 24.0, 0.5 * h));
+        double* a1 = record ? record->a1 : P<double>(c->ac);
+        CK(acc_pass(r1, nullptr, 0.0, 0.0, a1, c->accrec[0].p));
+        if (record) {
+            // the gradient pass adds its kick to a(x1) from the record and returns G(x1)
+            PairArgs a{};
+            a.irec = a.jrec = r1;
+            a.iacc = a.jacc = c->accrec[0].p;
+            a.n_i = a.n_j = n;
+            a.check = CHECK_DIAG;
+            a.eps2 = c->p.eps2;
+            a.epi.out = record->g1;
+            a.epi.v = vc;
+            a.epi.x = xc;
+            a.epi.base = a1;
+            a.epi.c_kick = 2.0 * h / 3.0;
+            a.epi.c_grad = h * h / 24.0;
+            a.epi.c_drift = 0.5 * h;
+            a.epi.rec_out = r0;
+            a.epi.mc = mc;
+            a.epi.ids = eids;
+            a.epi.ld = N;
+            CK(run_pair(c, KIND_GRAD, a, s));
+        } else {
+            CK(grad_pass(r1, r0, 2.0 * h / 3.0, h * h / 24.0, 0.5 * h));
+        }
         if (!pn && !last) {
             CK(acc_pass(r0, r1, h / 3.0, 0.5 * h, nullptr, nullptr));
         } else {
@@ -1106,6 +1139,18 @@ int fsi_kick_drift(fsi_ctx* c, int N, double* pos, double* vel, const double* ac
     return FSI_OK;
 }
 
+int fsi_step_record(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                    const int* idx, int n, double h, double* a0, double* a1, double* g1,
+                    void* stream) {
+    CK(check_common(c, N));
+    if (n < 0 || (!idx && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (c->p.c > 0.0) return fail(FSI_ERR_UNSUPPORTED, "the recorded cycle is Newtonian (PN off)");
+    if (n == 0) return FSI_OK;
+    if (!pos || !vel || !mass || !a0 || !a1 || !g1) return fail(FSI_ERR_ARG, "NULL array");
+    const StepRecord r{a0, a1, g1};
+    return step_core(c, N, pos, vel, mass, nullptr, idx, n, h, 1, S(stream), &r);
+}
+
 int fsi_step_sub(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
                  const int* idx, int n, const int* pairs, int n_pairs, double h, int nsteps,
                  void* stream) {
@@ -1348,9 +1393,12 @@ int fsi_level_stats(fsi_ctx* c, long long* counts, int max) {
     return used;
 }
 
-int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, const double* mass,
-                 const int* idx, int n, double h, const double* gx_out, const double* gv_out,
-                 double* gx_in, double* gv_in, double* gm, void* stream) {
+// Adjoint of one cycle; rec (nullable) holds the cycle's recorded intermediates a(x0),
+// a(x1), G(x1) (compact, set order), which are otherwise recomputed here.
+static int step_vjp_core(fsi_ctx* c, int N, const double* pos0, const double* vel0, const double* mass,
+                  const int* idx, int n, double h, const double* rec_a0, const double* rec_a1,
+                  const double* rec_g1, const double* gx_out, const double* gv_out,
+                  double* gx_in, double* gv_in, double* gm, void* stream) {
     CK(check_common(c, N));
     if (n < 0 || (!idx && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
     if (!pos0 || !vel0 || !mass || !gx_out || !gv_out || !gx_in || !gv_in || !gm)
@@ -1393,12 +1441,16 @@ int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, cons
         a.epi.mc = mc;
         return run_pair(c, KIND_ACC, a, s);
     };
-    // ---- forward recompute of the cycle's intermediates (compact, FP64 state)
-    CK(acc_at(x0, B(A0), nullptr));
-    CU(launch_lincomb3(n, v0, B(A0), h / 6.0, B(V1), s));
+    // ---- the cycle's intermediates: recorded by the forward step, or recomputed here
+    // (compact, FP64 state)
+    const double* A0p = rec_a0 ? rec_a0 : B(A0);
+    const double* A1p = rec_a0 ? rec_a1 : B(A1);
+    const double* G1p = rec_a0 ? rec_g1 : B(G1);
+    if (!rec_a0) CK(acc_at(x0, B(A0), nullptr));
+    CU(launch_lincomb3(n, v0, A0p, h / 6.0, B(V1), s));
     CU(launch_lincomb3(n, x0, B(V1), 0.5 * h, B(X1), s));
-    CK(acc_at(B(X1), B(A1), c->accrec[0].p));
-    {
+    if (!rec_a0) {
+        CK(acc_at(B(X1), B(A1), c->accrec[0].p));
         PairArgs a{};
         a.irec = a.jrec = c->rec[0].p;
         a.iacc = a.jacc = c->accrec[0].p;
@@ -1408,7 +1460,7 @@ int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, cons
         a.epi.out = B(G1);
         CK(run_pair(c, KIND_GRAD, a, s));
     }
-    CU(launch_lincomb3(n, B(A1), B(G1), h * h / 24.0, B(TMP), s));
+    CU(launch_lincomb3(n, A1p, G1p, h * h / 24.0, B(TMP), s));
     CU(launch_lincomb3(n, B(V1), B(TMP), 2.0 * h / 3.0, B(V2), s));
     CU(launch_lincomb3(n, B(X1), B(V2), 0.5 * h, B(X2), s));
     // ---- reverse (FP64 adjoint kernels on FP64 records)
@@ -1436,7 +1488,7 @@ int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, cons
     CK(vjp(0, B(X1), B(WT), cg, 0.0, B(AB), nullptr));               // abar = cg (dG/da)^T w
     CU(launch_lincomb3(n, B(WT), B(AB), 1.0, B(U), s));               // u = w + abar
     CK(vjp(0, B(X1), B(U), 1.0, 1.0, B(XB), B(MB)));
-    CU(launch_pack_acc(FSI_FP64, n, B(A1), mc, nullptr, n, racc, nullptr, s));
+    CU(launch_pack_acc(FSI_FP64, n, A1p, mc, nullptr, n, racc, nullptr, s));
     CK(vjp(1, B(X1), B(WT), cg, cg, B(XB), B(MB)));
     // x1 = x0 + h/2 v1
     CU(launch_lincomb3(n, B(VB), B(XB), 0.5 * h, B(VB), s));
@@ -1446,6 +1498,23 @@ int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, cons
     CU(launch_scatter3(N, B(VB), idx, n, gv_in, s));
     CU(launch_scatter_add1(n, B(MB), idx, gm, s));
     return FSI_OK;
+}
+
+int fsi_step_vjp(fsi_ctx* c, int N, const double* pos0, const double* vel0, const double* mass,
+                 const int* idx, int n, double h, const double* gx_out, const double* gv_out,
+                 double* gx_in, double* gv_in, double* gm, void* stream) {
+    return step_vjp_core(c, N, pos0, vel0, mass, idx, n, h, nullptr, nullptr, nullptr, gx_out,
+                         gv_out, gx_in, gv_in, gm, stream);
+}
+
+int fsi_step_vjp_rec(fsi_ctx* c, int N, const double* pos0, const double* vel0,
+                     const double* mass, const int* idx, int n, double h, const double* a0,
+                     const double* a1, const double* g1, const double* gx_out,
+                     const double* gv_out, double* gx_in, double* gv_in, double* gm,
+                     void* stream) {
+    if (n > 0 && (!a0 || !a1 || !g1)) return fail(FSI_ERR_ARG, "NULL recorded intermediate");
+    return step_vjp_core(c, N, pos0, vel0, mass, idx, n, h, a0, a1, g1, gx_out, gv_out, gx_in,
+                         gv_in, gm, stream);
 }
 
 int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps, fsi_batch** out) {

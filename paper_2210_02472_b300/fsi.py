@@ -36,10 +36,10 @@ FSI_MIXED = 1
 
 EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params", "fsi_reserve",
             "fsi_last_error", "fsi_sync_status", "fsi_accel", "fsi_grad", "fsi_accel_grad",
-            "fsi_pn_accel", "fsi_step", "fsi_kick_drift", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
+            "fsi_pn_accel", "fsi_step", "fsi_step_record", "fsi_kick_drift", "fsi_timesteps", "fsi_energy", "fsi_hhs_interval",
             "fsi_level_stats", "fsi_hhs_interval_restart", "fsi_step_sub", "fsi_profile", "fsi_profile_read", "fsi_launch_count",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
-            "fsi_step_vjp", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
+            "fsi_step_vjp", "fsi_step_vjp_rec", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall", "fsi_batch_stats",
             "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for"]
 
@@ -94,6 +94,9 @@ _lib.fsi_batch_inject_stall.argtypes = [_vp, _ip]
 _lib.fsi_batch_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong),
                                  C.POINTER(_ip), _ip]
 _lib.fsi_step_vjp.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _vp, _vp, _vp, _vp, _vp, _vp]
+_lib.fsi_step_record.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _vp, _vp, _vp, _vp]
+_lib.fsi_step_vjp_rec.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _vp, _vp, _vp, _vp, _vp,
+                                  _vp, _vp, _vp, _vp]
 
 
 class FsiError(RuntimeError):
@@ -411,6 +414,39 @@ def fsi_step_vjp(ctx: Context, pos0, vel0, mass, h: float, gx_out, gv_out, idx=N
                              _f64(gx_out, (3, N), "gx_out"), _f64(gv_out, (3, N), "gv_out"),
                              _f64(gx_in, (3, N), "gx_in"), _f64(gv_in, (3, N), "gv_in"),
                              _f64(gm, (N,), "gm"), _stream(stream)), "fsi_step_vjp")
+    return gx_in, gv_in, gm
+
+
+def fsi_step_record(ctx: Context, pos, vel, mass, h: float, idx=None, stream=None):
+    """One FSI cycle in place (as fsi_step, nsteps = 1); returns the intermediates
+    (a0, a1, g1), each (3, n) in the order of idx, for fsi_step_vjp_rec."""
+    N = mass.numel()
+    pi, n = _ids(idx, N, "idx")
+    a0 = torch.empty((3, n), dtype=torch.float64, device=pos.device)
+    a1, g1 = torch.empty_like(a0), torch.empty_like(a0)
+    _check(_lib.fsi_step_record(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                                _f64(mass, (N,), "mass"), pi, n, float(h), _f64(a0, (3, n), "a0"),
+                                _f64(a1, (3, n), "a1"), _f64(g1, (3, n), "g1"), _stream(stream)),
+           "fsi_step_record")
+    return a0, a1, g1
+
+
+def fsi_step_vjp_rec(ctx: Context, pos0, vel0, mass, h: float, rec, gx_out, gv_out, idx=None,
+                     gm=None, stream=None):
+    """fsi_step_vjp with the cycle's recorded intermediates rec = (a0, a1, g1)."""
+    N = mass.numel()
+    pi, n = _ids(idx, N, "idx")
+    a0, a1, g1 = rec
+    gx_in = torch.empty_like(gx_out)
+    gv_in = torch.empty_like(gv_out)
+    if gm is None:
+        gm = torch.zeros_like(mass)
+    _check(_lib.fsi_step_vjp_rec(ctx.handle, N, _f64(pos0, (3, N), "pos0"), _f64(vel0, (3, N), "vel0"),
+                                 _f64(mass, (N,), "mass"), pi, n, float(h), _f64(a0, (3, n), "a0"),
+                                 _f64(a1, (3, n), "a1"), _f64(g1, (3, n), "g1"),
+                                 _f64(gx_out, (3, N), "gx_out"), _f64(gv_out, (3, N), "gv_out"),
+                                 _f64(gx_in, (3, N), "gx_in"), _f64(gv_in, (3, N), "gv_in"),
+                                 _f64(gm, (N,), "gm"), _stream(stream)), "fsi_step_vjp_rec")
     return gx_in, gv_in, gm
 
 

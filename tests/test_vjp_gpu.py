@@ -107,3 +107,54 @@ def test_rollout_vjp_matches_finite_differences(F):
             an = grads[which][idx]
             tol = 1e-6 * max(1.0, abs(an)) if which < 2 else 1e-5 * abs(an)
             assert abs(fd - an) <= tol, (which, idx, fd, an)
+
+
+@pytest.mark.parametrize("subset", [False, True])
+def test_step_record_matches_step_and_oracle(F, subset):
+    """fsi_step_record advances the state exactly like fsi_step (one cycle) and returns
+    a(x0), a(x1) and G(x1) of the cycle (x1 after the first kick and drift), against the
+    oracle's sums at the oracle's x1."""
+    n = 1500
+    c = inputs.plummer(n, 64, imf="kroupa")
+    h = 1e-3
+    P = np.sort(inputs.random_subset(n, 700, 65)).astype(np.int32) if subset else None
+    with F.Context("fp64") as ctx:
+        idx = None if P is None else dev(P, torch.int32)
+        p1, v1 = dev(c.pos), dev(c.vel)
+        F.fsi_step(ctx, p1, v1, dev(c.mass), h, nsteps=1, idx=idx)
+        p2, v2 = dev(c.pos), dev(c.vel)
+        a0, a1, g1 = F.fsi_step_record(ctx, p2, v2, dev(c.mass), h, idx=idx)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        p1, v1, p2, v2 = (t.cpu().numpy() for t in (p1, v1, p2, v2))
+        a0, a1, g1 = (t.cpu().numpy() for t in (a0, a1, g1))
+    assert np.abs(p2 - p1).max() <= 1e-14 * np.abs(p1).max()
+    assert np.abs(v2 - v1).max() <= 1e-13 * np.abs(v1).max()
+    S = np.arange(n) if P is None else P
+    ra0 = np.asarray(oracle.acc(c.pos, c.mass, S, S))
+    x1 = c.pos.copy()
+    x1[:, S] = c.pos[:, S] + 0.5 * h * (c.vel[:, S] + h / 6.0 * ra0)
+    ra1 = np.asarray(oracle.acc(x1, c.mass, S, S))
+    accg = np.zeros_like(c.pos)
+    accg[:, S] = ra1
+    rg1 = np.asarray(oracle.grad(x1, c.mass, accg, S, S))
+    for got, ref, tol in ((a0, ra0, 1e-12), (a1, ra1, 1e-11), (g1, rg1, 1e-10)):
+        assert np.abs(got - ref).max() <= tol * np.abs(ref).max()
+
+
+def test_step_vjp_rec_matches_recomputing_vjp(F):
+    """The adjoint given the recorded intermediates equals the one that recomputes them."""
+    n = 2500
+    c = inputs.plummer(n, 66, imf="kroupa")
+    h = 1e-3
+    rng = np.random.default_rng(67)
+    gx, gv = rng.normal(size=(3, n)), rng.normal(size=(3, n))
+    with F.Context("fp64") as ctx:
+        x0, v0, m = dev(c.pos), dev(c.vel), dev(c.mass)
+        rec = F.fsi_step_record(ctx, x0.clone(), v0.clone(), m, h)
+        r1 = F.fsi_step_vjp(ctx, x0, v0, m, h, dev(gx), dev(gv))
+        r2 = F.fsi_step_vjp_rec(ctx, x0, v0, m, h, rec, dev(gx), dev(gv))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        r1 = [t.cpu().numpy() for t in r1]
+        r2 = [t.cpu().numpy() for t in r2]
+    for a, b in zip(r2, r1):
+        assert np.abs(a - b).max() <= 1e-12 * np.abs(b).max()
