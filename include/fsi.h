@@ -75,11 +75,10 @@ typedef struct fsi_params {
     double c;             /* speed of light in N-body units; 0 switches PN1.0 off */
     int split;            /* source-split factor override (0 = automatic) */
     long long timeout_ns; /* budget of every bounded device wait (0 = 2e9 ns) */
-    int symmetric;        /* 1 (default): a set's self-interaction, and in the mixed
-                             precision the two directions of a large cross-level pass,
-                             evaluate every unordered pair once and add it to both particles
-                             (Newton's third law); 0: every ordered pair is evaluated by its
-                             receiving particle */
+    int symmetric;        /* 1 (default): a set's self-interaction, and the two directions
+                             of a large cross-level pass, evaluate every unordered pair once
+                             and add it to both particles (Newton's third law); 0: every
+                             ordered pair is evaluated by its receiving particle */
     int hhs_small_max;    /* HHS: a fast set of at most this many particles (0 = 256; the
                              maximum is 512) runs its whole recursion inside one CTA; -1 =
                              always walk the levels from the host */

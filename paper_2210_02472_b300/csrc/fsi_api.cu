@@ -338,9 +338,9 @@ int run_pair2(fsi_ctx* c, int kind, PairArgs a, PairArgs b, cudaStream_t s) {
             return FSI_OK;
         }
     }
-    // mixed, symmetric: every S-F pair once in the bipartite packed kernel, the larger set
-    // in registers (full receiver blocks), then one finalize launch per side
-    if (prec == FSI_MIXED && c->p.symmetric && a.check == CHECK_NONE && b.check == CHECK_NONE &&
+    // symmetric: every S-F pair once in the bipartite kernel, the larger set in registers
+    // (full receiver blocks), then one finalize launch per side
+    if (c->p.symmetric && a.check == CHECK_NONE && b.check == CHECK_NONE &&
         a.irec == b.jrec && a.jrec == b.irec && a.n_i == b.n_j && a.n_j == b.n_i &&
         std::min(a.n_i, b.n_i) >= kTileJ) {
         PairArgs& L = a.n_i >= b.n_i ? a : b;
@@ -351,13 +351,13 @@ int run_pair2(fsi_ctx* c, int kind, PairArgs a, PairArgs b, cudaStream_t s) {
         CU(cudaMemsetAsync(c->accum.p, 0, 3 * (nL + nM) * sizeof(double), s));
         double* accL = P<double>(c->accum);
         double* accM = accL + 3 * nL;
-        const long long nb = (L.n_i + cross_block_size() - 1) / cross_block_size();
+        const long long nb = (L.n_i + cross_block_size(prec) - 1) / cross_block_size(prec);
         const long long visits = nb * ((M.n_i + kTileJ - 1) / kTileJ);
         const int chunk = (int)std::max(1LL, std::min(64LL, visits / (8LL * c->sm_count)));
         L.err = M.err = c->err_d;
         CK(timed(c, kind, s, [&] {
-            return launch_cross_pair(kind, L.irec, L.iacc, L.n_i, M.irec, M.iacc, M.n_i, L.eps2, chunk,
-                                     accL, accM, c->err_d, budget(c), s);
+            return launch_cross_pair(prec, kind, L.irec, L.iacc, L.n_i, M.irec, M.iacc, M.n_i, L.eps2,
+                                     chunk, accL, accM, c->err_d, budget(c), s);
         }));
         L.part = accL;
         M.part = accM;

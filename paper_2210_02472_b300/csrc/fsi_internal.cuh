@@ -231,14 +231,15 @@ cudaError_t launch_wide_pair(int precision, int kind, bool diag, const PairArgs&
 // Two unmasked wide passes (one source slice each) in one launch; each applies its epilogue.
 cudaError_t launch_wide_pair2(int precision, int kind, const PairArgs& a, const PairArgs& b,
                               int lga, int lgb, cudaStream_t s);
-// Bipartite symmetric pass (mixed precision, packed form): every pair of the disjoint sets
-// S (i: n_i) and F (j: n_j) once, S's sums added into acc_i (3 x n_i) and F's into acc_j
-// (3 x n_j), both zeroed by the caller; `chunk` F tiles per work item.
-cudaError_t launch_cross_pair(int kind, const void* irec, const void* iacc, int n_i,
-                              const void* jrec, const void* jacc, int n_j, double eps2, int chunk,
-                              double* acc_i, double* acc_j, int* err, long long timeout_ns,
-                              cudaStream_t s);
-int cross_block_size();
+// Bipartite symmetric pass (mixed: packed form; FP64: symmetric FP64 pair terms): every
+// pair of the disjoint sets S (i: n_i) and F (j: n_j) once, S's sums added into acc_i
+// (3 x n_i) and F's into acc_j (3 x n_j), both zeroed by the caller; `chunk` F tiles per
+// work item.
+cudaError_t launch_cross_pair(int precision, int kind, const void* irec, const void* iacc,
+                              int n_i, const void* jrec, const void* jacc, int n_j, double eps2,
+                              int chunk, double* acc_i, double* acc_j, int* err,
+                              long long timeout_ns, cudaStream_t s);
+int cross_block_size(int precision);
 // Symmetric self-interaction pass (every unordered pair once); adds into accum (3 x n,
 // zeroed by the caller); `chunk` source tiles per work item.
 // Far-tile inputs of the symmetric mixed kernel (second form with bit 64 in its variant):

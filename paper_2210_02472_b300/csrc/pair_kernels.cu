@@ -1664,12 +1664,151 @@ static cudaError_t launch_cross_x2_t(const CrossArgs& a, cudaStream_t s) {
     return cudaGetLastError();
 }
 
-int cross_block_size() { return kThreads * 4; }
+// FP64 form of the bipartite kernel: the symmetric FP64 pair terms of the single-set
+// kernel (I = 2 particles of S per thread), the F side reduced across the warp in FP64.
+template <int KIND, int I>
+__global__ void __launch_bounds__(kThreads, 2) cross_f64_kernel(const CrossArgs a) {
+    constexpr int ACCREC = SymCfg<FSI_FP64, KIND>::ACCREC;
+    constexpr int SB = SymCfg<FSI_FP64, KIND>::SB;
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ __align__(8) uint64_t bars[kStages];
+    double* jpart = reinterpret_cast<double*>(smem + kStages * SB);
+    const int b = blockIdx.x / a.nchunk;
+    const int c = blockIdx.x % a.nchunk;
+    const int ntj = (a.n_j + kTileJ - 1) / kTileJ;
+    const int t0 = c * a.chunk;
+    const int t1 = min(t0 + a.chunk, ntj);
+    if (t0 >= t1) return;                       // uniform: before any barrier
+    const int ntiles = t1 - t0;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int i0 = b * (kThreads * I);
+    if (tid == 0) {
+        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto issue = [&](int t) {
+        const int st = t % kStages;
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n_j - jt);
+        unsigned char* base = smem + st * SB;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC));
+        bulk_g2s(base, (const unsigned char*)a.jrec + (size_t)jt * kRec, (uint32_t)cnt * kRec, &bars[st]);
+        if (ACCREC)
+            bulk_g2s(base + kTileJ * kRec, (const unsigned char*)a.jacc + (size_t)jt * ACCREC,
+                     (uint32_t)cnt * ACCREC, &bars[st]);
+    };
+    if (tid == 0)
+        for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
+    double acc64[I][3];
+    bool valid[I];
+    int my_i[I];
+    SymF64I pi[I];
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        acc64[u][0] = acc64[u][1] = acc64[u][2] = 0.0;
+        my_i[u] = i0 + u * kThreads + tid;
+        valid[u] = my_i[u] < a.n_i;
+        const int i = min(my_i[u], a.n_i - 1);
+        const D4 r = reinterpret_cast<const D4*>(a.irec)[i];
+        pi[u].x = r.x; pi[u].y = r.y; pi[u].z = r.z;
+        pi[u].nm = valid[u] ? -r.w : 0.0;       // a receiver past the end adds nothing to F
+        if constexpr (KIND == KIND_GRAD) {
+            const D4 ai = reinterpret_cast<const D4*>(a.iacc)[i];
+            pi[u].ax = ai.x; pi[u].ay = ai.y; pi[u].az = ai.z;
+        } else {
+            pi[u].ax = pi[u].ay = pi[u].az = 0.0;
+        }
+    }
+    bool aborted = false;
+    int t_stop = ntiles;
+    for (int t = 0; t < ntiles; ++t) {
+        const int st = t % kStages;
+        const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
+        const int jt = (t0 + t) * kTileJ;
+        const int cnt = min(kTileJ, a.n_j - jt);
+        const unsigned char* base = smem + st * SB;
+        const D4* rec = reinterpret_cast<const D4*>(base);
+        const D4* arec = reinterpret_cast<const D4*>(base + kTileJ * kRec);
+        for (int jj = 0; jj < cnt; jj += 4) {
+            double fj[4][3];
+#pragma unroll
+            for (int g = 0; g < 4; ++g) {
+                fj[g][0] = fj[g][1] = fj[g][2] = 0.0;
+                if (jj + g < cnt) {
+                    const D4 r = rec[jj + g];
+                    if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                        for (int u = 0; u < I; ++u) f64_acc_sym(r, pi[u], a.eps2, acc64[u], fj[g]);
+                    } else {
+                        const D4 aj = arec[jj + g];
+#pragma unroll
+                        for (int u = 0; u < I; ++u) f64_grad_sym(r, aj, pi[u], a.eps2, acc64[u], fj[g]);
+                    }
+                }
+            }
+            double tot[3];
+            reduce_scatter4<double>(fj, lane, tot);
+            const int jl = jj + (lane >> 3);
+            if ((lane & 7) == 0 && jl < cnt) {
+                double* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
+                dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+            }
+        }
+        if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
+        if (tid < cnt) {
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                double sum = 0.0;
+#pragma unroll
+                for (int w = 0; w < kThreads / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
+                red_add(a.acc_j + (size_t)q * a.n_j + jt + tid, sum);
+            }
+        }
+        __syncthreads();
+        if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
+    }
+    if (aborted) {
+        if (tid == 0) {
+            const int issued = min(ntiles, t_stop + kStages);
+            for (int t = t_stop; t < issued; ++t)
+                mbar_wait_bounded(&bars[t % kStages], (uint32_t)((t / kStages) & 1), a.timeout_ns, nullptr);
+        }
+        __syncthreads();
+        return;
+    }
+#pragma unroll
+    for (int u = 0; u < I; ++u) {
+        if (!valid[u]) continue;
+#pragma unroll
+        for (int q = 0; q < 3; ++q) red_add(a.acc_i + (size_t)q * a.n_i + my_i[u], acc64[u][q]);
+    }
+}
 
-cudaError_t launch_cross_pair(int kind, const void* irec, const void* iacc, int n_i,
-                              const void* jrec, const void* jacc, int n_j, double eps2, int chunk,
-                              double* acc_i, double* acc_j, int* err, long long timeout_ns,
-                              cudaStream_t s) {
+template <int KIND>
+static cudaError_t launch_cross_f64_t(const CrossArgs& a, cudaStream_t s) {
+    constexpr int I = 2;
+    constexpr int SMEM = SymCfg<FSI_FP64, KIND>::SMEM;
+    static bool attr_set = false;
+    if (!attr_set) {
+        cudaError_t e = cudaFuncSetAttribute(cross_f64_kernel<KIND, I>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+        if (e != cudaSuccess) return e;
+        attr_set = true;
+    }
+    const long long nb = (a.n_i + kThreads * I - 1) / (kThreads * I);
+    const long long grid = nb * a.nchunk;
+    if (grid <= 0 || grid > 2147483647LL) return cudaErrorInvalidValue;
+    { cross_f64_kernel<KIND, I><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    return cudaGetLastError();
+}
+
+int cross_block_size(int precision) { return kThreads * (precision == FSI_MIXED ? 4 : 2); }
+
+cudaError_t launch_cross_pair(int precision, int kind, const void* irec, const void* iacc,
+                              int n_i, const void* jrec, const void* jacc, int n_j, double eps2,
+                              int chunk, double* acc_i, double* acc_j, int* err,
+                              long long timeout_ns, cudaStream_t s) {
     if (n_i <= 0 || n_j <= 0) return cudaErrorInvalidValue;
     CrossArgs a{};
     a.irec = irec; a.iacc = iacc; a.jrec = jrec; a.jacc = jacc;
@@ -1678,6 +1817,8 @@ cudaError_t launch_cross_pair(int kind, const void* irec, const void* iacc, int 
     a.chunk = std::max(1, std::min(chunk, ntj));
     a.nchunk = (ntj + a.chunk - 1) / a.chunk;
     a.eps2 = eps2; a.acc_i = acc_i; a.acc_j = acc_j; a.err = err; a.timeout_ns = timeout_ns;
+    if (precision == FSI_FP64)
+        return kind == KIND_ACC ? launch_cross_f64_t<KIND_ACC>(a, s) : launch_cross_f64_t<KIND_GRAD>(a, s);
     return kind == KIND_ACC ? launch_cross_x2_t<KIND_ACC>(a, s) : launch_cross_x2_t<KIND_GRAD>(a, s);
 }
 

@@ -511,17 +511,18 @@ def test_hhs_interval(F, prec, small, wide):
     assert np.abs(v - rv).max() <= tol * 100
 
 
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("symmetric", [True, False])
-def test_hhs_interval_large_cross_passes(F, symmetric):
+def test_hhs_interval_large_cross_passes(F, prec, symmetric):
     """HHS interval of 4000 particles: the top levels' cross-level kicks have slow and fast
-    sets of several hundred to thousands of particles, which the mixed path evaluates with
-    the bipartite symmetric kernel (every S-F pair once, symmetric = True) or as two
-    one-sided passes (False); both against the oracle."""
+    sets of several hundred to thousands of particles, evaluated by the bipartite symmetric
+    kernel (every S-F pair once, symmetric = True; packed FP32 or FP64) or as two one-sided
+    passes (False); both against the oracle."""
     c = inputs.plummer(4000, 30, imf="kroupa")
     tau = 1.0 / 32
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
     assert counts[0] >= 256 and counts[0] <= 4000 - 256      # both sets >= one tile at level 0
-    with F.Context("mixed", symmetric=symmetric) as ctx:
+    with F.Context(prec, symmetric=symmetric) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
@@ -530,8 +531,9 @@ def test_hhs_interval_large_cross_passes(F, symmetric):
         assert F.fsi_sync_status(ctx) == F.FSI_OK
     used = np.nonzero(counts)[0].max() + 1
     assert lv[:used] == list(counts[:used])
-    assert np.abs(p - rp).max() <= 1e-7
-    assert np.abs(v - rv).max() <= 1e-5
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
 
 
 RESTART_CASES = {
