@@ -92,7 +92,7 @@ struct fsi_ctx {
     // mixed sets of many receivers take the packed FP32x2 form
     int ipt[2][2][2] = {{{2, 2}, {2, 2}}, {{4, 36}, {2, 36}}};
     // [precision][kind][size class] symmetric kernel variant (sym_variants)
-    int symv[2][2][kSymClasses] = {{{2, 2, 2}, {2, 2, 2}}, {{2, 228, 230}, {2, 228, 246}}};
+    int symv[2][2][kSymClasses] = {{{2, 2, 2}, {2, 2, 2}}, {{226, 228, 230}, {226, 228, 246}}};
     long long work_pairs[2] = {0, 0};   // ordered pairs evaluated by acc / grad passes
     // far-tile path of the symmetric mixed kernel: while far_n > 0, the records of the set
     // being stepped (n = far_n) have valid masses in rel[].w (step_core, autotune)

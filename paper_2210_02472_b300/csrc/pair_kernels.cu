@@ -1910,6 +1910,8 @@ cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, c
     if (precision == FSI_MIXED && (ipt & 128)) {
         // packed form; bit 16 selects the one-CTA-per-SM register budget
         switch ((ipt & 16 ? 64 : 0) + I * 2 + kind) {
+            case 2 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 2, 2>(a, s);
+            case 2 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 2, 2>(a, s);
             case 4 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 4, 2>(a, s);
             case 6 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 6, 2>(a, s);
             case 4 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 4, 2>(a, s);
@@ -2005,6 +2007,7 @@ int sym_variants(int precision, int kind, int* out) {
         if (kind == KIND_ACC) { out[n++] = 96 + 4; out[n++] = 96 + 5; }
         else { out[n++] = 96 + 3; out[n++] = 96 + 4; }
         // packed FP32x2 form (far-tile path included)
+        out[n++] = 224 + 2;
         out[n++] = 224 + 4;
         out[n++] = 224 + 6;
         out[n++] = 240 + 6;     // one CTA per SM (255 registers)

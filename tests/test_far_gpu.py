@@ -23,7 +23,7 @@ from paper_2210_02472_b300 import inputs
 
 pytestmark = pytest.mark.gpu
 
-FAR_VARIANTS = [(101, 100), (100, 99), (228, 228), (230, 230), (246, 246), (248, 248)]
+FAR_VARIANTS = [(101, 100), (100, 99), (226, 226), (228, 228), (230, 230), (246, 246), (248, 248)]
 
 
 @pytest.fixture(scope="module")
@@ -218,10 +218,10 @@ def test_autotune_times_far_variants_in_order(F, cluster):
 
 def test_size_class_tuning_tables(F):
     """Symmetric variants are kept per set-size class (< 32768, < 196608, larger):
-    mixed defaults are the first form with 2 particles per thread for small sets and the
-    packed FP32x2 form (far-tile path included) above; fsi_set_tuning fixes every class."""
+    mixed defaults are the packed FP32x2 form (far-tile path included) with 2, 4 and 6
+    particles per thread; fsi_set_tuning fixes every class."""
     with F.Context("mixed") as ctx:
-        assert F.fsi_get_tuning_for(ctx, 1000) == (2, 2)
+        assert F.fsi_get_tuning_for(ctx, 1000) == (226, 226)
         assert F.fsi_get_tuning_for(ctx, 40000) == (228, 228)
         assert F.fsi_get_tuning_for(ctx, 1 << 20) == (230, 246)
         assert F.fsi_get_tuning(ctx) == (230, 246)
