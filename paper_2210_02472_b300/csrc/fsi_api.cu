@@ -1284,7 +1284,15 @@ int hhs_interval_core(fsi_ctx* c, int N, double* pos, double* vel, const double*
     CK(ensure(c->iota, (size_t)N * 4));
     CK(ensure(c->step0, (size_t)N * 8));
     CK(ensure(c->counts, 16));
-    CU(launch_iota(N, P<int>(c->iota), s));
+    if (c->p.precision == FSI_MIXED && c->p.symmetric && N >= order_threshold(c)) {
+        // level 0 in Morton order of the interval's starting positions: the stable
+        // partitions hand the order down, so every level's slow and fast lists are in
+        // spatial order too (only the summation order changes)
+        CK(order_set(c, N, pos, nullptr, N, s));
+        CU(cudaMemcpyAsync(c->iota.p, c->ordlist.p, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
+    } else {
+        CU(launch_iota(N, P<int>(c->iota), s));
+    }
     CK(ensure(c->dstats, 68 * sizeof(unsigned long long)));
     CU(cudaMemsetAsync(c->dstats.p, 0, 68 * sizeof(unsigned long long), s));
     c->level_counts.assign(std::max(c->p.max_level + 1, 64), 0);
