@@ -536,6 +536,26 @@ def test_hhs_interval_large_cross_passes(F, prec, symmetric):
     assert np.abs(v - rv).max() <= tol * 100
 
 
+def test_hhs_interval_morton_ordered_levels(F):
+    """Mixed HHS with the level-0 list in Morton order (order_min lowered so that 4000
+    particles qualify): every level list inherits the order; only summation orders change,
+    so the oracle's hierarchy and trajectories are met as without the order."""
+    c = inputs.plummer(4000, 30, imf="kroupa")
+    tau = 1.0 / 32
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    with F.Context("mixed", order_min=256) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    assert np.abs(p - rp).max() <= 1e-7
+    assert np.abs(v - rv).max() <= 1e-5
+
+
 RESTART_CASES = {
     # name: (N, seed, tau, tolerance or None (between attempts 1 and 2), max_restarts, etas)
     "halve": (300, 28, 1 / 16, None, 8, dict(eta_grad=0.1, eta_va=0.2)),
