@@ -85,7 +85,11 @@ typedef struct fsi_params {
     int order_min;        /* mixed + symmetric with a far-tile kernel variant selected (see
                              fsi_autotune): fsi_step puts a set of at least this many
                              particles in Morton order for the duration of the call (0 =
-                             32768; -1 = never).  The order only changes which pairs take
+                             32768; -1 = never); fsi_hhs_interval (mixed + symmetric) puts
+                             the level-0 list of N >= order_min in Morton order, and its
+                             bipartite cross-level passes whose smaller set has at least
+                             min(16384, order_min) particles take the far-tile arithmetic for
+                             that set's sub-tiles.  The order only changes which pairs take
                              the far-tile arithmetic and the summation order. */
     double eta_grad;      /* gradient time-step parameter eta_nabla (Sect. 3.4, Eqs. dt-nabla1
                              and dt-nabla2): eps = eta (|v_i| / |g'_i|)^{1/3} and

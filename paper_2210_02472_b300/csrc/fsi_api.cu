@@ -98,6 +98,10 @@ struct fsi_ctx {
     // being stepped (n = far_n) have valid masses in rel[].w (step_core, autotune)
     Buf rel, sub, ordws, ordperm, ordlist, farstats;
     int far_n = 0;
+    // far-tile path of the bipartite kernel: set while an HHS interval runs on level lists
+    // in Morton order; xrel/xsub hold the sub-tiles of the smaller set of a pass
+    bool lists_ordered = false;
+    Buf xrel, xsub;
     // instrumentation: event pairs around pair-kernel launches
     struct ProfRec { int kind; cudaEvent_t a, b; };
     bool profiling = false;
@@ -194,6 +198,9 @@ constexpr float kFarKappa = 3.0f;
 // Sets of at least this many particles are put in Morton order by step_core when the
 // symmetric mixed far-tile kernel is selected (order_min = 0).
 constexpr int kOrderMinDefault = 32768;
+// Bipartite passes take the far-tile path when the level lists are in Morton order and
+// the smaller set has at least this many particles (or order_min, if lower).
+constexpr int kCrossFarMin = 16384;
 
 int order_threshold(const fsi_ctx* c) {
     if (c->p.order_min < 0) return INT_MAX;
@@ -355,9 +362,22 @@ int run_pair2(fsi_ctx* c, int kind, PairArgs a, PairArgs b, cudaStream_t s) {
         const long long visits = nb * ((M.n_i + kTileJ - 1) / kTileJ);
         const int chunk = (int)std::max(1LL, std::min(64LL, visits / (8LL * c->sm_count)));
         L.err = M.err = c->err_d;
+        SymFar far{};
+        const SymFar* farp = nullptr;
+        if (prec == FSI_MIXED && c->lists_ordered &&
+            M.n_i >= std::min(kCrossFarMin, order_threshold(c))) {
+            // F's sub-tiles (the lists inherit Morton order); masses from the records
+            CK(ensure(c->xrel, pad_tile(M.n_i) * 16));
+            CK(ensure(c->xsub, (pad_tile(M.n_i) / 32) * 16));
+            CU(launch_subtiles(M.n_i, M.irec, c->xrel.p, c->xsub.p, s, true));
+            far.rel = c->xrel.p;
+            far.sub = c->xsub.p;
+            far.k2 = (kFarKappa + 1.0f) * (kFarKappa + 1.0f);
+            farp = &far;
+        }
         CK(timed(c, kind, s, [&] {
             return launch_cross_pair(prec, kind, L.irec, L.iacc, L.n_i, M.irec, M.iacc, M.n_i, L.eps2,
-                                     chunk, accL, accM, c->err_d, budget(c), s);
+                                     chunk, accL, accM, c->err_d, budget(c), s, farp);
         }));
         L.part = accL;
         M.part = accM;
@@ -879,7 +899,8 @@ int fsi_destroy(fsi_ctx* c) {
                    &c->part, &c->mark, &c->bhlist, &c->nbh, &c->apn, &c->pnpart, &c->epart,
                    &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
                    &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
-                   &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos, &c->stpart};
+                   &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos, &c->stpart,
+                   &c->xrel, &c->xsub};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -1284,12 +1305,17 @@ int hhs_interval_core(fsi_ctx* c, int N, double* pos, double* vel, const double*
     CK(ensure(c->iota, (size_t)N * 4));
     CK(ensure(c->step0, (size_t)N * 8));
     CK(ensure(c->counts, 16));
+    struct OrderedGuard {
+        fsi_ctx* c;
+        ~OrderedGuard() { c->lists_ordered = false; }
+    } ordered_guard{c};
     if (c->p.precision == FSI_MIXED && c->p.symmetric && N >= order_threshold(c)) {
         // level 0 in Morton order of the interval's starting positions: the stable
         // partitions hand the order down, so every level's slow and fast lists are in
         // spatial order too (only the summation order changes)
         CK(order_set(c, N, pos, nullptr, N, s));
         CU(cudaMemcpyAsync(c->iota.p, c->ordlist.p, (size_t)N * 4, cudaMemcpyDeviceToDevice, s));
+        c->lists_ordered = true;
     } else {
         CU(launch_iota(N, P<int>(c->iota), s));
     }

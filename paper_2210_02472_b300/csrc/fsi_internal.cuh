@@ -231,6 +231,7 @@ cudaError_t launch_wide_pair(int precision, int kind, bool diag, const PairArgs&
 // Two unmasked wide passes (one source slice each) in one launch; each applies its epilogue.
 cudaError_t launch_wide_pair2(int precision, int kind, const PairArgs& a, const PairArgs& b,
                               int lga, int lgb, cudaStream_t s);
+struct SymFar;
 // Bipartite symmetric pass (mixed: packed form; FP64: symmetric FP64 pair terms): every
 // pair of the disjoint sets S (i: n_i) and F (j: n_j) once, S's sums added into acc_i
 // (3 x n_i) and F's into acc_j (3 x n_j), both zeroed by the caller; `chunk` F tiles per
@@ -238,7 +239,7 @@ cudaError_t launch_wide_pair2(int precision, int kind, const PairArgs& a, const 
 cudaError_t launch_cross_pair(int precision, int kind, const void* irec, const void* iacc,
                               int n_i, const void* jrec, const void* jacc, int n_j, double eps2,
                               int chunk, double* acc_i, double* acc_j, int* err,
-                              long long timeout_ns, cudaStream_t s);
+                              long long timeout_ns, cudaStream_t s, const SymFar* far = nullptr);
 int cross_block_size(int precision);
 // Symmetric self-interaction pass (every unordered pair once); adds into accum (3 x n,
 // zeroed by the caller); `chunk` source tiles per work item.
@@ -270,7 +271,9 @@ cudaError_t launch_morton_order(int n, const double* xc, long long ld, int* perm
                                 size_t ws_bytes, cudaStream_t s);
 cudaError_t launch_compose(const int* idx, const int* perm, int n, int* list, cudaStream_t s);
 cudaError_t launch_rel_mass(const double* mass, const int* idx, int n, void* rel, cudaStream_t s);
-cudaError_t launch_subtiles(int n, const void* rec, void* rel, void* sub, cudaStream_t s);
+// mass_from_rec: rel.w from the records' 2.5 m instead of a preceding launch_rel_mass.
+cudaError_t launch_subtiles(int n, const void* rec, void* rel, void* sub, cudaStream_t s,
+                            bool mass_from_rec = false);
 
 // launch_pack of two id lists (no compact copies) in one launch.
 cudaError_t launch_pack2(int precision, int N, const double* pos, const double* mass,

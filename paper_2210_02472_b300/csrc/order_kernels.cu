@@ -213,8 +213,10 @@ __global__ void radix_scatter_kernel(int n, const unsigned* __restrict__ kin, co
 // ---- 4. sub-tiles of the packed records ---------------------------------------------
 // One warp per 32 records.  rel[k].w (the FP32 mass) is written once per set order by
 // rel_mass_kernel and kept; this kernel rewrites rel[k].xyz and sub[k / 32].
+// mass_from_rec: rel.w = m from the record's 2.5 m (within 1.5 ulp of the FP32 mass), for
+// sets whose rel.w was not filled from the FP64 masses.
 __global__ void subtile_kernel(int n, const RecMix* __restrict__ rec, float4* __restrict__ rel,
-                               float4* __restrict__ sub) {
+                               float4* __restrict__ sub, bool mass_from_rec) {
     const int k = (int)((blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 5);
     const int lane = threadIdx.x & 31;
     if (k >= (n + 31) >> 5) return;                      // warp-uniform
@@ -238,7 +240,7 @@ __global__ void subtile_kernel(int n, const RecMix* __restrict__ rec, float4* __
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) R = fmaxf(R, __shfl_xor_sync(0xffffffffu, R, o));
     if (j < n) {
-        float4 v = rel[j];
+        float4 v = mass_from_rec ? make_float4(0.f, 0.f, 0.f, (float)(0.4 * (double)r.hi.w)) : rel[j];
         v.x = d[0]; v.y = d[1]; v.z = d[2];
         rel[j] = v;
     }
@@ -323,12 +325,14 @@ cudaError_t launch_rel_mass(const double* mass, const int* idx, int n, void* rel
     return cudaGetLastError();
 }
 
-cudaError_t launch_subtiles(int n, const void* rec, void* rel, void* sub, cudaStream_t s) {
+cudaError_t launch_subtiles(int n, const void* rec, void* rel, void* sub, cudaStream_t s,
+                            bool mass_from_rec) {
     if (n <= 0) return cudaSuccess;
     const long long threads = (long long)((n + 31) / 32) * 32;
     const int blocks = (int)((threads + kOB - 1) / kOB);
     { subtile_kernel<<<blocks, kOB, 0, s>>>(n, reinterpret_cast<const RecMix*>(rec),
-                                             reinterpret_cast<float4*>(rel), reinterpret_cast<float4*>(sub));
+                                             reinterpret_cast<float4*>(rel), reinterpret_cast<float4*>(sub),
+                                             mass_from_rec);
       note_launch(); }
     return cudaGetLastError();
 }

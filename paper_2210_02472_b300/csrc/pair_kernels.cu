@@ -1509,6 +1509,11 @@ struct CrossArgs {
     double* acc_j;      // 3 x n_j, zeroed before the launch
     int* err;
     long long timeout_ns;
+    // far-tile path (mixed; null rel: never taken): F's records relative to the centres of
+    // their 32-record sub-tiles (w = mass) and the sub-tiles' (centre, radius)
+    const float4* rel;
+    const float4* sub;
+    float far_k2;
 };
 
 template <int KIND, int I, int MINB>
@@ -1516,10 +1521,13 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
     static_assert(I % 2 == 0, "particles are handled in packed pairs");
     constexpr int NP = I / 2;
     constexpr int ACCREC = SymCfg<FSI_MIXED, KIND>::ACCREC;
-    constexpr int SB = kTileJ * (kRec + ACCREC);
+    constexpr int RELB = 16;
+    constexpr int SUBB = (kTileJ / 32) * 16;
+    constexpr int SB = kTileJ * (kRec + ACCREC + RELB) + SUBB;
     constexpr int JPART = SymCfg<FSI_MIXED, KIND>::JPART;
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ float wbox[kThreads / 32][6];
     float* jpart = reinterpret_cast<float*>(smem + kStages * SB);
     float4* acc_s = reinterpret_cast<float4*>(smem + kStages * SB + JPART);
 
@@ -1532,6 +1540,7 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
     const int ntiles = t1 - t0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int i0 = b * (kThreads * I);
+    const bool far_on = a.rel != nullptr;
 
     if (tid == 0) {
         for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
@@ -1542,12 +1551,20 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
         const int st = t % kStages;
         const int jt = (t0 + t) * kTileJ;
         const int cnt = min(kTileJ, a.n_j - jt);
+        const int nsub = (cnt + 31) >> 5;
         unsigned char* base = smem + st * SB;
-        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC));
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * (kRec + ACCREC) +
+                                             (far_on ? (uint32_t)(cnt * 16 + nsub * 16) : 0u));
         bulk_g2s(base, (const unsigned char*)a.jrec + (size_t)jt * kRec, (uint32_t)cnt * kRec, &bars[st]);
         if (ACCREC)
             bulk_g2s(base + kTileJ * kRec, (const unsigned char*)a.jacc + (size_t)jt * ACCREC,
                      (uint32_t)cnt * ACCREC, &bars[st]);
+        if (far_on) {
+            bulk_g2s(base + kTileJ * (kRec + ACCREC), (const unsigned char*)(a.rel + jt),
+                     (uint32_t)cnt * 16, &bars[st]);
+            bulk_g2s(base + kTileJ * (kRec + ACCREC + RELB), (const unsigned char*)(a.sub + jt / 32),
+                     (uint32_t)nsub * 16, &bars[st]);
+        }
     };
     if (tid == 0)
         for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
@@ -1565,6 +1582,9 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
             const float4 ai = reinterpret_cast<const float4*>(a.iacc)[i];
             nax = -ai.x; nay = -ai.y; naz = -ai.z;
             nm = valid ? -ai.w : 0.f;
+        } else {
+            // -m_i for the far form, from the record's 2.5 m
+            nm = (far_on && valid) ? -(float)(0.4 * (double)r.hi.w) : 0.f;
         }
         const int h = u & 1;
         X2I& q = pp[u >> 1];
@@ -1582,6 +1602,31 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
 #pragma unroll
         for (int q = 0; q < 3; ++q) acc_s[(p * 3 + q) * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    if (far_on) {
+        // box of the warp's particles (FP32 high parts)
+        float bl[3] = {-pp[0].nxh.x, -pp[0].nyh.x, -pp[0].nzh.x};
+        float bh[3] = {bl[0], bl[1], bl[2]};
+#pragma unroll
+        for (int p = 0; p < NP; ++p) {
+            bl[0] = fminf(bl[0], -fmaxf(pp[p].nxh.x, pp[p].nxh.y));
+            bl[1] = fminf(bl[1], -fmaxf(pp[p].nyh.x, pp[p].nyh.y));
+            bl[2] = fminf(bl[2], -fmaxf(pp[p].nzh.x, pp[p].nzh.y));
+            bh[0] = fmaxf(bh[0], -fminf(pp[p].nxh.x, pp[p].nxh.y));
+            bh[1] = fmaxf(bh[1], -fminf(pp[p].nyh.x, pp[p].nyh.y));
+            bh[2] = fmaxf(bh[2], -fminf(pp[p].nzh.x, pp[p].nzh.y));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                bl[q] = fminf(bl[q], __shfl_xor_sync(0xffffffffu, bl[q], o));
+                bh[q] = fmaxf(bh[q], __shfl_xor_sync(0xffffffffu, bh[q], o));
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { wbox[warp][q] = bl[q]; wbox[warp][3 + q] = bh[q]; }
+        __syncwarp();
+    }
     const float2 eps2 = bc2((float)a.eps2);
     float2 D0[NP][3];                           // unused by the near form
     bool aborted = false;
@@ -1594,14 +1639,41 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
         const unsigned char* base = smem + st * SB;
         const RecMix* rec = reinterpret_cast<const RecMix*>(base);
         const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
+        const float4* rel_s = reinterpret_cast<const float4*>(base + kTileJ * (kRec + ACCREC));
+        const float4* sub_s = reinterpret_cast<const float4*>(base + kTileJ * (kRec + ACCREC + RELB));
+        unsigned fmask = 0;
+        if (far_on) {
+            // far test of this warp's box against each full 32-record sub-tile (warp-uniform)
+            bool fr = false;
+            if (lane < ((cnt + 31) >> 5)) {
+                const float4 sb = sub_s[lane];
+                const float* wb = wbox[warp];
+                const float gx = fmaxf(0.f, fmaxf(wb[0] - sb.x, sb.x - wb[3]));
+                const float gy = fmaxf(0.f, fmaxf(wb[1] - sb.y, sb.y - wb[4]));
+                const float gz = fmaxf(0.f, fmaxf(wb[2] - sb.z, sb.z - wb[5]));
+                fr = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= a.far_k2 * (sb.w * sb.w);
+            }
+            fmask = __ballot_sync(0xffffffffu, fr);
+        }
         for (int k0 = 0; k0 < cnt; k0 += 32) {
             const int jend = min(cnt, k0 + 32);
             if (jend - k0 < 32) {
                 for (int jj = k0; jj < jend; jj += 4)
-                    x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+                    x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D0, eps2, f, jpart);
+            } else if ((fmask >> (k0 >> 5)) & 1u) {
+                const float4 C = sub_s[k0 >> 5];
+                float2 D[NP][3];
+#pragma unroll
+                for (int p = 0; p < NP; ++p) {
+                    D[p][0] = __fadd2_rn(__fadd2_rn(bc2(C.x), pp[p].nxh), pp[p].nxl);
+                    D[p][1] = __fadd2_rn(__fadd2_rn(bc2(C.y), pp[p].nyh), pp[p].nyl);
+                    D[p][2] = __fadd2_rn(__fadd2_rn(bc2(C.z), pp[p].nzh), pp[p].nzl);
+                }
+                for (int jj = k0; jj < jend; jj += 4)
+                    x2_group<KIND, NP, true, true>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D, eps2, f, jpart);
             } else {
                 for (int jj = k0; jj < jend; jj += 4)
-                    x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
+                    x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D0, eps2, f, jpart);
             }
         }
 #pragma unroll
@@ -1648,7 +1720,7 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
 template <int KIND>
 static cudaError_t launch_cross_x2_t(const CrossArgs& a, cudaStream_t s) {
     constexpr int I = 4;
-    constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC);
+    constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + 16) + (kTileJ / 32) * 16;
     constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + (I / 2) * 3 * kThreads * 16;
     static bool attr_set = false;
     if (!attr_set) {
@@ -1808,7 +1880,7 @@ int cross_block_size(int precision) { return kThreads * (precision == FSI_MIXED 
 cudaError_t launch_cross_pair(int precision, int kind, const void* irec, const void* iacc,
                               int n_i, const void* jrec, const void* jacc, int n_j, double eps2,
                               int chunk, double* acc_i, double* acc_j, int* err,
-                              long long timeout_ns, cudaStream_t s) {
+                              long long timeout_ns, cudaStream_t s, const SymFar* far) {
     if (n_i <= 0 || n_j <= 0) return cudaErrorInvalidValue;
     CrossArgs a{};
     a.irec = irec; a.iacc = iacc; a.jrec = jrec; a.jacc = jacc;
@@ -1817,6 +1889,11 @@ cudaError_t launch_cross_pair(int precision, int kind, const void* irec, const v
     a.chunk = std::max(1, std::min(chunk, ntj));
     a.nchunk = (ntj + a.chunk - 1) / a.chunk;
     a.eps2 = eps2; a.acc_i = acc_i; a.acc_j = acc_j; a.err = err; a.timeout_ns = timeout_ns;
+    if (far && precision == FSI_MIXED) {
+        a.rel = reinterpret_cast<const float4*>(far->rel);
+        a.sub = reinterpret_cast<const float4*>(far->sub);
+        a.far_k2 = far->k2;
+    }
     if (precision == FSI_FP64)
         return kind == KIND_ACC ? launch_cross_f64_t<KIND_ACC>(a, s) : launch_cross_f64_t<KIND_GRAD>(a, s);
     return kind == KIND_ACC ? launch_cross_x2_t<KIND_ACC>(a, s) : launch_cross_x2_t<KIND_GRAD>(a, s);
