@@ -538,8 +538,10 @@ def test_hhs_interval_large_cross_passes(F, prec, symmetric):
 
 def test_hhs_interval_morton_ordered_levels(F):
     """Mixed HHS with the level-0 list in Morton order (order_min lowered so that 4000
-    particles qualify): every level list inherits the order; only summation orders change,
-    so the oracle's hierarchy and trajectories are met as without the order."""
+    particles qualify): every level list inherits the order, and the bipartite cross-level
+    passes whose smaller set has >= order_min particles take the far-tile arithmetic; only
+    summation orders and rounding change, so the oracle's hierarchy and trajectories are met
+    as without the order."""
     c = inputs.plummer(4000, 30, imf="kroupa")
     tau = 1.0 / 32
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
