@@ -633,7 +633,7 @@ def probe_peak_tflops(F, mode: int) -> float:
 
 def run_accgrad(args):
     """One same-set acceleration pass plus one force-gradient pass over all N(N-1) ordered
-    pairs (fsi_accel_grad), the north star's acc+grad measurement, in either precision;
+    pairs (fsi_accel_grad), the acc+grad throughput at N = 2^20, in either precision;
     each pass against the FMA peak of its pipe measured by the probe in the same run."""
     import torch
     from paper_2210_02472_b300 import fsi as F
