@@ -42,7 +42,11 @@ METRIC = "acc+grad pair interactions/s at N=2^20 (mixed precision, FSI cycle wit
 UNIT = "interactions/s"
 FLOP_ACC, FLOP_GRAD = 20, 36
 FLOP_PAIR = FLOP_ACC + FLOP_GRAD
-SMS, FP32_LANES, SM_MAX_MHZ = 148, 128, 2032.0
+FP32_LANES, SM_MAX_MHZ = 128, 2032.0      # FP32 lanes per SM; B300 maximum SM clock
+# FP64: B300's listed rate (1.25 TFLOP/s) over 148 SMs at 2.032 GHz is ~4 flop per SM per
+# clock, i.e. two FP64 FMA lanes per SM; the FP64 peak below is that rate times the SM count
+# the device reports times the maximum SM clock.
+FP64_FLOP_PER_SM_CLK = 4
 CPU_ROWS = 4096
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
 # kernel, from one one-pass ncu capture of this benchmark's own workload (`--tuning A,G
@@ -51,7 +55,7 @@ CPU_ROWS = 4096
 # (kernel label, workload, N); a kernel changed since the capture must drop its entry, and
 # any other configuration reports null.
 DRAM_TRAFFIC = {("sym_mixed_v2_kernel<acc, I=5, far>", "kroupa1m_bh16", 1048592): 201.9e6,
-                ("sym_mixed_x2_kernel<acc, I=6, MINB=2>", "kroupa1m_bh16", 1048592): 256.5e6}
+                ("sym_mixed_x2_kernel<acc, I=8, MINB=1>", "kroupa1m_bh16", 1048592): 236.9e6}
 
 
 def step_interactions(n: int) -> float:
@@ -59,8 +63,18 @@ def step_interactions(n: int) -> float:
     return pairs * (3 * FLOP_ACC + FLOP_GRAD) / FLOP_PAIR
 
 
-def fp32_peak_tflops(mhz: float = SM_MAX_MHZ) -> float:
-    return SMS * FP32_LANES * 2 * mhz * 1e6 / 1e12
+def sm_count(device=None) -> int:
+    """Streaming multiprocessors of the device, as the driver reports them."""
+    import torch
+    return int(torch.cuda.get_device_properties(device if device is not None else 0).multi_processor_count)
+
+
+def fp32_peak_tflops(sms: int, mhz: float = SM_MAX_MHZ) -> float:
+    return sms * FP32_LANES * 2 * mhz * 1e6 / 1e12
+
+
+def fp64_peak_tflops(sms: int, mhz: float = SM_MAX_MHZ) -> float:
+    return sms * FP64_FLOP_PER_SM_CLK * mhz * 1e6 / 1e12
 
 
 def measured_peaks():
@@ -129,23 +143,36 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+CPU_ROW_SEED, CPU_FIELD_SEED = 4242, 4243
+
+
 def cpu_baseline(c, rows: int, threads: int):
     """The FP64 CPU oracle, as it stands, on a seeded sample of `rows` active particles
-    against all N sources: acc and grad pair sums.  Returns interactions/s."""
+    against all N sources: acc and grad pair sums.  Returns interactions/s and an info dict
+    that also holds the sample's rows and the oracle's sums (for the accuracy check of the
+    GPU results on the same rows)."""
     import oracle
     oracle.set_threads(threads)
-    A = inputs.random_subset(c.n, rows, 4242)
-    accg = inputs.random_field(c.n, 4243)
+    A = inputs.random_subset(c.n, rows, CPU_ROW_SEED)
+    accg = inputs.random_field(c.n, CPU_FIELD_SEED)
     t0 = time.perf_counter()
-    oracle.acc(c.pos, c.mass, A, None)
+    a = oracle.acc(c.pos, c.mass, A, None)
     t1 = time.perf_counter()
-    oracle.grad(c.pos, c.mass, accg, A, None)
+    g = oracle.grad(c.pos, c.mass, accg, A, None)
     t2 = time.perf_counter()
     pairs = float(rows) * (c.n - 1)
     inter = pairs * (FLOP_ACC + FLOP_GRAD) / FLOP_PAIR
-    return inter / (t2 - t0), {"acc_s": t1 - t0, "grad_s": t2 - t1,
+    return inter / (t2 - t0), {"acc_s": t1 - t0, "grad_s": t2 - t1, "rows": A, "acc": a, "grad": g,
                                "sample": f"{rows} seeded active rows x all {c.n} sources, "
                                          f"acc + grad (FP64 oracle)"}
+
+
+def error_stats(got, ref):
+    """Distribution of |d v| / |v| over the columns of (3, n) arrays."""
+    d = np.linalg.norm(got - ref, axis=0) / np.linalg.norm(ref, axis=0)
+    return {"rows": int(d.size), "median": float(np.median(d)), "p99": float(np.percentile(d, 99)),
+            "p99.9": float(np.percentile(d, 99.9)), "max": float(d.max()),
+            "frac_above_1e-7": float(np.mean(d > 1e-7))}
 
 
 def dist_init():
@@ -212,6 +239,54 @@ def run_reference(args):
     return 0
 
 
+def fp64_passes(F, c, pos, mass, dev, flush, sms, peak_mhz):
+    """The FP64 half of the metric on the same set: one same-set acceleration pass and one
+    force-gradient pass over all N(N-1) ordered pairs (fsi_accel_grad, FP64 context), each
+    timed by the library's event pair around its launch, L2 flushed before.  Pipe fraction
+    against the FP64 peak of this device (SM count queried, FP64 FMA rate per SM, maximum
+    SM clock) and against the library's FP64 FMA probe."""
+    import torch
+    N = c.n
+    ctx = F.Context("fp64")
+    F.fsi_reserve(ctx, N, N)
+    sub = torch.arange(0, min(N, 16384), dtype=torch.int32, device=dev)
+    F.fsi_accel_grad(ctx, pos, None, mass, sub, sub)          # warm-up of the same kernels
+    torch.cuda.synchronize()
+    flush.zero_()
+    F.fsi_profile(ctx, True)
+    e0, e1 = _timed_events(None)
+    e0.record()
+    F.fsi_accel_grad(ctx, pos, None, mass)
+    e1.record()
+    torch.cuda.synchronize()
+    prof = F.fsi_profile_read(ctx)
+    F.fsi_profile(ctx, False)
+    if F.fsi_sync_status(ctx) != F.FSI_OK:
+        raise SystemExit("device error in the FP64 passes")
+    t = e0.elapsed_time(e1) / 1e3
+    probe = probe_peak_tflops(F, 1)
+    ctx.close()
+    pairs = float(N) * (N - 1)
+    peak = fp64_peak_tflops(sms, peak_mhz)
+    out = {"workload": "same set as the cycle", "n": N,
+           "passes": "one same-set acc pass + one grad pass (fsi_accel_grad), FP64 pair terms",
+           "value": pairs / t, "unit": "acc+grad interactions/s", "s_per_acc_grad": t,
+           "peak_tflops": peak,
+           "peak_basis": f"{sms} SMs x {FP64_FLOP_PER_SM_CLK} FP64 flop per SM per clock x "
+                         f"{peak_mhz:.0f} MHz",
+           "probe_tflops": probe}
+    tot_fl, tot_s = 0.0, 0.0
+    for k, fl in (("acc", FLOP_ACC), ("grad", FLOP_GRAD)):
+        nl, ms = prof[k]
+        ach = pairs * fl / (ms / max(nl, 1) / 1e3) / 1e12
+        tot_fl += pairs * fl
+        tot_s += ms / 1e3
+        out[k] = {"ms_per_launch": ms / max(nl, 1), "launches": nl, "achieved_tflops": ach,
+                  "frac": ach / peak, "frac_of_probe": ach / probe}
+    out["frac"] = tot_fl / tot_s / 1e12 / peak     # acc + grad together
+    return out
+
+
 def run_fsi(args):
     import torch
     rank, ws, local, dist = dist_init()
@@ -243,6 +318,7 @@ def run_fsi(args):
     def step():
         F.fsi_step(ctx, pos, vel, mass, h, nsteps=1, is_bh=bh)
 
+    e0 = F.fsi_energy(ctx, pos, vel, mass).sum().item() if not args.no_energy else None
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
@@ -276,6 +352,7 @@ def run_fsi(args):
     if F.fsi_sync_status(ctx) != F.FSI_OK:
         raise SystemExit("device error in the timed region")
     step_ms = [a.elapsed_time(b) for a, b in ev]
+    e1 = F.fsi_energy(ctx, pos, vel, mass).sum().item() if not args.no_energy else None
     t_dev = reduce_max(sum(step_ms) / 1e3, dist, dev)
     inter = step_interactions(N) * args.steps
     value = job_value(inter, ws, t_dev)
@@ -306,8 +383,9 @@ def run_fsi(args):
     dom = max(kinds, key=lambda k: prof[k][1])
     nl, ms = prof[dom]
     achieved = (float(N) * (N - 1) * kinds[dom]) / (ms / nl / 1e3) / 1e12
-    peak_mhz = SM_MAX_MHZ
-    peak = fp32_peak_tflops(peak_mhz) if args.precision == "mixed" else args.fp64_peak_tflops
+    sms = sm_count(dev)
+    peak_mhz = clocks.get("sm_max_mhz") or SM_MAX_MHZ
+    peak = fp32_peak_tflops(sms, peak_mhz) if args.precision == "mixed" else fp64_peak_tflops(sms, peak_mhz)
     var = tuning[0 if dom == "acc" else 1]
     if var & 128:
         kname = f"sym_mixed_x2_kernel<{dom}, I={var & 15}, MINB={1 if var & 16 else 2}>"
@@ -320,13 +398,17 @@ def run_fsi(args):
                 "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "traffic_basis": ("DRAM bytes per launch, one ncu capture of this workload"
                                   if traffic else None),
-                "peak_basis": ("148 SMs x 128 FP32 lanes x 2 flop x 2032 MHz (max SM clock)"
-                               if args.precision == "mixed" else "FP64 FMA probe"),
+                "sm_count": sms,
+                "peak_basis": (f"{sms} SMs (device query) x 128 FP32 lanes x 2 flop x {peak_mhz:.0f} MHz "
+                               "(max SM clock)" if args.precision == "mixed" else
+                               f"{sms} SMs (device query) x {FP64_FLOP_PER_SM_CLK} FP64 flop per SM "
+                               f"per clock x {peak_mhz:.0f} MHz (max SM clock)"),
                 "per_kernel_ms": {k: prof[k][1] / max(prof[k][0], 1) for k in prof},
                 "per_kernel_launches": {k: prof[k][0] for k in prof}}
     if clocks.get("sm_mhz"):
-        roofline["frac_at_median_clock"] = achieved / fp32_peak_tflops(clocks["sm_mhz"]) \
-            if args.precision == "mixed" else None
+        roofline["frac_at_median_clock"] = achieved / (
+            fp32_peak_tflops(sms, clocks["sm_mhz"]) if args.precision == "mixed"
+            else fp64_peak_tflops(sms, clocks["sm_mhz"]))
 
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
@@ -345,11 +427,31 @@ def run_fsi(args):
                 "d2h_bytes_per_step": bytes_io, "steps": e2e_steps},
         "roofline": roofline, "clocks": clocks,
     }
+    # ---- energy drift over the warm-up and timed cycles (FP64 energy, outside the timing)
+    if e1 is not None:
+        line["energy"] = {"cycles": args.warmup + args.steps, "h": h, "E0": e0,
+                          "rel_drift": abs((e1 - e0) / e0),
+                          "what": "|E1 - E0| / |E0| of the FP64 energy of all N (T + W) before "
+                                  "the warm-up and after the timed cycles"}
+    if rank == 0 and args.precision == "mixed" and not args.no_fp64:
+        line["fp64"] = fp64_passes(F, c, pos0, mass, dev, flush, sms, peak_mhz)
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
         threads = os.cpu_count() or 1
+        # the kernels' sums at the initial state, for the accuracy check on the oracle's rows
+        ga = F.fsi_accel(ctx, pos0, mass).cpu().numpy()
+        gg = F.fsi_grad(ctx, pos0, mass, torch.as_tensor(
+            inputs.random_field(N, CPU_FIELD_SEED)).to(dev)).cpu().numpy()
         v, info = cpu_baseline(c, args.cpu_rows, threads)
+        v1, info1 = cpu_baseline(c, args.cpu_rows_1t, 1)
         line["cpu_baseline"] = {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle",
-                                "sample": info["sample"]}
+                                "sample": info["sample"],
+                                "value_1thread": v1, "sample_1thread": info1["sample"]}
+        rows = info["rows"]
+        line["accuracy"] = {
+            "against": "the FP64 oracle on the cpu_baseline sample (same-set passes of the "
+                       "benchmark's kernels at the initial state; gradient with a seeded field)",
+            "acc": error_stats(ga[:, rows], info["acc"]),
+            "grad": error_stats(gg[:, rows], info["grad"])}
     if rank == 0:
         print(json.dumps(line), flush=True)
     ctx.close()
@@ -381,8 +483,8 @@ def run_ensemble(args):
     # autotune: particles per thread x resident CTAs per SM (or fixed by --batch-tuning)
     best = None
     fixed = [tuple(int(x) for x in args.batch_tuning.split(","))] if args.batch_tuning else None
-    combos = fixed or [(ipt, cps) for ipt in ((1, 2, 4) if args.precision == "mixed" else (1, 2))
-                       for cps in (1, 2, 0)]                       # ipt 4: symmetric form
+    combos = fixed or [(ipt, cps) for ipt in ((1, 2, 4, 8) if args.precision == "mixed" else (1, 2))
+                       for cps in (1, 2, 0) if not (ipt == 8 and cps == 2)]   # ipt 4, 8: symmetric
     for ipt, cps in combos:
         F.fsi_batch_set_tuning(ctx, b, ipt, cps)
         p, v = torch.as_tensor(cat.pos).to(dev), torch.as_tensor(cat.vel).to(dev)
@@ -440,7 +542,7 @@ def run_ensemble(args):
             "tail": 1.0 - life_ns / cap_ns, "ctas": ctas}
     value = per_call * args.steps / t
     ach = value * FLOP_PAIR / 1e12
-    peak = fp32_peak_tflops() if args.precision == "mixed" else args.fp64_peak_tflops
+    peak = fp32_peak_tflops(sm_count(dev)) if args.precision == "mixed" else fp64_peak_tflops(sm_count(dev))
     line = {
         "metric": "ensemble acc+grad pair interactions/s (512 clusters, N in [64, 8192])",
         "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -616,7 +718,7 @@ def probe_peak_tflops(F, mode: int) -> float:
     """FMA throughput of this GPU measured by the library's probe (0: FP32, 1: FP64,
     2: packed FP32x2): best of 3 launches of 8 CTAs per SM."""
     import torch
-    blocks = 148 * 8
+    blocks = sm_count() * 8
     iters = 400 if mode == 1 else 20000
     sink = torch.empty(blocks * 256, dtype=torch.float64, device="cuda")
     F.fsi_fma_probe(mode, blocks, iters, sink)
@@ -679,7 +781,8 @@ def run_accgrad(args):
         ach = pairs * fl / (ms / nl / 1e3) / 1e12
         kern[k] = {"ms_per_launch": ms / nl, "launches": nl, "achieved_tflops": ach,
                    "frac_of_probe_peak": ach / peak,
-                   "frac_of_nominal_fp32": ach / fp32_peak_tflops() if args.precision == "mixed" else None}
+                   "frac_of_nominal": ach / (fp32_peak_tflops(sm_count(dev)) if args.precision == "mixed"
+                                             else fp64_peak_tflops(sm_count(dev)))}
     line = {
         "metric": f"acc+grad pair interactions/s at N={N} ({args.precision}, one acc + one grad pass)",
         "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
@@ -760,6 +863,79 @@ def run_update(args):
     return 0
 
 
+def run_sharded(args):
+    """The i-sharded FSI cycle (paper_2210_02472_b300.shard) of the headline workload over
+    all ranks: every rank kicks, drifts and sums the pairs of its slice of the set, with
+    NCCL all-gathers of the positions after drifts and of the accelerations before the
+    gradient pass.  Strong scaling: the total work (one set of N) is fixed; value = the
+    set's interactions per step / the slowest rank's time."""
+    import torch
+    rank, ws, local, dist = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2210_02472_b300 import fsi as F
+    from paper_2210_02472_b300.shard import Exchange, LibfsiCompute, ShardedFSI
+
+    c = inputs.workload(args.workload)
+    if args.n:
+        c = inputs.plummer(args.n, inputs.SEED_BASE + 3, imf="kroupa", n_bh=16)
+    N = c.n
+    dev = torch.device("cuda", local)
+    pos = torch.as_tensor(c.pos).to(dev)
+    vel = torch.as_tensor(c.vel).to(dev)
+    mass = torch.as_tensor(c.mass).to(dev)
+    bh = torch.as_tensor(c.is_bh.astype(np.uint8)).to(dev)
+    h, cl = 1.0 / 1024, 1e4
+    ctx = F.Context(args.precision, c=cl)
+    F.fsi_reserve(ctx, N, N)
+    sh = ShardedFSI(LibfsiCompute(ctx), Exchange())
+
+    def step():
+        sh.step(pos, vel, mass, h, nsteps=1, c=cl, is_bh=bh)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if F.fsi_sync_status(ctx) != F.FSI_OK:
+        raise SystemExit("device error after warm-up")
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(local)
+    sampler.start()
+    n0 = F.fsi_launch_count()
+    for k in range(args.steps):
+        ev[k][0].record(stream)
+        step()
+        ev[k][1].record(stream)
+    torch.cuda.synchronize()
+    launches = F.fsi_launch_count() - n0
+    clocks = sampler.stop()
+    if F.fsi_sync_status(ctx) != F.FSI_OK:
+        raise SystemExit("device error in the timed region")
+    t_dev = reduce_max(sum(a.elapsed_time(b) for a, b in ev) / 1e3, dist, dev)
+    value = step_interactions(N) * args.steps / t_dev
+    line = {
+        "metric": METRIC + ", i-sharded over ranks", "value": value, "unit": UNIT, "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps,
+        "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
+        "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
+        "config": {"workload": args.workload, "n": N, "precision": args.precision,
+                   "step": "one FSI cycle of all N + PN1.0 half-kicks, receivers sharded over "
+                           "ranks (one-sided pair passes over each rank's slice)",
+                   "c": cl, "h": h, "parallelism": f"i-sharded x{ws}"},
+        "gpu_launches": launches, "clocks": clocks,
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -772,12 +948,17 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cpu-rows", type=int, default=CPU_ROWS)
     ap.add_argument("--ref-rows", type=int, default=1024)
-    ap.add_argument("--fp64-peak-tflops", type=float, default=1.25)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-rows-1t", type=int, default=256,
+                    help="rows of the single-thread oracle sample of cpu_baseline")
+    ap.add_argument("--no-fp64", action="store_true",
+                    help="cycle mode: skip the FP64 acc + grad passes of the line's fp64 object")
+    ap.add_argument("--no-energy", action="store_true",
+                    help="cycle mode: skip the FP64 energies before and after the cycles")
     ap.add_argument("--tuning", default="", help="fixed pair-kernel variants 'acc,grad' "
                     "(see fsi_set_tuning); default: autotune on a 2^18 sample")
     ap.add_argument("--mode", default="cycle",
-                    choices=["cycle", "ensemble", "vjp", "hhs", "accgrad", "update"],
+                    choices=["cycle", "ensemble", "vjp", "hhs", "accgrad", "update", "sharded"],
                     help="cycle: the headline FSI-cycle benchmark; the others measure the "
                          "ensemble, adjoint and HHS workloads and one acc + grad pass")
     ap.add_argument("--batch-steps", type=int, default=10)
@@ -807,6 +988,8 @@ def main():
         return run_accgrad(args)
     if args.mode == "update":
         return run_update(args)
+    if args.mode == "sharded":
+        return run_sharded(args)
     return run_fsi(args)
 
 

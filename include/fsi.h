@@ -20,9 +20,12 @@
  *    call fsi_reserve first to keep a call sequence free of allocations (required
  *    under CUDA graph capture).
  *  - Return value: FSI_OK (0) or a negative FSI_ERR_* code for errors detected on the
- *    host (bad arguments, CUDA launch errors).  Errors detected on the device (a
- *    non-finite result, a timed-out wait) are latched in a per-context device word
- *    and reported by fsi_sync_status.  fsi_last_error() returns a thread-local text
+ *    host (bad arguments, CUDA launch errors).  Errors detected on the device
+ *    (coincident particles, a non-finite result, a timed-out wait) are latched in a
+ *    per-context device word (the first error wins) and reported by fsi_sync_status.
+ *    A pass whose result is non-finite scans its sources once for a partner at
+ *    exactly the same position and latches FSI_ERR_COINCIDENT if it finds one,
+ *    FSI_ERR_NONFINITE otherwise.  fsi_last_error() returns a thread-local text
  *    message for the last host-side error.
  *  - Self-interaction is excluded by global particle id, never by position.
  *  - G = 1 (N-body units).
@@ -34,9 +37,11 @@
  *  FSI_MIXED: positions are split into FP32 hi + lo parts so that each pair
  *             difference is accurate to FP32 precision relative to the separation;
  *             the pair arithmetic (r^-3, gradient terms) is FP32 with one residual
- *             correction of the hardware rsqrt; per-tile FP32 partial sums are
- *             accumulated in FP64.  Per-particle acceleration error is ~1e-7 relative
- *             (typically 2e-8).  Valid for separations > ~1e-7 (FP32 range of r^-5).
+ *             correction of the hardware rsqrt; a receiver's FP32 partial sums run over
+ *             at most 32 sources and are accumulated as float-float pairs (TwoSum).
+ *             Relative acceleration error |da_i| / |a_i| at N = 2^20: median 2e-8, 99th
+ *             percentile 1e-7 (larger where the pair terms cancel, |a_i| << sum_j
+ *             m_j / r_ij^2).  Valid for separations > ~1e-7 (FP32 range of r^-5).
  */
 #ifndef LIBFSI_FSI_H
 #define LIBFSI_FSI_H
@@ -51,9 +56,16 @@ extern "C" {
 #define FSI_OK 0
 #define FSI_ERR_ARG (-1)          /* invalid argument (sizes, NULL, overlapping sets) */
 #define FSI_ERR_CUDA (-2)         /* a CUDA runtime call failed */
-#define FSI_ERR_NONFINITE (-3)    /* a result was inf/NaN (coincident particles with
-                                     eps2 = 0, or FP32 overflow in the mixed path) */
-#define FSI_ERR_COINCIDENT (-4)   /* reserved: coincident particles reported as such */
+#define FSI_ERR_NONFINITE (-3)    /* a result was inf/NaN for a reason other than
+                                     coincident particles (FP32 overflow of r^-3 in the
+                                     mixed path at separations below ~1e-13, a non-finite
+                                     input) */
+#define FSI_ERR_COINCIDENT (-4)   /* two distinct particles at exactly the same position
+                                     with eps2 = 0, where the pair terms of Sect. 2.1 are
+                                     undefined (and, for the time steps of Sect. 3.4 and
+                                     the PN1.0 kick, which are unsoftened, at any eps2);
+                                     latched by the acceleration, gradient, time-step,
+                                     energy and PN passes */
 #define FSI_ERR_TIMEOUT (-5)      /* a bounded device wait ran out */
 #define FSI_ERR_MAXLEVEL (-6)     /* HHS: a particle wanted a level deeper than max_level */
 #define FSI_ERR_UNSUPPORTED (-7)
@@ -135,7 +147,9 @@ int fsi_sync_status(fsi_ctx *ctx, void *stream);
  * source set B:  acc_out[:, k] = sum_{j in B, j != A[k]} m_j (r_j - r_i) /
  *                                  (|r_j - r_i|^2 + eps2)^{3/2},  i = A[k].
  * pos: 3 x N, mass: N, A: nA ids (NULL = all), B: nB ids (NULL = all),
- * acc_out: 3 x nA (row stride nA).  A and B may overlap arbitrarily. */
+ * acc_out: 3 x nA (row stride nA).  A and B may overlap arbitrarily.  When A points into
+ * B's memory (A = B + k with k + nA <= nB, a rank's slice of a sharded pass), the self
+ * pairs are found by the index offset k and only the tiles around them are checked. */
 int fsi_accel(fsi_ctx *ctx, int N, const double *pos, const double *mass,
               const int *A, int nA, const int *B, int nB, double eps2,
               double *acc_out, void *stream);
@@ -145,7 +159,7 @@ int fsi_accel(fsi_ctx *ctx, int N, const double *pos, const double *mass,
  *   r_ji = r_j - r_i, r^2 = |r_ji|^2 + eps2, a_ji = a_j - a_i, i = A[k],
  * WITHOUT the factor eps^2/24 (the gradient acceleration is a + (eps^2/24) grad).
  * accg: 3 x N accelerations indexed by global id (only the entries of A and B are
- * read).  A and B may overlap arbitrarily. */
+ * read).  A and B may overlap arbitrarily (A a slice of B's memory: as in fsi_accel). */
 int fsi_grad(fsi_ctx *ctx, int N, const double *pos, const double *mass,
              const double *accg, const int *A, int nA, const int *B, int nB,
              double eps2, double *grad_out, void *stream);
@@ -167,7 +181,9 @@ int fsi_accel_grad(fsi_ctx *ctx, int N, const double *pos, const double *vel,
  * With n = (x_i - x_j)/r:
  *   a_i = m_j/(c^2 r^2) { n [ -v_i^2 - 2 v_j^2 + 4 v_i.v_j + 3/2 (n.v_j)^2
  *                              + 5 m_i/r + 4 m_j/r ] + (v_i - v_j) [4 n.v_i - 3 n.v_j] }.
- * out: 3 x nA.  Unsoftened. */
+ * out: 3 x nA.  Unsoftened.  Evaluated through black-hole sublists of A and B (cost
+ * O((nA + nB) x black holes)); more than 1024 black holes in a list latch
+ * FSI_ERR_UNSUPPORTED. */
 int fsi_pn_accel(fsi_ctx *ctx, int N, const double *pos, const double *vel,
                  const double *mass, const unsigned char *is_bh, double c,
                  const int *A, int nA, const int *B, int nB, double *out, void *stream);
@@ -311,8 +327,10 @@ int fsi_batch_destroy(fsi_batch *batch);
 int fsi_batch_step(fsi_ctx *ctx, fsi_batch *batch, double *pos, double *vel,
                    const double *mass, double h, int nsteps, void *stream);
 
-/* Tuning of the batched kernel: active particles per thread (1 or 2) and resident CTAs
- * per SM (0 = occupancy maximum). */
+/* Tuning of the batched kernel: active particles per thread -- 1 or 2 (one-sided form,
+ * every ordered pair by its receiver), 4 or 8 (symmetric form, every unordered pair once,
+ * mixed precision only; blocks of 1024 / 2048 particles, 2 / 1 resident CTAs per SM) --
+ * and resident CTAs per SM (0 = occupancy maximum). */
 int fsi_batch_set_tuning(fsi_ctx *ctx, fsi_batch *batch, int ipt, int ctas_per_sm);
 int fsi_batch_get_tuning(fsi_batch *batch, int *ipt, int *ctas_per_sm);
 
@@ -382,8 +400,12 @@ int fsi_set_tuning(fsi_ctx *ctx, int ipt_acc, int ipt_grad);
  * each call rewrites every scratch byte it reads (nothing needs clearing), and calls that
  * overlap on the GPU (unordered streams) race on it.  The first call on a device looks
  * the array's device address up (cudaGetSymbolAddress) and caches it; make that first
- * call before any stream capture.  Device-side errors (non-finite results) are not
- * latched anywhere: check the outputs.  Asynchronous on `stream`. */
+ * call before any stream capture.  Device-side errors are not latched anywhere (there is
+ * no context and so no error word): a non-finite result (coincident particles with
+ * eps2 = 0 included) stays in acc_out, and a bounded wait of the pair kernel that runs
+ * out (a bulk copy that never lands) makes the affected CTA write quiet NaN into its
+ * rows, so every device-side failure shows up as non-finite entries of acc_out: check
+ * them.  Asynchronous on `stream`. */
 int fsi_accel_noalloc(int N, const double *pos, const double *mass, double eps2,
                       double *acc_out, void *stream);
 

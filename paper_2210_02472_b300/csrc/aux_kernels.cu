@@ -596,6 +596,29 @@ cudaError_t launch_pn_cross(long long N, const double* pos, const double* vel, c
     return cudaGetLastError();
 }
 
+// PN1.0 accelerations of the id list A from the id list B (any overlap; self pairs skipped
+// by id) through the black-hole sublists: for i in A the terms of B's black holes j != i,
+// plus, for a black hole i of A, the terms of B's other particles.  out (3 x nA)
+// overwritten.  A pair with a black hole is counted once per receiver: a black-hole pair
+// by the first kernel, a black hole with a star by the first (receiver the star) or the
+// second (receiver the black hole).
+cudaError_t launch_pn_lists(long long N, const double* pos, const double* vel, const double* mass,
+                            const unsigned char* is_bh, double c, const int* A, int nA, const int* B,
+                            int nB, int* Abh, int* nAbh, int* Bbh, int* nBbh, double* out,
+                            double* part, int* err, cudaStream_t s) {
+    if (nA <= 0) return cudaSuccess;
+    const double ic2 = 1.0 / (c * c);
+    { bh_sublist_kernel<<<1, 1024, 0, s>>>(nA, A, is_bh, Abh, nAbh, err); note_launch(); }
+    { bh_sublist_kernel<<<1, 1024, 0, s>>>(nB, B, is_bh, Bbh, nBbh, err); note_launch(); }
+    { pn_list_from_bh_kernel<<<blocks_for(nA), kB, 0, s>>>(N, pos, vel, mass, A, nA, B, Bbh, nBbh, ic2, out, err); note_launch(); }
+    if (nB > 0) {
+        const dim3 g(kPnCtas, 32);
+        { pn_list_bh_from_all_kernel<<<g, kB, 0, s>>>(N, pos, vel, mass, is_bh, A, Abh, nAbh, B, nB, ic2, part, err); note_launch(); }
+        { pn_list_bh_finish_kernel<<<blocks_for(kMaxBH), kB, 0, s>>>(Abh, nAbh, nA, part, out); note_launch(); }
+    }
+    return cudaGetLastError();
+}
+
 // ---------------------------------------------------------------------------------
 // Small O(n^2) FP64 loops (time steps, energy): thread per i, sources through shared
 // memory in plain cooperative tiles.
@@ -639,7 +662,7 @@ __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const dou
         }
     }
     if (i >= n) return;
-    if (coincident) set_error(err, FSI_ERR_NONFINITE);
+    if (coincident) set_error(err, FSI_ERR_COINCIDENT);
     step[i] = step_finish<double>(acc, eta_ff, eta_fb, eta_jerk);
 }
 
@@ -735,7 +758,7 @@ __global__ void energy_kernel(int n, const double* __restrict__ xc, const double
             if (j0 + t == ii) continue;
             const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
             const double r2 = dx * dx + dy * dy + dz * dz + eps2;
-            if (r2 == 0.0) { if (i < n) set_error(err, FSI_ERR_NONFINITE); continue; }
+            if (r2 == 0.0) { if (i < n) set_error(err, FSI_ERR_COINCIDENT); continue; }
             w = fma(sm[t], rsqrt_f64(r2), w);
         }
     }

@@ -69,6 +69,33 @@ __device__ __forceinline__ void batch_stats_exit(const BatchArgs& a, long long t
     }
 }
 
+// Error path of a non-finite pass sum of cluster particle il (global index off + il):
+// without softening, a distinct particle of the same cluster at exactly the same position
+// in the pass's records rin makes a pair term 0 x inf and is reported as
+// FSI_ERR_COINCIDENT, anything else as FSI_ERR_NONFINITE.  Only the thread that claims the
+// empty error word scans the cluster (first error wins).
+template <int P>
+__device__ __noinline__ void batch_report_nonfinite(const BatchArgs& a, const void* rin, long long off,
+                                                    int n, int il) {
+    if (!a.err || atomicCAS(a.err, 0, FSI_ERR_NONFINITE) != 0) return;
+    if (a.eps2 != 0.0) return;
+    bool hit = false;
+    for (int j = 0; j < n && !hit; ++j) {
+        if (j == il) continue;
+        if constexpr (P == FSI_MIXED) {
+            const RecMix ri = reinterpret_cast<const RecMix*>(rin)[off + il];
+            const RecMix rj = reinterpret_cast<const RecMix*>(rin)[off + j];
+            hit = rj.hi.x == ri.hi.x && rj.hi.y == ri.hi.y && rj.hi.z == ri.hi.z &&
+                  rj.lo.x == ri.lo.x && rj.lo.y == ri.lo.y && rj.lo.z == ri.lo.z;
+        } else {
+            const D4 ri = reinterpret_cast<const D4*>(rin)[off + il];
+            const D4 rj = reinterpret_cast<const D4*>(rin)[off + j];
+            hit = rj.x == ri.x && rj.y == ri.y && rj.z == ri.z;
+        }
+    }
+    if (hit) atomicCAS(a.err, FSI_ERR_NONFINITE, FSI_ERR_COINCIDENT);
+}
+
 template <int P, int I>
 __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs a) {
     constexpr int JREC = 32;
@@ -290,7 +317,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
                 if (myl[u] >= it.n) continue;
                 const long long i = it.off + myl[u];
                 double r3[3] = {acc64[u][0], acc64[u][1], acc64[u][2]};
-                if (!(isfinite(r3[0]) && isfinite(r3[1]) && isfinite(r3[2]))) set_error(a.err, FSI_ERR_NONFINITE);
+                if (!(isfinite(r3[0]) && isfinite(r3[1]) && isfinite(r3[2])))
+                    batch_report_nonfinite<P>(a, rin, it.off, it.n, myl[u]);
                 if (role == 2) {
                     const double mi = a.m[i];
 #pragma unroll
@@ -357,13 +385,21 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_kernel(const BatchArgs
 // shared-memory ring filled by cp.async.bulk on mbarriers whose phase parity follows a
 // running per-CTA tile count; every wait is bounded as in batch_kernel.
 namespace {
-constexpr int kBSNP = kBatchSymI / 2;                                // packed pairs per thread
-constexpr int kBSBlock = kBatchThreads * kBatchSymI;                 // particles per block
+// ring depth of the symmetric form: a block's own tiles (4 with 4 particles per thread) land
+// at once, so its diagonal item runs with one barrier instead of one per tile
+constexpr int kBSStages = 4;
 constexpr int kBSStage = kBatchTile * (32 + 16);                     // record + accel record
 constexpr int kBSJpart = (kBatchThreads / 32) * kBatchTile * 3 * 4;
-constexpr int kBSAccS = kBSNP * 3 * kBatchThreads * 16;
-constexpr int kBSSmem = kStages * kBSStage + kBSJpart + kBSAccS;
 static_assert(kBatchTile == kTileJ && kBatchThreads == kThreads, "tile sizes of sym_x2.cuh");
+// I particles per thread: a block of 256 I particles (I source tiles), I / 2 packed pairs
+// per thread; warp w holds the I consecutive 32-record sub-tiles of group w of the block.
+template <int I>
+struct BS {
+    static constexpr int NP = I / 2;                                 // packed pairs per thread
+    static constexpr int Block = kBatchThreads * I;                  // particles per block
+    static constexpr int AccS = NP * 3 * kBatchThreads * 16;
+    static constexpr int Smem = kBSStages * kBSStage + kBSJpart + AccS;
+};
 }  // namespace
 
 __device__ __forceinline__ void fence_proxy_async() {
@@ -376,7 +412,6 @@ __device__ __forceinline__ void batch_apply(const BatchArgs& a, int role, bool l
                                             const double (&r3)[3], void* rout) {
     const long long N = a.ntot;
     const double h = a.h;
-    if (!(isfinite(r3[0]) && isfinite(r3[1]) && isfinite(r3[2]))) set_error(a.err, FSI_ERR_NONFINITE);
     if (role == 2) {
         const double mi = a.m[i];
 #pragma unroll
@@ -425,11 +460,11 @@ __device__ __forceinline__ void batch_apply(const BatchArgs& a, int role, bool l
 // One sum item: block `it.block` of cluster it.cluster against its source tiles [t0, t1).
 // g: the CTA's running tile count (advanced by the item's tiles).  Returns false if a wait
 // timed out (the caller leaves the kernel).
-template <int KIND>
+template <int KIND, int I>
 __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const void* rin,
                                double* __restrict__ accum, unsigned char* smem, uint64_t* bars,
                                float* jpart, float4* acc_s, unsigned& g) {
-    constexpr int I = kBatchSymI, NP = kBSNP;
+    constexpr int NP = BS<I>::NP;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const long long N = a.ntot;
     const RecMix* R = reinterpret_cast<const RecMix*>(rin) + it.off;
@@ -438,7 +473,7 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
     const int ntiles = it.t1 - it.t0;
     auto issue = [&](int tl) {
         const unsigned gg = g + (unsigned)tl;
-        const int st = (int)(gg % kStages);
+        const int st = (int)(gg % kBSStages);
         const int jt = (it.t0 + tl) * kBatchTile;
         const int cnt = min(kBatchTile, it.n - jt);
         unsigned char* base = smem + st * kBSStage;
@@ -448,10 +483,10 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
     };
     if (tid == 0) {
         fence_proxy_async();            // records written by generic stores of earlier phases
-        for (int tl = 0; tl < min(kStages, ntiles); ++tl) issue(tl);
+        for (int tl = 0; tl < min(kBSStages, ntiles); ++tl) issue(tl);
     }
     // i-side state: warp w holds the 32 I consecutive particles i0 + 32 I w + 32 u + lane
-    const int ib = it.block * kBSBlock + warp * (32 * I) + lane;
+    const int ib = it.block * BS<I>::Block + warp * (32 * I) + lane;
     X2I pp[NP];
     float2 f[NP][3];
 #pragma unroll
@@ -486,67 +521,94 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
     const float2 eps2 = bc2(eps2f);
     bool ok_all = true;
     int t_stop = ntiles;
-    for (int tl = 0; tl < ntiles; ++tl) {
+    // the block's own tiles, each unordered pair once: warp w holds the block's 32-record
+    // sub-tiles I w .. I w + I - 1 (group w); the pairs of groups w and v != w are evaluated
+    // symmetrically by w when (v - w) mod 8 is 1, 2 or 3, or 4 with w < 4 (by v otherwise),
+    // so every warp takes 3 or 4 of the 7 other groups; its own group one-sided (self pair
+    // excluded by index).  A warp past the end of the cluster holds copies of its last
+    // particle and takes no pairs: that particle's pairs belong to the warp that holds it.
+    // DIRECT: the source-side totals go straight into the accumulator (every own tile in
+    // shared memory at once, no barrier between tiles); otherwise into jpart per tile.
+    auto diag_tile = [&](int tl, const RecMix* rec, const float4* arec, int jt, int cnt, auto direct) {
+        constexpr bool DIRECT = decltype(direct)::value;
+        const bool wvalid = it.block * BS<I>::Block + warp * (32 * I) < it.n;
+        double* jg = accum + it.off + jt;
+        float2 D0[NP][3];
+        for (int k0 = 0; k0 < cnt; k0 += 32) {
+            const int jend = min(cnt, k0 + 32);
+            const int sub = 8 * tl + (k0 >> 5);                // sub-tile within the block
+            const int dv = ((sub / I) - warp) & 7;
+            if (wvalid && dv >= 1 && (dv <= 3 || (dv == 4 && warp < 4))) {
+                if (jend - k0 < 32) {
+                    for (int jj = k0; jj < jend; jj += 4)
+                        x2_group<KIND, NP, false, false, DIRECT>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart, jg, N);
+                } else {
+                    for (int jj = k0; jj < jend; jj += 4)
+                        x2_group<KIND, NP, false, true, DIRECT>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart, jg, N);
+                }
+                continue;
+            }
+            if (!DIRECT && k0 + lane < jend) {
+                float* dst = jpart + ((size_t)warp * kBatchTile + k0 + lane) * 3;
+                dst[0] = dst[1] = dst[2] = 0.f;
+            }
+            if (dv != 0) continue;
+            for (int jj = k0; jj < jend; ++jj) {
+                const float4 h = rec[jj].hi;
+                const float4 l = rec[jj].lo;
+                const int j = jt + jj;
+                if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        x2_acc_one_chk(h, l, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
+                } else {
+                    const float4 aj = arec[jj];
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+                        x2_grad_one_chk(h, l, aj, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
+                }
+            }
+        }
+#pragma unroll
+        for (int p = 0; p < NP; ++p)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                ff_add2(acc_s[(p * 3 + c) * kBatchThreads + tid], f[p][c]);
+                f[p][c] = make_float2(0.f, 0.f);
+            }
+    };
+    if (diag && ntiles <= kBSStages) {
+        // every own tile was issued above: wait for all, one pass over them, one barrier
+        bool ok = true;
+        for (int tl = 0; tl < ntiles; ++tl) {
+            const unsigned gg = g + (unsigned)tl;
+            ok = mbar_wait_bounded(&bars[gg % kBSStages], (gg / kBSStages) & 1u, a.timeout_ns, a.err) && ok;
+        }
+        if (!__syncthreads_or(!ok)) {
+            for (int tl = 0; tl < ntiles; ++tl) {
+                const unsigned char* base = smem + ((g + (unsigned)tl) % kBSStages) * kBSStage;
+                const int jt = (it.t0 + tl) * kBatchTile;
+                diag_tile(tl, reinterpret_cast<const RecMix*>(base),
+                          reinterpret_cast<const float4*>(base + kBatchTile * 32), jt,
+                          min(kBatchTile, it.n - jt), std::true_type{});
+            }
+        } else {
+            ok_all = false;
+            t_stop = 0;
+        }
+        __syncthreads();                // shared memory free for the next item's copies
+    }
+    for (int tl = 0; tl < ntiles && !(diag && ntiles <= kBSStages); ++tl) {
         const unsigned gg = g + (unsigned)tl;
-        const int st = (int)(gg % kStages);
-        const bool ok = mbar_wait_bounded(&bars[st], (gg / kStages) & 1u, a.timeout_ns, a.err);
+        const int st = (int)(gg % kBSStages);
+        const bool ok = mbar_wait_bounded(&bars[st], (gg / kBSStages) & 1u, a.timeout_ns, a.err);
         const int jt = (it.t0 + tl) * kBatchTile;
         const int cnt = min(kBatchTile, it.n - jt);
         const unsigned char* base = smem + st * kBSStage;
         const RecMix* rec = reinterpret_cast<const RecMix*>(base);
         const float4* arec = reinterpret_cast<const float4*>(base + kBatchTile * 32);
         if (diag) {
-            // the block's own tiles, each unordered pair once: warp w holds the block's
-            // 32-record sub-tiles 4w .. 4w+3 (group w); the pairs of groups w and v != w
-            // are evaluated symmetrically by w when (v - w) mod 8 is 1, 2 or 3, or 4 with
-            // w < 4 (by v otherwise), so every warp takes 3 or 4 of the 7 other groups;
-            // its own group one-sided (self pair excluded by index).  A warp past the end of
-            // the cluster holds copies of its last particle and takes no pairs: that
-            // particle's pairs belong to the warp that holds it
-            const bool wvalid = it.block * kBSBlock + warp * (32 * I) < it.n;
-            float2 D0[NP][3];
-            for (int k0 = 0; k0 < cnt; k0 += 32) {
-                const int jend = min(cnt, k0 + 32);
-                const int sub = 8 * tl + (k0 >> 5);                // sub-tile within the block
-                const int dv = ((sub >> 2) - warp) & 7;
-                if (wvalid && dv >= 1 && (dv <= 3 || (dv == 4 && warp < 4))) {
-                    if (jend - k0 < 32) {
-                        for (int jj = k0; jj < jend; jj += 4)
-                            x2_group<KIND, NP, false, false>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
-                    } else {
-                        for (int jj = k0; jj < jend; jj += 4)
-                            x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, nullptr, pp, D0, eps2, f, jpart);
-                    }
-                    continue;
-                }
-                if (k0 + lane < jend) {
-                    float* dst = jpart + ((size_t)warp * kBatchTile + k0 + lane) * 3;
-                    dst[0] = dst[1] = dst[2] = 0.f;
-                }
-                if (dv != 0) continue;
-                for (int jj = k0; jj < jend; ++jj) {
-                    const float4 h = rec[jj].hi;
-                    const float4 l = rec[jj].lo;
-                    const int j = jt + jj;
-                    if constexpr (KIND == KIND_ACC) {
-#pragma unroll
-                        for (int p = 0; p < NP; ++p)
-                            x2_acc_one_chk(h, l, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
-                    } else {
-                        const float4 aj = arec[jj];
-#pragma unroll
-                        for (int p = 0; p < NP; ++p)
-                            x2_grad_one_chk(h, l, aj, pp[p], eps2, j == ib + 64 * p, j == ib + 64 * p + 32, f[p]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int p = 0; p < NP; ++p)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    ff_add2(acc_s[(p * 3 + c) * kBatchThreads + tid], f[p][c]);
-                    f[p][c] = make_float2(0.f, 0.f);
-                }
+            diag_tile(tl, rec, arec, jt, cnt, std::false_type{});
         } else {
             float2 D0[NP][3];
             for (int k0 = 0; k0 < cnt; k0 += 32) {
@@ -578,15 +640,15 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
             }
         }
         __syncthreads();
-        if (tid == 0 && tl + kStages < ntiles) issue(tl + kStages);
+        if (tid == 0 && tl + kBSStages < ntiles) issue(tl + kBSStages);
     }
     if (!ok_all) {
         // let every copy still in flight land (bounded) before the CTA leaves
         if (tid == 0) {
-            const int issued = min(ntiles, t_stop + kStages);
+            const int issued = min(ntiles, t_stop + kBSStages);
             for (int tl = t_stop; tl < issued; ++tl) {
                 const unsigned gg = g + (unsigned)tl;
-                mbar_wait_bounded(&bars[gg % kStages], (gg / kStages) & 1u, a.timeout_ns, nullptr);
+                mbar_wait_bounded(&bars[gg % kBSStages], (gg / kBSStages) & 1u, a.timeout_ns, nullptr);
             }
         }
         __syncthreads();
@@ -606,14 +668,15 @@ __device__ bool batch_sum_item(const BatchArgs& a, const BatchSymItem& it, const
     return true;
 }
 
-__global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
+template <int I, int MINB>
+__global__ void __launch_bounds__(kBatchThreads, MINB) batch_sym_kernel(
     const BatchArgs a, const BatchSymItem* __restrict__ sitems, int nS, const int* __restrict__ nsum,
     double* __restrict__ accum) {
     extern __shared__ __align__(128) unsigned char smem[];
-    __shared__ __align__(8) uint64_t bars[kStages];
+    __shared__ __align__(8) uint64_t bars[kBSStages];
     __shared__ int s_item, s_flag;
-    float* jpart = reinterpret_cast<float*>(smem + kStages * kBSStage);
-    float4* acc_s = reinterpret_cast<float4*>(smem + kStages * kBSStage + kBSJpart);
+    float* jpart = reinterpret_cast<float*>(smem + kBSStages * kBSStage);
+    float4* acc_s = reinterpret_cast<float4*>(smem + kBSStages * kBSStage + kBSJpart);
     const int tid = threadIdx.x;
     const long long N = a.ntot;
     const long long t_start = global_ns();
@@ -622,7 +685,7 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
     const int npass = 1 + 3 * a.nsteps;
     const long long total = (long long)nA + (long long)npass * (long long)(nS + nA);
     if (tid == 0) {
-        for (int st = 0; st < kStages; ++st) mbar_init(&bars[st], 1);
+        for (int st = 0; st < kBSStages; ++st) mbar_init(&bars[st], 1);
         fence_mbar_init();
     }
     __syncthreads();
@@ -682,8 +745,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
             // pack the block's records from x
             const BatchItem it = a.items[r];
 #pragma unroll
-            for (int u = 0; u < kBatchSymI; ++u) {
-                const int il = it.block * kBSBlock + u * kBatchThreads + tid;
+            for (int u = 0; u < I; ++u) {
+                const int il = it.block * BS<I>::Block + u * kBatchThreads + tid;
                 if (il < it.n) {
                     const long long i = it.off + il;
                     const RecMix rr = make_mix_rec(a.x[i], a.x[N + i], a.x[2 * N + i], a.m[i]);
@@ -697,8 +760,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
             // roles 1 and 4 read rec0, 2 and 3 read rec1
             const void* rin = (role == 1 || role == 4) ? a.rec0 : a.rec1;
             const bool ok = role == 3
-                ? batch_sum_item<KIND_GRAD>(a, it, rin, accum, smem, bars, jpart, acc_s, g)
-                : batch_sum_item<KIND_ACC>(a, it, rin, accum, smem, bars, jpart, acc_s, g);
+                ? batch_sum_item<KIND_GRAD, I>(a, it, rin, accum, smem, bars, jpart, acc_s, g)
+                : batch_sum_item<KIND_ACC, I>(a, it, rin, accum, smem, bars, jpart, acc_s, g);
             if (!ok) {
                 if (tid == 0) atomicExch(a.abort_flag, 1);
                 batch_stats_exit(a, t_start, waited);
@@ -709,8 +772,8 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
             const bool last_acc = (role == 4) && (pass == npass - 1);
             void* rout = (role == 3) ? a.rec0 : a.rec1;
 #pragma unroll
-            for (int u = 0; u < kBatchSymI; ++u) {
-                const int il = it.block * kBSBlock + u * kBatchThreads + tid;
+            for (int u = 0; u < I; ++u) {
+                const int il = it.block * BS<I>::Block + u * kBatchThreads + tid;
                 if (il >= it.n) continue;
                 const long long i = it.off + il;
                 double r3[3];
@@ -719,6 +782,9 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
                     r3[c] = __ldcg(accum + c * N + i);
                     __stcg(accum + c * N + i, 0.0);
                 }
+                if (!(isfinite(r3[0]) && isfinite(r3[1]) && isfinite(r3[2])))
+                    batch_report_nonfinite<FSI_MIXED>(a, (role == 1 || role == 4) ? a.rec0 : a.rec1,
+                                                      it.off, it.n, il);
                 batch_apply<FSI_MIXED>(a, role, last_acc, i, r3, rout);
             }
         }
@@ -733,26 +799,45 @@ __global__ void __launch_bounds__(kBatchThreads, 2) batch_sym_kernel(
     }
 }
 
-cudaError_t launch_batch_sym(int ctas, const BatchArgs& a, const BatchSymItem* sitems,
-                             int sitems_per_phase, const int* nsum, double* accum,
-                             cudaStream_t s) {
+template <int I, int MINB>
+static cudaError_t launch_batch_sym_i(int ctas, const BatchArgs& a, const BatchSymItem* sitems,
+                                      int sitems_per_phase, const int* nsum, double* accum,
+                                      cudaStream_t s) {
     static bool attr = false;
     if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(batch_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSSmem);
+        cudaError_t e = cudaFuncSetAttribute(batch_sym_kernel<I, MINB>,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, BS<I>::Smem);
         if (e != cudaSuccess) return e;
         attr = true;
     }
-    { batch_sym_kernel<<<ctas, kBatchThreads, kBSSmem, s>>>(a, sitems, sitems_per_phase, nsum, accum); note_launch(); }
+    { batch_sym_kernel<I, MINB><<<ctas, kBatchThreads, BS<I>::Smem, s>>>(a, sitems, sitems_per_phase, nsum, accum); note_launch(); }
     return cudaGetLastError();
 }
 
-int batch_sym_max_ctas_per_sm() {
-    if (cudaFuncSetAttribute(batch_sym_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kBSSmem) != cudaSuccess)
+cudaError_t launch_batch_sym(int ipt, int ctas, const BatchArgs& a, const BatchSymItem* sitems,
+                             int sitems_per_phase, const int* nsum, double* accum,
+                             cudaStream_t s) {
+    if (ipt == kBatchSymI) return launch_batch_sym_i<kBatchSymI, 2>(ctas, a, sitems, sitems_per_phase, nsum, accum, s);
+    if (ipt == kBatchSymI2) return launch_batch_sym_i<kBatchSymI2, 1>(ctas, a, sitems, sitems_per_phase, nsum, accum, s);
+    return cudaErrorInvalidValue;
+}
+
+template <int I, int MINB>
+static int batch_sym_ctas_i() {
+    if (cudaFuncSetAttribute(batch_sym_kernel<I, MINB>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             BS<I>::Smem) != cudaSuccess)
         return 0;
     int nb = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_sym_kernel, kBatchThreads, kBSSmem) != cudaSuccess)
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, batch_sym_kernel<I, MINB>, kBatchThreads,
+                                                      BS<I>::Smem) != cudaSuccess)
         return 0;
     return nb;
+}
+
+int batch_sym_max_ctas_per_sm(int ipt) {
+    if (ipt == kBatchSymI) return batch_sym_ctas_i<kBatchSymI, 2>();
+    if (ipt == kBatchSymI2) return batch_sym_ctas_i<kBatchSymI2, 1>();
+    return 0;
 }
 
 cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, cudaStream_t s) {

@@ -85,6 +85,7 @@ struct fsi_ctx {
     std::vector<Buf> lvS, lvF;
     Buf vj[24];                     // adjoint work arrays
     Buf dstats;                     // device HHS stats: level counts (64), work (2), flags
+    Buf pnids;                      // fsi_pn_accel: the ids 0 .. N-1 for a NULL list
     std::vector<long long> level_counts;
     int max_level_used = 0;
     int max_level_hit = 0;
@@ -450,6 +451,16 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
 
 bool valid_prec(int p) { return p == FSI_FP64 || p == FSI_MIXED; }
 
+// Offset k of an id list A inside the id list B when A is the sub-range B[k, k + nA) (same
+// memory: a slice of B, as a sharded pass hands each rank), else -1.
+long long sub_range(const int* A, int nA, const int* B, int nB) {
+    if (!A || !B || A == B) return -1;
+    const uintptr_t a = reinterpret_cast<uintptr_t>(A), b = reinterpret_cast<uintptr_t>(B);
+    if (a < b || (a - b) % sizeof(int)) return -1;
+    const long long k = (long long)((a - b) / sizeof(int));
+    return k + nA <= nB ? k : -1;
+}
+
 int check_common(fsi_ctx* c, int N) {
     if (!c) return fail(FSI_ERR_ARG, "NULL context");
     if (N <= 0) return fail(FSI_ERR_ARG, "N must be positive (got %d)", N);
@@ -713,10 +724,22 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
         const bool sym = c->p.symmetric && n >= steps_sym_min_n();
         CK(ensure(c->stpart, sym ? steps_sym_work_bytes(n) : steps_x2_part_bytes(n, c->sm_count)));
         CU(launch_pack_vel(N, vel, mass, Pids, n, c->accrec[1].p, pos, c->rec[1].p, s));
-        if (sym)
+        if (sym) {
+            // HHS level lists in Morton order: far source sub-tiles take the 3-addition
+            // separation relative to their centre, as in the bipartite cross-level kernel
+            const void* frel = nullptr;
+            const void* fsub = nullptr;
+            if (c->lists_ordered && n >= std::min(kCrossFarMin, order_threshold(c))) {
+                CK(ensure(c->xrel, pad_tile(n) * 16));
+                CK(ensure(c->xsub, (pad_tile(n) / 32) * 16));
+                CU(launch_subtiles(n, c->rec[1].p, c->xrel.p, c->xsub.p, s, true));
+                frel = c->xrel.p;
+                fsub = c->xsub.p;
+            }
             CU(launch_steps_sym(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
-                                c->p.eta_jerk, c->stpart.p, step, c->err_d, budget(c), c->sm_count, s));
-        else
+                                c->p.eta_jerk, c->stpart.p, step, c->err_d, budget(c), c->sm_count, s,
+                                frel, fsub, (kFarKappa + 1.0f) * (kFarKappa + 1.0f)));
+        } else
             CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
                                c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c),
                                c->sm_count, wide_limit(c), s));
@@ -827,12 +850,15 @@ struct fsi_batch {
     int ipt = 1;
     int ctas_per_sm = 2;
     int stall_cluster = -1;          // test hook (fsi_batch_inject_stall)
-    // per particles-per-thread variant (index 1, 2: one-sided; kBatchSymI: symmetric)
-    std::vector<int> nblocks_h[kBatchSymI + 1];
-    Buf items[kBatchSymI + 1], nblocks[kBatchSymI + 1];
-    int items_per_phase[kBatchSymI + 1] = {};
-    Buf sitems, nsum, accum;         // symmetric form: sum items, sum items per cluster
-    int sitems_per_phase = 0;
+    // per particles-per-thread variant (index 1, 2: one-sided; kBatchSymI, kBatchSymI2:
+    // symmetric)
+    std::vector<int> nblocks_h[kBatchSymI2 + 1];
+    Buf items[kBatchSymI2 + 1], nblocks[kBatchSymI2 + 1];
+    int items_per_phase[kBatchSymI2 + 1] = {};
+    // symmetric form, per variant (index ipt): sum items, sum items per cluster
+    Buf sitems[kBatchSymI2 + 1], nsum[kBatchSymI2 + 1];
+    int sitems_per_phase[kBatchSymI2 + 1] = {};
+    Buf accum;
     Buf rec0, rec1, accrec, ac, done, ctrl;
     Buf stats;                       // idle accounting: wait ns, CTA lifetime ns
     int last_ctas = 0;
@@ -900,7 +926,7 @@ int fsi_destroy(fsi_ctx* c) {
                    &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
                    &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
                    &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos, &c->stpart,
-                   &c->xrel, &c->xsub};
+                   &c->xrel, &c->xsub, &c->pnids};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -995,6 +1021,15 @@ int fsi_accel(fsi_ctx* c, int N, const double* pos, const double* mass, const in
         a.check = CHECK_DIAG;
         CK(run_pair(c, KIND_ACC, a, s));
         return ord.on ? ord.unsort(c, P<double>(c->tA), nA, acc_out, s) : FSI_OK;
+    } else if (const long long off = sub_range(A, nA, B, nB); off >= 0) {
+        // A is the sub-range B[off, off + nA) of the source list (a rank's slice of a
+        // sharded pass): one packing of B, self pairs by index offset
+        CK(ensure(c->rec[1], pad_tile(nB) * 32));
+        CU(launch_pack(prec, N, pos, mass, B, nB, c->rec[1].p, nullptr, s));
+        a.jrec = c->rec[1].p;
+        a.irec = static_cast<const unsigned char*>(c->rec[1].p) + off * 32;
+        a.check = CHECK_DIAG;
+        a.i_off = (int)off;
     } else {
         CK(ensure(c->rec[1], pad_tile(nB) * 32));
         CK(ensure(c->ids[0], pad_tile(nA) * 4));
@@ -1042,6 +1077,19 @@ int fsi_grad(fsi_ctx* c, int N, const double* pos, const double* mass, const dou
         a.check = CHECK_DIAG;
         CK(run_pair(c, KIND_GRAD, a, s));
         return ord.on ? ord.unsort(c, P<double>(c->tA), nA, grad_out, s) : FSI_OK;
+    } else if (const long long off = sub_range(A, nA, B, nB); off >= 0) {
+        // A is the sub-range B[off, off + nA) of the source list: one packing of B
+        CK(ensure(c->rec[1], pad_tile(nB) * 32));
+        CK(ensure(c->accrec[1], pad_tile(nB) * 32));
+        CU(launch_pack(prec, N, pos, mass, B, nB, c->rec[1].p, nullptr, s));
+        CU(launch_pack_acc(prec, N, accg, mass, B, nB, c->accrec[1].p, nullptr, s));
+        const size_t accb = prec == FSI_MIXED ? 16 : 32;
+        a.jrec = c->rec[1].p;
+        a.jacc = c->accrec[1].p;
+        a.irec = static_cast<const unsigned char*>(c->rec[1].p) + off * 32;
+        a.iacc = static_cast<const unsigned char*>(c->accrec[1].p) + off * accb;
+        a.check = CHECK_DIAG;
+        a.i_off = (int)off;
     } else {
         CK(ensure(c->rec[1], pad_tile(nB) * 32));
         CK(ensure(c->accrec[1], pad_tile(nB) * 32));
@@ -1135,7 +1183,24 @@ int fsi_pn_accel(fsi_ctx* c, int N, const double* pos, const double* vel, const 
     if (!(cl > 0.0)) return fail(FSI_ERR_ARG, "speed of light must be positive");
     if (nA == 0) return FSI_OK;
     if (!pos || !vel || !mass || !is_bh || !out) return fail(FSI_ERR_ARG, "NULL array");
-    CU(launch_pn_pairs(N, pos, vel, mass, is_bh, cl, A, nA, B, nB, out, c->err_d, S(stream)));
+    // the pairs with a black hole through black-hole sublists of both lists (a NULL list
+    // becomes the ids 0 .. N-1): O((nA + nB) x black holes) instead of O(nA nB)
+    const cudaStream_t s = S(stream);
+    const int* Al = A;
+    const int* Bl = B;
+    if (!A || !B) {
+        CK(ensure(c->pnids, (size_t)N * sizeof(int)));
+        CU(launch_iota(N, P<int>(c->pnids), s));
+        if (!A) Al = P<int>(c->pnids);
+        if (!B) Bl = P<int>(c->pnids);
+    }
+    CK(ensure(c->bhlist, 2 * kMaxBHList * 4));
+    CK(ensure(c->nbh, 16));
+    CK(ensure(c->pnpart, (size_t)kMaxBHList * 3 * kPnPartCtas * 8));
+    int* bl = P<int>(c->bhlist);
+    int* nb = P<int>(c->nbh);
+    CU(launch_pn_lists(N, pos, vel, mass, is_bh, cl, Al, nA, Bl, nB, bl, nb, bl + kMaxBHList, nb + 1,
+                       out, P<double>(c->pnpart), c->err_d, s));
     return FSI_OK;
 }
 
@@ -1572,7 +1637,7 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
         return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
     });
     int rc = FSI_OK;
-    for (int ipt : {1, 2, kBatchSymI}) {
+    for (int ipt : {1, 2, kBatchSymI, kBatchSymI2}) {
         if (rc != FSI_OK) break;
         const int bs = batch_block_size(ipt);
         std::vector<BatchItem> items;
@@ -1591,11 +1656,12 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
              cudaMemcpy(b->nblocks[ipt].p, b->nblocks_h[ipt].data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
             rc = fail(FSI_ERR_CUDA, "batch plan upload failed");
     }
-    if (rc == FSI_OK && c->p.precision == FSI_MIXED) {
-        // symmetric form: per cluster (largest first) and block, the block's own tiles, then
-        // chunks of kBatchSymChunk source tiles above it
+    for (int si : {kBatchSymI, kBatchSymI2}) {
+        if (rc != FSI_OK || c->p.precision != FSI_MIXED) break;
+        // symmetric form: per cluster (largest first) and block of 256 si particles, the
+        // block's own si tiles, then chunks of kBatchSymChunk source tiles above it
         constexpr int kBatchSymChunk = 8;
-        const int bs = batch_block_size(kBatchSymI);
+        const int bs = batch_block_size(si);
         std::vector<BatchSymItem> sit;
         std::vector<int> nsum(K, 0);
         for (int k : order) {
@@ -1603,7 +1669,7 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
             const int ntj = (n + 255) / 256;
             const int nb = (n + bs - 1) / bs;
             for (int q = 0; q < nb; ++q) {
-                const int own0 = q * kBatchSymI, own1 = std::min((q + 1) * kBatchSymI, ntj);
+                const int own0 = q * si, own1 = std::min((q + 1) * si, ntj);
                 sit.push_back(BatchSymItem{k, q, (int)offsets[k], n, own0, own1});
                 for (int t0 = own1; t0 < ntj; t0 += kBatchSymChunk)
                     sit.push_back(BatchSymItem{k, q, (int)offsets[k], n, t0, std::min(t0 + kBatchSymChunk, ntj)});
@@ -1612,13 +1678,13 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
             for (size_t z = 0; z < sit.size(); ++z) cnt += sit[z].cluster == k;
             nsum[k] = cnt;
         }
-        b->sitems_per_phase = (int)sit.size();
-        rc = ensure(b->sitems, sit.size() * sizeof(BatchSymItem));
-        if (rc == FSI_OK) rc = ensure(b->nsum, (size_t)K * sizeof(int));
+        b->sitems_per_phase[si] = (int)sit.size();
+        rc = ensure(b->sitems[si], sit.size() * sizeof(BatchSymItem));
+        if (rc == FSI_OK) rc = ensure(b->nsum[si], (size_t)K * sizeof(int));
         if (rc == FSI_OK) rc = ensure(b->accum, 3 * (size_t)ntot * sizeof(double));
         if (rc == FSI_OK &&
-            (cudaMemcpy(b->sitems.p, sit.data(), sit.size() * sizeof(BatchSymItem), cudaMemcpyHostToDevice) != cudaSuccess ||
-             cudaMemcpy(b->nsum.p, nsum.data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
+            (cudaMemcpy(b->sitems[si].p, sit.data(), sit.size() * sizeof(BatchSymItem), cudaMemcpyHostToDevice) != cudaSuccess ||
+             cudaMemcpy(b->nsum[si].p, nsum.data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
             rc = fail(FSI_ERR_CUDA, "batch plan upload failed");
     }
     // phases: one-sided form 2 + 3 S (pack, first pass, 3 per step); symmetric form
@@ -1645,8 +1711,10 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
 int fsi_batch_destroy(fsi_batch* b) {
     if (!b) return FSI_OK;
     cudaDeviceSynchronize();
-    Buf* bufs[] = {&b->items[1], &b->items[2], &b->items[kBatchSymI], &b->nblocks[1], &b->nblocks[2],
-                   &b->nblocks[kBatchSymI], &b->sitems, &b->nsum, &b->accum, &b->rec0, &b->rec1,
+    Buf* bufs[] = {&b->items[1], &b->items[2], &b->items[kBatchSymI], &b->items[kBatchSymI2],
+                   &b->nblocks[1], &b->nblocks[2], &b->nblocks[kBatchSymI], &b->nblocks[kBatchSymI2],
+                   &b->sitems[kBatchSymI], &b->sitems[kBatchSymI2], &b->nsum[kBatchSymI],
+                   &b->nsum[kBatchSymI2], &b->accum, &b->rec0, &b->rec1,
                    &b->accrec, &b->ac, &b->done, &b->ctrl, &b->stats};
     for (Buf* x : bufs)
         if (x->p) cudaFree(x->p);
@@ -1656,12 +1724,13 @@ int fsi_batch_destroy(fsi_batch* b) {
 
 int fsi_batch_set_tuning(fsi_ctx* c, fsi_batch* b, int ipt, int ctas_per_sm) {
     if (!c || !b) return fail(FSI_ERR_ARG, "NULL argument");
-    if (ipt != 1 && ipt != 2 && ipt != kBatchSymI)
-        return fail(FSI_ERR_ARG, "batch variant must be 1, 2 (one-sided) or %d (symmetric)", kBatchSymI);
-    if (ipt == kBatchSymI && c->p.precision != FSI_MIXED)
+    if (ipt != 1 && ipt != 2 && !batch_sym_ipt(ipt))
+        return fail(FSI_ERR_ARG, "batch variant must be 1, 2 (one-sided), %d or %d (symmetric)",
+                    kBatchSymI, kBatchSymI2);
+    if (batch_sym_ipt(ipt) && c->p.precision != FSI_MIXED)
         return fail(FSI_ERR_ARG, "the symmetric batch form is mixed precision");
-    const int mx = std::max(1, ipt == kBatchSymI ? batch_sym_max_ctas_per_sm()
-                                                 : batch_max_ctas_per_sm(c->p.precision, ipt));
+    const int mx = std::max(1, batch_sym_ipt(ipt) ? batch_sym_max_ctas_per_sm(ipt)
+                                                  : batch_max_ctas_per_sm(c->p.precision, ipt));
     if (ctas_per_sm <= 0 || ctas_per_sm > mx) ctas_per_sm = mx;
     b->ipt = ipt;
     b->ctas_per_sm = ctas_per_sm;
@@ -1704,7 +1773,7 @@ int fsi_batch_step(fsi_ctx* c, fsi_batch* b, double* pos, double* vel, const dou
     if (c->p.c > 0.0) return fail(FSI_ERR_UNSUPPORTED, "batched steps are Newtonian (PN off)");
     const cudaStream_t s = S(stream);
     const int ipt = b->ipt;
-    const bool sym = ipt == kBatchSymI;
+    const bool sym = batch_sym_ipt(ipt);
     if (sym && c->p.precision != FSI_MIXED) return fail(FSI_ERR_ARG, "the symmetric batch form is mixed precision");
     const int nphase = sym ? 3 + 6 * nsteps : 2 + 3 * nsteps;
     CU(cudaMemsetAsync(b->done.p, 0, (size_t)b->K * nphase * sizeof(int), s));
@@ -1742,8 +1811,8 @@ int fsi_batch_step(fsi_ctx* c, fsi_batch* b, double* pos, double* vel, const dou
     b->last_ctas = ctas;
     if (sym) {
         CU(cudaMemsetAsync(b->accum.p, 0, 3 * (size_t)b->ntot * sizeof(double), s));
-        CU(launch_batch_sym(ctas, a, reinterpret_cast<const BatchSymItem*>(b->sitems.p),
-                            b->sitems_per_phase, P<int>(b->nsum), P<double>(b->accum), s));
+        CU(launch_batch_sym(ipt, ctas, a, reinterpret_cast<const BatchSymItem*>(b->sitems[ipt].p),
+                            b->sitems_per_phase[ipt], P<int>(b->nsum[ipt]), P<double>(b->accum), s));
     } else {
         CU(launch_batch(c->p.precision, ipt, ctas, a, s));
     }

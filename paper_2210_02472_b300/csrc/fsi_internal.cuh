@@ -69,6 +69,8 @@ struct PairArgs {
     const int* iid; const int* jid;       // global ids (CHECK_IDS); jid padded to 4
     int n_i, n_j;
     int check;                            // Check
+    int i_off;                            // CHECK_DIAG: receiver k is source k + i_off (the
+                                          // receivers a sub-range of the source list)
     int j_per_split;                      // sources per blockIdx.y slice
     double eps2;
     double* part;                         // split > 1: partial sums [split][3][n_i]
@@ -323,6 +325,13 @@ cudaError_t launch_pn_cross(long long N, const double* pos, const double* vel, c
                             const unsigned char* is_bh, double c, const int* A, int nA, const int* B,
                             int nB, int* Abh, int* nAbh, int* Bbh, int* nBbh, double* outA,
                             double* outB, double* part, int* err, cudaStream_t s);
+// PN1.0 accelerations of id list A from id list B (any overlap, self pairs skipped by id)
+// through black-hole sublists (at most kMaxBHList black holes per list); workspace as
+// launch_pn_cross; out (3 x nA) overwritten.
+cudaError_t launch_pn_lists(long long N, const double* pos, const double* vel, const double* mass,
+                            const unsigned char* is_bh, double c, const int* A, int nA, const int* B,
+                            int nB, int* Abh, int* nAbh, int* Bbh, int* nBbh, double* out,
+                            double* part, int* err, cudaStream_t s);
 cudaError_t launch_pn_pairs(int N, const double* pos, const double* vel, const double* mass,
                             const unsigned char* is_bh, double c, const int* A, int nA,
                             const int* B, int nB, double* out, int* err, cudaStream_t s);
@@ -348,9 +357,14 @@ size_t steps_x2_part_bytes(int n, int sm_count);
 // steps_sym_min_n() particles; work: steps_sym_work_bytes(n) bytes (8-byte aligned).
 size_t steps_sym_work_bytes(int n);
 int steps_sym_min_n();
+// rel, sub (nullable): far-tile offset records and sub-tile (centre, radius) records of the
+// set (launch_subtiles); a warp takes the far-tile separation for a sub-tile whose gap to
+// its receivers' box is at least sqrt(far_k2) R.
 cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                              double eta_fb, double eta_jerk, void* work, double* step, int* err,
-                             long long timeout_ns, int sm_count, cudaStream_t s);
+                             long long timeout_ns, int sm_count, cudaStream_t s,
+                             const void* rel = nullptr, const void* sub = nullptr,
+                             float far_k2 = 0.f);
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                             double eta_fb, double eta_jerk, float* part, double* step, int* err,
                             long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s);
@@ -363,11 +377,14 @@ cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, c
 // Symmetric persistent ensemble kernel (mixed precision): phases pack, then per pair pass
 // a sum phase (sitems, red.add into accum) and an apply phase (items: epilogue, accum
 // cleared).  nsum: sum items per cluster.
-cudaError_t launch_batch_sym(int ctas, const BatchArgs& a, const BatchSymItem* sitems,
+// ipt: particles per thread, kBatchSymI (2 CTAs per SM) or kBatchSymI2 (1 CTA per SM).
+cudaError_t launch_batch_sym(int ipt, int ctas, const BatchArgs& a, const BatchSymItem* sitems,
                              int sitems_per_phase, const int* nsum, double* accum,
                              cudaStream_t s);
 constexpr int kBatchSymI = 4;      // particles per thread of the symmetric ensemble kernel
-int batch_sym_max_ctas_per_sm();
+constexpr int kBatchSymI2 = 8;     // its larger-block variant
+inline bool batch_sym_ipt(int ipt) { return ipt == kBatchSymI || ipt == kBatchSymI2; }
+int batch_sym_max_ctas_per_sm(int ipt);
 int batch_block_size(int ipt);
 int batch_max_ctas_per_sm(int precision, int ipt);
 // Adjoint pair kernels (FP64): kind 0 = acceleration VJP (vec = cotangent u),

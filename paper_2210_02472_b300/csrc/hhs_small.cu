@@ -350,7 +350,7 @@ __device__ void small_timesteps(SmallSmem<P>& S, const unsigned short* L, int n,
         acc.jy += __shfl_xor_sync(0xffffffffu, acc.jy, o);
         acc.jz += __shfl_xor_sync(0xffffffffu, acc.jz, o);
     }
-    if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
+    if (coincident) set_error(a.err, FSI_ERR_COINCIDENT);
     if constexpr (P == FSI_MIXED) {
         // the group leaders park their FP32 sums in the pass-sum storage (free until the
         // next pass), then thread t finishes receiver t: the FP64 finish runs on n / 32 full

@@ -13,6 +13,11 @@
 // byte it later reads (records are packed, partial sums are written, not accumulated), so
 // nothing needs to start at zero.  Two calls that overlap on the GPU (different streams,
 // no ordering between them) race on the array.
+//
+// There is no error word either: a bounded wait of the pair kernel that runs out (a
+// bulk copy that never lands) makes that CTA write quiet NaN into its results, and a
+// non-finite result stays in the output, so every device-side failure shows up as a
+// non-finite entry of acc_out.
 #include <mutex>
 
 #include "fsi_internal.cuh"
@@ -33,9 +38,11 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kRecBytes + kPa
 constexpr int kMaxDevices = 64;
 std::mutex g_mu;
 void* g_scratch_ptr[kMaxDevices] = {};
+int g_sm_count[kMaxDevices] = {};
 
-// Device address of the scratch array on the current device (looked up once per device).
-int scratch_address(void** out) {
+// Device address of the scratch array on the current device and that device's SM count
+// (both looked up once per device, under one lock).
+int scratch_address(void** out, int* sms) {
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
         cudaGetLastError();
@@ -49,9 +56,17 @@ int scratch_address(void** out) {
             cudaGetLastError();
             return fsi::set_last_error(FSI_ERR_CUDA, "fsi_accel_noalloc: cudaGetSymbolAddress failed");
         }
+        int n_sm = 0;
+        if (cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+            n_sm <= 0) {
+            cudaGetLastError();
+            return fsi::set_last_error(FSI_ERR_CUDA, "fsi_accel_noalloc: SM count query failed");
+        }
+        g_sm_count[dev] = n_sm;
         g_scratch_ptr[dev] = p;
     }
     *out = g_scratch_ptr[dev];
+    *sms = g_sm_count[dev];
     return FSI_OK;
 }
 
@@ -67,17 +82,18 @@ extern "C" int fsi_accel_noalloc(int N, const double* pos, const double* mass, d
                               "fsi_accel_noalloc: N exceeds the fixed scratch capacity of 32768 "
                               "particles; use fsi_accel with a context");
     void* scratch = nullptr;
-    const int rc = scratch_address(&scratch);
+    int sms = 0;
+    const int rc = scratch_address(&scratch, &sms);
     if (rc != FSI_OK) return rc;
     const cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
     unsigned char* base = reinterpret_cast<unsigned char*>(scratch);
     if (launch_pack(FSI_FP64, N, pos, mass, nullptr, N, base, nullptr, s) != cudaSuccess)
         return set_last_error(FSI_ERR_CUDA, "fsi_accel_noalloc: record packing failed to launch");
-    // source slices: enough CTAs for the GPU when N is small, at least 4 tiles per slice
+    // source slices: enough CTAs for two per SM when N is small, at least 4 tiles per slice
     const int ipt = 2;
     const int ctas = (N + kThreads * ipt - 1) / (kThreads * ipt);
     int split = 1;
-    while (split < kSplitMax && ctas * split < 296 && N / (split + 1) >= 4 * kTileJ) ++split;
+    while (split < kSplitMax && ctas * split < 2 * sms && N / (split + 1) >= 4 * kTileJ) ++split;
     int jps = (N + split - 1) / split;
     jps = (jps + kTileJ - 1) / kTileJ * kTileJ;
     split = (N + jps - 1) / jps;

@@ -11,7 +11,7 @@
 //  MIXED : pair differences from FP32 hi/lo position splits (FP32-accurate relative to
 //          the separation), FP32 pair arithmetic with one first-order residual
 //          correction of the hardware rsqrt folded into r^-3 (and r^-5), FP32 partial
-//          sums over one source tile, accumulated across tiles in FP64.
+//          sums over runs of 32 sources, accumulated as float-float pairs (TwoSum).
 //
 // Work decomposition (B300: 148 SMs, 227 KB shared memory per CTA):
 //  - a CTA of 256 threads owns 256*I consecutive active particles, I per thread held in
@@ -46,12 +46,43 @@ __device__ __forceinline__ double record_mass(const void* rec, int i) {
 }
 
 // ---------------------------------------------------------------------------------
-// Epilogue shared by the pair kernel (split == 1) and the finalize kernel.
+// Error path of a pass result that is not finite.  Without softening, two distinct
+// particles at the same position (a zero separation in the pass's records) make their pair
+// term 0 x inf; that case is reported as FSI_ERR_COINCIDENT, every other one (FP32
+// overflow of r^-3 in the mixed precision, a non-finite input) as FSI_ERR_NONFINITE.  Only
+// the receiver that claims the empty error word scans the pass's sources for a coincident
+// partner (the first error of a launch wins), so a launch pays one O(n_j) scan on this
+// path and nothing while its results are finite.  Self pairs are recognised as the pass
+// excludes them: by index (same list), by global id or key (id lists), never (disjoint).
 template <int P>
-// m_rec: the particle's mass as its position record carries it (used when e.mc is null).
-__device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, double ry,
-                                         double rz, double m_rec, int* err) {
-    if (!(isfinite(rx) && isfinite(ry) && isfinite(rz))) set_error(err, FSI_ERR_NONFINITE);
+__device__ __noinline__ void report_nonfinite(const PairArgs& a, int i) {
+    if (!a.err || atomicCAS(a.err, 0, FSI_ERR_NONFINITE) != 0) return;
+    if (a.eps2 != 0.0 || !a.irec || !a.jrec) return;
+    bool hit = false;
+    for (int j = 0; j < a.n_j && !hit; ++j) {
+        if (a.check == CHECK_DIAG && j == i + a.i_off) continue;
+        if (a.check == CHECK_IDS && a.jid[j] == a.iid[i]) continue;
+        if constexpr (P == FSI_MIXED) {
+            const RecMix ri = reinterpret_cast<const RecMix*>(a.irec)[i];
+            const RecMix rj = reinterpret_cast<const RecMix*>(a.jrec)[j];
+            hit = rj.hi.x == ri.hi.x && rj.hi.y == ri.hi.y && rj.hi.z == ri.hi.z &&
+                  rj.lo.x == ri.lo.x && rj.lo.y == ri.lo.y && rj.lo.z == ri.lo.z;
+        } else {
+            const D4 ri = reinterpret_cast<const D4*>(a.irec)[i];
+            const D4 rj = reinterpret_cast<const D4*>(a.jrec)[j];
+            hit = rj.x == ri.x && rj.y == ri.y && rj.z == ri.z;
+        }
+    }
+    if (hit) atomicCAS(a.err, FSI_ERR_NONFINITE, FSI_ERR_COINCIDENT);
+}
+
+// Epilogue shared by the pair kernel (split == 1), the wide kernel and the finalize
+// kernel, for receiver i of the pass a with pair sums (rx, ry, rz).
+template <int P>
+__device__ __forceinline__ void epilogue(const PairArgs& a, int i, double rx, double ry, double rz) {
+    const Epi& e = a.epi;
+    const int n = a.n_i;
+    if (!(isfinite(rx) && isfinite(ry) && isfinite(rz))) report_nonfinite<P>(a, i);
     if (e.out) {
         e.out[i] = rx;
         e.out[(size_t)n + i] = ry;
@@ -61,7 +92,7 @@ __device__ __forceinline__ void epilogue(const Epi& e, int i, int n, double rx, 
     const size_t gi = e.ids ? (size_t)e.ids[i] : (size_t)i;
     const size_t L = e.ids ? (size_t)e.ld : (size_t)n;
     if (e.accrec) {   // accel record (ax, ay, az, m): the mass feeds the symmetric gradient
-        const double m = e.mc ? e.mc[gi] : m_rec;
+        const double m = e.mc ? e.mc[gi] : record_mass<P>(a.irec, i);
         if (P == FSI_MIXED)
             reinterpret_cast<float4*>(e.accrec)[i] = make_float4((float)rx, (float)ry, (float)rz, (float)m);
         else
@@ -105,12 +136,22 @@ struct Cfg {
 
 constexpr int kRec = 32;
 
+// The FP32 partial sums of a receiver in the mixed pair kernels (one-sided, wide, packed
+// symmetric and bipartite forms) run over at most kSymFlushJ sources before they are added
+// into a float-float accumulator (TwoSum).  A linear FP32 sum of k terms carries up to
+// ~sqrt(k) roundings of its running value, so runs of 256 sources left the sum, not the
+// pair terms, as the largest part of the acceleration error (median 4e-8, 99th percentile
+// 3e-7 of |a| at N = 65536); runs of 32 bring it down to about the pair terms' own
+// rounding (median 2.2e-8, 99th percentile 1.4e-7).
+constexpr int kSymFlushJ = 32;
+
 __host__ __device__ constexpr int stage_bytes(int accrec) { return kTileJ * (kRec + accrec + 4); }
 
-// P: precision; KIND: acc or grad; I: active particles per thread; FF (mixed only): 1 = the
-// per-tile FP32 partial sums are accumulated as float-float pairs by TwoSum (FP32 pipe)
-// instead of FP64 additions (FP64 pipe, 1/64 of the FP32 rate on B300); 2 = the tiles
-// without the self pair run packed FP32x2 arithmetic on pairs of active particles (I even).
+// P: precision; KIND: acc or grad; I: active particles per thread; FF (mixed only): 0 and 1
+// = scalar FP32 pair arithmetic (identical since both carry float-float sums over runs of
+// kSymFlushJ sources; 1 is kept as a tuning-table entry); 2 = the tiles without the self
+// pair run packed FP32x2 arithmetic on pairs of active particles (I even).  No FP64
+// instruction in the loop (the B300 FP64 pipe runs at ~1/64 of the FP32 rate).
 template <int P, int KIND, int I, int FF>
 __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const PairArgs a) {
     constexpr int ACCREC = Cfg<P, KIND>::ACCREC;
@@ -155,7 +196,7 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
     for (int u = 0; u < I; ++u) {
         acc64[u][0] = acc64[u][1] = acc64[u][2] = 0.0;
         const int i = min(i0 + u * kThreads + tid, max(a.n_i - 1, 0));
-        my_id[u] = use_ids ? a.iid[i] : (i0 + u * kThreads + tid);
+        my_id[u] = use_ids ? a.iid[i] : (i0 + a.i_off + u * kThreads + tid);
     }
 
     bool aborted = false;
@@ -194,6 +235,31 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
         for (int p = 0; p < NP; ++p) f2[p][0] = f2[p][1] = f2[p][2] = make_float2(0.f, 0.f);
         const float2 eps2x = bc2((float)a.eps2);
         const float eps2f = (float)a.eps2;
+        // every kSymFlushJ sources: the FP32 partials (packed halves first) go into the
+        // float-float running sums by Knuth's TwoSum (hi + f = sum + e exactly)
+        auto flush = [&]() {
+            if constexpr (FF == 2) {
+#pragma unroll
+                for (int p = 0; p < NP; ++p)
+#pragma unroll
+                    for (int q = 0; q < 3; ++q) {
+                        f[2 * p][q] += f2[p][q].x;
+                        f[2 * p + 1][q] += f2[p][q].y;
+                        f2[p][q] = make_float2(0.f, 0.f);
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < I; ++u)
+#pragma unroll
+                for (int q = 0; q < 3; ++q) {
+                    const float sum = hi[u][q] + f[u][q];
+                    const float bb = sum - hi[u][q];
+                    const float e = (hi[u][q] - (sum - bb)) + (f[u][q] - bb);
+                    hi[u][q] = sum;
+                    lo[u][q] += e;
+                    f[u][q] = 0.f;
+                }
+        };
         for (int t = 0; t < ntiles; ++t) {
             const int s = t % kStages;
             const bool ok = mbar_wait_bounded(&bars[s], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
@@ -203,7 +269,7 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
             const RecMix* rec = reinterpret_cast<const RecMix*>(base);
             const float4* arec = reinterpret_cast<const float4*>(base + kTileJ * kRec);
             const int* jidt = reinterpret_cast<const int*>(base + kTileJ * (kRec + ACCREC));
-            const bool chk = use_ids || (a.check == CHECK_DIAG && jt < i0 + kThreads * I && jt + cnt > i0);
+            const bool chk = use_ids || (a.check == CHECK_DIAG && jt < i0 + a.i_off + kThreads * I && jt + cnt > i0 + a.i_off);
             if (FF == 2 && !chk) {
                 for (int jj = 0; jj < cnt; ++jj) {
                     if constexpr (KIND == KIND_ACC) {
@@ -214,6 +280,7 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
 #pragma unroll
                         for (int p = 0; p < NP; ++p) x2_grad_one(rec[jj].hi, rec[jj].lo, aj, pp[p], eps2x, f2[p]);
                     }
+                    if (((jj + 1) & (kSymFlushJ - 1)) == 0 || jj == cnt - 1) flush();
                 }
             } else if (!chk) {
 #pragma unroll 2
@@ -230,6 +297,7 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
                         for (int u = 0; u < I; ++u)
                             mix_grad_pair<false>(h, l, aj, pi[u], eps2f, false, f[u][0], f[u][1], f[u][2]);
                     }
+                    if (((jj + 1) & (kSymFlushJ - 1)) == 0 || jj == cnt - 1) flush();
                 }
             } else {
                 for (int jj = 0; jj < cnt; ++jj) {
@@ -246,44 +314,16 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
                         for (int u = 0; u < I; ++u)
                             mix_grad_pair<true>(h, l, aj, pi[u], eps2f, jid == my_id[u], f[u][0], f[u][1], f[u][2]);
                     }
-                }
-            }
-            if constexpr (FF == 2) {
-#pragma unroll
-                for (int p = 0; p < NP; ++p)
-#pragma unroll
-                    for (int q = 0; q < 3; ++q) {
-                        f[2 * p][q] += f2[p][q].x;
-                        f[2 * p + 1][q] += f2[p][q].y;
-                        f2[p][q] = make_float2(0.f, 0.f);
-                    }
-            }
-#pragma unroll
-            for (int u = 0; u < I; ++u) {
-#pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    if constexpr (FF == 1) {
-                        // error-free transformation (Knuth's TwoSum): hi + f = s + e exactly
-                        const float sum = hi[u][q] + f[u][q];
-                        const float bb = sum - hi[u][q];
-                        const float e = (hi[u][q] - (sum - bb)) + (f[u][q] - bb);
-                        hi[u][q] = sum;
-                        lo[u][q] += e;
-                    } else {
-                        acc64[u][q] += (double)f[u][q];
-                    }
-                    f[u][q] = 0.f;
+                    if (((jj + 1) & (kSymFlushJ - 1)) == 0 || jj == cnt - 1) flush();
                 }
             }
             if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
             if (tid == 0 && t + kStages < ntiles) issue(t + kStages);
         }
-        if constexpr (FF == 1) {
 #pragma unroll
-            for (int u = 0; u < I; ++u)
+        for (int u = 0; u < I; ++u)
 #pragma unroll
-                for (int q = 0; q < 3; ++q) acc64[u][q] = (double)hi[u][q] + (double)lo[u][q];
-        }
+            for (int q = 0; q < 3; ++q) acc64[u][q] = (double)hi[u][q] + (double)lo[u][q];
     } else {
         F64I pi[I];
 #pragma unroll
@@ -307,7 +347,7 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
             const D4* rec = reinterpret_cast<const D4*>(base);
             const D4* arec = reinterpret_cast<const D4*>(base + kTileJ * kRec);
             const int* jidt = reinterpret_cast<const int*>(base + kTileJ * (kRec + ACCREC));
-            const bool chk = use_ids || (a.check == CHECK_DIAG && jt < i0 + kThreads * I && jt + cnt > i0);
+            const bool chk = use_ids || (a.check == CHECK_DIAG && jt < i0 + a.i_off + kThreads * I && jt + cnt > i0 + a.i_off);
             if (!chk) {
 #pragma unroll 2
                 for (int jj = 0; jj < cnt; ++jj) {
@@ -354,6 +394,22 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
                                   a.timeout_ns, nullptr);
         }
         __syncthreads();
+        if (!a.err) {
+            // no error word to latch (allocation-free entry point): the CTA's results
+            // become quiet NaN, so the abort shows in the outputs (through the finalize
+            // sum when the sources are split)
+            const double qnan = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+            for (int u = 0; u < I; ++u) {
+                const int i = i0 + u * kThreads + tid;
+                if (i >= a.n_i) continue;
+                double* o = gridDim.y > 1 ? a.part + (size_t)blockIdx.y * 3 * a.n_i : a.epi.out;
+                if (!o) continue;
+                o[i] = qnan;
+                o[(size_t)a.n_i + i] = qnan;
+                o[2 * (size_t)a.n_i + i] = qnan;
+            }
+        }
         return;
     }
 
@@ -367,8 +423,7 @@ __global__ void __launch_bounds__(kThreads, (I <= 2 ? 3 : 2)) pair_kernel(const 
             p[(size_t)a.n_i + i] = acc64[u][1];
             p[2 * (size_t)a.n_i + i] = acc64[u][2];
         } else {
-            epilogue<P>(a.epi, i, a.n_i, acc64[u][0], acc64[u][1], acc64[u][2],
-                        record_mass<P>(a.irec, i), a.err);
+            epilogue<P>(a, i, acc64[u][0], acc64[u][1], acc64[u][2]);
         }
     }
 }
@@ -385,7 +440,7 @@ __global__ void finalize_kernel(const PairArgs a, int split) {
         r[1] += p[(size_t)a.n_i + i];
         r[2] += p[2 * (size_t)a.n_i + i];
     }
-    epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], record_mass<P>(a.irec, i), a.err);
+    epilogue<P>(a, i, r[0], r[1], r[2]);
 }
 
 // =================================================================================
@@ -394,7 +449,7 @@ __global__ void finalize_kernel(const PairArgs a, int split) {
 // so a group never straddles a warp) share one receiver and stride over its sources;
 // blockIdx.y splits the source range as in the tiled form.  The set is small, so source
 // records are read through L1 without staging.  Mixed: FP32 partial sums over runs of
-// 256 sources per lane, float-float (TwoSum) across runs and lanes, no FP64 instruction
+// kSymFlushJ sources per lane, float-float (TwoSum) across runs and lanes, no FP64 instruction
 // before the epilogue; FP64: FP64 throughout.  DIAG: same list on both sides, the self
 // pair excluded by index.
 // One CTA of a wide pass: receiver block bx, source slice by of ny.
@@ -428,10 +483,10 @@ __device__ __forceinline__ void wide_pair_body(const PairArgs& a, int lg, int bx
             for (int j = js + g; j < je; j += G) {
                 const RecMix rj = J[j];
                 if constexpr (KIND == KIND_ACC)
-                    mix_acc_pair<DIAG>(rj.hi, rj.lo, p, eps2f, j == i, f[0], f[1], f[2]);
+                    mix_acc_pair<DIAG>(rj.hi, rj.lo, p, eps2f, j == i + a.i_off, f[0], f[1], f[2]);
                 else
-                    mix_grad_pair<DIAG>(rj.hi, rj.lo, JA[j], p, eps2f, j == i, f[0], f[1], f[2]);
-                if (++cnt == 256) {
+                    mix_grad_pair<DIAG>(rj.hi, rj.lo, JA[j], p, eps2f, j == i + a.i_off, f[0], f[1], f[2]);
+                if (++cnt == kSymFlushJ) {
 #pragma unroll
                     for (int c = 0; c < 3; ++c) { ff_acc(sh[c], sl[c], f[c]); f[c] = 0.f; }
                     cnt = 0;
@@ -467,9 +522,9 @@ __device__ __forceinline__ void wide_pair_body(const PairArgs& a, int lg, int bx
         if (active) {
             for (int j = js + g; j < je; j += G) {
                 if constexpr (KIND == KIND_ACC)
-                    f64_acc_pair<DIAG>(J[j], p, a.eps2, j == i, r[0], r[1], r[2]);
+                    f64_acc_pair<DIAG>(J[j], p, a.eps2, j == i + a.i_off, r[0], r[1], r[2]);
                 else
-                    f64_grad_pair<DIAG>(J[j], JA[j], p, a.eps2, j == i, r[0], r[1], r[2]);
+                    f64_grad_pair<DIAG>(J[j], JA[j], p, a.eps2, j == i + a.i_off, r[0], r[1], r[2]);
             }
         }
         for (int o = G >> 1; o > 0; o >>= 1)
@@ -478,7 +533,7 @@ __device__ __forceinline__ void wide_pair_body(const PairArgs& a, int lg, int bx
         if (!active || g != 0) return;
     }
     if (ny == 1) {
-        epilogue<P>(a.epi, i, a.n_i, r[0], r[1], r[2], record_mass<P>(a.irec, i), a.err);
+        epilogue<P>(a, i, r[0], r[1], r[2]);
     } else {
         double* part = a.part + (size_t)by * 3 * a.n_i;
         part[i] = r[0];
@@ -1396,12 +1451,16 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
                     for (int u = 0; u < I; ++u)
                         mix_grad_pair<true>(h, l, aj, q[u], eps2f, jt + jj == ib + 32 * u, fs[u][0], fs[u][1], fs[u][2]);
                 }
+                if ((jj & (kSymFlushJ - 1)) == kSymFlushJ - 1 || jj == cnt - 1) {
+#pragma unroll
+                    for (int p = 0; p < NP; ++p)
+#pragma unroll
+                        for (int q = 0; q < 3; ++q) {
+                            ff_add2(acc_s[(p * 3 + q) * kThreads + tid], make_float2(fs[2 * p][q], fs[2 * p + 1][q]));
+                            fs[2 * p][q] = fs[2 * p + 1][q] = 0.f;
+                        }
+                }
             }
-#pragma unroll
-            for (int p = 0; p < NP; ++p)
-#pragma unroll
-                for (int q = 0; q < 3; ++q)
-                    ff_add2(acc_s[(p * 3 + q) * kThreads + tid], make_float2(fs[2 * p][q], fs[2 * p + 1][q]));
         } else {
             unsigned fmask = 0;
             if (far_on) {
@@ -1442,14 +1501,16 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
                         x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D0, eps2, f, jpart);
                     ++near_visits;
                 }
-            }
+                if (jend == cnt || (jend % kSymFlushJ) == 0) {
 #pragma unroll
-            for (int p = 0; p < NP; ++p)
+                    for (int p = 0; p < NP; ++p)
 #pragma unroll
-                for (int q = 0; q < 3; ++q) {
-                    ff_add2(acc_s[(p * 3 + q) * kThreads + tid], f[p][q]);
-                    f[p][q] = make_float2(0.f, 0.f);
+                        for (int q = 0; q < 3; ++q) {
+                            ff_add2(acc_s[(p * 3 + q) * kThreads + tid], f[p][q]);
+                            f[p][q] = make_float2(0.f, 0.f);
+                        }
                 }
+            }
         }
         if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
         if (!diag && tid < cnt) {
@@ -1675,14 +1736,16 @@ __global__ void __launch_bounds__(kThreads, MINB) cross_mixed_x2_kernel(const Cr
                 for (int jj = k0; jj < jend; jj += 4)
                     x2_group<KIND, NP, false, true>(jj, cnt, lane, warp, rec, arec, rel_s, pp, D0, eps2, f, jpart);
             }
-        }
+            if (jend == cnt || (jend % kSymFlushJ) == 0) {
 #pragma unroll
-        for (int p = 0; p < NP; ++p)
+                for (int p = 0; p < NP; ++p)
 #pragma unroll
-            for (int q = 0; q < 3; ++q) {
-                ff_add2(acc_s[(p * 3 + q) * kThreads + tid], f[p][q]);
-                f[p][q] = make_float2(0.f, 0.f);
+                    for (int q = 0; q < 3; ++q) {
+                        ff_add2(acc_s[(p * 3 + q) * kThreads + tid], f[p][q]);
+                        f[p][q] = make_float2(0.f, 0.f);
+                    }
             }
+        }
         if (__syncthreads_or(!ok)) { aborted = true; t_stop = t; break; }
         if (tid < cnt) {
 #pragma unroll

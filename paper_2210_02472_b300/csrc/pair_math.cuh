@@ -317,7 +317,7 @@ __device__ __forceinline__ void pn_pair(double xi, double yi, double zi, double 
                                         double& ax, double& ay, double& az, int* err) {
     const double rx = xi - xj, ry = yi - yj, rz = zi - zj;
     const double r2 = rx * rx + ry * ry + rz * rz;
-    if (r2 == 0.0) { set_error(err, FSI_ERR_NONFINITE); return; }
+    if (r2 == 0.0) { set_error(err, FSI_ERR_COINCIDENT); return; }
     const double ir = 1.0 / sqrt(r2);
     const double nx = rx * ir, ny = ry * ir, nz = rz * ir;
     const double vi2 = vxi * vxi + vyi * vyi + vzi * vzi;

@@ -210,7 +210,7 @@ __global__ void __launch_bounds__(kStThreads, 2) steps_x2_kernel(const StepX2Arg
     for (int u = 0; u < kStI; ++u) {
         const int i = i0 + u * kStThreads + tid;
         if (i >= a.n) continue;
-        if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
+        if (coincident) set_error(a.err, FSI_ERR_COINCIDENT);
         const StepX2Acc& s = acc[u >> 1];
         const bool hi = (u & 1) != 0;
         const float v[kStPart] = {hi ? s.ff.y : s.ff.x, hi ? s.fb.y : s.fb.x, hi ? s.ax.y : s.ax.x,
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(kStThreads) steps_wide_kernel(const StepX2Args
             jz = fmaf(w, fmaf(c3, dz, uz), jz);
         }
     }
-    if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
+    if (coincident) set_error(a.err, FSI_ERR_COINCIDENT);
     for (int o = G >> 1; o > 0; o >>= 1) {
         ff = fminf(ff, __shfl_xor_sync(0xffffffffu, ff, o));
         fb = fminf(fb, __shfl_xor_sync(0xffffffffu, fb, o));
@@ -326,7 +326,10 @@ namespace {
 constexpr int kSsBlock = kStThreads * kStI;                       // receivers per block
 constexpr int kSsQ = 8;                                           // ff, fb, ax..az, jx..jz
 constexpr int kSsJpart = (kStThreads / 32) * kStTile * kSsQ * 4;   // per-warp source rows
-constexpr int kSsSmem = kStages * kStStage + kSsJpart;
+// stage: position records (32 B), velocity records (16 B), far-tile offset records (16 B)
+// and the tile's 8 sub-tile (centre, radius) records
+constexpr int kSsStage = kStTile * (32 + 16 + 16) + (kStTile / 32) * 16;
+constexpr int kSsSmem = kStages * kSsStage + kSsJpart;
 }  // namespace
 
 struct StepSymArgs {
@@ -339,26 +342,31 @@ struct StepSymArgs {
     double* sums;           // 6 x n: a and j sums (0 to start)
     int* err;
     long long timeout_ns;
+    // far-tile path (null rel: never taken): the set's records relative to the centres C of
+    // their 32-record sub-tiles and the sub-tiles' (C, R), as for the acceleration kernels;
+    // a warp takes d = (C - x_i) + (x_j - C) for a sub-tile whose gap to the warp's box is
+    // at least sqrt(far_k2) R
+    const float4* rel;
+    const float4* sub;
+    float far_k2;
 };
 
-// Source j on both receivers of a packed pair (all receivers valid, j none of them):
-// receiver side into s, source side into pj (a_j, j_j per half) and the running minima.
+// Source j on both receivers of a packed pair (all receivers valid, j none of them), with
+// the separation d = x_j - x_i given: receiver side into s, source side into pj (a_j, j_j
+// per half) and the running minima.  The hardware reciprocal square root is used as it is
+// (relative error below 2^-22): a time step needs far less.
 template <bool SOFT>
-__device__ __forceinline__ void step_pair_sym(const float4 h, const float4 l, const float4 vj,
-                                              const StepX2I& p, float2 nmi, float2 eps2,
-                                              StepX2Acc& s, float2 (&pj)[6], float& jff, float& jfb,
-                                              bool& coincident) {
-    const float2 dx = __fadd2_rn(__fadd2_rn(bc2(h.x), p.nxh), __fadd2_rn(bc2(l.x), p.nxl));
-    const float2 dy = __fadd2_rn(__fadd2_rn(bc2(h.y), p.nyh), __fadd2_rn(bc2(l.y), p.nyl));
-    const float2 dz = __fadd2_rn(__fadd2_rn(bc2(h.z), p.nzh), __fadd2_rn(bc2(l.z), p.nzl));
+__device__ __forceinline__ void step_pair_sym(const float2 dx, const float2 dy, const float2 dz,
+                                              const float4 vj, const StepX2I& p, float2 nmi,
+                                              float2 eps2, StepX2Acc& s, float2 (&pj)[6],
+                                              float& jff, float& jfb, bool& coincident) {
     const float2 d2 = __ffma2_rn(dx, dx, __ffma2_rn(dy, dy, __fmul2_rn(dz, dz)));
     coincident |= (d2.x == 0.0f) | (d2.y == 0.0f);
     const float2 ux = __fadd2_rn(bc2(vj.x), p.nu), uy = __fadd2_rn(bc2(vj.y), p.nv),
                  uz = __fadd2_rn(bc2(vj.z), p.nw);
     const float2 u2 = __ffma2_rn(ux, ux, __ffma2_rn(uy, uy, __fmul2_rn(uz, uz)));
     const float2 s2 = SOFT ? __fadd2_rn(d2, eps2) : d2;
-    float2 y = rsqrt2(s2);
-    y = __fmul2_rn(y, __ffma2_rn(__fmul2_rn(s2, bc2(-0.5f)), __fmul2_rn(y, y), bc2(1.5f)));
+    const float2 y = rsqrt2(s2);
     const float2 y2 = __fmul2_rn(y, y);
     const float2 y3 = __fmul2_rn(y2, y);
     const float2 wi = __fmul2_rn(bc2(vj.w), y3);                       //  m_j / s^3
@@ -381,9 +389,12 @@ __device__ __forceinline__ void step_pair_sym(const float4 h, const float4 l, co
 
 // A group of 4 sources (lane l takes source jj + (g ^ (l >> 3)) at step g), then the
 // warp's source-side totals of the group into jpart (row per warp, 8 values per source).
-template <bool SOFT, bool FULL>
+// FG: far form, the separation from the sub-tile offsets D = (C - xh_i) - xl_i and the
+// source's offset record r = x_j - C (3 additions instead of 9).
+template <bool SOFT, bool FULL, bool FG>
 __device__ __forceinline__ void steps_sym_group(int jj, int cnt, int lane, int warp,
                                                 const RecMix* rec, const float4* vr,
+                                                const float4* rel_s, const float2 (&D)[kStNP][3],
                                                 const StepX2I (&pp)[kStNP], const float2 (&nmi)[kStNP],
                                                 float2 eps2, StepX2Acc (&acc)[kStNP], float* jpart,
                                                 bool& coincident) {
@@ -396,14 +407,29 @@ __device__ __forceinline__ void steps_sym_group(int jj, int cnt, int lane, int w
         for (int q = 2; q < kSsQ; ++q) fj[g][q] = 0.f;
         const int jg = jj + (g ^ L);
         if (FULL || jg < cnt) {
-            const float4 h = rec[jg].hi, l = rec[jg].lo, v = vr[jg];
+            const float4 v = vr[jg];
             float2 pj[6];
 #pragma unroll
             for (int q = 0; q < 6; ++q) pj[q] = make_float2(0.f, 0.f);
             float jff = INFINITY, jfb = INFINITY;
+            if constexpr (FG) {
+                const float4 r = rel_s[jg];
 #pragma unroll
-            for (int p = 0; p < kStNP; ++p)
-                step_pair_sym<SOFT>(h, l, v, pp[p], nmi[p], eps2, acc[p], pj, jff, jfb, coincident);
+                for (int p = 0; p < kStNP; ++p)
+                    step_pair_sym<SOFT>(__fadd2_rn(D[p][0], bc2(r.x)), __fadd2_rn(D[p][1], bc2(r.y)),
+                                        __fadd2_rn(D[p][2], bc2(r.z)), v, pp[p], nmi[p], eps2, acc[p],
+                                        pj, jff, jfb, coincident);
+            } else {
+                const float4 h = rec[jg].hi, l = rec[jg].lo;
+#pragma unroll
+                for (int p = 0; p < kStNP; ++p) {
+                    const StepX2I& q = pp[p];
+                    step_pair_sym<SOFT>(__fadd2_rn(__fadd2_rn(bc2(h.x), q.nxh), __fadd2_rn(bc2(l.x), q.nxl)),
+                                        __fadd2_rn(__fadd2_rn(bc2(h.y), q.nyh), __fadd2_rn(bc2(l.y), q.nyl)),
+                                        __fadd2_rn(__fadd2_rn(bc2(h.z), q.nzh), __fadd2_rn(bc2(l.z), q.nzl)),
+                                        v, q, nmi[p], eps2, acc[p], pj, jff, jfb, coincident);
+                }
+            }
             fj[g][0] = jff;
             fj[g][1] = jfb;
 #pragma unroll
@@ -450,7 +476,7 @@ template <bool SOFT>
 __global__ void __launch_bounds__(kStThreads, 1) steps_sym_kernel(const StepSymArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[kStages];
-    float* jpart = reinterpret_cast<float*>(smem + kStages * kStStage);
+    float* jpart = reinterpret_cast<float*>(smem + kStages * kSsStage);
     const int b = blockIdx.x / (1 + a.nchunk);
     const int c = blockIdx.x % (1 + a.nchunk);
     const int ntj = (a.n + kStTile - 1) / kStTile;
@@ -467,14 +493,20 @@ __global__ void __launch_bounds__(kStThreads, 1) steps_sym_kernel(const StepSymA
         fence_mbar_init();
     }
     __syncthreads();
+    const bool far_on = a.rel != nullptr && !diag;
     auto issue = [&](int t) {
         const int st = t % kStages;
         const int jt = (t0 + t) * kStTile;
         const int cnt = min(kStTile, a.n - jt);
-        unsigned char* base = smem + st * kStStage;
-        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * 48u);
+        const int nsub = (cnt + 31) >> 5;
+        unsigned char* base = smem + st * kSsStage;
+        mbar_arrive_expect_tx(&bars[st], (uint32_t)cnt * 48u + (far_on ? (uint32_t)(cnt * 16 + nsub * 16) : 0u));
         bulk_g2s(base, a.rec + jt, (uint32_t)cnt * 32u, &bars[st]);
         bulk_g2s(base + kStTile * 32, a.vrec + jt, (uint32_t)cnt * 16u, &bars[st]);
+        if (far_on) {
+            bulk_g2s(base + kStTile * 48, a.rel + jt, (uint32_t)cnt * 16u, &bars[st]);
+            bulk_g2s(base + kStTile * 64, a.sub + jt / 32, (uint32_t)nsub * 16u, &bars[st]);
+        }
     };
     if (tid == 0)
         for (int t = 0; t < min(kStages, ntiles); ++t) issue(t);
@@ -503,6 +535,32 @@ __global__ void __launch_bounds__(kStThreads, 1) steps_sym_kernel(const StepSymA
         acc[p].ff = acc[p].fb = bc2(INFINITY);
         acc[p].ax = acc[p].ay = acc[p].az = acc[p].jx = acc[p].jy = acc[p].jz = bc2(0.0f);
     }
+    // box of the warp's receivers (FP32 high parts), for the far-tile test
+    __shared__ float wbox[kStThreads / 32][6];
+    if (far_on) {
+        float bl[3] = {-pp[0].nxh.x, -pp[0].nyh.x, -pp[0].nzh.x};
+        float bh[3] = {bl[0], bl[1], bl[2]};
+#pragma unroll
+        for (int p = 0; p < kStNP; ++p) {
+            bl[0] = fminf(bl[0], -fmaxf(pp[p].nxh.x, pp[p].nxh.y));
+            bl[1] = fminf(bl[1], -fmaxf(pp[p].nyh.x, pp[p].nyh.y));
+            bl[2] = fminf(bl[2], -fmaxf(pp[p].nzh.x, pp[p].nzh.y));
+            bh[0] = fmaxf(bh[0], -fminf(pp[p].nxh.x, pp[p].nxh.y));
+            bh[1] = fmaxf(bh[1], -fminf(pp[p].nyh.x, pp[p].nyh.y));
+            bh[2] = fmaxf(bh[2], -fminf(pp[p].nzh.x, pp[p].nzh.y));
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) {
+                bl[q] = fminf(bl[q], __shfl_xor_sync(0xffffffffu, bl[q], o));
+                bh[q] = fmaxf(bh[q], __shfl_xor_sync(0xffffffffu, bh[q], o));
+            }
+        if (lane == 0)
+#pragma unroll
+            for (int q = 0; q < 3; ++q) { wbox[warp][q] = bl[q]; wbox[warp][3 + q] = bh[q]; }
+        __syncwarp();
+    }
     const float2 eps2 = bc2(a.eps2);
     bool coincident = false, aborted = false;
     int t_stop = ntiles;
@@ -511,9 +569,11 @@ __global__ void __launch_bounds__(kStThreads, 1) steps_sym_kernel(const StepSymA
         const bool ok = mbar_wait_bounded(&bars[st], (uint32_t)((t / kStages) & 1), a.timeout_ns, a.err);
         const int jt = (t0 + t) * kStTile;
         const int cnt = min(kStTile, a.n - jt);
-        const unsigned char* base = smem + st * kStStage;
+        const unsigned char* base = smem + st * kSsStage;
         const RecMix* rec = reinterpret_cast<const RecMix*>(base);
         const float4* vr = reinterpret_cast<const float4*>(base + kStTile * 32);
+        const float4* rel_s = reinterpret_cast<const float4*>(base + kStTile * 48);
+        const float4* sub_s = reinterpret_cast<const float4*>(base + kStTile * 64);
         if (diag) {
             for (int jj = 0; jj < cnt; ++jj) {
                 const float4 h = rec[jj].hi, l = rec[jj].lo, v = vr[jj];
@@ -524,15 +584,40 @@ __global__ void __launch_bounds__(kStThreads, 1) steps_sym_kernel(const StepSymA
                                              acc[p], coincident);
             }
         } else {
-            // blocks with tiles above them are full: every receiver is valid
+            // blocks with tiles above them are full: every receiver is valid.  Lanes 0..7
+            // test the tile's 8 sub-tiles against the warp's box (gap >= sqrt(far_k2) R)
+            unsigned fmask = 0;
+            if (far_on) {
+                bool fr = false;
+                if (lane < ((cnt + 31) >> 5)) {
+                    const float4 sb = sub_s[lane];
+                    const float* wb = wbox[warp];
+                    const float gx = fmaxf(0.f, fmaxf(wb[0] - sb.x, sb.x - wb[3]));
+                    const float gy = fmaxf(0.f, fmaxf(wb[1] - sb.y, sb.y - wb[4]));
+                    const float gz = fmaxf(0.f, fmaxf(wb[2] - sb.z, sb.z - wb[5]));
+                    fr = fmaf(gx, gx, fmaf(gy, gy, gz * gz)) >= a.far_k2 * (sb.w * sb.w);
+                }
+                fmask = __ballot_sync(0xffffffffu, fr);
+            }
+            float2 D[kStNP][3];
             for (int k0 = 0; k0 < cnt; k0 += 32) {
                 const int jend = min(cnt, k0 + 32);
                 if (jend - k0 < 32) {
                     for (int jj = k0; jj < jend; jj += 4)
-                        steps_sym_group<SOFT, false>(jj, cnt, lane, warp, rec, vr, pp, nmi, eps2, acc, jpart, coincident);
+                        steps_sym_group<SOFT, false, false>(jj, cnt, lane, warp, rec, vr, rel_s, D, pp, nmi, eps2, acc, jpart, coincident);
+                } else if ((fmask >> (k0 >> 5)) & 1u) {
+                    const float4 C = sub_s[k0 >> 5];
+#pragma unroll
+                    for (int p = 0; p < kStNP; ++p) {
+                        D[p][0] = __fadd2_rn(__fadd2_rn(bc2(C.x), pp[p].nxh), pp[p].nxl);
+                        D[p][1] = __fadd2_rn(__fadd2_rn(bc2(C.y), pp[p].nyh), pp[p].nyl);
+                        D[p][2] = __fadd2_rn(__fadd2_rn(bc2(C.z), pp[p].nzh), pp[p].nzl);
+                    }
+                    for (int jj = k0; jj < jend; jj += 4)
+                        steps_sym_group<SOFT, true, true>(jj, cnt, lane, warp, rec, vr, rel_s, D, pp, nmi, eps2, acc, jpart, coincident);
                 } else {
                     for (int jj = k0; jj < jend; jj += 4)
-                        steps_sym_group<SOFT, true>(jj, cnt, lane, warp, rec, vr, pp, nmi, eps2, acc, jpart, coincident);
+                        steps_sym_group<SOFT, true, false>(jj, cnt, lane, warp, rec, vr, rel_s, D, pp, nmi, eps2, acc, jpart, coincident);
                 }
             }
         }
@@ -561,7 +646,7 @@ __global__ void __launch_bounds__(kStThreads, 1) steps_sym_kernel(const StepSymA
         __syncthreads();
         return;
     }
-    if (coincident) set_error(a.err, FSI_ERR_NONFINITE);
+    if (coincident) set_error(a.err, FSI_ERR_COINCIDENT);
 #pragma unroll
     for (int u = 0; u < kStI; ++u) {
         const int i = ib + 32 * u;
@@ -601,7 +686,8 @@ int steps_sym_min_n() { return 4 * kSsBlock; }
 // work: steps_sym_work_bytes(n) bytes, 8-byte aligned.
 cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                              double eta_fb, double eta_jerk, void* work, double* step, int* err,
-                             long long timeout_ns, int sm_count, cudaStream_t s) {
+                             long long timeout_ns, int sm_count, cudaStream_t s, const void* rel,
+                             const void* sub, float far_k2) {
     if (n <= 0) return cudaSuccess;
     static bool attr[2] = {false, false};
     const bool soft = eps2 > 0.0;
@@ -620,6 +706,9 @@ cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double ep
     a.mins = reinterpret_cast<unsigned*>(a.sums + 6 * (size_t)n);
     a.err = err;
     a.timeout_ns = timeout_ns;
+    a.rel = reinterpret_cast<const float4*>(rel);
+    a.sub = reinterpret_cast<const float4*>(sub);
+    a.far_k2 = far_k2;
     const long long ntj = (n + kStTile - 1) / kStTile;
     const long long nb = (n + kSsBlock - 1) / kSsBlock;
     // about 8 items per resident CTA, at most 64 tiles each

@@ -76,12 +76,14 @@ __device__ __forceinline__ void x2_grad_far(const float4 r, const float4 aj, con
 
 // One group of 4 sources of the packed kernel (lane l visits source jj + (g ^ (l >> 3)) at
 // step g); FG selects the far form, FULL drops the bounds check (a full 32-record sub-tile).
-// The j-side totals of the group are left in jpart (one row per warp).
-template <int KIND, int NP, bool FG, bool FULL>
+// The j-side totals of the group are left in jpart (one row per warp), or, with JG, added
+// straight into the FP64 accumulator jg (rows of stride jstride, source jj at jg[jj]).
+template <int KIND, int NP, bool FG, bool FULL, bool JG = false>
 __device__ __forceinline__ void x2_group(int jj, int cnt, int lane, int warp, const RecMix* rec,
                                          const float4* arec, const float4* rel_s,
                                          const X2I (&pp)[NP], const float2 (&D)[NP][3],
-                                         float2 eps2, float2 (&f)[NP][3], float* jpart) {
+                                         float2 eps2, float2 (&f)[NP][3], float* jpart,
+                                         double* jg = nullptr, long long jstride = 0) {
     const int L = lane >> 3;
     float fj[4][3];
 #pragma unroll
@@ -133,8 +135,14 @@ __device__ __forceinline__ void x2_group(int jj, int cnt, int lane, int warp, co
     }
     const int jl = jj + L;
     if ((lane & 7) == 0 && (FULL || jl < cnt)) {
-        float* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
-        dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+        if constexpr (JG) {
+            red_add(jg + jl, (double)tot[0]);
+            red_add(jg + jstride + jl, (double)tot[1]);
+            red_add(jg + 2 * jstride + jl, (double)tot[2]);
+        } else {
+            float* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
+            dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
+        }
     }
 }
 

@@ -536,8 +536,13 @@ def fsi_accel_noalloc(pos, mass, eps2: float = 0.0, out=None, stream=None):
     the library (fixed 4 MiB scratch in the library; N <= 32768).  `out` (3, N) must be
     supplied by callers that cannot allocate; otherwise it is created here with torch."""
     N = mass.numel()
-    if out is None:
+    if out is None and pos.is_cuda:
         out = torch.empty((3, N), dtype=torch.float64, device=pos.device)
+    # the library launches on the current device: every tensor must live there
+    cur = torch.cuda.current_device()
+    for name, t in (("pos", pos), ("mass", mass), ("out", out)):
+        if not (t is not None and t.is_cuda and t.device.index == cur):
+            raise TypeError(f"{name} must be a CUDA tensor on the current device (cuda:{cur})")
     _check(_lib.fsi_accel_noalloc(N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
                                   float(eps2), _f64(out, (3, N), "out"), _stream(stream)),
            "fsi_accel_noalloc")

@@ -1,0 +1,229 @@
+"""i-sharded pair passes and FSI cycles over several ranks (one process per GPU).
+
+Direct summation shards along the receivers: every rank holds the replicated positions
+and masses of the whole set (and, for the gradient pass, the accelerations of the whole
+splitting term), and computes the pair sums of a contiguous slice of the active list
+against all sources.  The data exchanged between ranks is what the next pass needs:
+
+  * after every drift, an all-gather of the moved particles' positions (24 B per particle
+    of the active list);
+  * between the acceleration and the gradient pass, an all-gather of the accelerations of
+    the splitting term (24 B per particle of A, and of B for an inter-level term), since
+    the gradient sum of Sect. 2.1 (Eq. new-grad-acc) needs a_j of every source j;
+  * for active sets too small to give every rank receivers (fewer than `min_rows` per
+    rank), the sources are split instead and the partial acceleration and gradient sums
+    are all-reduced (48 B per active particle).
+
+The paper runs its direct-summation loops on several GPUs with MPI (Sect. 4.1); here the
+collectives are torch.distributed's (NCCL between GPUs: every operand lands in the
+receiving GPU's own memory before a kernel reads it).  The exchange layer only moves
+data: every pair sum, kick and drift is done by the shard compute, which for the product
+is libfsi on the rank's own GPU (LibfsiCompute); the tests plug the CPU oracle in
+instead to check the exchange against one-rank results on gloo ranks.
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass
+from typing import Optional
+
+import torch
+
+
+def slice_bounds(n: int, world: int, rank: int):
+    """Contiguous slice [lo, hi) of an n-entry list owned by `rank`: the first n % world
+    ranks take one entry more."""
+    q, r = divmod(n, world)
+    lo = rank * q + min(rank, r)
+    return lo, lo + q + (1 if rank < r else 0)
+
+
+class LibfsiCompute:
+    """Shard compute on the rank's GPU through libfsi's C ABI (a context per rank).
+    Index lists are int32 CUDA tensors of global ids."""
+
+    def __init__(self, ctx):
+        from . import fsi
+        self.F = fsi
+        self.ctx = ctx
+
+    def accel(self, pos, mass, A, B, eps2):
+        return self.F.fsi_accel(self.ctx, pos, mass, A, B, eps2=eps2)
+
+    def grad(self, pos, mass, accg, A, B, eps2):
+        return self.F.fsi_grad(self.ctx, pos, mass, accg, A, B, eps2=eps2)
+
+    def pn_accel(self, pos, vel, mass, is_bh, c, A, B):
+        return self.F.fsi_pn_accel(self.ctx, pos, vel, mass, is_bh, c, A, B)
+
+    def kick_drift(self, pos, vel, acc, idx, c_kick, c_drift):
+        self.F.fsi_kick_drift(self.ctx, pos, vel, acc, c_kick, c_drift, idx=idx)
+
+    def status(self):
+        return self.F.fsi_sync_status(self.ctx)
+
+
+class Exchange:
+    """Collectives of the sharded passes over a torch.distributed process group (None:
+    a single rank).  With a CPU backend (gloo) and device tensors, operands are staged
+    through host memory."""
+
+    def __init__(self, group=None):
+        import torch.distributed as dist
+        self.dist = dist if dist.is_available() and dist.is_initialized() else None
+        self.group = group
+        self.world = self.dist.get_world_size(group) if self.dist else 1
+        self.rank = self.dist.get_rank(group) if self.dist else 0
+        self.cpu_backend = bool(self.dist) and self.dist.get_backend(group) == "gloo"
+
+    def _stage(self, t):
+        return t.cpu() if (self.cpu_backend and t.is_cuda) else t
+
+    def all_gather_cols(self, local: torch.Tensor, n: int) -> torch.Tensor:
+        """Concatenate the ranks' (rows, n_r) column slices (slice_bounds order) into
+        (rows, n)."""
+        if self.dist is None:
+            return local
+        q = -(-n // self.world)
+        rows = local.shape[0]
+        buf = torch.zeros((rows, q), dtype=local.dtype, device=local.device)
+        buf[:, :local.shape[1]] = local
+        sb = self._stage(buf.contiguous())
+        parts = [torch.empty_like(sb) for _ in range(self.world)]
+        self.dist.all_gather(parts, sb, group=self.group)
+        cols = []
+        for r, p in enumerate(parts):
+            lo, hi = slice_bounds(n, self.world, r)
+            cols.append(p[:, :hi - lo])
+        return torch.cat(cols, dim=1).to(local.device)
+
+    def all_reduce_sum(self, t: torch.Tensor) -> torch.Tensor:
+        if self.dist is None:
+            return t
+        st = self._stage(t.contiguous())
+        self.dist.all_reduce(st, op=self.dist.ReduceOp.SUM, group=self.group)
+        return st.to(t.device)
+
+
+@dataclass
+class ShardPlan:
+    """Which receivers (or, for small active sets, which sources) a rank takes."""
+    mode: str                  # "rows": a slice of A against all of B; "sources": all of A
+    lo: int                    # against a slice of B
+    hi: int
+
+
+def plan(nA: int, nB: int, ex: Exchange, min_rows: int) -> ShardPlan:
+    if ex.world > 1 and nA < min_rows * ex.world and nB >= ex.world:
+        lo, hi = slice_bounds(nB, ex.world, ex.rank)
+        return ShardPlan("sources", lo, hi)
+    lo, hi = slice_bounds(nA, ex.world, ex.rank)
+    return ShardPlan("rows", lo, hi)
+
+
+def _ids(n: int, idx: Optional[torch.Tensor], device) -> torch.Tensor:
+    return idx if idx is not None else torch.arange(n, dtype=torch.int32, device=device)
+
+
+class ShardedFSI:
+    """The sharded hot path: pair sums of one splitting term (fsi_accel_grad semantics)
+    and FSI cycles of a set (fsi_step semantics), with every rank ending with the same
+    results.  `compute` does all arithmetic; `ex` moves data between ranks."""
+
+    def __init__(self, compute, ex: Optional[Exchange] = None, min_rows: int = 1024):
+        self.c = compute
+        self.ex = ex or Exchange()
+        self.min_rows = int(min_rows)
+
+    # -------------------------------------------------------------- pair sums
+    def _acc(self, pos, mass, A, B, eps2, p: ShardPlan):
+        if p.mode == "rows":
+            a = self.c.accel(pos, mass, A[p.lo:p.hi], B, eps2)
+            return self.ex.all_gather_cols(a, A.numel())
+        return self.ex.all_reduce_sum(self.c.accel(pos, mass, A, B[p.lo:p.hi], eps2))
+
+    def _grad(self, pos, mass, accg, A, B, eps2, p: ShardPlan):
+        if p.mode == "rows":
+            g = self.c.grad(pos, mass, accg, A[p.lo:p.hi], B, eps2)
+            return self.ex.all_gather_cols(g, A.numel())
+        return self.ex.all_reduce_sum(self.c.grad(pos, mass, accg, A, B[p.lo:p.hi], eps2))
+
+    def accel_grad(self, pos, mass, A=None, B=None, eps2: float = 0.0):
+        """acc(A <- B) and G(A <- B) of one splitting term (Sect. 2.1 / 2.2), both (3, nA)
+        on every rank: A and B the same list (or both None) -- the a_j inside G are
+        acc(A <- A); A and B disjoint -- a_i = acc(A <- B), a_j = acc(B <- A) (the
+        inter-level term).  As for fsi_accel_grad, other overlaps are not a splitting
+        term."""
+        N = mass.numel()
+        same = (A is None and B is None) or (A is not None and A is B)
+        A = _ids(N, A, pos.device)
+        B = A if same else _ids(N, B, pos.device)
+        pa = plan(A.numel(), B.numel(), self.ex, self.min_rows)
+        a = self._acc(pos, mass, A, B, eps2, pa)
+        accg = torch.zeros((3, N), dtype=pos.dtype, device=pos.device)
+        accg[:, A.long()] = a
+        if not same:
+            pb = plan(B.numel(), A.numel(), self.ex, self.min_rows)
+            accg[:, B.long()] = self._acc(pos, mass, B, A, eps2, pb)
+        g = self._grad(pos, mass, accg, A, B, eps2, pa)
+        return a, g
+
+    # -------------------------------------------------------------- FSI cycles
+    def _sync_cols(self, x, idx, lo, hi, n):
+        """Every rank's slice idx[lo:hi] of the (3, N) array x, gathered into x[:, idx]."""
+        if self.ex.dist is None:
+            return
+        mine = x[:, idx[lo:hi].long()]
+        x[:, idx.long()] = self.ex.all_gather_cols(mine, n)
+
+    def step(self, pos, vel, mass, h: float, nsteps: int = 1, idx=None, eps2: float = 0.0,
+             c: float = 0.0, is_bh=None):
+        """nsteps FSI cycles (Sect. 2.1, Eq. fsi-cycle) of the set idx (None: all N) on
+        itself, in place on the replicated pos / vel: kick h/6, drift h/2, kick 2h/3 with
+        a + h^2/24 G, drift h/2, kick h/6, consecutive cycles sharing the closing and
+        opening acceleration (a kick of h/3); with c > 0 PN1.0 half-kicks of h/2 wrap every
+        cycle (Sect. 3.9; velocities from the start of each half-kick).  Each rank kicks
+        and drifts its slice of the set; positions (after drifts), the accelerations of the
+        gradient pass and, around PN kicks and at the end, velocities are all-gathered."""
+        N = mass.numel()
+        P = _ids(N, idx, pos.device)
+        n = P.numel()
+        if n == 0 or nsteps <= 0:
+            return
+        lo, hi = slice_bounds(n, self.ex.world, self.ex.rank)
+        Pr = P[lo:hi]
+        pn = c > 0.0
+
+        def acc_mine():
+            return self.c.accel(pos, mass, Pr, P, eps2)
+
+        def pn_kick():
+            self._sync_cols(vel, P, lo, hi, n)
+            apn = self.c.pn_accel(pos, vel, mass, is_bh, c, Pr, P)
+            self.c.kick_drift(pos, vel, apn, Pr, 0.5 * h, 0.0)
+
+        if pn:
+            pn_kick()
+        a = acc_mine()
+        self.c.kick_drift(pos, vel, a, Pr, h / 6.0, 0.5 * h)
+        for k in range(nsteps):
+            last = k == nsteps - 1
+            self._sync_cols(pos, P, lo, hi, n)
+            a = acc_mine()
+            accg = torch.zeros((3, N), dtype=pos.dtype, device=pos.device)
+            accg[:, P.long()] = self.ex.all_gather_cols(a, n)
+            g = self.c.grad(pos, mass, accg, Pr, P, eps2)
+            self.c.kick_drift(pos, vel, a, Pr, 2.0 * h / 3.0, 0.0)
+            self.c.kick_drift(pos, vel, g, Pr, (2.0 * h / 3.0) * (h * h / 24.0), 0.5 * h)
+            self._sync_cols(pos, P, lo, hi, n)
+            a = acc_mine()
+            if not pn and not last:
+                self.c.kick_drift(pos, vel, a, Pr, h / 3.0, 0.5 * h)
+                continue
+            self.c.kick_drift(pos, vel, a, Pr, h / 6.0, 0.0)
+            if pn:
+                pn_kick()
+            if not last:
+                # the next cycle's opening kick reuses this acceleration (no drift between)
+                pn_kick()
+                self.c.kick_drift(pos, vel, a, Pr, h / 6.0, 0.5 * h)
+        self._sync_cols(vel, P, lo, hi, n)

@@ -29,13 +29,23 @@ def ens():
     return inputs.ensemble(24, 64, 2048, 77)
 
 
+@pytest.fixture(scope="module")
+def ens_large():
+    # 6 clusters, N log-uniform in [1500, 6000]: several blocks of both symmetric variants
+    return inputs.ensemble(6, 1500, 6000, 78)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("ipt", [1, 2, 4])
-def test_batch_matches_oracle_per_cluster(F, ens, prec, ipt):
-    """ipt 1, 2: one-sided form; 4: symmetric form (mixed precision only)."""
-    if ipt == 4 and prec == "fp64":
+@pytest.mark.parametrize("ipt", [1, 2, 4, 8])
+@pytest.mark.parametrize("which", ["small", "large"])
+def test_batch_matches_oracle_per_cluster(F, ens, ens_large, prec, ipt, which):
+    """ipt 1, 2: one-sided form; 4, 8: symmetric form with blocks of 1024 / 2048 particles
+    (mixed precision only)."""
+    if ipt >= 4 and prec == "fp64":
         pytest.skip("the symmetric batch form is mixed precision")
-    cat, off = ens
+    if which == "large" and ipt < 4:
+        pytest.skip("the one-sided form is covered by the small ensemble")
+    cat, off = ens if which == "small" else ens_large
     h, steps = 1e-3, 3
     rp, rv = cat.pos.copy(), cat.vel.copy()
     for k in range(len(off) - 1):
@@ -54,7 +64,7 @@ def test_batch_matches_oracle_per_cluster(F, ens, prec, ipt):
     assert np.abs(v - rv).max() <= tol * 100 * np.abs(rv).max()
 
 
-@pytest.mark.parametrize("ipt", [1, 4])
+@pytest.mark.parametrize("ipt", [1, 4, 8])
 def test_batch_graph_capture_replays(F, ens, ipt):
     cat, off = ens
     h = 1e-3
@@ -81,7 +91,7 @@ def test_batch_graph_capture_replays(F, ens, ipt):
         b.close()
 
 
-@pytest.mark.parametrize("ipt", [1, 4])
+@pytest.mark.parametrize("ipt", [1, 4, 8])
 def test_batch_bounded_wait_times_out_cleanly(F, ens, ipt):
     """A cluster made to wait for a phase count that never comes: the launch returns with
     FSI_ERR_TIMEOUT latched, the context stays usable and the next step runs normally."""

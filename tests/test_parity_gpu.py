@@ -4,17 +4,23 @@ Tolerances (per particle, max component error):
   FP64 path   1e-12 of the oracle vector's norm (every pair term in FP64; only the
               summation order differs).
   MIXED path  acceleration: 1e-6 of S_i = sum_j m_j / r_ij^2, the sum of the absolute
-              pair-term magnitudes, and a median of 2e-7 of |a_i|.  Derivation: a pair
-              term carries about five FP32 roundings (u = 2^-24 = 6e-8) on top of a
-              separation that is itself FP32-accurate (hi/lo split), i.e. <= ~4u = 2.4e-7
-              of its magnitude, and the FP32 partial sum over one source tile adds up to
-              another ~4u of the tile's term magnitudes before it is added in FP64; the
-              errors of different terms add at most linearly, so the sum is good to
-              ~8u S_i = 5e-7 S_i (observed up to 5.1e-7), bounded here by 16u = 1e-6.
-              Relative to |a_i| the error is larger where terms cancel.
+              pair-term magnitudes -- the worst case: a pair term carries about five FP32
+              roundings (u = 2^-24 = 6e-8) on top of a separation that is itself
+              FP32-accurate (hi/lo split), i.e. <= ~4u of its magnitude, and an FP32
+              partial sum over a run of sources adds up to another ~4u of the run's term
+              magnitudes before it enters the float-float (or FP64) accumulator; the
+              errors of different terms add at most linearly, ~8u S_i = 5e-7 S_i, bounded
+              here by 16u = 1e-6.  Relative to |a_i| (where terms cancel, |a_i| << S_i)
+              the errors are random and add in quadrature, so the distribution over the
+              rows is what the kernels are held to: the median of |da_i| / |a_i| within
+              1e-7 and every row within 3e-6 (measured on these sets: medians 1.8-4.3e-8,
+              maxima up to 1.2e-6), and the larger sets' medians and 99th percentiles
+              within about twice their measured values (MIXED_* below).
               gradient: the a_j - a_i differences are taken in FP32 from FP32 copies of
-              the accelerations, so the bound is relative to the scale
-              sum_j m_j (|a_i| + |a_j|) / r^3 (checked as 1e-5 of that scale).
+              the accelerations, so the worst case is relative to the scale
+              sum_j m_j (|a_i| + |a_j|) / r^3 (checked as 1e-5 of that scale); relative to
+              |G_i| the median within 3e-7 and the 99th percentile within 2e-6 (measured:
+              medians 5.6e-8-2.2e-7, 99th percentiles 5e-7-1.1e-6).
 """
 import os
 
@@ -30,7 +36,15 @@ pytestmark = pytest.mark.gpu
 
 PRECS = ["fp64", "mixed"]
 TOL = {"fp64": 1e-12, "mixed": 1e-6}
-TOL_MED = {"fp64": 1e-13, "mixed": 2e-7}
+TOL_MED = {"fp64": 1e-13, "mixed": 1e-7}
+MIXED_ROW_MAX = 3e-6          # per-row max component error / |a_i|, mixed
+MIXED_GRAD_MED, MIXED_GRAD_ROW_P99 = 3e-7, 2e-6
+# Mixed path, relative error |da_i| / |a_i| and |dG_i| / |G_i| over every row of the
+# 40000- and 65536-particle sets (the middle size class: packed symmetric form, far-tile
+# path): medians and 99th percentiles about twice the measured 2.2-2.4e-8 / 1.4-1.8e-7
+# (acceleration) and 6.4-6.9e-8 / 6.3-6.7e-7 (gradient with the set's accelerations).
+MIXED_ACC_MEDIAN, MIXED_ACC_P99 = 5e-8, 4e-7
+MIXED_GRAD_MEDIAN, MIXED_GRAD_P99 = 1.5e-7, 1.5e-6
 
 
 @pytest.fixture(scope="module")
@@ -74,12 +88,14 @@ def abs_scale(pos, mass, A=None, B=None, eps2=0.0):
     return out
 
 
-def assert_close(got, ref, prec, what="", scale=None):
+def assert_close(got, ref, prec, what="", scale=None, med=None):
+    """med: the median bound (default TOL_MED); it is only checked over >= 16 rows (for one
+    or two rows the median is a single pair term's rounding, up to ~3u = 1.8e-7)."""
     e = rel_err(got, ref)
     assert np.all(np.isfinite(got)), what
-    assert np.median(e) <= TOL_MED[prec], (what, e.max(), np.median(e))
-    if prec == "fp64" or scale is None:
-        assert e.max() <= (TOL[prec] if prec == "fp64" else 5e-5), (what, e.max(), np.median(e))
+    if e.size >= 16:
+        assert np.median(e) <= (med or TOL_MED[prec]), (what, e.max(), np.median(e))
+    assert e.max() <= (TOL[prec] if prec == "fp64" else MIXED_ROW_MAX), (what, e.max(), np.median(e))
     if prec == "mixed" and scale is not None:
         es = np.abs(got - ref).max(axis=0) / scale
         assert es.max() <= TOL[prec], (what, es.max(), e.max(), np.median(e))
@@ -127,6 +143,32 @@ def test_accel_general_overlapping_lists(F, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("lo,hi", [(0, 1000), (777, 2600), (2500, 3001)])
+def test_sub_range_receivers(F, prec, lo, hi):
+    """Receivers that are a slice of the source list (the same memory, as a sharded pass
+    gives each rank): self pairs excluded by the index offset, every other tile unchecked;
+    acceleration and gradient sum against the oracle."""
+    n = 3001
+    c = inputs.plummer(n, 60, imf="kroupa")
+    B = np.random.default_rng(61).permutation(n).astype(np.int32)
+    A = B[lo:hi]
+    accg = inputs.random_field(n, 62)
+    ra = oracle.acc(c.pos, c.mass, A, B)
+    rg = oracle.grad(c.pos, c.mass, accg, A, B)
+    with F.Context(prec) as ctx:
+        Bd = ids(B)
+        Ad = Bd[lo:hi]                          # a view into B's memory
+        a = host(F.fsi_accel(ctx, dev(c.pos), dev(c.mass), Ad, Bd))
+        g = host(F.fsi_grad(ctx, dev(c.pos), dev(c.mass), dev(accg), Ad, Bd))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(a, ra, prec, scale=abs_scale(c.pos, c.mass, A, B) if prec == "mixed" else None)
+    if prec == "fp64":
+        assert_close(g, rg, prec)
+    else:
+        assert_grad_close(g, rg, prec, grad_scale(c.pos, c.mass, accg, A, B))
+
+
+@pytest.mark.parametrize("prec", PRECS)
 def test_accel_softened_with_coincident_points(F, prec):
     c = inputs.plummer(700, 8)
     c.pos[:, 5] = c.pos[:, 6]                    # coincident distinct particles
@@ -139,15 +181,52 @@ def test_accel_softened_with_coincident_points(F, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_coincident_unsoftened_is_reported(F, prec):
-    c = inputs.plummer(300, 9)
-    c.pos[:, 10] = c.pos[:, 11]
-    with F.Context(prec) as ctx:
+@pytest.mark.parametrize("n,symmetric", [(300, True), (3000, True), (3000, False)])
+def test_coincident_unsoftened_is_reported(F, prec, n, symmetric):
+    """Two distinct particles at exactly the same position with eps2 = 0: the pair terms of
+    Sect. 2.1 (and the free-fall and fly-by steps of Sect. 3.4) are undefined there, and
+    every pass reports FSI_ERR_COINCIDENT -- the wide form (n = 300), the symmetric and the
+    one-sided tiled forms (n = 3000; the two particles in different blocks), the general
+    id-list path, the gradient, time-step and energy passes.  The error word is cleared by
+    the read."""
+    c = inputs.plummer(n, 9)
+    j = n - 40
+    c.pos[:, 10] = c.pos[:, j]
+    with F.Context(prec, symmetric=symmetric) as ctx:
+        p, v, m = dev(c.pos), dev(c.vel), dev(c.mass)
+        F.fsi_accel(ctx, p, m)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_COINCIDENT
+        A = ids(np.array([3, 10, 11], dtype=np.int32))
+        B = ids(np.arange(5, n, dtype=np.int32))
+        F.fsi_accel(ctx, p, m, A, B)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_COINCIDENT
+        F.fsi_grad(ctx, p, m, dev(inputs.random_field(n, 3)))
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_COINCIDENT
+        F.fsi_accel_grad(ctx, p, None, m)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_COINCIDENT
+        F.fsi_timesteps(ctx, p, v, m)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_COINCIDENT
+        F.fsi_energy(ctx, p, v, m)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_COINCIDENT
+        # the error word is cleared by the read; distinct positions are fine
+        F.fsi_accel(ctx, dev(inputs.plummer(n, 10).pos), m)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        # with softening the coincident pair is regular for the pair sums
+        with F.Context(prec, eps2=1e-4, symmetric=symmetric) as soft:
+            F.fsi_accel(soft, p, m, eps2=1e-4)
+            assert F.fsi_sync_status(soft) == F.FSI_OK
+
+
+def test_nonfinite_without_coincidence_is_not_coincident(F):
+    """Mixed precision: two particles 1e-30 apart (distinct in FP64) have r^2 below the FP32
+    range, so the pair term is not finite; that is FSI_ERR_NONFINITE, not a coincidence."""
+    c = inputs.plummer(400, 12)
+    c.pos[:, 10] = 0.0
+    c.pos[:, 11] = 0.0
+    c.pos[0, 11] = 1e-30
+    with F.Context("mixed") as ctx:
         F.fsi_accel(ctx, dev(c.pos), dev(c.mass))
         assert F.fsi_sync_status(ctx) == F.FSI_ERR_NONFINITE
-        # the error word is cleared by the read
-        F.fsi_accel(ctx, dev(inputs.plummer(300, 10).pos), dev(c.mass))
-        assert F.fsi_sync_status(ctx) == F.FSI_OK
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -164,38 +243,34 @@ def test_split_factor_does_not_change_results(F, prec):
 
 @pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n", [700, 4097, 20000])
-def test_symmetric_matches_one_sided(F, prec, n):
-    """Every unordered pair once (Newton's third law) vs every ordered pair: the same sums
-    up to rounding, for every kernel variant."""
+def test_every_variant_against_oracle(F, prec, n):
+    """Every built pair-kernel variant -- one-sided (every ordered pair by its receiver),
+    the wide form, and each symmetric form (every unordered pair once, Newton's third law)
+    -- against the oracle: acceleration and the gradient sum with the set's own
+    accelerations."""
     c = inputs.plummer(n, 41 + n, imf="kroupa")
-    with F.Context(prec, symmetric=False, wide_ctas=-1) as ctx:
-        a1, g1 = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
-        a1, g1 = host(a1), host(g1)
-    with F.Context(prec, wide_ctas=1 << 30) as ctx:          # the wide form
-        aw, gw = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
-        aw, gw = host(aw), host(gw)
-    if prec == "fp64":
-        assert rel_err(aw, a1).max() <= 1e-12
-    else:   # both forms within 1e-6 S_i of the exact sums (S_i = sum m_j / r_ij^2)
-        sc = abs_scale(c.pos, c.mass)
-        assert (np.abs(aw - a1).max(axis=0) / sc).max() <= 2e-6
-    eg = rel_err(gw, g1)
-    assert np.median(eg) <= (1e-12 if prec == "fp64" else 1e-4)
-    variants = ((2, 2), (3, 3), (4, 4), (36, 36), (37, 37), (38, 37), (226, 226), (228, 228), (230, 230), (246, 246), (248, 248)) \
-        if prec == "mixed" \
-        else ((1, 1), (2, 2), (3, 3))
-    with F.Context(prec, wide_ctas=-1) as ctx:
-        for va, vg in variants:
-            F.fsi_set_tuning(ctx, va, vg)
-            v = (va, vg)
-            a2, g2 = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
-            a2, g2 = host(a2), host(g2)
+    ra, rg = oracle.accel_grad(c.pos, c.mass)
+    sc = abs_scale(c.pos, c.mass) if prec == "mixed" else None
+    gs = grad_scale(c.pos, c.mass, ra, np.arange(n), np.arange(n)) if prec == "mixed" else None
+    cases = [("one-sided", dict(symmetric=False, wide_ctas=-1), None),
+             ("wide", dict(wide_ctas=1 << 30), None)]
+    sym = ((2, 2), (3, 3), (4, 4), (36, 36), (37, 37), (38, 37), (226, 226), (228, 228),
+           (230, 230), (246, 246), (248, 248)) if prec == "mixed" else ((1, 1), (2, 2), (3, 3))
+    one = ((2, 2), (3, 3), (4, 4), (18, 18), (36, 36)) if prec == "mixed" else ((1, 1), (2, 2), (3, 3))
+    cases += [(f"symmetric {v}", dict(wide_ctas=-1), v) for v in sym]
+    cases += [(f"one-sided {v}", dict(symmetric=False, wide_ctas=-1), v) for v in one]
+    for what, kw, v in cases:
+        with F.Context(prec, **kw) as ctx:
+            if v is not None:
+                F.fsi_set_tuning(ctx, *v)
+            a, g = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
+            a, g = host(a), host(g)
             assert F.fsi_sync_status(ctx) == F.FSI_OK
-            ea, eg = rel_err(a2, a1), rel_err(g2, g1)
-            tol_a = 1e-12 if prec == "fp64" else 2e-6
-            tol_g = 1e-11 if prec == "fp64" else 1e-3
-            assert ea.max() <= tol_a, (v, ea.max())
-            assert np.median(eg) <= tol_g / 10 and np.percentile(eg, 99) <= tol_g, (v, eg.max())
+        # the first and second symmetric forms (variants < 128) keep FP32 sums over whole
+        # 256-source tiles: their median error is about twice the other forms'
+        legacy = prec == "mixed" and what.startswith("symmetric") and v[0] < 128
+        assert_close(a, ra, prec, what, sc, med=2e-7 if legacy else None)
+        assert_grad_close(g, rg, prec, gs)
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -228,6 +303,9 @@ def assert_grad_close(got, ref, prec, scale):
     else:
         e = np.abs(got - ref).max(axis=0) / scale
         assert e.max() <= 1e-5, e.max()
+        r = rel_err(got, ref)
+        assert np.median(r) <= MIXED_GRAD_MED and np.percentile(r, 99) <= MIXED_GRAD_ROW_P99, \
+            (np.median(r), np.percentile(r, 99), r.max())
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -357,13 +435,33 @@ def test_fsi_step_with_pn(F, prec):
     assert np.abs(v - rv).max() <= STEP_TOL[prec] * 100
 
 
-def test_pn_accel_pairs(F):
-    c = inputs.plummer(500, 20, imf="kroupa", n_bh=5)
-    ref = oracle.pn_acc(c.pos, c.vel, c.mass, c.is_bh, 25.0)
+@pytest.mark.parametrize("lists", ["all", "overlapping", "slice", "disjoint"])
+def test_pn_accel_pairs(F, lists):
+    """PN1.0 pair accelerations through the black-hole sublists against the oracle: all
+    particles, overlapping id lists (self pairs skipped by id), receivers a slice of the
+    sources' memory, disjoint lists."""
+    n = 500
+    c = inputs.plummer(n, 20, imf="kroupa", n_bh=5)
+    bh = np.nonzero(c.is_bh)[0]
+    A = B = None
+    if lists != "all":
+        B = np.random.default_rng(21).permutation(n).astype(np.int32)
+        if lists == "overlapping":
+            A = np.concatenate([bh[:3], inputs.random_subset(n, 120, 22)]).astype(np.int32)
+        elif lists == "slice":
+            A = B[100:300]
+        else:
+            A, B = B[:200], B[200:]
+    ref = oracle.pn_acc(c.pos, c.vel, c.mass, c.is_bh, 25.0, A, B)
     with F.Context("fp64") as ctx:
+        Bd = ids(B)
+        Ad = Bd[100:300] if lists == "slice" else ids(A)
         got = host(F.fsi_pn_accel(ctx, dev(c.pos), dev(c.vel), dev(c.mass),
-                                  dev(c.is_bh, torch.uint8), 25.0))
-    assert_close(got, ref, "fp64")
+                                  dev(c.is_bh, torch.uint8), 25.0, Ad, Bd))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert np.abs(ref).max() > 0
+    nrm = np.maximum(np.linalg.norm(ref, axis=0), np.abs(ref).max() * 1e-3)
+    assert (np.abs(got - ref).max(axis=0) / nrm).max() <= 1e-12
 
 
 # ----------------------------------------------------------------------------- kick / drift
@@ -642,18 +740,19 @@ def big():
 
 def test_full_size_mixed_acc_sampled_rows(F, big):
     """N = 2^20 + 16 (Kroupa + 16 black holes): the all-pairs mixed pass of the benchmark's
-    launch configuration, checked on 256 sampled rows against the oracle."""
-    rows = inputs.random_subset(big.n, 256, 31)
+    launch configuration, checked on 1024 sampled rows against the oracle."""
+    rows = inputs.random_subset(big.n, 1024, 31)
     ref = oracle.acc(big.pos, big.mass, rows, None)
     with F.Context("mixed") as ctx:
         got = host(F.fsi_accel(ctx, dev(big.pos), dev(big.mass)))
         assert F.fsi_sync_status(ctx) == F.FSI_OK
     assert_close(got[:, rows], ref, "mixed", scale=abs_scale(big.pos, big.mass, rows))
-    # the relative acceleration error |da| / |a| of the mixed path at this size: the
-    # median within 1e-7 (measured 2.6e-8; 99th percentile 1.1e-7, maximum 2.4e-7 on 512
-    # rows), the 99th percentile within 2.5e-7
+    # the relative acceleration error |da| / |a| of the mixed path at this size, measured on
+    # 4096 rows: median 2.0e-8, 99th percentile 9.2e-8, 99.9th 2.3e-7, maximum 5.0e-7
+    # (0.8 % of the rows above 1e-7); held to about twice that
     d = np.linalg.norm(got[:, rows] - ref, axis=0) / np.linalg.norm(ref, axis=0)
-    assert np.median(d) <= 1e-7 and np.percentile(d, 99) <= 2.5e-7, (np.median(d), d.max())
+    assert np.median(d) <= 4e-8 and np.percentile(d, 99) <= 2e-7 and d.max() <= 1e-6, \
+        (np.median(d), np.percentile(d, 99), d.max())
 
 
 @pytest.mark.parametrize("prec", PRECS)
@@ -670,8 +769,9 @@ def test_full_size_sampled_rows_general_path(F, big, prec):
     if prec == "fp64":
         assert_close(gg, refg, prec)
     else:
-        e = np.abs(gg - refg).max(axis=0) / np.linalg.norm(refg, axis=0)
-        assert np.median(e) < 1e-4, np.median(e)
+        e = rel_err(gg, refg)
+        assert np.median(e) <= MIXED_GRAD_MED and np.percentile(e, 99) <= MIXED_GRAD_ROW_P99, \
+            (np.median(e), np.percentile(e, 99), e.max())
 
 
 def test_full_size_mixed_grad_sampled_rows(F, big):
@@ -687,6 +787,77 @@ def test_full_size_mixed_grad_sampled_rows(F, big):
     scale = grad_scale(big.pos, big.mass, accg, rows, np.arange(big.n))
     e = np.abs(got[:, rows] - ref).max(axis=0) / scale
     assert e.max() <= 1e-5, e.max()
+    # relative to |G_i|, measured on 1024 rows: median 1.4e-7, 99th percentile 7.7e-7
+    r = rel_err(got[:, rows], ref)
+    assert np.median(r) <= MIXED_GRAD_MED and np.percentile(r, 99) <= MIXED_GRAD_ROW_P99, \
+        (np.median(r), np.percentile(r, 99), r.max())
+
+
+def test_full_size_fp64_symmetric_sampled_rows(F, big):
+    """N = 2^20 + 16, FP64: the same-set symmetric passes behind the FP64 throughput figures
+    (every unordered pair once, sym_pair_kernel) -- the acceleration and the gradient sum
+    with a seeded field -- on 256 sampled rows against the oracle, at the FP64 tolerance."""
+    rows = inputs.random_subset(big.n, 256, 36)
+    ref = oracle.acc(big.pos, big.mass, rows, None)
+    accg = inputs.random_field(big.n, 37)
+    refg = oracle.grad(big.pos, big.mass, accg, rows, None)
+    with F.Context("fp64") as ctx:
+        got = host(F.fsi_accel(ctx, dev(big.pos), dev(big.mass)))
+        gg = host(F.fsi_grad(ctx, dev(big.pos), dev(big.mass), dev(accg)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(got[:, rows], ref, "fp64")
+    assert_close(gg[:, rows], refg, "fp64")
+
+
+@pytest.mark.parametrize("n", [40000, 65536])
+def test_mid_class_symmetric_variant_against_oracle(F, n):
+    """The mixed default of the middle size class (32768 <= n < 196608: the packed
+    symmetric form with 4 particles per thread, variant 228, on the Morton-ordered set with
+    the far-tile path) against the oracle on every row: acceleration and the gradient sum
+    with the set's own accelerations (the same splitting term).  n = 65536 is the Kroupa
+    cluster of the HHS workload."""
+    c = inputs.plummer(n, 41 + n, imf="kroupa") if n != 65536 else inputs.workload("kroupa64k")
+    ra = oracle.acc(c.pos, c.mass)
+    rg = oracle.grad(c.pos, c.mass, ra)
+    with F.Context("mixed") as ctx:
+        assert F.fsi_get_tuning_for(ctx, n) == (228, 228)
+        a, g = F.fsi_accel_grad(ctx, dev(c.pos), None, dev(c.mass))
+        a, g = host(a), host(g)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert_close(a, ra, "mixed")
+    d = np.linalg.norm(a - ra, axis=0) / np.linalg.norm(ra, axis=0)
+    assert np.median(d) <= MIXED_ACC_MEDIAN and np.percentile(d, 99) <= MIXED_ACC_P99, \
+        (np.median(d), np.percentile(d, 99), d.max())
+    e = np.linalg.norm(g - rg, axis=0) / np.linalg.norm(rg, axis=0)
+    assert np.median(e) <= MIXED_GRAD_MEDIAN and np.percentile(e, 99) <= MIXED_GRAD_P99, \
+        (np.median(e), np.percentile(e, 99), e.max())
+
+
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("small", [0, -1])
+def test_hhs_interval_softened(F, prec, small):
+    """One HHS interval with Plummer softening (eps2 > 0, the setting of the softened
+    equal-mass run of Sect. 5.2) against the oracle's interval at the same eps2: softened
+    pair sums (r^2 + eps2 in r^3 and r^5), unsoftened free-fall / fly-by distances, levels
+    walked from the host (small = -1) or recursed inside one CTA (0)."""
+    c = inputs.plummer(2000, 38)
+    tau, eps2 = 1.0 / 32, 1e-4
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, eps2=eps2)
+    rp0, _, counts0, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    assert np.abs(rp - rp0).max() > 1e-9                    # the softening matters here
+    assert np.count_nonzero(counts) >= 3                    # several levels
+    with F.Context(prec, eps2=eps2, hhs_small_max=small) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
 
 
 # ----------------------------------------------------------------------------- subsystems
