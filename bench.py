@@ -483,8 +483,8 @@ def run_ensemble(args):
     # autotune: particles per thread x resident CTAs per SM (or fixed by --batch-tuning)
     best = None
     fixed = [tuple(int(x) for x in args.batch_tuning.split(","))] if args.batch_tuning else None
-    combos = fixed or [(ipt, cps) for ipt in ((1, 2, 4, 8) if args.precision == "mixed" else (1, 2))
-                       for cps in (1, 2, 0) if not (ipt == 8 and cps == 2)]   # ipt 4, 8: symmetric
+    combos = fixed or [(ipt, cps) for ipt in ((1, 2, 4, 6, 8) if args.precision == "mixed" else (1, 2))
+                       for cps in (1, 2, 0) if not (ipt == 8 and cps == 2)]   # ipt 4, 6, 8: symmetric
     for ipt, cps in combos:
         F.fsi_batch_set_tuning(ctx, b, ipt, cps)
         p, v = torch.as_tensor(cat.pos).to(dev), torch.as_tensor(cat.vel).to(dev)

@@ -328,9 +328,9 @@ int fsi_batch_step(fsi_ctx *ctx, fsi_batch *batch, double *pos, double *vel,
                    const double *mass, double h, int nsteps, void *stream);
 
 /* Tuning of the batched kernel: active particles per thread -- 1 or 2 (one-sided form,
- * every ordered pair by its receiver), 4 or 8 (symmetric form, every unordered pair once,
- * mixed precision only; blocks of 1024 / 2048 particles, 2 / 1 resident CTAs per SM) --
- * and resident CTAs per SM (0 = occupancy maximum). */
+ * every ordered pair by its receiver), 4, 6 or 8 (symmetric form, every unordered pair
+ * once, mixed precision only; blocks of 1024 / 1536 / 2048 particles, 2 / 2 / 1 resident
+ * CTAs per SM) -- and resident CTAs per SM (0 = occupancy maximum). */
 int fsi_batch_set_tuning(fsi_ctx *ctx, fsi_batch *batch, int ipt, int ctas_per_sm);
 int fsi_batch_get_tuning(fsi_batch *batch, int *ipt, int *ctas_per_sm);
 

@@ -818,6 +818,7 @@ cudaError_t launch_batch_sym(int ipt, int ctas, const BatchArgs& a, const BatchS
                              int sitems_per_phase, const int* nsum, double* accum,
                              cudaStream_t s) {
     if (ipt == kBatchSymI) return launch_batch_sym_i<kBatchSymI, 2>(ctas, a, sitems, sitems_per_phase, nsum, accum, s);
+    if (ipt == kBatchSymI15) return launch_batch_sym_i<kBatchSymI15, 2>(ctas, a, sitems, sitems_per_phase, nsum, accum, s);
     if (ipt == kBatchSymI2) return launch_batch_sym_i<kBatchSymI2, 1>(ctas, a, sitems, sitems_per_phase, nsum, accum, s);
     return cudaErrorInvalidValue;
 }
@@ -836,6 +837,7 @@ static int batch_sym_ctas_i() {
 
 int batch_sym_max_ctas_per_sm(int ipt) {
     if (ipt == kBatchSymI) return batch_sym_ctas_i<kBatchSymI, 2>();
+    if (ipt == kBatchSymI15) return batch_sym_ctas_i<kBatchSymI15, 2>();
     if (ipt == kBatchSymI2) return batch_sym_ctas_i<kBatchSymI2, 1>();
     return 0;
 }

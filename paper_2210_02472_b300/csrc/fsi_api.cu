@@ -1637,7 +1637,7 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
         return offsets[x + 1] - offsets[x] > offsets[y + 1] - offsets[y];
     });
     int rc = FSI_OK;
-    for (int ipt : {1, 2, kBatchSymI, kBatchSymI2}) {
+    for (int ipt : {1, 2, kBatchSymI, kBatchSymI15, kBatchSymI2}) {
         if (rc != FSI_OK) break;
         const int bs = batch_block_size(ipt);
         std::vector<BatchItem> items;
@@ -1656,7 +1656,7 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
              cudaMemcpy(b->nblocks[ipt].p, b->nblocks_h[ipt].data(), (size_t)K * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess))
             rc = fail(FSI_ERR_CUDA, "batch plan upload failed");
     }
-    for (int si : {kBatchSymI, kBatchSymI2}) {
+    for (int si : {kBatchSymI, kBatchSymI15, kBatchSymI2}) {
         if (rc != FSI_OK || c->p.precision != FSI_MIXED) break;
         // symmetric form: per cluster (largest first) and block of 256 si particles, the
         // block's own si tiles, then chunks of kBatchSymChunk source tiles above it
@@ -1711,10 +1711,11 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
 int fsi_batch_destroy(fsi_batch* b) {
     if (!b) return FSI_OK;
     cudaDeviceSynchronize();
-    Buf* bufs[] = {&b->items[1], &b->items[2], &b->items[kBatchSymI], &b->items[kBatchSymI2],
-                   &b->nblocks[1], &b->nblocks[2], &b->nblocks[kBatchSymI], &b->nblocks[kBatchSymI2],
-                   &b->sitems[kBatchSymI], &b->sitems[kBatchSymI2], &b->nsum[kBatchSymI],
-                   &b->nsum[kBatchSymI2], &b->accum, &b->rec0, &b->rec1,
+    Buf* bufs[] = {&b->items[1], &b->items[2], &b->items[kBatchSymI], &b->items[kBatchSymI15],
+                   &b->items[kBatchSymI2], &b->nblocks[1], &b->nblocks[2], &b->nblocks[kBatchSymI],
+                   &b->nblocks[kBatchSymI15], &b->nblocks[kBatchSymI2], &b->sitems[kBatchSymI],
+                   &b->sitems[kBatchSymI15], &b->sitems[kBatchSymI2], &b->nsum[kBatchSymI],
+                   &b->nsum[kBatchSymI15], &b->nsum[kBatchSymI2], &b->accum, &b->rec0, &b->rec1,
                    &b->accrec, &b->ac, &b->done, &b->ctrl, &b->stats};
     for (Buf* x : bufs)
         if (x->p) cudaFree(x->p);
@@ -1725,8 +1726,8 @@ int fsi_batch_destroy(fsi_batch* b) {
 int fsi_batch_set_tuning(fsi_ctx* c, fsi_batch* b, int ipt, int ctas_per_sm) {
     if (!c || !b) return fail(FSI_ERR_ARG, "NULL argument");
     if (ipt != 1 && ipt != 2 && !batch_sym_ipt(ipt))
-        return fail(FSI_ERR_ARG, "batch variant must be 1, 2 (one-sided), %d or %d (symmetric)",
-                    kBatchSymI, kBatchSymI2);
+        return fail(FSI_ERR_ARG, "batch variant must be 1, 2 (one-sided), %d, %d or %d (symmetric)",
+                    kBatchSymI, kBatchSymI15, kBatchSymI2);
     if (batch_sym_ipt(ipt) && c->p.precision != FSI_MIXED)
         return fail(FSI_ERR_ARG, "the symmetric batch form is mixed precision");
     const int mx = std::max(1, batch_sym_ipt(ipt) ? batch_sym_max_ctas_per_sm(ipt)

@@ -377,13 +377,17 @@ cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, c
 // Symmetric persistent ensemble kernel (mixed precision): phases pack, then per pair pass
 // a sum phase (sitems, red.add into accum) and an apply phase (items: epilogue, accum
 // cleared).  nsum: sum items per cluster.
-// ipt: particles per thread, kBatchSymI (2 CTAs per SM) or kBatchSymI2 (1 CTA per SM).
+// ipt: particles per thread, kBatchSymI or kBatchSymI15 (2 CTAs per SM) or kBatchSymI2
+// (1 CTA per SM).
 cudaError_t launch_batch_sym(int ipt, int ctas, const BatchArgs& a, const BatchSymItem* sitems,
                              int sitems_per_phase, const int* nsum, double* accum,
                              cudaStream_t s);
 constexpr int kBatchSymI = 4;      // particles per thread of the symmetric ensemble kernel
-constexpr int kBatchSymI2 = 8;     // its larger-block variant
-inline bool batch_sym_ipt(int ipt) { return ipt == kBatchSymI || ipt == kBatchSymI2; }
+constexpr int kBatchSymI15 = 6;    // its larger-block variants
+constexpr int kBatchSymI2 = 8;
+inline bool batch_sym_ipt(int ipt) {
+    return ipt == kBatchSymI || ipt == kBatchSymI15 || ipt == kBatchSymI2;
+}
 int batch_sym_max_ctas_per_sm(int ipt);
 int batch_block_size(int ipt);
 int batch_max_ctas_per_sm(int precision, int ipt);

@@ -36,11 +36,11 @@ def ens_large():
 
 
 @pytest.mark.parametrize("prec", ["fp64", "mixed"])
-@pytest.mark.parametrize("ipt", [1, 2, 4, 8])
+@pytest.mark.parametrize("ipt", [1, 2, 4, 6, 8])
 @pytest.mark.parametrize("which", ["small", "large"])
 def test_batch_matches_oracle_per_cluster(F, ens, ens_large, prec, ipt, which):
-    """ipt 1, 2: one-sided form; 4, 8: symmetric form with blocks of 1024 / 2048 particles
-    (mixed precision only)."""
+    """ipt 1, 2: one-sided form; 4, 6, 8: symmetric form with blocks of 1024 / 1536 / 2048
+    particles (mixed precision only)."""
     if ipt >= 4 and prec == "fp64":
         pytest.skip("the symmetric batch form is mixed precision")
     if which == "large" and ipt < 4:
@@ -64,7 +64,7 @@ def test_batch_matches_oracle_per_cluster(F, ens, ens_large, prec, ipt, which):
     assert np.abs(v - rv).max() <= tol * 100 * np.abs(rv).max()
 
 
-@pytest.mark.parametrize("ipt", [1, 4, 8])
+@pytest.mark.parametrize("ipt", [1, 4, 6, 8])
 def test_batch_graph_capture_replays(F, ens, ipt):
     cat, off = ens
     h = 1e-3

@@ -440,8 +440,8 @@ def test_pn_accel_pairs(F, lists):
     """PN1.0 pair accelerations through the black-hole sublists against the oracle: all
     particles, overlapping id lists (self pairs skipped by id), receivers a slice of the
     sources' memory, disjoint lists."""
-    n = 500
-    c = inputs.plummer(n, 20, imf="kroupa", n_bh=5)
+    c = inputs.plummer(500, 20, imf="kroupa", n_bh=5)      # 505 particles, 500..504 black holes
+    n = c.n
     bh = np.nonzero(c.is_bh)[0]
     A = B = None
     if lists != "all":
