@@ -354,6 +354,21 @@ def test_hhs_all_slow_is_two_half_steps():
     assert counts[0] == c.n and counts[1:].sum() == 0
 
 
+def test_hhs_depth_cap_zero_is_two_half_steps():
+    """max_level = 0: the top level keeps every particle in S whatever its step (the depth
+    cap), so the interval is FSI(all, tau/2) twice and reports the cap."""
+    c = inputs.plummer(64, 25, imf="kroupa")
+    tau = 1.0 / 8
+    _, _, counts0, code0 = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    assert counts0[1:].sum() > 0                      # uncapped, the set splits
+    p, v, counts, code = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, max_level=0,
+                                             allow_maxlevel=True)
+    p2, v2 = oracle.fsi_step(c.pos, c.vel, c.mass, tau / 2, steps=2)
+    assert code == oracle.ERR_MAXLEVEL and code0 == oracle.OK
+    assert np.array_equal(p, p2) and np.array_equal(v, v2)
+    assert counts[0] == c.n
+
+
 def test_hhs_momentum_conserved_and_levels():
     c = inputs.plummer(96, 24, imf="kroupa")
     tau = 1.0 / 16

@@ -656,6 +656,34 @@ def test_hhs_interval_morton_ordered_levels(F):
     assert np.abs(v - rv).max() <= 1e-5
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("small", [0, -1])
+def test_hhs_interval_depth_cap(F, prec, small):
+    """The HHS depth cap (a particle that wants a level below max_level stays in S at
+    max_level): the interval completes, returns FSI_ERR_MAXLEVEL, and matches the oracle's
+    capped interval, in the host walk and the one-CTA recursion."""
+    c = inputs.plummer(600, 22, imf="kroupa")
+    tau = 1.0 / 16
+    _, _, counts_free, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    cap = 2
+    assert np.nonzero(counts_free)[0].max() > cap          # the hierarchy is deeper
+    rp, rv, counts, code = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, max_level=cap,
+                                               allow_maxlevel=True)
+    assert code == oracle.ERR_MAXLEVEL
+    with F.Context(prec, max_level=cap, hhs_small_max=small) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_ERR_MAXLEVEL
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert len(lv) <= cap + 1
+    assert lv == list(counts[:len(lv)])
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
+
+
 RESTART_CASES = {
     # name: (N, seed, tau, tolerance or None (between attempts 1 and 2), max_restarts, etas)
     "halve": (300, 28, 1 / 16, None, 8, dict(eta_grad=0.1, eta_va=0.2)),
