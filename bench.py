@@ -49,13 +49,14 @@ FP32_LANES, SM_MAX_MHZ = 128, 2032.0      # FP32 lanes per SM; B300 maximum SM c
 FP64_FLOP_PER_SM_CLK = 4
 CPU_ROWS = 4096
 # DRAM bytes (dram__bytes_read.sum + dram__bytes_write.sum) per launch of the dominant
-# kernel, from one one-pass ncu capture of this benchmark's own workload (`--tuning A,G
-# --steps 1 --warmup 3` with the kernel's variant, mean of the cycle's three acceleration
-# launches).  Keyed by
+# kernel (per pass: both kernels of a pass that takes two), from one one-pass ncu capture
+# of this benchmark's own workload (`--tuning A,G --steps 1 --warmup 3` with the kernel's
+# variant, mean of the cycle's three acceleration passes).  Keyed by
 # (kernel label, workload, N); a kernel changed since the capture must drop its entry, and
 # any other configuration reports null.
 DRAM_TRAFFIC = {("sym_mixed_v2_kernel<acc, I=5, far>", "kroupa1m_bh16", 1048592): 201.9e6,
-                ("sym_mixed_x2_kernel<acc, I=8, MINB=1>", "kroupa1m_bh16", 1048592): 236.9e6}
+                ("sym_mixed_x2_kernel<acc, I=8, MINB=1> + sym_diag_ff_kernel", "kroupa1m_bh16",
+                 1048592): 301.0e6}
 
 
 def step_interactions(n: int) -> float:
@@ -387,8 +388,13 @@ def run_fsi(args):
     peak_mhz = clocks.get("sm_max_mhz") or SM_MAX_MHZ
     peak = fp32_peak_tflops(sms, peak_mhz) if args.precision == "mixed" else fp64_peak_tflops(sms, peak_mhz)
     var = tuning[0 if dom == "acc" else 1]
-    if var & 128:
+    if var & 128 and var & 512:
+        kname = f"sym_mixed_x2_kernel<{dom}, I={var & 15}, MINB=1, NT=384>"
+    elif var & 128:
         kname = f"sym_mixed_x2_kernel<{dom}, I={var & 15}, MINB={1 if var & 16 else 2}>"
+    if var & 128 and dom == "acc" and args.precision == "mixed" and N >= 196608:
+        # the pass's time includes the float-float kernel of the pairs inside each i-block
+        kname += " + sym_diag_ff_kernel"
     elif var & 32:
         kname = f"sym_mixed_v2_kernel<{dom}, I={var & 15}{', far' if var & 64 else ''}>"
     else:

@@ -39,9 +39,12 @@
  *             the pair arithmetic (r^-3, gradient terms) is FP32 with one residual
  *             correction of the hardware rsqrt; a receiver's FP32 partial sums run over
  *             at most 32 sources and are accumulated as float-float pairs (TwoSum).
- *             Relative acceleration error |da_i| / |a_i| at N = 2^20: median 2e-8, 99th
- *             percentile 1e-7 (larger where the pair terms cancel, |a_i| << sum_j
- *             m_j / r_ij^2).  Valid for separations > ~1e-7 (FP32 range of r^-5).
+ *             Sets of >= 196608 particles take the pairs inside each i-block (each
+ *             particle's nearest neighbours in Morton order) in float-float arithmetic
+ *             in their acceleration passes.  Relative acceleration error |da_i| / |a_i|
+ *             at N = 2^20: median 2e-8, 99.9th percentile 1e-7 (larger where the pair
+ *             terms cancel, |a_i| << sum_j m_j / r_ij^2).  Valid for separations > ~1e-7
+ *             (FP32 range of r^-5).
  */
 #ifndef LIBFSI_FSI_H
 #define LIBFSI_FSI_H

@@ -274,9 +274,10 @@ struct SameSetOrder {
 
 // Source tiles per work item of the symmetric kernel: about 8 items per resident CTA
 // slot, at most 64 tiles each.
-int choose_chunk(const fsi_ctx* c, int n, int ipt) {
+int choose_chunk(const fsi_ctx* c, int n, int variant) {
     const long long ntj = (n + kTileJ - 1) / kTileJ;
-    const long long nb = (n + (long long)kThreads * ipt - 1) / ((long long)kThreads * ipt);
+    const long long bp = sym_block_particles(variant);
+    const long long nb = (n + bp - 1) / bp;
     const long long visits = nb * ntj / 2 + 1;
     const long long want = 8LL * 2 * c->sm_count;
     long long ch = visits / want;
@@ -407,7 +408,7 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
         const int sv = c->symv[prec][kind][sym_class(n)];
         CK(ensure(c->accum, 3 * (size_t)n * sizeof(double)));
         CU(cudaMemsetAsync(c->accum.p, 0, 3 * (size_t)n * sizeof(double), s));
-        const int chunk = choose_chunk(c, n, variant_ipt(sv));
+        const int chunk = choose_chunk(c, n, sv);
         a.err = c->err_d;
         a.timeout_ns = budget(c);
         SymFar far{};
@@ -424,9 +425,18 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
             far.stats = P<unsigned long long>(c->farstats);
             farp = &far;
         }
+        // mixed acceleration passes of the largest size class: the pairs inside each
+        // i-block (each particle's nearest neighbours in Morton order) in float-float
+        // arithmetic by their own kernel, which keeps the relative acceleration error of
+        // every particle within ~1e-7
+        const bool ff_diag = prec == FSI_MIXED && kind == KIND_ACC && (sv & 128) &&
+                             n >= kSymClassMin[2];
         CK(timed(c, kind, s, [&] {
-            return launch_sym_pair(prec, kind, sv, a.irec, a.iacc, n, a.eps2, chunk,
-                                   P<double>(c->accum), a.err, a.timeout_ns, farp, s);
+            cudaError_t e = launch_sym_pair(prec, kind, sv, a.irec, a.iacc, n, a.eps2, chunk,
+                                            P<double>(c->accum), a.err, a.timeout_ns, farp, s, ff_diag);
+            if (e == cudaSuccess && ff_diag)
+                e = launch_sym_diag_ff(a.irec, n, sym_block_particles(sv), a.eps2, P<double>(c->accum), s);
+            return e;
         }));
         a.part = P<double>(c->accum);
         CK(timed(c, 2, s, [&] { return launch_finalize_p(prec, a, 1, s); }));

@@ -256,9 +256,16 @@ struct SymFar {
     float k2;
     unsigned long long* stats;
 };
+// skip_diag (packed form only): the blocks' own pairs are left out, for launch_sym_diag_ff.
 cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
                             int n, double eps2, int chunk, double* accum, int* err,
-                            long long timeout_ns, const SymFar* far, cudaStream_t s);
+                            long long timeout_ns, const SymFar* far, cudaStream_t s,
+                            bool skip_diag = false);
+// The pairs inside each block of bsz consecutive members of a mixed-precision set
+// (records rec, n members), each member's sum over its block's other members in
+// float-float arithmetic, added into accum (3 x n).
+cudaError_t launch_sym_diag_ff(const void* rec, int n, int bsz, double eps2, double* accum,
+                               cudaStream_t s);
 // Supported ipt values for (precision, kind): writes up to 16 into out, returns the count.
 int pair_variants(int precision, int kind, int* out);
 int pair_default_ipt(int precision, int kind);
@@ -266,6 +273,8 @@ int pair_default_ipt(int precision, int kind);
 // mixed second form (FP64 sums in shared memory, select-free reduce-scatter).
 int sym_variants(int precision, int kind, int* out);
 int variant_ipt(int variant);
+// Particles per i-block of a symmetric variant (threads per CTA x particles per thread).
+int sym_block_particles(int variant);
 
 // Spatial ordering and far-tile inputs (order_kernels.cu).
 size_t morton_workspace_bytes(int n);

@@ -586,6 +586,7 @@ struct SymArgs {
     const float4* sub;
     float far_k2;
     unsigned long long* far_stats;
+    int skip_diag;      // packed form: the blocks' own pairs are left to sym_diag_ff_kernel
 };
 
 
@@ -1294,21 +1295,23 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
 //    half rounds exactly as the scalar code does; only the order of the j-side sums
 //    differs.
 
-template <int KIND, int I, int MINB>
-__global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymArgs a) {
-    static_assert(kThreads == kTileJ, "an i-block spans I source tiles");
+template <int KIND, int I, int MINB, int NT>
+__global__ void __launch_bounds__(NT, MINB) sym_mixed_x2_kernel(const SymArgs a) {
+    static_assert((NT * I) % kTileJ == 0 && NT >= kTileJ && NT % 32 == 0,
+                  "an i-block spans whole source tiles");
     static_assert(I % 2 == 0, "particles are handled in packed pairs");
+    constexpr int BT = NT * I / kTileJ;                 // source tiles per i-block
     constexpr int NP = I / 2;
     constexpr int ACCREC = SymCfg<FSI_MIXED, KIND>::ACCREC;
     constexpr int RELB = 16;
     constexpr int SUBB = (kTileJ / 32) * 16;
     constexpr int SB = kTileJ * (kRec + ACCREC + RELB) + SUBB;
-    constexpr int JPART = SymCfg<FSI_MIXED, KIND>::JPART;
+    constexpr int JPART = (NT / 32) * kTileJ * 3 * (int)sizeof(float);
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ __align__(8) uint64_t bars[kStages];
-    __shared__ float wbox[kThreads / 32][6];
+    __shared__ float wbox[NT / 32][6];
     float* jpart = reinterpret_cast<float*>(smem + kStages * SB);
-    // i-side sums across tiles as float-float pairs: acc_s[(p * 3 + q) * kThreads + tid] =
+    // i-side sums across tiles as float-float pairs: acc_s[(p * 3 + q) * NT + tid] =
     // (hi of 2p, hi of 2p+1, lo of 2p, lo of 2p+1) for component q
     float4* acc_s = reinterpret_cast<float4*>(smem + kStages * SB + JPART);
 
@@ -1317,12 +1320,12 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
     const int ntj = (a.n + kTileJ - 1) / kTileJ;
     const bool diag = (c == 0);
     int t0, t1;
-    if (diag) { t0 = b * I; t1 = min((b + 1) * I, ntj); }
-    else { t0 = (b + 1) * I + (c - 1) * a.chunk; t1 = min(t0 + a.chunk, ntj); }
-    if (t0 >= t1) return;
+    if (diag) { t0 = b * BT; t1 = min((b + 1) * BT, ntj); }
+    else { t0 = (b + 1) * BT + (c - 1) * a.chunk; t1 = min(t0 + a.chunk, ntj); }
+    if (t0 >= t1 || (diag && a.skip_diag)) return;
     const int ntiles = t1 - t0;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int i0 = b * (kThreads * I);
+    const int i0 = b * (NT * I);
     const bool far_on = a.rel != nullptr && !diag;
 
     if (tid == 0) {
@@ -1381,7 +1384,7 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
     for (int p = 0; p < NP; ++p) {
         f[p][0] = f[p][1] = f[p][2] = make_float2(0.f, 0.f);
 #pragma unroll
-        for (int q = 0; q < 3; ++q) acc_s[(p * 3 + q) * kThreads + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int q = 0; q < 3; ++q) acc_s[(p * 3 + q) * NT + tid] = make_float4(0.f, 0.f, 0.f, 0.f);
     }
     if (far_on) {
         // box of the warp's particles (FP32 high parts)
@@ -1456,7 +1459,7 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
                     for (int p = 0; p < NP; ++p)
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            ff_add2(acc_s[(p * 3 + q) * kThreads + tid], make_float2(fs[2 * p][q], fs[2 * p + 1][q]));
+                            ff_add2(acc_s[(p * 3 + q) * NT + tid], make_float2(fs[2 * p][q], fs[2 * p + 1][q]));
                             fs[2 * p][q] = fs[2 * p + 1][q] = 0.f;
                         }
                 }
@@ -1506,7 +1509,7 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
                     for (int p = 0; p < NP; ++p)
 #pragma unroll
                         for (int q = 0; q < 3; ++q) {
-                            ff_add2(acc_s[(p * 3 + q) * kThreads + tid], f[p][q]);
+                            ff_add2(acc_s[(p * 3 + q) * NT + tid], f[p][q]);
                             f[p][q] = make_float2(0.f, 0.f);
                         }
                 }
@@ -1518,7 +1521,7 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
             for (int q = 0; q < 3; ++q) {
                 float sum = 0.f;
 #pragma unroll
-                for (int w = 0; w < kThreads / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
+                for (int w = 0; w < NT / 32; ++w) sum += jpart[((size_t)w * kTileJ + tid) * 3 + q];
                 red_add(a.accum + (size_t)q * a.n + jt + tid, (double)sum);
             }
         }
@@ -1544,11 +1547,148 @@ __global__ void __launch_bounds__(kThreads, MINB) sym_mixed_x2_kernel(const SymA
 #pragma unroll
         for (int q = 0; q < 3; ++q)
         {
-            const float4 v = acc_s[((u >> 1) * 3 + q) * kThreads + tid];
+            const float4 v = acc_s[((u >> 1) * 3 + q) * NT + tid];
             const double sum = (u & 1) ? (double)v.y + (double)v.w : (double)v.x + (double)v.z;
             red_add(a.accum + (size_t)q * a.n + ib + 32 * u, sum);
         }
     }
+}
+
+// =================================================================================
+// The pairs inside each i-block of a packed symmetric acceleration pass (the block's own
+// tiles: in Morton order, each particle's nearest neighbours), evaluated in float-float
+// arithmetic on the FP32 pipe instead of plain FP32.  The nearest terms carry most of the
+// mixed path's rounding error: with them accurate the relative acceleration error of the
+// whole sum stays within ~1e-7 (the remaining terms' FP32 roundings are independent and
+// small).  Each receiver sums its block's other members one-sided; separations, r^2, the
+// r^-3 factor and the products are float-float pairs (TwoSum / exact FMA products), the
+// reciprocal square root refined from the hardware seed to first order in its residual
+// e (e^2 ~ 2^-44 dropped); the source mass is the record's FP32 value (0.4 x 2.5 m).  The
+// block's totals are added to the pass's FP64 accumulator.
+__device__ __forceinline__ void ff_two_sum(float a, float b, float& s, float& e) {
+    s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+__device__ __forceinline__ void ff_two_prod(float a, float b, float& p, float& e) {
+    p = __fmul_rn(a, b);
+    e = fmaf(a, b, -p);
+}
+
+// Float-float term m_j d / r^3 of source (h, l) on receiver (xh, xl) into (ah, al).
+__device__ __forceinline__ void ff_acc_pair(const float4 h, const float4 l, const float (&xh)[3],
+                                            const float (&xl)[3], float eps2,
+                                            float (&ah)[3], float (&al)[3]) {
+    const float hj[3] = {h.x, h.y, h.z}, lj[3] = {l.x, l.y, l.z};
+    float d[3], dt[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float a, ae;
+        ff_two_sum(hj[q], -xh[q], a, ae);
+        const float b = __fadd_rn(__fsub_rn(lj[q], xl[q]), ae);
+        ff_two_sum(a, b, d[q], dt[q]);
+    }
+    // r^2 = |d + dt|^2 + eps2 as (r2h, r2l)
+    float px, ex, py, ey, pz, ez;
+    ff_two_prod(d[0], d[0], px, ex);
+    ff_two_prod(d[1], d[1], py, ey);
+    ff_two_prod(d[2], d[2], pz, ez);
+    float s1, e1, s2, e2, s3, e3;
+    ff_two_sum(px, py, s1, e1);
+    ff_two_sum(s1, pz, s2, e2);
+    ff_two_sum(s2, eps2, s3, e3);
+    const float cross = 2.0f * fmaf(d[0], dt[0], fmaf(d[1], dt[1], d[2] * dt[2]));
+    const float low = ((e1 + e2) + (e3 + ex)) + ((ey + ez) + cross);
+    float r2h, r2l;
+    ff_two_sum(s3, low, r2h, r2l);
+    // r^-3 = y0^3 (1 - e)^{-3/2} ~ y0^3 (1 + 1.5 e), e = 1 - r^2 y0^2 formed accurately
+    const float y0 = rsqrt_hw(r2h);
+    float t, te;
+    ff_two_prod(y0, y0, t, te);
+    float qh, qe;
+    ff_two_prod(r2h, t, qh, qe);
+    const float ql = fmaf(r2h, te, fmaf(r2l, t, qe));
+    const float e = __fsub_rn(__fsub_rn(1.0f, qh), ql);
+    float c3, c3e;
+    ff_two_prod(t, y0, c3, c3e);
+    c3e = fmaf(te, y0, c3e);
+    // (c3 + c3e)(1 + 1.5 e) = c3 + (c3e + 1.5 e c3)
+    const float r3l = fmaf(1.5f * e, c3, c3e);
+    // w = m (c3 + r3l)
+    const float m = 0.4f * h.w;
+    float wh, we;
+    ff_two_prod(m, c3, wh, we);
+    we = fmaf(m, r3l, we);
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+        float th, tl;
+        ff_two_prod(wh, d[q], th, tl);
+        tl = fmaf(wh, dt[q], fmaf(we, d[q], tl));
+        float sh, se;
+        ff_two_sum(ah[q], th, sh, se);
+        ah[q] = sh;
+        al[q] = __fadd_rn(al[q], __fadd_rn(se, tl));
+    }
+}
+
+// CTA (x, y) of a grid over blocks of `bsz` consecutive members of a set of n (records
+// `rec`): the members r = block start + y RPT kThreads + tid + kThreads k (k < RPT) each
+// sum the other members of their block, added into accum (3 x n); sources staged through
+// shared memory in tiles.
+constexpr int kDiagFfRpt = 4;                           // receivers per thread
+__global__ void __launch_bounds__(kThreads) sym_diag_ff_kernel(const RecMix* __restrict__ rec, int n,
+                                                               int bsz, float eps2,
+                                                               double* __restrict__ accum) {
+    constexpr int RPT = kDiagFfRpt;
+    __shared__ RecMix src[kTileJ];
+    const int b0 = blockIdx.x * bsz;
+    const int b1 = min(n, b0 + bsz);
+    {
+        const int r0 = b0 + (int)blockIdx.y * RPT * kThreads;
+        if (r0 >= b1) return;                           // uniform: before any barrier
+        float xh[RPT][3], xl[RPT][3], ah[RPT][3], al[RPT][3];
+        int me[RPT];
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            me[u] = r0 + u * kThreads + threadIdx.x;
+            const RecMix r = rec[min(me[u], b1 - 1)];
+            xh[u][0] = r.hi.x; xh[u][1] = r.hi.y; xh[u][2] = r.hi.z;
+            xl[u][0] = r.lo.x; xl[u][1] = r.lo.y; xl[u][2] = r.lo.z;
+#pragma unroll
+            for (int q = 0; q < 3; ++q) ah[u][q] = al[u][q] = 0.f;
+        }
+        for (int j0 = b0; j0 < b1; j0 += kTileJ) {
+            const int cnt = min(kTileJ, b1 - j0);
+            __syncthreads();
+            if ((int)threadIdx.x < cnt) src[threadIdx.x] = rec[j0 + threadIdx.x];
+            __syncthreads();
+            for (int jj = 0; jj < cnt; ++jj) {
+                const float4 h = src[jj].hi, l = src[jj].lo;
+#pragma unroll
+                for (int u = 0; u < RPT; ++u)
+                    if (j0 + jj != me[u]) ff_acc_pair(h, l, xh[u], xl[u], eps2, ah[u], al[u]);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < RPT; ++u) {
+            if (me[u] >= b1) continue;
+#pragma unroll
+            for (int q = 0; q < 3; ++q)
+                red_add(accum + (size_t)q * n + me[u], (double)ah[u][q] + (double)al[u][q]);
+        }
+    }
+}
+
+cudaError_t launch_sym_diag_ff(const void* rec, int n, int bsz, double eps2, double* accum,
+                               cudaStream_t s) {
+    if (n <= 0 || bsz <= 0) return cudaSuccess;
+    const int nb = (n + bsz - 1) / bsz;
+    const int sweeps = (bsz + kDiagFfRpt * kThreads - 1) / (kDiagFfRpt * kThreads);
+    const dim3 grid((unsigned)nb, (unsigned)sweeps);
+    { sym_diag_ff_kernel<<<grid, kThreads, 0, s>>>(reinterpret_cast<const RecMix*>(rec), n, bsz,
+                                                   (float)eps2, accum); note_launch(); }
+    return cudaGetLastError();
 }
 
 // =================================================================================
@@ -1964,21 +2104,27 @@ cudaError_t launch_cross_pair(int precision, int kind, const void* irec, const v
 
 // MINB: resident CTAs per SM the register budget is sized for (2: 128 registers per
 // thread, 1: 255).
-template <int KIND, int I, int MINB>
-static cudaError_t launch_sym_x2(const SymArgs& a, cudaStream_t s) {
+template <int KIND, int I, int MINB, int NT = kThreads>
+static cudaError_t launch_sym_x2(SymArgs a, cudaStream_t s) {
     constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + 16) + (kTileJ / 32) * 16;
-    constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + I * 3 * kThreads * (int)sizeof(double);
+    constexpr int JPART = (NT / 32) * kTileJ * 3 * (int)sizeof(float);
+    constexpr int SMEM = kStages * SB + JPART + I * 3 * NT * (int)sizeof(double);
     static bool attr_set = false;
     if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sym_mixed_x2_kernel<KIND, I, MINB>,
+        cudaError_t e = cudaFuncSetAttribute(sym_mixed_x2_kernel<KIND, I, MINB, NT>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
         if (e != cudaSuccess) return e;
         attr_set = true;
     }
-    const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
+    // work items per i-block: its own tiles, then chunks of the tiles above it
+    constexpr int BT = NT * I / kTileJ;
+    const int ntj = (a.n + kTileJ - 1) / kTileJ;
+    const int above = ntj > BT ? ntj - BT : 0;
+    a.nchunk = (above + a.chunk - 1) / a.chunk;
+    const int nb = (a.n + NT * I - 1) / (NT * I);
     const long long grid = (long long)nb * (1 + a.nchunk);
     if (grid > 2147483647LL) return cudaErrorInvalidValue;
-    { sym_mixed_x2_kernel<KIND, I, MINB><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
+    { sym_mixed_x2_kernel<KIND, I, MINB, NT><<<(unsigned)grid, NT, SMEM, s>>>(a); note_launch(); }
     return cudaGetLastError();
 }
 
@@ -2031,11 +2177,12 @@ static cudaError_t launch_sym_ipt(int ipt, const SymArgs& a, cudaStream_t s) {
 
 cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
                             int n, double eps2, int chunk, double* accum, int* err,
-                            long long timeout_ns, const SymFar* far, cudaStream_t s) {
+                            long long timeout_ns, const SymFar* far, cudaStream_t s, bool skip_diag) {
     if (n <= 0) return cudaSuccess;
     SymArgs a{};
     a.rec = rec; a.accrec = accrec; a.n = n; a.eps2 = eps2; a.accum = accum; a.err = err;
     a.timeout_ns = timeout_ns;
+    a.skip_diag = skip_diag && precision == FSI_MIXED && (ipt & 128) ? 1 : 0;
     if (far && (ipt & 64)) {
         a.rel = reinterpret_cast<const float4*>(far->rel);
         a.sub = reinterpret_cast<const float4*>(far->sub);
@@ -2047,6 +2194,16 @@ cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, c
     a.chunk = chunk > 0 ? chunk : 1;
     const int above = ntj > I ? ntj - I : 0;       // most tiles above any block (block 0)
     a.nchunk = (above + a.chunk - 1) / a.chunk;
+    if (precision == FSI_MIXED && (ipt & 128) && (ipt & 512)) {
+        // packed form with CTAs of 384 threads (12 warps per SM, ~170 registers)
+        switch (I * 2 + kind) {
+            case 4 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 4, 1, 384>(a, s);
+            case 4 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 4, 1, 384>(a, s);
+            case 6 * 2 + KIND_ACC: return launch_sym_x2<KIND_ACC, 6, 1, 384>(a, s);
+            case 6 * 2 + KIND_GRAD: return launch_sym_x2<KIND_GRAD, 6, 1, 384>(a, s);
+            default: return cudaErrorInvalidValue;
+        }
+    }
     if (precision == FSI_MIXED && (ipt & 128)) {
         // packed form; bit 16 selects the one-CTA-per-SM register budget
         switch ((ipt & 16 ? 64 : 0) + I * 2 + kind) {
@@ -2152,6 +2309,8 @@ int sym_variants(int precision, int kind, int* out) {
         out[n++] = 224 + 6;
         out[n++] = 240 + 6;     // one CTA per SM (255 registers)
         out[n++] = 240 + 8;
+        out[n++] = 752 + 4;     // one CTA of 384 threads per SM (~170 registers)
+        out[n++] = 752 + 6;
     } else {
         out[n++] = 1; out[n++] = 2; out[n++] = 3;
     }
@@ -2163,6 +2322,8 @@ int pair_default_ipt(int precision, int kind) {
 }
 
 int variant_ipt(int v) { return v & 15; }
+
+int sym_block_particles(int v) { return ((v & 128) && (v & 512) ? 384 : kThreads) * (v & 15); }
 
 cudaError_t launch_pair(int precision, int kind, int ipt, const PairArgs& a, int split,
                         cudaStream_t s) {

@@ -255,7 +255,8 @@ def test_every_variant_against_oracle(F, prec, n):
     cases = [("one-sided", dict(symmetric=False, wide_ctas=-1), None),
              ("wide", dict(wide_ctas=1 << 30), None)]
     sym = ((2, 2), (3, 3), (4, 4), (36, 36), (37, 37), (38, 37), (226, 226), (228, 228),
-           (230, 230), (246, 246), (248, 248)) if prec == "mixed" else ((1, 1), (2, 2), (3, 3))
+           (230, 230), (246, 246), (248, 248), (756, 756), (758, 758)) if prec == "mixed" \
+        else ((1, 1), (2, 2), (3, 3))
     one = ((2, 2), (3, 3), (4, 4), (18, 18), (36, 36)) if prec == "mixed" else ((1, 1), (2, 2), (3, 3))
     cases += [(f"symmetric {v}", dict(wide_ctas=-1), v) for v in sym]
     cases += [(f"one-sided {v}", dict(symmetric=False, wide_ctas=-1), v) for v in one]
@@ -775,12 +776,13 @@ def test_full_size_mixed_acc_sampled_rows(F, big):
         got = host(F.fsi_accel(ctx, dev(big.pos), dev(big.mass)))
         assert F.fsi_sync_status(ctx) == F.FSI_OK
     assert_close(got[:, rows], ref, "mixed", scale=abs_scale(big.pos, big.mass, rows))
-    # the relative acceleration error |da| / |a| of the mixed path at this size, measured on
-    # 4096 rows: median 2.0e-8, 99th percentile 9.2e-8, 99.9th 2.3e-7, maximum 5.0e-7
-    # (0.8 % of the rows above 1e-7); held to about twice that
+    # the relative acceleration error |da| / |a| of the mixed path at this size (the pairs
+    # inside each i-block in float-float arithmetic), measured on 4096 rows: median
+    # 1.8e-8, 99th percentile 6.1e-8, 99.9th 1.0e-7, maximum 1.7e-7 (0.12 % of the rows
+    # above 1e-7; variant 230: 99.9th 1.7e-7, maximum 2.6e-7); held to about twice that
     d = np.linalg.norm(got[:, rows] - ref, axis=0) / np.linalg.norm(ref, axis=0)
-    assert np.median(d) <= 4e-8 and np.percentile(d, 99) <= 2e-7 and d.max() <= 1e-6, \
-        (np.median(d), np.percentile(d, 99), d.max())
+    assert np.median(d) <= 4e-8 and np.percentile(d, 99) <= 1.2e-7 and d.max() <= 5e-7 \
+        and np.mean(d > 1e-7) <= 0.01, (np.median(d), np.percentile(d, 99), d.max())
 
 
 @pytest.mark.parametrize("prec", PRECS)
