@@ -1441,7 +1441,7 @@ __global__ void __launch_bounds__(NT, MINB) sym_mixed_x2_kernel(const SymArgs a)
                 q[u].az = -(hi ? s.naz.y : s.naz.x);
                 fs[u][0] = fs[u][1] = fs[u][2] = 0.f;
             }
-            for (int jj = 0; jj < cnt; ++jj) {
+            auto own_pair = [&](int jj) {
                 const float4 h = rec[jj].hi;
                 const float4 l = rec[jj].lo;
                 if constexpr (KIND == KIND_ACC) {
@@ -1454,14 +1454,28 @@ __global__ void __launch_bounds__(NT, MINB) sym_mixed_x2_kernel(const SymArgs a)
                     for (int u = 0; u < I; ++u)
                         mix_grad_pair<true>(h, l, aj, q[u], eps2f, jt + jj == ib + 32 * u, fs[u][0], fs[u][1], fs[u][2]);
                 }
-                if ((jj & (kSymFlushJ - 1)) == kSymFlushJ - 1 || jj == cnt - 1) {
+            };
+            auto own_flush = [&]() {
 #pragma unroll
-                    for (int p = 0; p < NP; ++p)
+                for (int p = 0; p < NP; ++p)
 #pragma unroll
-                        for (int q = 0; q < 3; ++q) {
-                            ff_add2(acc_s[(p * 3 + q) * NT + tid], make_float2(fs[2 * p][q], fs[2 * p + 1][q]));
-                            fs[2 * p][q] = fs[2 * p + 1][q] = 0.f;
-                        }
+                    for (int q = 0; q < 3; ++q) {
+                        ff_add2(acc_s[(p * 3 + q) * NT + tid], make_float2(fs[2 * p][q], fs[2 * p + 1][q]));
+                        fs[2 * p][q] = fs[2 * p + 1][q] = 0.f;
+                    }
+            };
+            if constexpr (I <= 4) {
+                // few particles per thread: runs of kSymFlushJ sources as an inner loop
+                for (int k0 = 0; k0 < cnt; k0 += kSymFlushJ) {
+                    const int kend = min(cnt, k0 + kSymFlushJ);
+                    for (int jj = k0; jj < kend; ++jj) own_pair(jj);
+                    own_flush();
+                }
+            } else {
+                // (the nested form spills at 6 and 8 particles per thread)
+                for (int jj = 0; jj < cnt; ++jj) {
+                    own_pair(jj);
+                    if ((jj & (kSymFlushJ - 1)) == kSymFlushJ - 1 || jj == cnt - 1) own_flush();
                 }
             }
         } else {
