@@ -672,7 +672,8 @@ def run_hhs(args):
     tau = SOFT_TAU if soft else args.tau
     kw = dict(eps2=SOFT_EPS ** 2, eta_ff=0.2, eta_fb=0.2, eta_jerk=0.1, eta_grad=0.1) if soft else {}
     ctx = F.Context(args.precision, c=cl, wide_ctas=args.wide_ctas,
-                    hhs_small_max=args.hhs_small_max, order_min=args.order_min, **kw)
+                    hhs_small_max=args.hhs_small_max, order_min=args.order_min,
+                    hhs_grid_max=args.hhs_grid_max, **kw)
     if args.tuning:
         F.fsi_set_tuning(ctx, *[int(v) for v in args.tuning.split(",")])
     energy = lambda: float(F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum())
@@ -705,6 +706,7 @@ def run_hhs(args):
         "data": "synthetic",
         "config": {"workload": wl, "n": c.n, "tau": tau, "intervals": args.intervals, "c": cl,
                    "wide_ctas": args.wide_ctas, "hhs_small_max": args.hhs_small_max,
+                   "hhs_grid_max": args.hhs_grid_max,
                    "order_min": args.order_min,
                    "tuning": args.tuning or "default",
                    **({"eps2": SOFT_EPS ** 2, "eta": "ff 0.2, fb 0.2, jerk 0.1, gradient 0.1",
@@ -981,6 +983,7 @@ def main():
                     "(0 = 32, -1 = tiled passes only)")
     ap.add_argument("--hhs-small-max", type=int, default=0, help="HHS mode: fsi_params.hhs_small_max")
     ap.add_argument("--order-min", type=int, default=0, help="HHS mode: fsi_params.order_min")
+    ap.add_argument("--hhs-grid-max", type=int, default=0, help="HHS mode: fsi_params.hhs_grid_max")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

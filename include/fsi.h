@@ -117,6 +117,13 @@ typedef struct fsi_params {
                              fewer CTAs than this takes the wide form instead: up to 32
                              lanes per receiver splitting its sources (0 = 32; -1 =
                              never).  Only the summation order differs. */
+    int hhs_grid_max;     /* HHS with PN off: a fast set of more than hhs_small_max and at
+                             most this many particles (0 = 4096; -1 = never) runs its whole
+                             recursion in one cooperative launch over the GPU, and an
+                             interval of N <= hhs_grid_max particles is that one launch
+                             (no host synchronisation, so it can be captured in a CUDA
+                             graph; see fsi_hhs_interval).  Only summation orders differ
+                             from the host walk. */
 } fsi_params;
 
 /* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,
@@ -423,6 +430,15 @@ int fsi_profile(fsi_ctx *ctx, int enable);
  * 1 = gradient pass, 2 = split-finalize), the number of launches and their summed device
  * milliseconds, then clear the record.  launches: host long long[3], ms: host double[3]. */
 int fsi_profile_read(fsi_ctx *ctx, long long *launches, double *ms);
+
+/* Phase profile of the HHS recursions run in one cooperative launch (recorded while
+ * fsi_profile is on): per phase kind (0 time steps, 1 split, 2 inter-level kick, 3 FSI
+ * pass of the slow set, 4 one-CTA recursion of a small fast set, 5 gradient time-step
+ * criteria, 6 set-up), the wall-clock nanoseconds from the end of the previous phase to
+ * the end of this one as seen by CTA 0 (the work and the grid barrier after it), and the
+ * number of phases.  ns, phases: host long long[8].  reset != 0 clears after reading.
+ * Synchronises `stream`. */
+int fsi_grid_stats(fsi_ctx *ctx, long long *ns, long long *phases, int reset, void *stream);
 
 /* Pair-sum work issued by this context: ordered (receiver, source) pairs of the
  * acceleration passes and of the gradient passes (a symmetric pass counts both

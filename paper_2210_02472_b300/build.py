@@ -13,7 +13,7 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 LIB = PKG / "libfsi.so"
 INCLUDE = PKG.parent / "include"
-SOURCES = ["pair_kernels.cu", "aux_kernels.cu", "vjp_kernels.cu", "batch_kernels.cu", "hhs_small.cu", "order_kernels.cu", "noalloc.cu", "probe_kernels.cu", "subsys_kernels.cu", "steps_x2.cu", "fsi_api.cu"]
+SOURCES = ["pair_kernels.cu", "aux_kernels.cu", "vjp_kernels.cu", "batch_kernels.cu", "hhs_small.cu", "hhs_grid.cu", "order_kernels.cu", "noalloc.cu", "probe_kernels.cu", "subsys_kernels.cu", "steps_x2.cu", "fsi_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 
@@ -24,7 +24,7 @@ def nvcc() -> str:
 
 def build(force: bool = False, verbose_ptxas: bool = False) -> Path:
     srcs = [CSRC / s for s in SOURCES]
-    deps = srcs + [CSRC / "fsi_internal.cuh", CSRC / "pair_math.cuh", CSRC / "sym_x2.cuh", INCLUDE / "fsi.h"]
+    deps = srcs + [CSRC / "fsi_internal.cuh", CSRC / "pair_math.cuh", CSRC / "sym_x2.cuh", CSRC / "hhs_small.cuh", INCLUDE / "fsi.h"]
     if not force and LIB.exists() and all(LIB.stat().st_mtime >= d.stat().st_mtime for d in deps):
         return LIB
     objdir = PKG / "_build"

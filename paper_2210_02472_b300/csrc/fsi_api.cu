@@ -98,6 +98,12 @@ struct fsi_ctx {
     // far-tile path of the symmetric mixed kernel: while far_n > 0, the records of the set
     // being stepped (n = far_n) have valid masses in rel[].w (step_core, autotune)
     Buf rel, sub, ordws, ordperm, ordlist, farstats;
+    // HHS recursion of mid-size sets in one cooperative launch (hhs_grid.cu): scratch by
+    // particle id, list stack, barrier words; CTAs per launch (-1: not yet queried)
+    Buf grec[2], garec, gvrec, gacc, gaux, gst, glists, gbar, gprof;
+    int grid_nctas[2] = {-1, -1};
+    bool stats_on_device = false;   // the last interval was captured: its level statistics
+                                    // are read from dstats by fsi_level_stats
     int far_n = 0;
     // far-tile path of the bipartite kernel: set while an HHS interval runs on level lists
     // in Morton order; xrel/xsub hold the sub-tiles of the smaller set of a pass
@@ -145,6 +151,9 @@ size_t pad_tile(int n) { return (size_t)((n + kTileJ - 1) / kTileJ) * kTileJ; }
 // 512 particles are faster walked from the host (one HHS interval of 65536 particles,
 // mixed: 279.6 ms at 512, 269.5 ms at 256 and 128).
 constexpr int kSmallCapDefault = 256;
+// Default size cap of a fast set whose HHS recursion runs in one cooperative launch over
+// the GPU (hhs_grid.cu); larger sets are walked from the host.
+constexpr int kGridCapDefault = 4096;
 
 int choose_split(const fsi_ctx* c, int n_i, int n_j, int ipc) {
     const int ctas = (n_i + ipc - 1) / ipc;
@@ -784,6 +793,74 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     return FSI_OK;
 }
 
+int hhs_small_cap(const fsi_ctx* c) {
+    return c->p.hhs_small_max == 0 ? std::min(kSmallCapDefault, small_max())
+                                   : std::min(c->p.hhs_small_max, small_max());
+}
+
+// Largest fast set whose HHS recursion runs in one cooperative launch over the GPU; 0 when
+// that form is off (hhs_grid_max = -1, PN on, or no co-resident grid on this device).
+int hhs_grid_cap(fsi_ctx* c) {
+    if (c->p.hhs_grid_max < 0 || c->p.c > 0.0) return 0;
+    const int prec = c->p.precision;
+    if (c->grid_nctas[prec] < 0) c->grid_nctas[prec] = grid_ctas(prec, c->sm_count);
+    if (c->grid_nctas[prec] <= 0) return 0;
+    return c->p.hhs_grid_max == 0 ? kGridCapDefault : c->p.hhs_grid_max;
+}
+
+// HHS(ids, tau) at `level` in one cooperative launch (hhs_grid.cu); at level 0 the split
+// records the level-0 steps.  Statistics go to dstats.
+int run_hhs_grid(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                 const unsigned char* is_bh, const int* ids, int n, double tau, int level,
+                 bool latch_maxlevel, cudaStream_t s) {
+    const int prec = c->p.precision;
+    const size_t vb = prec == FSI_MIXED ? 16 : 32;
+    CK(ensure(c->grec[0], (size_t)N * 32));
+    CK(ensure(c->grec[1], (size_t)N * 32));
+    CK(ensure(c->garec, (size_t)N * vb));
+    CK(ensure(c->gvrec, (size_t)N * vb));
+    CK(ensure(c->gacc, 3 * (size_t)N * 8));
+    CK(ensure(c->gaux, 3 * (size_t)N * 8));
+    CK(ensure(c->gst, (size_t)N * 8));
+    // list stack: the root's copy plus one split per level down to max_level
+    const long long cap = (long long)n * std::max(2, c->p.max_level - level + 2);
+    if (cap > (1LL << 30)) return fail(FSI_ERR_ARG, "HHS list stack of %lld entries", cap);
+    CK(ensure(c->glists, (size_t)cap * 4));
+    CK(ensure(c->gbar, 64));
+    CU(cudaMemsetAsync(c->gbar.p, 0, 64, s));
+    GridArgs g{};
+    SmallArgs& sa = g.s;
+    sa.ids = ids; sa.n = n; sa.pos = pos; sa.vel = vel; sa.mass = mass;
+    sa.step0 = P<double>(c->step0); sa.N = N; sa.tau = tau; sa.level = level;
+    sa.max_level = c->p.max_level; sa.eps2 = c->p.eps2; sa.eta_ff = c->p.eta_ff;
+    sa.eta_fb = c->p.eta_fb; sa.eta_jerk = c->p.eta_jerk;
+    sa.eta_grad = c->p.eta_grad; sa.eta_va = c->p.eta_va;
+    unsigned long long* st = P<unsigned long long>(c->dstats);
+    sa.level_counts = st; sa.work = st + 64;
+    sa.maxlevel_hit = reinterpret_cast<int*>(st + 66);
+    sa.err = c->err_d;
+    sa.is_bh = is_bh;
+    sa.c = c->p.c;
+    g.step0w = level == 0 ? P<double>(c->step0) : nullptr;
+    g.small_cap = std::max(0, hhs_small_cap(c));
+    g.rec[0] = c->grec[0].p; g.rec[1] = c->grec[1].p;
+    g.arec = c->garec.p; g.vrec = c->gvrec.p;
+    g.acc = P<double>(c->gacc); g.aux = P<double>(c->gaux); g.st = P<double>(c->gst);
+    g.lists = P<int>(c->glists); g.list_cap = cap;
+    g.bar = P<unsigned long long>(c->gbar);
+    g.timeout_ns = budget(c);
+    g.latch_maxlevel = latch_maxlevel ? 1 : 0;
+    if (c->profiling) {
+        if (!c->gprof.p) {
+            CK(ensure(c->gprof, 16 * sizeof(unsigned long long)));
+            CU(cudaMemsetAsync(c->gprof.p, 0, 16 * sizeof(unsigned long long), s));
+        }
+        g.prof = P<unsigned long long>(c->gprof);
+    }
+    CU(launch_hhs_grid(prec, g, c->grid_nctas[prec], s));
+    return FSI_OK;
+}
+
 int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
               const unsigned char* is_bh, const int* Pids, int n, double tau, int level,
               cudaStream_t s) {
@@ -815,9 +892,10 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
         if (pn) CK(cross_pn_kick(c, N, pos, vel, mass, is_bh, Sids, nS, Fids, nF, 0.5 * tau, s));
         CK(cross_kick(c, N, pos, vel, mass, Sids, nS, Fids, nF, tau / 6.0, 0, 0.0, s));
     }
-    // HHS(F, tau/2): small fast sets recurse inside one CTA, larger ones level by level here
-    const int small_cap = c->p.hhs_small_max == 0 ? std::min(kSmallCapDefault, small_max())
-                          : std::min(c->p.hhs_small_max, small_max());
+    // HHS(F, tau/2): small fast sets recurse inside one CTA, mid-size ones in one
+    // cooperative launch over the GPU, larger ones level by level here
+    const int small_cap = hhs_small_cap(c);
+    const int grid_cap = hhs_grid_cap(c);
     auto recurse = [&]() -> int {
         if (nF <= 0) return FSI_OK;
         if (nF <= small_cap) {
@@ -836,6 +914,8 @@ int hhs_level(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
             CU(launch_hhs_small(c->p.precision, sa, s));
             return FSI_OK;
         }
+        if (nF <= grid_cap)
+            return run_hhs_grid(c, N, pos, vel, mass, is_bh, Fids, nF, 0.5 * tau, level + 1, false, s);
         return hhs_level(c, N, pos, vel, mass, is_bh, Fids, nF, 0.5 * tau, level + 1, s);
     };
     if (nS > 0) CK(step_core(c, N, pos, vel, mass, is_bh, Sids, nS, 0.5 * tau, 1, s));
@@ -898,6 +978,7 @@ void fsi_default_params(fsi_params* p) {
     p->eta_grad = 0.0;
     p->eta_va = 0.0;
     p->wide_ctas = 0;
+    p->hhs_grid_max = 0;
 }
 
 const char* fsi_last_error(void) { return g_err.c_str(); }
@@ -936,7 +1017,8 @@ int fsi_destroy(fsi_ctx* c) {
                    &c->iota, &c->steps, &c->step0, &c->counts, &c->accum, &c->dstats,
                    &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
                    &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos, &c->stpart,
-                   &c->xrel, &c->xsub, &c->pnids};
+                   &c->xrel, &c->xsub, &c->pnids, &c->grec[0], &c->grec[1], &c->garec,
+                   &c->gvrec, &c->gacc, &c->gaux, &c->gst, &c->glists, &c->gbar, &c->gprof};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }
@@ -1374,12 +1456,52 @@ int fsi_energy(fsi_ctx* c, int N, const double* pos, const double* vel, const do
 
 namespace {
 
-// One HHS interval (arguments checked by the caller); FSI_OK or FSI_ERR_MAXLEVEL.
+// Adds the statistics of the levels run on the device (one-CTA and grid-wide recursions)
+// to the host-walked ones (synchronous); FSI_OK or FSI_ERR_MAXLEVEL.
+int merge_hhs_stats(fsi_ctx* c, cudaStream_t s) {
+    unsigned long long st[68];
+    CU(cudaMemcpyAsync(st, c->dstats.p, sizeof st, cudaMemcpyDeviceToHost, s));
+    CU(cudaStreamSynchronize(s));
+    for (int k = 0; k < 64; ++k) {
+        c->level_counts[k] += (long long)st[k];
+        if (c->level_counts[k]) c->max_level_used = std::max(c->max_level_used, k);
+    }
+    c->work_pairs[0] += (long long)st[64];
+    c->work_pairs[1] += (long long)st[65];
+    if (reinterpret_cast<int*>(st + 66)[0]) c->max_level_hit = 1;
+    return c->max_level_hit ? FSI_ERR_MAXLEVEL : FSI_OK;
+}
+
+// One HHS interval (arguments checked by the caller); FSI_OK or FSI_ERR_MAXLEVEL.  Under
+// stream capture (N <= the grid cap only) the statistics stay on the device.
 int hhs_interval_core(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
                       const unsigned char* is_bh, double tau, cudaStream_t s) {
     CK(ensure(c->iota, (size_t)N * 4));
     CK(ensure(c->step0, (size_t)N * 8));
     CK(ensure(c->counts, 16));
+    CK(ensure(c->dstats, 68 * sizeof(unsigned long long)));
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    CU(cudaStreamIsCapturing(s, &cs));
+    const bool capturing = cs != cudaStreamCaptureStatusNone;
+    c->level_counts.assign(std::max(c->p.max_level + 1, 64), 0);
+    c->max_level_used = 0;
+    c->max_level_hit = 0;
+    c->stats_on_device = false;
+    if (N <= hhs_grid_cap(c)) {
+        // the whole interval in one cooperative launch: no host synchronisation
+        CU(launch_iota(N, P<int>(c->iota), s));
+        CU(cudaMemsetAsync(c->dstats.p, 0, 68 * sizeof(unsigned long long), s));
+        CK(run_hhs_grid(c, N, pos, vel, mass, is_bh, P<int>(c->iota), N, tau, 0, capturing, s));
+        if (capturing) {
+            c->stats_on_device = true;
+            return FSI_OK;
+        }
+        return merge_hhs_stats(c, s);
+    }
+    if (capturing)
+        return fail(FSI_ERR_UNSUPPORTED,
+                    "an HHS interval walked from the host cannot be captured (N = %d > %d, the "
+                    "largest N run in one launch with these parameters)", N, hhs_grid_cap(c));
     struct OrderedGuard {
         fsi_ctx* c;
         ~OrderedGuard() { c->lists_ordered = false; }
@@ -1394,25 +1516,9 @@ int hhs_interval_core(fsi_ctx* c, int N, double* pos, double* vel, const double*
     } else {
         CU(launch_iota(N, P<int>(c->iota), s));
     }
-    CK(ensure(c->dstats, 68 * sizeof(unsigned long long)));
     CU(cudaMemsetAsync(c->dstats.p, 0, 68 * sizeof(unsigned long long), s));
-    c->level_counts.assign(std::max(c->p.max_level + 1, 64), 0);
-    c->max_level_used = 0;
-    c->max_level_hit = 0;
     CK(hhs_level(c, N, pos, vel, mass, is_bh, P<int>(c->iota), N, tau, 0, s));
-    {   // merge the statistics of the levels run inside one CTA
-        unsigned long long st[68];
-        CU(cudaMemcpyAsync(st, c->dstats.p, sizeof st, cudaMemcpyDeviceToHost, s));
-        CU(cudaStreamSynchronize(s));
-        for (int k = 0; k < 64; ++k) {
-            c->level_counts[k] += (long long)st[k];
-            if (st[k]) c->max_level_used = std::max(c->max_level_used, k);
-        }
-        c->work_pairs[0] += (long long)st[64];
-        c->work_pairs[1] += (long long)st[65];
-        if (reinterpret_cast<int*>(st + 66)[0]) c->max_level_hit = 1;
-    }
-    return c->max_level_hit ? FSI_ERR_MAXLEVEL : FSI_OK;
+    return merge_hhs_stats(c, s);
 }
 
 // E = T + W of all N particles, FP64 (synchronous).
@@ -1497,6 +1603,18 @@ int fsi_hhs_interval_restart(fsi_ctx* c, int N, double* pos, double* vel, const 
 
 int fsi_level_stats(fsi_ctx* c, long long* counts, int max) {
     if (!c || (!counts && max > 0)) return fail(FSI_ERR_ARG, "NULL argument");
+    if (c->stats_on_device) {
+        // a captured interval: the level counts of its last replay
+        unsigned long long st[64];
+        CU(cudaDeviceSynchronize());
+        CU(cudaMemcpy(st, c->dstats.p, sizeof st, cudaMemcpyDeviceToHost));
+        c->level_counts.assign(std::max<size_t>(c->level_counts.size(), 64), 0);
+        c->max_level_used = 0;
+        for (int k = 0; k < 64; ++k) {
+            c->level_counts[k] = (long long)st[k];
+            if (st[k]) c->max_level_used = k;
+        }
+    }
     const int used = std::min<int>((int)c->level_counts.size(), c->max_level_used + 1);
     for (int k = 0; k < max; ++k) counts[k] = k < (int)c->level_counts.size() ? c->level_counts[k] : 0;
     return used;
@@ -1839,6 +1957,22 @@ int fsi_batch_step(fsi_ctx* c, fsi_batch* b, double* pos, double* vel, const dou
 int fsi_profile(fsi_ctx* c, int enable) {
     if (!c) return fail(FSI_ERR_ARG, "NULL context");
     c->profiling = enable != 0;
+    return FSI_OK;
+}
+
+int fsi_grid_stats(fsi_ctx* c, long long* ns, long long* phases, int reset, void* stream) {
+    if (!c || !ns || !phases) return fail(FSI_ERR_ARG, "NULL argument");
+    unsigned long long st[16] = {};
+    const cudaStream_t s = S(stream);
+    if (c->gprof.p) {
+        CU(cudaMemcpyAsync(st, c->gprof.p, sizeof st, cudaMemcpyDeviceToHost, s));
+        CU(cudaStreamSynchronize(s));
+        if (reset) CU(cudaMemsetAsync(c->gprof.p, 0, sizeof st, s));
+    }
+    for (int k = 0; k < 8; ++k) {
+        ns[k] = (long long)st[k];
+        phases[k] = (long long)st[8 + k];
+    }
     return FSI_OK;
 }
 

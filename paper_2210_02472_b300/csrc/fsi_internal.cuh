@@ -212,6 +212,26 @@ struct SmallArgs {
     double c;
 };
 
+// HHS recursion of a mid-size set in one cooperative launch over the GPU (hhs_grid.cu).
+// Scratch arrays are indexed by global particle id (N entries) unless noted.
+struct GridArgs {
+    SmallArgs s;                    // root set, state, parameters, statistics (as above)
+    double* step0w;                 // level-0 steps, recorded when the root is level 0
+    int small_cap;                  // fast sets of <= small_cap recurse in CTA 0 (one-CTA form)
+    void* rec[2];                   // position records (RecMix / D4), two buffers
+    void* arec;                     // acceleration records (float4 / D4)
+    void* vrec;                     // velocity records (float4 / D4) for the time steps
+    double* acc;                    // 3 x N: a of the current pass (gradient-kick base)
+    double* aux;                    // 3 x N: G of the gradient time-step criteria
+    double* st;                     // time steps
+    int* lists;                     // list stack (list_cap entries)
+    long long list_cap;
+    unsigned long long* bar;        // [0] arrivals, [1] abort, [2] nS, [3] nF; zeroed per launch
+    long long timeout_ns;           // budget of every barrier wait
+    int latch_maxlevel;             // also latch FSI_ERR_MAXLEVEL in err on a depth-cap hit
+    unsigned long long* prof;       // optional phase profile (16 words), or nullptr
+};
+
 // ---------------------------------------------------------------------------------
 // Host-side launchers (defined in pair_kernels.cu / aux_kernels.cu).
 namespace fsi {
@@ -382,6 +402,8 @@ cudaError_t launch_partition(int n, const int* ids, double* step, double* step0,
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s);
 cudaError_t launch_hhs_small(int precision, const SmallArgs& a, cudaStream_t s);
 int small_max();
+cudaError_t launch_hhs_grid(int precision, const GridArgs& a, int ctas, cudaStream_t s);
+int grid_ctas(int precision, int sm_count);   // CTAs of one cooperative launch (0: none fit)
 cudaError_t launch_batch(int precision, int ipt, int ctas, const BatchArgs& a, cudaStream_t s);
 // Symmetric persistent ensemble kernel (mixed precision): phases pack, then per pair pass
 // a sum phase (sitems, red.add into accum) and an apply phase (items: epilogue, accum

@@ -41,7 +41,7 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_step_vjp_rec", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall", "fsi_batch_stats",
-            "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for"]
+            "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for", "fsi_grid_stats"]
 
 
 class fsi_params(C.Structure):
@@ -49,7 +49,8 @@ class fsi_params(C.Structure):
                 ("eta_fb", C.c_double), ("eta_jerk", C.c_double), ("max_level", C.c_int),
                 ("c", C.c_double), ("split", C.c_int), ("timeout_ns", C.c_longlong),
                 ("symmetric", C.c_int), ("hhs_small_max", C.c_int), ("order_min", C.c_int),
-                ("eta_grad", C.c_double), ("eta_va", C.c_double), ("wide_ctas", C.c_int)]
+                ("eta_grad", C.c_double), ("eta_va", C.c_double), ("wide_ctas", C.c_int),
+                ("hhs_grid_max", C.c_int)]
 
 
 _vp, _ip, _dp = C.c_void_p, C.c_int, C.c_double
@@ -80,6 +81,7 @@ _lib.fsi_launch_count.restype = C.c_longlong
 _lib.fsi_accel_noalloc.argtypes = [_ip, _vp, _vp, _dp, _vp, _vp]
 _lib.fsi_work_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip]
 _lib.fsi_far_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip, _vp]
+_lib.fsi_grid_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip, _vp]
 _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
 _lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
@@ -150,7 +152,7 @@ class Context:
                  eta_fb: float = 0.2, eta_jerk: float = 0.1, max_level: int = 40,
                  c: float = 0.0, split: int = 0, timeout_ns: int = 0, symmetric: bool = True,
                  hhs_small_max: int = 0, order_min: int = 0, eta_grad: float = 0.0,
-                 eta_va: float = 0.0, wide_ctas: int = 0):
+                 eta_va: float = 0.0, wide_ctas: int = 0, hhs_grid_max: int = 0):
         p = fsi_params()
         _lib.fsi_default_params(C.byref(p))
         p.precision = {"fp64": FSI_FP64, "mixed": FSI_MIXED}[precision]
@@ -161,6 +163,7 @@ class Context:
         p.order_min = int(order_min)
         p.eta_grad, p.eta_va = float(eta_grad), float(eta_va)
         p.wide_ctas = int(wide_ctas)
+        p.hhs_grid_max = int(hhs_grid_max)
         self.params = p
         self.precision = precision
         h = _vp()
@@ -344,6 +347,16 @@ def fsi_level_stats(ctx: Context, max_levels: int = 64):
     counts = (C.c_longlong * max_levels)()
     used = _lib.fsi_level_stats(ctx.handle, counts, max_levels)
     return [int(x) for x in counts[:max(used, 0)]]
+
+
+def fsi_grid_stats(ctx: Context, reset: bool = False, stream=None):
+    """Phase profile of the cooperative-launch HHS recursions (while fsi_profile is on):
+    (ns, phases), each a list of 8 per phase kind (time steps, split, inter-level kick,
+    FSI pass, one-CTA recursion, gradient criteria, set-up, unused)."""
+    ns = (C.c_longlong * 8)()
+    ph = (C.c_longlong * 8)()
+    _check(_lib.fsi_grid_stats(ctx.handle, ns, ph, int(bool(reset)), _stream(stream)), "fsi_grid_stats")
+    return [int(x) for x in ns], [int(x) for x in ph]
 
 
 def fsi_profile(ctx: Context, enable: bool = True) -> None:

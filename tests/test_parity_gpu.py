@@ -562,17 +562,18 @@ def test_timesteps_gradient_criteria(F, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("small", [0, -1])
-def test_hhs_interval_gradient_criteria(F, prec, small):
+@pytest.mark.parametrize("small,grid", [(0, -1), (-1, -1), (0, 0), (-1, 0)])
+def test_hhs_interval_gradient_criteria(F, prec, small, grid):
     """One HHS interval with the gradient and velocity-per-acceleration criteria on, the
-    levels walked from the host (small = -1) or recursed inside one CTA (0)."""
+    levels walked from the host (grid = -1) or run in one cooperative launch (0), with
+    (small = 0) or without (-1) the one-CTA recursion of the small fast sets."""
     c = inputs.plummer(600, 22, imf="kroupa")
     tau = 1.0 / 16
     kw = dict(eta_grad=0.1, eta_va=0.1)
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, **kw)
     _, _, counts0, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
     assert not np.array_equal(counts, counts0)      # the criteria change the hierarchy
-    with F.Context(prec, hhs_small_max=small, **kw) as ctx:
+    with F.Context(prec, hhs_small_max=small, hhs_grid_max=grid, **kw) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
@@ -586,17 +587,28 @@ def test_hhs_interval_gradient_criteria(F, prec, small):
     assert np.abs(v - rv).max() <= tol * 100
 
 
+# (hhs_small_max, wide_ctas, hhs_grid_max) of the HHS interval tests: the whole interval
+# in one cooperative launch (grid 0, the default for N <= 4096) with fast sets of <= 256
+# (small 0) or <= 64 (small 64) handed to the one-CTA recursion, or none (small -1); the
+# levels walked from the host (grid -1) with the one-CTA recursion (small 0, 64) or
+# without (-1), the host-walked passes in the wide form where it is chosen (wide 0) or
+# tiled only (-1); the top levels walked from the host and fast sets of <= 300 handed to
+# the cooperative launch (grid 300).
+HHS_MODES = [(0, 0, 0), (64, 0, 0), (-1, 0, 0), (0, 0, -1), (64, 0, -1), (-1, 0, -1),
+             (0, -1, -1), (-1, -1, -1), (0, 0, 300), (-1, 0, 300)]
+
+
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("small", [0, -1, 64])
-@pytest.mark.parametrize("wide", [0, -1])
-def test_hhs_interval(F, prec, small, wide):
-    """One HHS interval against the oracle: the levels walked from the host (small = -1),
-    run inside one CTA once the fast set has <= 512 particles (0), or a mix (64); the
-    host-walked passes in the wide form where it is chosen (wide = 0) or tiled only (-1)."""
+@pytest.mark.parametrize("mode", HHS_MODES, ids=lambda m: "small%d-wide%d-grid%d" % m)
+def test_hhs_interval(F, prec, mode):
+    """One HHS interval against the oracle, in every combination of the four ways a level
+    set is run (HHS_MODES): walked from the host, in one cooperative launch over the GPU,
+    inside one CTA, and the wide or tiled host-walked passes."""
+    small, wide, grid = mode
     c = inputs.plummer(600, 22, imf="kroupa")
     tau = 1.0 / 16
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
-    with F.Context(prec, hhs_small_max=small, wide_ctas=wide) as ctx:
+    with F.Context(prec, hhs_small_max=small, wide_ctas=wide, hhs_grid_max=grid) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
@@ -611,17 +623,20 @@ def test_hhs_interval(F, prec, small, wide):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("symmetric", [True, False])
-def test_hhs_interval_large_cross_passes(F, prec, symmetric):
+@pytest.mark.parametrize("symmetric,grid", [(True, -1), (False, -1), (True, 0), (True, 1500)])
+def test_hhs_interval_large_cross_passes(F, prec, symmetric, grid):
     """HHS interval of 4000 particles: the top levels' cross-level kicks have slow and fast
-    sets of several hundred to thousands of particles, evaluated by the bipartite symmetric
-    kernel (every S-F pair once, symmetric = True; packed FP32 or FP64) or as two one-sided
-    passes (False); both against the oracle."""
+    sets of several hundred to thousands of particles.  Walked from the host (grid -1) they
+    are evaluated by the bipartite symmetric kernel (every S-F pair once, symmetric = True;
+    packed FP32 or FP64) or as two one-sided passes (False); in one cooperative launch
+    (grid 0: the whole interval) by the two directions on disjoint CTA ranges; or mixed
+    (grid 1500: the levels below the first fast set of <= 1500 in the cooperative launch).
+    All against the oracle."""
     c = inputs.plummer(4000, 30, imf="kroupa")
     tau = 1.0 / 32
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
     assert counts[0] >= 256 and counts[0] <= 4000 - 256      # both sets >= one tile at level 0
-    with F.Context(prec, symmetric=symmetric) as ctx:
+    with F.Context(prec, symmetric=symmetric, hhs_grid_max=grid) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
@@ -633,6 +648,51 @@ def test_hhs_interval_large_cross_passes(F, prec, symmetric):
     tol = 1e-11 if prec == "fp64" else 1e-7
     assert np.abs(p - rp).max() <= tol
     assert np.abs(v - rv).max() <= tol * 100
+
+
+@pytest.mark.parametrize("prec", PRECS)
+def test_hhs_interval_graph_capture(F, prec):
+    """An HHS interval of N <= hhs_grid_max is one cooperative launch with no host
+    synchronisation: captured in a CUDA graph and replayed, it reproduces the uncaptured
+    interval bit for bit (positions, velocities, level statistics), twice in a row; the
+    uncaptured interval matches the oracle.  An interval that needs the host walk refuses
+    capture with FSI_ERR_UNSUPPORTED."""
+    c = inputs.plummer(2000, 31, imf="kroupa")
+    tau = 1.0 / 32
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    m = dev(c.mass)
+    with F.Context(prec) as ctx:
+        p1, v1 = dev(c.pos), dev(c.vel)
+        assert F.fsi_hhs_interval(ctx, p1, v1, m, tau) == F.FSI_OK
+        lv1 = F.fsi_level_stats(ctx)
+        p2, v2 = dev(c.pos), dev(c.vel)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            assert F.fsi_hhs_interval(ctx, p2, v2, m, tau) == F.FSI_OK
+        for _ in range(2):
+            p2.copy_(dev(c.pos))
+            v2.copy_(dev(c.vel))
+            g.replay()
+            torch.cuda.synchronize()
+            assert torch.equal(p1, p2) and torch.equal(v1, v2)
+            assert F.fsi_level_stats(ctx) == lv1
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        p, v = host(p1), host(v1)
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv1[:used] == list(counts[:used])
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
+    with F.Context(prec, hhs_grid_max=1000) as ctx:
+        p3, v3 = dev(c.pos), dev(c.vel)
+        F.fsi_hhs_interval(ctx, p3, v3, m, tau)             # workspace, uncaptured
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with pytest.raises(F.FsiError) as ei:
+            with torch.cuda.graph(g):
+                F.fsi_hhs_interval(ctx, p3, v3, m, tau)
+        assert ei.value.code == F.FSI_ERR_UNSUPPORTED
+        torch.cuda.synchronize()
 
 
 def test_hhs_interval_morton_ordered_levels(F):
@@ -658,11 +718,12 @@ def test_hhs_interval_morton_ordered_levels(F):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("small", [0, -1])
-def test_hhs_interval_depth_cap(F, prec, small):
+@pytest.mark.parametrize("small,grid", [(0, -1), (-1, -1), (0, 0), (-1, 0)])
+def test_hhs_interval_depth_cap(F, prec, small, grid):
     """The HHS depth cap (a particle that wants a level below max_level stays in S at
     max_level): the interval completes, returns FSI_ERR_MAXLEVEL, and matches the oracle's
-    capped interval, in the host walk and the one-CTA recursion."""
+    capped interval, in the host walk (grid = -1), the cooperative launch (0) and the
+    one-CTA recursion (small = 0)."""
     c = inputs.plummer(600, 22, imf="kroupa")
     tau = 1.0 / 16
     _, _, counts_free, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
@@ -671,7 +732,7 @@ def test_hhs_interval_depth_cap(F, prec, small):
     rp, rv, counts, code = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, max_level=cap,
                                                allow_maxlevel=True)
     assert code == oracle.ERR_MAXLEVEL
-    with F.Context(prec, max_level=cap, hhs_small_max=small) as ctx:
+    with F.Context(prec, max_level=cap, hhs_small_max=small, hhs_grid_max=grid) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
@@ -864,19 +925,20 @@ def test_mid_class_symmetric_variant_against_oracle(F, n):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("small", [0, -1])
-def test_hhs_interval_softened(F, prec, small):
+@pytest.mark.parametrize("small,grid", [(0, -1), (-1, -1), (0, 0), (-1, 0)])
+def test_hhs_interval_softened(F, prec, small, grid):
     """One HHS interval with Plummer softening (eps2 > 0, the setting of the softened
     equal-mass run of Sect. 5.2) against the oracle's interval at the same eps2: softened
     pair sums (r^2 + eps2 in r^3 and r^5), unsoftened free-fall / fly-by distances, levels
-    walked from the host (small = -1) or recursed inside one CTA (0)."""
+    walked from the host (grid = -1) or run in one cooperative launch (0), with (small = 0)
+    or without (-1) the one-CTA recursion."""
     c = inputs.plummer(2000, 38)
     tau, eps2 = 1.0 / 32, 1e-4
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, eps2=eps2)
     rp0, _, counts0, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
     assert np.abs(rp - rp0).max() > 1e-9                    # the softening matters here
     assert np.count_nonzero(counts) >= 3                    # several levels
-    with F.Context(prec, eps2=eps2, hhs_small_max=small) as ctx:
+    with F.Context(prec, eps2=eps2, hhs_small_max=small, hhs_grid_max=grid) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
         lv = F.fsi_level_stats(ctx)
