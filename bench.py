@@ -679,6 +679,9 @@ def run_hhs(args):
     energy = lambda: float(F.fsi_energy(ctx, pos, vel, mass).cpu().numpy().sum())
     e0 = energy()
     F.fsi_work_stats(ctx, reset=True)
+    if args.grid_profile:
+        F.fsi_profile(ctx, True)
+        F.fsi_grid_stats(ctx, reset=True)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
     levels, per_interval, t_int = [], [], 0.0
@@ -696,6 +699,16 @@ def run_hhs(args):
     torch.cuda.synchronize()
     t = t_int if soft else time.perf_counter() - t0
     acc_p, grad_p = F.fsi_work_stats(ctx)
+    grid_profile = None
+    if args.grid_profile:
+        ns, ph = F.fsi_grid_stats(ctx)
+        F.fsi_profile(ctx, False)
+        F.fsi_profile_read(ctx)
+        kinds = ["time_steps", "split", "inter_level_kick", "fsi_pass", "one_cta_recursion",
+                 "gradient_criteria", "set_up"]
+        grid_profile = {k: {"ms_per_interval": ns[q] / 1e6 / args.intervals,
+                            "phases_per_interval": ph[q] / args.intervals}
+                        for q, k in enumerate(kinds) if ph[q]}
     e1 = energy()
     inter = (acc_p * FLOP_ACC + grad_p * FLOP_GRAD) / FLOP_PAIR
     line = {
@@ -717,6 +730,9 @@ def run_hhs(args):
         "mean_rel_energy_error_per_interval": float(np.mean(per_interval)) if per_interval else None,
         "acc_pairs": acc_p, "grad_pairs": grad_p, "maxlevel_status": code,
     }
+    if grid_profile is not None:
+        # wall clock of CTA 0 per phase kind of the cooperative-launch recursions
+        line["grid_phase_profile"] = grid_profile
     print(json.dumps(line), flush=True)
     ctx.close()
     return 0
@@ -984,6 +1000,8 @@ def main():
     ap.add_argument("--hhs-small-max", type=int, default=0, help="HHS mode: fsi_params.hhs_small_max")
     ap.add_argument("--order-min", type=int, default=0, help="HHS mode: fsi_params.order_min")
     ap.add_argument("--hhs-grid-max", type=int, default=0, help="HHS mode: fsi_params.hhs_grid_max")
+    ap.add_argument("--grid-profile", action="store_true",
+                    help="HHS mode: phase profile of the cooperative-launch recursions (fsi_grid_stats)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

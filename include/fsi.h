@@ -295,7 +295,19 @@ int fsi_energy(fsi_ctx *ctx, int N, const double *pos, const double *vel,
  * per level, time steps against the level set (level 0 against all N; deeper levels
  * take min with the level-0 step), the split S = {eps >= tau}, F = {eps < tau}, then
  * U_SF(tau/6) FSI(S, tau/2) HHS(F, tau/2) U~_SF(2 tau/3) HHS(F, tau/2) FSI(S, tau/2)
- * U_SF(tau/6).  In place on pos/vel.  Synchronous (the host walks the hierarchy). */
+ * U_SF(tau/6).  In place on pos/vel.
+ * How the levels run: the host walks the large levels (one device->host read of the
+ * split counts per level visit, so the call is synchronous); with PN off, a fast set of
+ * more than hhs_small_max and at most hhs_grid_max particles runs its whole recursion in
+ * one cooperative launch over the GPU, and a fast set of at most hhs_small_max in one CTA.
+ * When N <= hhs_grid_max (PN off) the whole interval is that one launch: the call then
+ * does not synchronise with the host and may be captured in a CUDA graph (stream
+ * capture); a replay repeats the interval bit for bit on the captured buffers.  Under
+ * capture the level statistics stay on the device (fsi_level_stats reads those of the
+ * last replay) and a depth-cap hit is latched as FSI_ERR_MAXLEVEL in the error word
+ * (fsi_sync_status) instead of being returned.  An interval that needs the host walk
+ * returns FSI_ERR_UNSUPPORTED when its stream is capturing.  Device waits are bounded by
+ * fsi_params.timeout_ns (FSI_ERR_TIMEOUT latched on expiry). */
 int fsi_hhs_interval(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
                      const unsigned char *is_bh, double tau, void *stream);
 
@@ -359,8 +371,10 @@ int fsi_batch_stats(fsi_batch *batch, long long *wait_ns, long long *life_ns, in
  * after that runs normally.  That call synchronises the stream. */
 int fsi_batch_inject_stall(fsi_batch *batch, int cluster);
 
-/* Per-level slow-set sizes summed over the visits of the last fsi_hhs_interval.
- * counts: host array of `max` entries.  Returns the number of levels used. */
+/* Per-level slow-set sizes summed over the visits of the last fsi_hhs_interval (of its
+ * last replay, when that interval was captured in a CUDA graph; the call then
+ * synchronises the device).  counts: host array of `max` entries.  Returns the number of
+ * levels used. */
 int fsi_level_stats(fsi_ctx *ctx, long long *counts, int max);
 
 /* ---- tuning ----------------------------------------------------------------------- */

@@ -226,7 +226,7 @@ struct GridArgs {
     double* st;                     // time steps
     int* lists;                     // list stack (list_cap entries)
     long long list_cap;
-    unsigned long long* bar;        // [0] arrivals, [1] abort, [2] nS, [3] nF; zeroed per launch
+    unsigned long long* bar;        // [0] arrivals, [1] abort; zeroed before each launch
     long long timeout_ns;           // budget of every barrier wait
     int latch_maxlevel;             // also latch FSI_ERR_MAXLEVEL in err on a depth-cap hit
     unsigned long long* prof;       // optional phase profile (16 words), or nullptr

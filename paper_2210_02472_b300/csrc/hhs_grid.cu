@@ -26,6 +26,8 @@
 // an inter-level kick run in one phase on disjoint CTA ranges.  Data written by other CTAs
 // in earlier phases is read with L1-bypassing loads.  PN1.0 pairs are not evaluated here
 // (the caller walks PN runs from the host).
+#include <algorithm>
+
 #include "hhs_small.cuh"
 
 namespace fsi {
@@ -51,7 +53,7 @@ struct GCtl {
     GFrame fr[kGridDepth];
     long long list_top;
     long long t_last;               // CTA 0, with a.prof: end of the previous phase
-    int top, ok, nS, nF;
+    int top, ok;
 };
 
 // Phase kinds of the optional profile (a.prof: [kind] ns, [8 + kind] phases, from CTA 0).
@@ -96,8 +98,10 @@ __device__ __forceinline__ void g_pack(const GridArgs& a, int i) {
 // ---------------------------------------------------------------------------------
 // Grid barrier: one monotonic arrival counter per launch (zeroed before it); barrier k
 // completes when the counter reaches (k + 1) * gridDim.x.  Thread 0 of each CTA arrives
-// after a fence (the CTA's writes become visible), waits with a bounded spin, and fences
-// again; the CTA's other threads wait at __syncthreads.
+// with a release add after the CTA's __syncthreads (the CTA's writes happen before it)
+// and waits with acquire loads (the other CTAs' writes happen before the CTA's
+// __syncthreads that follows); the wait is bounded, and a CTA that aborts never arrives,
+// so the others see the abort flag or run out of time while they spin.
 __device__ __forceinline__ unsigned long long ld_acq_u64(const unsigned long long* p) {
     unsigned long long v;
     asm volatile("ld.acquire.gpu.global.u64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
@@ -113,24 +117,26 @@ __device__ bool grid_sync(const GridArgs& a, unsigned long long& target, GCtl& C
     if (threadIdx.x == 0) {
         int ok = 1;
         target += gridDim.x;
-        __threadfence();
         red_rel_add_u64(a.bar, 1ull);
         if (ld_acq_u64(a.bar) < target) {
-            const long long t0 = global_ns();
-            int spins = 0;
-            while (ld_acq_u64(a.bar) < target) {
-                if (ld_acq_u64(a.bar + 1)) { ok = 0; break; }
-                if (global_ns() - t0 > a.timeout_ns) {
-                    set_error(a.s.err, FSI_ERR_TIMEOUT);
-                    atomicExch(a.bar + 1, 1ull);
-                    ok = 0;
-                    break;
+            long long t0 = 0;
+            for (int spins = 0;; ++spins) {
+                if (ld_acq_u64(a.bar) >= target) break;
+                if ((spins & 31) == 31) {
+                    // every 32 polls: the abort flag and the clock
+                    if (ld_acq_u64(a.bar + 1)) { ok = 0; break; }
+                    const long long now = global_ns();
+                    if (t0 == 0) t0 = now;
+                    else if (now - t0 > a.timeout_ns) {
+                        set_error(a.s.err, FSI_ERR_TIMEOUT);
+                        atomicExch(a.bar + 1, 1ull);
+                        ok = 0;
+                        break;
+                    }
+                    if (spins > 4096) __nanosleep(64);
                 }
-                if (++spins > 64) __nanosleep(32);
             }
         }
-        __threadfence();
-        if (ld_acq_u64(a.bar + 1)) ok = 0;
         C.ok = ok;
         if (a.prof && blockIdx.x == 0) {
             const long long now = global_ns();
@@ -156,12 +162,15 @@ struct GDir {
     int nA;
     const int* B;       // sources
     int nB;
+    const int* B2;      // a second source range, summed apart (acceleration passes)
+    int nB2;
 };
 
 struct GLayout {
     GDir d;
     int cb, nct, G, groups, rounds;
     bool mine;          // this CTA works on d
+    bool first;         // d is direction 0
 };
 
 // CTAs of direction 0 when two directions share a phase: enough for a warp per receiver
@@ -178,7 +187,7 @@ __device__ __forceinline__ GLayout g_layout(const GDir& d0, const GDir& d1) {
             if (need0 + need1 <= grid) {
                 c0 = (int)need0;
             } else {
-                const double w0 = (double)d0.nA * d0.nB, w1 = (double)d1.nA * d1.nB;
+                const double w0 = (double)d0.nA * (d0.nB + d0.nB2), w1 = (double)d1.nA * (d1.nB + d1.nB2);
                 c0 = (int)llround(grid * w0 / (w0 + w1));
                 c0 = min(max(c0, 1), grid - 1);
             }
@@ -187,6 +196,7 @@ __device__ __forceinline__ GLayout g_layout(const GDir& d0, const GDir& d1) {
     GLayout L;
     const bool first = (int)blockIdx.x < c0;
     L.d = first ? d0 : d1;
+    L.first = first;
     L.cb = first ? 0 : c0;
     L.nct = first ? c0 : grid - c0;
     L.mine = L.nct > 0 && L.d.nA > 0 && L.d.nB > 0;
@@ -203,17 +213,36 @@ __device__ __forceinline__ GLayout g_layout(const GDir& d0, const GDir& d1) {
 //   store:  acc[:, i] = s and the acceleration record of i (for a gradient pass);
 //   out:    out[:, i] = s;
 //   w != 0: kick v_i += w s (acceleration pass) or w (acc[:, i] + cg s) (gradient pass),
-//           then, wd != 0, drift x_i += wd v_i and write i's record into rout.
+//           and, with a second source range, v_i += w2 s2 (before the first kick when
+//           other_first, else after it); then, wd != 0, drift x_i += wd v_i and write i's
+//           record into rout.
 struct GEpi {
     int store;
     double* out;
     double w, cg, wd;
     const void* rin;
     void* rout;
+    double w2;          // kick weight of the second source range's sum
+    int other_first;    // kick by the second range's sum before the first's
 };
 
+// Shared-memory layout of a pass: a staged chunk of source records (and acceleration
+// records, ids), then per local receiver of the CTA its id and its sums (up to two
+// ranges), which the receiver's leader lane parks there for the epilogue.
+template <int P>
+struct GSm {
+    static constexpr size_t acc = kGridChunk * sizeof(GRec<P>);
+    static constexpr size_t id = acc + kGridChunk * sizeof(GVec<P>);
+    static constexpr size_t sum = id + kGridChunk * sizeof(int);
+    static constexpr size_t idx = sum + kGridThreads * 6 * sizeof(double);
+    static constexpr size_t bytes = idx + kGridThreads * sizeof(int);
+};
+
+// The epilogue of receiver i, run with one receiver per lane (the B300 FP64 unit issues
+// ~1/64 of the FP32 rate, so FP64 work is packed into as few warps as possible).
 template <int P, int KIND>
-__device__ __forceinline__ void g_epilogue(const GridArgs& a, const GEpi& e, int i, const double (&s)[3]) {
+__device__ __forceinline__ void g_epilogue(const GridArgs& a, const GEpi& e, int i, const double (&s)[3],
+                                           const double* s2) {
     const long long N = a.s.N;
     const double m = a.s.mass[i];
     if (e.store) {
@@ -226,11 +255,20 @@ __device__ __forceinline__ void g_epilogue(const GridArgs& a, const GEpi& e, int
         for (int c = 0; c < 3; ++c) e.out[c * N + i] = s[c];
     }
     if (e.w != 0.0) {
+        double v0[3], x0[3], a0[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            v0[c] = __ldcg(a.s.vel + c * N + i);
+            if (e.wd != 0.0) x0[c] = __ldcg(a.s.pos + c * N + i);
+            if (KIND == 1) a0[c] = __ldcg(a.acc + c * N + i);
+        }
         double v[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const double ac = KIND == 1 ? fma(e.cg, s[c], __ldcg(a.acc + c * N + i)) : s[c];
-            v[c] = fma(e.w, ac, __ldcg(a.s.vel + c * N + i));
+            const double ac = KIND == 1 ? fma(e.cg, s[c], a0[c]) : s[c];
+            if (s2 && e.other_first) v[c] = fma(e.w, ac, fma(e.w2, s2[c], v0[c]));
+            else if (s2) v[c] = fma(e.w2, s2[c], fma(e.w, ac, v0[c]));
+            else v[c] = fma(e.w, ac, v0[c]);
             a.s.vel[c * N + i] = v[c];
         }
         g_put_vec<P>(a.vrec, i, v[0], v[1], v[2], m);
@@ -238,7 +276,7 @@ __device__ __forceinline__ void g_epilogue(const GridArgs& a, const GEpi& e, int
             double x[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                x[c] = fma(e.wd, v[c], __ldcg(a.s.pos + c * N + i));
+                x[c] = fma(e.wd, v[c], x0[c]);
                 a.s.pos[c * N + i] = x[c];
             }
             g_put_pos<P>(e.rout, i, x[0], x[1], x[2], m);
@@ -247,114 +285,138 @@ __device__ __forceinline__ void g_epilogue(const GridArgs& a, const GEpi& e, int
 }
 
 // One pair pass (KIND 0: acceleration, 1: gradient with the acceleration records) over
-// up to two directions; SELF: the receivers are among the sources (the pair i-i is
-// skipped).
+// up to two directions (epilogue e0 for direction 0, e1 for direction 1); SELF: the receivers are among the sources (the pair i-i is
+// skipped).  An acceleration pass may give a direction a second source range, whose sum
+// is kept apart (parked in the receiver's shared-memory slot) and kicked with its own
+// weight.
 template <int P, int KIND, bool SELF>
 __device__ void g_pass(const GridArgs& a, unsigned char* smem, const GDir& d0, const GDir& d1,
-                       const GEpi& e) {
+                       const GEpi& e0, const GEpi& e1) {
     const GLayout L = g_layout(d0, d1);
     if (!L.mine) return;
+    const GEpi& e = L.first ? e0 : e1;
     const int t = threadIdx.x;
     if (t == 0 && blockIdx.x == L.cb && a.s.work)
-        atomicAdd(a.s.work + KIND, (unsigned long long)L.d.nA * (unsigned long long)L.d.nB);
+        atomicAdd(a.s.work + KIND, (unsigned long long)L.d.nA * (unsigned long long)(L.d.nB + L.d.nB2));
     GRec<P>* srec = reinterpret_cast<GRec<P>*>(smem);
     GVec<P>* sacc = reinterpret_cast<GVec<P>*>(smem + kGridChunk * sizeof(GRec<P>));
     int* sid = reinterpret_cast<int*>(smem + kGridChunk * (sizeof(GRec<P>) + sizeof(GVec<P>)));
+    double* ssum = reinterpret_cast<double*>(smem + GSm<P>::sum);
+    int* sidx = reinterpret_cast<int*>(smem + GSm<P>::idx);
     const int G = L.G;
     const int vt = ((int)blockIdx.x - L.cb) * kGridThreads + t;
     const int g = vt & (G - 1);
     const GRec<P>* rin = reinterpret_cast<const GRec<P>*>(e.rin);
     const GVec<P>* arec = reinterpret_cast<const GVec<P>*>(a.arec);
+    const int nparts = (KIND == 0 && L.d.nB2 > 0) ? 2 : 1;
     for (int r = 0; r < L.rounds; ++r) {
-        if (r * L.groups + ((int)blockIdx.x - L.cb) * (kGridThreads / G) >= L.d.nA) break;
+        const int slot0 = r * L.groups + ((int)blockIdx.x - L.cb) * (kGridThreads / G);
+        if (slot0 >= L.d.nA) break;
         const int slot = r * L.groups + vt / G;
         const bool active = slot < L.d.nA;
         const int i = active ? __ldcg(L.d.A + slot) : -1;
+        const bool lead = active && g == 0;
+        const int lr = t / G;                                  // local receiver
+        if (lead) sidx[lr] = i;
         double s[3];
-        if constexpr (P == FSI_MIXED) {
-            MixI p{};
-            if (active) {
-                const RecMix ri = g_ld(rin + i);
-                p.xh = ri.hi.x; p.yh = ri.hi.y; p.zh = ri.hi.z;
-                p.xl = ri.lo.x; p.yl = ri.lo.y; p.zl = ri.lo.z;
-                if (KIND == 1) {
-                    const float4 ai = g_ld(arec + i);
-                    p.ax = ai.x; p.ay = ai.y; p.az = ai.z;
-                }
-            }
-            const float eps2f = (float)a.s.eps2;
-            float f[3] = {0.f, 0.f, 0.f}, sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
-            int cnt = 0;
-            for (int q0 = 0; q0 < L.d.nB; q0 += kGridChunk) {
-                const int cn = min(kGridChunk, L.d.nB - q0);
-                __syncthreads();
-                for (int u = t; u < cn; u += kGridThreads) {
-                    const int j = __ldcg(L.d.B + q0 + u);
-                    srec[u] = g_ld(rin + j);
-                    if (KIND == 1) sacc[u] = g_ld(arec + j);
-                    if (SELF) sid[u] = j;
-                }
-                __syncthreads();
+        for (int part = 0; part < nparts; ++part) {
+            const int* B = part ? L.d.B2 : L.d.B;
+            const int nB = part ? L.d.nB2 : L.d.nB;
+            if constexpr (P == FSI_MIXED) {
+                MixI p{};
                 if (active) {
-                    for (int u = g; u < cn; u += G) {
-                        const RecMix rj = srec[u];
-                        if (KIND == 0) mix_acc_pair<SELF>(rj.hi, rj.lo, p, eps2f, SELF && sid[u] == i, f[0], f[1], f[2]);
-                        else mix_grad_pair<SELF>(rj.hi, rj.lo, sacc[u], p, eps2f, SELF && sid[u] == i, f[0], f[1], f[2]);
-                        if (++cnt == kGridRun) {
+                    const RecMix ri = g_ld(rin + i);
+                    p.xh = ri.hi.x; p.yh = ri.hi.y; p.zh = ri.hi.z;
+                    p.xl = ri.lo.x; p.yl = ri.lo.y; p.zl = ri.lo.z;
+                    if (KIND == 1) {
+                        const float4 ai = g_ld(arec + i);
+                        p.ax = ai.x; p.ay = ai.y; p.az = ai.z;
+                    }
+                }
+                const float eps2f = (float)a.s.eps2;
+                float f[3] = {0.f, 0.f, 0.f}, sh[3] = {0.f, 0.f, 0.f}, sl[3] = {0.f, 0.f, 0.f};
+                int cnt = 0;
+                for (int q0 = 0; q0 < nB; q0 += kGridChunk) {
+                    const int cn = min(kGridChunk, nB - q0);
+                    __syncthreads();
+                    for (int u = t; u < cn; u += kGridThreads) {
+                        const int j = __ldcg(B + q0 + u);
+                        srec[u] = g_ld(rin + j);
+                        if (KIND == 1) sacc[u] = g_ld(arec + j);
+                        if (SELF) sid[u] = j;
+                    }
+                    __syncthreads();
+                    if (active) {
+                        for (int u = g; u < cn; u += G) {
+                            const RecMix rj = srec[u];
+                            if (KIND == 0) mix_acc_pair<SELF>(rj.hi, rj.lo, p, eps2f, SELF && sid[u] == i, f[0], f[1], f[2]);
+                            else mix_grad_pair<SELF>(rj.hi, rj.lo, sacc[u], p, eps2f, SELF && sid[u] == i, f[0], f[1], f[2]);
+                            if (++cnt == kGridRun) {
 #pragma unroll
-                            for (int c = 0; c < 3; ++c) { ff_acc(sh[c], sl[c], f[c]); f[c] = 0.f; }
-                            cnt = 0;
+                                for (int c = 0; c < 3; ++c) { ff_acc(sh[c], sl[c], f[c]); f[c] = 0.f; }
+                                cnt = 0;
+                            }
                         }
                     }
                 }
-            }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) ff_acc(sh[c], sl[c], f[c]);
-            for (int o = G >> 1; o > 0; o >>= 1)
+                for (int c = 0; c < 3; ++c) ff_acc(sh[c], sl[c], f[c]);
+                for (int o = G >> 1; o > 0; o >>= 1)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) {
-                    const float oh = __shfl_xor_sync(0xffffffffu, sh[c], o);
-                    const float ol = __shfl_xor_sync(0xffffffffu, sl[c], o);
-                    ff_acc(sh[c], sl[c], oh);
-                    sl[c] = __fadd_rn(sl[c], ol);
-                }
+                    for (int c = 0; c < 3; ++c) {
+                        const float oh = __shfl_xor_sync(0xffffffffu, sh[c], o);
+                        const float ol = __shfl_xor_sync(0xffffffffu, sl[c], o);
+                        ff_acc(sh[c], sl[c], oh);
+                        sl[c] = __fadd_rn(sl[c], ol);
+                    }
 #pragma unroll
-            for (int c = 0; c < 3; ++c) s[c] = (double)sh[c] + (double)sl[c];
-        } else {
-            F64I p{};
-            if (active) {
-                const D4 ri = g_ld(rin + i);
-                p.x = ri.x; p.y = ri.y; p.z = ri.z;
-                if (KIND == 1) {
-                    const D4 ai = g_ld(arec + i);
-                    p.ax = ai.x; p.ay = ai.y; p.az = ai.z;
-                }
-            }
-            double f[3] = {0.0, 0.0, 0.0};
-            for (int q0 = 0; q0 < L.d.nB; q0 += kGridChunk) {
-                const int cn = min(kGridChunk, L.d.nB - q0);
-                __syncthreads();
-                for (int u = t; u < cn; u += kGridThreads) {
-                    const int j = __ldcg(L.d.B + q0 + u);
-                    srec[u] = g_ld(rin + j);
-                    if (KIND == 1) sacc[u] = g_ld(arec + j);
-                    if (SELF) sid[u] = j;
-                }
-                __syncthreads();
+                for (int c = 0; c < 3; ++c) s[c] = (double)sh[c] + (double)sl[c];
+            } else {
+                F64I p{};
                 if (active) {
-                    for (int u = g; u < cn; u += G) {
-                        if (KIND == 0) f64_acc_pair<SELF>(srec[u], p, a.s.eps2, SELF && sid[u] == i, f[0], f[1], f[2]);
-                        else f64_grad_pair<SELF>(srec[u], sacc[u], p, a.s.eps2, SELF && sid[u] == i, f[0], f[1], f[2]);
+                    const D4 ri = g_ld(rin + i);
+                    p.x = ri.x; p.y = ri.y; p.z = ri.z;
+                    if (KIND == 1) {
+                        const D4 ai = g_ld(arec + i);
+                        p.ax = ai.x; p.ay = ai.y; p.az = ai.z;
                     }
                 }
+                double f[3] = {0.0, 0.0, 0.0};
+                for (int q0 = 0; q0 < nB; q0 += kGridChunk) {
+                    const int cn = min(kGridChunk, nB - q0);
+                    __syncthreads();
+                    for (int u = t; u < cn; u += kGridThreads) {
+                        const int j = __ldcg(B + q0 + u);
+                        srec[u] = g_ld(rin + j);
+                        if (KIND == 1) sacc[u] = g_ld(arec + j);
+                        if (SELF) sid[u] = j;
+                    }
+                    __syncthreads();
+                    if (active) {
+                        for (int u = g; u < cn; u += G) {
+                            if (KIND == 0) f64_acc_pair<SELF>(srec[u], p, a.s.eps2, SELF && sid[u] == i, f[0], f[1], f[2]);
+                            else f64_grad_pair<SELF>(srec[u], sacc[u], p, a.s.eps2, SELF && sid[u] == i, f[0], f[1], f[2]);
+                        }
+                    }
+                }
+                for (int o = G >> 1; o > 0; o >>= 1)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) f[c] += __shfl_xor_sync(0xffffffffu, f[c], o);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) s[c] = f[c];
             }
-            for (int o = G >> 1; o > 0; o >>= 1)
+            if (lead)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) f[c] += __shfl_xor_sync(0xffffffffu, f[c], o);
-#pragma unroll
-            for (int c = 0; c < 3; ++c) s[c] = f[c];
+                for (int c = 0; c < 3; ++c) ssum[6 * lr + 3 * part + c] = s[c];
         }
-        if (active && g == 0) g_epilogue<P, KIND>(a, e, i, s);
+        // epilogues, one local receiver per lane
+        __syncthreads();
+        const int nloc = min(kGridThreads / G, L.d.nA - slot0);
+        for (int u = t; u < nloc; u += kGridThreads) {
+            const double s1[3] = {ssum[6 * u], ssum[6 * u + 1], ssum[6 * u + 2]};
+            g_epilogue<P, KIND>(a, e, sidx[u], s1, nparts == 2 ? ssum + 6 * u + 3 : nullptr);
+        }
+        __syncthreads();
     }
 }
 
@@ -370,6 +432,8 @@ __device__ void g_steps(const GridArgs& a, unsigned char* smem, const int* Lst, 
     GRec<P>* srec = reinterpret_cast<GRec<P>*>(smem);
     GVec<P>* svel = reinterpret_cast<GVec<P>*>(smem + kGridChunk * sizeof(GRec<P>));
     int* sid = reinterpret_cast<int*>(smem + kGridChunk * (sizeof(GRec<P>) + sizeof(GVec<P>)));
+    StepAcc<T>* sst = reinterpret_cast<StepAcc<T>*>(smem + GSm<P>::sum);
+    int* sidx = reinterpret_cast<int*>(smem + GSm<P>::sum + kGridThreads * sizeof(StepAcc<T>));
     const int G = L.G;
     const int vt = ((int)blockIdx.x - L.cb) * kGridThreads + t;
     const int g = vt & (G - 1);
@@ -434,7 +498,18 @@ __device__ void g_steps(const GridArgs& a, unsigned char* smem, const int* Lst, 
             acc.jz += __shfl_xor_sync(0xffffffffu, acc.jz, o);
         }
         if (coincident) set_error(a.s.err, FSI_ERR_COINCIDENT);
-        if (active && g == 0) a.st[i] = step_finish<T>(acc, a.s.eta_ff, a.s.eta_fb, a.s.eta_jerk);
+        // the FP64 finish with one receiver per lane
+        const int lr = t / G;
+        if (active && g == 0) {
+            sst[lr] = acc;
+            sidx[lr] = i;
+        }
+        __syncthreads();
+        const int slot0 = r * L.groups + ((int)blockIdx.x - L.cb) * (kGridThreads / G);
+        const int nloc = min(kGridThreads / G, n - slot0);
+        for (int u = t; u < nloc; u += kGridThreads)
+            a.st[sidx[u]] = step_finish<T>(sst[u], a.s.eta_ff, a.s.eta_fb, a.s.eta_jerk);
+        __syncthreads();
     }
 }
 
@@ -468,15 +543,18 @@ __device__ void g_grad_steps(const GridArgs& a, const int* Lst, int n) {
     }
 }
 
-// Stable split of list L (CTA 0 only) into S = {st >= tau} at out[0, nS) and F at
-// out[nS, n), with the level-step rule (level 0 records its steps as the level-0 steps,
-// deeper levels take the min with them).  With force_slow every particle stays in S, which
-// is then L itself and nothing is written.  Counts go to bar[2], bar[3].
-__device__ void g_split(const GridArgs& a, const int* Lst, int n, double tau, int level,
-                        bool force_slow, bool room, int* out) {
+// Stable split of list L into S = {st >= tau} at out[0, nS) and F at out[nS, n), with
+// the level-step rule (level 0 records its steps as the level-0 steps, deeper levels take
+// the min with them); returns nS.  Every CTA runs it and writes the same lists (no grid
+// barrier is needed before a CTA reads them: the lists it reads are the ones it wrote);
+// CTA 0 alone records the level-0 steps and the statistics.  With force_slow every
+// particle stays in S, which is then L itself and nothing is written.
+__device__ int g_split(const GridArgs& a, const int* Lst, int n, double tau, int level,
+                       bool force_slow, bool room, int* out) {
     __shared__ int wS[kGridThreads / 32];
     __shared__ int s_base, s_total, s_anyfast;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
+    const bool cta0 = blockIdx.x == 0;
     auto step_of = [&](int i) {
         const double st = __ldcg(a.st + i);
         return level == 0 ? st : fmin(st, __ldcg(a.s.step0 + i));
@@ -490,7 +568,7 @@ __device__ void g_split(const GridArgs& a, const int* Lst, int n, double tau, in
         if (k < n) {
             const int i = __ldcg(Lst + k);
             const double st = step_of(i);
-            if (level == 0 && a.step0w) a.step0w[i] = st;
+            if (cta0 && level == 0 && a.step0w) a.step0w[i] = st;
             const bool fast = st < tau;
             if (fast && force_slow) s_anyfast = 1;
             slow = force_slow || !fast;
@@ -525,15 +603,15 @@ __device__ void g_split(const GridArgs& a, const int* Lst, int n, double tau, in
             __syncthreads();
         }
     }
-    if (t == 0) {
-        a.bar[2] = (unsigned long long)nS;
-        a.bar[3] = (unsigned long long)(n - nS);
+    if (cta0 && t == 0) {
         if (a.s.level_counts) atomicAdd(a.s.level_counts + level, (unsigned long long)nS);
         if (force_slow && s_anyfast) {
             atomicExch(a.s.maxlevel_hit, 1);
             if (!room) set_error(a.s.err, FSI_ERR_MAXLEVEL);
         }
     }
+    __syncthreads();
+    return nS;
 }
 
 // ---------------------------------------------------------------------------------
@@ -543,31 +621,57 @@ __device__ bool g_cross(const GridArgs& a, unsigned char* smem, GCtl& C, unsigne
                         const int* Ls, int nS, const int* Lf, int nF, double w, bool gradient, double cg) {
     const GDir d0{Ls, nS, Lf, nF}, d1{Lf, nF, Ls, nS};
     if (!gradient) {
-        g_pass<P, 0, false>(a, smem, d0, d1, GEpi{0, nullptr, w, 0.0, 0.0, a.rec[0], nullptr});
+        const GEpi e{0, nullptr, w, 0.0, 0.0, a.rec[0], nullptr};
+        g_pass<P, 0, false>(a, smem, d0, d1, e, e);
         GSYNC(kPhCross);
         return true;
     }
-    g_pass<P, 0, false>(a, smem, d0, d1, GEpi{1, nullptr, 0.0, 0.0, 0.0, a.rec[0], nullptr});
+    const GEpi es{1, nullptr, 0.0, 0.0, 0.0, a.rec[0], nullptr};
+    g_pass<P, 0, false>(a, smem, d0, d1, es, es);
     GSYNC(kPhCross);
-    g_pass<P, 1, false>(a, smem, d0, d1, GEpi{0, nullptr, w, cg, 0.0, a.rec[0], nullptr});
+    const GEpi eg{0, nullptr, w, cg, 0.0, a.rec[0], nullptr};
+    g_pass<P, 1, false>(a, smem, d0, d1, eg, eg);
     GSYNC(kPhCross);
     return true;
 }
 
 // FSI(S, h) (Sect. 2.1, Eq. fsi-cycle): kick h/6 + drift h/2, a (stored), gradient kick
 // 2h/3 with a + (h^2/24) G + drift h/2, kick h/6.  Records: rec0 -> rec1 -> rec0.
+// w_open != 0: the inter-level kick of S and F with that weight, which comes right before
+// the cycle, shares its first pass; w_close != 0: the one right after the cycle shares its
+// last pass.  S sums its F sources apart from its S sources and F receives from S in the
+// same phase; the kicks are applied in the order of the unfused sequence.
 template <int P>
 __device__ bool g_fsi(const GridArgs& a, unsigned char* smem, GCtl& C, unsigned long long& target,
-                      const int* Ls, int nS, double h) {
+                      const int* Ls, int nS, const int* Lf, int nF, double h, double w_open,
+                      double w_close) {
     const GDir d{Ls, nS, Ls, nS}, none{nullptr, 0, nullptr, 0};
-    g_pass<P, 0, true>(a, smem, d, none, GEpi{0, nullptr, h / 6.0, 0.0, 0.5 * h, a.rec[0], a.rec[1]});
-    GSYNC(kPhFsi);
-    g_pass<P, 0, true>(a, smem, d, none, GEpi{1, nullptr, 0.0, 0.0, 0.0, a.rec[1], nullptr});
-    GSYNC(kPhFsi);
-    g_pass<P, 1, true>(a, smem, d, none, GEpi{0, nullptr, 2.0 * h / 3.0, h * h / 24.0, 0.5 * h, a.rec[1], a.rec[0]});
-    GSYNC(kPhFsi);
-    g_pass<P, 0, true>(a, smem, d, none, GEpi{0, nullptr, h / 6.0, 0.0, 0.0, a.rec[0], nullptr});
-    GSYNC(kPhFsi);
+    const GDir dSF{Ls, nS, Ls, nS, Lf, nF}, dF{Lf, nF, Ls, nS};
+    const bool open = w_open != 0.0 && nF > 0, close = w_close != 0.0 && nF > 0;
+    {
+        const GEpi e{0, nullptr, h / 6.0, 0.0, 0.5 * h, a.rec[0], a.rec[1], w_open, 1};
+        const GEpi ef{0, nullptr, w_open, 0.0, 0.0, a.rec[0], nullptr};
+        if (open) g_pass<P, 0, true>(a, smem, dSF, dF, e, ef);
+        else g_pass<P, 0, true>(a, smem, d, none, e, e);
+        GSYNC(open ? kPhCross : kPhFsi);
+    }
+    {
+        const GEpi e{1, nullptr, 0.0, 0.0, 0.0, a.rec[1], nullptr};
+        g_pass<P, 0, true>(a, smem, d, none, e, e);
+        GSYNC(kPhFsi);
+    }
+    {
+        const GEpi e{0, nullptr, 2.0 * h / 3.0, h * h / 24.0, 0.5 * h, a.rec[1], a.rec[0]};
+        g_pass<P, 1, true>(a, smem, d, none, e, e);
+        GSYNC(kPhFsi);
+    }
+    {
+        const GEpi e{0, nullptr, h / 6.0, 0.0, 0.0, a.rec[0], nullptr, w_close, 0};
+        const GEpi ef{0, nullptr, w_close, 0.0, 0.0, a.rec[0], nullptr};
+        if (close) g_pass<P, 0, true>(a, smem, dSF, dF, e, ef);
+        else g_pass<P, 0, true>(a, smem, d, none, e, e);
+        GSYNC(close ? kPhCross : kPhFsi);
+    }
     return true;
 }
 
@@ -580,9 +684,11 @@ __device__ bool g_assign(const GridArgs& a, unsigned char* smem, GCtl& C, unsign
     GSYNC(kPhSteps);
     if (a.s.eta_grad > 0.0 || a.s.eta_va > 0.0) {
         const GDir d{Lst, f.nP, Lst, f.nP}, none{nullptr, 0, nullptr, 0};
-        g_pass<P, 0, true>(a, smem, d, none, GEpi{1, nullptr, 0.0, 0.0, 0.0, a.rec[0], nullptr});
+        const GEpi es{1, nullptr, 0.0, 0.0, 0.0, a.rec[0], nullptr};
+        g_pass<P, 0, true>(a, smem, d, none, es, es);
         GSYNC(kPhCrit);
-        g_pass<P, 1, true>(a, smem, d, none, GEpi{0, a.aux, 0.0, 0.0, 0.0, a.rec[0], nullptr});
+        const GEpi eo{0, a.aux, 0.0, 0.0, 0.0, a.rec[0], nullptr};
+        g_pass<P, 1, true>(a, smem, d, none, eo, eo);
         GSYNC(kPhCrit);
         g_grad_steps(a, Lst, f.nP);
         GSYNC(kPhCrit);
@@ -590,17 +696,11 @@ __device__ bool g_assign(const GridArgs& a, unsigned char* smem, GCtl& C, unsign
     const long long lt = C.list_top;
     const bool room = lt + f.nP <= a.list_cap;
     const bool stop = f.level >= a.s.max_level || !room;
-    if (blockIdx.x == 0) g_split(a, Lst, f.nP, f.tau, f.level, stop, room, a.lists + lt);
-    GSYNC(kPhSplit);
-    if (threadIdx.x == 0) {
-        C.nS = (int)__ldcg(a.bar + 2);
-        C.nF = (int)__ldcg(a.bar + 3);
-    }
-    __syncthreads();
+    const int nS = g_split(a, Lst, f.nP, f.tau, f.level, stop, room, a.lists + lt);
     f.offS = stop ? f.offP : (int)lt;
-    f.nS = C.nS;
-    f.offF = f.offS + f.nS;
-    f.nF = C.nF;
+    f.nS = nS;
+    f.offF = f.offS + nS;
+    f.nF = f.nP - nS;
     return true;
 }
 
@@ -634,11 +734,9 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
             const double tau = f.tau;
             if (f.stage == 0) {
                 if (!g_assign<P>(a, smem, C, target, f)) return false;
-                const int* Ls = a.lists + f.offS;
-                const int* Lf = a.lists + f.offF;
-                if (f.nS > 0 && f.nF > 0 &&
-                    !g_cross<P>(a, smem, C, target, Ls, f.nS, Lf, f.nF, tau / 6.0, false, 0.0)) return false;
-                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, Ls, f.nS, 0.5 * tau)) return false;
+                // U_SF(tau/6) then FSI(S, tau/2): the kick shares the cycle's first pass
+                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, a.lists + f.offS, f.nS, a.lists + f.offF,
+                                          f.nF, 0.5 * tau, tau / 6.0, 0.0)) return false;
                 f.stage = 1;
             } else if (f.stage == 1) {
                 if (f.nS > 0 && f.nF > 0 &&
@@ -646,11 +744,9 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
                                 2.0 * tau / 3.0, true, tau * tau / 24.0)) return false;
                 f.stage = 2;
             } else {
-                const int* Ls = a.lists + f.offS;
-                const int* Lf = a.lists + f.offF;
-                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, Ls, f.nS, 0.5 * tau)) return false;
-                if (f.nS > 0 && f.nF > 0 &&
-                    !g_cross<P>(a, smem, C, target, Ls, f.nS, Lf, f.nF, tau / 6.0, false, 0.0)) return false;
+                // FSI(S, tau/2) then U_SF(tau/6): the kick shares the cycle's last pass
+                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, a.lists + f.offS, f.nS, a.lists + f.offF,
+                                          f.nF, 0.5 * tau, 0.0, tau / 6.0)) return false;
                 f.stage = 3;
             }
             __syncthreads();
@@ -705,8 +801,8 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
 
 static size_t grid_smem_bytes(int precision) {
     const size_t stage = precision == FSI_MIXED
-        ? (size_t)kGridChunk * (sizeof(RecMix) + sizeof(float4) + sizeof(int))
-        : (size_t)kGridChunk * (sizeof(D4) + sizeof(D4) + sizeof(int));
+        ? std::max(GSm<FSI_MIXED>::bytes, GSm<FSI_MIXED>::sum + kGridThreads * (sizeof(StepAcc<float>) + sizeof(int)))
+        : std::max(GSm<FSI_FP64>::bytes, GSm<FSI_FP64>::sum + kGridThreads * (sizeof(StepAcc<double>) + sizeof(int)));
     const size_t small = precision == FSI_MIXED ? sizeof(SmallSmem<FSI_MIXED>) : sizeof(SmallSmem<FSI_FP64>);
     return stage > small ? stage : small;
 }
