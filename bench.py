@@ -527,6 +527,7 @@ def run_ensemble(args):
     sampler = ClockSampler(0)
     sampler.start()
     F.fsi_batch_stats(b, reset=True)
+    F.fsi_batch_item_stats(b, reset=True)
     ms = []
     for _ in range(args.steps):
         flush.zero_()
@@ -538,6 +539,7 @@ def run_ensemble(args):
         ms.append(e0.elapsed_time(e1))
     clocks = sampler.stop()
     wait_ns, life_ns, ctas = F.fsi_batch_stats(b)
+    item_stats = F.fsi_batch_item_stats(b)
     de = np.abs((energies() - e_start) / e_start)
     assert F.fsi_sync_status(ctx) == F.FSI_OK
     t = sum(ms) / 1e3
@@ -546,6 +548,9 @@ def run_ensemble(args):
     cap_ns = ctas * t * 1e9
     idle = {"fraction": 1.0 - (life_ns - wait_ns) / cap_ns, "phase_waits": wait_ns / cap_ns,
             "tail": 1.0 - life_ns / cap_ns, "ctas": ctas}
+    # busy CTA time by work-item kind (symmetric form), as fractions of the CTA capacity
+    busy = {k: {"fraction": ns / cap_ns, "items": n}
+            for k, (ns, n) in zip(("own_pairs", "two_blocks", "pack_apply"), item_stats)}
     value = per_call * args.steps / t
     ach = value * FLOP_PAIR / 1e12
     peak = fp32_peak_tflops(sm_count(dev)) if args.precision == "mixed" else fp64_peak_tflops(sm_count(dev))
@@ -564,7 +569,7 @@ def run_ensemble(args):
         "roofline": {"bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                      "frac": ach / peak, "traffic": None,
                      "kernel": "batch_sym_kernel" if best[1][0] == 4 else "batch_kernel"},
-        "idle": idle,
+        "idle": idle, "busy": busy,
         # fixed h, no softening: a few of the smallest clusters meet close encounters the
         # step does not resolve (the oracle's own FSI gives |dE/E| ~ 1-10 on them)
         "energy": {"fsi_cycles": (args.warmup + args.steps) * S, "h": 1e-3,

@@ -123,7 +123,9 @@ typedef struct fsi_params {
                              interval of N <= hhs_grid_max particles is that one launch
                              (no host synchronisation, so it can be captured in a CUDA
                              graph; see fsi_hhs_interval).  Only summation orders differ
-                             from the host walk. */
+                             from the host walk.  Raising it to N makes any interval
+                             (PN off) capturable; its large levels then run the launch's
+                             one-sided passes (an N = 65536 interval: ~2x the time). */
 } fsi_params;
 
 /* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,
@@ -364,6 +366,13 @@ int fsi_batch_get_tuning(fsi_batch *batch, int *ipt, int *ctas_per_sm);
  * launch ends.  Synchronises the device; reset != 0 zeroes the counters after reading. */
 int fsi_batch_stats(fsi_batch *batch, long long *wait_ns, long long *life_ns, int *ctas,
                     int reset);
+
+/* Busy time of the symmetric persistent launches' work items by kind since the last
+ * reset: ns[0] / items[0] the sum items of a block with itself (its own pairs), [1] the
+ * sum items of two blocks, [2] pack and apply items (thread 0 of the CTA, from the end of
+ * the item's phase wait to its completion signal).  ns, items: host long long[3].
+ * Synchronises the device; reset != 0 zeroes these counters after reading. */
+int fsi_batch_item_stats(fsi_batch *batch, long long *ns, long long *items, int reset);
 
 /* Test hook: during the next fsi_batch_step the items of `cluster` wait for a phase
  * count that is never reached, so their bounded waits run out and the launch ends with

@@ -740,6 +740,10 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_sym_kernel(
             __syncthreads();
             if (s_flag) { batch_stats_exit(a, t_start, waited); return; }
         }
+        // item time by kind (stats[2 + k] ns, stats[5 + k] items): k = 0 a sum item of a
+        // block with itself, 1 a sum item of two blocks, 2 a pack or apply item
+        const long long t_item = global_ns();
+        const int ikind = is_sum ? (sitems[r].t0 == sitems[r].block * I ? 0 : 1) : 2;
         const int role = phase == 0 ? 0 : (pass == 0 ? 1 : 2 + (pass - 1) % 3);
         if (phase == 0) {
             // pack the block's records from x
@@ -795,6 +799,10 @@ __global__ void __launch_bounds__(kBatchThreads, MINB) batch_sym_kernel(
         if (tid == 0) {
             __threadfence();
             atomicAdd(a.done + (size_t)cluster * a.nphase + phase, 1);
+            if (a.stats) {
+                atomicAdd(a.stats + 2 + ikind, (unsigned long long)(global_ns() - t_item));
+                atomicAdd(a.stats + 5 + ikind, 1ull);
+            }
         }
     }
 }

@@ -1824,8 +1824,8 @@ int fsi_batch_create(fsi_ctx* c, int K, const long long* offsets, int max_steps,
     if (rc == FSI_OK) rc = ensure(b->ac, 3 * (size_t)ntot * 8);
     if (rc == FSI_OK) rc = ensure(b->done, (size_t)K * nphase * sizeof(int));
     if (rc == FSI_OK) rc = ensure(b->ctrl, 64);
-    if (rc == FSI_OK) rc = ensure(b->stats, 2 * sizeof(unsigned long long));
-    if (rc == FSI_OK && cudaMemset(b->stats.p, 0, 2 * sizeof(unsigned long long)) != cudaSuccess)
+    if (rc == FSI_OK) rc = ensure(b->stats, 8 * sizeof(unsigned long long));
+    if (rc == FSI_OK && cudaMemset(b->stats.p, 0, 8 * sizeof(unsigned long long)) != cudaSuccess)
         rc = fail(FSI_ERR_CUDA, "batch counters");
     if (rc == FSI_OK) {
         b->ctas_per_sm = std::max(1, batch_max_ctas_per_sm(c->p.precision, b->ipt));
@@ -1884,6 +1884,21 @@ int fsi_batch_stats(fsi_batch* b, long long* wait_ns, long long* life_ns, int* c
     if (wait_ns) *wait_ns = (long long)st[0];
     if (life_ns) *life_ns = (long long)st[1];
     if (ctas) *ctas = b->last_ctas;
+    return FSI_OK;
+}
+
+int fsi_batch_item_stats(fsi_batch* b, long long* ns, long long* items, int reset) {
+    if (!b || !ns || !items) return fail(FSI_ERR_ARG, "NULL argument");
+    unsigned long long st[6] = {};
+    if (cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemcpy(st, P<unsigned long long>(b->stats) + 2, sizeof st, cudaMemcpyDeviceToHost) != cudaSuccess)
+        return fail(FSI_ERR_CUDA, "batch counters read");
+    if (reset && cudaMemset(P<unsigned long long>(b->stats) + 2, 0, sizeof st) != cudaSuccess)
+        return fail(FSI_ERR_CUDA, "batch counters reset");
+    for (int k = 0; k < 3; ++k) {
+        ns[k] = (long long)st[k];
+        items[k] = (long long)st[3 + k];
+    }
     return FSI_OK;
 }
 

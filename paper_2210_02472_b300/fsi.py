@@ -41,7 +41,8 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_fma_probe", "fsi_autotune", "fsi_get_tuning", "fsi_set_tuning",
             "fsi_step_vjp", "fsi_step_vjp_rec", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall", "fsi_batch_stats",
-            "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for", "fsi_grid_stats"]
+            "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for", "fsi_grid_stats",
+            "fsi_batch_item_stats"]
 
 
 class fsi_params(C.Structure):
@@ -82,6 +83,7 @@ _lib.fsi_accel_noalloc.argtypes = [_ip, _vp, _vp, _dp, _vp, _vp]
 _lib.fsi_work_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip]
 _lib.fsi_far_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip, _vp]
 _lib.fsi_grid_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip, _vp]
+_lib.fsi_batch_item_stats.argtypes = [_vp, C.POINTER(C.c_longlong), C.POINTER(C.c_longlong), _ip]
 _lib.fsi_fma_probe.argtypes = [_ip, _ip, _ip, _vp, C.POINTER(C.c_double), _vp]
 _lib.fsi_autotune.argtypes = [_vp, _ip, _vp, _vp, _ip, _ip, _vp]
 _lib.fsi_get_tuning.argtypes = [_vp, C.POINTER(_ip), C.POINTER(_ip)]
@@ -169,6 +171,14 @@ class Context:
         h = _vp()
         _check(_lib.fsi_create(C.byref(h), C.byref(p)), "fsi_create")
         self.handle = h
+
+    def set_params(self, **fields) -> None:
+        """Change fields of the context's fsi_params (fsi_set_params), e.g. timeout_ns=0."""
+        for k, v in fields.items():
+            if not hasattr(self.params, k):
+                raise AttributeError(k)
+            setattr(self.params, k, v)
+        _check(_lib.fsi_set_params(self.handle, C.byref(self.params)), "fsi_set_params")
 
     def close(self) -> None:
         if getattr(self, "handle", None):
@@ -522,6 +532,15 @@ def fsi_batch_stats(batch: Batch, reset: bool = False):
     _check(_lib.fsi_batch_stats(batch.handle, C.byref(w), C.byref(l), C.byref(n), int(bool(reset))),
            "fsi_batch_stats")
     return int(w.value), int(l.value), int(n.value)
+
+
+def fsi_batch_item_stats(batch: Batch, reset: bool = False):
+    """Busy ns and item counts of the symmetric launches' work items by kind: (own-pair sum
+    items, two-block sum items, pack / apply items), each a (ns, items) pair."""
+    ns = (C.c_longlong * 3)()
+    it = (C.c_longlong * 3)()
+    _check(_lib.fsi_batch_item_stats(batch.handle, ns, it, int(bool(reset))), "fsi_batch_item_stats")
+    return [(int(ns[k]), int(it[k])) for k in range(3)]
 
 
 def fsi_batch_inject_stall(batch: Batch, cluster: int) -> None:

@@ -651,17 +651,18 @@ def test_hhs_interval_large_cross_passes(F, prec, symmetric, grid):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_hhs_interval_graph_capture(F, prec):
-    """An HHS interval of N <= hhs_grid_max is one cooperative launch with no host
-    synchronisation: captured in a CUDA graph and replayed, it reproduces the uncaptured
-    interval bit for bit (positions, velocities, level statistics), twice in a row; the
-    uncaptured interval matches the oracle.  An interval that needs the host walk refuses
-    capture with FSI_ERR_UNSUPPORTED."""
-    c = inputs.plummer(2000, 31, imf="kroupa")
+@pytest.mark.parametrize("n,cap", [(2000, 0), (6000, 6000)])
+def test_hhs_interval_graph_capture(F, prec, n, cap):
+    """An HHS interval of N <= hhs_grid_max (4096 by default, raised to 6000 here) is one
+    cooperative launch with no host synchronisation: captured in a CUDA graph and
+    replayed, it reproduces the uncaptured interval bit for bit (positions, velocities,
+    level statistics), twice in a row; the uncaptured interval matches the oracle.  An
+    interval that needs the host walk refuses capture with FSI_ERR_UNSUPPORTED."""
+    c = inputs.plummer(n, 31, imf="kroupa")
     tau = 1.0 / 32
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
     m = dev(c.mass)
-    with F.Context(prec) as ctx:
+    with F.Context(prec, hhs_grid_max=cap) as ctx:
         p1, v1 = dev(c.pos), dev(c.vel)
         assert F.fsi_hhs_interval(ctx, p1, v1, m, tau) == F.FSI_OK
         lv1 = F.fsi_level_stats(ctx)
@@ -683,7 +684,7 @@ def test_hhs_interval_graph_capture(F, prec):
     tol = 1e-11 if prec == "fp64" else 1e-7
     assert np.abs(p - rp).max() <= tol
     assert np.abs(v - rv).max() <= tol * 100
-    with F.Context(prec, hhs_grid_max=1000) as ctx:
+    with F.Context(prec, hhs_grid_max=n // 2) as ctx:
         p3, v3 = dev(c.pos), dev(c.vel)
         F.fsi_hhs_interval(ctx, p3, v3, m, tau)             # workspace, uncaptured
         torch.cuda.synchronize()
@@ -693,6 +694,31 @@ def test_hhs_interval_graph_capture(F, prec):
                 F.fsi_hhs_interval(ctx, p3, v3, m, tau)
         assert ei.value.code == F.FSI_ERR_UNSUPPORTED
         torch.cuda.synchronize()
+
+
+def test_hhs_grid_barrier_timeout(F):
+    """A grid barrier wait of the cooperative HHS launch that runs out (timeout_ns = 1 ns, so
+    a CTA that arrives early gives up after its first clock check) latches FSI_ERR_TIMEOUT,
+    raises the abort flag and ends the launch instead of hanging; the context then runs a
+    normal interval that matches the oracle."""
+    c = inputs.plummer(2000, 31, imf="kroupa")
+    tau = 1.0 / 32
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    m = dev(c.mass)
+    with F.Context("mixed", timeout_ns=1) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        F.fsi_hhs_interval(ctx, p, v, m, tau)
+        assert F.fsi_sync_status(ctx) == F.FSI_ERR_TIMEOUT
+        ctx.set_params(timeout_ns=0)
+        p, v = dev(c.pos), dev(c.vel)
+        assert F.fsi_hhs_interval(ctx, p, v, m, tau) == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    assert np.abs(p - rp).max() <= 1e-7
+    assert np.abs(v - rv).max() <= 1e-5
 
 
 def test_hhs_interval_morton_ordered_levels(F):
