@@ -126,6 +126,8 @@ typedef struct fsi_params {
                              from the host walk.  Raising it to N makes any interval
                              (PN off) capturable; its large levels then run the launch's
                              one-sided passes (an N = 65536 interval: ~2x the time). */
+    int hhs_grid_ctas;    /* CTAs of that cooperative launch (0 = one per SM, the most that
+                             are co-resident; otherwise clamped to [2, that maximum]). */
 } fsi_params;
 
 /* Fill *p with the defaults (FP64, eps2 0, eta 0.2/0.2/0.1, max_level 40, PN off,

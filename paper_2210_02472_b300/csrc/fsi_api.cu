@@ -804,7 +804,7 @@ int hhs_grid_cap(fsi_ctx* c) {
     if (c->p.hhs_grid_max < 0 || c->p.c > 0.0) return 0;
     const int prec = c->p.precision;
     if (c->grid_nctas[prec] < 0) c->grid_nctas[prec] = grid_ctas(prec, c->sm_count);
-    if (c->grid_nctas[prec] <= 0) return 0;
+    if (c->grid_nctas[prec] < 2) return 0;
     return c->p.hhs_grid_max == 0 ? kGridCapDefault : c->p.hhs_grid_max;
 }
 
@@ -857,7 +857,9 @@ int run_hhs_grid(fsi_ctx* c, int N, double* pos, double* vel, const double* mass
         }
         g.prof = P<unsigned long long>(c->gprof);
     }
-    CU(launch_hhs_grid(prec, g, c->grid_nctas[prec], s));
+    const int most = c->grid_nctas[prec];
+    const int ctas = c->p.hhs_grid_ctas > 0 ? std::min(most, std::max(2, c->p.hhs_grid_ctas)) : most;
+    CU(launch_hhs_grid(prec, g, ctas, s));
     return FSI_OK;
 }
 
@@ -979,6 +981,7 @@ void fsi_default_params(fsi_params* p) {
     p->eta_va = 0.0;
     p->wide_ctas = 0;
     p->hhs_grid_max = 0;
+    p->hhs_grid_ctas = 0;
 }
 
 const char* fsi_last_error(void) { return g_err.c_str(); }

@@ -51,7 +51,7 @@ class fsi_params(C.Structure):
                 ("c", C.c_double), ("split", C.c_int), ("timeout_ns", C.c_longlong),
                 ("symmetric", C.c_int), ("hhs_small_max", C.c_int), ("order_min", C.c_int),
                 ("eta_grad", C.c_double), ("eta_va", C.c_double), ("wide_ctas", C.c_int),
-                ("hhs_grid_max", C.c_int)]
+                ("hhs_grid_max", C.c_int), ("hhs_grid_ctas", C.c_int)]
 
 
 _vp, _ip, _dp = C.c_void_p, C.c_int, C.c_double
@@ -154,7 +154,8 @@ class Context:
                  eta_fb: float = 0.2, eta_jerk: float = 0.1, max_level: int = 40,
                  c: float = 0.0, split: int = 0, timeout_ns: int = 0, symmetric: bool = True,
                  hhs_small_max: int = 0, order_min: int = 0, eta_grad: float = 0.0,
-                 eta_va: float = 0.0, wide_ctas: int = 0, hhs_grid_max: int = 0):
+                 eta_va: float = 0.0, wide_ctas: int = 0, hhs_grid_max: int = 0,
+                 hhs_grid_ctas: int = 0):
         p = fsi_params()
         _lib.fsi_default_params(C.byref(p))
         p.precision = {"fp64": FSI_FP64, "mixed": FSI_MIXED}[precision]
@@ -166,6 +167,7 @@ class Context:
         p.eta_grad, p.eta_va = float(eta_grad), float(eta_va)
         p.wide_ctas = int(wide_ctas)
         p.hhs_grid_max = int(hhs_grid_max)
+        p.hhs_grid_ctas = int(hhs_grid_ctas)
         self.params = p
         self.precision = precision
         h = _vp()

@@ -696,6 +696,28 @@ def test_hhs_interval_graph_capture(F, prec, n, cap):
         torch.cuda.synchronize()
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("ctas", [2, 3, 7])
+def test_hhs_interval_grid_few_ctas(F, prec, ctas):
+    """The cooperative HHS launch on 2, 3 or 7 CTAs (hhs_grid_ctas): a phase then has more
+    receivers than lane groups, so every CTA takes several rounds of receivers, and the two
+    directions of an inter-level kick split an odd number of CTAs; against the oracle."""
+    c = inputs.plummer(2000, 37, imf="kroupa")
+    tau = 1.0 / 32
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    with F.Context(prec, hhs_grid_ctas=ctas) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        assert F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau) == F.FSI_OK
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
+
+
 def test_hhs_grid_barrier_timeout(F):
     """A grid barrier wait of the cooperative HHS launch that runs out (timeout_ns = 1 ns, so
     a CTA that arrives early gives up after its first clock check) latches FSI_ERR_TIMEOUT,
