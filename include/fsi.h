@@ -117,14 +117,14 @@ typedef struct fsi_params {
                              fewer CTAs than this takes the wide form instead: up to 32
                              lanes per receiver splitting its sources (0 = 32; -1 =
                              never).  Only the summation order differs. */
-    int hhs_grid_max;     /* HHS with PN off: a fast set of more than hhs_small_max and at
+    int hhs_grid_max;     /* HHS: a fast set of more than hhs_small_max and at
                              most this many particles (0 = 4096; -1 = never) runs its whole
                              recursion in one cooperative launch over the GPU, and an
                              interval of N <= hhs_grid_max particles is that one launch
                              (no host synchronisation, so it can be captured in a CUDA
                              graph; see fsi_hhs_interval).  Only summation orders differ
                              from the host walk.  Raising it to N makes any interval
-                             (PN off) capturable; its large levels then run the launch's
+                             capturable; its large levels then run the launch's
                              one-sided passes (an N = 65536 interval: ~2x the time). */
     int hhs_grid_ctas;    /* CTAs of that cooperative launch (0 = one per SM, the most that
                              are co-resident; otherwise clamped to [2, that maximum]). */
@@ -301,17 +301,18 @@ int fsi_energy(fsi_ctx *ctx, int N, const double *pos, const double *vel,
  * U_SF(tau/6) FSI(S, tau/2) HHS(F, tau/2) U~_SF(2 tau/3) HHS(F, tau/2) FSI(S, tau/2)
  * U_SF(tau/6).  In place on pos/vel.
  * How the levels run: the host walks the large levels (one device->host read of the
- * split counts per level visit, so the call is synchronous); with PN off, a fast set of
+ * split counts per level visit, so the call is synchronous); a fast set of
  * more than hhs_small_max and at most hhs_grid_max particles runs its whole recursion in
  * one cooperative launch over the GPU, and a fast set of at most hhs_small_max in one CTA.
- * When N <= hhs_grid_max (PN off) the whole interval is that one launch: the call then
+ * When N <= hhs_grid_max the whole interval is that one launch: the call then
  * does not synchronise with the host and may be captured in a CUDA graph (stream
  * capture); a replay repeats the interval bit for bit on the captured buffers.  Under
  * capture the level statistics stay on the device (fsi_level_stats reads those of the
  * last replay) and a depth-cap hit is latched as FSI_ERR_MAXLEVEL in the error word
  * (fsi_sync_status) instead of being returned.  An interval that needs the host walk
- * returns FSI_ERR_UNSUPPORTED when its stream is capturing.  Device waits are bounded by
- * fsi_params.timeout_ns (FSI_ERR_TIMEOUT latched on expiry). */
+ * returns FSI_ERR_UNSUPPORTED when its stream is capturing.  PN (c > 0): at most 1024
+ * black holes per level set (FSI_ERR_UNSUPPORTED latched otherwise).  Device waits are
+ * bounded by fsi_params.timeout_ns (FSI_ERR_TIMEOUT latched on expiry). */
 int fsi_hhs_interval(fsi_ctx *ctx, int N, double *pos, double *vel, const double *mass,
                      const unsigned char *is_bh, double tau, void *stream);
 

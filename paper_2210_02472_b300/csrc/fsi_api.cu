@@ -100,7 +100,7 @@ struct fsi_ctx {
     Buf rel, sub, ordws, ordperm, ordlist, farstats;
     // HHS recursion of mid-size sets in one cooperative launch (hhs_grid.cu): scratch by
     // particle id, list stack, barrier words; CTAs per launch (-1: not yet queried)
-    Buf grec[2], garec, gvrec, gacc, gaux, gst, glists, gbar, gprof;
+    Buf grec[2], garec, gvrec, gacc, gaux, gst, glists, gbar, gprof, gbhl, gpnpart;
     int grid_nctas[2] = {-1, -1};
     bool stats_on_device = false;   // the last interval was captured: its level statistics
                                     // are read from dstats by fsi_level_stats
@@ -799,9 +799,9 @@ int hhs_small_cap(const fsi_ctx* c) {
 }
 
 // Largest fast set whose HHS recursion runs in one cooperative launch over the GPU; 0 when
-// that form is off (hhs_grid_max = -1, PN on, or no co-resident grid on this device).
+// that form is off (hhs_grid_max = -1, or no co-resident grid of 2 CTAs on this device).
 int hhs_grid_cap(fsi_ctx* c) {
-    if (c->p.hhs_grid_max < 0 || c->p.c > 0.0) return 0;
+    if (c->p.hhs_grid_max < 0) return 0;
     const int prec = c->p.precision;
     if (c->grid_nctas[prec] < 0) c->grid_nctas[prec] = grid_ctas(prec, c->sm_count);
     if (c->grid_nctas[prec] < 2) return 0;
@@ -826,6 +826,10 @@ int run_hhs_grid(fsi_ctx* c, int N, double* pos, double* vel, const double* mass
     const long long cap = (long long)n * std::max(2, c->p.max_level - level + 2);
     if (cap > (1LL << 30)) return fail(FSI_ERR_ARG, "HHS list stack of %lld entries", cap);
     CK(ensure(c->glists, (size_t)cap * 4));
+    CK(ensure(c->gbhl, (size_t)cap * 4));
+    // PN: one chunk sum per (black hole, kGridPnChunk sources) and direction
+    const long long pncap = c->p.c > 0.0 ? 6LL * kMaxBHList * ((n + kGridPnChunk - 1) / kGridPnChunk) : 0;
+    if (pncap) CK(ensure(c->gpnpart, (size_t)pncap * 8));
     CK(ensure(c->gbar, 64));
     CU(cudaMemsetAsync(c->gbar.p, 0, 64, s));
     GridArgs g{};
@@ -850,6 +854,9 @@ int run_hhs_grid(fsi_ctx* c, int N, double* pos, double* vel, const double* mass
     g.bar = P<unsigned long long>(c->gbar);
     g.timeout_ns = budget(c);
     g.latch_maxlevel = latch_maxlevel ? 1 : 0;
+    g.bhl = P<int>(c->gbhl);
+    g.pnpart = pncap ? P<double>(c->gpnpart) : nullptr;
+    g.pnpart_cap = pncap;
     if (c->profiling) {
         if (!c->gprof.p) {
             CK(ensure(c->gprof, 16 * sizeof(unsigned long long)));
@@ -1021,7 +1028,8 @@ int fsi_destroy(fsi_ctx* c) {
                    &c->rel, &c->sub, &c->ordws, &c->ordperm, &c->ordlist, &c->farstats,
                    &c->eout, &c->snapx, &c->snapv, &c->subwhere, &c->subkey, &c->subppos, &c->stpart,
                    &c->xrel, &c->xsub, &c->pnids, &c->grec[0], &c->grec[1], &c->garec,
-                   &c->gvrec, &c->gacc, &c->gaux, &c->gst, &c->glists, &c->gbar, &c->gprof};
+                   &c->gvrec, &c->gacc, &c->gaux, &c->gst, &c->glists, &c->gbar, &c->gprof, &c->gbhl,
+                   &c->gpnpart};
     for (Buf* b : bufs)
         if (b->p) cudaFree(b->p);
     for (auto& r : c->prof) { cudaEventDestroy(r.a); cudaEventDestroy(r.b); }

@@ -230,6 +230,9 @@ struct GridArgs {
     long long timeout_ns;           // budget of every barrier wait
     int latch_maxlevel;             // also latch FSI_ERR_MAXLEVEL in err on a depth-cap hit
     unsigned long long* prof;       // optional phase profile (16 words), or nullptr
+    int* bhl;                       // black-hole sublists of the frames' S and F (list_cap)
+    double* pnpart;                 // PN partial sums of black-hole receivers
+    long long pnpart_cap;           // doubles in pnpart
 };
 
 // ---------------------------------------------------------------------------------
@@ -341,6 +344,7 @@ cudaError_t launch_kepler_pairs(int n_pairs, const int* ppos, int n, double* x, 
 cudaError_t launch_drift_singles(int n, double* x, const double* v, const int* key, int N, double w,
                                  cudaStream_t s);
 constexpr int kMaxBHList = 1024;   // black holes per set handled by the PN kernels
+constexpr int kGridPnChunk = 256;  // cooperative HHS launch: sources per black-hole PN item
 constexpr int kPnPartCtas = 64;    // CTAs per black hole in the PN reduction
 cudaError_t launch_bh_list(int n, const unsigned char* bhc, int* bh_list, int* n_bh, int* err,
                            cudaStream_t s);

@@ -24,8 +24,8 @@
 // A receiver's sources are split over G lanes (a power of two up to 32, the largest that
 // still gives every receiver a group within the CTAs of the phase).  The two directions of
 // an inter-level kick run in one phase on disjoint CTA ranges.  Data written by other CTAs
-// in earlier phases is read with L1-bypassing loads.  PN1.0 pairs are not evaluated here
-// (the caller walks PN runs from the host).
+// in earlier phases is read with L1-bypassing loads.  PN1.0 kicks (pairs with a black
+// hole) take two phases of their own, from black-hole sublists kept per frame.
 #include <algorithm>
 
 #include "hhs_small.cuh"
@@ -44,6 +44,7 @@ using GVec = typename std::conditional<P == FSI_MIXED, float4, D4>::type;   // (
 
 struct GFrame {
     int offP, nP, offS, nS, offF, nF;
+    int offB, nBS, nBF;             // black holes of S, then of F, at bhl[offB ...] (PN on)
     double tau;
     int level, stage;
 };
@@ -51,13 +52,14 @@ struct GFrame {
 // Per-CTA control state (the same in every CTA).
 struct GCtl {
     GFrame fr[kGridDepth];
-    long long list_top;
+    long long list_top, bh_top;
     long long t_last;               // CTA 0, with a.prof: end of the previous phase
     int top, ok;
 };
 
 // Phase kinds of the optional profile (a.prof: [kind] ns, [8 + kind] phases, from CTA 0).
-enum GPhase { kPhSteps = 0, kPhSplit, kPhCross, kPhFsi, kPhSmall, kPhCrit, kPhInit };
+enum GPhase { kPhSteps = 0, kPhSplit, kPhCross, kPhFsi, kPhSmall, kPhCrit, kPhInit, kPhPn };
+
 
 // ---------------------------------------------------------------------------------
 // Loads of data other CTAs wrote (L2, not L1) and record packing.
@@ -545,26 +547,32 @@ __device__ void g_grad_steps(const GridArgs& a, const int* Lst, int n) {
 
 // Stable split of list L into S = {st >= tau} at out[0, nS) and F at out[nS, n), with
 // the level-step rule (level 0 records its steps as the level-0 steps, deeper levels take
-// the min with them); returns nS.  Every CTA runs it and writes the same lists (no grid
-// barrier is needed before a CTA reads them: the lists it reads are the ones it wrote);
-// CTA 0 alone records the level-0 steps and the statistics.  With force_slow every
-// particle stays in S, which is then L itself and nothing is written.
-__device__ int g_split(const GridArgs& a, const int* Lst, int n, double tau, int level,
-                       bool force_slow, bool room, int* out) {
-    __shared__ int wS[kGridThreads / 32];
-    __shared__ int s_base, s_total, s_anyfast;
+// the min with them); with PN on, also the black holes of S, then of F, in list order at
+// bh[0, nBS + nBF).  Every CTA runs it and writes the same lists (no grid barrier is
+// needed before a CTA reads them: the lists it reads are the ones it wrote); CTA 0 alone
+// records the level-0 steps and the statistics.  With force_slow every particle stays in
+// S, which is then L itself and not written (its black-hole list still is).
+struct GSplit {
+    int nS, nBS, nBF;
+};
+
+__device__ GSplit g_split(const GridArgs& a, const int* Lst, int n, double tau, int level,
+                          bool force_slow, bool room, int* out, int* bh) {
+    __shared__ int wS[kGridThreads / 32], wBS[kGridThreads / 32], wBF[kGridThreads / 32];
+    __shared__ int s_base, s_bs, s_bf, s_total, s_tbs, s_tbf, s_anyfast;
     const int t = threadIdx.x, lane = t & 31, wid = t >> 5;
     const bool cta0 = blockIdx.x == 0;
+    const bool pn = a.s.c > 0.0 && a.s.is_bh;
     auto step_of = [&](int i) {
         const double st = __ldcg(a.st + i);
         return level == 0 ? st : fmin(st, __ldcg(a.s.step0 + i));
     };
-    if (t == 0) { s_total = 0; s_anyfast = 0; }
+    if (t == 0) { s_total = 0; s_tbs = 0; s_tbf = 0; s_anyfast = 0; }
     __syncthreads();
-    // pass 1: count S (and record the level-0 steps)
+    // pass 1: count S and the black holes of S and F (and record the level-0 steps)
     for (int k0 = 0; k0 < n; k0 += kGridThreads) {
         const int k = k0 + t;
-        bool slow = false;
+        bool slow = false, bhk = false;
         if (k < n) {
             const int i = __ldcg(Lst + k);
             const double st = step_of(i);
@@ -572,46 +580,186 @@ __device__ int g_split(const GridArgs& a, const int* Lst, int n, double tau, int
             const bool fast = st < tau;
             if (fast && force_slow) s_anyfast = 1;
             slow = force_slow || !fast;
+            bhk = pn && a.s.is_bh[i];
         }
         const unsigned b = __ballot_sync(0xffffffffu, slow);
-        if (lane == 0 && b) atomicAdd(&s_total, __popc(b));
+        const unsigned bs = __ballot_sync(0xffffffffu, slow && bhk);
+        const unsigned bf = __ballot_sync(0xffffffffu, k < n && !slow && bhk);
+        if (lane == 0) {
+            if (b) atomicAdd(&s_total, __popc(b));
+            if (bs) atomicAdd(&s_tbs, __popc(bs));
+            if (bf) atomicAdd(&s_tbf, __popc(bf));
+        }
     }
     __syncthreads();
-    const int nS = s_total;
-    if (!force_slow) {
-        if (t == 0) s_base = 0;
+    GSplit r;
+    r.nS = s_total;
+    r.nBS = s_tbs;
+    r.nBF = s_tbf;
+    if (!force_slow || r.nBS + r.nBF > 0) {
+        if (t == 0) { s_base = 0; s_bs = 0; s_bf = 0; }
         __syncthreads();
-        // pass 2: write S to out[0, nS) and F to out[nS, n) in list order
+        // pass 2: S to out[0, nS) and F to out[nS, n) in list order (not when force_slow),
+        // the black holes of S to bh[0, nBS) and of F to bh[nBS, nBS + nBF)
         for (int k0 = 0; k0 < n; k0 += kGridThreads) {
             const int k = k0 + t;
             const bool valid = k < n;
             const int i = valid ? __ldcg(Lst + k) : 0;
-            const bool slow = valid && !(step_of(i) < tau);
+            const bool slow = valid && (force_slow || !(step_of(i) < tau));
+            const bool bhk = valid && pn && a.s.is_bh[i];
             const unsigned b = __ballot_sync(0xffffffffu, slow);
-            if (lane == 0) wS[wid] = __popc(b);
+            const unsigned bs = __ballot_sync(0xffffffffu, slow && bhk);
+            const unsigned bf = __ballot_sync(0xffffffffu, valid && !slow && bhk);
+            if (lane == 0) { wS[wid] = __popc(b); wBS[wid] = __popc(bs); wBF[wid] = __popc(bf); }
             __syncthreads();
-            int before = s_base;
-            for (int w = 0; w < wid; ++w) before += wS[w];
-            const int rs = before + __popc(b & ((1u << lane) - 1u));
-            if (valid) {
+            int before = s_base, bbs = s_bs, bbf = s_bf;
+            for (int w = 0; w < wid; ++w) { before += wS[w]; bbs += wBS[w]; bbf += wBF[w]; }
+            const unsigned lm = (1u << lane) - 1u;
+            const int rs = before + __popc(b & lm);
+            if (valid && !force_slow) {
                 if (slow) out[rs] = i;
-                else out[nS + (k - rs)] = i;           // k - rs: fast entries before k
+                else out[r.nS + (k - rs)] = i;          // k - rs: fast entries before k
+            }
+            if (bhk) {
+                if (slow) bh[bbs + __popc(bs & lm)] = i;
+                else bh[r.nBS + bbf + __popc(bf & lm)] = i;
             }
             __syncthreads();
             if (t == 0)
-                for (int w = 0; w < kGridThreads / 32; ++w) s_base += wS[w];
+                for (int w = 0; w < kGridThreads / 32; ++w) { s_base += wS[w]; s_bs += wBS[w]; s_bf += wBF[w]; }
             __syncthreads();
         }
     }
     if (cta0 && t == 0) {
-        if (a.s.level_counts) atomicAdd(a.s.level_counts + level, (unsigned long long)nS);
+        if (a.s.level_counts) atomicAdd(a.s.level_counts + level, (unsigned long long)r.nS);
         if (force_slow && s_anyfast) {
             atomicExch(a.s.maxlevel_hit, 1);
             if (!room) set_error(a.s.err, FSI_ERR_MAXLEVEL);
         }
     }
     __syncthreads();
-    return nS;
+    return r;
+}
+
+// ---------------------------------------------------------------------------------
+// PN1.0 kicks (Sect. 3.9): pairs with a black hole, accelerations from the velocities at
+// the start of the kick.  Phase 1 (g_pn_acc) evaluates, per direction (receivers A,
+// sources B, their black-hole sublists bA, bB): a receiver that is not a black hole sums
+// over bB (one receiver per lane, into aux); a black-hole receiver (k-th of bA) sums over
+// all of B in chunks of kGridPnChunk sources, one warp per (k, chunk) item across the
+// grid, each chunk's sum into pnpart.  Phase 2 (g_pn_kick) adds a black hole's chunk sums
+// in chunk order and kicks every receiver: v += w pn.  Fixed orders throughout.
+struct GPnDir {
+    const int* A;
+    int nA;
+    const int* B;
+    int nB;
+    const int* bA;
+    int nbA;
+    const int* bB;
+    int nbB;
+};
+
+__device__ __forceinline__ void g_pn_pair(const GridArgs& a, int i, const double (&xi)[3],
+                                          const double (&vi)[3], double mi, int j, double ic2,
+                                          double (&p)[3]) {
+    const long long N = a.s.N;
+    pn_pair(xi[0], xi[1], xi[2], vi[0], vi[1], vi[2], mi, __ldcg(a.s.pos + j),
+            __ldcg(a.s.pos + N + j), __ldcg(a.s.pos + 2 * N + j), __ldcg(a.s.vel + j),
+            __ldcg(a.s.vel + N + j), __ldcg(a.s.vel + 2 * N + j), a.s.mass[j], ic2, p[0], p[1],
+            p[2], a.s.err);
+}
+
+__device__ void g_pn_acc(const GridArgs& a, const GPnDir* d, int ndir) {
+    const long long N = a.s.N;
+    const double ic2 = 1.0 / (a.s.c * a.s.c);
+    const int lane = threadIdx.x & 31;
+    const int gw = blockIdx.x * (kGridThreads / 32) + (threadIdx.x >> 5);
+    const int nw = gridDim.x * (kGridThreads / 32);
+    long long part0 = 0;
+    for (int q = 0; q < ndir; ++q) {
+        // black-hole receivers: one warp per (black hole, chunk of sources)
+        const int nch = (d[q].nB + kGridPnChunk - 1) / kGridPnChunk;
+        const long long items = (long long)d[q].nbA * nch;
+        if (part0 + 3 * items > a.pnpart_cap) {
+            if (gw == 0 && lane == 0) set_error(a.s.err, FSI_ERR_UNSUPPORTED);
+            return;
+        }
+        for (long long it = gw; it < items; it += nw) {
+            const int k = (int)(it / nch), ch = (int)(it - (long long)k * nch);
+            const int i = __ldcg(d[q].bA + k);
+            double xi[3], vi[3], p[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xi[c] = __ldcg(a.s.pos + c * N + i);
+                vi[c] = __ldcg(a.s.vel + c * N + i);
+            }
+            const double mi = a.s.mass[i];
+            const int q1 = min(d[q].nB, (ch + 1) * kGridPnChunk);
+            for (int u = ch * kGridPnChunk + lane; u < q1; u += 32) {
+                const int j = __ldcg(d[q].B + u);
+                if (j != i) g_pn_pair(a, i, xi, vi, mi, j, ic2, p);
+            }
+            for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) p[c] += __shfl_xor_sync(0xffffffffu, p[c], o);
+            if (lane == 0)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) a.pnpart[part0 + 3 * it + c] = p[c];
+        }
+        part0 += 3 * items;
+        // the other receivers: one per lane, over the black holes of B
+        for (int u = blockIdx.x * kGridThreads + threadIdx.x; u < d[q].nA; u += gridDim.x * kGridThreads) {
+            const int i = __ldcg(d[q].A + u);
+            if (a.s.is_bh[i]) continue;
+            double xi[3], vi[3], p[3] = {0.0, 0.0, 0.0};
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                xi[c] = __ldcg(a.s.pos + c * N + i);
+                vi[c] = __ldcg(a.s.vel + c * N + i);
+            }
+            const double mi = a.s.mass[i];
+            for (int b = 0; b < d[q].nbB; ++b) g_pn_pair(a, i, xi, vi, mi, __ldcg(d[q].bB + b), ic2, p);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) a.aux[c * N + i] = p[c];
+        }
+    }
+}
+
+template <int P>
+__device__ void g_pn_kick(const GridArgs& a, const GPnDir* d, int ndir, double w) {
+    const long long N = a.s.N;
+    long long part0 = 0;
+    for (int q = 0; q < ndir; ++q) {
+        const int nch = (d[q].nB + kGridPnChunk - 1) / kGridPnChunk;
+        const long long items = (long long)d[q].nbA * nch;
+        if (part0 + 3 * items > a.pnpart_cap) return;
+        for (int u = blockIdx.x * kGridThreads + threadIdx.x; u < d[q].nA; u += gridDim.x * kGridThreads) {
+            const int i = __ldcg(d[q].A + u);
+            double p[3];
+            if (a.s.is_bh[i]) {
+                // the k-th black hole of A: its chunk sums, in chunk order
+                int k = 0;
+                while (k < d[q].nbA && __ldcg(d[q].bA + k) != i) ++k;
+                if (k == d[q].nbA) continue;
+                p[0] = p[1] = p[2] = 0.0;
+                for (int ch = 0; ch < nch; ++ch)
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) p[c] += __ldcg(a.pnpart + part0 + 3 * ((long long)k * nch + ch) + c);
+            } else {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) p[c] = __ldcg(a.aux + c * N + i);
+            }
+            double v[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                v[c] = fma(w, p[c], __ldcg(a.s.vel + c * N + i));
+                a.s.vel[c * N + i] = v[c];
+            }
+            g_put_vec<P>(a.vrec, i, v[0], v[1], v[2], a.s.mass[i]);
+        }
+        part0 += 3 * items;
+    }
 }
 
 // ---------------------------------------------------------------------------------
@@ -635,19 +783,51 @@ __device__ bool g_cross(const GridArgs& a, unsigned char* smem, GCtl& C, unsigne
     return true;
 }
 
-// FSI(S, h) (Sect. 2.1, Eq. fsi-cycle): kick h/6 + drift h/2, a (stored), gradient kick
-// 2h/3 with a + (h^2/24) G + drift h/2, kick h/6.  Records: rec0 -> rec1 -> rec0.
-// w_open != 0: the inter-level kick of S and F with that weight, which comes right before
-// the cycle, shares its first pass; w_close != 0: the one right after the cycle shares its
-// last pass.  S sums its F sources apart from its S sources and F receives from S in the
-// same phase; the kicks are applied in the order of the unfused sequence.
+// PN1.0 kick of weight w (Sect. 3.9) of the frame's S within itself, or between S and F
+// (cross); nothing when no black hole is involved.
+template <int P>
+__device__ bool g_pn(const GridArgs& a, GCtl& C, unsigned long long& target, const GFrame& f,
+                     bool cross, double w) {
+    const int* Ls = a.lists + f.offS;
+    const int* Lf = a.lists + f.offF;
+    const int* bS = a.bhl + f.offB;
+    const int* bF = bS + f.nBS;
+    if (f.nBS + (cross ? f.nBF : 0) == 0) return true;
+    GPnDir d[2];
+    int nd = 1;
+    if (cross) {
+        d[0] = GPnDir{Ls, f.nS, Lf, f.nF, bS, f.nBS, bF, f.nBF};
+        d[1] = GPnDir{Lf, f.nF, Ls, f.nS, bF, f.nBF, bS, f.nBS};
+        nd = 2;
+    } else {
+        d[0] = GPnDir{Ls, f.nS, Ls, f.nS, bS, f.nBS, bS, f.nBS};
+    }
+    g_pn_acc(a, d, nd);
+    GSYNC(kPhPn);
+    g_pn_kick<P>(a, d, nd, w);
+    GSYNC(kPhPn);
+    return true;
+}
+
+// FSI(S, h) (Sect. 2.1, Eq. fsi-cycle) of the frame's S: kick h/6 + drift h/2, a (stored),
+// gradient kick 2h/3 with a + (h^2/24) G + drift h/2, kick h/6, between PN1.0 half-kicks
+// h/2 when PN is on (Sect. 3.9).  Records: rec0 -> rec1 -> rec0.  w_open != 0: the
+// inter-level kick of S and F with that weight, which comes right before the cycle, shares
+// its first pass; w_close != 0: the one right after the cycle shares its last pass (PN
+// off only: the PN half-kicks sit between them).  S sums its F sources apart from its S
+// sources and F receives from S in the same phase; the kicks are applied in the order of
+// the unfused sequence.
 template <int P>
 __device__ bool g_fsi(const GridArgs& a, unsigned char* smem, GCtl& C, unsigned long long& target,
-                      const int* Ls, int nS, const int* Lf, int nF, double h, double w_open,
-                      double w_close) {
+                      const GFrame& f, double h, double w_open, double w_close) {
+    const int* Ls = a.lists + f.offS;
+    const int* Lf = a.lists + f.offF;
+    const int nS = f.nS, nF = f.nF;
+    const bool pn = a.s.c > 0.0;
     const GDir d{Ls, nS, Ls, nS}, none{nullptr, 0, nullptr, 0};
     const GDir dSF{Ls, nS, Ls, nS, Lf, nF}, dF{Lf, nF, Ls, nS};
     const bool open = w_open != 0.0 && nF > 0, close = w_close != 0.0 && nF > 0;
+    if (pn && !g_pn<P>(a, C, target, f, false, 0.5 * h)) return false;
     {
         const GEpi e{0, nullptr, h / 6.0, 0.0, 0.5 * h, a.rec[0], a.rec[1], w_open, 1};
         const GEpi ef{0, nullptr, w_open, 0.0, 0.0, a.rec[0], nullptr};
@@ -672,6 +852,7 @@ __device__ bool g_fsi(const GridArgs& a, unsigned char* smem, GCtl& C, unsigned 
         else g_pass<P, 0, true>(a, smem, d, none, e, e);
         GSYNC(close ? kPhCross : kPhFsi);
     }
+    if (pn && !g_pn<P>(a, C, target, f, false, 0.5 * h)) return false;
     return true;
 }
 
@@ -693,14 +874,18 @@ __device__ bool g_assign(const GridArgs& a, unsigned char* smem, GCtl& C, unsign
         g_grad_steps(a, Lst, f.nP);
         GSYNC(kPhCrit);
     }
-    const long long lt = C.list_top;
-    const bool room = lt + f.nP <= a.list_cap;
+    const long long lt = C.list_top, bt = C.bh_top;
+    const bool room = lt + f.nP <= a.list_cap && bt + f.nP <= a.list_cap;
     const bool stop = f.level >= a.s.max_level || !room;
-    const int nS = g_split(a, Lst, f.nP, f.tau, f.level, stop, room, a.lists + lt);
+    const GSplit r = g_split(a, Lst, f.nP, f.tau, f.level, stop, room, a.lists + lt,
+                             room ? a.bhl + bt : a.bhl);
     f.offS = stop ? f.offP : (int)lt;
-    f.nS = nS;
-    f.offF = f.offS + nS;
-    f.nF = f.nP - nS;
+    f.nS = r.nS;
+    f.offF = f.offS + r.nS;
+    f.nF = f.nP - r.nS;
+    f.offB = (int)bt;
+    f.nBS = room ? r.nBS : 0;
+    f.nBF = room ? r.nBF : 0;
     return true;
 }
 
@@ -723,6 +908,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
         C.fr[0] = f;
         C.top = 0;
         C.list_top = s.n;
+        C.bh_top = 0;
         C.t_last = global_ns();
     }
     if (!grid_sync(a, target, C, kPhInit)) return;
@@ -732,11 +918,19 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
             if (top < 0) return true;
             GFrame f = C.fr[top];
             const double tau = f.tau;
+            const bool pn = s.c > 0.0;
             if (f.stage == 0) {
                 if (!g_assign<P>(a, smem, C, target, f)) return false;
-                // U_SF(tau/6) then FSI(S, tau/2): the kick shares the cycle's first pass
-                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, a.lists + f.offS, f.nS, a.lists + f.offF,
-                                          f.nF, 0.5 * tau, tau / 6.0, 0.0)) return false;
+                const bool cross = f.nS > 0 && f.nF > 0;
+                // [PN U_SF(tau/2)] U_SF(tau/6) FSI(S, tau/2): without PN the kick shares the
+                // cycle's first pass
+                if (cross && pn) {
+                    if (!g_pn<P>(a, C, target, f, true, 0.5 * tau)) return false;
+                    if (!g_cross<P>(a, smem, C, target, a.lists + f.offS, f.nS, a.lists + f.offF, f.nF,
+                                    tau / 6.0, false, 0.0)) return false;
+                }
+                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, f, 0.5 * tau, pn ? 0.0 : tau / 6.0, 0.0))
+                    return false;
                 f.stage = 1;
             } else if (f.stage == 1) {
                 if (f.nS > 0 && f.nF > 0 &&
@@ -744,9 +938,16 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
                                 2.0 * tau / 3.0, true, tau * tau / 24.0)) return false;
                 f.stage = 2;
             } else {
-                // FSI(S, tau/2) then U_SF(tau/6): the kick shares the cycle's last pass
-                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, a.lists + f.offS, f.nS, a.lists + f.offF,
-                                          f.nF, 0.5 * tau, 0.0, tau / 6.0)) return false;
+                // FSI(S, tau/2) U_SF(tau/6) [PN U_SF(tau/2)]: without PN the kick shares the
+                // cycle's last pass
+                const bool cross = f.nS > 0 && f.nF > 0;
+                if (f.nS > 0 && !g_fsi<P>(a, smem, C, target, f, 0.5 * tau, 0.0, pn ? 0.0 : tau / 6.0))
+                    return false;
+                if (cross && pn) {
+                    if (!g_cross<P>(a, smem, C, target, a.lists + f.offS, f.nS, a.lists + f.offF, f.nF,
+                                    tau / 6.0, false, 0.0)) return false;
+                    if (!g_pn<P>(a, C, target, f, true, 0.5 * tau)) return false;
+                }
                 f.stage = 3;
             }
             __syncthreads();
@@ -755,6 +956,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
                 if (t == 0) {
                     C.top = top - 1;
                     C.list_top = f.offS;
+                    C.bh_top = f.offB;
                 }
                 __syncthreads();
                 continue;
@@ -763,6 +965,7 @@ __global__ void __launch_bounds__(kGridThreads, 1) hhs_grid_kernel(const GridArg
             if (t == 0) {
                 C.fr[top] = f;
                 C.list_top = (long long)f.offS + f.nS + f.nF;
+                C.bh_top = (long long)f.offB + f.nBS + f.nBF;
             }
             __syncthreads();
             if (f.nF <= 0) continue;

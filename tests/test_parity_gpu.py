@@ -718,6 +718,43 @@ def test_hhs_interval_grid_few_ctas(F, prec, ctas):
     assert np.abs(v - rv).max() <= tol * 100
 
 
+@pytest.mark.parametrize("prec", PRECS)
+def test_hhs_interval_with_pn_grid_many_bh(F, prec):
+    """PN HHS in one cooperative launch with 40 black holes among 3000 particles (c = 50):
+    black-hole receivers whose sources span several 256-source chunks, black holes in both
+    S and F of the top levels, and a graph capture of the PN interval replayed bit for bit;
+    against the oracle."""
+    c = inputs.plummer(3000, 41, imf="kroupa", n_bh=40)
+    tau, cl = 1.0 / 32, 50.0
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, c=cl, is_bh=c.is_bh)
+    m, bh = dev(c.mass), dev(c.is_bh, torch.uint8)
+    with F.Context(prec, c=cl) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        assert F.fsi_hhs_interval(ctx, p, v, m, tau, is_bh=bh) == F.FSI_OK
+        lv = F.fsi_level_stats(ctx)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        p2, v2 = dev(c.pos), dev(c.vel)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            F.fsi_hhs_interval(ctx, p2, v2, m, tau, is_bh=bh)
+        p2.copy_(dev(c.pos))
+        v2.copy_(dev(c.vel))
+        g.replay()
+        torch.cuda.synchronize()
+        assert torch.equal(p, p2) and torch.equal(v, v2)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        p, v = host(p), host(v)
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    scale = max(1.0, np.abs(rv).max())
+    if prec == "fp64":
+        assert np.abs(p - rp).max() <= 1e-11
+        assert np.abs(v - rv).max() <= 1e-9 * scale
+    else:
+        assert np.abs(p - rp).max() <= 1e-5
+        assert np.abs(v - rv).max() <= 1e-3 * scale
+
+
 def test_hhs_grid_barrier_timeout(F):
     """A grid barrier wait of the cooperative HHS launch that runs out (timeout_ns = 1 ns, so
     a CTA that arrives early gives up after its first clock check) latches FSI_ERR_TIMEOUT,
@@ -839,14 +876,17 @@ def test_hhs_interval_restart(F, case):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-@pytest.mark.parametrize("small", [0, -1])
-def test_hhs_interval_with_pn(F, prec, small):
+@pytest.mark.parametrize("small,grid", [(0, -1), (-1, -1), (0, 0), (-1, 0), (64, 0)])
+def test_hhs_interval_with_pn(F, prec, small, grid):
     """HHS with the PN1.0 pair term (4 black holes, c = 30): S-S half-kicks around every
-    FSI(S, .) step and S-F kicks with the opening and closing U_SF."""
+    FSI(S, .) step and S-F kicks with the opening and closing U_SF; the levels walked from
+    the host (grid = -1) or the whole interval in one cooperative launch (0: black-hole
+    sublists per frame, the black-hole receivers' sums in chunks over the grid), with or
+    without the one-CTA recursion (small)."""
     c = inputs.plummer(500, 26, imf="kroupa", n_bh=4)
     tau, cl = 1.0 / 16, 30.0
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, c=cl, is_bh=c.is_bh)
-    with F.Context(prec, c=cl, hhs_small_max=small) as ctx:
+    with F.Context(prec, c=cl, hhs_small_max=small, hhs_grid_max=grid) as ctx:
         p, v = dev(c.pos), dev(c.vel)
         code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau, is_bh=dev(c.is_bh, torch.uint8))
         lv = F.fsi_level_stats(ctx)
