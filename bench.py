@@ -710,7 +710,7 @@ def run_hhs(args):
         F.fsi_profile(ctx, False)
         F.fsi_profile_read(ctx)
         kinds = ["time_steps", "split", "inter_level_kick", "fsi_pass", "one_cta_recursion",
-                 "gradient_criteria", "set_up"]
+                 "gradient_criteria", "set_up", "pn_kick"]
         grid_profile = {k: {"ms_per_interval": ns[q] / 1e6 / args.intervals,
                             "phases_per_interval": ph[q] / args.intervals}
                         for q, k in enumerate(kinds) if ph[q]}

@@ -458,12 +458,14 @@ int fsi_profile(fsi_ctx *ctx, int enable);
 int fsi_profile_read(fsi_ctx *ctx, long long *launches, double *ms);
 
 /* Phase profile of the HHS recursions run in one cooperative launch (recorded while
- * fsi_profile is on): per phase kind (0 time steps, 1 split, 2 inter-level kick, 3 FSI
- * pass of the slow set, 4 one-CTA recursion of a small fast set, 5 gradient time-step
- * criteria, 6 set-up), the wall-clock nanoseconds from the end of the previous phase to
- * the end of this one as seen by CTA 0 (the work and the grid barrier after it), and the
- * number of phases.  ns, phases: host long long[8].  reset != 0 clears after reading.
- * Synchronises `stream`. */
+ * fsi_profile is on): per phase kind (0 time steps, 1 split (empty: every CTA splits on
+ * its own without a barrier, and that time counts toward the next phase), 2 inter-level
+ * kick (incl. the FSI passes that share one), 3 FSI pass of the slow set, 4 one-CTA
+ * recursion of a small fast set, 5 gradient time-step criteria, 6 set-up, 7 PN1.0 kick
+ * phases), the wall-clock nanoseconds from the end of the previous phase to the end of
+ * this one as seen by CTA 0 (the work and the grid barrier after it), and the number of
+ * phases.  ns, phases: host long long[8].  reset != 0 clears after reading.  Synchronises
+ * `stream`. */
 int fsi_grid_stats(fsi_ctx *ctx, long long *ns, long long *phases, int reset, void *stream);
 
 /* Pair-sum work issued by this context: ordered (receiver, source) pairs of the

@@ -58,8 +58,9 @@ struct GCtl {
 };
 
 // Phase kinds of the optional profile (a.prof: [kind] ns, [8 + kind] phases, from CTA 0).
+// The split has no barrier of its own (every CTA splits on its own), so kind 1 stays empty
+// and the split's time counts toward the phase after it.
 enum GPhase { kPhSteps = 0, kPhSplit, kPhCross, kPhFsi, kPhSmall, kPhCrit, kPhInit, kPhPn };
-
 
 // ---------------------------------------------------------------------------------
 // Loads of data other CTAs wrote (L2, not L1) and record packing.
@@ -211,7 +212,7 @@ __device__ __forceinline__ GLayout g_layout(const GDir& d0, const GDir& d1) {
     return L;
 }
 
-// What the leader lane of receiver i does with its pass sum s:
+// What the epilogue of receiver i does with its pass sum s:
 //   store:  acc[:, i] = s and the acceleration record of i (for a gradient pass);
 //   out:    out[:, i] = s;
 //   w != 0: kick v_i += w s (acceleration pass) or w (acc[:, i] + cg s) (gradient pass),
@@ -287,10 +288,11 @@ __device__ __forceinline__ void g_epilogue(const GridArgs& a, const GEpi& e, int
 }
 
 // One pair pass (KIND 0: acceleration, 1: gradient with the acceleration records) over
-// up to two directions (epilogue e0 for direction 0, e1 for direction 1); SELF: the receivers are among the sources (the pair i-i is
-// skipped).  An acceleration pass may give a direction a second source range, whose sum
-// is kept apart (parked in the receiver's shared-memory slot) and kicked with its own
-// weight.
+// up to two directions (epilogue e0 for direction 0, e1 for direction 1); SELF: the
+// receivers are among the sources (the pair i-i is skipped).  An acceleration pass may
+// give a direction a second source range, whose sum is kept apart and kicked with its own
+// weight.  The leader lane of each receiver parks its sums in shared memory; the
+// epilogues then run with one receiver per lane.
 template <int P, int KIND, bool SELF>
 __device__ void g_pass(const GridArgs& a, unsigned char* smem, const GDir& d0, const GDir& d1,
                        const GEpi& e0, const GEpi& e1) {

@@ -363,8 +363,8 @@ def fsi_level_stats(ctx: Context, max_levels: int = 64):
 
 def fsi_grid_stats(ctx: Context, reset: bool = False, stream=None):
     """Phase profile of the cooperative-launch HHS recursions (while fsi_profile is on):
-    (ns, phases), each a list of 8 per phase kind (time steps, split, inter-level kick,
-    FSI pass, one-CTA recursion, gradient criteria, set-up, unused)."""
+    (ns, phases), each a list of 8 per phase kind (time steps, split (empty), inter-level
+    kick, FSI pass, one-CTA recursion, gradient criteria, set-up, PN kick)."""
     ns = (C.c_longlong * 8)()
     ph = (C.c_longlong * 8)()
     _check(_lib.fsi_grid_stats(ctx.handle, ns, ph, int(bool(reset)), _stream(stream)), "fsi_grid_stats")
