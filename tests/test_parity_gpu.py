@@ -755,6 +755,31 @@ def test_hhs_interval_with_pn_grid_many_bh(F, prec):
         assert np.abs(v - rv).max() <= 1e-3 * scale
 
 
+@pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n", [1, 2, 3, 17])
+@pytest.mark.parametrize("grid", [0, -1])
+def test_hhs_interval_tiny_sets(F, prec, n, grid):
+    """HHS intervals of 1, 2, 3 and 17 particles: level sets of one particle (no pair: an
+    infinite step, so it stays slow), the fast set handed down level after level, in the
+    cooperative launch (grid = 0) and the host walk with the one-CTA recursion (-1); against
+    the oracle."""
+    c = inputs.plummer(max(n, 2), 50 + n, imf="kroupa")
+    pos, vel, mass = c.pos[:, :n].copy(), c.vel[:, :n].copy(), c.mass[:n].copy()
+    tau = 1.0 / 8
+    rp, rv, counts, _ = oracle.hhs_interval(pos, vel, mass, tau)
+    with F.Context(prec, hhs_grid_max=grid) as ctx:
+        p, v = dev(pos), dev(vel)
+        assert F.fsi_hhs_interval(ctx, p, v, dev(mass), tau) == F.FSI_OK
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    tol = 1e-11 if prec == "fp64" else 1e-7
+    assert np.abs(p - rp).max() <= tol
+    assert np.abs(v - rv).max() <= tol * 100
+
+
 def test_hhs_grid_barrier_timeout(F):
     """A grid barrier wait of the cooperative HHS launch that runs out (timeout_ns = 1 ns, so
     a CTA that arrives early gives up after its first clock check) latches FSI_ERR_TIMEOUT,
