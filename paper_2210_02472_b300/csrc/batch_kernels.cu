@@ -811,12 +811,10 @@ template <int I, int MINB>
 static cudaError_t launch_batch_sym_i(int ctas, const BatchArgs& a, const BatchSymItem* sitems,
                                       int sitems_per_phase, const int* nsum, double* accum,
                                       cudaStream_t s) {
-    static bool attr = false;
-    if (!attr) {
-        cudaError_t e = cudaFuncSetAttribute(batch_sym_kernel<I, MINB>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, BS<I>::Smem);
+    static std::atomic<unsigned long long> attr_dev{0};
+    {
+        const cudaError_t e = smem_attr_once(batch_sym_kernel<I, MINB>, (int)BS<I>::Smem, attr_dev);
         if (e != cudaSuccess) return e;
-        attr = true;
     }
     { batch_sym_kernel<I, MINB><<<ctas, kBatchThreads, BS<I>::Smem, s>>>(a, sitems, sitems_per_phase, nsum, accum); note_launch(); }
     return cudaGetLastError();

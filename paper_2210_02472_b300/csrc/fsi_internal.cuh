@@ -2,6 +2,8 @@
 #pragma once
 #include <cuda_runtime.h>
 #include <stdint.h>
+
+#include <atomic>
 #include "../../include/fsi.h"
 
 namespace fsi {
@@ -78,6 +80,23 @@ struct PairArgs {
     long long timeout_ns;
     Epi epi;
 };
+
+// ---------------------------------------------------------------------------------
+// Raises the dynamic shared-memory limit of kernel fn to `bytes` once per device: the
+// attribute belongs to the function on the current device, so a process with contexts on
+// several GPUs sets it on each (bit d of `devices` records device d < 64; others set it on
+// every call).
+template <class F>
+inline cudaError_t smem_attr_once(F* fn, int bytes, std::atomic<unsigned long long>& devices) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    const unsigned long long bit = dev < 64 ? (1ull << dev) : 0ull;
+    if (bit && (devices.load(std::memory_order_relaxed) & bit)) return cudaSuccess;
+    e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    if (e == cudaSuccess && bit) devices.fetch_or(bit, std::memory_order_relaxed);
+    return e;
+}
 
 // ---------------------------------------------------------------------------------
 // Error word helpers.

@@ -1013,14 +1013,10 @@ static size_t grid_smem_bytes(int precision) {
 }
 
 static cudaError_t grid_attr(int precision) {
-    static bool done[2] = {false, false};
-    if (done[precision]) return cudaSuccess;
+    static std::atomic<unsigned long long> attr_dev[2];
     const int smem = (int)grid_smem_bytes(precision);
-    const cudaError_t e = precision == FSI_MIXED
-        ? cudaFuncSetAttribute(hhs_grid_kernel<FSI_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem)
-        : cudaFuncSetAttribute(hhs_grid_kernel<FSI_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-    if (e == cudaSuccess) done[precision] = true;
-    return e;
+    return precision == FSI_MIXED ? smem_attr_once(hhs_grid_kernel<FSI_MIXED>, smem, attr_dev[1])
+                                  : smem_attr_once(hhs_grid_kernel<FSI_FP64>, smem, attr_dev[0]);
 }
 
 int grid_ctas(int precision, int sm_count) {

@@ -18,13 +18,12 @@ int small_max() { return kSmallMax; }
 
 cudaError_t launch_hhs_small(int precision, const SmallArgs& a, cudaStream_t s) {
     const size_t smem = small_smem_bytes(precision);
-    static bool attr[2] = {false, false};
-    if (!attr[precision]) {
-        cudaError_t e = precision == FSI_MIXED
-            ? cudaFuncSetAttribute(hhs_small_kernel<FSI_MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)
-            : cudaFuncSetAttribute(hhs_small_kernel<FSI_FP64>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    static std::atomic<unsigned long long> attr_dev[2];
+    {
+        const cudaError_t e = precision == FSI_MIXED
+            ? smem_attr_once(hhs_small_kernel<FSI_MIXED>, (int)smem, attr_dev[1])
+            : smem_attr_once(hhs_small_kernel<FSI_FP64>, (int)smem, attr_dev[0]);
         if (e != cudaSuccess) return e;
-        attr[precision] = true;
     }
     if (precision == FSI_MIXED) { hhs_small_kernel<FSI_MIXED><<<1, kSmallMax, smem, s>>>(a); note_launch(); }
     else { hhs_small_kernel<FSI_FP64><<<1, kSmallMax, smem, s>>>(a); note_launch(); }

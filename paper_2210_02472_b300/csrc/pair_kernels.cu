@@ -1939,12 +1939,10 @@ static cudaError_t launch_cross_x2_t(const CrossArgs& a, cudaStream_t s) {
     constexpr int I = 4;
     constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + 16) + (kTileJ / 32) * 16;
     constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + (I / 2) * 3 * kThreads * 16;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(cross_mixed_x2_kernel<KIND, I, 2>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    static std::atomic<unsigned long long> attr_dev{0};
+    {
+        const cudaError_t e = smem_attr_once(cross_mixed_x2_kernel<KIND, I, 2>, SMEM, attr_dev);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const long long nb = (a.n_i + kThreads * I - 1) / (kThreads * I);
     const long long grid = nb * a.nchunk;
@@ -2078,12 +2076,10 @@ template <int KIND>
 static cudaError_t launch_cross_f64_t(const CrossArgs& a, cudaStream_t s) {
     constexpr int I = 2;
     constexpr int SMEM = SymCfg<FSI_FP64, KIND>::SMEM;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(cross_f64_kernel<KIND, I>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    static std::atomic<unsigned long long> attr_dev{0};
+    {
+        const cudaError_t e = smem_attr_once(cross_f64_kernel<KIND, I>, SMEM, attr_dev);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const long long nb = (a.n_i + kThreads * I - 1) / (kThreads * I);
     const long long grid = nb * a.nchunk;
@@ -2123,12 +2119,10 @@ static cudaError_t launch_sym_x2(SymArgs a, cudaStream_t s) {
     constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + 16) + (kTileJ / 32) * 16;
     constexpr int JPART = (NT / 32) * kTileJ * 3 * (int)sizeof(float);
     constexpr int SMEM = kStages * SB + JPART + I * 3 * NT * (int)sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sym_mixed_x2_kernel<KIND, I, MINB, NT>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    static std::atomic<unsigned long long> attr_dev{0};
+    {
+        const cudaError_t e = smem_attr_once(sym_mixed_x2_kernel<KIND, I, MINB, NT>, SMEM, attr_dev);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     // work items per i-block: its own tiles, then chunks of the tiles above it
     constexpr int BT = NT * I / kTileJ;
@@ -2147,12 +2141,10 @@ static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
     constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + (FAR ? 16 : 0)) +
                        (FAR ? (kTileJ / 32) * 16 : 0);
     constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + I * 3 * kThreads * (int)sizeof(double);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sym_mixed_v2_kernel<KIND, I, FAR>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    static std::atomic<unsigned long long> attr_dev{0};
+    {
+        const cudaError_t e = smem_attr_once(sym_mixed_v2_kernel<KIND, I, FAR>, SMEM, attr_dev);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
     const long long grid = (long long)nb * (1 + a.nchunk);
@@ -2164,12 +2156,10 @@ static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
 template <int P, int KIND, int I>
 static cudaError_t launch_sym_one(const SymArgs& a, cudaStream_t s) {
     constexpr int SMEM = SymCfg<P, KIND>::SMEM;
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(sym_pair_kernel<P, KIND, I>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    static std::atomic<unsigned long long> attr_dev{0};
+    {
+        const cudaError_t e = smem_attr_once(sym_pair_kernel<P, KIND, I>, SMEM, attr_dev);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
     const long long grid = (long long)nb * (1 + a.nchunk);
@@ -2264,12 +2254,10 @@ cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, c
 template <int P, int KIND, int I, int FF>
 static cudaError_t launch_one(const PairArgs& a, int split, cudaStream_t s) {
     constexpr int SMEM = kStages * stage_bytes(Cfg<P, KIND>::ACCREC);
-    static bool attr_set = false;
-    if (!attr_set) {
-        cudaError_t e = cudaFuncSetAttribute(pair_kernel<P, KIND, I, FF>,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM);
+    static std::atomic<unsigned long long> attr_dev{0};
+    {
+        const cudaError_t e = smem_attr_once(pair_kernel<P, KIND, I, FF>, SMEM, attr_dev);
         if (e != cudaSuccess) return e;
-        attr_set = true;
     }
     dim3 grid((a.n_i + kThreads * I - 1) / (kThreads * I), split);
     { pair_kernel<P, KIND, I, FF><<<grid, kThreads, SMEM, s>>>(a); note_launch(); }

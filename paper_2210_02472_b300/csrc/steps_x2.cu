@@ -689,13 +689,12 @@ cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double ep
                              long long timeout_ns, int sm_count, cudaStream_t s, const void* rel,
                              const void* sub, float far_k2) {
     if (n <= 0) return cudaSuccess;
-    static bool attr[2] = {false, false};
+    static std::atomic<unsigned long long> attr_dev[2];
     const bool soft = eps2 > 0.0;
-    if (!attr[soft]) {
-        cudaError_t e = soft ? cudaFuncSetAttribute(steps_sym_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSsSmem)
-                             : cudaFuncSetAttribute(steps_sym_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kSsSmem);
+    {
+        const cudaError_t e = soft ? smem_attr_once(steps_sym_kernel<true>, (int)kSsSmem, attr_dev[1])
+                                   : smem_attr_once(steps_sym_kernel<false>, (int)kSsSmem, attr_dev[0]);
         if (e != cudaSuccess) return e;
-        attr[soft] = true;
     }
     StepSymArgs a{};
     a.n = n;
@@ -762,12 +761,11 @@ cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps
             return cudaGetLastError();
         }
     }
-    static bool attr[2] = {false, false};
-    if (!attr[soft]) {
-        cudaError_t e = soft ? cudaFuncSetAttribute(steps_x2_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem)
-                             : cudaFuncSetAttribute(steps_x2_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, kStSmem);
+    static std::atomic<unsigned long long> attr_dev[2];
+    {
+        const cudaError_t e = soft ? smem_attr_once(steps_x2_kernel<true>, (int)kStSmem, attr_dev[1])
+                                   : smem_attr_once(steps_x2_kernel<false>, (int)kStSmem, attr_dev[0]);
         if (e != cudaSuccess) return e;
-        attr[soft] = true;
     }
     const int nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
     const int want = (2 * sm_count + nb - 1) / nb;
