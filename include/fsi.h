@@ -145,7 +145,8 @@ int fsi_destroy(fsi_ctx *ctx);
 int fsi_set_params(fsi_ctx *ctx, const fsi_params *p);
 
 /* Grow the workspace so that calls on sets of up to n particles (out of N total)
- * allocate nothing.  Synchronous. */
+ * allocate nothing; with n == N also an HHS interval of the N particles (so that an
+ * interval captured in a CUDA graph right after it allocates nothing).  Synchronous. */
 int fsi_reserve(fsi_ctx *ctx, int N, int n);
 
 /* Thread-local text of the last host-side error (never NULL). */
@@ -306,7 +307,8 @@ int fsi_energy(fsi_ctx *ctx, int N, const double *pos, const double *vel,
  * one cooperative launch over the GPU, and a fast set of at most hhs_small_max in one CTA.
  * When N <= hhs_grid_max the whole interval is that one launch: the call then
  * does not synchronise with the host and may be captured in a CUDA graph (stream
- * capture); a replay repeats the interval bit for bit on the captured buffers.  Under
+ * capture; reserve the workspace first with fsi_reserve(ctx, N, N) or one uncaptured
+ * interval); a replay repeats the interval bit for bit on the captured buffers.  Under
  * capture the level statistics stay on the device (fsi_level_stats reads those of the
  * last replay) and a depth-cap hit is latched as FSI_ERR_MAXLEVEL in the error word
  * (fsi_sync_status) instead of being returned.  An interval that needs the host walk

@@ -810,9 +810,8 @@ int hhs_grid_cap(fsi_ctx* c) {
 
 // HHS(ids, tau) at `level` in one cooperative launch (hhs_grid.cu); at level 0 the split
 // records the level-0 steps.  Statistics go to dstats.
-int run_hhs_grid(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
-                 const unsigned char* is_bh, const int* ids, int n, double tau, int level,
-                 bool latch_maxlevel, cudaStream_t s) {
+// Workspace of a cooperative HHS launch with a root set of n particles at `level`.
+int reserve_hhs_grid(fsi_ctx* c, int N, int n, int level) {
     const int prec = c->p.precision;
     const size_t vb = prec == FSI_MIXED ? 16 : 32;
     CK(ensure(c->grec[0], (size_t)N * 32));
@@ -831,6 +830,16 @@ int run_hhs_grid(fsi_ctx* c, int N, double* pos, double* vel, const double* mass
     const long long pncap = c->p.c > 0.0 ? 6LL * kMaxBHList * ((n + kGridPnChunk - 1) / kGridPnChunk) : 0;
     if (pncap) CK(ensure(c->gpnpart, (size_t)pncap * 8));
     CK(ensure(c->gbar, 64));
+    return FSI_OK;
+}
+
+int run_hhs_grid(fsi_ctx* c, int N, double* pos, double* vel, const double* mass,
+                 const unsigned char* is_bh, const int* ids, int n, double tau, int level,
+                 bool latch_maxlevel, cudaStream_t s) {
+    const int prec = c->p.precision;
+    CK(reserve_hhs_grid(c, N, n, level));
+    const long long cap = (long long)n * std::max(2, c->p.max_level - level + 2);
+    const long long pncap = c->p.c > 0.0 ? 6LL * kMaxBHList * ((n + kGridPnChunk - 1) / kGridPnChunk) : 0;
     CU(cudaMemsetAsync(c->gbar.p, 0, 64, s));
     GridArgs g{};
     SmallArgs& sa = g.s;
@@ -1082,6 +1091,17 @@ int fsi_reserve(fsi_ctx* c, int N, int n) {
     if (!c->farstats.p) {
         CK(ensure(c->farstats, 2 * sizeof(unsigned long long)));
         CU(cudaMemset(c->farstats.p, 0, 2 * sizeof(unsigned long long)));
+    }
+    if (n == N) {
+        // an HHS interval of all N: its level-0 lists and statistics, and the cooperative
+        // launch's workspace for the largest set it may take (the interval itself when
+        // N <= hhs_grid_max, else a fast set of at most hhs_grid_max one level down)
+        CK(ensure(c->iota, (size_t)N * 4));
+        CK(ensure(c->step0, (size_t)N * 8));
+        CK(ensure(c->counts, 16));
+        CK(ensure(c->dstats, 68 * sizeof(unsigned long long)));
+        const int gcap = hhs_grid_cap(c);
+        if (gcap > 0) CK(reserve_hhs_grid(c, N, std::min(N, gcap), 0));
     }
     CU(cudaDeviceSynchronize());
     return FSI_OK;

@@ -656,8 +656,9 @@ def test_hhs_interval_graph_capture(F, prec, n, cap):
     """An HHS interval of N <= hhs_grid_max (4096 by default, raised to 6000 here) is one
     cooperative launch with no host synchronisation: captured in a CUDA graph and
     replayed, it reproduces the uncaptured interval bit for bit (positions, velocities,
-    level statistics), twice in a row; the uncaptured interval matches the oracle.  An
-    interval that needs the host walk refuses capture with FSI_ERR_UNSUPPORTED."""
+    level statistics), twice in a row, also in a fresh context whose workspace comes from
+    fsi_reserve; the uncaptured interval matches the oracle.  An interval that needs the
+    host walk refuses capture with FSI_ERR_UNSUPPORTED."""
     c = inputs.plummer(n, 31, imf="kroupa")
     tau = 1.0 / 32
     rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
@@ -679,6 +680,19 @@ def test_hhs_interval_graph_capture(F, prec, n, cap):
             assert F.fsi_level_stats(ctx) == lv1
         assert F.fsi_sync_status(ctx) == F.FSI_OK
         p, v = host(p1), host(v1)
+    with F.Context(prec, hhs_grid_max=cap) as ctx:
+        # a fresh context whose workspace comes from fsi_reserve: captured at once
+        F.fsi_reserve(ctx, n, n)
+        p4, v4 = dev(c.pos), dev(c.vel)
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g):
+            F.fsi_hhs_interval(ctx, p4, v4, m, tau)
+        p4.copy_(dev(c.pos))
+        v4.copy_(dev(c.vel))
+        g.replay()
+        torch.cuda.synchronize()
+        assert np.array_equal(host(p4), p) and np.array_equal(host(v4), v)
+        assert F.fsi_level_stats(ctx) == lv1
     used = np.nonzero(counts)[0].max() + 1
     assert lv1[:used] == list(counts[:used])
     tol = 1e-11 if prec == "fp64" else 1e-7
