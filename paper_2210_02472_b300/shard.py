@@ -1,4 +1,5 @@
-"""i-sharded pair passes and FSI cycles over several ranks (one process per GPU).
+"""i-sharded pair passes, FSI cycles and HHS intervals over several ranks (one process per
+GPU).
 
 Direct summation shards along the receivers: every rank holds the replicated positions
 and masses of the whole set (and, for the gradient pass, the accelerations of the whole
@@ -13,6 +14,9 @@ against all sources.  The data exchanged between ranks is what the next pass nee
   * for active sets too small to give every rank receivers (fewer than `min_rows` per
     rank), the sources are split instead and the partial acceleration and gradient sums
     are all-reduced (48 B per active particle).
+
+An HHS interval shards every level's active list the same way: the inter-level kicks split
+the rows of S and F, and FSI(S) is a sharded FSI cycle of S.
 
 The paper runs its direct-summation loops on several GPUs with MPI (Sect. 4.1); here the
 collectives are torch.distributed's (NCCL between GPUs: every operand lands in the
@@ -57,6 +61,13 @@ class LibfsiCompute:
 
     def kick_drift(self, pos, vel, acc, idx, c_kick, c_drift):
         self.F.fsi_kick_drift(self.ctx, pos, vel, acc, c_kick, c_drift, idx=idx)
+
+    def timesteps(self, pos, vel, mass, P, eps2):
+        """Time steps of the set P against itself with the context's criteria; eps2 must be
+        the context's (the time-step call takes it from there)."""
+        if float(self.ctx.params.eps2) != float(eps2):
+            raise ValueError("timesteps: eps2 differs from the context's fsi_params.eps2")
+        return self.F.fsi_timesteps(self.ctx, pos, vel, mass, P)
 
     def status(self):
         return self.F.fsi_sync_status(self.ctx)
@@ -125,9 +136,10 @@ def _ids(n: int, idx: Optional[torch.Tensor], device) -> torch.Tensor:
 
 
 class ShardedFSI:
-    """The sharded hot path: pair sums of one splitting term (fsi_accel_grad semantics)
-    and FSI cycles of a set (fsi_step semantics), with every rank ending with the same
-    results.  `compute` does all arithmetic; `ex` moves data between ranks."""
+    """The sharded hot path: pair sums of one splitting term (fsi_accel_grad semantics),
+    FSI cycles of a set (fsi_step semantics) and HHS intervals (fsi_hhs_interval
+    semantics), with every rank ending with the same results.  `compute` does all
+    arithmetic; `ex` moves data between ranks."""
 
     def __init__(self, compute, ex: Optional[Exchange] = None, min_rows: int = 1024):
         self.c = compute
@@ -227,3 +239,101 @@ class ShardedFSI:
                 pn_kick()
                 self.c.kick_drift(pos, vel, a, Pr, h / 6.0, 0.5 * h)
         self._sync_cols(vel, P, lo, hi, n)
+
+    # -------------------------------------------------------------- HHS intervals
+    def hhs_interval(self, pos, vel, mass, tau: float, eps2: float = 0.0, c: float = 0.0,
+                     is_bh=None, max_level: int = 40):
+        """One HHS interval of length tau over all N particles (Sect. 2.2, Eq.
+        hhsfsi-cycle), in place on the replicated pos / vel, with every level's active list
+        sharded over the ranks: per level visit the time steps of the level set (computed
+        in full on every rank by the shard compute: its time-step call takes a set against
+        itself), the split S = {eps >= tau}, F = {eps < tau} with the level-step rule (level 0
+        records its steps, deeper levels take the min with them; at max_level every
+        particle stays in S), then U_SF(tau/6) FSI(S, tau/2) HHS(F, tau/2) U~_SF(2 tau/3)
+        HHS(F, tau/2) FSI(S, tau/2) U_SF(tau/6), with PN1.0 S-F kicks of tau/2 around the
+        opening and closing U_SF when c > 0 (Sect. 3.9).  The inter-level kicks split S and
+        F into row slices, all-gather their accelerations (and, for U~_SF, the gradient
+        sums) and kick on every rank; FSI(S) is `step`.  Returns (level_counts,
+        maxlevel_hit); the compute's time-step criteria must use the same eps2."""
+        N = mass.numel()
+        self._hhs_step0 = torch.zeros(N, dtype=pos.dtype, device=pos.device)
+        counts = [0] * (max_level + 1)
+        hit = [False]
+        P = torch.arange(N, dtype=torch.int32, device=pos.device)
+        self._hhs(pos, vel, mass, P, float(tau), 0, float(eps2), float(c), is_bh,
+                  int(max_level), counts, hit)
+        while len(counts) > 1 and counts[-1] == 0:
+            counts.pop()
+        return counts, hit[0]
+
+    def _hhs(self, pos, vel, mass, P, tau, level, eps2, c, is_bh, max_level, counts, hit):
+        """HHS(P, tau) at `level` (see hhs_interval)."""
+        n = P.numel()
+        if n == 0:
+            return
+        st = self.c.timesteps(pos, vel, mass, P, eps2).to(pos.dtype)
+        Pl = P.long()
+        if level == 0:
+            self._hhs_step0[Pl] = st
+        else:
+            st = torch.minimum(st, self._hhs_step0[Pl])
+        fast = st < tau
+        if level >= max_level:
+            if bool(fast.any()):
+                hit[0] = True
+            fast = torch.zeros_like(fast)
+        S, F = P[~fast], P[fast]                     # stable: list order kept
+        counts[level] += S.numel()
+        cross = S.numel() > 0 and F.numel() > 0
+        pn = c > 0.0
+        if cross and pn:
+            self._pn_cross(pos, vel, mass, S, F, 0.5 * tau, c, is_bh)
+        if cross:
+            self._cross(pos, vel, mass, S, F, tau / 6.0, eps2)
+        if S.numel():
+            self.step(pos, vel, mass, 0.5 * tau, 1, idx=S, eps2=eps2, c=c, is_bh=is_bh)
+        if F.numel():
+            self._hhs(pos, vel, mass, F, 0.5 * tau, level + 1, eps2, c, is_bh, max_level, counts, hit)
+        if cross:
+            self._cross(pos, vel, mass, S, F, 2.0 * tau / 3.0, eps2, grad_eps=tau)
+        if F.numel():
+            self._hhs(pos, vel, mass, F, 0.5 * tau, level + 1, eps2, c, is_bh, max_level, counts, hit)
+        if S.numel():
+            self.step(pos, vel, mass, 0.5 * tau, 1, idx=S, eps2=eps2, c=c, is_bh=is_bh)
+        if cross:
+            self._cross(pos, vel, mass, S, F, tau / 6.0, eps2)
+            if pn:
+                self._pn_cross(pos, vel, mass, S, F, 0.5 * tau, c, is_bh)
+
+    def _cross(self, pos, vel, mass, S, F, w, eps2, grad_eps=None):
+        """Inter-level kick of S and F (Sect. 2.2): v_S += w acc(S <- F), v_F += w acc(F <- S);
+        with grad_eps, the accelerations a + (grad_eps^2 / 24) G of the same inter-level
+        term.  Rows of S and F are split over the ranks; the gathered sums are applied on
+        every rank."""
+        N = mass.numel()
+        nS, nF = S.numel(), F.numel()
+        pS = plan(nS, nF, self.ex, self.min_rows)
+        pF = plan(nF, nS, self.ex, self.min_rows)
+        aS = self._acc(pos, mass, S, F, eps2, pS)
+        aF = self._acc(pos, mass, F, S, eps2, pF)
+        if grad_eps is not None:
+            accg = torch.zeros((3, N), dtype=pos.dtype, device=pos.device)
+            accg[:, S.long()] = aS
+            accg[:, F.long()] = aF
+            cg = grad_eps * grad_eps / 24.0
+            aS = aS + cg * self._grad(pos, mass, accg, S, F, eps2, pS)
+            aF = aF + cg * self._grad(pos, mass, accg, F, S, eps2, pF)
+        self.c.kick_drift(pos, vel, aS, S, w, 0.0)
+        self.c.kick_drift(pos, vel, aF, F, w, 0.0)
+
+    def _pn_cross(self, pos, vel, mass, S, F, w, c, is_bh):
+        """PN1.0 kick of the S-F pairs (Sect. 3.9), both directions, from the velocities at
+        the start of the kick: rows split over the ranks, the sums gathered and applied on
+        every rank."""
+        nS, nF = S.numel(), F.numel()
+        lo, hi = slice_bounds(nS, self.ex.world, self.ex.rank)
+        pS = self.ex.all_gather_cols(self.c.pn_accel(pos, vel, mass, is_bh, c, S[lo:hi], F), nS)
+        lo, hi = slice_bounds(nF, self.ex.world, self.ex.rank)
+        pF = self.ex.all_gather_cols(self.c.pn_accel(pos, vel, mass, is_bh, c, F[lo:hi], S), nF)
+        self.c.kick_drift(pos, vel, pS, S, w, 0.0)
+        self.c.kick_drift(pos, vel, pF, F, w, 0.0)

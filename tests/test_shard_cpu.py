@@ -40,6 +40,10 @@ class OracleCompute:
         pos.copy_(torch.as_tensor(p))
         vel.copy_(torch.as_tensor(v))
 
+    def timesteps(self, pos, vel, mass, P, eps2):
+        return torch.as_tensor(oracle.timesteps(pos.numpy(), vel.numpy(), mass.numpy(), P.numpy(),
+                                                eps2=eps2))
+
 
 def _free_port():
     s = socket.socket()
@@ -113,8 +117,24 @@ def _steps_subset_pn(sh):
     return pos.numpy(), vel.numpy()
 
 
+def _hhs(sh):
+    c = inputs.plummer(300, 58, imf="kroupa")
+    pos, vel = torch.as_tensor(c.pos.copy()), torch.as_tensor(c.vel.copy())
+    counts, hit = sh.hhs_interval(pos, vel, torch.as_tensor(c.mass), 1.0 / 16)
+    return pos.numpy(), vel.numpy(), counts, hit
+
+
+def _hhs_pn_softened_capped(sh):
+    c = inputs.plummer(240, 59, imf="kroupa", n_bh=4)
+    pos, vel = torch.as_tensor(c.pos.copy()), torch.as_tensor(c.vel.copy())
+    counts, hit = sh.hhs_interval(pos, vel, torch.as_tensor(c.mass), 1.0 / 16, eps2=1e-5, c=30.0,
+                                  is_bh=torch.as_tensor(c.is_bh.astype(np.uint8)), max_level=3)
+    return pos.numpy(), vel.numpy(), counts, hit
+
+
 CASES = {"same": _same_set, "disjoint": _disjoint_softened, "small": _small_set_split_sources,
-         "steps": _steps, "steps_pn": _steps_subset_pn}
+         "steps": _steps, "steps_pn": _steps_subset_pn, "hhs": _hhs,
+         "hhs_pn": _hhs_pn_softened_capped}
 
 
 # ---------------------------------------------------------------- tests
@@ -181,3 +201,35 @@ def test_sharded_fsi_steps_subset_with_pn():
         assert np.abs(v - rv).max() <= 1e-12 * np.abs(rv).max()
         others = np.setdiff1d(np.arange(260), P)
         assert np.array_equal(p[:, others], c.pos[:, others])
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_hhs_interval_matches_oracle(world):
+    """One HHS interval (Sect. 2.2) with every level's active list sharded over 2 or 3
+    ranks (row slices of the inter-level kicks and the FSI(S) cycles, gathered sums)
+    against the oracle's interval on one rank: the same level histogram, the state to
+    rounding, and the same state on every rank."""
+    c = inputs.plummer(300, 58, imf="kroupa")
+    rp, rv, counts, code = oracle.hhs_interval(c.pos, c.vel, c.mass, 1.0 / 16)
+    outs = _run("hhs", world)
+    used = np.nonzero(counts)[0].max() + 1
+    for p, v, lv, hit in outs:
+        assert lv[:used] == list(counts[:used]) and not hit
+        assert np.abs(p - rp).max() <= 1e-13
+        assert np.abs(v - rv).max() <= 1e-11
+    assert np.array_equal(outs[0][0], outs[-1][0]) and np.array_equal(outs[0][1], outs[-1][1])
+
+
+def test_sharded_hhs_interval_pn_softened_depth_cap():
+    """The sharded interval with PN1.0 S-F and S-S kicks (4 black holes, c = 30),
+    softening and a depth cap of 3 levels, against the oracle's capped interval."""
+    c = inputs.plummer(240, 59, imf="kroupa", n_bh=4)
+    rp, rv, counts, code = oracle.hhs_interval(c.pos, c.vel, c.mass, 1.0 / 16, eps2=1e-5, c=30.0,
+                                               is_bh=c.is_bh, max_level=3, allow_maxlevel=True)
+    outs = _run("hhs_pn", 2)
+    used = np.nonzero(counts)[0].max() + 1
+    for p, v, lv, hit in outs:
+        assert lv[:used] == list(counts[:used])
+        assert hit and code == oracle.ERR_MAXLEVEL
+        assert np.abs(p - rp).max() <= 1e-13
+        assert np.abs(v - rv).max() <= 1e-11 * max(1.0, np.abs(rv).max())

@@ -2,7 +2,8 @@
 
 Two gloo ranks share cuda:0 (independent contexts and kernels; no kernel waits on the other
 rank, the exchange goes through host memory), and one NCCL rank runs the same path through
-NCCL collectives; both against the oracle and the one-rank library calls.
+NCCL collectives; both against the oracle and the one-rank library calls: the pair sums of
+a set, FSI cycles with PN kicks, and an HHS interval with every level's list sharded.
 """
 import os
 import socket
@@ -48,6 +49,12 @@ def _rank(rank, world, port, backend, out):
                 torch.cuda.synchronize()
                 assert F.fsi_sync_status(ctx) == F.FSI_OK
                 res[prec + "_step"] = (pos.cpu().numpy(), vel.cpu().numpy())
+                c = inputs.plummer(1500, 63, imf="kroupa")
+                pos, vel = torch.as_tensor(c.pos).cuda(), torch.as_tensor(c.vel).cuda()
+                counts, hit = sh.hhs_interval(pos, vel, torch.as_tensor(c.mass).cuda(), 1.0 / 32)
+                torch.cuda.synchronize()
+                assert F.fsi_sync_status(ctx) == F.FSI_OK and not hit
+                res[prec + "_hhs"] = (pos.cpu().numpy(), vel.cpu().numpy(), np.array(counts))
         out[rank] = res
     finally:
         dist.destroy_process_group()
@@ -74,6 +81,9 @@ def _check(outs):
     d = inputs.plummer(900, 62, imf="kroupa", n_bh=3)
     rp, rv = oracle.fsi_step(d.pos, d.vel, d.mass, 1e-3, c=40.0, is_bh=d.is_bh, steps=3)
     na, ng = np.linalg.norm(ra, axis=0), np.linalg.norm(rg, axis=0)
+    e = inputs.plummer(1500, 63, imf="kroupa")
+    hp, hv, hc, _ = oracle.hhs_interval(e.pos, e.vel, e.mass, 1.0 / 32)
+    used = np.nonzero(hc)[0].max() + 1
     for res in outs:
         a, g = res["fp64_ag"]
         assert (np.abs(a - ra).max(axis=0) / na).max() <= 1e-12
@@ -85,6 +95,10 @@ def _check(outs):
         assert np.median(np.linalg.norm(g - rg, axis=0) / ng) <= 1e-5
         p, v = res["mixed_step"]
         assert np.abs(p - rp).max() <= 1e-9 and np.abs(v - rv).max() <= 1e-7
+        for prec, tol in (("fp64", 1e-11), ("mixed", 1e-7)):
+            p, v, lv = res[prec + "_hhs"]
+            assert list(lv[:used]) == list(hc[:used])
+            assert np.abs(p - hp).max() <= tol and np.abs(v - hv).max() <= 100 * tol
     for k in outs[0]:
         for x, y in zip(outs[0][k], outs[-1][k]):
             assert np.array_equal(x, y), k          # every rank ends with the same data
