@@ -290,6 +290,14 @@ int fsi_step_sub(fsi_ctx *ctx, int N, double *pos, double *vel, const double *ma
 int fsi_timesteps(fsi_ctx *ctx, int N, const double *pos, const double *vel,
                   const double *mass, const int *P, int n, double *step_out, void *stream);
 
+/* Time steps of the entries P[lo, hi) of the set against the whole set P (the criteria of
+ * fsi_timesteps; one receiver slice of an i-sharded time-step pass).  step_out: hi - lo.
+ * FSI_ERR_ARG for a bad range; FSI_ERR_UNSUPPORTED when eta_grad or eta_va > 0 (those
+ * criteria need the whole set's own accelerations). */
+int fsi_timesteps_sub(fsi_ctx *ctx, int N, const double *pos, const double *vel,
+                      const double *mass, const int *P, int n, int lo, int hi, double *step_out,
+                      void *stream);
+
 /* Kinetic and potential energy of the set P (Sect. 2.1 Hamiltonian), FP64:
  * out[0] = sum 1/2 m v^2, out[1] = -sum_{i<j} m_i m_j / (r^2 + eps2)^{1/2}.
  * out: 2 doubles, device. */

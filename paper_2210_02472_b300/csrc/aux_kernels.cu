@@ -626,13 +626,16 @@ constexpr int kAuxTile = 128;
 
 // Time steps (Sect. 3.4), FP64: thread per i, sources through shared memory, the
 // division-free pair update of step_pair (pair_math.cuh).
+// Receivers: entries [i_off, i_off + n_i) of the compact set (step[k] for entry i_off + k);
+// sources: all n entries.
 __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
                                  const double* __restrict__ mc, double eta_ff, double eta_fb,
-                                 double eta_jerk, double eps2, double* __restrict__ step, int* err) {
+                                 double eta_jerk, double eps2, double* __restrict__ step, int* err,
+                                 int i_off, int n_i) {
     __shared__ double sx[kAuxTile], sy[kAuxTile], sz[kAuxTile], su[kAuxTile], sv[kAuxTile],
         sw[kAuxTile], sm[kAuxTile];
-    const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ii = min(i, n - 1);
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ii = i_off + min(k, n_i - 1);
     const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
     const double ui = vc[ii], vi = vc[(size_t)n + ii], wi = vc[2 * (size_t)n + ii];
     const double mi = mc[ii];
@@ -661,17 +664,19 @@ __global__ void timesteps_kernel(int n, const double* __restrict__ xc, const dou
             step_pair<double>(acc, dx, dy, dz, su[t] - ui, sv[t] - vi, sw[t] - wi, d2, sm[t], mi + sm[t], y);
         }
     }
-    if (i >= n) return;
+    if (k >= n_i) return;
     if (coincident) set_error(err, FSI_ERR_COINCIDENT);
-    step[i] = step_finish<double>(acc, eta_ff, eta_fb, eta_jerk);
+    step[k] = step_finish<double>(acc, eta_ff, eta_fb, eta_jerk);
 }
 
 cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
                              double eta_ff, double eta_fb, double eta_jerk, double eps2,
-                             double* step, int* err, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
-    { timesteps_kernel<<<blocks_for(n, kAuxTile), kAuxTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb,
-                                                                  eta_jerk, eps2, step, err); note_launch(); }
+                             double* step, int* err, cudaStream_t s, int i_off, int n_i) {
+    if (n_i < 0) n_i = n;
+    if (n <= 0 || n_i <= 0) return cudaSuccess;
+    { timesteps_kernel<<<blocks_for(n_i, kAuxTile), kAuxTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb,
+                                                                    eta_jerk, eps2, step, err, i_off,
+                                                                    n_i); note_launch(); }
     return cudaGetLastError();
 }
 

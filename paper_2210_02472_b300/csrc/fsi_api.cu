@@ -716,9 +716,14 @@ int cross_pn_kick(fsi_ctx* c, int N, const double* pos, double* vel, const doubl
     return FSI_OK;
 }
 
+// Time steps of the set's entries [lo, hi) (hi < 0: all n) against the whole set, into
+// step[0, hi - lo).  A proper sub-range takes the one-sided kernels and needs the gradient
+// criteria off (the caller checks).
 int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
-                   const int* Pids, int n, double* step, cudaStream_t s) {
-    if (n <= 0) return FSI_OK;
+                   const int* Pids, int n, double* step, cudaStream_t s, int lo = 0, int hi = -1) {
+    if (hi < 0) hi = n;
+    if (n <= 0 || hi <= lo) return FSI_OK;
+    const bool whole = lo == 0 && hi == n;
     const double* xc = pos;
     const double* vc = vel;
     const double* mc = mass;
@@ -740,8 +745,8 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     if (mixed) {
         CK(ensure(c->rec[1], pad_tile(n) * 32));
         CK(ensure(c->accrec[1], pad_tile(n) * 32));
-        const bool sym = c->p.symmetric && n >= steps_sym_min_n();
-        CK(ensure(c->stpart, sym ? steps_sym_work_bytes(n) : steps_x2_part_bytes(n, c->sm_count)));
+        const bool sym = whole && c->p.symmetric && n >= steps_sym_min_n();
+        CK(ensure(c->stpart, sym ? steps_sym_work_bytes(n) : steps_x2_part_bytes(n, c->sm_count, hi - lo)));
         CU(launch_pack_vel(N, vel, mass, Pids, n, c->accrec[1].p, pos, c->rec[1].p, s));
         if (sym) {
             // HHS level lists in Morton order: far source sub-tiles take the 3-addition
@@ -761,11 +766,12 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
         } else
             CU(launch_steps_x2(n, c->rec[1].p, c->accrec[1].p, c->p.eps2, c->p.eta_ff, c->p.eta_fb,
                                c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c),
-                               c->sm_count, wide_limit(c), s));
+                               c->sm_count, wide_limit(c), s, lo, hi - lo));
     }
     else
         CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
-                            c->err_d, s));
+                            c->err_d, s, lo, hi - lo));
+    if (!whole) return crit ? fail(FSI_ERR_UNSUPPORTED, "time steps of a sub-range with the gradient criteria") : FSI_OK;
     if (c->p.eta_grad > 0.0 || c->p.eta_va > 0.0) {
         // gradient and velocity-per-acceleration criteria (Sect. 3.4): a and G of the set
         // from itself, G with the set's own accelerations, then the min into step
@@ -1452,6 +1458,18 @@ int fsi_timesteps(fsi_ctx* c, int N, const double* pos, const double* vel, const
     if (n == 0) return FSI_OK;
     if (!pos || !vel || !mass || !step_out) return fail(FSI_ERR_ARG, "NULL array");
     return timesteps_core(c, N, pos, vel, mass, Pids, n, step_out, S(stream));
+}
+
+int fsi_timesteps_sub(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,
+                      const int* Pids, int n, int lo, int hi, double* step_out, void* stream) {
+    CK(check_common(c, N));
+    if (n < 0 || (!Pids && n != N)) return fail(FSI_ERR_ARG, "bad set size n=%d N=%d", n, N);
+    if (lo < 0 || hi < lo || hi > n) return fail(FSI_ERR_ARG, "bad range [%d, %d) of %d", lo, hi, n);
+    if (c->p.eta_grad > 0.0 || c->p.eta_va > 0.0)
+        return fail(FSI_ERR_UNSUPPORTED, "time steps of a sub-range with the gradient criteria");
+    if (hi == lo) return FSI_OK;
+    if (!pos || !vel || !mass || !step_out) return fail(FSI_ERR_ARG, "NULL array");
+    return timesteps_core(c, N, pos, vel, mass, Pids, n, step_out, S(stream), lo, hi);
 }
 
 int fsi_energy(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,

@@ -390,9 +390,11 @@ cudaError_t launch_pn_pairs(int N, const double* pos, const double* vel, const d
 int energy_blocks(int n);
 cudaError_t launch_energy(int n, const double* xc, const double* vc, const double* mc,
                           double eps2, double* part, double* out, int* err, cudaStream_t s);
+// Time steps of entries [i_off, i_off + n_i) of the compact set (n_i < 0: all n) against
+// all n entries, into step[0, n_i).
 cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
                              double eta_ff, double eta_fb, double eta_jerk, double eps2,
-                             double* step, int* err, cudaStream_t s);
+                             double* step, int* err, cudaStream_t s, int i_off = 0, int n_i = -1);
 // rec_ws, vrec_ws: workspace of >= 32 n and 16 n bytes (mixed records, FP32 velocities)
 // step[k] = min(step[k], gradient and velocity-per-acceleration steps) from the set's
 // velocities vc, accelerations a and force-gradient sums G (all 3 x n).
@@ -404,7 +406,7 @@ cudaError_t launch_grad_steps(int n, const double* vc, const double* a, const do
 cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const int* idx, int n,
                             void* vrec, const double* pos, void* rec, cudaStream_t s);
 // Mixed time steps with packed FP32 pairs (steps_x2.cu); part: steps_x2_part_bytes bytes.
-size_t steps_x2_part_bytes(int n, int sm_count);
+size_t steps_x2_part_bytes(int n, int sm_count, int n_i = -1);   // n_i receivers (-1: n)
 // Symmetric mixed time steps (every unordered pair once) for sets of at least
 // steps_sym_min_n() particles; work: steps_sym_work_bytes(n) bytes (8-byte aligned).
 size_t steps_sym_work_bytes(int n);
@@ -417,9 +419,13 @@ cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double ep
                              long long timeout_ns, int sm_count, cudaStream_t s,
                              const void* rel = nullptr, const void* sub = nullptr,
                              float far_k2 = 0.f);
+// Mixed time steps (one-sided packed kernel, or its wide form) of records [i_off, i_off +
+// n_i) (n_i < 0: all n) against all n records, into step[0, n_i); part: split partials of
+// at least steps_x2_part_bytes(n, sm_count, n_i) bytes.
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                             double eta_fb, double eta_jerk, float* part, double* step, int* err,
-                            long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s);
+                            long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s,
+                            int i_off = 0, int n_i = -1);
 cudaError_t launch_partition(int n, const int* ids, double* step, double* step0, int level0,
                              double tau, int force_slow, int* S, int* F, int* counts, cudaStream_t s);
 cudaError_t launch_iota(int n, int* ids, cudaStream_t s);

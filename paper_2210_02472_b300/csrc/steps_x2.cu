@@ -105,13 +105,14 @@ __device__ __forceinline__ double step_from(float ff, float fb, float ax, float 
 }
 
 struct StepX2Args {
-    int n;
+    int n;                  // sources: records [0, n)
+    int i_off, n_i;         // receivers: records [i_off, i_off + n_i), outputs [0, n_i)
     const RecMix* rec;
     const float4* vrec;
     float eps2;
     double eta_ff, eta_fb, eta_jerk;
     int j_per_split;
-    float* part;            // split > 1: [split][kStPart][n]
+    float* part;            // split > 1: [split][kStPart][n_i]
     double* step;
     int* err;
     long long timeout_ns;
@@ -145,11 +146,12 @@ __global__ void __launch_bounds__(kStThreads, 2) steps_x2_kernel(const StepX2Arg
     // receivers: i0 + u * 256 + tid, u = 0..3; pair p holds u = 2p (low) and 2p + 1 (high)
     StepX2I pp[kStNP];
     StepX2Acc acc[kStNP];
-    // lanes past the end hold a copy of particle n - 1 and use its index for the self test
+    // lanes past the end hold a copy of the last receiver and use its index for the self
+    // test; receiver k is record i_off + k
     int me[kStI];
 #pragma unroll
     for (int u = 0; u < kStI; ++u) {
-        const int i = min(i0 + u * kStThreads + tid, a.n - 1);
+        const int i = a.i_off + min(i0 + u * kStThreads + tid, a.n_i - 1);
         me[u] = i;
         const RecMix r = a.rec[i];
         const float4 v = a.vrec[i];
@@ -176,7 +178,7 @@ __global__ void __launch_bounds__(kStThreads, 2) steps_x2_kernel(const StepX2Arg
         const unsigned char* base = smem + st * kStStage;
         const RecMix* rec = reinterpret_cast<const RecMix*>(base);
         const float4* vr = reinterpret_cast<const float4*>(base + kStTile * 32);
-        const bool chk = jt < i0 + kStThreads * kStI && jt + cnt > i0;
+        const bool chk = jt < a.i_off + i0 + kStThreads * kStI && jt + cnt > a.i_off + i0;
         if (!chk) {
             for (int jj = 0; jj < cnt; ++jj) {
                 const float4 h = rec[jj].hi, l = rec[jj].lo, v = vr[jj];
@@ -209,7 +211,7 @@ __global__ void __launch_bounds__(kStThreads, 2) steps_x2_kernel(const StepX2Arg
 #pragma unroll
     for (int u = 0; u < kStI; ++u) {
         const int i = i0 + u * kStThreads + tid;
-        if (i >= a.n) continue;
+        if (i >= a.n_i) continue;
         if (coincident) set_error(a.err, FSI_ERR_COINCIDENT);
         const StepX2Acc& s = acc[u >> 1];
         const bool hi = (u & 1) != 0;
@@ -218,7 +220,7 @@ __global__ void __launch_bounds__(kStThreads, 2) steps_x2_kernel(const StepX2Arg
                                   hi ? s.jy.y : s.jy.x, hi ? s.jz.y : s.jz.x};
         if (gridDim.y > 1) {
 #pragma unroll
-            for (int k = 0; k < kStPart; ++k) a.part[((size_t)blockIdx.y * kStPart + k) * a.n + i] = v[k];
+            for (int k = 0; k < kStPart; ++k) a.part[((size_t)blockIdx.y * kStPart + k) * a.n_i + i] = v[k];
         } else {
             if (!(isfinite(v[2]) && isfinite(v[3]) && isfinite(v[4]))) set_error(a.err, FSI_ERR_NONFINITE);
             a.step[i] = step_from(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], a.eta_ff, a.eta_fb, a.eta_jerk);
@@ -229,16 +231,16 @@ __global__ void __launch_bounds__(kStThreads, 2) steps_x2_kernel(const StepX2Arg
 // Combine the per-split partials: minima of the ratios, sums of a and j (fixed order).
 __global__ void steps_x2_finalize_kernel(const StepX2Args a, int split) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.n) return;
+    if (i >= a.n_i) return;
     float v[kStPart];
 #pragma unroll
-    for (int k = 0; k < kStPart; ++k) v[k] = a.part[(size_t)k * a.n + i];
+    for (int k = 0; k < kStPart; ++k) v[k] = a.part[(size_t)k * a.n_i + i];
     for (int s = 1; s < split; ++s) {
-        const float* q = a.part + (size_t)s * kStPart * a.n + i;
+        const float* q = a.part + (size_t)s * kStPart * a.n_i + i;
         v[0] = fminf(v[0], q[0]);
-        v[1] = fminf(v[1], q[(size_t)a.n]);
+        v[1] = fminf(v[1], q[(size_t)a.n_i]);
 #pragma unroll
-        for (int k = 2; k < kStPart; ++k) v[k] += q[(size_t)k * a.n];
+        for (int k = 2; k < kStPart; ++k) v[k] += q[(size_t)k * a.n_i];
     }
     if (!(isfinite(v[2]) && isfinite(v[3]) && isfinite(v[4]))) set_error(a.err, FSI_ERR_NONFINITE);
     a.step[i] = step_from(v[0], v[1], v[2], v[3], v[4], v[5], v[6], v[7], a.eta_ff, a.eta_fb, a.eta_jerk);
@@ -253,8 +255,8 @@ __global__ void __launch_bounds__(kStThreads) steps_wide_kernel(const StepX2Args
     const long long gt = (long long)blockIdx.x * kStThreads + threadIdx.x;
     const int slot = (int)(gt >> lg);
     const int g = (int)(gt & (G - 1));
-    const bool active = slot < a.n;
-    const int i = active ? slot : a.n - 1;
+    const bool active = slot < a.n_i;
+    const int i = a.i_off + (active ? slot : a.n_i - 1);
     float ff = INFINITY, fb = INFINITY, ax = 0.f, ay = 0.f, az = 0.f, jx = 0.f, jy = 0.f, jz = 0.f;
     bool coincident = false;
     if (active) {
@@ -306,7 +308,7 @@ __global__ void __launch_bounds__(kStThreads) steps_wide_kernel(const StepX2Args
     }
     if (!active || g != 0) return;
     if (!(isfinite(ax) && isfinite(ay) && isfinite(az))) set_error(a.err, FSI_ERR_NONFINITE);
-    a.step[i] = step_from(ff, fb, ax, ay, az, jx, jy, jz, a.eta_ff, a.eta_fb, a.eta_jerk);
+    a.step[slot] = step_from(ff, fb, ax, ay, az, jx, jy, jz, a.eta_ff, a.eta_fb, a.eta_jerk);
 }
 
 // =================================================================================
@@ -724,11 +726,16 @@ cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double ep
     return cudaGetLastError();
 }
 
-size_t steps_x2_part_bytes(int n, int sm_count) {
-    const int nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
+size_t steps_x2_part_bytes(int n, int sm_count, int n_i) {
+    if (n_i < 0) n_i = n;
+    if (n <= 0 || n_i <= 0) return 0;
+    const int nb = (n_i + kStThreads * kStI - 1) / (kStThreads * kStI);
     const int want = (2 * sm_count + nb - 1) / nb;
-    const int split = std::max(1, std::min(want, (n + kStTile - 1) / kStTile));
-    return split > 1 ? (size_t)split * kStPart * (size_t)n * sizeof(float) : 0;
+    int split = std::max(1, std::min(want, (n + kStTile - 1) / kStTile));
+    int jps = (n + split - 1) / split;
+    jps = (jps + kStTile - 1) / kStTile * kStTile;
+    split = (n + jps - 1) / jps;
+    return split > 1 ? (size_t)split * kStPart * (size_t)n_i * sizeof(float) : 0;
 }
 
 // rec, vrec: the set's mixed position records and FP32 velocity records (vx, vy, vz, m),
@@ -736,12 +743,14 @@ size_t steps_x2_part_bytes(int n, int sm_count) {
 // wide_ctas: a set whose tiled launch would run fewer CTAs takes steps_wide_kernel.
 cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps2, double eta_ff,
                             double eta_fb, double eta_jerk, float* part, double* step, int* err,
-                            long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s) {
-    if (n <= 0) return cudaSuccess;
+                            long long timeout_ns, int sm_count, int wide_ctas, cudaStream_t s,
+                            int i_off, int n_i) {
+    if (n_i < 0) n_i = n;
+    if (n <= 0 || n_i <= 0) return cudaSuccess;
     const bool soft = eps2 > 0.0;
     {
-        // tiled CTAs this set would get; below wide_ctas the wide form runs instead
-        const long long nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
+        // tiled CTAs these receivers would get; below wide_ctas the wide form runs instead
+        const long long nb = (n_i + kStThreads * kStI - 1) / (kStThreads * kStI);
         const long long want = (2LL * sm_count + nb - 1) / nb;
         const long long tiled = nb * std::max(1LL, std::min(want, (long long)(n + kStTile - 1) / kStTile));
         if (tiled < wide_ctas) {
@@ -749,13 +758,15 @@ cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps
             while (lg > 0 && (8 << lg) > n) --lg;
             StepX2Args a{};
             a.n = n;
+            a.i_off = i_off;
+            a.n_i = n_i;
             a.rec = reinterpret_cast<const RecMix*>(rec);
             a.vrec = reinterpret_cast<const float4*>(vrec);
             a.eps2 = (float)eps2;
             a.eta_ff = eta_ff; a.eta_fb = eta_fb; a.eta_jerk = eta_jerk;
             a.step = step;
             a.err = err;
-            const unsigned grid = (unsigned)((((long long)n << lg) + kStThreads - 1) / kStThreads);
+            const unsigned grid = (unsigned)((((long long)n_i << lg) + kStThreads - 1) / kStThreads);
             if (soft) { steps_wide_kernel<true><<<grid, kStThreads, 0, s>>>(a, lg); note_launch(); }
             else { steps_wide_kernel<false><<<grid, kStThreads, 0, s>>>(a, lg); note_launch(); }
             return cudaGetLastError();
@@ -767,7 +778,7 @@ cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps
                                    : smem_attr_once(steps_x2_kernel<false>, (int)kStSmem, attr_dev[0]);
         if (e != cudaSuccess) return e;
     }
-    const int nb = (n + kStThreads * kStI - 1) / (kStThreads * kStI);
+    const int nb = (n_i + kStThreads * kStI - 1) / (kStThreads * kStI);
     const int want = (2 * sm_count + nb - 1) / nb;
     int split = std::max(1, std::min(want, (n + kStTile - 1) / kStTile));
     int jps = (n + split - 1) / split;
@@ -775,6 +786,8 @@ cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps
     split = (n + jps - 1) / jps;
     StepX2Args a{};
     a.n = n;
+    a.i_off = i_off;
+    a.n_i = n_i;
     a.rec = reinterpret_cast<const RecMix*>(rec);
     a.vrec = reinterpret_cast<const float4*>(vrec);
     a.eps2 = (float)eps2;
@@ -787,7 +800,7 @@ cudaError_t launch_steps_x2(int n, const void* rec, const void* vrec, double eps
     dim3 grid(nb, split);
     if (soft) { steps_x2_kernel<true><<<grid, kStThreads, kStSmem, s>>>(a); note_launch(); }
     else { steps_x2_kernel<false><<<grid, kStThreads, kStSmem, s>>>(a); note_launch(); }
-    if (split > 1) { steps_x2_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(a, split); note_launch(); }
+    if (split > 1) { steps_x2_finalize_kernel<<<(n_i + 255) / 256, 256, 0, s>>>(a, split); note_launch(); }
     return cudaGetLastError();
 }
 

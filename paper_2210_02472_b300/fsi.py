@@ -42,7 +42,7 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_step_vjp", "fsi_step_vjp_rec", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall", "fsi_batch_stats",
             "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for", "fsi_grid_stats",
-            "fsi_batch_item_stats"]
+            "fsi_batch_item_stats", "fsi_timesteps_sub"]
 
 
 class fsi_params(C.Structure):
@@ -70,6 +70,7 @@ _lib.fsi_pn_accel.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp, _ip, _vp, 
 _lib.fsi_step.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _vp, _ip, _dp, _ip, _vp]
 _lib.fsi_kick_drift.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _dp, _dp, _vp]
 _lib.fsi_timesteps.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
+_lib.fsi_timesteps_sub.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _ip, _ip, _vp, _vp]
 _lib.fsi_energy.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _vp]
 _lib.fsi_hhs_interval.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp]
 _lib.fsi_level_stats.argtypes = [_vp, C.POINTER(C.c_longlong), _ip]
@@ -295,6 +296,20 @@ def fsi_timesteps(ctx: Context, pos, vel, mass, P=None, out=None, stream=None):
     _check(_lib.fsi_timesteps(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
                               _f64(mass, (N,), "mass"), pp, n, _f64(out, (n,), "out"),
                               _stream(stream)), "fsi_timesteps")
+    return out
+
+
+def fsi_timesteps_sub(ctx: Context, pos, vel, mass, P, lo: int, hi: int, out=None, stream=None):
+    """Time steps of the entries P[lo:hi] against the whole set P (one receiver slice)."""
+    N = mass.numel()
+    pp, n = _ids(P, N, "P")
+    lo, hi = int(lo), int(hi)
+    if out is None:
+        out = torch.empty((max(hi - lo, 0),), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_timesteps_sub(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(vel, (3, N), "vel"),
+                                  _f64(mass, (N,), "mass"), pp, n, lo, hi,
+                                  _f64(out, (max(hi - lo, 0),), "out"), _stream(stream)),
+           "fsi_timesteps_sub")
     return out
 
 

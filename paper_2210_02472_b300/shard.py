@@ -65,9 +65,20 @@ class LibfsiCompute:
     def timesteps(self, pos, vel, mass, P, eps2):
         """Time steps of the set P against itself with the context's criteria; eps2 must be
         the context's (the time-step call takes it from there)."""
+        self._check_eps2(eps2)
+        return self.F.fsi_timesteps(self.ctx, pos, vel, mass, P)
+
+    def timesteps_rows(self, pos, vel, mass, P, lo, hi, eps2):
+        """Time steps of P[lo:hi] against the whole set P, or None when the context's
+        gradient criteria are on (they need the whole set's accelerations)."""
+        self._check_eps2(eps2)
+        if self.ctx.params.eta_grad > 0.0 or self.ctx.params.eta_va > 0.0:
+            return None
+        return self.F.fsi_timesteps_sub(self.ctx, pos, vel, mass, P, lo, hi)
+
+    def _check_eps2(self, eps2):
         if float(self.ctx.params.eps2) != float(eps2):
             raise ValueError("timesteps: eps2 differs from the context's fsi_params.eps2")
-        return self.F.fsi_timesteps(self.ctx, pos, vel, mass, P)
 
     def status(self):
         return self.F.fsi_sync_status(self.ctx)
@@ -245,9 +256,10 @@ class ShardedFSI:
                      is_bh=None, max_level: int = 40):
         """One HHS interval of length tau over all N particles (Sect. 2.2, Eq.
         hhsfsi-cycle), in place on the replicated pos / vel, with every level's active list
-        sharded over the ranks: per level visit the time steps of the level set (computed
-        in full on every rank by the shard compute: its time-step call takes a set against
-        itself), the split S = {eps >= tau}, F = {eps < tau} with the level-step rule (level 0
+        sharded over the ranks: per level visit the time steps of the level set (each rank
+        those of its slice against the whole set, all-gathered; in full on every rank when
+        the compute has no slice form or declines it, as libfsi does with the gradient
+        criteria on), the split S = {eps >= tau}, F = {eps < tau} with the level-step rule (level 0
         records its steps, deeper levels take the min with them; at max_level every
         particle stays in S), then U_SF(tau/6) FSI(S, tau/2) HHS(F, tau/2) U~_SF(2 tau/3)
         HHS(F, tau/2) FSI(S, tau/2) U_SF(tau/6), with PN1.0 S-F kicks of tau/2 around the
@@ -271,7 +283,17 @@ class ShardedFSI:
         n = P.numel()
         if n == 0:
             return
-        st = self.c.timesteps(pos, vel, mass, P, eps2).to(pos.dtype)
+        st = None
+        rows = getattr(self.c, "timesteps_rows", None)
+        if rows is not None and self.ex.world > 1:
+            # each rank the steps of its slice, all-gathered (the same choice on every
+            # rank: it depends only on the compute's parameters)
+            lo, hi = slice_bounds(n, self.ex.world, self.ex.rank)
+            mine = rows(pos, vel, mass, P, lo, hi, eps2)
+            if mine is not None:
+                st = self.ex.all_gather_cols(mine.to(pos.dtype).reshape(1, -1), n)[0]
+        if st is None:
+            st = self.c.timesteps(pos, vel, mass, P, eps2).to(pos.dtype)
         Pl = P.long()
         if level == 0:
             self._hhs_step0[Pl] = st

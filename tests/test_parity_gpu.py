@@ -562,6 +562,31 @@ def test_timesteps_gradient_criteria(F, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,lo,hi,eps2", [(9000, 0, 4500, 0.0), (9000, 4500, 9000, 1e-4),
+                                          (9000, 1234, 1235, 0.0), (300, 17, 200, 0.0),
+                                          (300, 0, 300, 1e-4), (300, 120, 120, 0.0)])
+def test_timesteps_sub_range(F, prec, n, lo, hi, eps2):
+    """fsi_timesteps_sub: the steps of the slice P[lo:hi] of an id list against the whole
+    set (one rank's share of an i-sharded time-step pass), in the tiled and the wide form,
+    softened or not, against the oracle's steps of the whole set; FSI_ERR_UNSUPPORTED with
+    the gradient criteria on."""
+    c = inputs.plummer(12000, 71, imf="kroupa")
+    P = np.sort(inputs.random_subset(12000, n, 72)).astype(np.int32)
+    ref = oracle.timesteps(c.pos, c.vel, c.mass, P, eps2=eps2)[lo:hi]
+    with F.Context(prec, eps2=eps2) as ctx:
+        s = host(F.fsi_timesteps_sub(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P), lo, hi))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert s.shape == (hi - lo,)
+    tol = 1e-12 if prec == "fp64" else 2e-5
+    if hi > lo:
+        assert np.abs(s / ref - 1).max() < tol
+    with F.Context(prec, eta_grad=0.1) as ctx:
+        with pytest.raises(F.FsiError) as ei:
+            F.fsi_timesteps_sub(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P), 0, 10)
+        assert ei.value.code == F.FSI_ERR_UNSUPPORTED
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("small,grid", [(0, -1), (-1, -1), (0, 0), (-1, 0)])
 def test_hhs_interval_gradient_criteria(F, prec, small, grid):
     """One HHS interval with the gradient and velocity-per-acceleration criteria on, the

@@ -44,6 +44,9 @@ class OracleCompute:
         return torch.as_tensor(oracle.timesteps(pos.numpy(), vel.numpy(), mass.numpy(), P.numpy(),
                                                 eps2=eps2))
 
+    def timesteps_rows(self, pos, vel, mass, P, lo, hi, eps2):
+        return self.timesteps(pos, vel, mass, P, eps2)[lo:hi]
+
 
 def _free_port():
     s = socket.socket()
