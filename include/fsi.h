@@ -290,8 +290,9 @@ int fsi_step_sub(fsi_ctx *ctx, int N, double *pos, double *vel, const double *ma
 int fsi_timesteps(fsi_ctx *ctx, int N, const double *pos, const double *vel,
                   const double *mass, const int *P, int n, double *step_out, void *stream);
 
-/* Time steps of the entries P[lo, hi) of the set against the whole set P (the criteria of
- * fsi_timesteps; one receiver slice of an i-sharded time-step pass).  step_out: hi - lo.
+/* Time steps of the entries P[lo, hi) of the set against the whole set P (Sect. 3.4: the
+ * free-fall, fly-by and jerk criteria of fsi_timesteps; one receiver slice of an i-sharded
+ * time-step pass).  step_out: hi - lo, device, in the order of P[lo, hi).  Asynchronous.
  * FSI_ERR_ARG for a bad range; FSI_ERR_UNSUPPORTED when eta_grad or eta_va > 0 (those
  * criteria need the whole set's own accelerations). */
 int fsi_timesteps_sub(fsi_ctx *ctx, int N, const double *pos, const double *vel,
@@ -380,8 +381,8 @@ int fsi_batch_get_tuning(fsi_batch *batch, int *ipt, int *ctas_per_sm);
 int fsi_batch_stats(fsi_batch *batch, long long *wait_ns, long long *life_ns, int *ctas,
                     int reset);
 
-/* Busy time of the symmetric persistent launches' work items by kind since the last
- * reset: ns[0] / items[0] the sum items of a block with itself (its own pairs), [1] the
+/* Instrumentation of the ensemble launch (Sect. 2.1 FSI cycles of every cluster): busy
+ * time of the symmetric persistent launches' work items by kind since the last reset: ns[0] / items[0] the sum items of a block with itself (its own pairs), [1] the
  * sum items of two blocks, [2] pack and apply items (thread 0 of the CTA, from the end of
  * the item's phase wait to its completion signal).  ns, items: host long long[3].
  * Synchronises the device; reset != 0 zeroes these counters after reading. */
@@ -467,7 +468,7 @@ int fsi_profile(fsi_ctx *ctx, int enable);
  * milliseconds, then clear the record.  launches: host long long[3], ms: host double[3]. */
 int fsi_profile_read(fsi_ctx *ctx, long long *launches, double *ms);
 
-/* Phase profile of the HHS recursions run in one cooperative launch (recorded while
+/* Phase profile of the HHS recursions (Sect. 2.2) run in one cooperative launch (recorded while
  * fsi_profile is on): per phase kind (0 time steps, 1 split (empty: every CTA splits on
  * its own without a barrier, and that time counts toward the next phase), 2 inter-level
  * kick (incl. the FSI passes that share one), 3 FSI pass of the slow set, 4 one-CTA
