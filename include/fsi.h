@@ -468,8 +468,8 @@ int fsi_profile(fsi_ctx *ctx, int enable);
  * milliseconds, then clear the record.  launches: host long long[3], ms: host double[3]. */
 int fsi_profile_read(fsi_ctx *ctx, long long *launches, double *ms);
 
-/* Phase profile of the HHS recursions (Sect. 2.2) run in one cooperative launch (recorded while
- * fsi_profile is on): per phase kind (0 time steps, 1 split (empty: every CTA splits on
+/* Phase profile of the HHS recursions (Sect. 2.2) run in one cooperative launch
+ * (recorded while fsi_profile is on): per phase kind (0 time steps, 1 split (empty: every CTA splits on
  * its own without a barrier, and that time counts toward the next phase), 2 inter-level
  * kick (incl. the FSI passes that share one), 3 FSI pass of the slow set, 4 one-CTA
  * recursion of a small fast set, 5 gradient time-step criteria, 6 set-up, 7 PN1.0 kick
