@@ -819,6 +819,29 @@ def test_hhs_interval_tiny_sets(F, prec, n, grid):
     assert np.abs(v - rv).max() <= tol * 100
 
 
+def test_hhs_interval_full_size(F):
+    """One HHS interval of the N = 65536 Kroupa workload the benchmark times (tau0 = 1/64,
+    12 levels; the top levels walked from the host, the mid-size ones in cooperative
+    launches, the small ones in the one-CTA recursion) against the oracle's interval of
+    the same set: the same level histogram in both precisions, the FP64 state to rounding
+    and the mixed state within the mixed path's error (measured: positions 8.9e-10,
+    velocities 9.8e-8)."""
+    c = inputs.workload("kroupa64k")
+    tau = 1.0 / 64
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau)
+    used = np.nonzero(counts)[0].max() + 1
+    for prec, tp, tv in (("fp64", 1e-12, 1e-11), ("mixed", 1e-8, 1e-6)):
+        with F.Context(prec) as ctx:
+            p, v = dev(c.pos), dev(c.vel)
+            assert F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau) == F.FSI_OK
+            lv = F.fsi_level_stats(ctx)
+            p, v = host(p), host(v)
+            assert F.fsi_sync_status(ctx) == F.FSI_OK
+        assert lv[:used] == list(counts[:used]), prec
+        assert np.abs(p - rp).max() <= tp, prec
+        assert np.abs(v - rv).max() <= tv, prec
+
+
 def test_hhs_grid_barrier_timeout(F):
     """A grid barrier wait of the cooperative HHS launch that runs out (timeout_ns = 1 ns, so
     a CTA that arrives early gives up after its first clock check) latches FSI_ERR_TIMEOUT,
