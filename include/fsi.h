@@ -90,10 +90,11 @@ typedef struct fsi_params {
     double c;             /* speed of light in N-body units; 0 switches PN1.0 off */
     int split;            /* source-split factor override (0 = automatic) */
     long long timeout_ns; /* budget of every bounded device wait (0 = 2e9 ns) */
-    int symmetric;        /* 1 (default): a set's self-interaction, and the two directions
-                             of a large cross-level pass, evaluate every unordered pair once
-                             and add it to both particles (Newton's third law); 0: every
-                             ordered pair is evaluated by its receiving particle */
+    int symmetric;        /* 1 (default): a set's self-interaction (pair sums and time
+                             steps), and the two directions of a large cross-level pass,
+                             evaluate every unordered pair once and add it to both
+                             particles (Newton's third law); 0: every ordered pair is
+                             evaluated by its receiving particle */
     int hhs_small_max;    /* HHS: a fast set of at most this many particles (0 = 256; the
                              maximum is 512) runs its whole recursion inside one CTA; -1 =
                              always walk the levels from the host */
@@ -285,8 +286,10 @@ int fsi_step_sub(fsi_ctx *ctx, int N, double *pos, double *vel, const double *ma
  * fsi_params.eta_grad / eta_va are > 0, the gradient criteria (Eqs. dt-nabla1, dt-nabla2)
  * and the velocity-per-acceleration criterion (Eq. vel-acc-crit) from the set's own
  * accelerations and force-gradient sums (one extra acc + grad pass).  step_out: n.
- * FSI_FP64: FP64 throughout.  FSI_MIXED: FP32 pair arithmetic (hi/lo separations,
- * minima of squared ratios), ~1e-6 relative. */
+ * FSI_FP64: FP64 throughout; with fsi_params.symmetric = 1 and n >= 2048 every unordered
+ * pair is evaluated once (the a and j sums of the jerk criterion then add in another
+ * order, the free-fall and fly-by minima are the same).  FSI_MIXED: FP32 pair arithmetic
+ * (hi/lo separations, minima of squared ratios), ~1e-6 relative. */
 int fsi_timesteps(fsi_ctx *ctx, int N, const double *pos, const double *vel,
                   const double *mass, const int *P, int n, double *step_out, void *stream);
 

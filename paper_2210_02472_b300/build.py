@@ -13,7 +13,7 @@ PKG = Path(__file__).resolve().parent
 CSRC = PKG / "csrc"
 LIB = PKG / "libfsi.so"
 INCLUDE = PKG.parent / "include"
-SOURCES = ["pair_kernels.cu", "aux_kernels.cu", "vjp_kernels.cu", "batch_kernels.cu", "hhs_small.cu", "hhs_grid.cu", "order_kernels.cu", "noalloc.cu", "probe_kernels.cu", "subsys_kernels.cu", "steps_x2.cu", "fsi_api.cu"]
+SOURCES = ["pair_kernels.cu", "aux_kernels.cu", "vjp_kernels.cu", "batch_kernels.cu", "hhs_small.cu", "hhs_grid.cu", "order_kernels.cu", "noalloc.cu", "probe_kernels.cu", "subsys_kernels.cu", "steps_x2.cu", "steps_f64.cu", "fsi_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -729,9 +729,11 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
     const double* mc = mass;
     const bool mixed = c->p.precision == FSI_MIXED;
     const bool crit = c->p.eta_grad > 0.0 || c->p.eta_va > 0.0;
-    // compact copies for the FP64 kernel and the gradient criteria; the mixed kernel packs
-    // its records straight from the global arrays through the id list
-    if (Pids && (!mixed || crit)) {
+    const bool sym64 = !mixed && whole && c->p.symmetric && n >= steps_sym_f64_min_n();
+    // compact copies for the one-sided FP64 kernel and the gradient criteria; the mixed
+    // and the symmetric FP64 kernels pack their records straight from the global arrays
+    // through the id list
+    if (Pids && ((!mixed && !sym64) || crit)) {
         CK(ensure(c->xc, 3 * (size_t)n * 8));
         CK(ensure(c->vc, 3 * (size_t)n * 8));
         CK(ensure(c->mc, (size_t)n * 8));
@@ -768,7 +770,14 @@ int timesteps_core(fsi_ctx* c, int N, const double* pos, const double* vel, cons
                                c->p.eta_jerk, P<float>(c->stpart), step, c->err_d, budget(c),
                                c->sm_count, wide_limit(c), s, lo, hi - lo));
     }
-    else
+    else if (sym64) {
+        CK(ensure(c->rec[1], pad_tile(n) * 32));
+        CK(ensure(c->accrec[1], pad_tile(n) * 32));
+        CK(ensure(c->stpart, steps_sym_f64_work_bytes(n)));
+        CU(launch_steps_sym_f64(N, pos, vel, mass, Pids, n, c->rec[1].p, c->accrec[1].p, c->p.eps2,
+                                c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->stpart.p, step, c->err_d,
+                                budget(c), c->sm_count, s));
+    } else
         CU(launch_timesteps(n, xc, vc, mc, c->p.eta_ff, c->p.eta_fb, c->p.eta_jerk, c->p.eps2, step,
                             c->err_d, s, lo, hi - lo));
     if (!whole) return crit ? fail(FSI_ERR_UNSUPPORTED, "time steps of a sub-range with the gradient criteria") : FSI_OK;
@@ -1087,7 +1096,8 @@ int fsi_reserve(fsi_ctx* c, int N, int n) {
     CK(ensure(c->part, (size_t)64 * 3 * n * 8));
     CK(ensure(c->epart, (size_t)(energy_blocks(n) * 2 + 2) * 8));
     CK(ensure(c->accum, 3 * (size_t)n * 8));      // also both sides of a bipartite pass
-    CK(ensure(c->stpart, std::max(steps_x2_part_bytes(n, c->sm_count), steps_sym_work_bytes(n))));
+    CK(ensure(c->stpart, std::max({steps_x2_part_bytes(n, c->sm_count), steps_sym_work_bytes(n),
+                                   steps_sym_f64_work_bytes(n)})));
     // spatial ordering and far-tile inputs of the symmetric mixed kernel
     CK(ensure(c->rel, pad_tile(n) * 16));
     CK(ensure(c->sub, (pad_tile(n) / 32) * 16));

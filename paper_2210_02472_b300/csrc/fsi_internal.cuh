@@ -419,6 +419,17 @@ cudaError_t launch_steps_sym(int n, const void* rec, const void* vrec, double ep
                              long long timeout_ns, int sm_count, cudaStream_t s,
                              const void* rel = nullptr, const void* sub = nullptr,
                              float far_k2 = 0.f);
+// Symmetric FP64 time steps (steps_f64.cu, every unordered pair once) of the set idx (null:
+// the first n) of the 3 x N rows, for sets of at least steps_sym_f64_min_n() particles.
+// rec, vrec: workspace of >= 32 n bytes each (16-byte aligned), filled with the set's
+// position and velocity records; work: steps_sym_f64_work_bytes(n) bytes (8-byte aligned).
+size_t steps_sym_f64_work_bytes(int n);
+int steps_sym_f64_min_n();
+cudaError_t launch_steps_sym_f64(int N, const double* pos, const double* vel, const double* mass,
+                                 const int* idx, int n, void* rec, void* vrec, double eps2,
+                                 double eta_ff, double eta_fb, double eta_jerk, void* work,
+                                 double* step, int* err, long long timeout_ns, int sm_count,
+                                 cudaStream_t s);
 // Mixed time steps (one-sided packed kernel, or its wide form) of records [i_off, i_off +
 // n_i) (n_i < 0: all n) against all n records, into step[0, n_i); part: split partials of
 // at least steps_x2_part_bytes(n, sm_count, n_i) bytes.

@@ -541,6 +541,44 @@ def test_timesteps_mixed(F, n, wide, eps2, symmetric):
         assert np.all(np.abs(got[fin] / want[fin] - 1) < 2e-5)
 
 
+@pytest.mark.parametrize("n", [2048, 3000, 13001])
+@pytest.mark.parametrize("eps2", [0.0, 1e-4])
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_timesteps_fp64_forms(F, n, eps2, symmetric):
+    """FP64 time steps against the oracle: the symmetric kernel (every unordered pair once,
+    sets of >= 2048 with symmetric = True; 2048: whole blocks of 512, 3000 and 13001: a
+    ragged last tile and block) and the one-sided kernel, softened or not, for the whole
+    set and for a subset given by an id list (all of it at n = 2048)."""
+    c = inputs.plummer(n, 31 + n, imf="kroupa")
+    ref = oracle.timesteps(c.pos, c.vel, c.mass, eps2=eps2)
+    P = inputs.random_subset(n, max(2048, n // 2), 11)
+    refp = oracle.timesteps(c.pos, c.vel, c.mass, P, eps2=eps2)
+    with F.Context("fp64", eps2=eps2, symmetric=symmetric) as ctx:
+        s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+        sp = host(F.fsi_timesteps(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert np.abs(s / ref - 1).max() < 1e-12
+    assert np.abs(sp / refp - 1).max() < 1e-12
+
+
+@pytest.mark.parametrize("symmetric", [True, False])
+def test_timesteps_fp64_cold_start_and_massless(F, symmetric):
+    """Zero denominators in the FP64 minima: all velocities zero (no fly-by bound for any
+    pair, and no jerk), and massless particles (a pair of two has no free-fall bound)."""
+    n = 3000
+    c = inputs.plummer(n, 41, imf="kroupa")
+    vel = np.zeros_like(c.vel)
+    mass = c.mass.copy()
+    mass[:40] = 0.0
+    ref = oracle.timesteps(c.pos, vel, mass)
+    base = oracle.timesteps(c.pos, vel, c.mass)
+    assert np.all(np.isfinite(ref)) and not np.array_equal(ref[:40], base[:40])
+    with F.Context("fp64", symmetric=symmetric) as ctx:
+        s = host(F.fsi_timesteps(ctx, dev(c.pos), dev(vel), dev(mass)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert np.abs(s / ref - 1).max() < 1e-12
+
+
 @pytest.mark.parametrize("prec", PRECS)
 def test_timesteps_gradient_criteria(F, prec):
     """Gradient (Eqs. dt-nabla1/2) and velocity-per-acceleration (Eq. vel-acc-crit)
