@@ -567,8 +567,9 @@ __global__ void __launch_bounds__(kThreads) wide_pair2_kernel(const PairArgs a, 
 //             by index) -- every pair inside a block is then evaluated twice, which is
 //             only (256 I)/n of the work;
 //   c >= 1  : chunk c-1 of `chunk` tiles among the tiles above the block, symmetric.
-// Items past the end of the tile range exit at once.  The i-side sums (FP32 per tile,
-// FP64 across tiles) and the j-side sums (FP32 warp reduce-scatter + shared-memory sum
+// Items past the end of the tile range exit at once.  The i-side sums (mixed: FP32 per
+// tile, FP64 across tiles; FP64: FP64) and the j-side sums (mixed: FP32 warp
+// reduce-scatter; FP64: carried around the warp by f64_rotate32; then a shared-memory sum
 // over the CTA's warps, per tile) are added to the FP64 accumulator with red.global.add;
 // a finalize kernel then applies the epilogue.
 struct SymArgs {
@@ -725,6 +726,57 @@ __device__ __forceinline__ void f64_grad_sym(const D4 j, const D4 aj, const SymF
     const double tx = fma(y3, bx, s * dx), ty = fma(y3, by, s * dy), tz = fma(y3, bz, s * dz);
     gi[0] = fma(aj.w, tx, gi[0]); gi[1] = fma(aj.w, ty, gi[1]); gi[2] = fma(aj.w, tz, gi[2]);
     gj[0] = fma(p.nm, tx, gj[0]); gj[1] = fma(p.nm, ty, gj[1]); gj[2] = fma(p.nm, tz, gj[2]);
+}
+
+// 32 sources jj .. jj + 31 of a staged tile on the thread's I receivers, both sides, with
+// the source side carried around the warp: lane l starts with a packet of source jj + l
+// (position record, acceleration record for the gradient, partial sums) and hands it to
+// lane l - 1 after each step, so that after 32 steps the packet is back in lane l with
+// the terms of all the warp's receivers, and the lanes' partial sums need no FP64 adds to
+// be combined (the B300 FP64 pipe issues only two lane operations per SM and clock; the
+// shuffles run elsewhere).  tot: the warp's sums for source jj + lane (zero past cnt).
+// FULL: all 32 sources exist; otherwise a packet past the tile's cnt sources is carried
+// along without terms.
+template <int KIND, int I, bool FULL>
+__device__ __forceinline__ void f64_rotate32(const D4* rec, const D4* arec, int jj, int cnt,
+                                             int lane, const SymF64I (&pi)[I], double eps2,
+                                             double (&acc)[I][3], double (&tot)[3]) {
+    const int jh = jj + lane;
+    int valid = FULL || jh < cnt;
+    const int jl = valid ? jh : jj;
+    D4 r = rec[jl];
+    D4 aj = make_d4(0.0, 0.0, 0.0, 0.0);
+    if constexpr (KIND == KIND_GRAD) aj = arec[jl];
+    double f[3] = {0.0, 0.0, 0.0};
+    const int from = (lane + 1) & 31;
+#pragma unroll 2
+    for (int k = 0; k < 32; ++k) {
+        if (FULL || valid) {
+            if constexpr (KIND == KIND_ACC) {
+#pragma unroll
+                for (int u = 0; u < I; ++u) f64_acc_sym(r, pi[u], eps2, acc[u], f);
+            } else {
+#pragma unroll
+                for (int u = 0; u < I; ++u) f64_grad_sym(r, aj, pi[u], eps2, acc[u], f);
+            }
+        }
+        r.x = __shfl_sync(0xffffffffu, r.x, from);
+        r.y = __shfl_sync(0xffffffffu, r.y, from);
+        r.z = __shfl_sync(0xffffffffu, r.z, from);
+        if constexpr (KIND == KIND_ACC) {
+            r.w = __shfl_sync(0xffffffffu, r.w, from);
+        } else {
+            aj.x = __shfl_sync(0xffffffffu, aj.x, from);
+            aj.y = __shfl_sync(0xffffffffu, aj.y, from);
+            aj.z = __shfl_sync(0xffffffffu, aj.z, from);
+            aj.w = __shfl_sync(0xffffffffu, aj.w, from);
+        }
+        f[0] = __shfl_sync(0xffffffffu, f[0], from);
+        f[1] = __shfl_sync(0xffffffffu, f[1], from);
+        f[2] = __shfl_sync(0xffffffffu, f[2], from);
+        if (!FULL) valid = __shfl_sync(0xffffffffu, valid, from);
+    }
+    tot[0] = f[0]; tot[1] = f[1]; tot[2] = f[2];
 }
 
 template <int P, int KIND>
@@ -934,27 +986,12 @@ __global__ void __launch_bounds__(kThreads, 2) sym_pair_kernel(const SymArgs a) 
                     }
                 }
             } else {
-                for (int jj = 0; jj < cnt; jj += 4) {
-                    double fj[4][3];
-#pragma unroll
-                    for (int g = 0; g < 4; ++g) {
-                        fj[g][0] = fj[g][1] = fj[g][2] = 0.0;
-                        if (jj + g < cnt) {
-                            const D4 r = rec[jj + g];
-                            if constexpr (KIND == KIND_ACC) {
-#pragma unroll
-                                for (int u = 0; u < I; ++u) f64_acc_sym(r, pi[u], a.eps2, acc64[u], fj[g]);
-                            } else {
-                                const D4 aj = arec[jj + g];
-#pragma unroll
-                                for (int u = 0; u < I; ++u) f64_grad_sym(r, aj, pi[u], a.eps2, acc64[u], fj[g]);
-                            }
-                        }
-                    }
+                for (int jj = 0; jj < cnt; jj += 32) {
                     double tot[3];
-                    reduce_scatter4<double>(fj, lane, tot);
-                    const int jl = jj + (lane >> 3);
-                    if ((lane & 7) == 0 && jl < cnt) {
+                    if (jj + 32 <= cnt) f64_rotate32<KIND, I, true>(rec, arec, jj, cnt, lane, pi, a.eps2, acc64, tot);
+                    else f64_rotate32<KIND, I, false>(rec, arec, jj, cnt, lane, pi, a.eps2, acc64, tot);
+                    const int jl = jj + lane;
+                    if (jl < cnt) {
                         JT* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
                         dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
                     }
@@ -1952,7 +1989,8 @@ static cudaError_t launch_cross_x2_t(const CrossArgs& a, cudaStream_t s) {
 }
 
 // FP64 form of the bipartite kernel: the symmetric FP64 pair terms of the single-set
-// kernel (I = 2 particles of S per thread), the F side reduced across the warp in FP64.
+// kernel (I = 2 particles of S per thread), the F side carried around the warp
+// (f64_rotate32).
 template <int KIND, int I>
 __global__ void __launch_bounds__(kThreads, 2) cross_f64_kernel(const CrossArgs a) {
     constexpr int ACCREC = SymCfg<FSI_FP64, KIND>::ACCREC;
@@ -2017,27 +2055,12 @@ __global__ void __launch_bounds__(kThreads, 2) cross_f64_kernel(const CrossArgs 
         const unsigned char* base = smem + st * SB;
         const D4* rec = reinterpret_cast<const D4*>(base);
         const D4* arec = reinterpret_cast<const D4*>(base + kTileJ * kRec);
-        for (int jj = 0; jj < cnt; jj += 4) {
-            double fj[4][3];
-#pragma unroll
-            for (int g = 0; g < 4; ++g) {
-                fj[g][0] = fj[g][1] = fj[g][2] = 0.0;
-                if (jj + g < cnt) {
-                    const D4 r = rec[jj + g];
-                    if constexpr (KIND == KIND_ACC) {
-#pragma unroll
-                        for (int u = 0; u < I; ++u) f64_acc_sym(r, pi[u], a.eps2, acc64[u], fj[g]);
-                    } else {
-                        const D4 aj = arec[jj + g];
-#pragma unroll
-                        for (int u = 0; u < I; ++u) f64_grad_sym(r, aj, pi[u], a.eps2, acc64[u], fj[g]);
-                    }
-                }
-            }
+        for (int jj = 0; jj < cnt; jj += 32) {
             double tot[3];
-            reduce_scatter4<double>(fj, lane, tot);
-            const int jl = jj + (lane >> 3);
-            if ((lane & 7) == 0 && jl < cnt) {
+            if (jj + 32 <= cnt) f64_rotate32<KIND, I, true>(rec, arec, jj, cnt, lane, pi, a.eps2, acc64, tot);
+            else f64_rotate32<KIND, I, false>(rec, arec, jj, cnt, lane, pi, a.eps2, acc64, tot);
+            const int jl = jj + lane;
+            if (jl < cnt) {
                 double* dst = jpart + ((size_t)warp * kTileJ + jl) * 3;
                 dst[0] = tot[0]; dst[1] = tot[1]; dst[2] = tot[2];
             }
