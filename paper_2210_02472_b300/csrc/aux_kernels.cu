@@ -740,8 +740,12 @@ cudaError_t launch_pack_vel(int N, const double* vel, const double* mass, const 
     return cudaGetLastError();
 }
 
-// Energy: per-CTA partial sums of the kinetic energy and of -1/2 sum_i sum_{j != i}
-// m_i m_j / sqrt(r^2 + eps2), reduced in a fixed order by energy_finish_kernel.
+// Energy (Sect. 2.1, the Hamiltonian): per-CTA partial sums of the kinetic energy and of
+// the potential -sum_{i<j} m_i m_j / sqrt(r^2 + eps2), every unordered pair once: thread i
+// sums m_j / r over the sources j > i, from its block's own tile on, so the blocks of
+// small i carry the most sources and, dispatched first, leave the short ones for the
+// tail.  The partials are reduced in a fixed order by energy_finish_kernel.  A coincident
+// unsoftened pair (r^2 = 0, tested on its bits) is skipped and reported.
 __global__ void energy_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
                               const double* __restrict__ mc, double eps2, double* __restrict__ part,
                               int* err) {
@@ -751,7 +755,9 @@ __global__ void energy_kernel(int n, const double* __restrict__ xc, const double
     const int ii = min(i, n - 1);
     const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
     double w = 0.0;
-    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
+    bool coincident = false;
+    const int jstart = blockIdx.x * blockDim.x;
+    for (int j0 = jstart; j0 < n; j0 += kAuxTile) {
         __syncthreads();
         for (int t = threadIdx.x; t < kAuxTile; t += blockDim.x) {
             const int j = j0 + t;
@@ -759,19 +765,22 @@ __global__ void energy_kernel(int n, const double* __restrict__ xc, const double
         }
         __syncthreads();
         const int cnt = min(kAuxTile, n - j0);
-        for (int t = 0; t < cnt; ++t) {
-            if (j0 + t == ii) continue;
+        // the block's own tile: only j > i (a thread past the end, ii = n - 1, has none)
+        const int t0 = j0 == jstart ? ii - j0 + 1 : 0;
+#pragma unroll 4
+        for (int t = t0; t < cnt; ++t) {
             const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
-            const double r2 = dx * dx + dy * dy + dz * dz + eps2;
-            if (r2 == 0.0) { if (i < n) set_error(err, FSI_ERR_COINCIDENT); continue; }
+            const double r2 = fma(dx, dx, fma(dy, dy, fma(dz, dz, eps2)));
+            if (__double_as_longlong(r2) == 0) { coincident = true; continue; }
             w = fma(sm[t], rsqrt_f64(r2), w);
         }
     }
+    if (coincident && i < n) set_error(err, FSI_ERR_COINCIDENT);
     double kin = 0.0;
     if (i < n) {
         const double u = vc[i], v = vc[(size_t)n + i], ww = vc[2 * (size_t)n + i];
         kin = 0.5 * mc[i] * (u * u + v * v + ww * ww);
-        w = -0.5 * mc[i] * w;
+        w = -mc[i] * w;
     } else {
         w = 0.0;
     }

@@ -516,6 +516,23 @@ def test_timesteps_and_energy(F):
     assert abs(e[0] / T - 1) < 1e-13 and abs(e[1] / W - 1) < 1e-12
 
 
+@pytest.mark.parametrize("n,eps2", [(2, 0.0), (129, 0.0), (13001, 0.0), (13001, 1e-4)])
+def test_energy_every_pair_once(F, n, eps2):
+    """The FP64 energy (each unordered pair once: receiver i over the sources j > i from
+    its block's own 128-particle tile on) against the oracle: two particles, one particle
+    past a full block, a ragged last block, softened, and a subset given by an id list."""
+    c = inputs.plummer(n, 61 + n, imf="kroupa")
+    T, W = oracle.energy(c.pos, c.vel, c.mass, eps2=eps2)
+    P = inputs.random_subset(n, max(2, n // 3), 12)
+    Tp, Wp = oracle.energy(c.pos, c.vel, c.mass, P, eps2=eps2)
+    with F.Context("fp64", eps2=eps2) as ctx:
+        e = host(F.fsi_energy(ctx, dev(c.pos), dev(c.vel), dev(c.mass)))
+        ep = host(F.fsi_energy(ctx, dev(c.pos), dev(c.vel), dev(c.mass), ids(P)))
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    assert abs(e[0] / T - 1) < 1e-13 and abs(e[1] / W - 1) < 1e-12
+    assert abs(ep[0] / Tp - 1) < 1e-13 and abs(ep[1] / Wp - 1) < 1e-12
+
+
 @pytest.mark.parametrize("n", [2, 3, 257, 3000, 4096, 13001])
 @pytest.mark.parametrize("wide", WIDE)
 @pytest.mark.parametrize("eps2", [0.0, 1e-4])
