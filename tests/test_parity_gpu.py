@@ -597,11 +597,14 @@ def test_timesteps_fp64_cold_start_and_massless(F, symmetric):
 
 
 @pytest.mark.parametrize("prec", PRECS)
-def test_timesteps_gradient_criteria(F, prec):
+@pytest.mark.parametrize("n,k", [(2000, 500), (3000, 2100)])
+def test_timesteps_gradient_criteria(F, prec, n, k):
     """Gradient (Eqs. dt-nabla1/2) and velocity-per-acceleration (Eq. vel-acc-crit)
-    criteria on top of free fall, fly-by and jerk, for the whole set and a subset."""
-    c = inputs.plummer(2000, 24, imf="kroupa")
-    P = inputs.random_subset(2000, 500, 8)
+    criteria on top of free fall, fly-by and jerk, for the whole set and a subset (3000 /
+    2100: both take the symmetric FP64 time-step kernel, with the set's compact copies for
+    the criteria)."""
+    c = inputs.plummer(n, 24, imf="kroupa")
+    P = inputs.random_subset(n, k, 8)
     kw = dict(eta_grad=0.1, eta_va=0.05)
     ref = oracle.timesteps(c.pos, c.vel, c.mass, **kw)
     refp = oracle.timesteps(c.pos, c.vel, c.mass, P, **kw)
@@ -665,6 +668,32 @@ def test_hhs_interval_gradient_criteria(F, prec, small, grid):
     tol = 1e-11 if prec == "fp64" else 1e-7
     assert np.abs(p - rp).max() <= tol
     assert np.abs(v - rv).max() <= tol * 100
+
+
+@pytest.mark.parametrize("grid", [-1, 0])
+def test_hhs_interval_gradient_criteria_fp64_large_sets(F, grid):
+    """FP64, N = 2500, the gradient and velocity-per-acceleration criteria on.  Walked from
+    the host (grid = -1), the level sets of >= 2048 take the symmetric FP64 time-step kernel
+    and the criteria's extra acc + grad pass over the set's compact copies; grid = 0: the
+    whole interval in one cooperative launch.  Seed 26 keeps the hierarchy 10 levels deep
+    (levels 0 and 1: 2500 and 2149 particles); with seed 22 a tight binary is stepped 2^25
+    times in the interval and amplifies rounding until the deepest levels' counts differ
+    from the oracle's, identically in every kernel form."""
+    c = inputs.plummer(2500, 26, imf="kroupa")
+    tau = 1.0 / 16
+    kw = dict(eta_grad=0.1, eta_va=0.1)
+    rp, rv, counts, _ = oracle.hhs_interval(c.pos, c.vel, c.mass, tau, **kw)
+    with F.Context("fp64", hhs_grid_max=grid, **kw) as ctx:
+        p, v = dev(c.pos), dev(c.vel)
+        code = F.fsi_hhs_interval(ctx, p, v, dev(c.mass), tau)
+        lv = F.fsi_level_stats(ctx)
+        p, v = host(p), host(v)
+        assert code == F.FSI_OK
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+    used = np.nonzero(counts)[0].max() + 1
+    assert lv[:used] == list(counts[:used])
+    assert np.abs(p - rp).max() <= 1e-11
+    assert np.abs(v - rv).max() <= 1e-9
 
 
 # (hhs_small_max, wide_ctas, hhs_grid_max) of the HHS interval tests: the whole interval
