@@ -180,6 +180,25 @@ int fsi_grad(fsi_ctx *ctx, int N, const double *pos, const double *mass,
              const double *accg, const int *A, int nA, const int *B, int nB,
              double eps2, double *grad_out, void *stream);
 
+/* Share `part` (0 <= part < nparts) of the same-set pass acc(A <- A) (Sect. 2.1, Eq.
+ * new-newton-acc) or G(A <- A) (Eq. new-grad-acc, accg as for fsi_grad): the pair sums
+ * of a subset of the set's unordered pairs, for all nA receivers (out: 3 x nA, device,
+ * in the order of A; overwritten).  The nparts shares add up to fsi_accel / fsi_grad of
+ * the set (up to the order of the additions): one rank's part of a pass split over ranks
+ * by pairs, each pair evaluated once on one rank for both of its particles (Newton's
+ * third law), then summed over the ranks.  With fsi_params.symmetric = 1 and a set large
+ * enough for the tiled symmetric kernel (not the wide form of small passes), share k is a
+ * contiguous range of the kernel's blocks of receivers with about 1/nparts of its work;
+ * otherwise share 0 is the whole pass and the other shares are zero.  All shares of a pass
+ * must come from contexts with the same fsi_params and tuning on the same set and inputs
+ * (the split depends on the kernel variant and on the set's spatial order).  FSI_ERR_ARG
+ * for a bad share.  Asynchronous. */
+int fsi_accel_part(fsi_ctx *ctx, int N, const double *pos, const double *mass, const int *A,
+                   int nA, int part, int nparts, double eps2, double *acc_out, void *stream);
+int fsi_grad_part(fsi_ctx *ctx, int N, const double *pos, const double *mass,
+                  const double *accg, const int *A, int nA, int part, int nparts, double eps2,
+                  double *grad_out, void *stream);
+
 /* acc(A <- B) and the gradient sum G(A <- B) of one splitting term:
  *  - A and B the same list (same pointer, or both NULL): the set's self-interaction
  *    (Sect. 2.1); the a_j inside G are acc(A <- A).

@@ -109,6 +109,8 @@ struct fsi_ctx {
     // in Morton order; xrel/xsub hold the sub-tiles of the smaller set of a pass
     bool lists_ordered = false;
     Buf xrel, xsub;
+    // fsi_accel_part / fsi_grad_part: the share of the same-set pass run_pair evaluates
+    int share_part = 0, share_n = 1;
     // instrumentation: event pairs around pair-kernel launches
     struct ProfRec { int kind; cudaEvent_t a, b; };
     bool profiling = false;
@@ -442,9 +444,11 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
                              n >= kSymClassMin[2];
         CK(timed(c, kind, s, [&] {
             cudaError_t e = launch_sym_pair(prec, kind, sv, a.irec, a.iacc, n, a.eps2, chunk,
-                                            P<double>(c->accum), a.err, a.timeout_ns, farp, s, ff_diag);
+                                            P<double>(c->accum), a.err, a.timeout_ns, farp, s, ff_diag,
+                                            c->share_part, c->share_n);
             if (e == cudaSuccess && ff_diag)
-                e = launch_sym_diag_ff(a.irec, n, sym_block_particles(sv), a.eps2, P<double>(c->accum), s);
+                e = launch_sym_diag_ff(a.irec, n, sym_block_particles(sv), a.eps2, P<double>(c->accum), s,
+                                       c->share_part, c->share_n);
             return e;
         }));
         a.part = P<double>(c->accum);
@@ -469,6 +473,37 @@ int run_pair(fsi_ctx* c, int kind, PairArgs a, cudaStream_t s) {
 }
 
 bool valid_prec(int p) { return p == FSI_FP64 || p == FSI_MIXED; }
+
+// Whether the same-set pass of n particles of this kind takes the tiled symmetric branch
+// of run_pair: the only form whose work a share of fsi_accel_part / fsi_grad_part divides.
+bool sym_same_set(const fsi_ctx* c, int kind, int n) {
+    if (!c->p.symmetric || n <= 0) return false;
+    const int ipt = c->ipt[c->p.precision][kind][n >= kOneSidedLarge];
+    int lg = 0, split = 1;
+    return !wide_plan(c, n, n, kThreads * variant_ipt(ipt), lg, split);
+}
+
+// Share `part` of nparts of a same-set pass: `run` evaluates the pass with the share set
+// (its tiled symmetric form then takes only the share's work items); a pass without that
+// form runs whole in share 0 and leaves zeros (3 x n in out) in the others.
+template <class Run>
+int run_share(fsi_ctx* c, int kind, int n, int part, int nparts, double* out, cudaStream_t s,
+              Run run) {
+    if (nparts < 1 || part < 0 || part >= nparts)
+        return fail(FSI_ERR_ARG, "bad share %d of %d", part, nparts);
+    if (nparts == 1) return run();
+    if (!sym_same_set(c, kind, n)) {
+        if (part == 0) return run();
+        CU(cudaMemsetAsync(out, 0, 3 * (size_t)n * sizeof(double), s));
+        return FSI_OK;
+    }
+    c->share_part = part;
+    c->share_n = nparts;
+    const int r = run();
+    c->share_part = 0;
+    c->share_n = 1;
+    return r;
+}
 
 // Offset k of an id list A inside the id list B when A is the sub-range B[k, k + nA) (same
 // memory: a slice of B, as a sharded pass hands each rank), else -1.
@@ -1245,6 +1280,29 @@ int fsi_grad(fsi_ctx* c, int N, const double* pos, const double* mass, const dou
         a.jid = P<int>(c->ids[1]);
     }
     return run_pair(c, KIND_GRAD, a, s);
+}
+
+int fsi_accel_part(fsi_ctx* c, int N, const double* pos, const double* mass, const int* A,
+                   int nA, int part, int nparts, double eps2, double* acc_out, void* stream) {
+    CK(check_common(c, N));
+    if (nA == 0) return FSI_OK;
+    if (nA < 0 || (!A && nA != N)) return fail(FSI_ERR_ARG, "bad set size nA=%d N=%d", nA, N);
+    if (!pos || !mass || !acc_out) return fail(FSI_ERR_ARG, "NULL array");
+    return run_share(c, KIND_ACC, nA, part, nparts, acc_out, S(stream), [&] {
+        return fsi_accel(c, N, pos, mass, A, nA, A, nA, eps2, acc_out, stream);
+    });
+}
+
+int fsi_grad_part(fsi_ctx* c, int N, const double* pos, const double* mass, const double* accg,
+                  const int* A, int nA, int part, int nparts, double eps2, double* grad_out,
+                  void* stream) {
+    CK(check_common(c, N));
+    if (nA == 0) return FSI_OK;
+    if (nA < 0 || (!A && nA != N)) return fail(FSI_ERR_ARG, "bad set size nA=%d N=%d", nA, N);
+    if (!pos || !mass || !accg || !grad_out) return fail(FSI_ERR_ARG, "NULL array");
+    return run_share(c, KIND_GRAD, nA, part, nparts, grad_out, S(stream), [&] {
+        return fsi_grad(c, N, pos, mass, accg, A, nA, A, nA, eps2, grad_out, stream);
+    });
 }
 
 int fsi_accel_grad(fsi_ctx* c, int N, const double* pos, const double* vel, const double* mass,

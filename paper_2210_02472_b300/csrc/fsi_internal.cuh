@@ -299,15 +299,18 @@ struct SymFar {
     unsigned long long* stats;
 };
 // skip_diag (packed form only): the blocks' own pairs are left out, for launch_sym_diag_ff.
+// part / nparts: only the work items of share `part` of the pass (a contiguous range of
+// i-blocks with about 1/nparts of the tile visits); the shares' sums add up to the pass.
 cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
                             int n, double eps2, int chunk, double* accum, int* err,
                             long long timeout_ns, const SymFar* far, cudaStream_t s,
-                            bool skip_diag = false);
+                            bool skip_diag = false, int part = 0, int nparts = 1);
 // The pairs inside each block of bsz consecutive members of a mixed-precision set
 // (records rec, n members), each member's sum over its block's other members in
-// float-float arithmetic, added into accum (3 x n).
+// float-float arithmetic, added into accum (3 x n); part / nparts: the blocks of that
+// share of the symmetric launch with blocks of bsz.
 cudaError_t launch_sym_diag_ff(const void* rec, int n, int bsz, double eps2, double* accum,
-                               cudaStream_t s);
+                               cudaStream_t s, int part = 0, int nparts = 1);
 // Supported ipt values for (precision, kind): writes up to 16 into out, returns the count.
 int pair_variants(int precision, int kind, int* out);
 int pair_default_ipt(int precision, int kind);

@@ -588,7 +588,33 @@ struct SymArgs {
     float far_k2;
     unsigned long long* far_stats;
     int skip_diag;      // packed form: the blocks' own pairs are left to sym_diag_ff_kernel
+    // share `part` of nparts (0: all): the launch covers the items of a contiguous range of
+    // i-blocks (sym_part_blocks), item index = blockIdx.x + item0
+    int part, nparts;
+    int item0;
 };
+
+// i-blocks [b0, b1) of share `part` of nparts of a symmetric pass over nb blocks of bt
+// source tiles each (ntj tiles in all): contiguous ranges with about equal tile visits,
+// block b costing its own bt tiles plus the ntj - (b + 1) bt tiles above it, each block in
+// the share where the midpoint of its visits falls.  Shares may be empty.
+static void sym_part_blocks(int nb, int bt, int ntj, int part, int nparts, int& b0, int& b1) {
+    if (nparts <= 1) { b0 = 0; b1 = nb; return; }
+    auto w = [&](int b) { return (long long)bt + std::max(0, ntj - (b + 1) * bt); };
+    long long total = 0;
+    for (int b = 0; b < nb; ++b) total += w(b);
+    long long cum = 0;
+    b0 = b1 = nb;
+    bool open = false;
+    for (int b = 0; b < nb; ++b) {
+        const long long wb = w(b);
+        const int owner = (int)std::min<long long>(nparts - 1, (2 * cum + wb) * nparts / (2 * total));
+        if (owner == part && !open) { b0 = b; open = true; }
+        if (owner > part) { if (!open) b0 = b; b1 = b; return; }
+        cum += wb;
+    }
+    if (!open) b0 = nb;
+}
 
 
 // Reduce-scatter of 4 j-groups x 3 components over a warp: on return every lane holds in
@@ -798,8 +824,9 @@ __global__ void __launch_bounds__(kThreads, 2) sym_pair_kernel(const SymArgs a) 
     __shared__ __align__(8) uint64_t bars[kStages];
     JT* jpart = reinterpret_cast<JT*>(smem + kStages * SB);
 
-    const int b = blockIdx.x / (1 + a.nchunk);
-    const int c = blockIdx.x % (1 + a.nchunk);
+    const int item = (int)blockIdx.x + a.item0;
+    const int b = item / (1 + a.nchunk);
+    const int c = item % (1 + a.nchunk);
     const int ntj = (a.n + kTileJ - 1) / kTileJ;
     const bool diag = (c == 0);
     int t0, t1;
@@ -1060,8 +1087,9 @@ __global__ void __launch_bounds__(kThreads, 2) sym_mixed_v2_kernel(const SymArgs
     float* jpart = reinterpret_cast<float*>(smem + kStages * SB);
     double* acc_s = reinterpret_cast<double*>(smem + kStages * SB + JPART);   // [I][3][kThreads]
 
-    const int b = blockIdx.x / (1 + a.nchunk);
-    const int c = blockIdx.x % (1 + a.nchunk);
+    const int item = (int)blockIdx.x + a.item0;
+    const int b = item / (1 + a.nchunk);
+    const int c = item % (1 + a.nchunk);
     const int ntj = (a.n + kTileJ - 1) / kTileJ;
     const bool diag = (c == 0);
     int t0, t1;
@@ -1352,8 +1380,9 @@ __global__ void __launch_bounds__(NT, MINB) sym_mixed_x2_kernel(const SymArgs a)
     // (hi of 2p, hi of 2p+1, lo of 2p, lo of 2p+1) for component q
     float4* acc_s = reinterpret_cast<float4*>(smem + kStages * SB + JPART);
 
-    const int b = blockIdx.x / (1 + a.nchunk);
-    const int c = blockIdx.x % (1 + a.nchunk);
+    const int item = (int)blockIdx.x + a.item0;
+    const int b = item / (1 + a.nchunk);
+    const int c = item % (1 + a.nchunk);
     const int ntj = (a.n + kTileJ - 1) / kTileJ;
     const bool diag = (c == 0);
     int t0, t1;
@@ -1683,17 +1712,17 @@ __device__ __forceinline__ void ff_acc_pair(const float4 h, const float4 l, cons
     }
 }
 
-// CTA (x, y) of a grid over blocks of `bsz` consecutive members of a set of n (records
+// CTA (x, y) of a grid over blocks block0 + x of `bsz` consecutive members of a set of n (records
 // `rec`): the members r = block start + y RPT kThreads + tid + kThreads k (k < RPT) each
 // sum the other members of their block, added into accum (3 x n); sources staged through
 // shared memory in tiles.
 constexpr int kDiagFfRpt = 4;                           // receivers per thread
 __global__ void __launch_bounds__(kThreads) sym_diag_ff_kernel(const RecMix* __restrict__ rec, int n,
-                                                               int bsz, float eps2,
+                                                               int bsz, int block0, float eps2,
                                                                double* __restrict__ accum) {
     constexpr int RPT = kDiagFfRpt;
     __shared__ RecMix src[kTileJ];
-    const int b0 = blockIdx.x * bsz;
+    const int b0 = ((int)blockIdx.x + block0) * bsz;
     const int b1 = min(n, b0 + bsz);
     {
         const int r0 = b0 + (int)blockIdx.y * RPT * kThreads;
@@ -1732,12 +1761,16 @@ __global__ void __launch_bounds__(kThreads) sym_diag_ff_kernel(const RecMix* __r
 }
 
 cudaError_t launch_sym_diag_ff(const void* rec, int n, int bsz, double eps2, double* accum,
-                               cudaStream_t s) {
+                               cudaStream_t s, int part, int nparts) {
     if (n <= 0 || bsz <= 0) return cudaSuccess;
     const int nb = (n + bsz - 1) / bsz;
+    // the blocks of the same share as the symmetric launch (blocks of bsz = bt tiles)
+    int b0, b1;
+    sym_part_blocks(nb, bsz / kTileJ, (n + kTileJ - 1) / kTileJ, part, nparts, b0, b1);
+    if (b1 <= b0) return cudaSuccess;
     const int sweeps = (bsz + kDiagFfRpt * kThreads - 1) / (kDiagFfRpt * kThreads);
-    const dim3 grid((unsigned)nb, (unsigned)sweeps);
-    { sym_diag_ff_kernel<<<grid, kThreads, 0, s>>>(reinterpret_cast<const RecMix*>(rec), n, bsz,
+    const dim3 grid((unsigned)(b1 - b0), (unsigned)sweeps);
+    { sym_diag_ff_kernel<<<grid, kThreads, 0, s>>>(reinterpret_cast<const RecMix*>(rec), n, bsz, b0,
                                                    (float)eps2, accum); note_launch(); }
     return cudaGetLastError();
 }
@@ -2153,14 +2186,18 @@ static cudaError_t launch_sym_x2(SymArgs a, cudaStream_t s) {
     const int above = ntj > BT ? ntj - BT : 0;
     a.nchunk = (above + a.chunk - 1) / a.chunk;
     const int nb = (a.n + NT * I - 1) / (NT * I);
-    const long long grid = (long long)nb * (1 + a.nchunk);
+    int b0, b1;
+    sym_part_blocks(nb, BT, ntj, a.part, a.nparts, b0, b1);
+    a.item0 = b0 * (1 + a.nchunk);
+    const long long grid = (long long)(b1 - b0) * (1 + a.nchunk);
     if (grid > 2147483647LL) return cudaErrorInvalidValue;
+    if (grid == 0) return cudaSuccess;
     { sym_mixed_x2_kernel<KIND, I, MINB, NT><<<(unsigned)grid, NT, SMEM, s>>>(a); note_launch(); }
     return cudaGetLastError();
 }
 
 template <int KIND, int I, bool FAR>
-static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
+static cudaError_t launch_sym_v2(SymArgs a, cudaStream_t s) {
     constexpr int SB = kTileJ * (kRec + SymCfg<FSI_MIXED, KIND>::ACCREC + (FAR ? 16 : 0)) +
                        (FAR ? (kTileJ / 32) * 16 : 0);
     constexpr int SMEM = kStages * SB + SymCfg<FSI_MIXED, KIND>::JPART + I * 3 * kThreads * (int)sizeof(double);
@@ -2170,14 +2207,18 @@ static cudaError_t launch_sym_v2(const SymArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
-    const long long grid = (long long)nb * (1 + a.nchunk);
+    int b0, b1;
+    sym_part_blocks(nb, I, (a.n + kTileJ - 1) / kTileJ, a.part, a.nparts, b0, b1);
+    a.item0 = b0 * (1 + a.nchunk);
+    const long long grid = (long long)(b1 - b0) * (1 + a.nchunk);
     if (grid > 2147483647LL) return cudaErrorInvalidValue;
+    if (grid == 0) return cudaSuccess;
     { sym_mixed_v2_kernel<KIND, I, FAR><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
     return cudaGetLastError();
 }
 
 template <int P, int KIND, int I>
-static cudaError_t launch_sym_one(const SymArgs& a, cudaStream_t s) {
+static cudaError_t launch_sym_one(SymArgs a, cudaStream_t s) {
     constexpr int SMEM = SymCfg<P, KIND>::SMEM;
     static std::atomic<unsigned long long> attr_dev{0};
     {
@@ -2185,8 +2226,12 @@ static cudaError_t launch_sym_one(const SymArgs& a, cudaStream_t s) {
         if (e != cudaSuccess) return e;
     }
     const int nb = (a.n + kThreads * I - 1) / (kThreads * I);
-    const long long grid = (long long)nb * (1 + a.nchunk);
+    int b0, b1;
+    sym_part_blocks(nb, I, (a.n + kTileJ - 1) / kTileJ, a.part, a.nparts, b0, b1);
+    a.item0 = b0 * (1 + a.nchunk);
+    const long long grid = (long long)(b1 - b0) * (1 + a.nchunk);
     if (grid > 2147483647LL) return cudaErrorInvalidValue;
+    if (grid == 0) return cudaSuccess;
     { sym_pair_kernel<P, KIND, I><<<(unsigned)grid, kThreads, SMEM, s>>>(a); note_launch(); }
     return cudaGetLastError();
 }
@@ -2204,11 +2249,15 @@ static cudaError_t launch_sym_ipt(int ipt, const SymArgs& a, cudaStream_t s) {
 
 cudaError_t launch_sym_pair(int precision, int kind, int ipt, const void* rec, const void* accrec,
                             int n, double eps2, int chunk, double* accum, int* err,
-                            long long timeout_ns, const SymFar* far, cudaStream_t s, bool skip_diag) {
+                            long long timeout_ns, const SymFar* far, cudaStream_t s, bool skip_diag,
+                            int part, int nparts) {
     if (n <= 0) return cudaSuccess;
+    if (nparts < 1 || part < 0 || part >= nparts) return cudaErrorInvalidValue;
     SymArgs a{};
     a.rec = rec; a.accrec = accrec; a.n = n; a.eps2 = eps2; a.accum = accum; a.err = err;
     a.timeout_ns = timeout_ns;
+    a.part = part;
+    a.nparts = nparts;
     a.skip_diag = skip_diag && precision == FSI_MIXED && (ipt & 128) ? 1 : 0;
     if (far && (ipt & 64)) {
         a.rel = reinterpret_cast<const float4*>(far->rel);

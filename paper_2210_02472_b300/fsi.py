@@ -42,7 +42,7 @@ EXPORTED = ["fsi_default_params", "fsi_create", "fsi_destroy", "fsi_set_params",
             "fsi_step_vjp", "fsi_step_vjp_rec", "fsi_batch_create", "fsi_batch_destroy", "fsi_batch_step",
             "fsi_batch_set_tuning", "fsi_batch_get_tuning", "fsi_batch_inject_stall", "fsi_batch_stats",
             "fsi_work_stats", "fsi_accel_noalloc", "fsi_far_stats", "fsi_get_tuning_for", "fsi_grid_stats",
-            "fsi_batch_item_stats", "fsi_timesteps_sub"]
+            "fsi_batch_item_stats", "fsi_timesteps_sub", "fsi_accel_part", "fsi_grad_part"]
 
 
 class fsi_params(C.Structure):
@@ -65,6 +65,8 @@ _lib.fsi_last_error.restype = C.c_char_p
 _lib.fsi_sync_status.argtypes = [_vp, _vp]
 _lib.fsi_accel.argtypes = [_vp, _ip, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp, _vp]
 _lib.fsi_grad.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp, _vp]
+_lib.fsi_accel_part.argtypes = [_vp, _ip, _vp, _vp, _vp, _ip, _ip, _ip, _dp, _vp, _vp]
+_lib.fsi_grad_part.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _ip, _ip, _dp, _vp, _vp]
 _lib.fsi_accel_grad.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _ip, _vp, _ip, _dp, _vp, _vp, _vp]
 _lib.fsi_pn_accel.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _dp, _vp, _ip, _vp, _ip, _vp, _vp]
 _lib.fsi_step.argtypes = [_vp, _ip, _vp, _vp, _vp, _vp, _vp, _ip, _dp, _ip, _vp]
@@ -231,6 +233,35 @@ def fsi_grad(ctx: Context, pos, mass, accg, A=None, B=None, eps2: float = 0.0, o
     _check(_lib.fsi_grad(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
                          _f64(accg, (3, N), "accg"), pa, nA, pb, nB, float(eps2),
                          _f64(out, (3, nA), "out"), _stream(stream)), "fsi_grad")
+    return out
+
+
+def fsi_accel_part(ctx: Context, pos, mass, part: int, nparts: int, A=None, eps2: float = 0.0,
+                   out=None, stream=None):
+    """Share `part` of nparts of the same-set pass acc(A <- A): (3, nA) partial sums; the
+    shares add up to fsi_accel(A <- A)."""
+    N = mass.numel()
+    pa, nA = _ids(A, N, "A")
+    if out is None:
+        out = torch.empty((3, nA), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_accel_part(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
+                               pa, nA, int(part), int(nparts), float(eps2),
+                               _f64(out, (3, nA), "out"), _stream(stream)), "fsi_accel_part")
+    return out
+
+
+def fsi_grad_part(ctx: Context, pos, mass, accg, part: int, nparts: int, A=None,
+                  eps2: float = 0.0, out=None, stream=None):
+    """Share `part` of nparts of the same-set pass G(A <- A) with the accelerations accg
+    (3, N): (3, nA) partial sums; the shares add up to fsi_grad(A <- A)."""
+    N = mass.numel()
+    pa, nA = _ids(A, N, "A")
+    if out is None:
+        out = torch.empty((3, nA), dtype=torch.float64, device=pos.device)
+    _check(_lib.fsi_grad_part(ctx.handle, N, _f64(pos, (3, N), "pos"), _f64(mass, (N,), "mass"),
+                              _f64(accg, (3, N), "accg"), pa, nA, int(part), int(nparts),
+                              float(eps2), _f64(out, (3, nA), "out"), _stream(stream)),
+           "fsi_grad_part")
     return out
 
 

@@ -15,6 +15,13 @@ against all sources.  The data exchanged between ranks is what the next pass nee
     rank), the sources are split instead and the partial acceleration and gradient sums
     are all-reduced (48 B per active particle).
 
+With `pairs=True` (and a compute that has the share form) the same-set passes of the pair
+sums and of FSI cycles are split by pairs instead of rows: every rank evaluates its share
+of the set's unordered pairs for both particles of each (Newton's third law: half the pair
+evaluations of a row split), the shares are all-reduced (24 B per particle and pass), and
+every rank kicks and drifts the whole set with the same sums, so the replicated positions
+stay identical without an all-gather.
+
 An HHS interval shards every level's active list the same way: the inter-level kicks split
 the rows of S and F, and FSI(S) is a sharded FSI cycle of S.
 
@@ -55,6 +62,12 @@ class LibfsiCompute:
 
     def grad(self, pos, mass, accg, A, B, eps2):
         return self.F.fsi_grad(self.ctx, pos, mass, accg, A, B, eps2=eps2)
+
+    def accel_part(self, pos, mass, A, part, nparts, eps2):
+        return self.F.fsi_accel_part(self.ctx, pos, mass, part, nparts, A, eps2=eps2)
+
+    def grad_part(self, pos, mass, accg, A, part, nparts, eps2):
+        return self.F.fsi_grad_part(self.ctx, pos, mass, accg, part, nparts, A, eps2=eps2)
 
     def pn_accel(self, pos, vel, mass, is_bh, c, A, B):
         return self.F.fsi_pn_accel(self.ctx, pos, vel, mass, is_bh, c, A, B)
@@ -152,10 +165,23 @@ class ShardedFSI:
     semantics), with every rank ending with the same results.  `compute` does all
     arithmetic; `ex` moves data between ranks."""
 
-    def __init__(self, compute, ex: Optional[Exchange] = None, min_rows: int = 1024):
+    def __init__(self, compute, ex: Optional[Exchange] = None, min_rows: int = 1024,
+                 pairs: bool = False):
         self.c = compute
         self.ex = ex or Exchange()
         self.min_rows = int(min_rows)
+        self.pairs = bool(pairs) and hasattr(compute, "accel_part") and hasattr(compute, "grad_part")
+
+    def _split_pairs(self) -> bool:
+        return self.pairs and self.ex.world > 1
+
+    def _acc_share(self, pos, mass, P, eps2):
+        """acc(P <- P) on every rank: this rank's share of the pairs, all-reduced."""
+        return self.ex.all_reduce_sum(self.c.accel_part(pos, mass, P, self.ex.rank, self.ex.world, eps2))
+
+    def _grad_share(self, pos, mass, accg, P, eps2):
+        return self.ex.all_reduce_sum(self.c.grad_part(pos, mass, accg, P, self.ex.rank,
+                                                       self.ex.world, eps2))
 
     # -------------------------------------------------------------- pair sums
     def _acc(self, pos, mass, A, B, eps2, p: ShardPlan):
@@ -180,6 +206,11 @@ class ShardedFSI:
         same = (A is None and B is None) or (A is not None and A is B)
         A = _ids(N, A, pos.device)
         B = A if same else _ids(N, B, pos.device)
+        if same and self._split_pairs():
+            a = self._acc_share(pos, mass, A, eps2)
+            accg = torch.zeros((3, N), dtype=pos.dtype, device=pos.device)
+            accg[:, A.long()] = a
+            return a, self._grad_share(pos, mass, accg, A, eps2)
         pa = plan(A.numel(), B.numel(), self.ex, self.min_rows)
         a = self._acc(pos, mass, A, B, eps2, pa)
         accg = torch.zeros((3, N), dtype=pos.dtype, device=pos.device)
@@ -212,6 +243,8 @@ class ShardedFSI:
         n = P.numel()
         if n == 0 or nsteps <= 0:
             return
+        if self._split_pairs():
+            return self._step_pairs(pos, vel, mass, h, nsteps, P, eps2, c, is_bh)
         lo, hi = slice_bounds(n, self.ex.world, self.ex.rank)
         Pr = P[lo:hi]
         pn = c > 0.0
@@ -250,6 +283,40 @@ class ShardedFSI:
                 pn_kick()
                 self.c.kick_drift(pos, vel, a, Pr, h / 6.0, 0.5 * h)
         self._sync_cols(vel, P, lo, hi, n)
+
+    def _step_pairs(self, pos, vel, mass, h, nsteps, P, eps2, c, is_bh):
+        """step() with its same-set passes split by pairs: every rank gets the set's full
+        sums from the all-reduced shares and kicks and drifts all of P itself (the PN1.0
+        terms, pairs with a black hole, are evaluated whole on every rank)."""
+        N = mass.numel()
+        pn = c > 0.0
+
+        def pn_kick():
+            apn = self.c.pn_accel(pos, vel, mass, is_bh, c, P, P)
+            self.c.kick_drift(pos, vel, apn, P, 0.5 * h, 0.0)
+
+        if pn:
+            pn_kick()
+        a = self._acc_share(pos, mass, P, eps2)
+        self.c.kick_drift(pos, vel, a, P, h / 6.0, 0.5 * h)
+        for k in range(nsteps):
+            last = k == nsteps - 1
+            a = self._acc_share(pos, mass, P, eps2)
+            accg = torch.zeros((3, N), dtype=pos.dtype, device=pos.device)
+            accg[:, P.long()] = a
+            g = self._grad_share(pos, mass, accg, P, eps2)
+            self.c.kick_drift(pos, vel, a, P, 2.0 * h / 3.0, 0.0)
+            self.c.kick_drift(pos, vel, g, P, (2.0 * h / 3.0) * (h * h / 24.0), 0.5 * h)
+            a = self._acc_share(pos, mass, P, eps2)
+            if not pn and not last:
+                self.c.kick_drift(pos, vel, a, P, h / 3.0, 0.5 * h)
+                continue
+            self.c.kick_drift(pos, vel, a, P, h / 6.0, 0.0)
+            if pn:
+                pn_kick()
+            if not last:
+                pn_kick()
+                self.c.kick_drift(pos, vel, a, P, h / 6.0, 0.5 * h)
 
     # -------------------------------------------------------------- HHS intervals
     def hhs_interval(self, pos, vel, mass, tau: float, eps2: float = 0.0, c: float = 0.0,

@@ -181,6 +181,45 @@ def test_accel_softened_with_coincident_points(F, prec):
 
 
 @pytest.mark.parametrize("prec", PRECS)
+@pytest.mark.parametrize("n,nparts", [(300, 3), (3000, 2), (3000, 8), (13001, 3), (40000, 5),
+                                      (200000, 2)])
+def test_pass_shares_add_up(F, prec, n, nparts):
+    """fsi_accel_part / fsi_grad_part: the nparts shares of a same-set pass (block ranges
+    of the tiled symmetric kernel; a pass in the wide form, as at 300, whole in share 0)
+    add up to fsi_accel / fsi_grad of the set and to the oracle's sums.  3000 in 8 shares:
+    more shares than blocks where the tiled form runs; 200000 (mixed): the largest size
+    class, whose float-float pairs inside each block are split the same way."""
+    if n == 200000 and prec == "fp64":
+        pytest.skip("the largest-class split is a mixed-precision kernel path")
+    c = inputs.plummer(n, 81 + n, imf="kroupa")
+    rows = np.sort(np.random.default_rng(82).choice(n, min(n, 256), replace=False)).astype(np.int32)
+    with F.Context(prec) as ctx:
+        p, m = dev(c.pos), dev(c.mass)
+        full = F.fsi_accel(ctx, p, m)
+        parts = [F.fsi_accel_part(ctx, p, m, k, nparts) for k in range(nparts)]
+        gfull = F.fsi_grad(ctx, p, m, full)
+        gparts = [F.fsi_grad_part(ctx, p, m, full, k, nparts) for k in range(nparts)]
+        assert F.fsi_sync_status(ctx) == F.FSI_OK
+        with pytest.raises(F.FsiError) as ei:
+            F.fsi_accel_part(ctx, p, m, nparts, nparts)
+        assert ei.value.code == F.FSI_ERR_ARG
+    full, gfull = host(full), host(gfull)
+    a = sum(host(t) for t in parts)
+    g = sum(host(t) for t in gparts)
+    nonzero = [bool(np.any(host(t) != 0.0)) for t in parts]
+    if n >= 13001:
+        assert all(nonzero)             # the tiled symmetric form, split into nparts
+    elif n == 300:
+        assert sum(nonzero) == 1        # the wide form: the whole pass in one share
+    else:
+        assert any(nonzero)
+    assert np.abs(a - full).max() <= 1e-13 * np.abs(full).max()
+    assert np.abs(g - gfull).max() <= 1e-13 * np.abs(gfull).max()
+    ref = oracle.acc(c.pos, c.mass, rows)
+    assert_close(a[:, rows], ref, prec, "acc shares")
+
+
+@pytest.mark.parametrize("prec", PRECS)
 @pytest.mark.parametrize("n,symmetric", [(300, True), (3000, True), (3000, False)])
 def test_coincident_unsoftened_is_reported(F, prec, n, symmetric):
     """Two distinct particles at exactly the same position with eps2 = 0: the pair terms of

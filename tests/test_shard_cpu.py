@@ -30,6 +30,17 @@ class OracleCompute:
         return torch.as_tensor(oracle.grad(pos.numpy(), mass.numpy(), accg.numpy(), A.numpy(),
                                            B.numpy(), eps2))
 
+    # a share of a same-set pass: the receivers against slice `part` of the sources (any
+    # partition of the pairs serves the exchange; libfsi's shares are blocks of its
+    # symmetric kernel)
+    def accel_part(self, pos, mass, A, part, nparts, eps2):
+        lo, hi = slice_bounds(A.numel(), nparts, part)
+        return self.accel(pos, mass, A, A[lo:hi].contiguous(), eps2)
+
+    def grad_part(self, pos, mass, accg, A, part, nparts, eps2):
+        lo, hi = slice_bounds(A.numel(), nparts, part)
+        return self.grad(pos, mass, accg, A, A[lo:hi].contiguous(), eps2)
+
     def pn_accel(self, pos, vel, mass, is_bh, c, A, B):
         return torch.as_tensor(oracle.pn_acc(pos.numpy(), vel.numpy(), mass.numpy(), is_bh.numpy(),
                                              c, A.numpy(), B.numpy()))
@@ -62,7 +73,8 @@ def _rank(rank, world, port, case, out):
     dist.init_process_group("gloo", rank=rank, world_size=world)
     oracle.set_threads(1)
     try:
-        out[rank] = CASES[case](ShardedFSI(OracleCompute(), min_rows=16))
+        name, _, mode = case.partition("+")
+        out[rank] = CASES[name](ShardedFSI(OracleCompute(), min_rows=16, pairs=mode == "pairs"))
     finally:
         dist.destroy_process_group()
 
@@ -179,6 +191,40 @@ def test_sharded_small_set_splits_sources():
         assert np.abs(a - ra).max() <= 1e-13 * np.abs(ra).max()
         assert np.abs(g - rg).max() <= 1e-13 * np.abs(rg).max()
     assert np.array_equal(outs[0][0], outs[1][0])       # every rank holds the same sums
+
+
+@pytest.mark.parametrize("world", [2, 3])
+def test_sharded_accel_grad_same_set_split_by_pairs(world):
+    """pairs=True: each rank sums a share of the set's pairs for all receivers and the
+    shares are all-reduced; the sums agree with the one-rank ones to rounding and are the
+    same on every rank."""
+    c = inputs.plummer(701, 51, imf="kroupa")
+    ra, rg = oracle.accel_grad(c.pos, c.mass)
+    outs = _run("same+pairs", world)
+    for a, g in outs:
+        assert np.abs(a - ra).max() <= 1e-13 * np.abs(ra).max()
+        assert np.abs(g - rg).max() <= 1e-13 * np.abs(rg).max()
+    assert all(np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1]) for o in outs)
+
+
+@pytest.mark.parametrize("case,world", [("steps+pairs", 2), ("steps+pairs", 3), ("steps_pn+pairs", 2)])
+def test_sharded_fsi_steps_split_by_pairs(case, world):
+    """FSI cycles with the same-set passes split by pairs: every rank kicks and drifts the
+    whole set with the all-reduced sums, so the replicas stay identical with no position
+    exchange; against the one-rank oracle (the whole set, and a subset with PN1.0)."""
+    if case.startswith("steps_pn"):
+        c = inputs.plummer(260, 56, imf="kroupa", n_bh=4)
+        P = np.sort(inputs.random_subset(260, 150, 57)).astype(np.int32)
+        P = np.union1d(P, np.nonzero(c.is_bh)[0]).astype(np.int32)
+        rp, rv = oracle.fsi_step(c.pos, c.vel, c.mass, 1e-3, P=P, c=30.0, is_bh=c.is_bh, steps=2)
+    else:
+        c = inputs.plummer(301, 55, imf="kroupa")
+        rp, rv = oracle.fsi_step(c.pos, c.vel, c.mass, 1e-3, steps=3)
+    outs = _run(case, world)
+    for p, v in outs:
+        assert np.abs(p - rp).max() <= 1e-14 * np.abs(rp).max()
+        assert np.abs(v - rv).max() <= 1e-12 * np.abs(rv).max()
+    assert all(np.array_equal(o[0], outs[0][0]) and np.array_equal(o[1], outs[0][1]) for o in outs)
 
 
 @pytest.mark.parametrize("world", [2, 3])
