@@ -253,14 +253,16 @@ def test_sharded_fsi_steps_subset_with_pn():
 
 
 @pytest.mark.parametrize("world", [2, 3])
-def test_sharded_hhs_interval_matches_oracle(world):
+@pytest.mark.parametrize("mode", ["", "+pairs"])
+def test_sharded_hhs_interval_matches_oracle(world, mode):
     """One HHS interval (Sect. 2.2) with every level's active list sharded over 2 or 3
-    ranks (row slices of the inter-level kicks and the FSI(S) cycles, gathered sums)
-    against the oracle's interval on one rank: the same level histogram, the state to
-    rounding, and the same state on every rank."""
+    ranks (row slices of the inter-level kicks and the FSI(S) cycles, gathered sums; with
+    "+pairs" the FSI(S) passes split by pairs instead, shares all-reduced) against the
+    oracle's interval on one rank: the same level histogram, the state to rounding, and
+    the same state on every rank."""
     c = inputs.plummer(300, 58, imf="kroupa")
     rp, rv, counts, code = oracle.hhs_interval(c.pos, c.vel, c.mass, 1.0 / 16)
-    outs = _run("hhs", world)
+    outs = _run("hhs" + mode, world)
     used = np.nonzero(counts)[0].max() + 1
     for p, v, lv, hit in outs:
         assert lv[:used] == list(counts[:used]) and not hit
