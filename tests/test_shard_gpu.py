@@ -3,7 +3,9 @@
 Two gloo ranks share cuda:0 (independent contexts and kernels; no kernel waits on the other
 rank, the exchange goes through host memory), and one NCCL rank runs the same path through
 NCCL collectives; both against the oracle and the one-rank library calls: the pair sums of
-a set, FSI cycles with PN kicks, and an HHS interval with every level's list sharded.
+a set, FSI cycles with PN kicks, and an HHS interval with every level's list sharded.  A
+third run takes the same-set passes split by pairs (fsi_accel_part / fsi_grad_part, shares
+all-reduced), the pair sums on a set of 13001 that the symmetric kernel splits.
 """
 import os
 import socket
@@ -27,7 +29,7 @@ def _free_port():
     return port
 
 
-def _rank(rank, world, port, backend, out):
+def _rank(rank, world, port, backend, out, pairs):
     import torch.distributed as dist
     os.environ.update({"MASTER_ADDR": "127.0.0.1", "MASTER_PORT": str(port)})
     torch.cuda.set_device(0)
@@ -38,8 +40,8 @@ def _rank(rank, world, port, backend, out):
         res = {}
         for prec in ("fp64", "mixed"):
             with F.Context(prec) as ctx:
-                sh = ShardedFSI(LibfsiCompute(ctx), min_rows=64)
-                c = inputs.plummer(3001, 61, imf="kroupa")
+                sh = ShardedFSI(LibfsiCompute(ctx), min_rows=64, pairs=pairs)
+                c = inputs.plummer(13001 if pairs else 3001, 61, imf="kroupa")
                 a, g = sh.accel_grad(torch.as_tensor(c.pos).cuda(), torch.as_tensor(c.mass).cuda())
                 res[prec + "_ag"] = (a.cpu().numpy(), g.cpu().numpy())
                 c = inputs.plummer(900, 62, imf="kroupa", n_bh=3)
@@ -60,12 +62,13 @@ def _rank(rank, world, port, backend, out):
         dist.destroy_process_group()
 
 
-def _run(world, backend):
+def _run(world, backend, pairs=False):
     ctx = mp.get_context("spawn")
     with ctx.Manager() as m:
         out = m.dict()
         port = _free_port()
-        procs = [ctx.Process(target=_rank, args=(r, world, port, backend, out)) for r in range(world)]
+        procs = [ctx.Process(target=_rank, args=(r, world, port, backend, out, pairs))
+                 for r in range(world)]
         for p in procs:
             p.start()
         for p in procs:
@@ -74,9 +77,9 @@ def _run(world, backend):
         return [out[r] for r in range(world)]
 
 
-def _check(outs):
+def _check(outs, n_ag=3001):
     oracle.set_threads(os.cpu_count() or 1)
-    c = inputs.plummer(3001, 61, imf="kroupa")
+    c = inputs.plummer(n_ag, 61, imf="kroupa")
     ra, rg = oracle.accel_grad(c.pos, c.mass)
     d = inputs.plummer(900, 62, imf="kroupa", n_bh=3)
     rp, rv = oracle.fsi_step(d.pos, d.vel, d.mass, 1e-3, c=40.0, is_bh=d.is_bh, steps=3)
@@ -110,3 +113,7 @@ def test_sharded_libfsi_two_gloo_ranks_on_one_gpu():
 
 def test_sharded_libfsi_one_nccl_rank():
     _check(_run(1, "nccl"))
+
+
+def test_sharded_libfsi_pairs_two_gloo_ranks_on_one_gpu():
+    _check(_run(2, "gloo", pairs=True), n_ag=13001)
