@@ -896,8 +896,10 @@ def run_sharded(args):
     """The i-sharded FSI cycle (paper_2210_02472_b300.shard) of the headline workload over
     all ranks: every rank kicks, drifts and sums the pairs of its slice of the set, with
     NCCL all-gathers of the positions after drifts and of the accelerations before the
-    gradient pass.  Strong scaling: the total work (one set of N) is fixed; value = the
-    set's interactions per step / the slowest rank's time."""
+    gradient pass; with --shard-pairs the same-set passes are split by pairs instead (every
+    rank a share of the unordered pairs for both particles, the shares all-reduced, every
+    rank kicking and drifting the whole set).  Strong scaling: the total work (one set of
+    N) is fixed; value = the set's interactions per step / the slowest rank's time."""
     import torch
     rank, ws, local, dist = dist_init()
     torch.cuda.set_device(local)
@@ -916,7 +918,7 @@ def run_sharded(args):
     h, cl = 1.0 / 1024, 1e4
     ctx = F.Context(args.precision, c=cl)
     F.fsi_reserve(ctx, N, N)
-    sh = ShardedFSI(LibfsiCompute(ctx), Exchange())
+    sh = ShardedFSI(LibfsiCompute(ctx), Exchange(), pairs=args.shard_pairs)
 
     def step():
         sh.step(pos, vel, mass, h, nsteps=1, c=cl, is_bh=bh)
@@ -952,9 +954,13 @@ def run_sharded(args):
         "higher_is_better": True, "scaling": "strong", "vs_baseline": None,
         "dtype": "f32+f64" if args.precision == "mixed" else "f64", "data": "synthetic",
         "config": {"workload": args.workload, "n": N, "precision": args.precision,
-                   "step": "one FSI cycle of all N + PN1.0 half-kicks, receivers sharded over "
-                           "ranks (one-sided pair passes over each rank's slice)",
-                   "c": cl, "h": h, "parallelism": f"i-sharded x{ws}"},
+                   "step": ("one FSI cycle of all N + PN1.0 half-kicks, the same-set passes "
+                            "split by pairs (shares of the symmetric kernel, all-reduced)"
+                            if args.shard_pairs else
+                            "one FSI cycle of all N + PN1.0 half-kicks, receivers sharded over "
+                            "ranks (one-sided pair passes over each rank's slice)"),
+                   "c": cl, "h": h,
+                   "parallelism": f"{'pair' if args.shard_pairs else 'i'}-sharded x{ws}"},
         "gpu_launches": launches, "clocks": clocks,
     }
     if rank == 0:
@@ -1005,6 +1011,8 @@ def main():
     ap.add_argument("--hhs-small-max", type=int, default=0, help="HHS mode: fsi_params.hhs_small_max")
     ap.add_argument("--order-min", type=int, default=0, help="HHS mode: fsi_params.order_min")
     ap.add_argument("--hhs-grid-max", type=int, default=0, help="HHS mode: fsi_params.hhs_grid_max")
+    ap.add_argument("--shard-pairs", action="store_true",
+                    help="sharded mode: split the same-set passes by pairs, not by receivers")
     ap.add_argument("--grid-profile", action="store_true",
                     help="HHS mode: phase profile of the cooperative-launch recursions (fsi_grid_stats)")
     args = ap.parse_args()
