@@ -620,65 +620,9 @@ cudaError_t launch_pn_lists(long long N, const double* pos, const double* vel, c
 }
 
 // ---------------------------------------------------------------------------------
-// Small O(n^2) FP64 loops (time steps, energy): thread per i, sources through shared
-// memory in plain cooperative tiles.
+// Small O(n^2) FP64 loop (energy): thread per i, sources through shared memory in plain
+// cooperative tiles.
 constexpr int kAuxTile = 128;
-
-// Time steps (Sect. 3.4), FP64: thread per i, sources through shared memory, the
-// division-free pair update of step_pair (pair_math.cuh).
-// Receivers: entries [i_off, i_off + n_i) of the compact set (step[k] for entry i_off + k);
-// sources: all n entries.
-__global__ void timesteps_kernel(int n, const double* __restrict__ xc, const double* __restrict__ vc,
-                                 const double* __restrict__ mc, double eta_ff, double eta_fb,
-                                 double eta_jerk, double eps2, double* __restrict__ step, int* err,
-                                 int i_off, int n_i) {
-    __shared__ double sx[kAuxTile], sy[kAuxTile], sz[kAuxTile], su[kAuxTile], sv[kAuxTile],
-        sw[kAuxTile], sm[kAuxTile];
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    const int ii = i_off + min(k, n_i - 1);
-    const double xi = xc[ii], yi = xc[(size_t)n + ii], zi = xc[2 * (size_t)n + ii];
-    const double ui = vc[ii], vi = vc[(size_t)n + ii], wi = vc[2 * (size_t)n + ii];
-    const double mi = mc[ii];
-    StepAcc<double> acc;
-    acc.init();
-    bool coincident = false;
-    for (int j0 = 0; j0 < n; j0 += kAuxTile) {
-        __syncthreads();
-        for (int t = threadIdx.x; t < kAuxTile; t += blockDim.x) {
-            const int j = j0 + t;
-            if (j < n) {
-                sx[t] = xc[j]; sy[t] = xc[(size_t)n + j]; sz[t] = xc[2 * (size_t)n + j];
-                su[t] = vc[j]; sv[t] = vc[(size_t)n + j]; sw[t] = vc[2 * (size_t)n + j];
-                sm[t] = mc[j];
-            }
-        }
-        __syncthreads();
-        const int cnt = min(kAuxTile, n - j0);
-        for (int t = 0; t < cnt; ++t) {
-            if (j0 + t == ii) continue;
-            const double dx = sx[t] - xi, dy = sy[t] - yi, dz = sz[t] - zi;
-            const double d2 = dx * dx + dy * dy + dz * dz;
-            if (d2 == 0.0) { coincident = true; continue; }
-            const double s2 = d2 + eps2;
-            const double y = rsqrt_f64(s2);
-            step_pair<double>(acc, dx, dy, dz, su[t] - ui, sv[t] - vi, sw[t] - wi, d2, sm[t], mi + sm[t], y);
-        }
-    }
-    if (k >= n_i) return;
-    if (coincident) set_error(err, FSI_ERR_COINCIDENT);
-    step[k] = step_finish<double>(acc, eta_ff, eta_fb, eta_jerk);
-}
-
-cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
-                             double eta_ff, double eta_fb, double eta_jerk, double eps2,
-                             double* step, int* err, cudaStream_t s, int i_off, int n_i) {
-    if (n_i < 0) n_i = n;
-    if (n <= 0 || n_i <= 0) return cudaSuccess;
-    { timesteps_kernel<<<blocks_for(n_i, kAuxTile), kAuxTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb,
-                                                                    eta_jerk, eps2, step, err, i_off,
-                                                                    n_i); note_launch(); }
-    return cudaGetLastError();
-}
 
 // Gradient and velocity-per-acceleration time steps (Sect. 3.4, Eqs. dt-nabla1,
 // dt-nabla2, vel-acc-crit) of a compact set from its velocities v, accelerations a and

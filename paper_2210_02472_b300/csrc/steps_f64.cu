@@ -120,6 +120,18 @@ __device__ __forceinline__ void sf_pair(const D4& pj, const D4& vj, const SfRecv
     }
 }
 
+// The step from the minima (as ratios) and the a and j sums (Sect. 3.4).
+__device__ __forceinline__ double sf_finish(double ff, double fb, double ax, double ay, double az,
+                                            double jx, double jy, double jz, double eta_ff,
+                                            double eta_fb, double eta_jerk) {
+    double e = INFINITY;
+    if (ff < INFINITY) e = eta_ff * sqrt(sqrt(ff));
+    if (fb < INFINITY) e = fmin(e, eta_fb * sqrt(fb));
+    const double jn = sqrt(jx * jx + jy * jy + jz * jz);
+    if (jn > 0.0) e = fmin(e, eta_jerk * sqrt(ax * ax + ay * ay + az * az) / jn);
+    return e;
+}
+
 // One particle's accumulators into the set's: minima as ratio bits, sums by red.add.
 __device__ __forceinline__ void sf_put(unsigned long long* mins, double* sums, int n, int i,
                                        const SfAcc& s) {
@@ -309,12 +321,7 @@ __global__ void steps_f64_finalize_kernel(int n, const unsigned long long* __res
     const double ax = sums[i], ay = sums[(size_t)n + i], az = sums[2 * (size_t)n + i];
     const double jx = sums[3 * (size_t)n + i], jy = sums[4 * (size_t)n + i], jz = sums[5 * (size_t)n + i];
     if (!(isfinite(ax) && isfinite(ay) && isfinite(az))) set_error(err, FSI_ERR_NONFINITE);
-    double e = INFINITY;
-    if (ff < INFINITY) e = eta_ff * sqrt(sqrt(ff));
-    if (fb < INFINITY) e = fmin(e, eta_fb * sqrt(fb));
-    const double jn = sqrt(jx * jx + jy * jy + jz * jz);
-    if (jn > 0.0) e = fmin(e, eta_jerk * sqrt(ax * ax + ay * ay + az * az) / jn);
-    step[i] = e;
+    step[i] = sf_finish(ff, fb, ax, ay, az, jx, jy, jz, eta_ff, eta_fb, eta_jerk);
 }
 
 size_t steps_sym_f64_work_bytes(int n) { return (size_t)n * 8 * sizeof(double); }
@@ -359,6 +366,72 @@ cudaError_t launch_steps_sym_f64(int N, const double* pos, const double* vel, co
     else { steps_sym_f64_kernel<false><<<(unsigned)grid, kSfThreads, kSfSmem, s>>>(a); note_launch(); }
     { steps_f64_finalize_kernel<<<(n + 255) / 256, 256, 0, s>>>(n, a.mins, a.sums, eta_ff, eta_fb,
                                                                 eta_jerk, step, err); note_launch(); }
+    return cudaGetLastError();
+}
+
+// =================================================================================
+// One-sided form: receivers [i_off, i_off + n_i) of a compact set (3 x n SoA positions and
+// velocities, masses) against all n members, every pair evaluated by its receiver: a
+// receiver slice of i-sharded time steps, sets below the symmetric form's size, or
+// `symmetric` off.  Thread per receiver, sources through shared memory in tiles, the
+// receiver side of sf_pair (the same fractions and integer compares), the step finished in
+// the thread (step[k] for entry i_off + k).
+constexpr int kSfRowTile = 128;
+
+template <bool SOFT>
+__global__ void __launch_bounds__(kSfRowTile) steps_f64_rows_kernel(
+    int n, const double* __restrict__ xc, const double* __restrict__ vc,
+    const double* __restrict__ mc, double eta_ff, double eta_fb, double eta_jerk, double eps2,
+    double* __restrict__ step, int* err, int i_off, int n_i) {
+    __shared__ D4 sp[kSfRowTile], sv[kSfRowTile];
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int ii = i_off + min(k, n_i - 1);            // a thread past n_i repeats the last
+    SfRecv p;
+    p.x = xc[ii]; p.y = xc[(size_t)n + ii]; p.z = xc[2 * (size_t)n + ii];
+    p.u = vc[ii]; p.v = vc[(size_t)n + ii]; p.w = vc[2 * (size_t)n + ii];
+    p.m = mc[ii];
+    SfAcc acc;
+    acc.init();
+    bool coincident = false;
+    for (int j0 = 0; j0 < n; j0 += kSfRowTile) {
+        __syncthreads();
+        {
+            const int j = j0 + (int)threadIdx.x;
+            if (j < n) {
+                sp[threadIdx.x] = make_d4(xc[j], xc[(size_t)n + j], xc[2 * (size_t)n + j], mc[j]);
+                sv[threadIdx.x] = make_d4(vc[j], vc[(size_t)n + j], vc[2 * (size_t)n + j], 0.0);
+            }
+        }
+        __syncthreads();
+        const int cnt = min(kSfRowTile, n - j0);
+        if (ii >= j0 && ii < j0 + cnt) {
+            for (int t = 0; t < cnt; ++t)
+                if (j0 + t != ii) sf_pair<SOFT, false>(sp[t], sv[t], p, eps2, acc, acc, coincident);
+        } else {
+#pragma unroll 4
+            for (int t = 0; t < cnt; ++t) sf_pair<SOFT, false>(sp[t], sv[t], p, eps2, acc, acc, coincident);
+        }
+    }
+    if (k >= n_i) return;
+    if (coincident) set_error(err, FSI_ERR_COINCIDENT);
+    step[k] = sf_finish(frac_ratio(acc.ffn, acc.ffd), frac_ratio(acc.fbn, acc.fbd), acc.ax, acc.ay,
+                        acc.az, acc.jx, acc.jy, acc.jz, eta_ff, eta_fb, eta_jerk);
+}
+
+cudaError_t launch_timesteps(int n, const double* xc, const double* vc, const double* mc,
+                             double eta_ff, double eta_fb, double eta_jerk, double eps2,
+                             double* step, int* err, cudaStream_t s, int i_off, int n_i) {
+    if (n_i < 0) n_i = n;
+    if (n <= 0 || n_i <= 0) return cudaSuccess;
+    const unsigned grid = (unsigned)((n_i + kSfRowTile - 1) / kSfRowTile);
+    if (eps2 > 0.0) {
+        steps_f64_rows_kernel<true><<<grid, kSfRowTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb, eta_jerk,
+                                                                 eps2, step, err, i_off, n_i);
+    } else {
+        steps_f64_rows_kernel<false><<<grid, kSfRowTile, 0, s>>>(n, xc, vc, mc, eta_ff, eta_fb, eta_jerk,
+                                                                  eps2, step, err, i_off, n_i);
+    }
+    note_launch();
     return cudaGetLastError();
 }
 
