@@ -1,5 +1,6 @@
-// steps_f64.cu -- time steps of a set against itself (Sect. 3.4) in FP64, every unordered
-// pair of the set evaluated once.
+// steps_f64.cu -- time steps of a set against itself (Sect. 3.4) in FP64: the symmetric
+// form (every unordered pair of the set evaluated once) and, at the end of the file, the
+// one-sided form for receiver slices and small sets with the same pair update.
 //
 // For receiver i over the other members j of the set (d = x_j - x_i, u = v_j - v_i,
 // s^2 = |d|^2 + eps^2):
